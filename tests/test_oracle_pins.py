@@ -1,0 +1,531 @@
+"""CPU pins of the FP64 oracle against closed forms, textbook identities and
+library routines (paper Sec. III-B Eq. 1-3, Sec. III-C, Sec. III-D).
+
+Each test fixes something the mathematics fixes independently of the oracle's
+own code, chosen so that a dropped term, a flipped sign or a transposed block
+in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2503_09203_b300 import vehicles, workloads
+
+G = 9.81
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def env_from_class(c, Vc=(0.0, 0.0, 0.0), target=(0.0, 0.0, 0.0), **over):
+    e = dict(cls=0, mass=c["mass"], Ig=np.array(c["Ig"]), rg=np.array(c["rg"]), rb=np.array(c["rb"]),
+             W=c["mass"] * G, B=c["buoy_ratio"] * c["mass"] * G, Ma=np.array(c["Ma"]),
+             dl=np.array(c["dl"]), dq=np.array(c["dq"]), Vc=np.array(Vc, float),
+             target=np.array(target, float))
+    e.update(over)
+    return e
+
+
+def run(c, e, state, actions, dt, K, obs=False):
+    envs = oracle.make_envs({k: np.asarray(v)[None] if k != "cls" else np.array([0], np.int32)
+                             for k, v in e.items()})
+    s = np.array(state, dtype=np.float64).reshape(1, 21).copy()
+    a = np.asarray(actions, dtype=np.float32)
+    if a.ndim == 1:
+        a = a.reshape(1, 1, 8)
+    return oracle.rollout([c], envs, s, a, dt, K, obs=obs)
+
+
+def rest_state(q=(1.0, 0.0, 0.0, 0.0), nu=(0.0,) * 6, p=(0.0, 0.0, 0.0), n=(0.0,) * 8):
+    return np.array(list(p) + list(q) + list(nu) + list(n), dtype=np.float64)
+
+
+def quiet_env(c, **over):
+    """No damping, no restoring (neutral, CoB at CoG), no current."""
+    return env_from_class(c, dl=np.zeros(6), dq=np.zeros(6), rb=np.zeros(3), **over)
+
+
+def steps(c, e, s0, n_steps, dt, K=1, action=None):
+    a = np.zeros((n_steps, 1, 8), np.float32)
+    if action is not None:
+        a[:, 0, :len(action)] = action
+    traj = [np.array(s0, float)]
+    s = np.array(s0, float).reshape(1, 21)
+    for t in range(n_steps):
+        s, _, _ = run(c, e, s, a[t:t + 1], dt, K)
+        traj.append(s[0].copy())
+    return np.array(traj)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based generator (Salmon et al., SC'11) vs numpy's Philox4x64-10.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("key,ctr", [((0, 0), (1, 0, 0, 0)), ((123, 456), (6, 0, 0, 0)),
+                                     ((0x4D47, 1), (17, 3, 0, 0)), ((2**64 - 1, 2**63), (1, 2**40, 9, 7))])
+def test_philox_matches_numpy(key, ctr):
+    # numpy's Philox(counter=c) emits the block of counter c + 1.
+    g = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                         counter=np.array((ctr[0] - 1,) + tuple(ctr[1:]), dtype=np.uint64))
+    ref = [int(v) for v in g.random_raw(4)]
+    assert oracle.philox4x64(ctr, key) == ref
+
+
+def test_action_grid():
+    vals = np.array([oracle.action(7, e, t, i) for e in range(3) for t in range(5) for i in range(8)])
+    assert np.all(vals >= -1.0) and np.all(vals < 1.0)
+    assert np.all((vals.astype(np.float64) + 1.0) * 2 ** 23 == np.round((vals.astype(np.float64) + 1.0) * 2 ** 23))
+
+
+# ---------------------------------------------------------------------------
+# Kinematics: R(q) against scipy's rotation and the ZYX Euler matrix.
+# ---------------------------------------------------------------------------
+def test_rotation_matches_scipy_euler_zyx():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        phi, th, psi = rng.uniform(-3, 3), rng.uniform(-1.5, 1.5), rng.uniform(-3, 3)
+        rot = Rotation.from_euler("ZYX", [psi, th, phi])
+        x, y, z, w = rot.as_quat()
+        R = oracle.rotation([w, x, y, z])
+        cz, sz, cy, sy, cx, sx = math.cos(psi), math.sin(psi), math.cos(th), math.sin(th), math.cos(phi), math.sin(phi)
+        Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+        Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+        Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+        np.testing.assert_allclose(R, Rz @ Ry @ Rx, atol=1e-14)
+        np.testing.assert_allclose(R, rot.as_matrix(), atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Restoring forces against Fossen's Euler-angle closed form (g(eta), Eq. 1).
+# ---------------------------------------------------------------------------
+def test_restoring_matches_fossen_closed_form():
+    rng = np.random.default_rng(2)
+    c = vehicles.heavy8()
+    for _ in range(40):
+        rg = rng.uniform(-0.05, 0.05, 3)
+        rb = rng.uniform(-0.05, 0.05, 3)
+        W, B = rng.uniform(50, 150), rng.uniform(50, 150)
+        e = env_from_class(c, rg=rg, rb=rb, W=W, B=B)
+        phi, th, psi = rng.uniform(-3, 3), rng.uniform(-1.5, 1.5), rng.uniform(-3, 3)
+        x, y, z, w = Rotation.from_euler("ZYX", [psi, th, phi]).as_quat()
+        g = oracle.restoring(e, [w, x, y, z])
+        xg, yg, zg = rg
+        xb, yb, zb = rb
+        sf, cf, st, ct = math.sin(phi), math.cos(phi), math.sin(th), math.cos(th)
+        ref = np.array([
+            (W - B) * st,
+            -(W - B) * ct * sf,
+            -(W - B) * ct * cf,
+            -(yg * W - yb * B) * ct * cf + (zg * W - zb * B) * ct * sf,
+            (zg * W - zb * B) * st + (xg * W - xb * B) * ct * cf,
+            -(xg * W - xb * B) * ct * sf - (yg * W - yb * B) * st,
+        ])
+        np.testing.assert_allclose(g, ref, atol=1e-11, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Coriolis-centripetal terms: skew-symmetry (passivity) and Newton-Euler.
+# ---------------------------------------------------------------------------
+def test_coriolis_passivity_and_newton_euler():
+    rng = np.random.default_rng(3)
+    c = vehicles.heavy8()
+    for _ in range(40):
+        rg = rng.uniform(-0.05, 0.05, 3)
+        e = env_from_class(c, rg=rg, Ma=rng.uniform(0.1, 10, 6))
+        nu = rng.uniform(-2, 2, 6)
+        Crb, Ca = oracle.coriolis(e, nu)
+        M = oracle.mass_matrix(e)
+        scale = np.abs(M).max() * (nu @ nu)
+        assert abs(nu @ Crb @ nu) <= 1e-12 * scale
+        assert abs(nu @ Ca @ nu) <= 1e-12 * scale
+        # Newton-Euler about the body origin with CoG at r_g (textbook):
+        # force  m (w x v + w x (w x r_g)),  moment  w x (I_o w) + m r_g x (w x v).
+        m = e["mass"]
+        v, w = nu[:3], nu[3:]
+        S = np.array([[0, -rg[2], rg[1]], [rg[2], 0, -rg[0]], [-rg[1], rg[0], 0]])
+        Io = np.diag(e["Ig"]) - m * S @ S
+        f = m * (np.cross(w, v) + np.cross(w, np.cross(w, rg)))
+        mom = np.cross(w, Io @ w) + m * np.cross(rg, np.cross(w, v))
+        np.testing.assert_allclose(Crb @ nu, np.concatenate([f, mom]), atol=1e-12 * scale)
+        # Added-mass terms with diagonal A: Kirchhoff's [w x A1 v ; v x A1 v + w x A2 w].
+        A = np.array(e["Ma"])
+        ref = np.concatenate([np.cross(w, A[:3] * v), np.cross(v, A[:3] * v) + np.cross(w, A[3:] * w)])
+        np.testing.assert_allclose(Ca @ nu, ref, atol=1e-12 * scale)
+
+
+# ---------------------------------------------------------------------------
+# Free motion: Kirchhoff impulse and energy.
+# ---------------------------------------------------------------------------
+def _free_drift(h, T=1.0):
+    c = vehicles.heavy8()
+    e = quiet_env(c)
+    nu0 = (0.4, -0.3, 0.2, 0.6, -0.5, 0.7)
+    n = int(round(T / h))
+    tr = steps(c, e, rest_state(nu=nu0), n, h)
+    M = np.concatenate([c["mass"] + np.array(c["Ma"][:3]), np.array(c["Ig"]) + np.array(c["Ma"][3:])])
+    out = []
+    for s in (tr[0], tr[-1]):
+        R = oracle.rotation(s[3:7])
+        P = R @ (M[:3] * s[7:10])
+        L = R @ (M[3:] * s[10:13]) + np.cross(s[0:3], P)
+        ke = 0.5 * np.sum(M * s[7:13] ** 2)
+        out.append((P, L, ke))
+    dP = np.linalg.norm(out[1][0] - out[0][0]) / np.linalg.norm(out[0][0])
+    dL = np.linalg.norm(out[1][1] - out[0][1]) / np.linalg.norm(out[0][1])
+    dE = (out[1][2] - out[0][2]) / out[0][2]
+    return dP, dL, dE
+
+
+def test_free_motion_impulse_and_energy_first_order():
+    dP1, dL1, dE1 = _free_drift(2e-3)
+    dP2, dL2, dE2 = _free_drift(1e-3)
+    # Inertial linear and angular impulse (Kirchhoff) are conserved by the
+    # continuous law; the discrete map drifts at first order in h.
+    for a, b in ((dP1, dP2), (dL1, dL2)):
+        assert a < 0.05 and 1.6 < a / b < 2.4
+    # Explicit Euler on a skew-symmetric (gyroscopic) term adds energy: > 0, O(h).
+    assert dE1 > 0 and dE2 > 0
+    assert dE1 < 0.05 and 1.6 < dE1 / dE2 < 2.4
+
+
+def test_monotone_energy_decay_with_damping():
+    c = vehicles.heavy8()
+    e = env_from_class(c, rb=np.zeros(3))
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        nu0 = rng.uniform(-1, 1, 6)
+        nu0 /= max(1.0, np.abs(nu0).max())
+        tr = steps(c, e, rest_state(nu=nu0), 200, 0.01)
+        M = np.concatenate([c["mass"] + np.array(c["Ma"][:3]), np.array(c["Ig"]) + np.array(c["Ma"][3:])])
+        ke = 0.5 * np.sum(M * tr[:, 7:13] ** 2, axis=1)
+        assert np.all(np.diff(ke) < 0)
+
+
+def test_linear_surge_decay_is_discrete_exact():
+    c = vehicles.heavy8()
+    e = env_from_class(c, dq=np.zeros(6), rb=np.zeros(3))
+    h, u0, n = 0.01, 0.8, 300
+    tr = steps(c, e, rest_state(nu=(u0, 0, 0, 0, 0, 0)), n, h)
+    ref = u0 * (1.0 - h * c["dl"][0] / (c["mass"] + c["Ma"][0])) ** np.arange(n + 1)
+    np.testing.assert_allclose(tr[:, 7], ref, rtol=1e-13, atol=0)
+    assert np.all(tr[:, 8:13] == 0.0)
+
+
+def test_steady_surge_speed_closed_form():
+    c = dict(vehicles.heavy8())
+    c.update(n_thr=2, thr_pos=[(0.0, 0.1, 0.0), (0.0, -0.1, 0.0)], thr_dir=[(1.0, 0.0, 0.0)] * 2,
+             k_f=[30.0, 30.0], T_rotor=[0.05, 0.05], deadzone=[0.0, 0.0])
+    e = env_from_class(c)
+    for cmd in (0.75, -0.5):
+        Tn = 2 * c["k_f"][0] * cmd * abs(cmd)
+        dl, dq = c["dl"][0], c["dq"][0]
+        u_star = math.copysign((-dl + math.sqrt(dl * dl + 4 * dq * abs(Tn))) / (2 * dq), Tn)
+        tr = steps(c, e, rest_state(), 3000, 0.01, action=[cmd, cmd])
+        assert abs(tr[-1, 7] - u_star) <= 1e-9 * abs(u_star)
+        assert np.all(np.abs(tr[-1, 8:13]) < 1e-12)
+
+
+def test_rest_stays_rest_bit_exact():
+    c = vehicles.heavy8()
+    e = env_from_class(c)
+    s0 = rest_state(p=(1.25, -2.5, 3.0))
+    tr = steps(c, e, s0, 100, 0.01)
+    assert np.array_equal(tr[-1], s0)
+
+
+def test_small_roll_period():
+    c = vehicles.heavy8()
+    e = env_from_class(c, dl=np.zeros(6), dq=np.zeros(6))
+    phi0 = math.radians(1.0)
+    q0 = (math.cos(phi0 / 2), math.sin(phi0 / 2), 0.0, 0.0)
+    h = 5e-4
+    n = int(6.0 / h)
+    tr = steps(c, e, rest_state(q=q0), n, h)
+    w, x, y, z = tr[:, 3], tr[:, 4], tr[:, 5], tr[:, 6]
+    roll = np.arctan2(2 * (w * x + y * z), 1 - 2 * (x * x + y * y))
+    t = np.arange(n + 1) * h
+    cross = [t[i] - roll[i] * h / (roll[i + 1] - roll[i]) for i in range(n) if roll[i] > 0 >= roll[i + 1]]
+    period = np.mean(np.diff(cross))
+    zb = -c["rb"][2]
+    ref = 2 * math.pi * math.sqrt((c["Ig"][0] + c["Ma"][3]) / (c["buoy_ratio"] * c["mass"] * G * zb))
+    assert abs(period - ref) / ref < 0.005
+
+
+def test_rotor_first_order_step():
+    c = vehicles.heavy8()
+    e = env_from_class(c)
+    dt, K, cmd = 0.01, 4, 0.6
+    h = dt / K
+    alpha = 1.0 - math.exp(-h / c["T_rotor"][0])
+    a = np.zeros((1, 1, 8), np.float32)
+    a[0, 0, :] = cmd
+    s = rest_state().reshape(1, 21)
+    for t in range(1, 6):
+        s, _, _ = run(c, e, s, a, dt, K)
+        k = t * K
+        ref = float(np.float32(cmd)) * (1 - (1 - alpha) ** k)
+        np.testing.assert_allclose(s[0, 13:21], ref, rtol=1e-13)
+
+
+def test_zero_order_rotor_and_clamp():
+    c = dict(vehicles.heavy8(), T_rotor=[0.0] * 8)
+    e = env_from_class(c)
+    a = np.array([[[1.7, -3.0, 0.25, -0.5, 1.0, -1.0, 0.0, 0.9]]], np.float32)
+    s, _, _ = run(c, e, rest_state().reshape(1, 21), a, 0.01, 2)
+    np.testing.assert_array_equal(s[0, 13:21], np.clip(a[0, 0].astype(np.float64), -1, 1))
+
+
+def test_drift_with_current():
+    c = vehicles.heavy8()
+    Vc = np.array([0.3, -0.2, 0.0])
+    e = env_from_class(c, Vc=Vc)
+    tr = steps(c, e, rest_state(), 6000, 0.01)
+    s = tr[-1]
+    R = oracle.rotation(s[3:7])
+    np.testing.assert_allclose(R @ s[7:10], Vc, atol=1e-7)
+    np.testing.assert_allclose(s[10:13], 0.0, atol=1e-7)
+
+
+def test_two_forms_of_current_law_agree():
+    rng = np.random.default_rng(5)
+    c = vehicles.heavy8()
+    for _ in range(50):
+        e = env_from_class(c, rg=rng.uniform(-0.05, 0.05, 3), Vc=rng.uniform(-0.5, 0.5, 3),
+                           Ma=rng.uniform(0.1, 10, 6), W=rng.uniform(90, 130))
+        s = rest_state(q=tuple(Rotation.random(random_state=rng).as_quat()[[3, 0, 1, 2]]),
+                       nu=tuple(rng.uniform(-1, 1, 6)))
+        tau = rng.uniform(-50, 50, 6)
+        a0 = oracle.acceleration(e, s, tau, form=0)
+        a1 = oracle.acceleration(e, s, tau, form=1)
+        np.testing.assert_allclose(a0, a1, rtol=0, atol=1e-13 * max(1.0, np.abs(a0).max()))
+
+
+def test_quaternion_unit_and_pure_yaw_closed_form():
+    c = vehicles.heavy8()
+    e = quiet_env(c)
+    h, wz, n = 0.01, 0.5, 400
+    tr = steps(c, e, rest_state(nu=(0, 0, 0, 0, 0, wz)), n, h)
+    w, z = tr[:, 3], tr[:, 6]
+    yaw = 2 * np.unwrap(np.arctan2(z, w) * 2) / 2
+    # Normalising q + h/2 q (x) (0, w) turns by 2 atan(h w / 2) per step exactly.
+    np.testing.assert_allclose(yaw, np.arange(n + 1) * 2 * math.atan(h * wz / 2), atol=1e-12)
+    assert abs(yaw[-1] - wz * n * h) < 1e-4
+    # Random motion keeps |q| = 1.
+    rng = np.random.default_rng(6)
+    a = workloads.actions(6, 200, 1)
+    envs = oracle.make_envs({k: np.asarray(v)[None] if k != "cls" else np.array([0], np.int32)
+                             for k, v in env_from_class(c).items()})
+    s = rest_state(nu=tuple(rng.uniform(-1, 1, 6))).reshape(1, 21)
+    s, _, _ = oracle.rollout([c], envs, s, a, 0.01, 4)
+    assert abs(np.linalg.norm(s[0, 3:7]) - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Brute force: one substep expanded by hand in numpy (product forms, r_g = 0).
+# ---------------------------------------------------------------------------
+def _brute_substep(c, e, s, cmd, h):
+    s = np.array(s, float)
+    n = s[13:21].copy()
+    for i in range(c["n_thr"]):
+        alpha = 1 - math.exp(-h / c["T_rotor"][i])
+        n[i] = n[i] + alpha * (cmd[i] - n[i])
+    tau = np.zeros(6)
+    for i in range(c["n_thr"]):
+        f = c["k_f"][i] * n[i] * abs(n[i])
+        d = np.array(c["thr_dir"][i]); r = np.array(c["thr_pos"][i])
+        tau[:3] += f * d
+        tau[3:] += np.cross(r, f * d)
+    w0, x, y, z = s[3:7]
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w0 * z), 2 * (x * z + w0 * y)],
+                  [2 * (x * y + w0 * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w0 * x)],
+                  [2 * (x * z - w0 * y), 2 * (y * z + w0 * x), 1 - 2 * (x * x + y * y)]])
+    v, w = s[7:10], s[10:13]
+    vc = R.T @ e["Vc"]
+    vr = v - vc
+    A = np.array(e["Ma"])
+    m, Ig = e["mass"], np.array(e["Ig"])
+    crb = np.concatenate([m * np.cross(w, v), np.cross(w, Ig * w)])
+    a1, a2 = A[:3] * vr, A[3:] * w
+    ca = np.concatenate([np.cross(w, a1), np.cross(vr, a1) + np.cross(w, a2)])
+    cur = np.concatenate([A[:3] * np.cross(w, vc), np.zeros(3)])
+    nur = np.concatenate([vr, w])
+    dmp = np.array(e["dl"]) * nur + np.array(e["dq"]) * np.abs(nur) * nur
+    ez = R[2]
+    g = np.concatenate([-(e["W"] - e["B"]) * ez, e["B"] * np.cross(np.array(e["rb"]), ez)])
+    rhs = tau - crb - ca - cur - dmp - g
+    Mdiag = np.concatenate([m + A[:3], Ig + A[3:]])
+    nu1 = s[7:13] + h * rhs / Mdiag
+    p1 = s[0:3] + h * R @ nu1[:3]
+    P, Q, Rr = nu1[3:]
+    qd = np.array([-x * P - y * Q - z * Rr, w0 * P + y * Rr - z * Q, w0 * Q - x * Rr + z * P, w0 * Rr + x * Q - y * P])
+    qn = s[3:7] + 0.5 * h * qd
+    return np.concatenate([p1, qn / np.linalg.norm(qn), nu1, n])
+
+
+def test_brute_force_one_substep():
+    rng = np.random.default_rng(7)
+    for ci, c in enumerate(vehicles.five_classes()):
+        for _ in range(10):
+            e = env_from_class(c, Vc=rng.uniform(-0.5, 0.5, 3), W=c["mass"] * G * rng.uniform(0.8, 1.2))
+            n_thr = np.array([c["n_thr"]])
+            s = workloads.random_states(int(rng.integers(1 << 30)), 1, n_thr)[0].astype(np.float64)
+            cmd = np.zeros(8, np.float32)
+            cmd[:c["n_thr"]] = rng.uniform(-1, 1, c["n_thr"])
+            ref = _brute_substep(c, e, s, cmd.astype(np.float64), 0.01)
+            out, _, _ = run(c, e, s.reshape(1, 21), cmd.reshape(1, 1, 8), 0.01, 1)
+            np.testing.assert_allclose(out[0], ref, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Forward-mode gradients against FP64 central differences.
+# ---------------------------------------------------------------------------
+def test_jvp_matches_central_differences():
+    classes = vehicles.five_classes()
+    counts = [2, 2, 2, 2, 2]
+    ec = workloads.env_classes(counts)
+    cfg = dict(vehicles.HOVER_DR)
+    envs, s0 = oracle.reset(classes, ec, cfg, 11)
+    E, T, K, dt = len(ec), 12, 2, 0.01
+    a = workloads.actions(12, T, E, lo=-0.99, hi=0.99)
+    rng = np.random.default_rng(8)
+    da = rng.normal(size=a.shape); dMa = rng.normal(size=(E, 6)); ddl = rng.normal(size=(E, 6))
+    ddq = rng.normal(size=(E, 6)); ds0 = rng.normal(size=(E, 21)) * 0.1
+    ds0[:, 13:] = 0.0
+    j = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, ds0, dMa, ddl, ddq)
+    arr = oracle.envs_to_arrays(envs)
+
+    def f(eps):
+        arr2 = dict(arr)
+        arr2["Ma"] = arr["Ma"] + eps * dMa
+        arr2["dl"] = arr["dl"] + eps * ddl
+        arr2["dq"] = arr["dq"] + eps * ddq
+        e2 = oracle.make_envs(arr2)
+        # Actions enter as float32; perturb through the FP64 path by rescaling
+        # the tangent onto the state instead: use only param/state directions.
+        s, o, r = oracle.rollout(classes, e2, (s0 + eps * ds0).copy(), a, dt, K)
+        return s, o, r
+
+    hstep = 1e-6
+    sp, op, rp = f(hstep)
+    sm, om, rm = f(-hstep)
+    j0 = oracle.rollout_jvp(classes, envs, s0, a, dt, K, None, ds0, dMa, ddl, ddq)
+    fd_r = (rp - rm) / (2 * hstep)
+    fd_s = (sp - sm) / (2 * hstep)
+    assert np.linalg.norm(j0["d_reward"] - fd_r) <= 1e-6 * np.linalg.norm(fd_r)
+    assert np.linalg.norm(j0["d_state"] - fd_s) <= 1e-6 * np.linalg.norm(fd_s)
+    # Action tangent: linearity check of the JVP in its direction argument.
+    ja = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, None, None, None, None)
+    np.testing.assert_allclose(j["d_reward"], j0["d_reward"] + ja["d_reward"], rtol=1e-10, atol=1e-10)
+
+
+def test_jvp_actions_against_fd_on_fp64_path():
+    """Action tangents against central differences taken on the FP64 substep
+    chain through the state (the rollout API takes float32 actions, so the
+    check perturbs an equivalent zero-order rotor command through n)."""
+    c = dict(vehicles.heavy8(), T_rotor=[0.0] * 8)   # n = clamp(a) exactly
+    e = env_from_class(c, Vc=(0.2, 0.1, 0.0))
+    envs = oracle.make_envs({k: np.asarray(v)[None] if k != "cls" else np.array([0], np.int32)
+                             for k, v in e.items()})
+    a = workloads.actions(3, 1, 1, lo=-0.9, hi=0.9)
+    s0 = rest_state(nu=(0.3, -0.1, 0.2, 0.1, 0.2, -0.3)).reshape(1, 21)
+    da = np.zeros((1, 1, 8)); da[0, 0, 2] = 1.0
+    j = oracle.rollout_jvp([c], envs, s0, a, 0.01, 1, da)
+    # With a zero-order rotor and K = 1, d(state)/d(a_2) equals d(state)/d(n_2)
+    # through the same substep; difference it via a state whose n is the command.
+    c2 = dict(c, T_rotor=[1e9] * 8)  # alpha ~ 0: rotor holds its state value
+    hstep = 1e-6
+    outs = []
+    for sgn in (1, -1):
+        s = s0.copy()
+        s[0, 13:21] = a[0, 0].astype(np.float64)
+        s[0, 15] += sgn * hstep
+        out, _, _ = oracle.rollout([c2], envs, s, np.zeros((1, 1, 8), np.float32) + a, 0.01, 1)
+        outs.append(out[0])
+    fd = (outs[0] - outs[1]) / (2 * hstep)
+    np.testing.assert_allclose(j["d_state"][0, :13], fd[:13], rtol=1e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Domain randomisation and hover reset (Table 2, Sec. IV-B).
+# ---------------------------------------------------------------------------
+def test_dr_ranges_match_table2_and_are_uniform():
+    with open(os.path.join(GOLDEN, "table2_train_ranges.json")) as f:
+        table = json.load(f)
+    classes = vehicles.five_classes()
+    counts = [400] * 5
+    ec = workloads.env_classes(counts)
+    envs, state = oracle.reset(classes, ec, vehicles.DR_TRAIN, 0x4D47)
+    arr = oracle.envs_to_arrays(envs)
+    lo, hi = table["Model mass*"]
+    nom = np.array([classes[k]["mass"] for k in ec])
+    fm = arr["mass"] / nom
+    assert fm.min() >= lo and fm.max() <= hi and abs(fm.mean() - 1.0) < 0.01
+    for key, fld in (("Added mass*", "Ma"), ("Damping*", "dl"), ("Damping*", "dq")):
+        lo, hi = table[key]
+        nomv = np.array([classes[k][fld] for k in ec])
+        fac = arr[fld] / nomv
+        assert fac.min() >= lo and fac.max() <= hi and abs(fac.mean() - 1.0) < 0.01
+        # Independent factors per coefficient.
+        assert abs(np.corrcoef(fac[:, 0], fac[:, 1])[0, 1]) < 0.1
+    lo, hi = table["Current velocity"]
+    sp = np.linalg.norm(arr["Vc"], axis=1)
+    assert sp.min() >= lo and sp.max() <= hi and np.all(arr["Vc"][:, 2] == 0.0)
+    np.testing.assert_allclose(sp.mean(), 0.5 * (lo + hi), atol=0.02)
+    # Inertia scales with the mass factor; weight follows mass, buoyancy the nominal volume.
+    nomI = np.array([classes[k]["Ig"] for k in ec])
+    np.testing.assert_allclose(arr["Ig"] / nomI, np.repeat(fm[:, None], 3, 1), rtol=1e-14)
+    np.testing.assert_allclose(arr["W"], arr["mass"] * G, rtol=1e-15)
+    np.testing.assert_allclose(arr["B"], nom * G, rtol=1e-15)
+    # Rest state without the hover initialiser.
+    assert np.all(state[:, 3] == 1.0) and np.all(state[:, [0, 1, 2, 4, 5, 6]] == 0.0)
+
+
+def test_hover_initial_pose():
+    classes = vehicles.five_classes()
+    ec = workloads.env_classes([100] * 5)
+    envs, state = oracle.reset(classes, ec, vehicles.HOVER, 3)
+    arr = oracle.envs_to_arrays(envs)
+    d = np.linalg.norm(state[:, 0:3] - arr["target"], axis=1)
+    assert d.max() <= 2.0 + 1e-12 and d.max() > 1.8
+    ang = 2 * np.arccos(np.clip(state[:, 3], -1, 1))
+    assert ang.max() <= math.radians(30) + 1e-12 and ang.max() > math.radians(28)
+    np.testing.assert_allclose(np.linalg.norm(state[:, 3:7], axis=1), 1.0, atol=1e-15)
+    assert np.abs(arr["target"]).max() <= 5.0
+    # Same draws for the same env id whatever the subset.
+    envs2, state2 = oracle.reset(classes, ec[:7], vehicles.HOVER, 3)
+    np.testing.assert_array_equal(state2, state[:7])
+
+
+def test_observation_and_reward_definition():
+    c = vehicles.heavy8()
+    e = env_from_class(c, target=(1.0, 2.0, 3.0))
+    # Yaw by +90 degrees: the NED offset (-1, 0, 0) reads (0, +1, 0) in the body frame.
+    q = (math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4))
+    s = rest_state(q=q, p=(0.0, 2.0, 3.0)).reshape(1, 21)
+    a = np.zeros((1, 1, 8), np.float32)
+    cq = dict(c, T_rotor=[0.0] * 8)
+    out, o, r = run(cq, dict(e, rb=np.zeros(3)), s, a, 1e-9, 1, obs=True)
+    np.testing.assert_allclose(o[0, 0, 0:3], [0.0, 1.0, 0.0], atol=1e-8)
+    np.testing.assert_allclose(r[0, 0], -1.0, atol=1e-8)
+    # Quaternion sign is normalised to w >= 0 in the observation only.
+    s2 = rest_state(q=(-1.0, 0.0, 0.0, 0.0)).reshape(1, 21)
+    out, o, r = run(cq, env_from_class(c), s2, a, 1e-9, 1, obs=True)
+    assert o[0, 0, 3] == 1.0 and out[0, 3] == -1.0
+
+
+def test_classes_explicit_step_stable_at_dr_extremes():
+    """h (d_l + 2 d_q |nu|max) / M_ii <= 1 for every DOF at the DR extremes,
+    with |nu|max the steady speed under the largest generalised thrust."""
+    for c in vehicles.five_classes():
+        Bm = np.zeros((6, c["n_thr"]))
+        for i in range(c["n_thr"]):
+            d = np.array(c["thr_dir"][i]); r = np.array(c["thr_pos"][i])
+            Bm[:3, i] = d; Bm[3:, i] = np.cross(r, d)
+        Fmax = np.abs(Bm) @ np.array(c["k_f"]) * 1.0
+        M = np.concatenate([c["mass"] + np.array(c["Ma"][:3]), np.array(c["Ig"]) + np.array(c["Ma"][3:])])
+        dl, dq = np.array(c["dl"]) * 1.2, np.array(c["dq"]) * 1.2
+        vmax = (-dl * 0.8 / 1.2 + np.sqrt((dl * 0.8 / 1.2) ** 2 + 4 * dq * 0.8 / 1.2 * Fmax)) / (2 * dq * 0.8 / 1.2)
+        ratio = 0.01 * (dl + 2 * dq * vmax) / (0.8 * M)
+        assert ratio.max() <= 1.0, (c["name"], ratio)
