@@ -1,0 +1,451 @@
+"""Benchmark of the batched UUV step on B300.
+
+Default workload (N=1): 1,048,576 envs over five vehicle classes (4/6/8
+thrusters, 10-200 kg), fused hover observation + reward every step, random
+initial pose within 2 m and 30 degrees, K substeps (default 4) per control
+step, dt = 0.01 s, FP32 state. A "step" is one mg_step call: every env
+advances one control step (K substeps) and writes its observation and reward.
+
+`value` is whole-job env-steps/s with actions already on the device; `e2e`
+is the same through mg_step_host with pinned host buffers (actions in,
+observations and rewards out, every step). Under torchrun each rank runs its
+own 1,048,576 envs on its own GPU (weak scaling, no data-path collective).
+
+`--impl reference` times the FP64 CPU oracle on this host on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s at 1M envs vs roofline; serving p50/p99 step latency; err vs FP64"
+UNIT = "env-steps/s"
+SEED = 0x4D47
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2032.0), src="measured")
+    return dict(hbm_gbs=6400.0, sm_max_mhz=2032.0, src="fallback")
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling (nvidia-smi) around the timed region.
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.lines = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        for t, line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if t0 <= r[0] <= t1 + 0.05]
+        window = "timed"
+        if len(inside) < 3:
+            inside = rows
+            window = "whole run"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "window": window}
+
+
+# ---------------------------------------------------------------------------
+# Workload helpers.
+# ---------------------------------------------------------------------------
+def workload(n_envs, K):
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(n_envs, len(classes))
+    return classes, counts, dict(vehicles.HOVER)
+
+
+def algorithmic(classes, counts, K):
+    """Bytes and FP32 ops per env-step of the hover step (class parameters):
+    state in + out 2*4*(13+n), actions 4n, target 12, observation 52, reward 4."""
+    from paper_2503_09203_b300 import binding as B
+    tot_b = tot_f = 0.0
+    for c, n in zip(classes, counts):
+        nt = c["n_thr"]
+        sub, obs = B.mg_count_flops(nt)
+        tot_b += n * (2 * 4 * (13 + nt) + 4 * nt + 12 + 52 + 4)
+        tot_f += n * (K * sub + obs)
+    E = sum(counts)
+    return tot_b / E, tot_f / E
+
+
+def time_steps(sim, acts, steps, warmup, stream):
+    """Device time of `steps` mg_step calls (events on the launching stream)."""
+    import torch
+    from paper_2503_09203_b300 import binding as B
+    n_act = acts.shape[0]
+    for i in range(warmup):
+        B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def action_pool(sim, n_pool, seed):
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    a = torch.rand(n_pool, sim.action_floats, device="cuda", generator=g) * 2 - 1
+    return a
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload.
+# ---------------------------------------------------------------------------
+def cpu_baseline(n_envs, K, budget_s=12.0, sample_envs=4096):
+    import oracle
+    from paper_2503_09203_b300 import workloads
+    classes, counts, cfg = workload(n_envs, K)
+    rng = np.random.default_rng(1)
+    ids = np.sort(rng.choice(n_envs, min(sample_envs, n_envs), replace=False))
+    ec = workloads.env_classes(counts)[ids]
+    envs, s = oracle.reset(classes, ec, cfg, SEED, env_ids=ids)
+    threads = os.cpu_count() or 1
+    a = workloads.actions(3, 1, len(ids))
+    oracle.rollout(classes, envs, s.copy(), a, 0.01, K, threads=threads)  # warm-up
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        s, _, _ = oracle.rollout(classes, envs, s, a, 0.01, K, threads=threads)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    v = len(ids) * steps / dt
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(ids)} envs sampled from the {n_envs}-env workload x {steps} steps "
+                      f"(K={K}, hover obs+reward), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# Extras: sweep, adjoint, serving, parity (N=1 only).
+# ---------------------------------------------------------------------------
+def sweep(pk, stream, sizes=(65536, 262144, 1048576), Ks=(1, 4, 8), steps=200):
+    from paper_2503_09203_b300 import binding as B
+    out = []
+    for E in sizes:
+        for K in Ks:
+            classes, counts, cfg = workload(E, K)
+            sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
+            sim.reset(seed=SEED)
+            acts = action_pool(sim, 4, 7)
+            t = time_steps(sim, acts, steps, 10, stream)
+            bpe, fpe = algorithmic(classes, counts, K)
+            v = E * steps / t
+            alu_peak = 2 * 128 * 148 * pk["sm_max_mhz"] * 1e6
+            out.append({"envs": E, "K": K, "env_steps_per_s": v, "us_per_step": t / steps * 1e6,
+                        "hbm_frac": v * bpe / (pk["hbm_gbs"] * 1e9), "alu_frac": v * fpe / alu_peak,
+                        "l2_resident": E * bpe < 126e6})
+            sim.close()
+    return out
+
+
+def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
+    import torch
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(E, 5)
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR),
+                record_steps=T, ckpt_every=ckpt)
+    sim.reset(seed=SEED)
+    s0 = sim.get_state()
+    acts = (torch.rand(T, sim.action_floats, device="cuda") * 2 - 1) * 0.99
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    g_rew = -torch.ones(T, sim.n_slots, device="cuda")
+    g_act = torch.zeros(T, sim.action_floats, device="cuda")
+    gA = torch.zeros(sim.n_slots, 6, device="cuda")
+    gD = torch.zeros(sim.n_slots, 12, device="cuda")
+    times = []
+    for rep in range(4):
+        sim.set_state(s0)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        B.mg_rollout(sim.handle, acts, T, None, rew, True, stream)
+        e1.record(stream)
+        B.mg_step_backward(sim.handle, acts, None, g_rew, None, g_act, gA, gD, None, stream)
+        e2.record(stream)
+        e2.synchronize()
+        times.append((e0.elapsed_time(e1) * 1e-3, e1.elapsed_time(e2) * 1e-3))
+    tf, tb = np.median([t[0] for t in times]), np.median([t[1] for t in times])
+    sim.close()
+    return {"envs": E, "horizon": T, "K": K, "ckpt_every": ckpt, "forward_s": tf, "backward_s": tb,
+            "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb}
+
+
+def serving_bench(plain_rate, n_req=300, load=0.7, seed=11, horizon_max=200):
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles
+    rng = np.random.default_rng(seed)
+    classes = vehicles.five_classes()
+    reqs = []
+    for i in range(n_req):
+        n = int(np.exp(rng.uniform(0, np.log(16384))))
+        reqs.append((int(rng.integers(0, 5)), max(1, n), int(rng.integers(1, horizon_max + 1)),
+                     int(rng.integers(1, 9)), int(rng.integers(1 << 62))))
+    mean_work = np.mean([r[1] * r[2] * r[3] for r in reqs])  # env-substeps per request
+    # Offered load: `load` x the plain path's substep throughput.
+    lam = load * plain_rate / mean_work
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=2 << 30, max_requests=1024, reset=dict(vehicles.HOVER))
+    t0 = time.perf_counter()
+    ids = []
+    t_next = t0
+    for r in reqs:
+        t_next += rng.exponential(1.0 / lam)
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+        ids.append(B.mg_server_submit(srv, *r))
+    B.mg_server_wait_idle(srv, 600.0)
+    wall = time.perf_counter() - t0
+    st = B.mg_server_stats_get(srv)
+    B.mg_server_destroy(srv)
+    return {"requests": n_req, "offered_load": load, "arrival_rate_per_s": lam, "wall_s": wall,
+            "env_steps_per_s": st["env_steps"] / wall, "busy_env_steps_per_s": st["env_steps"] / max(st["busy_seconds"], 1e-9),
+            "step_latency_p50_ms": st["step_latency_p50"] * 1e3, "step_latency_p99_ms": st["step_latency_p99"] * 1e3,
+            "queue_delay_p50_ms": st["queue_delay_p50"] * 1e3, "queue_delay_p99_ms": st["queue_delay_p99"] * 1e3,
+            "tick_p50_ms": st["tick_p50"] * 1e3, "tick_p99_ms": st["tick_p99"] * 1e3, "ticks": st["ticks"],
+            "request_mix": "class U{0..4}, envs log-uniform [1,16384], horizon U{1..%d}, K U{1..8}" % horizon_max}
+
+
+def parity_sample(sim_classes, counts, K, n=512):
+    """Sampled one-step error of the benchmark workload vs the oracle."""
+    import torch
+    import oracle
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import workloads
+    E = sum(counts)
+    cfg = workload(E, K)[2]
+    sim = B.Sim(sim_classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
+    sim.reset(seed=SEED)
+    rng = np.random.default_rng(2)
+    ids = np.sort(rng.choice(E, n, replace=False))
+    a_s = workloads.actions(5, 1, n)
+    a_env = np.zeros((1, E, 8), np.float32)
+    a_env[:, ids] = a_s
+    sim.step(sim.pack_actions(a_env))
+    torch.cuda.synchronize()
+    gpu = sim.get_state()[ids].astype(np.float64)
+    envs, s0 = oracle.reset(sim_classes, workloads.env_classes(counts)[ids], cfg, SEED, env_ids=ids)
+    ref, _, _ = oracle.rollout(sim_classes, envs, s0, a_s, 0.01, K)
+    sgn = np.sign(np.sum(gpu[:, 3:7] * ref[:, 3:7], 1, keepdims=True))
+    gpu[:, 3:7] *= np.where(sgn == 0, 1, sgn)
+    err = np.linalg.norm(gpu - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1)
+    sim.close()
+    return {"one_step_max_rel_err": float(err.max()), "p99": float(np.quantile(err, 0.99)), "sampled_envs": n,
+            "tol": 1e-5}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=1 << 20)
+    ap.add_argument("--substeps", type=int, default=4)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    E, K = args.envs, args.substeps
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(E, K, budget_s=max(5.0, 2.0 * args.steps / 1000.0 + 8.0))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"hover step, {E} envs, 5 classes, K={K}", "envs": E, "K": K},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import build as mgbuild
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mgbuild.build()
+    pk = peaks()
+    classes, counts, cfg = workload(E, K)
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
+    sim.reset(seed=SEED + rank)
+    stream = torch.cuda.current_stream()
+    acts = action_pool(sim, 8, 100 + rank)
+    bpe, fpe = algorithmic(classes, counts, K)
+    n_groups = len({c["n_thr"] for c in classes})
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.5)
+    # Warm-up, then exactly `steps` timed steps between barriers.
+    for i in range(args.warmup):
+        B.mg_step(sim.handle, acts[i % 8], 1, sim.obs, sim.reward, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(stream)
+    for i in range(args.steps):
+        B.mg_step(sim.handle, acts[i % 8], 1, sim.obs, sim.reward, stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    t = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        t = float(tt.item())
+    if rank == 0:
+        clocks.stop()
+    B.mg_status(sim.handle, stream)
+    value = E * world * args.steps / t
+
+    # End to end through the host-buffer entry point (pinned buffers).
+    a_host = acts[0].cpu().pin_memory()
+    o_host = torch.zeros(sim.n_slots, 13).pin_memory()
+    r_host = torch.zeros(sim.n_slots).pin_memory()
+    for _ in range(3):
+        B.mg_step_host(sim.handle, a_host, 1, o_host, r_host, stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        B.mg_step_host(sim.handle, a_host, 1, o_host, r_host, stream)
+    te = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([te], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": E * world * args.e2e_steps / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(sim.action_floats * 4), "d2h_bytes_per_step": int(sim.n_slots * 14 * 4),
+           "steps": args.e2e_steps, "api": "mg_step_host"}
+
+    if rank != 0:
+        sim.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    per_step = t / args.steps
+    achieved_gbs = E * bpe / per_step / 1e9
+    alu_peak = 2 * 128 * 148 * pk["sm_max_mhz"] * 1e6
+    achieved_flops = E * fpe / per_step
+    t_mem, t_alu = E * bpe / (pk["hbm_gbs"] * 1e9), E * fpe / alu_peak
+    if t_mem >= t_alu:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
+                "peak_src": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved_flops / alu_peak, "traffic": None,
+                "peak_src": "2 x 128 FP32 lanes x 148 SMs x max SM clock"}
+    roof.update({"kernel": "mg_step_kernel<4,6,8> (one launch per thruster count, per step)",
+                 "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
+                 "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"hover step, {E} envs per GPU, 5 classes (4/6/8 thr), K={K}, dt=0.01",
+                       "envs_per_gpu": E, "K": K, "classes": [c["name"] for c in classes], "counts": counts,
+                       "l2": f"inputs larger than L2 ({E * bpe / 1e6:.0f} MB touched per step)",
+                       "parallelism": f"replicas x{world} (independent envs per GPU)"},
+            "e2e": e2e, "gpu_launches": args.steps * n_groups, "roofline": roof,
+            "clocks": clocks.summary(tw0, tw1)}
+    if world == 1 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(E, K)
+        sim.close()
+        line["parity"] = parity_sample(classes, counts, K)
+        line["sweep"] = sweep(pk, stream)
+        line["adjoint"] = adjoint_bench(stream)
+        plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)
+        line["serving"] = serving_bench(plain_substeps)
+    else:
+        sim.close()
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

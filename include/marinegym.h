@@ -1,0 +1,313 @@
+/*
+ * marinegym.h - C-ABI of libmarinegym, the B300 (sm_103a) batched underwater
+ * vehicle step of MarineGym (arXiv 2503.09203).
+ *
+ * One call advances many independent environments (one vehicle each) by the
+ * Fossen equation of motion of Sec. III-B, Eq. 1:
+ *     tau = M nu_dot + C(nu) nu + D(nu) nu + g(eta),
+ * split as in Eq. 2 into the rigid-body term (M_RB, C_RB, g_RB) and the
+ * hydrodynamic term of Eq. 3 (M_A, C_A, D, g_A), the latter evaluated at the
+ * relative velocity nu_r = nu - nu_c against an ocean current (Sec. III-B,
+ * paragraph after Eq. 3). Actuators follow Sec. III-D: a first-order rotor lag
+ * (zero-order when the time constant is 0), quadratic thrust k n|n| with a
+ * dead zone, and forces applied at fixed actuator frames (a 6 x n_thr
+ * allocation matrix). Domain randomisation follows Sec. III-C and the ranges of
+ * Table 2; the hover (station-keeping) observation and reward follow Sec. IV-B.
+ *
+ * Conventions. NED world frame (z down, gravity +z), body frame x forward,
+ * y starboard, z down. Pose: position p (3) and unit quaternion q = (w,x,y,z),
+ * Hamilton, body -> NED. Body velocity nu = (u,v,w,p,q,r). Added-mass and
+ * damping coefficients are positive magnitudes. The integrator is
+ * semi-implicit Euler over K substeps of h = dt/K per control step (the paper
+ * names no integrator).
+ *
+ * Memory and errors. All pointers named *_dev are device pointers owned by the
+ * caller; they must stay valid until the work queued on `stream` completes.
+ * The library owns the simulator state and never frees caller memory. Every
+ * call returns MG_OK (0) or a negative MG_ERR_* code; the text of the last
+ * error is returned by mg_last_error(). Calls that take a stream are
+ * asynchronous on it; a non-finite state produced by a step is reported by the
+ * next mg_status() call (it synchronises the stream).
+ *
+ * Environment order. Environments are grouped by class: class 0 owns env
+ * indices [0, n_0), class 1 owns [n_0, n_0 + n_1), and so on. Per-env arrays
+ * (observations, rewards) are indexed by *slot*: each class's first slot is a
+ * multiple of 4, so class c occupies slots [slot_offset_c, slot_offset_c +
+ * n_c) and up to 3 padding slots may follow it. mg_get_layout() reports all
+ * offsets.
+ */
+#ifndef MARINEGYM_H
+#define MARINEGYM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mg_stream_t; /* same type as cudaStream_t */
+
+enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = -1,      /* bad handle, size, pointer or value */
+  MG_ERR_OOM = -2,              /* device allocation failed or budget exceeded */
+  MG_ERR_CUDA = -3,             /* a CUDA runtime call failed */
+  MG_ERR_NONFINITE = -4,        /* a step produced a NaN or Inf state */
+  MG_ERR_TIMEOUT = -5,          /* a bounded device wait gave up */
+  MG_ERR_ADMISSION_REFUSED = -6,/* serving: request can never fit the budget */
+  MG_ERR_STATE = -7             /* call order (e.g. backward with no recorded rollout) */
+};
+
+#define MG_MAX_THR 8
+#define MG_MAX_CLASSES 16
+#define MG_STATE_DIM 21   /* canonical host state record: p3 q4 nu6 n8 */
+#define MG_OBS_DIM 13     /* hover observation: R^T(p-p*) 3, q 4 (w>=0), v 3, w 3 */
+#define MG_ENV_PARAM_DIM 34 /* canonical host per-env parameter record (doubles) */
+
+/* A vehicle class (Sec. III-D model library): rigid body, hydrodynamic
+ * coefficients and up to 8 thrusters. FP64 on the host; the library derives
+ * the allocation matrix B = [d_i ; r_i x d_i], the rotor factor
+ * alpha = 1 - exp(-h/T) and the inverse inertia in FP64 and stores them FP32.
+ * Only r_g = 0 and diagonal added mass are supported by the kernels. */
+typedef struct {
+  int32_t n_thr;            /* 1..8 (the workloads use 4, 6, 8) */
+  int32_t pad0;
+  double mass;              /* kg */
+  double Ig[3];             /* principal inertia about the CoG, kg m^2 */
+  double rg[3];             /* CoG in body frame (must be 0) */
+  double rb[3];             /* CoB in body frame, m */
+  double buoy_ratio;        /* B / (mass g) at nominal volume (1 = neutral) */
+  double Ma[6];             /* added mass diag (kg, kg m^2) */
+  double dl[6];             /* linear damping diag */
+  double dq[6];             /* quadratic damping diag */
+  double thr_pos[8][3];     /* thruster positions, body frame, m */
+  double thr_dir[8][3];     /* thruster unit directions, body frame */
+  double k_f[8];            /* thrust at |n| = 1, N */
+  double T_rotor[8];        /* rotor time constant, s; 0 = zero-order model */
+  double deadzone[8];       /* |n| below which the thrust is 0 */
+} mg_class_desc;
+
+/* Reset configuration: domain randomisation (Sec. III-C, Table 2 train
+ * column shape) and the initial state. Uniform draws come from Philox4x64-10
+ * (Salmon et al. 2011) keyed by (seed, stream) with counter (env, draw/4, 0, 0).
+ * DR factors: mass (inertia scales with it), each added-mass coefficient, each
+ * linear and quadratic damping coefficient, CoB offset; current speed
+ * U[cur_lo, cur_hi] with heading U[0, 2 pi) (horizontal unless current_3d). */
+typedef struct {
+  int32_t dr_enabled;
+  int32_t current_enabled;
+  int32_t current_3d;
+  int32_t init_mode;        /* 0: rest at the origin; 1: hover-task random pose */
+  double mass_lo, mass_hi;
+  double added_lo, added_hi;
+  double damp_lo, damp_hi;
+  double cob_lo, cob_hi;
+  double cur_lo, cur_hi;
+  double target_half;       /* hover target p* ~ U[-L, L]^3 */
+  double pos_radius;        /* |p - p*| uniform in a ball of this radius */
+  double max_angle;         /* attitude error angle ~ U[0, max_angle], rad */
+} mg_reset_cfg;
+
+typedef struct {
+  int32_t n_classes;            /* 1..MG_MAX_CLASSES */
+  const int32_t* class_counts;  /* host [n_classes]: envs per class (>= 0) */
+  double dt;                    /* control step, s (> 0) */
+  int32_t K;                    /* substeps per control step (1..64) */
+  int32_t per_env_params;       /* 1: per-env parameter block (needed for DR,
+                                   current and gradients); 0: class values */
+  mg_reset_cfg reset;
+  int32_t record_steps;         /* longest rollout mg_step_backward may
+                                   differentiate (0: no gradient buffers) */
+  int32_t ckpt_every;           /* checkpoint interval in steps (0: 20) */
+  size_t mem_budget;            /* 0: none; else mg_create fails with
+                                   MG_ERR_OOM above this many device bytes */
+} mg_config;
+
+/* Placement of class c inside the device buffers. */
+typedef struct {
+  int32_t n_envs, n_thr, env_offset, slot_offset;
+  int64_t state_offset;   /* floats, start of the class's AoS state block */
+  int32_t state_stride;   /* floats per env: 13 + n_thr (p3 q4 nu6 n[n_thr]) */
+  int32_t pad0;
+  int64_t action_offset;  /* floats, start of the class's [n_slots_c][n_thr] actions */
+} mg_class_layout;
+
+typedef struct {
+  int32_t n_classes, n_envs, n_slots, pad0;
+  int64_t action_floats;  /* floats per control step in an actions buffer */
+  int64_t state_floats;
+  mg_class_layout cls[MG_MAX_CLASSES];
+} mg_layout;
+
+typedef struct mg_sim mg_sim;
+
+/* Create a simulator: validates the classes (n_thr in 1..8, r_g = 0, positive
+ * mass and inertia, non-negative coefficients) and allocates the device state,
+ * parameter, target and (if record_steps > 0) checkpoint buffers on the
+ * current device. The state starts at rest; call mg_reset to sample.
+ * Errors: INVALID_ARG, OOM (allocation failed or above mem_budget), CUDA. */
+int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out);
+int mg_destroy(mg_sim* sim);
+int mg_get_layout(const mg_sim* sim, mg_layout* out);
+
+/* Reset envs (indices into [0, n_envs), device int32 array; NULL = all,
+ * then n is ignored): sample DR parameters (if enabled), the current (if
+ * enabled), the hover target and the initial state from `seed`
+ * (Sec. III-C, Table 2; reading of the DR ranges as independent per-coefficient
+ * factors). Inverse inertia is computed in FP64 on the GPU. */
+int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, mg_stream_t stream);
+
+/* Advance all envs by n_steps control steps (K substeps each, zero-order hold
+ * of clamp(action, -1, 1)). actions_dev: [n_steps][action_floats] floats laid
+ * out per mg_layout (class c's [n_envs_c][n_thr_c] row-major block at
+ * action_offset_c). obs_dev [n_slots][13] and reward_dev [n_slots] receive the
+ * hover observation and reward r = -|p-p*|^2 - 0.1|nu|^2 - 0.01|c|^2 after
+ * the last step; either may be NULL. Padding slots receive zeros. */
+int mg_step(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+            mg_stream_t stream);
+
+/* As mg_step, with observations and rewards written after EVERY step:
+ * obs_dev [n_steps][n_slots][13], reward_dev [n_steps][n_slots] (either may be
+ * NULL). The whole rollout is one persistent launch with the state held in
+ * registers. record != 0 stores checkpoints every ckpt_every steps for
+ * mg_step_backward (needs n_steps <= record_steps and per_env_params). */
+int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+               int32_t record, mg_stream_t stream);
+
+/* Observation of the current state (no step): obs_dev [n_slots][13]. */
+int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream);
+
+/* Host-buffer variant of mg_step for callers without device memory: copies
+ * actions (host, as for mg_step) in, steps, copies obs/reward (host, may be
+ * NULL) out, all on `stream`, and synchronises it. Host buffers should be
+ * pinned for asynchronous copies. */
+int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float* obs_host, float* reward_host,
+                 mg_stream_t stream);
+
+/* Reverse-mode gradient of the last recorded mg_rollout (discretise-then-
+ * differentiate: the exact adjoint of the discrete map, including the clamp,
+ * rotor lag, quaternion renormalisation, and M^-1 = (M_RB + M_A)^-1 through
+ * the added mass). Inputs: the same actions_dev, cotangents g_obs
+ * [T][n_slots][13] and g_rew [T][n_slots] (either may be NULL = 0) and
+ * g_state_T [n_slots][21] on the final state (NULL = 0). Outputs (each may be
+ * NULL): g_actions [T][action_floats], g_added_mass [n_slots][6],
+ * g_damping [n_slots][12] (6 linear then 6 quadratic), g_state0
+ * [n_slots][21]. Segments between checkpoints are recomputed into
+ * library-owned scratch. Errors: STATE if nothing was recorded. */
+int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
+                     const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
+                     float* g_state0, mg_stream_t stream);
+
+/* Overwrite the added-mass (A [n_slots][6]), linear damping (dl) and quadratic
+ * damping (dq) of every env from device arrays (each may be NULL = keep) and
+ * recompute M^-1 in FP64 on the GPU. Needs per_env_params. */
+int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const float* dq_dev, mg_stream_t stream);
+
+/* FP64 rollout used only for finite-difference checks: runs the double
+ * instantiation of the step from the current state (not modified) with the
+ * current parameters, the added mass and damping optionally perturbed by
+ * eps * (dA, ddl, ddq) (device doubles [n_slots][6] each, NULL = 0), and writes
+ * reward_dev [n_steps][n_slots] (double) and, if not NULL, the final state
+ * state_dev [n_slots][21] (double). Inverse inertia is recomputed in FP64. */
+int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, const double* dA,
+                    const double* ddl, const double* ddq, double eps, double* reward_dev, double* state_dev,
+                    mg_stream_t stream);
+
+/* Checkpoint / resume: the state as [n_envs][21] floats (canonical record,
+ * rotor entries beyond n_thr are 0), and the per-env parameters as
+ * [n_envs][34] doubles: mass, Ig[3], rb[3], W, B, Ma[6], dl[6], dq[6], Vc[3],
+ * target[3], pad. Setting parameters recomputes M^-1 in FP64 (the live
+ * re-tuning interface of Sec. III-C). These calls synchronise the device. */
+int mg_get_state(const mg_sim* sim, float* host, size_t bytes);
+int mg_set_state(mg_sim* sim, const float* host, size_t bytes);
+int mg_get_params(const mg_sim* sim, double* host, size_t bytes);
+int mg_set_params(mg_sim* sim, const double* host, size_t bytes);
+
+/* Synchronise `stream`; return MG_ERR_NONFINITE (and clear the flag) if any
+ * step since the last call produced a non-finite state, else MG_OK. */
+int mg_status(mg_sim* sim, mg_stream_t stream);
+
+/* Choose threads per block and the number of resident blocks per SM of the
+ * persistent rollout by timing candidates on `stream` (state is saved and
+ * restored). Writes the choice into *threads / *blocks_per_sm if not NULL. */
+int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads, int32_t* blocks_per_sm);
+
+/* CUDA-graph capture of mg_rollout(actions, n_steps, obs, reward, record=0)
+ * on `stream`; mg_graph_launch replays it. Buffers are bound at capture. */
+typedef struct mg_graph mg_graph;
+int mg_graph_capture(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+                     mg_stream_t stream, mg_graph** out);
+int mg_graph_launch(mg_graph* g, mg_stream_t stream);
+int mg_graph_destroy(mg_graph* g);
+
+/* Algorithmic FP32 operations (FMA = 2, divide and square root = 1 each) for
+ * a class with n_thr thrusters, counted by running the kernels' own templated
+ * arithmetic with a counting scalar on the host: one substep (current terms
+ * included), the observation + reward, and one substep's adjoint (its
+ * forward recompute included). Any output may be NULL. */
+int mg_count_flops(int32_t n_thr, double* substep_flops, double* observe_flops, double* adjoint_flops);
+
+const char* mg_last_error(const mg_sim* sim);
+const char* mg_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (continuous batching). A server owns a device arena of
+ * `budget_bytes` and a scheduler thread. Each request is a rollout of n_envs
+ * envs of one class for `horizon` control steps of K substeps; its actions are
+ * drawn on the device from Philox4x64-10 (key (seed, 3), counter
+ * (env, step, thr/4, 0), top 24 bits: a = k 2^-23 - 1). Requests are admitted
+ * as soon as the arena has room, their envs live on the device until done, and
+ * every scheduler tick advances all admitted requests by one step in ONE
+ * shared launch. A finished request's final state ([n_envs][21] floats) and
+ * per-env return (sum of rewards, [n_envs] floats) are copied to host memory
+ * owned by the server and read with mg_server_poll.
+ * ------------------------------------------------------------------------ */
+typedef struct mg_server mg_server;
+
+typedef struct {
+  double dt;
+  size_t budget_bytes;      /* arena size; 0: 50% of free device memory */
+  int32_t max_requests;     /* simultaneously admitted requests (<= 4096) */
+  int32_t max_queue;        /* pending requests before submit refuses */
+  mg_reset_cfg reset;       /* initial state / DR per request (seeded by request) */
+} mg_server_config;
+
+typedef struct {
+  int32_t cls, n_envs, horizon, K;
+  uint64_t seed;            /* reset draws and actions */
+} mg_request;
+
+enum { MG_REQ_PENDING = 0, MG_REQ_RUNNING = 1, MG_REQ_DONE = 2, MG_REQ_UNKNOWN = -1 };
+
+typedef struct {
+  int32_t status;           /* MG_REQ_* */
+  int32_t n_envs;
+  double t_submit, t_admit, t_done;   /* seconds, steady clock */
+  int64_t steps_done;
+  const float* final_state; /* server-owned host [n_envs][21], valid until mg_server_release */
+  const float* returns;     /* server-owned host [n_envs] */
+} mg_request_result;
+
+typedef struct {
+  int64_t requests_done, env_steps, ticks;
+  double busy_seconds;
+  double step_latency_p50, step_latency_p99;   /* s, per request step (tick completion spacing) */
+  double queue_delay_p50, queue_delay_p99;     /* s, submit -> admit */
+  double tick_p50, tick_p99;                   /* s, device time of one shared launch */
+} mg_server_stats;
+
+int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, int32_t n_classes,
+                     mg_server** out);
+int mg_server_submit(mg_server* srv, const mg_request* req, int64_t* id_out);
+int mg_server_poll(mg_server* srv, int64_t id, mg_request_result* out);
+int mg_server_release(mg_server* srv, int64_t id);
+int mg_server_wait_idle(mg_server* srv, double timeout_s);
+int mg_server_stats_get(mg_server* srv, mg_server_stats* out);
+int mg_server_destroy(mg_server* srv);
+const char* mg_server_last_error(const mg_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MARINEGYM_H */

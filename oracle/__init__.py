@@ -84,7 +84,7 @@ def lib():
         _lib.or_rollout_jvp.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
                                         fp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
         _lib.or_reset.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_int64, C.c_void_p,
-                                  C.c_uint64, C.c_void_p, dp]
+                                  C.c_uint64, C.POINTER(C.c_int64), C.c_void_p, dp]
         _lib.or_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]
         _lib.or_uniform.restype = C.c_double
         _lib.or_action.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int]
@@ -182,10 +182,14 @@ def make_envs(arrays: dict):
 # Entry points.
 # ---------------------------------------------------------------------------
 
-def reset(classes, env_class, cfg: dict, seed: int):
-    """Sample per-env parameters and initial states. Returns (envs, state[E,21])."""
+def reset(classes, env_class, cfg: dict, seed: int, env_ids=None):
+    """Sample per-env parameters and initial states. Returns (envs, state[E,21]).
+
+    env_ids: the env index that keys each record's random draws (default
+    0..E-1), so that any subset of a large batch can be reproduced."""
     L = lib()
     env_class = np.ascontiguousarray(env_class, dtype=np.int32)
+    ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int64)
     n = len(env_class)
     envs = (or_env * n)()
     state = np.zeros((n, STATE_DIM))
@@ -193,6 +197,7 @@ def reset(classes, env_class, cfg: dict, seed: int):
     rc = L.or_reset(C.cast(cls, C.c_void_p), len(classes),
                     env_class.ctypes.data_as(C.POINTER(C.c_int32)), n,
                     C.cast(C.pointer(pack_reset_cfg(cfg)), C.c_void_p), int(seed) & (2**64 - 1),
+                    None if ids is None else ids.ctypes.data_as(C.POINTER(C.c_int64)),
                     C.cast(envs, C.c_void_p), _dp(state))
     if rc != 0:
         raise ValueError(f"or_reset failed: {rc}")

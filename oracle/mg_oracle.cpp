@@ -516,8 +516,10 @@ float or_action(uint64_t seed, uint64_t env, uint64_t step, int thr) {
 // 21 current heading, 22 current vertical (3D variant).
 // Draw numbers of stream 2: 0-2 target, 3 radius, 4-5 offset direction,
 // 6-7 rotation axis, 8 rotation angle.
+// env_ids (may be NULL): the env index each record's draws are keyed by
+// (default: the record index).
 int or_reset(const or_class* classes, int n_classes, const int32_t* env_class, int64_t n_envs,
-             const or_reset_cfg* cfg, uint64_t seed, or_env* envs, double* state) {
+             const or_reset_cfg* cfg, uint64_t seed, const int64_t* env_ids, or_env* envs, double* state) {
   for (int64_t ei = 0; ei < n_envs; ++ei) {
     const int ci = env_class[ei];
     if (ci < 0 || ci >= n_classes) return -1;
@@ -525,7 +527,7 @@ int or_reset(const or_class* classes, int n_classes, const int32_t* env_class, i
     or_env& e = envs[ei];
     std::memset(&e, 0, sizeof(e));
     e.cls = ci;
-    const uint64_t id = (uint64_t)ei;
+    const uint64_t id = env_ids ? (uint64_t)env_ids[ei] : (uint64_t)ei;
     auto f = [&](int j, double lo, double hi) {
       return cfg->dr_enabled ? lo + (hi - lo) * draw_u(seed, kStreamDR, id, j) : 1.0;
     };

@@ -1,0 +1,485 @@
+// Per-environment step arithmetic of the batched UUV simulator, templated on
+// the scalar (float for the hot kernels, double for the FP64 check path, a
+// counting type on the host for the FLOP count) and on the thruster count.
+//
+// One substep (h = dt/K) of the discrete map, in the order a1..a8:
+//   a1 rotor lag      n <- n + alpha (c - n)                 (Sec. III-D)
+//   a2 thrust/alloc   f_i = k_i n_i |n_i| (0 in dead zone), tau = B f
+//   a3 kinematics     R(q), v_c = R^T V_c, v_r = v - v_c     (Sec. III-B, current)
+//   a4 C_RB(nu) nu  = [m w x v ; w x (I_g w)]                 (Eq. 2, r_g = 0)
+//   a5 C_A(nu_r)nu_r= [w x a1 ; v_r x a1 + w x a2], a1 = A_lin v_r, a2 = A_ang w,
+//      plus the current-acceleration term M_A [w x v_c ; 0]  (Eq. 3 with nu_r)
+//   a6 D(nu_r)nu_r  = d_l o nu_r + d_q o |nu_r| o nu_r
+//   a7 g(q)         = [-(W-B) e ; B r_b x e], e = R^T e_3    (Eq. 1-2, r_g = 0)
+//   a8 nu += h M^-1 (tau - a4 - a5 - a6 - a7); p += h R v; q <- |q + h/2 q(x)(0,w)|
+// The hover observation / reward (Sec. IV-B station keeping) and the exact
+// vector-Jacobian products of both are here too.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define MG_HD __host__ __device__ __forceinline__
+
+namespace mg {
+
+MG_HD float mabs(float x) { return fabsf(x); }
+MG_HD double mabs(double x) { return fabs(x); }
+MG_HD float msqrt(float x) { return sqrtf(x); }
+MG_HD double msqrt(double x) { return sqrt(x); }
+
+// Actuator table of one (class, substep length).
+template <typename S>
+struct Act {
+  S alloc[6][8];  // B = [d_i ; r_i x d_i]
+  S kf[8];
+  S dz[8];
+  S alpha[8];
+};
+
+// Per-env physical parameters (device block of 36 floats in this order).
+template <typename S>
+struct Phys {
+  S minv[6], A[6], dl[6], dq[6];
+  S m, Ig[3], W, B, rb[3], Vc[3];
+};
+
+template <typename S, int NT>
+struct St {
+  S p[3], q[4], nu[6], n[NT];
+};
+
+template <typename S>
+struct HydroGrad {
+  S A[6], dl[6], dq[6];
+};
+
+template <typename S>
+MG_HD void cross3(const S a[3], const S b[3], S o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename S>
+MG_HD void rot(const S q[4], S R[3][3]) {
+  const S w = q[0], x = q[1], y = q[2], z = q[3];
+  const S two = S(2.0f), one = S(1.0f);
+  R[0][0] = one - two * (y * y + z * z);
+  R[0][1] = two * (x * y - w * z);
+  R[0][2] = two * (x * z + w * y);
+  R[1][0] = two * (x * y + w * z);
+  R[1][1] = one - two * (x * x + z * z);
+  R[1][2] = two * (y * z - w * x);
+  R[2][0] = two * (x * z - w * y);
+  R[2][1] = two * (y * z + w * x);
+  R[2][2] = one - two * (x * x + y * y);
+}
+
+// Intermediates of one substep kept for the vector-Jacobian product.
+template <typename S, int NT>
+struct Tape {
+  S n1[NT], R[3][3], vc[3], vr[3], w[3], rhs[6], nu1[6], qn[4], inv;
+};
+
+// a1-a8. `x` is updated in place; `c` is the clamped command (zero-order hold).
+// `A` is an Act<S> or a volatile view of one in shared memory (a volatile view
+// keeps the class table in shared memory instead of hoisting it into registers).
+template <typename S, int NT, bool TAPE, typename ActT>
+MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const Phys<S>& P, const ActT& A, S h,
+                   Tape<S, NT>* tp) {
+  // a1 + a2
+  S f[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    x.n[i] = x.n[i] + S(A.alpha[i]) * (c[i] - x.n[i]);
+    const S an = mabs(x.n[i]);
+    f[i] = (an < S(A.dz[i])) ? S(0.0f) : S(A.kf[i]) * x.n[i] * an;
+  }
+  S tau[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    S s = S(A.alloc[k][0]) * f[0];
+#pragma unroll
+    for (int i = 1; i < NT; ++i) s = s + S(A.alloc[k][i]) * f[i];
+    tau[k] = s;
+  }
+  // a3
+  S R[3][3];
+  rot(x.q, R);
+  const S v[3] = {x.nu[0], x.nu[1], x.nu[2]};
+  const S w[3] = {x.nu[3], x.nu[4], x.nu[5]};
+  S vc[3], vr[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    vc[j] = R[0][j] * P.Vc[0] + R[1][j] * P.Vc[1] + R[2][j] * P.Vc[2];
+    vr[j] = v[j] - vc[j];
+  }
+  // a4
+  S wxv[3], Iw[3], wxIw[3];
+  cross3(w, v, wxv);
+  Iw[0] = P.Ig[0] * w[0]; Iw[1] = P.Ig[1] * w[1]; Iw[2] = P.Ig[2] * w[2];
+  cross3(w, Iw, wxIw);
+  // a5
+  S a1[3], a2[3], wxa1[3], vrxa1[3], wxa2[3], wxvc[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) { a1[j] = P.A[j] * vr[j]; a2[j] = P.A[3 + j] * w[j]; }
+  cross3(w, a1, wxa1);
+  cross3(vr, a1, vrxa1);
+  cross3(w, a2, wxa2);
+  cross3(w, vc, wxvc);
+  // a6 (nu_r = [v_r ; w])
+  S dmp[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dmp[j] = (P.dl[j] + P.dq[j] * mabs(vr[j])) * vr[j];
+    dmp[3 + j] = (P.dl[3 + j] + P.dq[3 + j] * mabs(w[j])) * w[j];
+  }
+  // a7: e = R^T e_3 is the third row of R.
+  const S e[3] = {R[2][0], R[2][1], R[2][2]};
+  const S WmB = P.W - P.B;
+  S Brb[3] = {P.B * P.rb[0], P.B * P.rb[1], P.B * P.rb[2]}, mb[3];
+  cross3(Brb, e, mb);
+  // a8
+  S rhs[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    rhs[j] = tau[j] - P.m * wxv[j] - wxa1[j] - P.A[j] * wxvc[j] - dmp[j] + WmB * e[j];
+    rhs[3 + j] = tau[3 + j] - wxIw[j] - vrxa1[j] - wxa2[j] - dmp[3 + j] - mb[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (P.minv[j] * rhs[j]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    x.p[i] = x.p[i] + h * (R[i][0] * x.nu[0] + R[i][1] * x.nu[1] + R[i][2] * x.nu[2]);
+  const S qw = x.q[0], qx = x.q[1], qy = x.q[2], qz = x.q[3];
+  const S P_ = x.nu[3], Q_ = x.nu[4], R_ = x.nu[5];
+  const S hh = S(0.5f) * h;
+  S qn[4];
+  qn[0] = qw + hh * (-qx * P_ - qy * Q_ - qz * R_);
+  qn[1] = qx + hh * (qw * P_ + qy * R_ - qz * Q_);
+  qn[2] = qy + hh * (qw * Q_ - qx * R_ + qz * P_);
+  qn[3] = qz + hh * (qw * R_ + qx * Q_ - qy * P_);
+  const S inv = S(1.0f) / msqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.q[i] = qn[i] * inv;
+  if (TAPE) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) tp->n1[i] = x.n[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tp->vc[i] = vc[i]; tp->vr[i] = vr[i]; tp->w[i] = w[i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tp->R[i][j] = R[i][j];
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) { tp->rhs[j] = rhs[j]; tp->nu1[j] = x.nu[j]; }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tp->qn[i] = qn[i];
+    tp->inv = inv;
+  }
+}
+
+// Hover observation and reward after a control step.
+template <typename S, int NT>
+MG_HD void observe(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], S obs[13], S& rew) {
+  S R[3][3];
+  rot(x.q, R);
+  const S d[3] = {x.p[0] - tgt[0], x.p[1] - tgt[1], x.p[2] - tgt[2]};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) obs[j] = R[0][j] * d[0] + R[1][j] * d[1] + R[2][j] * d[2];
+  const S sg = (x.q[0] < S(0.0f)) ? S(-1.0f) : S(1.0f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) obs[3 + i] = sg * x.q[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) obs[7 + i] = x.nu[i];
+  S dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  S vv = x.nu[0] * x.nu[0];
+#pragma unroll
+  for (int i = 1; i < 6; ++i) vv = vv + x.nu[i] * x.nu[i];
+  S cc = c[0] * c[0];
+#pragma unroll
+  for (int i = 1; i < NT; ++i) cc = cc + c[i] * c[i];
+  rew = -dd - S(0.1f) * vv - S(0.01f) * cc;
+}
+
+// ---------------------------------------------------------------------------
+// Vector-Jacobian products (discretise-then-differentiate).
+// ---------------------------------------------------------------------------
+
+// d R / d q contracted with an adjoint LR (3x3): returns LR : dR/dq_k.
+template <typename S>
+MG_HD void rot_vjp(const S q[4], const S LR[3][3], S lq[4]) {
+  const S w = q[0], x = q[1], y = q[2], z = q[3];
+  const S t = S(2.0f);
+  // R00 = 1-2(y^2+z^2), R01 = 2(xy-wz), R02 = 2(xz+wy)
+  // R10 = 2(xy+wz), R11 = 1-2(x^2+z^2), R12 = 2(yz-wx)
+  // R20 = 2(xz-wy), R21 = 2(yz+wx), R22 = 1-2(x^2+y^2)
+  lq[0] += t * (-z * LR[0][1] + y * LR[0][2] + z * LR[1][0] - x * LR[1][2] - y * LR[2][0] + x * LR[2][1]);
+  lq[1] += t * (y * LR[0][1] + z * LR[0][2] + y * LR[1][0] - S(2.0f) * x * LR[1][1] - w * LR[1][2] +
+                z * LR[2][0] + w * LR[2][1] - S(2.0f) * x * LR[2][2]);
+  lq[2] += t * (-S(2.0f) * y * LR[0][0] + x * LR[0][1] + w * LR[0][2] + x * LR[1][0] + z * LR[1][2] -
+                w * LR[2][0] + z * LR[2][1] - S(2.0f) * y * LR[2][2]);
+  lq[3] += t * (-S(2.0f) * z * LR[0][0] - w * LR[0][1] + x * LR[0][2] + w * LR[1][0] - S(2.0f) * z * LR[1][1] +
+                y * LR[1][2] + x * LR[2][0] + y * LR[2][1]);
+}
+
+// y = a x b:  l_a += b x l_y ;  l_b += l_y x a.
+template <typename S>
+MG_HD void cross_vjp(const S a[3], const S b[3], const S ly[3], S la[3], S lb[3]) {
+  S t[3];
+  cross3(b, ly, t);
+  la[0] += t[0]; la[1] += t[1]; la[2] += t[2];
+  cross3(ly, a, t);
+  lb[0] += t[0]; lb[1] += t[1]; lb[2] += t[2];
+}
+
+// Observation/reward adjoint: adds to the state adjoint `lx` and the command
+// adjoint `lc` the contribution of cotangents g_obs (13, may be null) and g_rew.
+template <typename S, int NT>
+MG_HD void observe_vjp(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], const S* g_obs, S g_rew,
+                       St<S, NT>& lx, S (&lc)[NT]) {
+  S R[3][3];
+  rot(x.q, R);
+  const S d[3] = {x.p[0] - tgt[0], x.p[1] - tgt[1], x.p[2] - tgt[2]};
+  S LR[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) LR[i][j] = S(0.0f);
+  S lq[4] = {S(0.0f), S(0.0f), S(0.0f), S(0.0f)};
+  if (g_obs) {
+    // obs_j = sum_i R_ij d_i
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lx.p[i] = lx.p[i] + R[i][0] * g_obs[0] + R[i][1] * g_obs[1] + R[i][2] * g_obs[2];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) LR[i][j] = d[i] * g_obs[j];
+    }
+    const S sg = (x.q[0] < S(0.0f)) ? S(-1.0f) : S(1.0f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lq[i] = sg * g_obs[3 + i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) lx.nu[i] = lx.nu[i] + g_obs[7 + i];
+    rot_vjp(x.q, LR, lq);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lx.q[i] = lx.q[i] + lq[i];
+  }
+  // r = -|d|^2 - 0.1|nu|^2 - 0.01|c|^2
+#pragma unroll
+  for (int i = 0; i < 3; ++i) lx.p[i] = lx.p[i] - S(2.0f) * d[i] * g_rew;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) lx.nu[i] = lx.nu[i] - S(0.2f) * x.nu[i] * g_rew;
+#pragma unroll
+  for (int i = 0; i < NT; ++i) lc[i] = lc[i] - S(0.02f) * c[i] * g_rew;
+}
+
+// Adjoint of one substep. x0 is the substep's start state; `lx` holds the
+// adjoint of its end state on entry and of its start state on exit. The
+// command adjoint and the hydrodynamic-coefficient adjoints accumulate.
+template <typename S, int NT, typename ActT>
+MG_HD void substep_vjp(const St<S, NT>& x0, const S (&c)[NT], const Phys<S>& P, const ActT& A, S h,
+                       St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
+  St<S, NT> x = x0;
+  Tape<S, NT> tp;
+  substep<S, NT, true>(x, c, P, A, h, &tp);
+  const S z0 = S(0.0f);
+
+  // q1 = qn * inv
+  S dot = x.q[0] * lx.q[0] + x.q[1] * lx.q[1] + x.q[2] * lx.q[2] + x.q[3] * lx.q[3];
+  S lqn[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lqn[i] = tp.inv * (lx.q[i] - x.q[i] * dot);
+  // qn = q + hh * W(w1) q ; W(w) q = q (x) (0, w)
+  const S hh = S(0.5f) * h;
+  const S qw = x0.q[0], qx = x0.q[1], qy = x0.q[2], qz = x0.q[3];
+  const S P_ = tp.nu1[3], Q_ = tp.nu1[4], R_ = tp.nu1[5];
+  S lq[4];
+  lq[0] = lqn[0] + hh * (P_ * lqn[1] + Q_ * lqn[2] + R_ * lqn[3]);
+  lq[1] = lqn[1] + hh * (-P_ * lqn[0] - R_ * lqn[2] + Q_ * lqn[3]);
+  lq[2] = lqn[2] + hh * (-Q_ * lqn[0] + R_ * lqn[1] - P_ * lqn[3]);
+  lq[3] = lqn[3] + hh * (-R_ * lqn[0] - Q_ * lqn[1] + P_ * lqn[2]);
+  S lnu1[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) lnu1[j] = lx.nu[j];
+  lnu1[3] = lnu1[3] + hh * (-qx * lqn[0] + qw * lqn[1] + qz * lqn[2] - qy * lqn[3]);
+  lnu1[4] = lnu1[4] + hh * (-qy * lqn[0] - qz * lqn[1] + qw * lqn[2] + qx * lqn[3]);
+  lnu1[5] = lnu1[5] + hh * (-qz * lqn[0] + qy * lqn[1] - qx * lqn[2] + qw * lqn[3]);
+  // p1 = p + h R v1
+  S LR[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      LR[i][j] = h * lx.p[i] * tp.nu1[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    lnu1[j] = lnu1[j] + h * (tp.R[0][j] * lx.p[0] + tp.R[1][j] * lx.p[1] + tp.R[2][j] * lx.p[2]);
+  // lp unchanged (identity).
+  // nu1 = nu + h minv o rhs
+  S lrhs[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    lrhs[j] = h * P.minv[j] * lnu1[j];
+    // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2
+    g.A[j] = g.A[j] - h * tp.rhs[j] * lnu1[j] * P.minv[j] * P.minv[j];
+  }
+  S lnu[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) lnu[j] = lnu1[j];
+  // rhs_lin = tau - m w x v - w x a1 - A_lin o (w x vc) - dmp_lin + (W-B) e
+  // rhs_ang = tau - w x Iw - vr x a1 - w x a2 - dmp_ang - (B rb) x e
+  const S* vr = tp.vr;
+  const S* w = tp.w;
+  const S* vc = tp.vc;
+  const S v[3] = {x0.nu[0], x0.nu[1], x0.nu[2]};
+  S lv[3] = {z0, z0, z0}, lw[3] = {z0, z0, z0}, lvr[3] = {z0, z0, z0}, lvc[3] = {z0, z0, z0};
+  S le[3] = {z0, z0, z0};
+  // (W-B) e  and  -(B rb) x e
+  const S WmB = P.W - P.B;
+  const S Brb[3] = {P.B * P.rb[0], P.B * P.rb[1], P.B * P.rb[2]};
+  {
+    S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    S dummy[3] = {z0, z0, z0};
+    S e[3] = {tp.R[2][0], tp.R[2][1], tp.R[2][2]};
+    cross_vjp(Brb, e, nl, dummy, le);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) le[j] = le[j] + WmB * lrhs[j];
+  }
+  // damping on nu_r
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const S ldm = -lrhs[j];
+    const S a = mabs(vr[j]);
+    lvr[j] = lvr[j] + ldm * (P.dl[j] + S(2.0f) * P.dq[j] * a);
+    g.dl[j] = g.dl[j] + ldm * vr[j];
+    g.dq[j] = g.dq[j] + ldm * a * vr[j];
+    const S ldw = -lrhs[3 + j];
+    const S b = mabs(w[j]);
+    lw[j] = lw[j] + ldw * (P.dl[3 + j] + S(2.0f) * P.dq[3 + j] * b);
+    g.dl[3 + j] = g.dl[3 + j] + ldw * w[j];
+    g.dq[3 + j] = g.dq[3 + j] + ldw * b * w[j];
+  }
+  // C_RB: m w x v ; w x (Ig o w)
+  {
+    S ly[3] = {-P.m * lrhs[0], -P.m * lrhs[1], -P.m * lrhs[2]};
+    cross_vjp(w, v, ly, lw, lv);
+    S Iw[3] = {P.Ig[0] * w[0], P.Ig[1] * w[1], P.Ig[2] * w[2]};
+    S ly2[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    S lIw[3] = {z0, z0, z0};
+    cross_vjp(w, Iw, ly2, lw, lIw);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lw[j] = lw[j] + P.Ig[j] * lIw[j];
+  }
+  // C_A: w x a1 ; vr x a1 + w x a2, a1 = A_lin vr, a2 = A_ang w
+  {
+    S a1[3] = {P.A[0] * vr[0], P.A[1] * vr[1], P.A[2] * vr[2]};
+    S a2[3] = {P.A[3] * w[0], P.A[4] * w[1], P.A[5] * w[2]};
+    S la1[3] = {z0, z0, z0}, la2[3] = {z0, z0, z0};
+    S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
+    S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    cross_vjp(w, a1, nl, lw, la1);
+    cross_vjp(vr, a1, na, lvr, la1);
+    cross_vjp(w, a2, na, lw, la2);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      g.A[j] = g.A[j] + la1[j] * vr[j];
+      lvr[j] = lvr[j] + la1[j] * P.A[j];
+      g.A[3 + j] = g.A[3 + j] + la2[j] * w[j];
+      lw[j] = lw[j] + la2[j] * P.A[3 + j];
+    }
+    // current-acceleration term A_lin o (w x vc)
+    S wxvc[3];
+    cross3(w, vc, wxvc);
+    S lwv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      g.A[j] = g.A[j] - lrhs[j] * wxvc[j];
+      lwv[j] = -lrhs[j] * P.A[j];
+    }
+    cross_vjp(w, vc, lwv, lw, lvc);
+  }
+  // vr = v - vc ; vc = R^T Vc
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lv[j] = lv[j] + lvr[j];
+    lvc[j] = lvc[j] - lvr[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) LR[i][j] = LR[i][j] + P.Vc[i] * lvc[j];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) LR[2][j] = LR[2][j] + le[j];
+  rot_vjp(x0.q, LR, lq);
+  // tau = B f ; f_i = k n1 |n1|
+  S ln1[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    S lf = S(A.alloc[0][i]) * lrhs[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) lf = lf + S(A.alloc[k][i]) * lrhs[k];
+    const S an = mabs(tp.n1[i]);
+    const S df = (an < S(A.dz[i])) ? z0 : S(2.0f) * S(A.kf[i]) * an;
+    ln1[i] = lx.n[i] + lf * df;
+  }
+  // n1 = n + alpha (c - n)
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    lc[i] = lc[i] + S(A.alpha[i]) * ln1[i];
+    lx.n[i] = (S(1.0f) - S(A.alpha[i])) * ln1[i];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lx.nu[j] = lnu[j] + lv[j];
+    lx.nu[3 + j] = lnu[3 + j] + lw[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lx.q[i] = lq[i];
+  // lx.p: identity through p1 = p + ...
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): published multipliers
+// and Weyl increments.
+// ---------------------------------------------------------------------------
+MG_HD void mulhilo64(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+#ifdef __CUDA_ARCH__
+  hi = __umul64hi(a, b);
+  lo = a * b;
+#else
+  unsigned __int128 p = (unsigned __int128)a * b;
+  hi = (uint64_t)(p >> 64);
+  lo = (uint64_t)p;
+#endif
+}
+
+MG_HD void philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1,
+                      uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(M0, c0, hi0, lo0);
+    mulhilo64(M1, c2, hi1, lo1);
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Draw j of (seed, stream, env): block j/4, lane j%4, top 53 bits -> [0,1).
+MG_HD double uniform53(uint64_t seed, uint64_t stream, uint64_t env, uint32_t j) {
+  uint64_t o[4];
+  philox4x64(env, j / 4, 0, 0, seed, stream, o);
+  return (double)(o[j % 4] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+enum : uint64_t { STREAM_DR = 1, STREAM_INIT = 2, STREAM_ACTION = 3 };
+
+}  // namespace mg

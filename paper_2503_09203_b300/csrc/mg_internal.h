@@ -1,0 +1,153 @@
+// Shared host/device records of libmarinegym (not part of the public C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+// One segment of a launch: envs of a single class (and, for serving, of a
+// single request) that share K, the substep length and the actuator factors.
+// Tiles of `threads` envs never straddle segments.
+struct SegDesc {
+  int32_t tile_begin;   // first tile of this segment
+  int32_t n_envs;       // valid envs
+  int32_t cls;          // class index
+  int32_t n_thr;
+  int32_t K;
+  int32_t step0;        // serving: step counter of the request at launch
+  int32_t n4;           // slots of the segment's storage (n_envs rounded up to 4)
+  int32_t pad0;
+  int64_t st_off;       // float offset of the segment's state planes
+  int64_t act_off;      // float offset of the segment's [n4][n_thr] actions
+  int64_t slot_off;     // first slot (obs / reward / parameter planes)
+  int64_t env_base;     // global env id of local env 0 (random draws)
+  float h;
+  float pad1[3];
+  float alpha[8];
+  uint64_t seed;        // serving: action seed
+  uint64_t pad2;
+};
+static_assert(sizeof(SegDesc) == 128, "SegDesc layout");
+
+// Per-class constants in FP32 (staged into shared memory per tile).
+struct ClassF {
+  float alloc[6][8];
+  float kf[8];
+  float dz[8];
+  float phys[36];       // nominal Phys block (current 0)
+  float pad[4];
+};
+static_assert(sizeof(ClassF) == 104 * 4, "ClassF layout");
+
+// Per-class constants in FP64 for the finite-difference check path.
+struct ClassD {
+  double alloc[6][8];
+  double kf[8];
+  double dz[8];
+  double alpha[8];
+  double Mrb[6];        // rigid-body diagonal inertia (m, m, m, Ig)
+};
+
+// Per-env physical parameter block (36 floats, 9 float4 planes) field offsets.
+enum { PAR_MINV = 0, PAR_A = 6, PAR_DL = 12, PAR_DQ = 18, PAR_M = 24, PAR_IG = 25, PAR_W = 28,
+       PAR_B = 29, PAR_RB = 30, PAR_VC = 33, PAR_DIM = 36 };
+
+// Number of float4 parameter planes: 9 for the 36 physical floats + 1 target.
+enum { PAR_PLANES = 9, TGT_PLANE = 9, N_PLANES = 10 };
+
+// A launch covers the segments [seg_lo, seg_hi) of one thruster count, whose
+// tiles are tile_lo .. tile_lo + n_tiles - 1.
+struct StepArgs {
+  const SegDesc* segs;
+  int32_t seg_lo, seg_hi;
+  int32_t tile_lo;
+  int32_t n_tiles;
+  const ClassF* classes;
+  float* state;
+  const float* actions;       // [n_steps][act_stride]
+  int64_t act_stride;
+  int32_t n_steps;
+  int32_t act_mode;           // 0: load actions; 1: Philox actions (serving)
+  const float4* planes;       // [N_PLANES][n_slots] (per-env) or target plane only
+  int32_t per_env;            // 1: physical parameters from planes 0..8
+  int32_t obs_every;          // 1: obs/reward every step; 0: after the last step
+  int64_t n_slots;
+  float* obs;                 // [*][n_slots][13] or null
+  float* reward;              // [*][n_slots] or null
+  float* ret;                 // serving: per-slot sum of rewards (or null)
+  float* ckpt;                // record: [n_ckpt][21][n_slots] or null
+  int32_t ckpt_every;
+  int32_t pad0;
+  uint32_t* status;           // bit 0: non-finite state
+};
+
+struct AdjArgs {
+  const SegDesc* segs;
+  int32_t seg_lo, seg_hi;
+  int32_t tile_lo;
+  int32_t n_tiles;
+  const ClassF* classes;
+  const float4* planes;
+  int64_t n_slots;
+  const float* actions;
+  int64_t act_stride;
+  int32_t T;
+  int32_t ckpt_every;
+  const float* ckpt;          // [n_ckpt][21][n_slots]
+  float* scratch;             // [(ckpt_every*K_max+1)][21][n_slots]
+  const float* g_obs;         // [T][n_slots][13] or null
+  const float* g_rew;         // [T][n_slots] or null
+  const float* g_state_T;     // [n_slots][21] or null
+  float* g_actions;           // [T][act_stride] or null
+  float* g_A;                 // [n_slots][6] or null
+  float* g_D;                 // [n_slots][12] or null
+  float* g_state0;            // [n_slots][21] or null
+};
+
+// Class nominal record for the reset kernel (FP64).
+struct ClassNominal {
+  double mass, Ig[3], rb[3], B, Ma[6], dl[6], dq[6];
+};
+
+struct ResetArgs {
+  const SegDesc* segs;
+  int32_t n_segs;
+  int32_t n_sel;              // number of env ids (or total envs when ids is null)
+  const int32_t* env_ids;     // global env ids or null = all
+  const ClassNominal* nominal;
+  int32_t per_env;
+  int32_t serving;            // 1: draws keyed by (segment seed, env id within the segment)
+  float* state;
+  float4* planes;
+  int64_t n_slots;
+  uint64_t seed;
+  int32_t dr, cur, cur3d, init_mode;
+  double mass_lo, mass_hi, added_lo, added_hi, damp_lo, damp_hi, cob_lo, cob_hi, cur_lo, cur_hi;
+  double target_half, pos_radius, max_angle;
+};
+
+// Arguments of the FP64 finite-difference rollout.
+struct Fp64Args {
+  const SegDesc* segs;
+  int32_t seg_lo, seg_hi;
+  int32_t tile_lo;
+  int32_t n_tiles;
+  const ClassD* classes;
+  const float* state;
+  const float4* planes;
+  int64_t n_slots;
+  const float* actions;
+  int64_t act_stride;
+  int32_t T;
+  int32_t pad0;
+  const double* dA;
+  const double* ddl;
+  const double* ddq;
+  double eps;
+  double h;                   // dt / K in FP64
+  double* reward;
+  double* state_out;
+};
+
+}  // namespace mg

@@ -1,0 +1,827 @@
+// Host runtime of libmarinegym: validation, layout, device buffers, launches,
+// checkpoint/resume, CUDA-graph capture and the launch-shape autotuner. All
+// per-class derived quantities (allocation matrix, rotor factor, inverse
+// inertia) are computed here in FP64 and stored FP32 for the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/marinegym.h"
+#include "mg_internal.h"
+
+namespace mg {
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, int block, cudaStream_t st);
+cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
+cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
+                             cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
+cudaError_t step_kernel_occupancy(int nt, int block, int* blocks_per_sm);
+}  // namespace mg
+
+namespace mg {
+cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st);
+}  // namespace mg
+
+using namespace mg;
+
+static const double kG = 9.81;
+static thread_local std::string g_create_err;
+
+struct ClassLay {
+  int32_t n_envs, n_thr, env_off, slot_off, n4;
+  int64_t st_off, act_off;
+};
+
+// Segments with the same thruster count, launched by one kernel instantiation.
+struct Group {
+  int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles;
+};
+
+struct mg_sim {
+  mg_config cfg;
+  std::vector<int32_t> counts;
+  std::vector<mg_class_desc> classes;
+  std::vector<ClassLay> lay;
+  int32_t n_classes = 0, n_envs = 0, n_slots = 0;
+  int64_t act_floats = 0, state_floats = 0;
+  int32_t threads = 128;
+  int32_t blocks_per_sm = 0;   // 0: one tile per block (grid = tiles)
+  int32_t num_sms = 148;
+  int32_t n_tiles = 0, n_segs = 0;
+  double h = 0.0;
+  std::vector<SegDesc> segs;
+  std::vector<Group> groups;
+  // device
+  float* d_state = nullptr;
+  float4* d_planes = nullptr;
+  int32_t n_planes = 0;
+  ClassF* d_cls = nullptr;
+  ClassD* d_cls64 = nullptr;
+  ClassNominal* d_nominal = nullptr;
+  SegDesc* d_segs = nullptr;
+  uint32_t* d_status = nullptr;
+  float* d_ckpt = nullptr;
+  float* d_scratch = nullptr;
+  float* d_stage = nullptr;
+  size_t stage_floats = 0;
+  int32_t ckpt_every = 20;
+  int32_t rec_T = 0;           // steps of the last recorded rollout (0: none)
+  size_t bytes = 0;
+  std::string err;
+};
+
+struct mg_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static int fail(mg_sim* s, int code, const char* fmt, ...) {
+  if (s) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    s->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(sim, MG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+static bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+static int validate_class(mg_sim* sim, const mg_class_desc& c, int ci) {
+  if (c.n_thr < 1 || c.n_thr > MG_MAX_THR) return fail(sim, MG_ERR_INVALID_ARG, "class %d: n_thr %d not in 1..8", ci, c.n_thr);
+  if (!(std::isfinite(c.mass) && c.mass > 0)) return fail(sim, MG_ERR_INVALID_ARG, "class %d: mass must be > 0", ci);
+  for (int i = 0; i < 3; ++i) {
+    if (!(std::isfinite(c.Ig[i]) && c.Ig[i] > 0)) return fail(sim, MG_ERR_INVALID_ARG, "class %d: inertia must be > 0", ci);
+    if (c.rg[i] != 0.0) return fail(sim, MG_ERR_INVALID_ARG, "class %d: r_g != 0 is not supported", ci);
+    if (!std::isfinite(c.rb[i])) return fail(sim, MG_ERR_INVALID_ARG, "class %d: r_b not finite", ci);
+  }
+  if (!finite_nonneg(c.buoy_ratio)) return fail(sim, MG_ERR_INVALID_ARG, "class %d: buoy_ratio", ci);
+  for (int i = 0; i < 6; ++i)
+    if (!finite_nonneg(c.Ma[i]) || !finite_nonneg(c.dl[i]) || !finite_nonneg(c.dq[i]))
+      return fail(sim, MG_ERR_INVALID_ARG, "class %d: added mass / damping must be finite and >= 0", ci);
+  for (int i = 0; i < c.n_thr; ++i) {
+    if (!finite_nonneg(c.k_f[i]) || !finite_nonneg(c.T_rotor[i]) || !finite_nonneg(c.deadzone[i]))
+      return fail(sim, MG_ERR_INVALID_ARG, "class %d thruster %d: k_f, T_rotor, deadzone must be >= 0", ci, i);
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(c.thr_pos[i][k]) || !std::isfinite(c.thr_dir[i][k]))
+        return fail(sim, MG_ERR_INVALID_ARG, "class %d thruster %d: geometry not finite", ci, i);
+  }
+  return MG_OK;
+}
+
+static void alpha_of(const mg_class_desc& c, double h, double* a) {
+  for (int i = 0; i < 8; ++i) a[i] = 1.0;
+  for (int i = 0; i < c.n_thr; ++i) a[i] = c.T_rotor[i] > 0.0 ? 1.0 - std::exp(-h / c.T_rotor[i]) : 1.0;
+}
+
+// Allocation matrix B = [d_i ; r_i x d_i] (FP64).
+static void alloc_of(const mg_class_desc& c, double B[6][8]) {
+  for (int k = 0; k < 6; ++k) for (int i = 0; i < 8; ++i) B[k][i] = 0.0;
+  for (int i = 0; i < c.n_thr; ++i) {
+    const double* r = c.thr_pos[i];
+    const double* d = c.thr_dir[i];
+    B[0][i] = d[0]; B[1][i] = d[1]; B[2][i] = d[2];
+    B[3][i] = r[1] * d[2] - r[2] * d[1];
+    B[4][i] = r[2] * d[0] - r[0] * d[2];
+    B[5][i] = r[0] * d[1] - r[1] * d[0];
+  }
+}
+
+// Segments ordered by thruster count (then class); tiles are numbered in that
+// order so that each thruster count owns one contiguous tile range.
+static void build_segs(mg_sim* sim) {
+  sim->segs.clear();
+  sim->groups.clear();
+  int tiles = 0;
+  for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
+    Group g;
+    g.nt = nt;
+    g.seg_lo = (int32_t)sim->segs.size();
+    g.tile_lo = tiles;
+    for (int c = 0; c < sim->n_classes; ++c) {
+      const ClassLay& L = sim->lay[c];
+      if (L.n_envs == 0 || L.n_thr != nt) continue;
+      SegDesc sd;
+      std::memset(&sd, 0, sizeof(sd));
+      sd.tile_begin = tiles;
+      sd.n_envs = L.n_envs;
+      sd.cls = c;
+      sd.n_thr = L.n_thr;
+      sd.K = sim->cfg.K;
+      sd.n4 = L.n4;
+      sd.st_off = L.st_off;
+      sd.act_off = L.act_off;
+      sd.slot_off = L.slot_off;
+      sd.env_base = L.env_off;
+      sd.h = (float)sim->h;
+      double a[8];
+      alpha_of(sim->classes[c], sim->h, a);
+      for (int i = 0; i < 8; ++i) sd.alpha[i] = (float)a[i];
+      tiles += (L.n4 + sim->threads - 1) / sim->threads;
+      sim->segs.push_back(sd);
+    }
+    g.seg_hi = (int32_t)sim->segs.size();
+    g.n_tiles = tiles - g.tile_lo;
+    if (g.seg_hi > g.seg_lo) sim->groups.push_back(g);
+  }
+  sim->n_tiles = tiles;
+  sim->n_segs = (int32_t)sim->segs.size();
+}
+
+static int upload_segs(mg_sim* sim) {
+  build_segs(sim);
+  CK(cudaMemcpy(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+static int dev_alloc(mg_sim* sim, void** p, size_t bytes) {
+  if (sim->cfg.mem_budget && sim->bytes + bytes > sim->cfg.mem_budget)
+    return fail(sim, MG_ERR_OOM, "device memory budget of %zu bytes exceeded (%zu needed)", sim->cfg.mem_budget,
+                sim->bytes + bytes);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(sim, MG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  sim->bytes += bytes;
+  return MG_OK;
+}
+
+static void free_all(mg_sim* sim) {
+  void* ps[] = {sim->d_state, sim->d_planes, sim->d_cls, sim->d_cls64, sim->d_nominal,
+                sim->d_segs, sim->d_status, sim->d_ckpt, sim->d_scratch, sim->d_stage};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+static ResetArgs reset_args(mg_sim* sim, const mg_reset_cfg& r, uint64_t seed) {
+  ResetArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = sim->d_segs;
+  a.n_segs = sim->n_segs;
+  a.nominal = sim->d_nominal;
+  a.per_env = sim->cfg.per_env_params;
+  a.state = sim->d_state;
+  a.planes = sim->d_planes;
+  a.n_slots = sim->n_slots;
+  a.seed = seed;
+  a.dr = r.dr_enabled;
+  a.cur = r.current_enabled;
+  a.cur3d = r.current_3d;
+  a.init_mode = r.init_mode;
+  a.mass_lo = r.mass_lo; a.mass_hi = r.mass_hi;
+  a.added_lo = r.added_lo; a.added_hi = r.added_hi;
+  a.damp_lo = r.damp_lo; a.damp_hi = r.damp_hi;
+  a.cob_lo = r.cob_lo; a.cob_hi = r.cob_hi;
+  a.cur_lo = r.cur_lo; a.cur_hi = r.cur_hi;
+  a.target_half = r.target_half; a.pos_radius = r.pos_radius; a.max_angle = r.max_angle;
+  return a;
+}
+
+extern "C" {
+
+const char* mg_strerror(int code) {
+  switch (code) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_OOM: return "out of device memory or over budget";
+    case MG_ERR_CUDA: return "CUDA runtime error";
+    case MG_ERR_NONFINITE: return "non-finite state";
+    case MG_ERR_TIMEOUT: return "bounded wait timed out";
+    case MG_ERR_ADMISSION_REFUSED: return "admission refused";
+    case MG_ERR_STATE: return "invalid call order";
+    default: return "unknown error";
+  }
+}
+
+const char* mg_last_error(const mg_sim* sim) { return sim ? sim->err.c_str() : g_create_err.c_str(); }
+
+int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) {
+  if (!out) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || !classes || !cfg->class_counts) return MG_ERR_INVALID_ARG;
+  mg_sim* sim = new mg_sim();
+  sim->cfg = *cfg;
+  auto bail = [&](int code) {
+    // keep the handle alive only on success; report the message on stderr-free path
+    free_all(sim);
+    g_create_err = sim->err.empty() ? mg_strerror(code) : sim->err;
+    delete sim;
+    return code;
+  };
+  if (cfg->n_classes < 1 || cfg->n_classes > MG_MAX_CLASSES) return bail(MG_ERR_INVALID_ARG);
+  if (!(std::isfinite(cfg->dt) && cfg->dt > 0)) return bail(MG_ERR_INVALID_ARG);
+  if (cfg->K < 1 || cfg->K > 64) return bail(MG_ERR_INVALID_ARG);
+  if (cfg->record_steps < 0 || cfg->ckpt_every < 0) return bail(MG_ERR_INVALID_ARG);
+  if (!cfg->per_env_params && (cfg->reset.dr_enabled || cfg->reset.current_enabled || cfg->record_steps > 0))
+    return bail(MG_ERR_INVALID_ARG);
+  sim->n_classes = cfg->n_classes;
+  sim->classes.assign(classes, classes + cfg->n_classes);
+  sim->counts.assign(cfg->class_counts, cfg->class_counts + cfg->n_classes);
+  for (int c = 0; c < sim->n_classes; ++c) {
+    if (validate_class(sim, sim->classes[c], c) != MG_OK) return bail(MG_ERR_INVALID_ARG);
+    if (sim->counts[c] < 0) return bail(MG_ERR_INVALID_ARG);
+  }
+  sim->h = cfg->dt / cfg->K;
+  sim->ckpt_every = cfg->ckpt_every > 0 ? cfg->ckpt_every : 20;
+  int64_t env = 0, slot = 0, st = 0, act = 0;
+  for (int c = 0; c < sim->n_classes; ++c) {
+    ClassLay L;
+    L.n_envs = sim->counts[c];
+    L.n_thr = sim->classes[c].n_thr;
+    L.env_off = (int32_t)env;
+    L.slot_off = (int32_t)slot;
+    L.n4 = (L.n_envs + 3) & ~3;
+    L.st_off = st;
+    L.act_off = act;
+    env += L.n_envs;
+    slot += L.n4;
+    st += (int64_t)L.n4 * (13 + L.n_thr);
+    act += (int64_t)L.n4 * L.n_thr;
+    sim->lay.push_back(L);
+  }
+  if (env == 0 || slot > (int64_t)1 << 30) return bail(MG_ERR_INVALID_ARG);
+  sim->n_envs = (int32_t)env;
+  sim->n_slots = (int32_t)slot;
+  sim->state_floats = st;
+  sim->act_floats = act;
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
+  cudaDeviceGetAttribute(&sim->num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+  sim->n_planes = cfg->per_env_params ? N_PLANES : 1;
+  int rc;
+  if ((rc = dev_alloc(sim, (void**)&sim->d_state, sizeof(float) * st)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_planes, sizeof(float4) * sim->n_planes * slot)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_cls, sizeof(ClassF) * sim->n_classes)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_cls64, sizeof(ClassD) * sim->n_classes)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_nominal, sizeof(ClassNominal) * sim->n_classes)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_segs, sizeof(SegDesc) * MG_MAX_CLASSES)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_status, sizeof(uint32_t))) != MG_OK) return bail(rc);
+  if (cfg->record_steps > 0) {
+    const int64_t n_ck = (cfg->record_steps + sim->ckpt_every - 1) / sim->ckpt_every;
+    if ((rc = dev_alloc(sim, (void**)&sim->d_ckpt, sizeof(float) * n_ck * 21 * slot)) != MG_OK) return bail(rc);
+    const int64_t n_scr = (int64_t)sim->ckpt_every * cfg->K + 1;
+    if ((rc = dev_alloc(sim, (void**)&sim->d_scratch, sizeof(float) * n_scr * 21 * slot)) != MG_OK) return bail(rc);
+  }
+  {
+    cudaError_t e1 = cudaMemset(sim->d_state, 0, sizeof(float) * st);
+    cudaError_t e2 = cudaMemset(sim->d_planes, 0, sizeof(float4) * sim->n_planes * slot);
+    cudaError_t e3 = cudaMemset(sim->d_status, 0, sizeof(uint32_t));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      fail(sim, MG_ERR_CUDA, "cudaMemset failed");
+      return bail(MG_ERR_CUDA);
+    }
+  }
+  // Class tables.
+  std::vector<ClassF> cf(sim->n_classes);
+  std::vector<ClassD> cd(sim->n_classes);
+  std::vector<ClassNominal> cn(sim->n_classes);
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const mg_class_desc& d = sim->classes[c];
+    double B[6][8], al[8];
+    alloc_of(d, B);
+    alpha_of(d, sim->h, al);
+    ClassF& f = cf[c];
+    ClassD& g = cd[c];
+    std::memset(&f, 0, sizeof(f));
+    std::memset(&g, 0, sizeof(g));
+    for (int k = 0; k < 6; ++k)
+      for (int i = 0; i < 8; ++i) { f.alloc[k][i] = (float)B[k][i]; g.alloc[k][i] = B[k][i]; }
+    for (int i = 0; i < 8; ++i) {
+      const bool on = i < d.n_thr;
+      f.kf[i] = on ? (float)d.k_f[i] : 0.0f; g.kf[i] = on ? d.k_f[i] : 0.0;
+      f.dz[i] = on ? (float)d.deadzone[i] : 0.0f; g.dz[i] = on ? d.deadzone[i] : 0.0;
+      g.alpha[i] = al[i];
+    }
+    const double Mrb[6] = {d.mass, d.mass, d.mass, d.Ig[0], d.Ig[1], d.Ig[2]};
+    for (int j = 0; j < 6; ++j) {
+      g.Mrb[j] = Mrb[j];
+      f.phys[PAR_MINV + j] = (float)(1.0 / (Mrb[j] + d.Ma[j]));
+      f.phys[PAR_A + j] = (float)d.Ma[j];
+      f.phys[PAR_DL + j] = (float)d.dl[j];
+      f.phys[PAR_DQ + j] = (float)d.dq[j];
+    }
+    f.phys[PAR_M] = (float)d.mass;
+    for (int j = 0; j < 3; ++j) { f.phys[PAR_IG + j] = (float)d.Ig[j]; f.phys[PAR_RB + j] = (float)d.rb[j]; }
+    f.phys[PAR_W] = (float)(d.mass * kG);
+    f.phys[PAR_B] = (float)(d.buoy_ratio * d.mass * kG);
+    ClassNominal& n = cn[c];
+    n.mass = d.mass;
+    for (int j = 0; j < 3; ++j) { n.Ig[j] = d.Ig[j]; n.rb[j] = d.rb[j]; }
+    n.B = d.buoy_ratio * d.mass * kG;
+    for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
+  }
+  ce = cudaMemcpy(sim->d_cls, cf.data(), sizeof(ClassF) * cf.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_cls64, cd.data(), sizeof(ClassD) * cd.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_nominal, cn.data(), sizeof(ClassNominal) * cn.size(), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "class upload: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
+  if ((rc = upload_segs(sim)) != MG_OK) return bail(rc);
+  // Rest state with nominal parameters.
+  mg_reset_cfg rest;
+  std::memset(&rest, 0, sizeof(rest));
+  ResetArgs ra = reset_args(sim, rest, 0);
+  ra.n_sel = sim->n_envs;
+  ce = launch_reset(ra, 0);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "initial reset: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
+  *out = sim;
+  return MG_OK;
+}
+
+int mg_destroy(mg_sim* sim) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  free_all(sim);
+  delete sim;
+  return MG_OK;
+}
+
+int mg_get_layout(const mg_sim* sim, mg_layout* out) {
+  if (!sim || !out) return MG_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->n_classes = sim->n_classes;
+  out->n_envs = sim->n_envs;
+  out->n_slots = sim->n_slots;
+  out->action_floats = sim->act_floats;
+  out->state_floats = sim->state_floats;
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    mg_class_layout& o = out->cls[c];
+    o.n_envs = L.n_envs; o.n_thr = L.n_thr; o.env_offset = L.env_off; o.slot_offset = L.slot_off;
+    o.state_offset = L.st_off; o.state_stride = 13 + L.n_thr; o.action_offset = L.act_off;
+  }
+  return MG_OK;
+}
+
+int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (env_ids_dev && (n < 0 || n > sim->n_envs)) return fail(sim, MG_ERR_INVALID_ARG, "reset: bad env count %d", n);
+  ResetArgs a = reset_args(sim, sim->cfg.reset, seed);
+  a.env_ids = env_ids_dev;
+  a.n_sel = env_ids_dev ? n : sim->n_envs;
+  CK(launch_reset(a, (cudaStream_t)stream));
+  sim->rec_T = 0;
+  return MG_OK;
+}
+
+static StepArgs step_args(mg_sim* sim) {
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = sim->d_segs;
+  a.classes = sim->d_cls;
+  a.state = sim->d_state;
+  a.act_stride = sim->act_floats;
+  a.planes = sim->d_planes;
+  a.per_env = sim->cfg.per_env_params;
+  a.n_slots = sim->n_slots;
+  a.status = sim->d_status;
+  a.ckpt_every = sim->ckpt_every;
+  return a;
+}
+
+static int grid_of(mg_sim* sim, const Group& g) {
+  if (sim->blocks_per_sm <= 0) return g.n_tiles;
+  return std::min(g.n_tiles, sim->blocks_per_sm * sim->num_sms);
+}
+
+// Launch the step kernel once per thruster-count group.
+static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
+  for (const Group& g : sim->groups) {
+    a.seg_lo = g.seg_lo;
+    a.seg_hi = g.seg_hi;
+    a.tile_lo = g.tile_lo;
+    a.n_tiles = g.n_tiles;
+    CK(launch_step(a, g.nt, grid_of(sim, g), sim->threads, st));
+  }
+  return MG_OK;
+}
+
+int mg_step(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+            mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!actions_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "step: need actions and n_steps >= 1");
+  StepArgs a = step_args(sim);
+  a.actions = actions_dev;
+  a.n_steps = n_steps;
+  a.obs = obs_dev;
+  a.reward = reward_dev;
+  a.obs_every = 0;
+  int rc = launch_groups(sim, a, (cudaStream_t)stream);
+  sim->rec_T = 0;
+  return rc;
+}
+
+int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+               int32_t record, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!actions_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout: need actions and n_steps >= 1");
+  if (record && (!sim->d_ckpt || n_steps > sim->cfg.record_steps))
+    return fail(sim, MG_ERR_INVALID_ARG, "rollout: record needs record_steps >= n_steps (have %d)", sim->cfg.record_steps);
+  StepArgs a = step_args(sim);
+  a.actions = actions_dev;
+  a.n_steps = n_steps;
+  a.obs = obs_dev;
+  a.reward = reward_dev;
+  a.obs_every = 1;
+  a.ckpt = record ? sim->d_ckpt : nullptr;
+  int rc = launch_groups(sim, a, (cudaStream_t)stream);
+  sim->rec_T = (record && rc == MG_OK) ? n_steps : 0;
+  return rc;
+}
+
+int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream) {
+  if (!sim || !obs_dev) return sim ? fail(sim, MG_ERR_INVALID_ARG, "observe: null obs") : MG_ERR_INVALID_ARG;
+  StepArgs a = step_args(sim);
+  a.n_steps = 0;
+  a.obs = obs_dev;
+  return launch_groups(sim, a, (cudaStream_t)stream);
+}
+
+int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float* obs_host, float* reward_host,
+                 mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!actions_host || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "step_host: need actions and n_steps >= 1");
+  const size_t need = (size_t)n_steps * sim->act_floats + (size_t)sim->n_slots * 14;
+  if (need > sim->stage_floats) {
+    if (sim->d_stage) { cudaFree(sim->d_stage); sim->bytes -= sim->stage_floats * sizeof(float); sim->d_stage = nullptr; }
+    sim->stage_floats = 0;
+    int rc = dev_alloc(sim, (void**)&sim->d_stage, need * sizeof(float));
+    if (rc != MG_OK) return rc;
+    sim->stage_floats = need;
+  }
+  float* d_act = sim->d_stage;
+  float* d_obs = d_act + (size_t)n_steps * sim->act_floats;
+  float* d_rew = d_obs + (size_t)sim->n_slots * 13;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(d_act, actions_host, sizeof(float) * n_steps * sim->act_floats, cudaMemcpyHostToDevice, st));
+  int rc = mg_step(sim, d_act, n_steps, obs_host ? d_obs : nullptr, reward_host ? d_rew : nullptr, stream);
+  if (rc != MG_OK) return rc;
+  if (obs_host) CK(cudaMemcpyAsync(obs_host, d_obs, sizeof(float) * sim->n_slots * 13, cudaMemcpyDeviceToHost, st));
+  if (reward_host) CK(cudaMemcpyAsync(reward_host, d_rew, sizeof(float) * sim->n_slots, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
+                     const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
+                     float* g_state0, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (sim->rec_T <= 0) return fail(sim, MG_ERR_STATE, "backward: no recorded rollout (call mg_rollout with record=1)");
+  if (!actions_dev) return fail(sim, MG_ERR_INVALID_ARG, "backward: actions required");
+  AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = sim->d_segs;
+  a.classes = sim->d_cls;
+  a.planes = sim->d_planes;
+  a.n_slots = sim->n_slots;
+  a.actions = actions_dev;
+  a.act_stride = sim->act_floats;
+  a.T = sim->rec_T;
+  a.ckpt_every = sim->ckpt_every;
+  a.ckpt = sim->d_ckpt;
+  a.scratch = sim->d_scratch;
+  a.g_obs = g_obs;
+  a.g_rew = g_rew;
+  a.g_state_T = g_state_T;
+  a.g_actions = g_actions;
+  a.g_A = g_added_mass;
+  a.g_D = g_damping;
+  a.g_state0 = g_state0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
+  for (const Group& g : sim->groups) {
+    a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
+    CK(launch_adjoint(a, g.nt, sim->threads, st));
+  }
+  return MG_OK;
+}
+
+int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const float* dq_dev, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "set_hydro needs per_env_params");
+  CK(launch_set_hydro(sim->d_planes, sim->n_slots, A_dev, dl_dev, dq_dev, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, const double* dA, const double* ddl,
+                    const double* ddq, double eps, double* reward_dev, double* state_dev, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64 needs per_env_params");
+  if (!actions_dev || !reward_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: bad arguments");
+  Fp64Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = sim->d_segs;
+  a.classes = sim->d_cls64;
+  a.state = sim->d_state;
+  a.planes = sim->d_planes;
+  a.n_slots = sim->n_slots;
+  a.actions = actions_dev;
+  a.act_stride = sim->act_floats;
+  a.T = n_steps;
+  a.dA = dA; a.ddl = ddl; a.ddq = ddq;
+  a.eps = eps;
+  a.h = sim->h;
+  a.reward = reward_dev;
+  a.state_out = state_dev;
+  for (const Group& g : sim->groups) {
+    a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
+    CK(launch_fp64(a, g.nt, sim->threads, (cudaStream_t)stream));
+  }
+  return MG_OK;
+}
+
+// Canonical field j of env (class layout L, local index i) inside the SoA planes.
+static int64_t field_off(const ClassLay& L, int64_t i, int j) {
+  const int SS = 13 + L.n_thr, NF4 = SS / 4;
+  if (j < NF4 * 4) return L.st_off + ((int64_t)(j / 4) * L.n4 + i) * 4 + (j % 4);
+  return L.st_off + (int64_t)NF4 * 4 * L.n4 + (int64_t)(j - NF4 * 4) * L.n4 + i;
+}
+
+int mg_get_state(const mg_sim* csim, float* host, size_t bytes) {
+  mg_sim* sim = const_cast<mg_sim*>(csim);
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(float) * 21 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "get_state: buffer too small");
+  std::vector<float> buf(sim->state_floats);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(buf.data(), sim->d_state, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      float* o = host + (L.env_off + i) * 21;
+      for (int j = 0; j < 21; ++j) o[j] = (j < 13 + L.n_thr) ? buf[field_off(L, i, j)] : 0.0f;
+    }
+  }
+  return MG_OK;
+}
+
+int mg_set_state(mg_sim* sim, const float* host, size_t bytes) {
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(float) * 21 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "set_state: buffer too small");
+  std::vector<float> buf(sim->state_floats, 0.0f);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(buf.data(), sim->d_state, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const float* s = host + (L.env_off + i) * 21;
+      for (int j = 0; j < 13 + L.n_thr; ++j) buf[field_off(L, i, j)] = s[j];
+    }
+  }
+  CK(cudaMemcpy(sim->d_state, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice));
+  sim->rec_T = 0;
+  return MG_OK;
+}
+
+int mg_get_params(const mg_sim* csim, double* host, size_t bytes) {
+  mg_sim* sim = const_cast<mg_sim*>(csim);
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(double) * MG_ENV_PARAM_DIM * (size_t)sim->n_envs)
+    return fail(sim, MG_ERR_INVALID_ARG, "get_params: buffer too small");
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  std::vector<ClassF> cf(sim->n_classes);
+  CK(cudaMemcpy(cf.data(), sim->d_cls, sizeof(ClassF) * cf.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const int64_t slot = L.slot_off + i;
+      float v[40];
+      if (sim->cfg.per_env_params) {
+        for (int k = 0; k < N_PLANES; ++k) {
+          const float4 x = pl[(size_t)k * sim->n_slots + slot];
+          v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+        }
+      } else {
+        for (int k = 0; k < 36; ++k) v[k] = cf[c].phys[k];
+        const float4 x = pl[slot];
+        v[36] = x.x; v[37] = x.y; v[38] = x.z; v[39] = x.w;
+      }
+      double* o = host + (L.env_off + i) * MG_ENV_PARAM_DIM;
+      int q = 0;
+      o[q++] = v[PAR_M];
+      for (int j = 0; j < 3; ++j) o[q++] = v[PAR_IG + j];
+      for (int j = 0; j < 3; ++j) o[q++] = v[PAR_RB + j];
+      o[q++] = v[PAR_W];
+      o[q++] = v[PAR_B];
+      for (int j = 0; j < 6; ++j) o[q++] = v[PAR_A + j];
+      for (int j = 0; j < 6; ++j) o[q++] = v[PAR_DL + j];
+      for (int j = 0; j < 6; ++j) o[q++] = v[PAR_DQ + j];
+      for (int j = 0; j < 3; ++j) o[q++] = v[PAR_VC + j];
+      for (int j = 0; j < 3; ++j) o[q++] = v[36 + j];
+      o[q++] = 0.0;
+    }
+  }
+  return MG_OK;
+}
+
+int mg_set_params(mg_sim* sim, const double* host, size_t bytes) {
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(double) * MG_ENV_PARAM_DIM * (size_t)sim->n_envs)
+    return fail(sim, MG_ERR_INVALID_ARG, "set_params: buffer too small");
+  if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "set_params needs per_env_params");
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const double* s = host + (L.env_off + i) * MG_ENV_PARAM_DIM;
+      const double m = s[0], Ig[3] = {s[1], s[2], s[3]};
+      for (int j = 0; j < 31; ++j)
+        if (!std::isfinite(s[j])) return fail(sim, MG_ERR_INVALID_ARG, "set_params: env %lld not finite", (long long)(L.env_off + i));
+      if (m <= 0 || Ig[0] <= 0 || Ig[1] <= 0 || Ig[2] <= 0)
+        return fail(sim, MG_ERR_INVALID_ARG, "set_params: env %lld mass/inertia must be > 0", (long long)(L.env_off + i));
+      float v[40];
+      const double Mrb[6] = {m, m, m, Ig[0], Ig[1], Ig[2]};
+      for (int j = 0; j < 6; ++j) {
+        const double A = s[9 + j];
+        v[PAR_MINV + j] = (float)(1.0 / (Mrb[j] + A));
+        v[PAR_A + j] = (float)A;
+        v[PAR_DL + j] = (float)s[15 + j];
+        v[PAR_DQ + j] = (float)s[21 + j];
+      }
+      v[PAR_M] = (float)m;
+      for (int j = 0; j < 3; ++j) { v[PAR_IG + j] = (float)Ig[j]; v[PAR_RB + j] = (float)s[4 + j]; v[PAR_VC + j] = (float)s[27 + j]; }
+      v[PAR_W] = (float)s[7];
+      v[PAR_B] = (float)s[8];
+      v[36] = (float)s[30]; v[37] = (float)s[31]; v[38] = (float)s[32]; v[39] = 0.0f;
+      const int64_t slot = L.slot_off + i;
+      for (int k = 0; k < N_PLANES; ++k)
+        pl[(size_t)k * sim->n_slots + slot] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+  }
+  CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+int mg_status(mg_sim* sim, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  uint32_t st = 0;
+  CK(cudaMemcpy(&st, sim->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st & 1u) {
+    CK(cudaMemset(sim->d_status, 0, sizeof(uint32_t)));
+    return fail(sim, MG_ERR_NONFINITE, "a step produced a non-finite state");
+  }
+  return MG_OK;
+}
+
+int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* bps_out) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int steps = 4;
+  float* d_save = nullptr;
+  float* d_act = nullptr;
+  CK(cudaMalloc(&d_save, sizeof(float) * sim->state_floats));
+  if (cudaMalloc(&d_act, sizeof(float) * sim->act_floats * steps) != cudaSuccess) {
+    cudaFree(d_save);
+    return fail(sim, MG_ERR_OOM, "autotune: scratch allocation failed");
+  }
+  cudaMemcpyAsync(d_save, sim->d_state, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(d_act, 0, sizeof(float) * sim->act_floats * steps, st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand_t[] = {64, 128, 256};
+  int best_t = sim->threads, best_b = sim->blocks_per_sm;
+  float best = 1e30f;
+  const int old_t = sim->threads, old_b = sim->blocks_per_sm;
+  for (int t : cand_t) {
+    int occ = 1 << 30;
+    for (const Group& g : sim->groups) {
+      int o = 0;
+      if (step_kernel_occupancy(g.nt, t, &o) != cudaSuccess) o = 0;
+      occ = std::min(occ, o);
+    }
+    if (occ <= 0 || occ == (1 << 30)) continue;
+    sim->threads = t;
+    build_segs(sim);
+    cudaMemcpyAsync(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice, st);
+    for (int b = 0; b <= occ; ++b) {
+      sim->blocks_per_sm = b;   // 0: one tile per block
+      float ms = 0.0f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        mg_rollout(sim, d_act, steps, nullptr, nullptr, 0, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float x = 0.0f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (rep > 0) ms += x;
+      }
+      if (ms < best) { best = ms; best_t = t; best_b = b; }
+    }
+  }
+  (void)old_t; (void)old_b;
+  sim->threads = best_t;
+  sim->blocks_per_sm = best_b;
+  build_segs(sim);
+  cudaMemcpyAsync(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(sim->d_state, d_save, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_save);
+  cudaFree(d_act);
+  sim->rec_T = 0;
+  CK(cudaGetLastError());
+  if (threads_out) *threads_out = best_t;
+  if (bps_out) *bps_out = best_b;
+  return MG_OK;
+}
+
+int mg_graph_capture(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
+                     mg_stream_t stream, mg_graph** out) {
+  if (!sim || !out) return MG_ERR_INVALID_ARG;
+  if (!stream) return fail(sim, MG_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = mg_rollout(sim, actions_dev, n_steps, obs_dev, reward_dev, 0, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != MG_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return fail(sim, MG_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  mg_graph* G = new mg_graph();
+  G->graph = g;
+  e = cudaGraphInstantiate(&G->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete G;
+    return fail(sim, MG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  *out = G;
+  return MG_OK;
+}
+
+int mg_graph_launch(mg_graph* g, mg_stream_t stream) {
+  if (!g) return MG_ERR_INVALID_ARG;
+  return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+int mg_graph_destroy(mg_graph* g) {
+  if (!g) return MG_ERR_INVALID_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,599 @@
+// Serving loop of libmarinegym: continuous batching of rollout requests.
+//
+// A server owns one device arena split into a slot space (per-env parameter
+// planes, hover target and return accumulators, indexed by slot) and a state
+// space (per-request SoA state planes). A scheduler thread repeats ticks:
+//   1. admit pending requests in FIFO order while both spaces have room
+//      (first-fit allocators) and reset their envs on the device;
+//   2. advance every admitted request by one control step in one shared launch
+//      per thruster count (segments = requests, each with its own class, K,
+//      seed and step counter; actions drawn on the device);
+//   3. wait for the tick's completion event, retire finished requests (copy
+//      final state and returns to host memory) and free their space.
+// Requests that arrive while others run are admitted at the next tick, so
+// their work shares launches with the running ones. Nothing on the device
+// waits on the host or on another kernel: every device call is an ordinary
+// launch or copy on the server's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/marinegym.h"
+#include "mg_internal.h"
+
+namespace mg {
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, int block, cudaStream_t st);
+cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
+}  // namespace mg
+
+using namespace mg;
+
+namespace {
+
+const double kG = 9.81;
+const int kThreads = 128;
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, capacity) in units.
+class RangeAlloc {
+ public:
+  explicit RangeAlloc(int64_t cap = 0) { reset(cap); }
+  void reset(int64_t cap) {
+    free_.clear();
+    if (cap > 0) free_[0] = cap;
+    cap_ = cap;
+  }
+  int64_t alloc(int64_t n) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        const int64_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > n) free_[off + n] = len - n;
+        return off;
+      }
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t n) {
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  int64_t capacity() const { return cap_; }
+
+ private:
+  std::map<int64_t, int64_t> free_;
+  int64_t cap_ = 0;
+};
+
+struct Req {
+  int64_t id = 0;
+  mg_request r{};
+  int32_t status = MG_REQ_PENDING;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int64_t steps_done = 0;
+  int32_t n_thr = 0, n4 = 0;
+  int64_t slot_off = -1, st_off = -1;
+  float h = 0;
+  float alpha[8] = {0};
+  std::vector<float> final_state, returns;
+};
+
+// Weighted quantile over (value, weight) samples.
+double wquantile(std::vector<std::pair<double, double>> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  double tot = 0;
+  for (auto& x : v) tot += x.second;
+  double acc = 0;
+  for (auto& x : v) {
+    acc += x.second;
+    if (acc >= q * tot) return x.first;
+  }
+  return v.back().first;
+}
+
+}  // namespace
+
+struct mg_server {
+  mg_server_config cfg{};
+  std::vector<mg_class_desc> classes;
+  int device = 0;
+  // device
+  void* arena = nullptr;
+  ClassF* d_cls = nullptr;
+  ClassNominal* d_nominal = nullptr;
+  SegDesc* d_segs = nullptr;     // tick segment table
+  SegDesc* d_rsegs = nullptr;    // reset segment table
+  float4* d_planes = nullptr;    // [N_PLANES][S]
+  float* d_ret = nullptr;        // [S]
+  float* d_state = nullptr;      // state space (floats)
+  uint32_t* d_status = nullptr;
+  SegDesc* h_segs = nullptr;     // pinned
+  int64_t S = 0, state_cap = 0;
+  RangeAlloc slots, states;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // scheduler
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  int64_t next_id = 1;
+  std::deque<int64_t> pending;
+  std::vector<int64_t> active;
+  std::unordered_map<int64_t, Req> reqs;
+  // stats
+  int64_t requests_done = 0, env_steps = 0, ticks = 0;
+  double busy = 0, last_tick_end = 0;
+  std::vector<std::pair<double, double>> lat;   // (inter-step time, #requests)
+  std::vector<std::pair<double, double>> qdel;  // (queue delay, 1)
+  std::vector<std::pair<double, double>> tick;  // (device time, 1)
+  std::string err;
+  int32_t fatal = MG_OK;
+};
+
+static int sfail(mg_server* s, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+  return code;
+}
+
+static int64_t state_units(int n_thr, int n4) { return (int64_t)n4 * (13 + n_thr); }
+
+// Admit pending requests in FIFO order while they fit; reset their envs.
+static void admit_locked(mg_server* s, std::vector<int64_t>& admitted) {
+  while (!s->pending.empty() && (int)s->active.size() < s->cfg.max_requests) {
+    Req& q = s->reqs[s->pending.front()];
+    const int64_t so = s->slots.alloc(q.n4);
+    if (so < 0) break;
+    const int64_t st = s->states.alloc(state_units(q.n_thr, q.n4));
+    if (st < 0) {
+      s->slots.release(so, q.n4);
+      break;
+    }
+    q.slot_off = so;
+    q.st_off = st;
+    q.status = MG_REQ_RUNNING;
+    q.t_admit = now_s();
+    s->qdel.push_back({q.t_admit - q.t_submit, 1.0});
+    s->active.push_back(q.id);
+    admitted.push_back(q.id);
+    s->pending.pop_front();
+  }
+}
+
+static SegDesc seg_of(const Req& q) {
+  SegDesc sd;
+  std::memset(&sd, 0, sizeof(sd));
+  sd.n_envs = q.r.n_envs;
+  sd.cls = q.r.cls;
+  sd.n_thr = q.n_thr;
+  sd.K = q.r.K;
+  sd.step0 = (int32_t)q.steps_done;
+  sd.n4 = q.n4;
+  sd.st_off = q.st_off;
+  sd.slot_off = q.slot_off;
+  sd.env_base = 0;
+  sd.h = q.h;
+  for (int i = 0; i < 8; ++i) sd.alpha[i] = q.alpha[i];
+  sd.seed = q.r.seed;
+  return sd;
+}
+
+// One scheduler tick. Returns false when there is nothing to do.
+static bool tick_once(mg_server* s) {
+  std::vector<int64_t> admitted;
+  std::vector<SegDesc> segs;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    admit_locked(s, admitted);
+    if (s->active.empty()) return false;
+    // Reset table for new requests.
+    if (!admitted.empty()) {
+      for (size_t k = 0; k < admitted.size(); ++k) segs.push_back(seg_of(s->reqs[admitted[k]]));
+    }
+  }
+  cudaStream_t st = s->stream;
+  if (!segs.empty()) {
+    // Reset each admitted request: one launch per request over its envs.
+    cudaMemcpyAsync(s->d_rsegs, segs.data(), sizeof(SegDesc) * segs.size(), cudaMemcpyHostToDevice, st);
+    for (size_t k = 0; k < segs.size(); ++k) {
+      ResetArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.segs = s->d_rsegs + k;
+      a.n_segs = 1;
+      a.n_sel = segs[k].n_envs;
+      a.nominal = s->d_nominal;
+      a.per_env = 1;
+      a.serving = 1;
+      a.state = s->d_state;
+      a.planes = s->d_planes;
+      a.n_slots = s->S;
+      const mg_reset_cfg& r = s->cfg.reset;
+      a.dr = r.dr_enabled; a.cur = r.current_enabled; a.cur3d = r.current_3d; a.init_mode = r.init_mode;
+      a.mass_lo = r.mass_lo; a.mass_hi = r.mass_hi; a.added_lo = r.added_lo; a.added_hi = r.added_hi;
+      a.damp_lo = r.damp_lo; a.damp_hi = r.damp_hi; a.cob_lo = r.cob_lo; a.cob_hi = r.cob_hi;
+      a.cur_lo = r.cur_lo; a.cur_hi = r.cur_hi; a.target_half = r.target_half; a.pos_radius = r.pos_radius;
+      a.max_angle = r.max_angle;
+      launch_reset(a, st);
+      cudaMemsetAsync(s->d_ret + segs[k].slot_off, 0, sizeof(float) * segs[k].n4, st);
+    }
+    // The reset table must not be overwritten before the resets ran.
+    cudaStreamSynchronize(st);
+  }
+  // Tick table: active requests grouped by thruster count.
+  std::vector<SegDesc> tab;
+  struct G { int nt, lo, hi, tile_lo, tiles; };
+  std::vector<G> groups;
+  int64_t envs = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    int tiles = 0;
+    for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
+      G g{nt, (int)tab.size(), 0, tiles, 0};
+      for (int64_t id : s->active) {
+        const Req& q = s->reqs[id];
+        if (q.n_thr != nt) continue;
+        SegDesc sd = seg_of(q);
+        sd.tile_begin = tiles;
+        tiles += (q.n4 + kThreads - 1) / kThreads;
+        tab.push_back(sd);
+        envs += q.r.n_envs;
+      }
+      g.hi = (int)tab.size();
+      g.tiles = tiles - g.tile_lo;
+      if (g.hi > g.lo) groups.push_back(g);
+    }
+  }
+  std::memcpy(s->h_segs, tab.data(), sizeof(SegDesc) * tab.size());
+  cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(SegDesc) * tab.size(), cudaMemcpyHostToDevice, st);
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = s->d_segs;
+  a.classes = s->d_cls;
+  a.state = s->d_state;
+  a.n_steps = 1;
+  a.act_mode = 1;
+  a.planes = s->d_planes;
+  a.per_env = 1;
+  a.obs_every = 0;
+  a.n_slots = s->S;
+  a.ret = s->d_ret;
+  a.status = s->d_status;
+  a.ckpt_every = 1;
+  cudaEventRecord(s->ev0, st);
+  for (const G& g : groups) {
+    a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
+    launch_step(a, g.nt, g.tiles, kThreads, st);
+  }
+  cudaEventRecord(s->ev1, st);
+  cudaError_t e = cudaEventSynchronize(s->ev1);
+  const double t_end = now_s();
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fatal = MG_ERR_CUDA;
+    s->err = std::string("tick: ") + cudaGetErrorString(e);
+    return false;
+  }
+  // Book-keeping and retirement.
+  std::vector<int64_t> done;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double spacing = s->last_tick_end > 0 ? t_end - s->last_tick_end : ms * 1e-3;
+    s->last_tick_end = t_end;
+    s->ticks++;
+    s->env_steps += envs;
+    s->busy += ms * 1e-3;
+    s->tick.push_back({ms * 1e-3, 1.0});
+    int n_cont = 0;
+    for (int64_t id : s->active) {
+      Req& q = s->reqs[id];
+      // First step of a request admitted this tick is measured from admission.
+      const bool fresh = std::find(admitted.begin(), admitted.end(), id) != admitted.end();
+      if (fresh) s->lat.push_back({t_end - q.t_admit, 1.0});
+      else ++n_cont;
+      q.steps_done++;
+      if (q.steps_done >= q.r.horizon) done.push_back(id);
+    }
+    if (n_cont > 0) s->lat.push_back({spacing, (double)n_cont});
+  }
+  for (int64_t id : done) {
+    Req* qp;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      qp = &s->reqs[id];
+    }
+    Req& q = *qp;
+    const int SS = 13 + q.n_thr, NF4 = SS / 4;
+    std::vector<float> buf((size_t)q.n4 * SS);
+    cudaMemcpyAsync(buf.data(), s->d_state + q.st_off, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, st);
+    std::vector<float> ret(q.n4);
+    cudaMemcpyAsync(ret.data(), s->d_ret + q.slot_off, sizeof(float) * q.n4, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    std::vector<float> fs((size_t)q.r.n_envs * 21, 0.0f);
+    for (int64_t i = 0; i < q.r.n_envs; ++i)
+      for (int j = 0; j < SS; ++j) {
+        const int64_t off = (j < NF4 * 4) ? ((int64_t)(j / 4) * q.n4 + i) * 4 + (j % 4)
+                                          : (int64_t)NF4 * 4 * q.n4 + (int64_t)(j - NF4 * 4) * q.n4 + i;
+        fs[i * 21 + j] = buf[off];
+      }
+    std::lock_guard<std::mutex> lk(s->mu);
+    q.final_state.swap(fs);
+    q.returns.assign(ret.begin(), ret.begin() + q.r.n_envs);
+    q.t_done = now_s();
+    q.status = MG_REQ_DONE;
+    s->slots.release(q.slot_off, q.n4);
+    s->states.release(q.st_off, state_units(q.n_thr, q.n4));
+    s->active.erase(std::find(s->active.begin(), s->active.end(), id));
+    s->requests_done++;
+  }
+  if (!done.empty()) s->cv.notify_all();
+  return true;
+}
+
+static void scheduler(mg_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
+      if (s->stop) return;
+      if (s->fatal != MG_OK) return;
+    }
+    if (!tick_once(s)) {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->fatal != MG_OK) { s->cv.notify_all(); return; }
+      // Nothing admitted and nothing active: wait for a submission or a release.
+      if (s->active.empty()) s->last_tick_end = 0;
+      s->cv.wait_for(lk, std::chrono::milliseconds(1));
+    }
+    s->cv.notify_all();
+  }
+}
+
+extern "C" {
+
+const char* mg_server_last_error(const mg_server* s) { return s ? s->err.c_str() : "null server handle"; }
+
+int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, int32_t n_classes,
+                     mg_server** out) {
+  if (!out || !cfg || !classes || n_classes < 1 || n_classes > MG_MAX_CLASSES) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(cfg->dt > 0) || cfg->max_requests < 1 || cfg->max_requests > 4096 || cfg->max_queue < 1)
+    return MG_ERR_INVALID_ARG;
+  for (int c = 0; c < n_classes; ++c) {
+    const mg_class_desc& d = classes[c];
+    if (d.n_thr < 1 || d.n_thr > 8 || !(d.mass > 0) || d.rg[0] != 0 || d.rg[1] != 0 || d.rg[2] != 0)
+      return MG_ERR_INVALID_ARG;
+  }
+  mg_server* s = new mg_server();
+  s->cfg = *cfg;
+  s->classes.assign(classes, classes + n_classes);
+  cudaGetDevice(&s->device);
+  size_t budget = cfg->budget_bytes;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget = fr / 2;
+  }
+  // Per slot: 10 float4 planes + return; per state unit one float. A slot
+  // holds at most 21 state floats, so size the spaces in that ratio.
+  const size_t per_slot = sizeof(float4) * N_PLANES + sizeof(float) + 21 * sizeof(float);
+  int64_t S = (int64_t)(budget / per_slot) & ~int64_t(3);
+  if (S < 4) { delete s; return MG_ERR_OOM; }
+  s->S = S;
+  s->state_cap = S * 21;
+  const size_t bytes = sizeof(float4) * N_PLANES * S + sizeof(float) * S + sizeof(float) * s->state_cap;
+  auto cleanup = [&](int code) {
+    if (s->arena) cudaFree(s->arena);
+    if (s->d_cls) cudaFree(s->d_cls);
+    if (s->d_nominal) cudaFree(s->d_nominal);
+    if (s->d_segs) cudaFree(s->d_segs);
+    if (s->d_rsegs) cudaFree(s->d_rsegs);
+    if (s->d_status) cudaFree(s->d_status);
+    if (s->h_segs) cudaFreeHost(s->h_segs);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    delete s;
+    return code;
+  };
+  if (cudaMalloc(&s->arena, bytes) != cudaSuccess) { cudaGetLastError(); return cleanup(MG_ERR_OOM); }
+  s->d_planes = (float4*)s->arena;
+  s->d_ret = (float*)(s->d_planes + (size_t)N_PLANES * S);
+  s->d_state = s->d_ret + S;
+  s->slots.reset(S);
+  s->states.reset(s->state_cap);
+  if (cudaMalloc(&s->d_cls, sizeof(ClassF) * n_classes) != cudaSuccess ||
+      cudaMalloc(&s->d_nominal, sizeof(ClassNominal) * n_classes) != cudaSuccess ||
+      cudaMalloc(&s->d_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
+      cudaMalloc(&s->d_rsegs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
+      cudaMalloc(&s->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(&s->h_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(MG_ERR_OOM);
+  }
+  std::vector<ClassF> cf(n_classes);
+  std::vector<ClassNominal> cn(n_classes);
+  for (int c = 0; c < n_classes; ++c) {
+    const mg_class_desc& d = classes[c];
+    ClassF& f = cf[c];
+    std::memset(&f, 0, sizeof(f));
+    for (int i = 0; i < d.n_thr; ++i) {
+      const double* r = d.thr_pos[i];
+      const double* u = d.thr_dir[i];
+      const double B[6] = {u[0], u[1], u[2], r[1] * u[2] - r[2] * u[1], r[2] * u[0] - r[0] * u[2],
+                           r[0] * u[1] - r[1] * u[0]};
+      for (int k = 0; k < 6; ++k) f.alloc[k][i] = (float)B[k];
+      f.kf[i] = (float)d.k_f[i];
+      f.dz[i] = (float)d.deadzone[i];
+    }
+    ClassNominal& n = cn[c];
+    n.mass = d.mass;
+    for (int j = 0; j < 3; ++j) { n.Ig[j] = d.Ig[j]; n.rb[j] = d.rb[j]; }
+    n.B = d.buoy_ratio * d.mass * kG;
+    for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
+  }
+  if (cudaMemcpy(s->d_cls, cf.data(), sizeof(ClassF) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_nominal, cn.data(), sizeof(ClassNominal) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(MG_ERR_CUDA);
+  }
+  s->th = std::thread(scheduler, s);
+  *out = s;
+  return MG_OK;
+}
+
+int mg_server_submit(mg_server* s, const mg_request* r, int64_t* id_out) {
+  if (!s || !r) return MG_ERR_INVALID_ARG;
+  if (r->cls < 0 || r->cls >= (int)s->classes.size() || r->n_envs < 1 || r->horizon < 1 || r->K < 1 || r->K > 64)
+    return sfail(s, MG_ERR_INVALID_ARG, "submit: bad request (class %d, n_envs %d, horizon %d, K %d)", r->cls,
+                 r->n_envs, r->horizon, r->K);
+  Req q;
+  q.r = *r;
+  q.n_thr = s->classes[r->cls].n_thr;
+  q.n4 = (r->n_envs + 3) & ~3;
+  if (q.n4 > s->S || state_units(q.n_thr, q.n4) > s->state_cap)
+    return sfail(s, MG_ERR_ADMISSION_REFUSED, "submit: %d envs can never fit the %lld-slot arena", r->n_envs,
+                 (long long)s->S);
+  const double h = s->cfg.dt / r->K;
+  q.h = (float)h;
+  const mg_class_desc& d = s->classes[r->cls];
+  for (int i = 0; i < 8; ++i)
+    q.alpha[i] = (i < d.n_thr && d.T_rotor[i] > 0) ? (float)(1.0 - std::exp(-h / d.T_rotor[i])) : 1.0f;
+  q.t_submit = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->fatal != MG_OK) return sfail(s, s->fatal, "server stopped: %s", s->err.c_str());
+  if ((int)s->pending.size() >= s->cfg.max_queue)
+    return sfail(s, MG_ERR_ADMISSION_REFUSED, "submit: queue full (%d pending)", (int)s->pending.size());
+  q.id = s->next_id++;
+  s->reqs[q.id] = q;
+  s->pending.push_back(q.id);
+  if (id_out) *id_out = q.id;
+  s->cv.notify_all();
+  return MG_OK;
+}
+
+int mg_server_poll(mg_server* s, int64_t id, mg_request_result* out) {
+  if (!s || !out) return MG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) {
+    out->status = MG_REQ_UNKNOWN;
+    return MG_OK;
+  }
+  const Req& q = it->second;
+  out->status = q.status;
+  out->n_envs = q.r.n_envs;
+  out->t_submit = q.t_submit;
+  out->t_admit = q.t_admit;
+  out->t_done = q.t_done;
+  out->steps_done = q.steps_done;
+  if (q.status == MG_REQ_DONE) {
+    out->final_state = q.final_state.data();
+    out->returns = q.returns.data();
+  }
+  return MG_OK;
+}
+
+int mg_server_release(mg_server* s, int64_t id) {
+  if (!s) return MG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end() || it->second.status != MG_REQ_DONE)
+    return sfail(s, MG_ERR_STATE, "release: request %lld is not done", (long long)id);
+  s->reqs.erase(it);
+  return MG_OK;
+}
+
+int mg_server_wait_idle(mg_server* s, double timeout_s) {
+  if (!s) return MG_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const bool ok = s->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+    return (s->pending.empty() && s->active.empty()) || s->fatal != MG_OK;
+  });
+  if (s->fatal != MG_OK) return s->fatal;
+  return ok ? MG_OK : sfail(s, MG_ERR_TIMEOUT, "wait_idle: %d pending, %d active after %.1f s",
+                            (int)s->pending.size(), (int)s->active.size(), timeout_s);
+}
+
+int mg_server_stats_get(mg_server* s, mg_server_stats* out) {
+  if (!s || !out) return MG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->requests_done = s->requests_done;
+  out->env_steps = s->env_steps;
+  out->ticks = s->ticks;
+  out->busy_seconds = s->busy;
+  out->step_latency_p50 = wquantile(s->lat, 0.50);
+  out->step_latency_p99 = wquantile(s->lat, 0.99);
+  out->queue_delay_p50 = wquantile(s->qdel, 0.50);
+  out->queue_delay_p99 = wquantile(s->qdel, 0.99);
+  out->tick_p50 = wquantile(s->tick, 0.50);
+  out->tick_p99 = wquantile(s->tick, 0.99);
+  return MG_OK;
+}
+
+int mg_server_destroy(mg_server* s) {
+  if (!s) return MG_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->th.joinable()) s->th.join();
+  cudaStreamSynchronize(s->stream);
+  cudaFree(s->arena);
+  cudaFree(s->d_cls);
+  cudaFree(s->d_nominal);
+  cudaFree(s->d_segs);
+  cudaFree(s->d_rsegs);
+  cudaFree(s->d_status);
+  cudaFreeHost(s->h_segs);
+  cudaEventDestroy(s->ev0);
+  cudaEventDestroy(s->ev1);
+  cudaStreamDestroy(s->stream);
+  delete s;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -52,3 +52,38 @@ def random_states(seed: int, n_envs: int, n_thr: np.ndarray, pos_scale: float = 
     n[np.arange(8)[None, :] >= np.asarray(n_thr)[:, None]] = 0.0
     s[:, 13:21] = n
     return s.astype(np.float32)
+
+
+def random_params(seed: int, classes, counts, spread: float = 0.2, current: float = 0.5,
+                  target_half: float = 5.0) -> dict:
+    """Per-env physical parameters drawn around the class values, rounded to
+    float32 so that FP32 and FP64 consumers read identical numbers.
+
+    Returns a dict of arrays keyed mass, Ig, rb, W, B, Ma, dl, dq, Vc, target
+    and cls (env order, envs grouped by class)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cls = env_classes(counts)
+    n = len(cls)
+    f = lambda shape: rng.uniform(1.0 - spread, 1.0 + spread, shape)
+    pick = lambda key: np.array([classes[c][key] for c in cls], dtype=np.float64).reshape(n, -1)
+    out = {}
+    fm = f((n, 1))
+    out["mass"] = (pick("mass") * fm)[:, 0]
+    out["Ig"] = pick("Ig") * fm
+    out["rb"] = pick("rb") * f((n, 1))
+    # Weight and buoyancy near the class's nominal weight (slightly non-neutral).
+    w0 = pick("mass")[:, 0] * 9.81
+    out["W"] = out["mass"] * 9.81
+    out["B"] = w0 * rng.uniform(0.97, 1.03, n)
+    out["Ma"] = pick("Ma") * f((n, 6))
+    out["dl"] = pick("dl") * f((n, 6))
+    out["dq"] = pick("dq") * f((n, 6))
+    psi = rng.uniform(0.0, 2.0 * np.pi, n)
+    sp = rng.uniform(0.0, current, n)
+    out["Vc"] = np.stack([sp * np.cos(psi), sp * np.sin(psi), np.zeros(n)], axis=1)
+    out["target"] = rng.uniform(-target_half, target_half, (n, 3))
+    for k in list(out):
+        out[k] = out[k].astype(np.float32).astype(np.float64)
+    out["cls"] = cls
+    out["rg"] = np.zeros((n, 3))
+    return out

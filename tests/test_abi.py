@@ -1,0 +1,103 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that
+include/marinegym.h declares, its record layouts match the binding's, and the
+host-only paths (argument validation, FLOP count) behave. No compute calls."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2503_09203_b300 import binding as B
+from paper_2503_09203_b300 import build as mgbuild
+from paper_2503_09203_b300 import vehicles
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "marinegym.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mgbuild.build()
+    return B.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(mg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 30
+    out = subprocess.check_output(["nm", "-D", "--defined-only", B.LIB_PATH]).decode()
+    exported = set(re.findall(r"\bT\s+(mg_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_header(lib):
+    names = set(declared_functions())
+    bound = set(B._SIGS) | {"mg_last_error", "mg_strerror", "mg_server_last_error"}
+    assert names == bound
+
+
+def test_record_layouts_match_header(tmp_path):
+    structs = ["mg_class_desc", "mg_reset_cfg", "mg_config", "mg_class_layout", "mg_layout",
+               "mg_server_config", "mg_request", "mg_request_result", "mg_server_stats"]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){"]
+    for s in structs:
+        prog.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for f, _ in getattr(B, s)._fields_:
+            prog.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    prog.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", str(c), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    for line in out:
+        if not line:
+            continue
+        key, val = line.split()
+        if "." in key:
+            s, f = key.split(".")
+            assert getattr(getattr(B, s), f).offset == int(val), key
+        else:
+            assert C.sizeof(getattr(B, key)) == int(val), key
+
+
+def test_flop_count_is_host_only_and_sane(lib):
+    s8, o8 = B.mg_count_flops(8)
+    s4, o4 = B.mg_count_flops(4)
+    assert 300 <= s8 <= 500 and s4 < s8 and 60 <= o8 <= 120
+    with pytest.raises(B.MGError) as e:
+        B.mg_count_flops(9)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env"])
+def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
+    classes = [vehicles.heavy8()]
+    counts, dt, K, per_env, reset = [8], 0.01, 1, True, dict(vehicles.NO_DR)
+    if bad == "dt":
+        dt = -1.0
+    elif bad == "K":
+        K = 0
+    elif bad == "n_thr":
+        classes = [dict(vehicles.heavy8(), n_thr=9)]
+    elif bad == "rg":
+        classes = [dict(vehicles.heavy8(), rg=(0.0, 0.0, 0.01))]
+    elif bad == "counts":
+        counts = [-1]
+    elif bad == "per_env":
+        per_env, reset = False, dict(vehicles.DR_TRAIN)
+    with pytest.raises(B.MGError) as e:
+        B.mg_create(classes, counts, dt, K, per_env, reset)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+
+
+def test_error_strings(lib):
+    for code in (B.MG_OK, B.MG_ERR_INVALID_ARG, B.MG_ERR_OOM, B.MG_ERR_NONFINITE, B.MG_ERR_STATE):
+        assert lib.mg_strerror(code)

@@ -1,0 +1,325 @@
+"""GPU parity of the batched step (CUDA path through the C-ABI) against the
+FP64 oracle on the same seeded inputs.
+
+Tolerances: per-env relative state error <= 1e-5 after one control step from
+an identical FP32 state, and trajectory-relative error <= 1e-3 over 1000 steps
+(error = ||x_gpu - x_ref|| / max(||x_ref||, 1), quaternion sign-aligned).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle
+from paper_2503_09203_b300 import binding as B
+from paper_2503_09203_b300 import vehicles, workloads
+from tests.helpers import align_q, oracle_env_arrays, rel_state_err
+
+pytestmark = pytest.mark.gpu
+
+ONE_STEP_TOL = 1e-5
+TRAJ_TOL = 1e-3
+
+
+def make_sim(classes, counts, K=1, dt=0.01, reset=None, per_env=True, **kw):
+    return B.Sim(classes, counts, dt=dt, K=K, per_env_params=per_env, reset=reset or dict(vehicles.NO_DR), **kw)
+
+
+def set_inputs(sim, classes, counts, seed, n_thr_of_env):
+    p = workloads.random_params(seed, classes, counts)
+    sim.set_params(B.dict_to_params(p, sim.n_envs))
+    s0 = workloads.random_states(seed + 1, sim.n_envs, n_thr_of_env)
+    sim.set_state(s0)
+    return p, s0
+
+
+def n_thr_of(classes, counts):
+    return np.array([classes[c]["n_thr"] for c in workloads.env_classes(counts)])
+
+
+@pytest.mark.parametrize("counts,K", [([1024], 1), ([37, 1, 0, 130, 5], 4), ([3, 5, 7, 9, 11], 8),
+                                      ([129, 128, 127, 4, 256], 2)])
+def test_one_step_matches_oracle(counts, K):
+    classes = vehicles.five_classes()[:len(counts)]
+    sim = make_sim(classes, counts, K=K)
+    nthr = n_thr_of(classes, counts)
+    p, s0 = set_inputs(sim, classes, counts, 100 + K, nthr)
+    a = workloads.actions(7, 1, sim.n_envs)
+    sim.step(sim.pack_actions(a))
+    torch.cuda.synchronize()
+    gpu = sim.get_state()
+    envs = oracle.make_envs(oracle_env_arrays(p))
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0.astype(np.float64), a, 0.01, K)
+    err = rel_state_err(gpu, ref)
+    assert err.max() <= ONE_STEP_TOL, (err.max(), np.argmax(err))
+    # Fused observation and reward of the same step.
+    slots = sim.slots_of_envs()
+    obs = sim.obs.cpu().numpy()[slots]
+    rew = sim.reward.cpu().numpy()[slots]
+    np.testing.assert_allclose(obs, o_ref[0], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(rew, r_ref[0], rtol=1e-5, atol=1e-4)
+    sim.status()
+    sim.close()
+
+
+def test_reset_matches_oracle_draws():
+    classes = vehicles.five_classes()
+    counts = [64, 33, 1, 40, 70]
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=0x4D47)
+    torch.cuda.synchronize()
+    envs, ref_state = oracle.reset(classes, workloads.env_classes(counts), vehicles.HOVER_DR, 0x4D47)
+    ref = oracle.envs_to_arrays(envs)
+    got = B.params_to_dict(sim.get_params())
+    for k in ("mass", "Ig", "rb", "W", "B", "Ma", "dl", "dq", "Vc", "target"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=2e-7, atol=1e-7, err_msg=k)
+    st = sim.get_state()
+    np.testing.assert_allclose(st[:, :13], ref_state[:, :13], rtol=2e-7, atol=1e-7)
+    sim.close()
+
+
+def test_reset_subset_and_full_size_sampled():
+    """The benchmark workload size (1,048,576 envs, 5 classes, hover + DR, K=4):
+    a sampled set of envs after reset + one step against the oracle run on
+    those envs alone (draws are keyed by env id)."""
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(1 << 20, 5)
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=5)
+    a_full = torch.zeros(1, sim.action_floats, device="cuda")
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(sim.n_envs, 2048, replace=False))
+    ids = np.unique(np.concatenate([ids, [0, sim.n_envs - 1] + [sum(counts[:c]) for c in range(1, 5)]]))
+    # Actions for the sampled envs; zeros elsewhere.
+    a_s = workloads.actions(9, 1, len(ids))
+    a_env = np.zeros((1, sim.n_envs, 8), np.float32)
+    a_env[:, ids] = a_s
+    a_full = sim.pack_actions(a_env)
+    sim.step(a_full)
+    torch.cuda.synchronize()
+    gpu = sim.get_state()[ids]
+    ec = workloads.env_classes(counts)[ids]
+    envs, s0 = oracle.reset(classes, ec, vehicles.HOVER_DR, 5, env_ids=ids)
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0, a_s, 0.01, 4)
+    err = rel_state_err(gpu, ref)
+    assert err.max() <= ONE_STEP_TOL, err.max()
+    slots = sim.slots_of_envs()[ids]
+    np.testing.assert_allclose(sim.obs.cpu().numpy()[slots], o_ref[0], rtol=2e-5, atol=2e-5)
+    sim.close()
+
+
+def test_thousand_step_trajectory_plain_workload():
+    """Plain workload: 1024 envs of class 0, no DR, zero current, K=1, dt=0.01,
+    1000 steps of uniform actions from rest."""
+    classes = [vehicles.heavy8()]
+    sim = make_sim(classes, [1024], K=1, per_env=False)
+    sim.reset(seed=0x4D47)
+    T, every = 1000, 50
+    a = workloads.actions(0x4D47, T, 1024)
+    a_dev = sim.pack_actions(a)
+    envs, s_ref = oracle.reset(classes, np.zeros(1024, np.int32), vehicles.NO_DR, 0x4D47)
+    gpu_traj, ref_traj = [], []
+    for t0 in range(0, T, every):
+        B.mg_step(sim.handle, a_dev[t0:t0 + every], every, None, None)
+        torch.cuda.synchronize()
+        gpu_traj.append(sim.get_state().astype(np.float64))
+        s_ref, _, _ = oracle.rollout(classes, envs, s_ref, a[t0:t0 + every], 0.01, 1, obs=False)
+        ref_traj.append(s_ref.copy())
+    g = np.stack(gpu_traj, 1)
+    r = np.stack(ref_traj, 1)
+    g = align_q(g, r)
+    num = np.linalg.norm(g - r, axis=-1).max(1)
+    den = np.maximum(np.linalg.norm(r, axis=-1).max(1), 1.0)
+    traj_err = num / den
+    assert traj_err.max() <= TRAJ_TOL, traj_err.max()
+    sim.status()
+    sim.close()
+
+
+def test_rollout_obs_reward_every_step_and_multi_step_equivalence():
+    classes = vehicles.five_classes()
+    counts = [20, 12, 8, 16, 4]
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=3)
+    s_init = sim.get_state()
+    T = 25
+    a = workloads.actions(11, T, sim.n_envs)
+    a_dev = sim.pack_actions(a)
+    obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    sim.rollout(a_dev, T, obs, rew)
+    torch.cuda.synchronize()
+    s_roll = sim.get_state()
+    # Same rollout as one multi-step launch and as T single-step launches.
+    sim.set_state(s_init)
+    B.mg_step(sim.handle, a_dev, T, None, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(sim.get_state(), s_roll)
+    sim.set_state(s_init)
+    for t in range(T):
+        sim.step(a_dev[t:t + 1])
+    torch.cuda.synchronize()
+    assert np.array_equal(sim.get_state(), s_roll)
+    np.testing.assert_array_equal(sim.obs.cpu().numpy(), obs[-1].cpu().numpy())
+    # Against the oracle from its own reset draws.
+    envs, s0 = oracle.reset(classes, workloads.env_classes(counts), vehicles.HOVER_DR, 3)
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0, a, 0.01, 4)
+    slots = sim.slots_of_envs()
+    o = obs.cpu().numpy()[:, slots]
+    r = rew.cpu().numpy()[:, slots]
+    np.testing.assert_allclose(o, o_ref, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(r, r_ref, rtol=1e-4, atol=1e-3)
+    # Padding slots read zero.
+    pad = np.setdiff1d(np.arange(sim.n_slots), slots)
+    assert np.all(obs.cpu().numpy()[:, pad] == 0) and np.all(rew.cpu().numpy()[:, pad] == 0)
+    sim.close()
+
+
+def test_rest_stays_rest_bit_exact_on_gpu():
+    classes = vehicles.five_classes()
+    counts = [8, 4, 4, 8, 4]
+    sim = make_sim(classes, counts, K=4, per_env=False)
+    sim.reset(seed=1)
+    s0 = sim.get_state()
+    s0[:, 0:3] = np.random.default_rng(0).uniform(-3, 3, (sim.n_envs, 3)).astype(np.float32)
+    sim.set_state(s0)
+    a = sim.new_actions(50)
+    B.mg_step(sim.handle, a, 50, None, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(sim.get_state(), s0)
+    sim.close()
+
+
+def test_env_result_independent_of_co_resident_classes():
+    """Class-3 envs alone vs inside a 5-class mix with the same inputs:
+    bit-identical states (permutation / class-mix invariance)."""
+    classes = vehicles.five_classes()
+    counts_mix = [30, 17, 9, 21, 13]
+    sim = make_sim(classes, counts_mix, K=4)
+    nthr = n_thr_of(classes, counts_mix)
+    p, s0 = set_inputs(sim, classes, counts_mix, 5, nthr)
+    a = workloads.actions(5, 10, sim.n_envs)
+    sim.step(sim.pack_actions(a), n_steps=10)
+    torch.cuda.synchronize()
+    mixed = sim.get_state()
+    lo, hi = sum(counts_mix[:3]), sum(counts_mix[:4])
+    solo = make_sim([classes[3]], [counts_mix[3]], K=4)
+    ps = {k: v[lo:hi] for k, v in p.items()}
+    ps["cls"] = np.zeros(hi - lo, np.int32)
+    solo.set_params(B.dict_to_params(ps, hi - lo))
+    solo.set_state(s0[lo:hi])
+    solo.step(solo.pack_actions(a[:, lo:hi]), n_steps=10)
+    torch.cuda.synchronize()
+    assert np.array_equal(solo.get_state(), mixed[lo:hi])
+    sim.close()
+    solo.close()
+
+
+def test_nonfinite_state_is_reported_and_cleared():
+    sim = make_sim([vehicles.heavy8()], [64], K=1)
+    a = np.zeros((1, 64, 8), np.float32)
+    a[0, 5, 2] = np.nan
+    sim.step(sim.pack_actions(a))
+    with pytest.raises(B.MGError) as e:
+        sim.status()
+    assert e.value.code == B.MG_ERR_NONFINITE
+    sim.status()  # cleared
+    sim.close()
+
+
+def test_state_and_params_roundtrip_byte_exact():
+    classes = vehicles.five_classes()
+    counts = [5, 6, 7, 8, 9]
+    sim = make_sim(classes, counts, K=2, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=77)
+    s = sim.get_state()
+    p = sim.get_params()
+    sim.step(sim.new_actions(1) + 0.3)
+    sim.set_state(s)
+    sim.set_params(p)
+    assert np.array_equal(sim.get_state(), s)
+    p2 = sim.get_params()
+    assert np.array_equal(p2, p)
+    sim.close()
+
+
+def test_error_paths():
+    sim = make_sim([vehicles.heavy8()], [16], K=1, record_steps=0)
+    with pytest.raises(B.MGError) as e:
+        B.mg_step(sim.handle, None, 1, None, None)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+    with pytest.raises(B.MGError) as e:
+        B.mg_step(sim.handle, sim.new_actions(1), 0, None, None)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+    with pytest.raises(B.MGError) as e:
+        B.mg_step_backward(sim.handle, sim.new_actions(1))
+    assert e.value.code == B.MG_ERR_STATE
+    with pytest.raises(B.MGError) as e:
+        B.mg_rollout(sim.handle, sim.new_actions(2), 2, record=True)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+    with pytest.raises(B.MGError) as e:
+        B.mg_create([vehicles.heavy8()], [1 << 20], 0.01, 1, True, None, mem_budget=1 << 20)
+    assert e.value.code == B.MG_ERR_OOM
+    sim.close()
+
+
+def test_host_buffer_step_equals_device_step():
+    classes = vehicles.five_classes()
+    counts = [10, 10, 10, 10, 10]
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=2)
+    s0 = sim.get_state()
+    a = workloads.actions(2, 1, sim.n_envs)
+    a_dev = sim.pack_actions(a)
+    sim.step(a_dev)
+    torch.cuda.synchronize()
+    s_dev, o_dev = sim.get_state(), sim.obs.cpu().numpy().copy()
+    sim.set_state(s0)
+    a_host = a_dev.cpu().pin_memory()
+    o_host = torch.zeros(sim.n_slots, 13).pin_memory()
+    r_host = torch.zeros(sim.n_slots).pin_memory()
+    B.mg_step_host(sim.handle, a_host, 1, o_host, r_host)
+    assert np.array_equal(sim.get_state(), s_dev)
+    assert np.array_equal(o_host.numpy(), o_dev)
+    sim.close()
+
+
+def test_graph_replay_and_autotune_keep_results():
+    classes = vehicles.five_classes()
+    counts = [100, 50, 60, 70, 80]
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.DR_TRAIN))
+    sim.reset(seed=9)
+    s0 = sim.get_state()
+    T = 8
+    a_dev = sim.pack_actions(workloads.actions(4, T, sim.n_envs))
+    obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    sim.rollout(a_dev, T, obs, rew)
+    torch.cuda.synchronize()
+    s_ref, o_ref = sim.get_state(), obs.clone()
+    threads, bps = B.mg_autotune(sim.handle)
+    assert threads in (64, 128, 256) and bps >= 0
+    assert np.array_equal(sim.get_state(), s_ref)   # autotune restores the state
+    sim.set_state(s0)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = B.mg_graph_capture(sim.handle, a_dev, T, obs, rew, stream=st)
+        obs.zero_()
+        B.mg_graph_launch(g, stream=st)
+    st.synchronize()
+    assert np.array_equal(sim.get_state(), s_ref)
+    assert torch.equal(obs, o_ref)
+    B.mg_graph_destroy(g)
+    sim.close()
+
+
+def test_flop_count_matches_hand_count():
+    """The counted substep of the 8-thruster class: rotor 3/thr, thrust 2/thr,
+    allocation 6 x (8 mul + 7 add) = 90; the remaining terms are fixed."""
+    s8, o8 = B.mg_count_flops(8)
+    s4, _ = B.mg_count_flops(4)
+    assert s8 - s4 == 4 * (3 + 2) + 6 * 4 * 2
