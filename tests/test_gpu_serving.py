@@ -1,0 +1,117 @@
+"""Serving loop (continuous batching): admission by device memory, shared
+launches across requests, and per-request results that are identical alone
+and in the mix and match the oracle.
+
+A request's random draws (reset and actions) are keyed by its own seed and
+its envs' indices within the request, so its trajectory does not depend on
+which other requests share its launches.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle
+from paper_2503_09203_b300 import binding as B
+from paper_2503_09203_b300 import vehicles
+from tests.helpers import rel_state_err
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(vehicles.HOVER_DR)
+
+
+def run_alone(classes, req, budget=256 << 20):
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=budget, max_requests=64, reset=CFG)
+    rid = B.mg_server_submit(srv, *req)
+    B.mg_server_wait_idle(srv, 120)
+    out = B.mg_server_poll(srv, rid)
+    B.mg_server_destroy(srv)
+    return out
+
+
+def oracle_request(classes, req):
+    cls, n, horizon, K, seed = req
+    envs, s = oracle.reset(classes, np.full(n, cls, np.int32), CFG, seed)
+    a = np.zeros((horizon, n, 8), np.float32)
+    nt = classes[cls]["n_thr"]
+    for t in range(horizon):
+        for e in range(n):
+            for i in range(nt):
+                a[t, e, i] = oracle.action(seed, e, t, i)
+    s, _, r = oracle.rollout(classes, envs, s, a, 0.01, K)
+    return s, r.sum(0)
+
+
+def test_request_alone_equals_in_mix_and_matches_oracle():
+    classes = vehicles.five_classes()
+    probe = (2, 37, 40, 3, 1234567)
+    alone = run_alone(classes, probe)
+    assert alone["status"] == B.MG_REQ_DONE and alone["steps_done"] == 40
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=CFG)
+    rng = np.random.default_rng(0)
+    others = [(int(rng.integers(0, 5)), int(rng.integers(1, 3000)), int(rng.integers(5, 80)),
+               int(rng.integers(1, 9)), int(rng.integers(1 << 40))) for _ in range(24)]
+    ids = [B.mg_server_submit(srv, *r) for r in others[:12]]
+    time.sleep(0.02)                      # the probe arrives while others run
+    pid = B.mg_server_submit(srv, *probe)
+    for r in others[12:]:
+        ids.append(B.mg_server_submit(srv, *r))
+        time.sleep(0.002)
+    B.mg_server_wait_idle(srv, 300)
+    mixed = B.mg_server_poll(srv, pid)
+    st = B.mg_server_stats_get(srv)
+    B.mg_server_destroy(srv)
+    assert mixed["status"] == B.MG_REQ_DONE
+    assert np.array_equal(mixed["final_state"], alone["final_state"])
+    assert np.array_equal(mixed["returns"], alone["returns"])
+    # Shared launches actually happened: fewer ticks than total request steps.
+    assert st["ticks"] < sum(r[2] for r in others) + probe[2]
+    s_ref, ret_ref = oracle_request(classes, probe)
+    err = rel_state_err(alone["final_state"].astype(np.float64), s_ref)
+    assert err.max() <= 1e-3, err.max()
+    np.testing.assert_allclose(alone["returns"], ret_ref, rtol=1e-4, atol=1e-3)
+
+
+def test_admission_waits_for_memory_and_refuses_impossible_requests():
+    classes = vehicles.five_classes()
+    # Budget for roughly 2 x 4096 envs: requests queue until space frees up.
+    per_slot = 16 * 10 + 4 + 21 * 4
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=per_slot * 8200, max_requests=16, reset=CFG)
+    with pytest.raises(B.MGError) as e:
+        B.mg_server_submit(srv, 0, 100000, 10, 1, 1)
+    assert e.value.code == B.MG_ERR_ADMISSION_REFUSED
+    ids = [B.mg_server_submit(srv, k % 5, 4000, 20, 2, k) for k in range(8)]
+    B.mg_server_wait_idle(srv, 300)
+    res = [B.mg_server_poll(srv, i) for i in ids]
+    assert all(r["status"] == B.MG_REQ_DONE for r in res)
+    # No more than two fit at once, so later requests waited in the queue.
+    admits = sorted(r["t_admit"] for r in res)
+    dones = sorted(r["t_done"] for r in res)
+    assert admits[2] >= dones[0] - 1e-3
+    for i in ids:
+        B.mg_server_release(srv, i)
+    assert B.mg_server_poll(srv, ids[0])["status"] == B.MG_REQ_UNKNOWN
+    with pytest.raises(B.MGError):
+        B.mg_server_submit(srv, 7, 10, 10, 1, 1)   # no such class
+    B.mg_server_destroy(srv)
+
+
+def test_serving_stats_report_latency_quantiles():
+    classes = vehicles.five_classes()
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=128 << 20, max_requests=64, reset=CFG)
+    rng = np.random.default_rng(4)
+    for k in range(30):
+        B.mg_server_submit(srv, int(rng.integers(0, 5)), int(rng.integers(1, 2000)), int(rng.integers(1, 50)),
+                           int(rng.integers(1, 9)), k)
+    B.mg_server_wait_idle(srv, 300)
+    st = B.mg_server_stats_get(srv)
+    B.mg_server_destroy(srv)
+    assert st["requests_done"] == 30
+    assert 0 < st["step_latency_p50"] <= st["step_latency_p99"]
+    assert 0 < st["tick_p50"] <= st["tick_p99"]
+    assert st["env_steps"] > 0 and st["busy_seconds"] > 0
