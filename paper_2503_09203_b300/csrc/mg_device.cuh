@@ -77,6 +77,21 @@ MG_HD void rot(const S q[4], S R[3][3]) {
   R[2][2] = one - two * (x * x + y * y);
 }
 
+// Actuator-table access: row k of the allocation matrix, and the thrust
+// constant, dead zone and rotor factor vectors. Generic versions index the
+// arrays of an Act<S> (or a volatile view of one); the hot kernel supplies
+// overloads for its shared-memory view that use vector loads.
+template <typename S, int NT, typename ActT>
+MG_HD void act_row(const ActT& A, int k, S (&r)[NT]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) r[i] = S(A.alloc[k][i]);
+}
+template <typename S, int NT, typename ActT>
+MG_HD void act_rotor(const ActT& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) { kf[i] = S(A.kf[i]); dz[i] = S(A.dz[i]); al[i] = S(A.alpha[i]); }
+}
+
 // Intermediates of one substep kept for the vector-Jacobian product.
 template <typename S, int NT>
 struct Tape {
@@ -86,23 +101,31 @@ struct Tape {
 // a1-a8. `x` is updated in place; `c` is the clamped command (zero-order hold).
 // `A` is an Act<S> or a volatile view of one in shared memory (a volatile view
 // keeps the class table in shared memory instead of hoisting it into registers).
-template <typename S, int NT, bool TAPE, typename ActT>
-MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const Phys<S>& P, const ActT& A, S h,
+// `P` is a Phys<S> or a view with the same members (arrays minv, A, dl, dq,
+// Ig, rb, Vc and scalars m, W, B) that reads shared memory on use.
+template <typename S, int NT, bool TAPE, typename ActT, typename PhysT>
+MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
                    Tape<S, NT>* tp) {
   // a1 + a2
   S f[NT];
+  {
+    S kf[NT], dz[NT], al[NT];
+    act_rotor<S, NT>(A, kf, dz, al);
 #pragma unroll
-  for (int i = 0; i < NT; ++i) {
-    x.n[i] = x.n[i] + S(A.alpha[i]) * (c[i] - x.n[i]);
-    const S an = mabs(x.n[i]);
-    f[i] = (an < S(A.dz[i])) ? S(0.0f) : S(A.kf[i]) * x.n[i] * an;
+    for (int i = 0; i < NT; ++i) {
+      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+      const S an = mabs(x.n[i]);
+      f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
+    }
   }
   S tau[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    S s = S(A.alloc[k][0]) * f[0];
+    S r[NT];
+    act_row<S, NT>(A, k, r);
+    S s = r[0] * f[0];
 #pragma unroll
-    for (int i = 1; i < NT; ++i) s = s + S(A.alloc[k][i]) * f[i];
+    for (int i = 1; i < NT; ++i) s = s + r[i] * f[i];
     tau[k] = s;
   }
   // a3
@@ -113,18 +136,18 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const Phys<S>& P, const ActT&
   S vc[3], vr[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    vc[j] = R[0][j] * P.Vc[0] + R[1][j] * P.Vc[1] + R[2][j] * P.Vc[2];
+    vc[j] = R[0][j] * S(P.Vc[0]) + R[1][j] * S(P.Vc[1]) + R[2][j] * S(P.Vc[2]);
     vr[j] = v[j] - vc[j];
   }
   // a4
   S wxv[3], Iw[3], wxIw[3];
   cross3(w, v, wxv);
-  Iw[0] = P.Ig[0] * w[0]; Iw[1] = P.Ig[1] * w[1]; Iw[2] = P.Ig[2] * w[2];
+  Iw[0] = S(P.Ig[0]) * w[0]; Iw[1] = S(P.Ig[1]) * w[1]; Iw[2] = S(P.Ig[2]) * w[2];
   cross3(w, Iw, wxIw);
   // a5
   S a1[3], a2[3], wxa1[3], vrxa1[3], wxa2[3], wxvc[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) { a1[j] = P.A[j] * vr[j]; a2[j] = P.A[3 + j] * w[j]; }
+  for (int j = 0; j < 3; ++j) { a1[j] = S(P.A[j]) * vr[j]; a2[j] = S(P.A[3 + j]) * w[j]; }
   cross3(w, a1, wxa1);
   cross3(vr, a1, vrxa1);
   cross3(w, a2, wxa2);
@@ -133,23 +156,24 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const Phys<S>& P, const ActT&
   S dmp[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    dmp[j] = (P.dl[j] + P.dq[j] * mabs(vr[j])) * vr[j];
-    dmp[3 + j] = (P.dl[3 + j] + P.dq[3 + j] * mabs(w[j])) * w[j];
+    dmp[j] = (S(P.dl[j]) + S(P.dq[j]) * mabs(vr[j])) * vr[j];
+    dmp[3 + j] = (S(P.dl[3 + j]) + S(P.dq[3 + j]) * mabs(w[j])) * w[j];
   }
   // a7: e = R^T e_3 is the third row of R.
   const S e[3] = {R[2][0], R[2][1], R[2][2]};
-  const S WmB = P.W - P.B;
-  S Brb[3] = {P.B * P.rb[0], P.B * P.rb[1], P.B * P.rb[2]}, mb[3];
+  const S Pw = S(P.W), Pb = S(P.B);
+  const S WmB = Pw - Pb;
+  S Brb[3] = {Pb * S(P.rb[0]), Pb * S(P.rb[1]), Pb * S(P.rb[2])}, mb[3];
   cross3(Brb, e, mb);
   // a8
   S rhs[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    rhs[j] = tau[j] - P.m * wxv[j] - wxa1[j] - P.A[j] * wxvc[j] - dmp[j] + WmB * e[j];
+    rhs[j] = tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j];
     rhs[3 + j] = tau[3 + j] - wxIw[j] - vrxa1[j] - wxa2[j] - dmp[3 + j] - mb[j];
   }
 #pragma unroll
-  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (P.minv[j] * rhs[j]);
+  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (S(P.minv[j]) * rhs[j]);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     x.p[i] = x.p[i] + h * (R[i][0] * x.nu[0] + R[i][1] * x.nu[1] + R[i][2] * x.nu[2]);
@@ -201,7 +225,7 @@ MG_HD void observe(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], S obs[1
   S cc = c[0] * c[0];
 #pragma unroll
   for (int i = 1; i < NT; ++i) cc = cc + c[i] * c[i];
-  rew = -dd - S(0.1f) * vv - S(0.01f) * cc;
+  rew = -dd - S(0.1) * vv - S(0.01) * cc;
 }
 
 // ---------------------------------------------------------------------------
@@ -270,9 +294,9 @@ MG_HD void observe_vjp(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], con
 #pragma unroll
   for (int i = 0; i < 3; ++i) lx.p[i] = lx.p[i] - S(2.0f) * d[i] * g_rew;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) lx.nu[i] = lx.nu[i] - S(0.2f) * x.nu[i] * g_rew;
+  for (int i = 0; i < 6; ++i) lx.nu[i] = lx.nu[i] - S(0.2) * x.nu[i] * g_rew;
 #pragma unroll
-  for (int i = 0; i < NT; ++i) lc[i] = lc[i] - S(0.02f) * c[i] * g_rew;
+  for (int i = 0; i < NT; ++i) lc[i] = lc[i] - S(0.02) * c[i] * g_rew;
 }
 
 // Adjoint of one substep. x0 is the substep's start state; `lx` holds the

@@ -148,11 +148,84 @@ __device__ __forceinline__ void load_actions(const float* base, float (&a)[NT]) 
   }
 }
 
-// Shared-memory tile: actuator table, nominal physics and the observation tile.
-struct TileSmem {
-  Act<float> act;
-  float phys[36];
+// ---------------------------------------------------------------------------
+// Shared-memory views read at the point of use. Class constants and per-env
+// parameters stay in shared memory (vector loads for the actuator table)
+// instead of occupying registers across the substep loop; the loads are
+// volatile so that they are not hoisted out of the loop.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ float lds1(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float4 lds4(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+
+// Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
+struct ActSmem {
+  unsigned base;
 };
+enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
+
+template <int NT>
+__device__ __forceinline__ void lds_vec(unsigned a, float (&r)[NT]) {
+#pragma unroll
+  for (int q = 0; q < (NT + 3) / 4; ++q) {
+    const float4 v = lds4(a + 16 * q);
+    if (4 * q + 0 < NT) r[(4 * q + 0) % NT] = v.x;
+    if (4 * q + 1 < NT) r[(4 * q + 1) % NT] = v.y;
+    if (4 * q + 2 < NT) r[(4 * q + 2) % NT] = v.z;
+    if (4 * q + 3 < NT) r[(4 * q + 3) % NT] = v.w;
+  }
+}
+template <typename S, int NT>
+__device__ __forceinline__ void act_row(const ActSmem& A, int k, S (&r)[NT]) {
+  lds_vec<NT>(A.base + 4 * (SA_ALLOC + 8 * k), r);
+}
+template <typename S, int NT>
+__device__ __forceinline__ void act_rotor(const ActSmem& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
+  lds_vec<NT>(A.base + 4 * SA_KF, kf);
+  lds_vec<NT>(A.base + 4 * SA_DZ, dz);
+  lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
+}
+
+// Physical parameters in shared memory, field f at base + 4 * f * STRIDE
+// (STRIDE = 1: class block read as a broadcast; STRIDE = tile width: per-env
+// columns, one per thread, bank-conflict free).
+template <int OFF, int STRIDE>
+struct SArr {
+  unsigned base;
+  __device__ __forceinline__ float operator[](int j) const { return lds1(base + 4u * (unsigned)((OFF + j) * STRIDE)); }
+};
+template <int OFF, int STRIDE>
+struct SScl {
+  unsigned base;
+  __device__ __forceinline__ operator float() const { return lds1(base + 4u * (unsigned)(OFF * STRIDE)); }
+};
+template <int STRIDE>
+struct PhysSmem {
+  SArr<PAR_MINV, STRIDE> minv;
+  SArr<PAR_A, STRIDE> A;
+  SArr<PAR_DL, STRIDE> dl;
+  SArr<PAR_DQ, STRIDE> dq;
+  SScl<PAR_M, STRIDE> m;
+  SArr<PAR_IG, STRIDE> Ig;
+  SScl<PAR_W, STRIDE> W;
+  SScl<PAR_B, STRIDE> B;
+  SArr<PAR_RB, STRIDE> rb;
+  SArr<PAR_VC, STRIDE> Vc;
+  __device__ __forceinline__ explicit PhysSmem(unsigned b)
+      : minv{b}, A{b}, dl{b}, dq{b}, m{b}, Ig{b}, W{b}, B{b}, rb{b}, Vc{b} {}
+};
+
+constexpr int STEP_BLK = 128;
 
 // Cooperative store of the observation tile (nv4 envs x 13 floats, 16-byte
 // aligned on both sides) from shared memory to global memory.
@@ -163,26 +236,35 @@ __device__ __forceinline__ void store_obs_tile(const float* s_obs, float* g_obs,
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
-template <int NT>
-__device__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const TileSmem& ts, float* s_obs) {
-  const int64_t local0 = (int64_t)(tile - sd.tile_begin) * blockDim.x;
+template <int NT, bool PER_ENV>
+__device__ __forceinline__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
+                                          const float* s_phys, float* s_obs, float* s_par) {
+  const int64_t local0 = (int64_t)(tile - sd.tile_begin) * STEP_BLK;
   const int64_t i = local0 + threadIdx.x;
   const bool valid = i < sd.n_envs;
   const bool in_storage = i < sd.n4;
-  const int nv4 = (int)min((int64_t)blockDim.x, (int64_t)sd.n4 - local0);
+  const int nv4 = (int)min((int64_t)STEP_BLK, (int64_t)sd.n4 - local0);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
+  const ActSmem A{smem_addr(s_act)};
 
   St<float, NT> x;
-  Phys<float> P;
-  float tgt[3] = {0.0f, 0.0f, 0.0f};
   if (valid) {
     load_state<NT>(st_base, sd.n4, i, x);
-    if (a.per_env) load_phys(a.planes, a.n_slots, slot, P);
-    else phys_from_array(ts.phys, P);
-    const float4 tg = __ldg(&a.planes[(a.per_env ? TGT_PLANE : 0) * a.n_slots + slot]);
-    tgt[0] = tg.x; tgt[1] = tg.y; tgt[2] = tg.z;
+    if (PER_ENV) {
+#pragma unroll
+      for (int k = 0; k < PAR_PLANES; ++k) {
+        const float4 v = __ldg(&a.planes[k * a.n_slots + slot]);
+        s_par[(4 * k + 0) * STEP_BLK + threadIdx.x] = v.x;
+        s_par[(4 * k + 1) * STEP_BLK + threadIdx.x] = v.y;
+        s_par[(4 * k + 2) * STEP_BLK + threadIdx.x] = v.z;
+        s_par[(4 * k + 3) * STEP_BLK + threadIdx.x] = v.w;
+      }
+    }
   }
+  // Each thread reads only its own parameter column: no barrier needed.
+  using PV = PhysSmem<PER_ENV ? STEP_BLK : 1>;
+  const PV P(PER_ENV ? smem_addr(s_par) + 4u * threadIdx.x : smem_addr(s_phys));
   float c[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) c[j] = 0.0f;
@@ -201,7 +283,7 @@ __device__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const 
           philox4x64((uint64_t)i, (uint64_t)(sd.step0 + t), (uint64_t)g, 0, sd.seed, STREAM_ACTION, o);
 #pragma unroll
           for (int l = 0; l < 4; ++l)
-            if (4 * g + l < NT) c[4 * g + l] = clamp1(action_of_bits(o[l]));
+            if (4 * g + l < NT) c[(4 * g + l) % NT] = clamp1(action_of_bits(o[l]));
         }
       }
       if (a.ckpt && (t % a.ckpt_every) == 0) {
@@ -209,10 +291,9 @@ __device__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const 
         state_to_fields<NT>(x, f);
         float* ck = a.ckpt + (int64_t)(t / a.ckpt_every) * 21 * a.n_slots + slot;
 #pragma unroll
-        for (int j = 0; j < 21; ++j) ck[j * a.n_slots] = (j < 13 + NT) ? f[j] : 0.0f;
+        for (int j = 0; j < 21; ++j) ck[j * a.n_slots] = (j < 13 + NT) ? f[j % (13 + NT)] : 0.0f;
       }
-      const volatile Act<float>& va = ts.act;
-      for (int k = 0; k < sd.K; ++k) substep<float, NT, false>(x, c, P, va, sd.h, nullptr);
+      for (int k = 0; k < sd.K; ++k) substep<float, NT, false>(x, c, P, A, sd.h, nullptr);
     }
     const bool emit = a.obs_every || t == n_out_steps - 1;
     if (emit) {
@@ -220,7 +301,11 @@ __device__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const 
       float o[13], r = 0.0f;
 #pragma unroll
       for (int j = 0; j < 13; ++j) o[j] = 0.0f;
-      if (valid) observe<float, NT>(x, c, tgt, o, r);
+      if (valid) {
+        const float4 tg = __ldg(&a.planes[(PER_ENV ? TGT_PLANE : 0) * a.n_slots + slot]);
+        const float tgt[3] = {tg.x, tg.y, tg.z};
+        observe<float, NT>(x, c, tgt, o, r);
+      }
       if (a.obs) {
 #pragma unroll
         for (int j = 0; j < 13; ++j) s_obs[threadIdx.x * 13 + j] = o[j];
@@ -247,34 +332,31 @@ __device__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const 
   }
 }
 
-__device__ __forceinline__ void stage_class(const StepArgs& a, const SegDesc& sd, TileSmem& ts) {
-  const ClassF& cf = a.classes[sd.cls];
-  for (int k = threadIdx.x; k < 48 + 8 + 8 + 8 + 36; k += blockDim.x) {
-    if (k < 48) (&ts.act.alloc[0][0])[k] = cf.alloc[k / 8][k % 8];
-    else if (k < 56) ts.act.kf[k - 48] = cf.kf[k - 48];
-    else if (k < 64) ts.act.dz[k - 56] = cf.dz[k - 56];
-    else if (k < 72) ts.act.alpha[k - 64] = sd.alpha[k - 64];
-    else ts.phys[k - 72] = cf.phys[k - 72];
-  }
-}
-
 // Persistent-capable step kernel for envs with NT thrusters: each block walks
-// tiles tile_lo + blockIdx.x, + gridDim.x, ... A tile is blockDim.x envs of
-// one segment. One instantiation per thruster count keeps each kernel's
-// register allocation to its own arithmetic.
-template <int NT>
-__global__ void __launch_bounds__(256) mg_step_kernel(const __grid_constant__ StepArgs a) {
-  __shared__ TileSmem ts;
-  extern __shared__ float4 dyn_smem[];
-  float* s_obs = reinterpret_cast<float*>(dyn_smem);
+// tiles tile_lo + blockIdx.x, + gridDim.x, ... A tile is 128 envs of one
+// segment. One instantiation per thruster count (and parameter source) keeps
+// each kernel's register allocation to its own arithmetic.
+template <int NT, bool PER_ENV>
+__global__ void __launch_bounds__(STEP_BLK, 6) mg_step_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ __align__(16) float s_act[SA_DIM];
+  __shared__ __align__(16) float s_phys[PAR_DIM];
+  __shared__ __align__(16) float s_obs[STEP_BLK * 13];
+  __shared__ __align__(16) float s_par[PER_ENV ? PAR_DIM * STEP_BLK : 4];
   for (int tt = blockIdx.x; tt < a.n_tiles; tt += gridDim.x) {
     const int tile = a.tile_lo + tt;
     const int si = a.seg_lo + find_seg(a.segs + a.seg_lo, a.seg_hi - a.seg_lo, tile);
     const SegDesc& sd = a.segs[si];
     __syncthreads();
-    stage_class(a, sd, ts);
+    const ClassF& cf = a.classes[sd.cls];
+    for (int k = threadIdx.x; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
+      if (k < 48) s_act[k] = cf.alloc[k / 8][k % 8];
+      else if (k < 56) s_act[k] = cf.kf[k - 48];
+      else if (k < 64) s_act[k] = cf.dz[k - 56];
+      else if (k < 72) s_act[k] = sd.alpha[k - 64];
+      else s_phys[k - 72] = cf.phys[k - 72];
+    }
     __syncthreads();
-    step_tile<NT>(a, sd, tile, ts, s_obs);
+    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, s_obs, s_par);
   }
 }
 
@@ -615,12 +697,17 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
     default: return cudaErrorInvalidValue; \
   }
 
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, int block, cudaStream_t st) {
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
-  const size_t smem = (size_t)block * 13 * sizeof(float);
-#define MG_L(N) mg_step_kernel<N><<<grid, block, smem, st>>>(a)
-  MG_NT_SWITCH(nt, MG_L)
+  if (a.per_env) {
+#define MG_L(N) mg_step_kernel<N, true><<<grid, STEP_BLK, 0, st>>>(a)
+    MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
+  } else {
+#define MG_L(N) mg_step_kernel<N, false><<<grid, STEP_BLK, 0, st>>>(a)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  }
   return cudaGetLastError();
 }
 
@@ -652,11 +739,16 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t step_kernel_occupancy(int nt, int block, int* blocks_per_sm) {
-  const size_t smem = (size_t)block * 13 * sizeof(float);
-#define MG_L(N) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<N>, block, smem)
-  MG_NT_SWITCH(nt, MG_L)
+cudaError_t step_kernel_occupancy(int nt, bool per_env, int* blocks_per_sm) {
+  if (per_env) {
+#define MG_L(N) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<N, true>, STEP_BLK, 0)
+    MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
+  } else {
+#define MG_L(N) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<N, false>, STEP_BLK, 0)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -16,12 +16,12 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, int block, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
-cudaError_t step_kernel_occupancy(int nt, int block, int* blocks_per_sm);
+cudaError_t step_kernel_occupancy(int nt, bool per_env, int* blocks_per_sm);
 }  // namespace mg
 
 namespace mg {
@@ -448,7 +448,7 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    CK(launch_step(a, g.nt, grid_of(sim, g), sim->threads, st));
+    CK(launch_step(a, g.nt, grid_of(sim, g), st));
   }
   return MG_OK;
 }
@@ -740,35 +740,31 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand_t[] = {64, 128, 256};
+  // Tiles are 128 envs (the kernels' fixed block); the tuned knob is the grid:
+  // one block per tile (0) or a persistent grid of b blocks per SM.
   int best_t = sim->threads, best_b = sim->blocks_per_sm;
   float best = 1e30f;
   const int old_t = sim->threads, old_b = sim->blocks_per_sm;
-  for (int t : cand_t) {
-    int occ = 1 << 30;
-    for (const Group& g : sim->groups) {
-      int o = 0;
-      if (step_kernel_occupancy(g.nt, t, &o) != cudaSuccess) o = 0;
-      occ = std::min(occ, o);
+  int occ = 1 << 30;
+  for (const Group& g : sim->groups) {
+    int o = 0;
+    if (step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, &o) != cudaSuccess) o = 0;
+    occ = std::min(occ, o);
+  }
+  if (occ == (1 << 30)) occ = 0;
+  for (int b = 0; b <= occ; ++b) {
+    sim->blocks_per_sm = b;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      mg_rollout(sim, d_act, steps, nullptr, nullptr, 0, stream);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float x = 0.0f;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (rep > 0) ms += x;
     }
-    if (occ <= 0 || occ == (1 << 30)) continue;
-    sim->threads = t;
-    build_segs(sim);
-    cudaMemcpyAsync(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice, st);
-    for (int b = 0; b <= occ; ++b) {
-      sim->blocks_per_sm = b;   // 0: one tile per block
-      float ms = 0.0f;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, st);
-        mg_rollout(sim, d_act, steps, nullptr, nullptr, 0, stream);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float x = 0.0f;
-        cudaEventElapsedTime(&x, e0, e1);
-        if (rep > 0) ms += x;
-      }
-      if (ms < best) { best = ms; best_t = t; best_b = b; }
-    }
+    if (ms < best) { best = ms; best_b = b; }
   }
   (void)old_t; (void)old_b;
   sim->threads = best_t;

@@ -36,7 +36,7 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, int block, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 }  // namespace mg
 
@@ -297,7 +297,7 @@ static bool tick_once(mg_server* s) {
   cudaEventRecord(s->ev0, st);
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
-    launch_step(a, g.nt, g.tiles, kThreads, st);
+    launch_step(a, g.nt, g.tiles, st);
   }
   cudaEventRecord(s->ev1, st);
   cudaError_t e = cudaEventSynchronize(s->ev1);
