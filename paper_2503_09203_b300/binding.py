@@ -20,7 +20,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmarinegym.so")
+LIB_PATH = os.environ.get("MG_LIB_PATH") or os.path.join(_HERE, "libmarinegym.so")
 
 MG_OK = 0
 MG_ERR_INVALID_ARG = -1

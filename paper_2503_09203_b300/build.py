@@ -14,12 +14,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-LIB = os.path.join(HERE, "libmarinegym.so")
-BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.environ.get("MG_LIB_PATH") or os.path.join(HERE, "libmarinegym.so")
+BUILD_DIR = os.path.join(HERE, "_build", os.path.basename(LIB))
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-           "--expt-relaxed-constexpr"]
+           "--expt-relaxed-constexpr"] + os.environ.get("MG_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:

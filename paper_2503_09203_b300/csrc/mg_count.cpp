@@ -1,7 +1,7 @@
 // FLOP count of the step arithmetic: the kernels' own templated substep and
 // observation run on the host with a counting scalar. Convention: add, sub,
-// mul = 1; a fused multiply-add is a mul and an add (2); divide and square
-// root = 1 each; compare, abs and negate = 0.
+// mul = 1; a fused multiply-add is a mul and an add (2); divide, square root
+// and reciprocal square root = 1 each; compare, abs and negate = 0.
 #include <cstdint>
 
 #include "../../include/marinegym.h"
@@ -29,6 +29,7 @@ inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
 inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
 inline Cnt mabs(Cnt a) { return Cnt(a.v < 0 ? -a.v : a.v); }
 inline Cnt msqrt(Cnt a) { ++g_ops; return Cnt(__builtin_sqrt(a.v)); }
+inline Cnt minvsqrt(Cnt a) { ++g_ops; return Cnt(1.0 / __builtin_sqrt(a.v)); }
 
 }  // namespace mgcount
 
@@ -36,6 +37,7 @@ namespace mg {
 using mgcount::Cnt;
 using mgcount::mabs;
 using mgcount::msqrt;
+using mgcount::minvsqrt;
 }  // namespace mg
 
 template <int NT>

@@ -22,12 +22,34 @@
 
 #define MG_HD __host__ __device__ __forceinline__
 
+// Build switches of the hot path (0/1).
+#ifndef MG_FAST_RSQRT
+#define MG_FAST_RSQRT 1
+#endif
+#ifndef MG_DZ_BRANCH
+#define MG_DZ_BRANCH 0
+#endif
+#ifndef MG_USE_PDL
+#define MG_USE_PDL 1
+#endif
+
 namespace mg {
 
 MG_HD float mabs(float x) { return fabsf(x); }
 MG_HD double mabs(double x) { return fabs(x); }
 MG_HD float msqrt(float x) { return sqrtf(x); }
 MG_HD double msqrt(double x) { return sqrt(x); }
+// Reciprocal norm used to renormalise the quaternion. FP32: the hardware
+// reciprocal square root (about 2 ulp), exactly 1 for an exactly unit input so
+// that a vehicle at rest stays bit-identical; FP64: correctly rounded.
+MG_HD float minvsqrt(float x) {
+#if defined(__CUDA_ARCH__) && MG_FAST_RSQRT
+  return x == 1.0f ? 1.0f : rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+MG_HD double minvsqrt(double x) { return 1.0 / sqrt(x); }
 
 // Actuator table of one (class, substep length).
 template <typename S>
@@ -91,6 +113,9 @@ MG_HD void act_rotor(const ActT& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) { kf[i] = S(A.kf[i]); dz[i] = S(A.dz[i]); al[i] = S(A.alpha[i]); }
 }
+// Whether any thruster of the table has a dead zone (generic: always test).
+template <typename ActT>
+MG_HD bool act_has_deadzone(const ActT&) { return true; }
 
 // Intermediates of one substep kept for the vector-Jacobian product.
 template <typename S, int NT>
@@ -111,11 +136,19 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   {
     S kf[NT], dz[NT], al[NT];
     act_rotor<S, NT>(A, kf, dz, al);
+    if (!MG_DZ_BRANCH || act_has_deadzone(A)) {
 #pragma unroll
-    for (int i = 0; i < NT; ++i) {
-      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
-      const S an = mabs(x.n[i]);
-      f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
+      for (int i = 0; i < NT; ++i) {
+        x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+        const S an = mabs(x.n[i]);
+        f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+        f[i] = kf[i] * x.n[i] * mabs(x.n[i]);
+      }
     }
   }
   S tau[6];
@@ -185,7 +218,7 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   qn[1] = qx + hh * (qw * P_ + qy * R_ - qz * Q_);
   qn[2] = qy + hh * (qw * Q_ - qx * R_ + qz * P_);
   qn[3] = qz + hh * (qw * R_ + qx * Q_ - qy * P_);
-  const S inv = S(1.0f) / msqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+  const S inv = minvsqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.q[i] = qn[i] * inv;
   if (TAPE) {

@@ -110,12 +110,13 @@ __device__ __forceinline__ void phys_from_array(const float* v, Phys<float>& P) 
   P.W = v[PAR_W]; P.B = v[PAR_B];
 }
 
-// Segment of a tile: binary search over tile_begin (segments sorted).
+// Segment of a tile: binary search over tile_begin (segments sorted). The
+// table may live in global or in shared memory, so the loads are generic.
 __device__ __forceinline__ int find_seg(const SegDesc* segs, int n_segs, int tile) {
   int lo = 0, hi = n_segs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&segs[mid].tile_begin) <= tile) lo = mid; else hi = mid - 1;
+    if (segs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -157,6 +158,25 @@ __device__ __forceinline__ void load_actions(const float* base, float (&a)[NT]) 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
+#ifndef MG_SMEM_PLAIN
+#define MG_SMEM_PLAIN 0
+#endif
+#ifndef MG_PHYS_REGS
+#define MG_PHYS_REGS 0
+#endif
+#if MG_SMEM_PLAIN
+// Plain (non-volatile) shared loads: the compiler may schedule or hoist them.
+__device__ __forceinline__ float lds1(unsigned a) {
+  float v;
+  asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float4 lds4(unsigned a) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+#else
 __device__ __forceinline__ float lds1(unsigned a) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
@@ -167,11 +187,14 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
 }
+#endif
 
 // Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
 struct ActSmem {
   unsigned base;
+  bool has_dz;   // any dead zone in the class (block-uniform)
 };
+__device__ __forceinline__ bool act_has_deadzone(const ActSmem& A) { return A.has_dz; }
 enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
 
 template <int NT>
@@ -192,7 +215,7 @@ __device__ __forceinline__ void act_row(const ActSmem& A, int k, S (&r)[NT]) {
 template <typename S, int NT>
 __device__ __forceinline__ void act_rotor(const ActSmem& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
-  lds_vec<NT>(A.base + 4 * SA_DZ, dz);
+  if (A.has_dz) lds_vec<NT>(A.base + 4 * SA_DZ, dz);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
 
@@ -226,56 +249,193 @@ struct PhysSmem {
 };
 
 constexpr int STEP_BLK = 128;
+#ifndef MG_STEP_MIN_BLOCKS
+#define MG_STEP_MIN_BLOCKS 4
+#endif
 
-// Cooperative store of the observation tile (nv4 envs x 13 floats, 16-byte
-// aligned on both sides) from shared memory to global memory.
-__device__ __forceinline__ void store_obs_tile(const float* s_obs, float* g_obs, int nv4) {
-  const int n = nv4 * 13 / 4;
-  const float4* src = reinterpret_cast<const float4*>(s_obs);
-  float4* dst = reinterpret_cast<float4*>(g_obs);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+
+// ---------------------------------------------------------------------------
+// Bulk-copy (1-D TMA) and mbarrier helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Global -> shared bulk copy completing on `bar` (addresses 16-byte aligned,
+// size a multiple of 16).
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Shared -> global bulk copy in the current bulk group.
+__device__ __forceinline__ void bulk_store(void* dst, unsigned src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase: gives up after `limit_ns` and reports it.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+// Per-warp stage buffer: the warp's 32 envs of one tile. State planes (NF4
+// float4 planes, then REM float planes, 32 entries each), actions [32][NT],
+// target [32] float4. Each warp of a block owns two stage buffers and one
+// observation buffer [32][13] and runs its own copy pipeline.
+constexpr int WENV = 32;
+constexpr int N_WARPS = STEP_BLK / WENV;
+template <int NT>
+struct Stage {
+  static constexpr int SS = 13 + NT, NF4 = SS / 4, REM = SS % 4;
+  static constexpr int ACT_OFF = WENV * SS;                     // floats
+  static constexpr int TGT_OFF = ACT_OFF + WENV * NT;           // floats (16-byte aligned)
+  static constexpr int FLOATS = TGT_OFF + 4 * WENV;
+  static constexpr int OBS = WENV * 13;
+  static constexpr int WARP_FLOATS = 2 * FLOATS + OBS;          // per warp
+  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (FLOATS % 4) == 0 && (OBS % 4) == 0,
+                "16-byte aligned sections");
+};
+constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
+
+// Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
+// (a multiple of 4, > 0) envs start at local env index w0 of the segment.
+template <int NT, bool PER_ENV>
+__device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDesc& sd, int64_t w0, unsigned nvw,
+                                                 float* buf, unsigned bar) {
+  using SG = Stage<NT>;
+  const float* st = a.state + sd.st_off;
+  unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
+  const bool load_act = a.n_steps > 0 && a.act_mode == 0;
+  if (load_act) bytes += nvw * NT * 4;
+  mbar_expect_tx(bar, bytes);
+  const unsigned b = smem_addr(buf);
+#pragma unroll
+  for (int k = 0; k < SG::NF4; ++k) bulk_load(b + 16u * k * WENV, st + ((int64_t)k * sd.n4 + w0) * 4, nvw * 16, bar);
+#pragma unroll
+  for (int r = 0; r < SG::REM; ++r)
+    bulk_load(b + 16u * SG::NF4 * WENV + 4u * r * WENV, st + (int64_t)SG::NF4 * 4 * sd.n4 + (int64_t)r * sd.n4 + w0,
+              nvw * 4, bar);
+  if (load_act) bulk_load(b + 4u * SG::ACT_OFF, a.actions + sd.act_off + w0 * NT, nvw * NT * 4, bar);
+  bulk_load(b + 4u * SG::TGT_OFF, a.planes + (PER_ENV ? TGT_PLANE : 0) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
+}
+
+// Envs of warp `warp` in a tile that starts at local env local0 (0 if none).
+__device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0, int warp) {
+  const int64_t n = (int64_t)sd.n4 - local0 - (int64_t)warp * WENV;
+  return n <= 0 ? 0u : (unsigned)min((int64_t)WENV, n);
 }
 
 template <int NT, bool PER_ENV>
-__device__ __forceinline__ void step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
-                                          const float* s_phys, float* s_obs, float* s_par) {
+__device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
+                                          const float* s_phys, const float* buf, float* obs_w, float* s_par,
+                                          int& n_emit) {
+  using SG = Stage<NT>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t local0 = (int64_t)(tile - sd.tile_begin) * STEP_BLK;
-  const int64_t i = local0 + threadIdx.x;
+  const int64_t w0 = local0 + warp * WENV;
+  const int64_t i = w0 + lane;
   const bool valid = i < sd.n_envs;
   const bool in_storage = i < sd.n4;
-  const int nv4 = (int)min((int64_t)STEP_BLK, (int64_t)sd.n4 - local0);
+  const unsigned nvw = warp_envs(sd, local0, warp);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
-  const ActSmem A{smem_addr(s_act)};
-
-  St<float, NT> x;
-  if (valid) {
-    load_state<NT>(st_base, sd.n4, i, x);
-    if (PER_ENV) {
+  bool has_dz = false;
 #pragma unroll
-      for (int k = 0; k < PAR_PLANES; ++k) {
-        const float4 v = __ldg(&a.planes[k * a.n_slots + slot]);
-        s_par[(4 * k + 0) * STEP_BLK + threadIdx.x] = v.x;
-        s_par[(4 * k + 1) * STEP_BLK + threadIdx.x] = v.y;
-        s_par[(4 * k + 2) * STEP_BLK + threadIdx.x] = v.z;
-        s_par[(4 * k + 3) * STEP_BLK + threadIdx.x] = v.w;
-      }
-    }
+  for (int k = 0; k < NT; ++k) has_dz |= s_act[SA_DZ + k] > 0.0f;
+  const ActSmem A{smem_addr(s_act), has_dz};
+
+  constexpr bool STAGE_PAR = PER_ENV && !MG_PHYS_REGS;
+  float4 pv[STAGE_PAR ? PAR_PLANES : 1];
+  if (STAGE_PAR && valid) {
+#pragma unroll
+    for (int k = 0; k < PAR_PLANES; ++k) pv[k % (STAGE_PAR ? PAR_PLANES : 1)] = __ldg(&a.planes[k * a.n_slots + slot]);
   }
-  // Each thread reads only its own parameter column: no barrier needed.
-  using PV = PhysSmem<PER_ENV ? STEP_BLK : 1>;
-  const PV P(PER_ENV ? smem_addr(s_par) + 4u * threadIdx.x : smem_addr(s_phys));
+  St<float, NT> x;
   float c[NT];
+  float tgt[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int j = 0; j < NT; ++j) c[j] = 0.0f;
+  bool have_act0 = false;
+  if (valid) {
+    float f[13 + NT];
+    const float4* p4 = reinterpret_cast<const float4*>(buf);
+#pragma unroll
+    for (int k = 0; k < SG::NF4; ++k) {
+      const float4 v = p4[k * WENV + lane];
+      f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < SG::REM; ++r) f[(SG::NF4 * 4 + r) % (13 + NT)] = buf[SG::NF4 * 4 * WENV + r * WENV + lane];
+    fields_to_state<NT>(f, x);
+    const float4 tg = reinterpret_cast<const float4*>(buf + SG::TGT_OFF)[lane];
+    tgt[0] = tg.x; tgt[1] = tg.y; tgt[2] = tg.z;
+    if (a.n_steps > 0 && a.act_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) c[j] = clamp1(buf[SG::ACT_OFF + lane * NT + j]);
+      have_act0 = true;
+    }
+  }
+  if (STAGE_PAR && valid) {
+#pragma unroll
+    for (int k = 0; k < PAR_PLANES; ++k) {
+      const float4 v = pv[k % (STAGE_PAR ? PAR_PLANES : 1)];
+      s_par[(4 * k + 0) * STEP_BLK + tid] = v.x;
+      s_par[(4 * k + 1) * STEP_BLK + tid] = v.y;
+      s_par[(4 * k + 2) * STEP_BLK + tid] = v.z;
+      s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
+    }
+  }
+#if MG_PHYS_REGS
+  // Parameters held in registers for the whole tile.
+  Phys<float> P;
+  if (PER_ENV) {
+    if (valid) load_phys(a.planes, a.n_slots, slot, P);
+  } else {
+    phys_from_array(s_phys, P);
+  }
+#else
+  // Each thread reads only its own parameter column: no barrier needed.
+  using PV = PhysSmem<PER_ENV ? STEP_BLK : 1>;
+  const PV P(PER_ENV ? smem_addr(s_par) + 4u * tid : smem_addr(s_phys));
+#endif
   const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
   for (int t = 0; t < n_out_steps; ++t) {
     if (valid && a.n_steps > 0) {
       if (a.act_mode == 0) {
-        float raw[NT];
-        load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
+        if (!(t == 0 && have_act0)) {
+          float raw[NT];
+          load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) c[j] = clamp1(raw[j]);
+          for (int j = 0; j < NT; ++j) c[j] = clamp1(raw[j]);
+        }
       } else {
 #pragma unroll
         for (int g = 0; g < (NT + 3) / 4; ++g) {
@@ -301,17 +461,20 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SegDesc& sd, 
       float o[13], r = 0.0f;
 #pragma unroll
       for (int j = 0; j < 13; ++j) o[j] = 0.0f;
-      if (valid) {
-        const float4 tg = __ldg(&a.planes[(PER_ENV ? TGT_PLANE : 0) * a.n_slots + slot]);
-        const float tgt[3] = {tg.x, tg.y, tg.z};
-        observe<float, NT>(x, c, tgt, o, r);
-      }
-      if (a.obs) {
+      if (valid) observe<float, NT>(x, c, tgt, o, r);
+      if (a.obs && nvw > 0) {
+        // The warp's previous observation store must have read its buffer.
+        if (lane == 0 && n_emit > 0) bulk_wait_read0();
+        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 13; ++j) s_obs[threadIdx.x * 13 + j] = o[j];
-        __syncthreads();
-        store_obs_tile(s_obs, a.obs + (out * a.n_slots + sd.slot_off + local0) * 13, nv4);
-        __syncthreads();
+        for (int j = 0; j < 13; ++j) obs_w[lane * 13 + j] = o[j];
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          bulk_store(a.obs + (out * a.n_slots + sd.slot_off + w0) * 13, smem_addr(obs_w), nvw * 52u);
+          bulk_commit();
+        }
+        ++n_emit;
       }
       if (a.reward && in_storage) a.reward[out * a.n_slots + slot] = valid ? r : 0.0f;
       if (a.ret && valid && a.n_steps > 0) a.ret[slot] += r;
@@ -330,34 +493,113 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SegDesc& sd, 
     for (int j = 0; j < NT; ++j) s += x.n[j];
     if (!isfinite(s)) atomicOr(a.status, 1u);
   }
+  return true;
 }
 
-// Persistent-capable step kernel for envs with NT thrusters: each block walks
-// tiles tile_lo + blockIdx.x, + gridDim.x, ... A tile is 128 envs of one
-// segment. One instantiation per thruster count (and parameter source) keeps
-// each kernel's register allocation to its own arithmetic.
+// Persistent step kernel for envs with NT thrusters. Block b walks the tiles
+// tile_lo + b, + gridDim.x, ...; a tile is 128 envs of one segment, 32 per
+// warp. Every warp runs its own pipeline: while it computes its slice of tile
+// j, its lane 0 has already issued the bulk copies of its slice of the next
+// tile into the warp's other stage buffer, and observation rows leave through
+// a per-warp bulk store. Warps never wait on one another except when the
+// class constants change. Every wait is bounded (2 s); a warp that gives up
+// sets bit 1 of the status word and leaves.
 template <int NT, bool PER_ENV>
-__global__ void __launch_bounds__(STEP_BLK, 6) mg_step_kernel(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(const __grid_constant__ StepArgs a) {
+  using SG = Stage<NT>;
+  extern __shared__ __align__(16) float s_dyn[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* const w_base = s_dyn + warp * SG::WARP_FLOATS;
+  float* const buf0 = w_base;
+  float* const buf1 = w_base + SG::FLOATS;
+  float* const obs_w = w_base + 2 * SG::FLOATS;
+  float* const s_par = s_dyn + N_WARPS * SG::WARP_FLOATS;
   __shared__ __align__(16) float s_act[SA_DIM];
   __shared__ __align__(16) float s_phys[PAR_DIM];
-  __shared__ __align__(16) float s_obs[STEP_BLK * 13];
-  __shared__ __align__(16) float s_par[PER_ENV ? PAR_DIM * STEP_BLK : 4];
-  for (int tt = blockIdx.x; tt < a.n_tiles; tt += gridDim.x) {
-    const int tile = a.tile_lo + tt;
-    const int si = a.seg_lo + find_seg(a.segs + a.seg_lo, a.seg_hi - a.seg_lo, tile);
-    const SegDesc& sd = a.segs[si];
-    __syncthreads();
-    const ClassF& cf = a.classes[sd.cls];
-    for (int k = threadIdx.x; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
-      if (k < 48) s_act[k] = cf.alloc[k / 8][k % 8];
-      else if (k < 56) s_act[k] = cf.kf[k - 48];
-      else if (k < 64) s_act[k] = cf.dz[k - 56];
-      else if (k < 72) s_act[k] = sd.alpha[k - 64];
-      else s_phys[k - 72] = cf.phys[k - 72];
-    }
-    __syncthreads();
-    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, s_obs, s_par);
+  __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
+  __shared__ SegDesc s_seg[SEG_CACHE];
+  // The next launch of a step (another thruster count, disjoint envs) may
+  // start filling SMs as soon as this grid's blocks are resident.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if ((int)blockIdx.x >= a.n_tiles) return;
+  const int n_seg = a.seg_hi - a.seg_lo;
+  const bool cached = n_seg <= SEG_CACHE;
+  if (cached) {
+    const int32_t* src = reinterpret_cast<const int32_t*>(a.segs + a.seg_lo);
+    int32_t* dst = reinterpret_cast<int32_t*>(s_seg);
+    for (int k = tid; k < n_seg * (int)(sizeof(SegDesc) / 4); k += STEP_BLK) dst[k] = src[k];
   }
+  const SegDesc* segs = cached ? s_seg : a.segs + a.seg_lo;
+  const unsigned full0 = smem_addr(&s_bar[warp][0]), full1 = smem_addr(&s_bar[warp][1]);
+  if (lane == 0) {
+    mbar_init(full0, 1);
+    mbar_init(full1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // Prologue: this warp's slice of the first tile.
+  unsigned nvw_cur = 0;
+  {
+    const int tile0 = a.tile_lo + blockIdx.x;
+    const SegDesc& s0 = segs[find_seg(segs, n_seg, tile0)];
+    const int64_t local0 = (int64_t)(tile0 - s0.tile_begin) * STEP_BLK;
+    nvw_cur = warp_envs(s0, local0, warp);
+    if (lane == 0 && nvw_cur > 0)
+      issue_warp_loads<NT, PER_ENV>(a, s0, local0 + warp * WENV, nvw_cur, buf0, full0);
+  }
+  int prev_seg = -1, n_emit = 0;
+  unsigned use[2] = {0u, 0u};   // completed uses of each stage barrier
+  bool failed = false;
+  for (int j = 0, tt = blockIdx.x; tt < a.n_tiles; ++j, tt += gridDim.x) {
+    const int tile = a.tile_lo + tt;
+    const int b = j & 1;
+    const int si = find_seg(segs, n_seg, tile);
+    // Refill the other buffer (read during tile j - 1) with the next slice.
+    const int tt_next = tt + gridDim.x;
+    unsigned nvw_next = 0;
+    if (tt_next < a.n_tiles) {
+      const int tile_n = a.tile_lo + tt_next;
+      const SegDesc& sn = segs[find_seg(segs, n_seg, tile_n)];
+      const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
+      nvw_next = warp_envs(sn, ln, warp);
+      if (lane == 0 && nvw_next > 0) {
+        fence_async_smem();
+        issue_warp_loads<NT, PER_ENV>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
+      }
+    }
+    const SegDesc& sd = segs[si];
+    if (si != prev_seg) {
+      // Class constants change: rewrite them between two block barriers.
+      __syncthreads();
+      const ClassF& cf = a.classes[sd.cls];
+      for (int k = tid; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
+        if (k < 48) s_act[k] = cf.alloc[k / 8][k % 8];
+        else if (k < 56) s_act[k] = cf.kf[k - 48];
+        else if (k < 64) s_act[k] = cf.dz[k - 56];
+        else if (k < 72) s_act[k] = sd.alpha[k - 64];
+        else s_phys[k - 72] = cf.phys[k - 72];
+      }
+      __syncthreads();
+      prev_seg = si;
+    }
+    if (nvw_cur > 0) {
+      if (!mbar_wait_bounded(b ? full1 : full0, use[b] & 1u, kWaitLimitNs)) {
+        failed = true;
+        break;
+      }
+      use[b]++;
+    }
+    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, obs_w, s_par, n_emit);
+    // The warp has read its stage buffer b; lane 0 may refill it next round.
+    __syncwarp();
+    nvw_cur = nvw_next;
+  }
+  if (failed && lane == 0) atomicOr(a.status, 2u);
+  // Observation stores must finish reading shared memory before the warp exits.
+  if (lane == 0) bulk_wait0();
+  // A grid launched as a programmatic dependent completes only after the grid
+  // it depends on, so that completion stays ordered along the stream.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -697,18 +939,49 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
     default: return cudaErrorInvalidValue; \
   }
 
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st) {
+// Dynamic shared memory of mg_step_kernel<NT, PER_ENV>.
+template <int NT, bool PER_ENV>
+static size_t step_smem() {
+  return sizeof(float) * (N_WARPS * Stage<NT>::WARP_FLOATS + (PER_ENV ? PAR_DIM * STEP_BLK : 0));
+}
+
+// `dependent`: launch as a programmatic dependent of the previous kernel in
+// the stream (the previous launch of the same step, on disjoint envs).
+template <int NT, bool PER_ENV>
+static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
+  static bool attr_set = false;   // per instantiation, per process (one device)
+  const size_t smem = step_smem<NT, PER_ENV>();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(STEP_BLK);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PER_ENV>, a);
+}
+
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (a.per_env) {
-#define MG_L(N) mg_step_kernel<N, true><<<grid, STEP_BLK, 0, st>>>(a)
+#define MG_L(N) return launch_step_t<N, true>(a, grid, dependent, st)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   } else {
-#define MG_L(N) mg_step_kernel<N, false><<<grid, STEP_BLK, 0, st>>>(a)
+#define MG_L(N) return launch_step_t<N, false>(a, grid, dependent, st)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st) {
@@ -739,13 +1012,22 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int NT, bool PER_ENV>
+static cudaError_t occupancy_t(int* blocks_per_sm) {
+  const size_t smem = step_smem<NT, PER_ENV>();
+  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PER_ENV>, STEP_BLK, smem);
+}
+
 cudaError_t step_kernel_occupancy(int nt, bool per_env, int* blocks_per_sm) {
   if (per_env) {
-#define MG_L(N) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<N, true>, STEP_BLK, 0)
+#define MG_L(N) return occupancy_t<N, true>(blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   } else {
-#define MG_L(N) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<N, false>, STEP_BLK, 0)
+#define MG_L(N) return occupancy_t<N, false>(blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   }

@@ -16,7 +16,7 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
@@ -51,7 +51,7 @@ struct mg_sim {
   int32_t n_classes = 0, n_envs = 0, n_slots = 0;
   int64_t act_floats = 0, state_floats = 0;
   int32_t threads = 128;
-  int32_t blocks_per_sm = 0;   // 0: one tile per block (grid = tiles)
+  int32_t blocks_per_sm = 0;   // persistent blocks per SM (0: occupancy limit)
   int32_t num_sms = 148;
   int32_t n_tiles = 0, n_segs = 0;
   double h = 0.0;
@@ -436,19 +436,33 @@ static StepArgs step_args(mg_sim* sim) {
   return a;
 }
 
+// Persistent grid: blocks_per_sm resident blocks per SM (0: the kernel's
+// occupancy limit), never more blocks than tiles.
 static int grid_of(mg_sim* sim, const Group& g) {
-  if (sim->blocks_per_sm <= 0) return g.n_tiles;
-  return std::min(g.n_tiles, sim->blocks_per_sm * sim->num_sms);
+  int b = sim->blocks_per_sm;
+  if (b <= 0) {
+    b = 1;
+    step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, &b);
+    if (b < 1) b = 1;
+  }
+  return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
 }
 
+static bool misaligned(const void* p) { return p && ((uintptr_t)p & 15u) != 0; }
+
 // Launch the step kernel once per thruster-count group.
+// The first group is an ordinary launch (it waits for everything before it in
+// the stream); later groups touch disjoint envs and are programmatic
+// dependents, so they fill the SMs that the previous group's tail leaves idle.
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
+  bool first = true;
   for (const Group& g : sim->groups) {
     a.seg_lo = g.seg_lo;
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    CK(launch_step(a, g.nt, grid_of(sim, g), st));
+    CK(launch_step(a, g.nt, grid_of(sim, g), !first, st));
+    first = false;
   }
   return MG_OK;
 }
@@ -457,6 +471,8 @@ int mg_step(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_d
             mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!actions_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "step: need actions and n_steps >= 1");
+  if (misaligned(actions_dev) || misaligned(obs_dev))
+    return fail(sim, MG_ERR_INVALID_ARG, "step: actions and obs buffers must be 16-byte aligned");
   StepArgs a = step_args(sim);
   a.actions = actions_dev;
   a.n_steps = n_steps;
@@ -472,6 +488,8 @@ int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* ob
                int32_t record, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!actions_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout: need actions and n_steps >= 1");
+  if (misaligned(actions_dev) || misaligned(obs_dev))
+    return fail(sim, MG_ERR_INVALID_ARG, "rollout: actions and obs buffers must be 16-byte aligned");
   if (record && (!sim->d_ckpt || n_steps > sim->cfg.record_steps))
     return fail(sim, MG_ERR_INVALID_ARG, "rollout: record needs record_steps >= n_steps (have %d)", sim->cfg.record_steps);
   StepArgs a = step_args(sim);
@@ -488,6 +506,7 @@ int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* ob
 
 int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream) {
   if (!sim || !obs_dev) return sim ? fail(sim, MG_ERR_INVALID_ARG, "observe: null obs") : MG_ERR_INVALID_ARG;
+  if (misaligned(obs_dev)) return fail(sim, MG_ERR_INVALID_ARG, "observe: obs buffer must be 16-byte aligned");
   StepArgs a = step_args(sim);
   a.n_steps = 0;
   a.obs = obs_dev;
@@ -717,10 +736,9 @@ int mg_status(mg_sim* sim, mg_stream_t stream) {
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   uint32_t st = 0;
   CK(cudaMemcpy(&st, sim->d_status, sizeof(st), cudaMemcpyDeviceToHost));
-  if (st & 1u) {
-    CK(cudaMemset(sim->d_status, 0, sizeof(uint32_t)));
-    return fail(sim, MG_ERR_NONFINITE, "a step produced a non-finite state");
-  }
+  if (st) CK(cudaMemset(sim->d_status, 0, sizeof(uint32_t)));
+  if (st & 2u) return fail(sim, MG_ERR_TIMEOUT, "a bounded wait in the step kernel gave up; results are invalid");
+  if (st & 1u) return fail(sim, MG_ERR_NONFINITE, "a step produced a non-finite state");
   return MG_OK;
 }
 
@@ -740,8 +758,8 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // Tiles are 128 envs (the kernels' fixed block); the tuned knob is the grid:
-  // one block per tile (0) or a persistent grid of b blocks per SM.
+  // Tiles are 128 envs (the kernels' fixed block); the tuned knob is the
+  // persistent grid: b resident blocks per SM.
   int best_t = sim->threads, best_b = sim->blocks_per_sm;
   float best = 1e30f;
   const int old_t = sim->threads, old_b = sim->blocks_per_sm;
@@ -752,7 +770,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;
-  for (int b = 0; b <= occ; ++b) {
+  for (int b = 1; b <= occ; ++b) {
     sim->blocks_per_sm = b;
     float ms = 0.0f;
     for (int rep = 0; rep < 3; ++rep) {

@@ -36,7 +36,7 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 }  // namespace mg
 
@@ -127,6 +127,7 @@ struct mg_server {
   mg_server_config cfg{};
   std::vector<mg_class_desc> classes;
   int device = 0;
+  int num_sms = 148;
   // device
   void* arena = nullptr;
   ClassF* d_cls = nullptr;
@@ -295,9 +296,11 @@ static bool tick_once(mg_server* s) {
   a.status = s->d_status;
   a.ckpt_every = 1;
   cudaEventRecord(s->ev0, st);
+  bool first = true;
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
-    launch_step(a, g.nt, g.tiles, st);
+    launch_step(a, g.nt, std::min(g.tiles, 4 * s->num_sms), !first, st);
+    first = false;
   }
   cudaEventRecord(s->ev1, st);
   cudaError_t e = cudaEventSynchronize(s->ev1);
@@ -405,6 +408,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   s->cfg = *cfg;
   s->classes.assign(classes, classes + n_classes);
   cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   size_t budget = cfg->budget_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
