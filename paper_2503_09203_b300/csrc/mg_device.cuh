@@ -26,9 +26,6 @@
 #ifndef MG_FAST_RSQRT
 #define MG_FAST_RSQRT 1
 #endif
-#ifndef MG_DZ_BRANCH
-#define MG_DZ_BRANCH 0
-#endif
 #ifndef MG_USE_PDL
 #define MG_USE_PDL 1
 #endif
@@ -113,9 +110,7 @@ MG_HD void act_rotor(const ActT& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) { kf[i] = S(A.kf[i]); dz[i] = S(A.dz[i]); al[i] = S(A.alpha[i]); }
 }
-// Whether any thruster of the table has a dead zone (generic: always test).
-template <typename ActT>
-MG_HD bool act_has_deadzone(const ActT&) { return true; }
+
 
 // Intermediates of one substep kept for the vector-Jacobian product.
 template <typename S, int NT>
@@ -136,19 +131,11 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   {
     S kf[NT], dz[NT], al[NT];
     act_rotor<S, NT>(A, kf, dz, al);
-    if (!MG_DZ_BRANCH || act_has_deadzone(A)) {
 #pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
-        const S an = mabs(x.n[i]);
-        f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
-        f[i] = kf[i] * x.n[i] * mabs(x.n[i]);
-      }
+    for (int i = 0; i < NT; ++i) {
+      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+      const S an = mabs(x.n[i]);
+      f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
     }
   }
   S tau[6];

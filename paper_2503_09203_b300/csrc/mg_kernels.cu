@@ -192,9 +192,7 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
 // Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
 struct ActSmem {
   unsigned base;
-  bool has_dz;   // any dead zone in the class (block-uniform)
 };
-__device__ __forceinline__ bool act_has_deadzone(const ActSmem& A) { return A.has_dz; }
 enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
 
 template <int NT>
@@ -215,7 +213,7 @@ __device__ __forceinline__ void act_row(const ActSmem& A, int k, S (&r)[NT]) {
 template <typename S, int NT>
 __device__ __forceinline__ void act_rotor(const ActSmem& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
-  if (A.has_dz) lds_vec<NT>(A.base + 4 * SA_DZ, dz);
+  lds_vec<NT>(A.base + 4 * SA_DZ, dz);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
 
@@ -367,10 +365,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   const unsigned nvw = warp_envs(sd, local0, warp);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
-  bool has_dz = false;
-#pragma unroll
-  for (int k = 0; k < NT; ++k) has_dz |= s_act[SA_DZ + k] > 0.0f;
-  const ActSmem A{smem_addr(s_act), has_dz};
+  const ActSmem A{smem_addr(s_act)};
 
   constexpr bool STAGE_PAR = PER_ENV && !MG_PHYS_REGS;
   float4 pv[STAGE_PAR ? PAR_PLANES : 1];
