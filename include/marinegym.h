@@ -199,6 +199,27 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
                      const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
                      float* g_state0, mg_stream_t stream);
 
+/* Allocation-free variant of mg_step_backward (the paper has no counterpart;
+ * this is an interface for callers that cannot allocate device memory while
+ * they run the backward pass: a host framework whose own pool owns the
+ * device, a process whose memory budget is already committed, or a loop that
+ * must not take cudaMalloc's implicit device synchronisation).
+ * Same arguments, outputs and errors as mg_step_backward, but the segment-
+ * recompute scratch is a fixed 32 MiB array compiled into the library (held
+ * by every GPU that loads it until the process exits) instead of the
+ * simulator's own scratch buffer; the call allocates nothing.
+ * Limit: (ckpt_every * K + 1) * 21 * n_slots <= 8,388,608 floats, else
+ * MG_ERR_INVALID_ARG with the sizes in mg_last_error(). Every entry of the
+ * scratch that the kernel reads it writes earlier in the same call, so nothing
+ * needs clearing between calls; the array keeps the last call's contents.
+ * All calls share the one array: calls that overlap on the GPU (for example on
+ * two streams) race. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture. */
+int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
+                             const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
+                             float* g_state0, mg_stream_t stream);
+
 /* Overwrite the added-mass (A [n_slots][6]), linear damping (dl) and quadratic
  * damping (dq) of every env from device arrays (each may be NULL = keep) and
  * recompute M^-1 in FP64 on the GPU. Needs per_env_params. */

@@ -118,6 +118,7 @@ _SIGS = {
     "mg_observe": [_VP, _VP, _VP],
     "mg_step_host": [_VP, _VP, _I32, _VP, _VP, _VP],
     "mg_step_backward": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "mg_step_backward_noalloc": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "mg_set_hydro": [_VP, _VP, _VP, _VP, _VP],
     "mg_rollout_fp64": [_VP, _VP, _I32, _VP, _VP, _VP, _D, _VP, _VP, _VP],
     "mg_get_state": [_VP, _VP, C.c_size_t],
@@ -276,6 +277,15 @@ def mg_step_backward(sim, actions, g_obs=None, g_rew=None, g_state_T=None, g_act
     return _check(lib().mg_step_backward(sim, _ptr(actions), _ptr(g_obs), _ptr(g_rew), _ptr(g_state_T),
                                          _ptr(g_actions), _ptr(g_added_mass), _ptr(g_damping), _ptr(g_state0),
                                          _stream(stream)), sim)
+
+
+def mg_step_backward_noalloc(sim, actions, g_obs=None, g_rew=None, g_state_T=None, g_actions=None,
+                             g_added_mass=None, g_damping=None, g_state0=None, stream=None):
+    """mg_step_backward without any device allocation: for callers that cannot
+    allocate device memory during the backward pass (see the header)."""
+    return _check(lib().mg_step_backward_noalloc(sim, _ptr(actions), _ptr(g_obs), _ptr(g_rew), _ptr(g_state_T),
+                                                 _ptr(g_actions), _ptr(g_added_mass), _ptr(g_damping),
+                                                 _ptr(g_state0), _stream(stream)), sim)
 
 
 def mg_set_hydro(sim, A=None, dl=None, dq=None, stream=None):

@@ -839,3 +839,55 @@ int mg_graph_destroy(mg_graph* g) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint: as mg_step_backward, with the segment-recompute
+// scratch taken from the library's fixed device array (mg_noalloc.cu).
+// ---------------------------------------------------------------------------
+namespace mg {
+cudaError_t noalloc_scratch(float** ptr, size_t* capacity_floats);
+}  // namespace mg
+
+extern "C" int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, const float* g_obs,
+                                        const float* g_rew, const float* g_state_T, float* g_actions,
+                                        float* g_added_mass, float* g_damping, float* g_state0,
+                                        mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (sim->rec_T <= 0) return fail(sim, MG_ERR_STATE, "backward: no recorded rollout (call mg_rollout with record=1)");
+  if (!actions_dev) return fail(sim, MG_ERR_INVALID_ARG, "backward: actions required");
+  float* scratch = nullptr;
+  size_t cap = 0;
+  CK(noalloc_scratch(&scratch, &cap));
+  const size_t need = ((size_t)sim->ckpt_every * (size_t)sim->cfg.K + 1) * 21 * (size_t)sim->n_slots;
+  if (need > cap)
+    return fail(sim, MG_ERR_INVALID_ARG,
+                "backward_noalloc: scratch of %zu floats needed ((ckpt_every*K+1)*21*n_slots), the fixed array "
+                "holds %zu; lower ckpt_every or the env count",
+                need, cap);
+  AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = sim->d_segs;
+  a.classes = sim->d_cls;
+  a.planes = sim->d_planes;
+  a.n_slots = sim->n_slots;
+  a.actions = actions_dev;
+  a.act_stride = sim->act_floats;
+  a.T = sim->rec_T;
+  a.ckpt_every = sim->ckpt_every;
+  a.ckpt = sim->d_ckpt;
+  a.scratch = scratch;
+  a.g_obs = g_obs;
+  a.g_rew = g_rew;
+  a.g_state_T = g_state_T;
+  a.g_actions = g_actions;
+  a.g_A = g_added_mass;
+  a.g_D = g_damping;
+  a.g_state0 = g_state0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
+  for (const Group& g : sim->groups) {
+    a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
+    CK(launch_adjoint(a, g.nt, sim->threads, st));
+  }
+  return MG_OK;
+}
