@@ -36,6 +36,53 @@ UNIT = "env-steps/s"
 SEED = 0x4D47
 
 
+def kernel_sha() -> str:
+    """Hash of the kernel sources (the profile summaries record the one they measured)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2503_09203_b300", "csrc", "*")) +
+                    glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name="step_kernel_full_hover_1M_K4.md"):
+    """DRAM bytes per step from the committed ncu summary, if it measured these sources."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    sha = traffic = None
+    for line in open(p):
+        if line.startswith("source_sha:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_bytes_per_step:"):
+            traffic = float(line.split(":", 1)[1])
+    return traffic if sha == kernel_sha() else None
+
+
+def dist_max(x: float, device="cuda") -> float:
+    """Max of a per-rank float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(envs_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Env-steps per second of all ranks together (weak scaling: every rank runs
+    its own envs_per_rank envs)."""
+    return envs_per_rank * world * steps / seconds
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank simulates an independent batch of envs."""
+    return SEED + rank
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -303,7 +350,7 @@ def parity_sample(sim_classes, counts, K, n=512):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=1 << 20)
@@ -343,7 +390,7 @@ def main():
     pk = peaks()
     classes, counts, cfg = workload(E, K)
     sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
-    sim.reset(seed=SEED + rank)
+    sim.reset(seed=rank_seed(rank))
     stream = torch.cuda.current_stream()
     acts = action_pool(sim, 8, 100 + rank)
     bpe, fpe = algorithmic(classes, counts, K)
@@ -370,16 +417,13 @@ def main():
     e1.synchronize()
     torch.cuda.synchronize()
     tw1 = time.time()
-    t = e0.elapsed_time(e1) * 1e-3
+    t = dist_max(e0.elapsed_time(e1) * 1e-3)
     if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        t = float(tt.item())
     if rank == 0:
         clocks.stop()
     B.mg_status(sim.handle, stream)
-    value = E * world * args.steps / t
+    value = whole_job_rate(E, world, args.steps, t)
 
     # End to end through the host-buffer entry point (pinned buffers).
     a_host = acts[0].cpu().pin_memory()
@@ -392,12 +436,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         B.mg_step_host(sim.handle, a_host, 1, o_host, r_host, stream)
-    te = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([te], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": E * world * args.e2e_steps / te, "unit": UNIT,
+    te = dist_max(time.perf_counter() - t0)
+    e2e = {"value": whole_job_rate(E, world, args.e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": int(sim.action_floats * 4), "d2h_bytes_per_step": int(sim.n_slots * 14 * 4),
            "steps": args.e2e_steps, "api": "mg_step_host"}
 
@@ -420,6 +460,11 @@ def main():
         roof = {"bound": "alu", "achieved": achieved_flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved_flops / alu_peak, "traffic": None,
                 "peak_src": "2 x 128 FP32 lanes x 148 SMs x max SM clock"}
+    traffic = profiled_traffic() if (E == 1 << 20 and K == 4) else None
+    roof["traffic"] = traffic
+    roof["traffic_note"] = ("DRAM read+write bytes per step (3 launches) from profiles/step_kernel_full_hover_1M_K4.md "
+                            "(ncu serialised replay: reads = algorithmic, writes partly deferred in L2)"
+                            if traffic else "null: no ncu capture of these kernel sources at this workload")
     roof.update({"kernel": "mg_step_kernel<4,6,8> (one launch per thruster count, per step)",
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
                  "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
