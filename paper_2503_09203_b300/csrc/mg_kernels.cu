@@ -158,8 +158,11 @@ __device__ __forceinline__ void load_actions(const float* base, float (&a)[NT]) 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
+#ifndef MG_SMEM_LAUNDER
+#define MG_SMEM_LAUNDER 1
+#endif
 #ifndef MG_SMEM_PLAIN
-#define MG_SMEM_PLAIN 0
+#define MG_SMEM_PLAIN MG_SMEM_LAUNDER
 #endif
 #ifndef MG_PHYS_REGS
 #define MG_PHYS_REGS 0
@@ -448,7 +451,19 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 #pragma unroll
         for (int j = 0; j < 21; ++j) ck[j * a.n_slots] = (j < 13 + NT) ? f[j % (13 + NT)] : 0.0f;
       }
+#if MG_SMEM_LAUNDER && !MG_PHYS_REGS
+      // Shared-memory bases made opaque once per substep: loads may be
+      // scheduled freely inside a substep but not hoisted out of the loop.
+      for (int k = 0; k < sd.K; ++k) {
+        unsigned pb = P.minv.base, ab = A.base;
+        asm volatile("" : "+r"(pb), "+r"(ab));
+        const PV Pk(pb);
+        const ActSmem Ak{ab};
+        substep<float, NT, false>(x, c, Pk, Ak, sd.h, nullptr);
+      }
+#else
       for (int k = 0; k < sd.K; ++k) substep<float, NT, false>(x, c, P, A, sd.h, nullptr);
+#endif
     }
     const bool emit = a.obs_every || t == n_out_steps - 1;
     if (emit) {
