@@ -250,6 +250,25 @@ def sweep(pk, stream, sizes=(65536, 262144, 1048576), Ks=(1, 4, 8), steps=200):
     return out
 
 
+def tracking_bench(pk, stream, E=1 << 20, K=4, steps=200):
+    """Trajectory-tracking variant of the headline step (helix references)."""
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(E, 5)
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=dict(vehicles.TRACK_HELIX),
+                task=B.TASK_TRACK)
+    sim.reset(seed=SEED)
+    acts = action_pool(sim, 4, 9)
+    t = time_steps(sim, acts, steps, 10, stream)
+    bpe, fpe = algorithmic(classes, counts, K)
+    bpe += 48 + 4   # trajectory planes read at the observation, counter written back
+    v = E * steps / t
+    sim.close()
+    return {"envs": E, "K": K, "reference": "helix", "env_steps_per_s": v, "us_per_step": t / steps * 1e6,
+            "hbm_frac": v * bpe / (pk["hbm_gbs"] * 1e9)}
+
+
 def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
     import torch
     from paper_2503_09203_b300 import binding as B
@@ -482,6 +501,7 @@ def main():
         sim.close()
         line["parity"] = parity_sample(classes, counts, K)
         line["sweep"] = sweep(pk, stream)
+        line["tracking"] = tracking_bench(pk, stream)
         line["adjoint"] = adjoint_bench(stream)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)
         line["serving"] = serving_bench(plain_substeps)

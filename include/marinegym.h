@@ -107,6 +107,8 @@ typedef struct {
   double target_half;       /* hover target p* ~ U[-L, L]^3 */
   double pos_radius;        /* |p - p*| uniform in a ball of this radius */
   double max_angle;         /* attitude error angle ~ U[0, max_angle], rad */
+  int32_t track_kind;       /* tracking runs: 0 helix, 1 Lissajous reference */
+  int32_t pad0;
 } mg_reset_cfg;
 
 typedef struct {
@@ -122,6 +124,9 @@ typedef struct {
   int32_t ckpt_every;           /* checkpoint interval in steps (0: 20) */
   size_t mem_budget;            /* 0: none; else mg_create fails with
                                    MG_ERR_OOM above this many device bytes */
+  int32_t task;                 /* 0: station keeping (fixed target p*);
+                                   1: trajectory tracking (time-varying p*(t)) */
+  int32_t pad0;
 } mg_config;
 
 /* Placement of class c inside the device buffers. */
@@ -174,6 +179,22 @@ int mg_step(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_d
  * mg_step_backward (needs n_steps <= record_steps and per_env_params). */
 int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
                int32_t record, mg_stream_t stream);
+
+/* Trajectory tracking (task = 1; Sec. IV-B tracking task). Every env follows
+ * p*(t) = c + a o sin(w t + phi) + v t with t = k dt and k the env's step
+ * counter (reset to 0 by mg_reset, advanced by every step). The observation
+ * and reward of mg_step / mg_rollout / mg_observe use p*(t) in place of the
+ * fixed target, evaluated at the step's end time. Reset draws (stream 2, draws
+ * 9..): helix (track_kind 0): radius R ~ U[1, 3] m, rate W ~ U[0.2, 0.6]
+ * rad/s, phase psi ~ U[0, 2 pi), climb v_z ~ U[-0.2, 0.2] m/s, so
+ * p*(t) = c + (R cos(W t + psi), R sin(W t + psi), v_z t);
+ * Lissajous (track_kind 1): a_i ~ U[1, 3] m, w_i ~ U[0.2, 0.6] rad/s,
+ * phi_i ~ U[0, 2 pi), v = 0. The initial position is drawn around p*(0).
+ * mg_get_task / mg_set_task read and write the reference as [n_envs][16]
+ * doubles: c[3], a[3], w[3], phi[3], v[3], k (hover runs: c and k only,
+ * the rest 0). Both synchronise the device. */
+int mg_get_task(const mg_sim* sim, double* host, size_t bytes);
+int mg_set_task(mg_sim* sim, const double* host, size_t bytes);
 
 /* Observation of the current state (no step): obs_dev [n_slots][13]. */
 int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream);

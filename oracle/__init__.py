@@ -55,7 +55,8 @@ class or_env(C.Structure):
                 ("Ig", C.c_double * 3), ("rg", C.c_double * 3), ("rb", C.c_double * 3),
                 ("W", C.c_double), ("B", C.c_double), ("Ma", C.c_double * 6),
                 ("dl", C.c_double * 6), ("dq", C.c_double * 6), ("Vc", C.c_double * 3),
-                ("target", C.c_double * 3)]
+                ("target", C.c_double * 3), ("traj_a", C.c_double * 3), ("traj_w", C.c_double * 3),
+                ("traj_phi", C.c_double * 3), ("traj_v", C.c_double * 3), ("k0", C.c_double)]
 
 
 class or_reset_cfg(C.Structure):
@@ -67,7 +68,7 @@ class or_reset_cfg(C.Structure):
                 ("cob_lo", C.c_double), ("cob_hi", C.c_double),
                 ("cur_lo", C.c_double), ("cur_hi", C.c_double),
                 ("target_half", C.c_double), ("pos_radius", C.c_double),
-                ("max_angle", C.c_double)]
+                ("max_angle", C.c_double), ("track", C.c_int32), ("track_kind", C.c_int32)]
 
 
 _lib = None
@@ -148,7 +149,8 @@ def envs_to_arrays(envs) -> dict:
     n = len(envs)
     out = {k: np.zeros((n,) + s) for k, s in
            (("mass", ()), ("Ig", (3,)), ("rg", (3,)), ("rb", (3,)), ("W", ()), ("B", ()),
-            ("Ma", (6,)), ("dl", (6,)), ("dq", (6,)), ("Vc", (3,)), ("target", (3,)))}
+            ("Ma", (6,)), ("dl", (6,)), ("dq", (6,)), ("Vc", (3,)), ("target", (3,)),
+            ("traj_a", (3,)), ("traj_w", (3,)), ("traj_phi", (3,)), ("traj_v", (3,)), ("k0", ()))}
     out["cls"] = np.zeros(n, dtype=np.int32)
     for i in range(n):
         e = envs[i]
@@ -170,8 +172,12 @@ def make_envs(arrays: dict):
         e.cls = int(arrays["cls"][i])
         for k in ("mass", "W", "B"):
             setattr(e, k, float(arrays[k][i]))
+        if "k0" in arrays:
+            e.k0 = float(arrays["k0"][i])
         for k, m in (("Ig", 3), ("rg", 3), ("rb", 3), ("Ma", 6), ("dl", 6), ("dq", 6), ("Vc", 3),
-                     ("target", 3)):
+                     ("target", 3), ("traj_a", 3), ("traj_w", 3), ("traj_phi", 3), ("traj_v", 3)):
+            if k not in arrays:
+                continue
             dst = getattr(e, k)
             for j in range(m):
                 dst[j] = float(arrays[k][i][j])

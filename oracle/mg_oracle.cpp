@@ -105,7 +105,9 @@ typedef struct {
   double mass, Ig[3], rg[3], rb[3], W, B;
   double Ma[6], dl[6], dq[6];
   double Vc[3];       // ocean current, NED, m/s
-  double target[3];   // hover target p*, NED, m
+  double target[3];   // hover target p* (tracking: the reference centre c), NED, m
+  double traj_a[3], traj_w[3], traj_phi[3], traj_v[3];   // tracking reference (zeros: hover)
+  double k0;          // step counter at the start of the rollout
 } or_env;
 
 // Reset configuration: domain-randomisation ranges (Table 2 train column
@@ -123,6 +125,8 @@ typedef struct {
   double target_half;      // hover target p* ~ U[-L, L]^3
   double pos_radius;       // initial |p - p*| <= radius (uniform in ball)
   double max_angle;        // initial attitude error angle ~ U[0, max], rad
+  int32_t track;           // 1: draw a tracking reference
+  int32_t track_kind;      // 0 helix, 1 Lissajous
 } or_reset_cfg;
 
 }  // extern "C"
@@ -232,7 +236,15 @@ template <class T> struct EnvT {
   double mass, Ig[3], rg[3], rb[3], W, B;
   T Ma[6], dl[6], dq[6];
   double Vc[3], target[3];
+  double ta[3], tw[3], tph[3], tv[3], k0;
 };
+
+// Station-keeping target / tracking reference at time t (Sec. IV-B tasks):
+// a helix or Lissajous curve written as c + a o sin(w t + phi) + v t
+// (all of a, w, phi, v zero for station keeping).
+template <class T> static void reference(const EnvT<T>& e, double t, double out[3]) {
+  for (int i = 0; i < 3; ++i) out[i] = e.target[i] + e.ta[i] * std::sin(e.tw[i] * t + e.tph[i]) + e.tv[i] * t;
+}
 
 // Rigid-body inertia about the body origin with the CoG at r_g:
 // M_RB = [[m I, -m S(r_g)], [m S(r_g), I_g - m S(r_g)^2]].
@@ -450,12 +462,15 @@ static void substep(const or_class& c, const EnvT<T>& e, const double alpha[8], 
 
 // Hover-task observation (13) and reward after a control step.
 template <class T>
-static void observe(const or_class& c, const EnvT<T>& e, const T s[SDIM], const T cmd[8], T obs[13], T* reward) {
+static void observe(const or_class& c, const EnvT<T>& e, double t_ref, const T s[SDIM], const T cmd[8], T obs[13],
+                    T* reward) {
   T q[4] = {s[SQ], s[SQ + 1], s[SQ + 2], s[SQ + 3]};
   T R[3][3];
   rotation(q, R);
+  double pstar[3];
+  reference(e, t_ref, pstar);
   T d[3];
-  for (int i = 0; i < 3; ++i) d[i] = s[SP + i] - T(e.target[i]);
+  for (int i = 0; i < 3; ++i) d[i] = s[SP + i] - T(pstar[i]);
   for (int j = 0; j < 3; ++j) obs[j] = R[0][j] * d[0] + R[1][j] * d[1] + R[2][j] * d[2];
   T sgn = (val(q[0]) < 0.0) ? T(-1.0) : T(1.0);
   for (int i = 0; i < 4; ++i) obs[3 + i] = sgn * q[i];
@@ -482,6 +497,10 @@ template <class T> static EnvT<T> env_of(const or_env& in) {
   }
   e.W = in.W; e.B = in.B;
   for (int i = 0; i < 6; ++i) { e.Ma[i] = T(in.Ma[i]); e.dl[i] = T(in.dl[i]); e.dq[i] = T(in.dq[i]); }
+  for (int i = 0; i < 3; ++i) {
+    e.ta[i] = in.traj_a[i]; e.tw[i] = in.traj_w[i]; e.tph[i] = in.traj_phi[i]; e.tv[i] = in.traj_v[i];
+  }
+  e.k0 = in.k0;
   return e;
 }
 
@@ -557,15 +576,38 @@ int or_reset(const or_class* classes, int n_classes, const int32_t* env_class, i
     double* s = state + ei * SDIM;
     for (int i = 0; i < SDIM; ++i) s[i] = 0.0;
     s[SQ] = 1.0;
-    if (cfg->init_mode == 1) {
+    if (cfg->init_mode == 1 || cfg->track)
       for (int i = 0; i < 3; ++i)
         e.target[i] = cfg->target_half * (2.0 * draw_u(seed, kStreamInit, id, i) - 1.0);
+    if (cfg->track) {
+      // Helix: c + (R cos(W t + psi), R sin(W t + psi), v_z t), written with
+      // sin(x + pi/2) = cos(x). Lissajous: c + a o sin(w t + phi).
+      if (cfg->track_kind == 0) {
+        const double R = 1.0 + 2.0 * draw_u(seed, kStreamInit, id, 9);
+        const double W = 0.2 + 0.4 * draw_u(seed, kStreamInit, id, 10);
+        const double psi = 2.0 * kPi * draw_u(seed, kStreamInit, id, 11);
+        const double vz = -0.2 + 0.4 * draw_u(seed, kStreamInit, id, 12);
+        e.traj_a[0] = R; e.traj_a[1] = R;
+        e.traj_w[0] = W; e.traj_w[1] = W;
+        e.traj_phi[0] = psi + 0.5 * kPi; e.traj_phi[1] = psi;
+        e.traj_v[2] = vz;
+      } else {
+        for (int i = 0; i < 3; ++i) {
+          e.traj_a[i] = 1.0 + 2.0 * draw_u(seed, kStreamInit, id, 9 + i);
+          e.traj_w[i] = 0.2 + 0.4 * draw_u(seed, kStreamInit, id, 12 + i);
+          e.traj_phi[i] = 2.0 * kPi * draw_u(seed, kStreamInit, id, 15 + i);
+        }
+      }
+    }
+    if (cfg->init_mode == 1) {
+      double p0[3];
+      for (int i = 0; i < 3; ++i) p0[i] = e.target[i] + e.traj_a[i] * std::sin(e.traj_phi[i]);
       const double rad = cfg->pos_radius * std::cbrt(draw_u(seed, kStreamInit, id, 3));
       const double zd = 2.0 * draw_u(seed, kStreamInit, id, 4) - 1.0;
       const double ph = 2.0 * kPi * draw_u(seed, kStreamInit, id, 5);
       const double rd = std::sqrt(1.0 - zd * zd);
       const double dir[3] = {rd * std::cos(ph), rd * std::sin(ph), zd};
-      for (int i = 0; i < 3; ++i) s[SP + i] = e.target[i] + rad * dir[i];
+      for (int i = 0; i < 3; ++i) s[SP + i] = p0[i] + rad * dir[i];
       const double za = 2.0 * draw_u(seed, kStreamInit, id, 6) - 1.0;
       const double pa = 2.0 * kPi * draw_u(seed, kStreamInit, id, 7);
       const double ra = std::sqrt(1.0 - za * za);
@@ -602,7 +644,7 @@ int or_rollout(const or_class* classes, const or_env* envs, int64_t n_envs, doub
       for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, form, s);
       if (obs || reward) {
         double o[13], r;
-        observe(c, e, s, cmd, o, &r);
+        observe(c, e, (e.k0 + t + 1) * dt, s, cmd, o, &r);
         if (obs) for (int i = 0; i < 13; ++i) obs[((int64_t)t * n_envs + ei) * 13 + i] = o[i];
         if (reward) reward[(int64_t)t * n_envs + ei] = r;
       }
@@ -643,7 +685,7 @@ int or_rollout_jvp(const or_class* classes, const or_env* envs, int64_t n_envs, 
         cmd[i] = clamp1(Dual((double)actions[ai + i], d_actions ? d_actions[ai + i] : 0.0));
       for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, 0, s);
       Dual o[13], r;
-      observe(c, e, s, cmd, o, &r);
+      observe(c, e, (e.k0 + t + 1) * dt, s, cmd, o, &r);
       for (int i = 0; i < 13; ++i) {
         const int64_t oi = ((int64_t)t * n_envs + ei) * 13 + i;
         if (obs) obs[oi] = o[i].v;

@@ -62,14 +62,14 @@ class mg_reset_cfg(C.Structure):
                 ("cob_lo", C.c_double), ("cob_hi", C.c_double),
                 ("cur_lo", C.c_double), ("cur_hi", C.c_double),
                 ("target_half", C.c_double), ("pos_radius", C.c_double),
-                ("max_angle", C.c_double)]
+                ("max_angle", C.c_double), ("track_kind", C.c_int32), ("pad0", C.c_int32)]
 
 
 class mg_config(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("class_counts", C.POINTER(C.c_int32)),
                 ("dt", C.c_double), ("K", C.c_int32), ("per_env_params", C.c_int32),
                 ("reset", mg_reset_cfg), ("record_steps", C.c_int32), ("ckpt_every", C.c_int32),
-                ("mem_budget", C.c_size_t)]
+                ("mem_budget", C.c_size_t), ("task", C.c_int32), ("pad0", C.c_int32)]
 
 
 class mg_class_layout(C.Structure):
@@ -124,6 +124,8 @@ _SIGS = {
     "mg_get_state": [_VP, _VP, C.c_size_t],
     "mg_set_state": [_VP, _VP, C.c_size_t],
     "mg_get_params": [_VP, _VP, C.c_size_t],
+    "mg_get_task": [_VP, _VP, C.c_size_t],
+    "mg_set_task": [_VP, _VP, C.c_size_t],
     "mg_set_params": [_VP, _VP, C.c_size_t],
     "mg_status": [_VP, _VP],
     "mg_autotune": [_VP, _VP, C.POINTER(_I32), C.POINTER(_I32)],
@@ -227,14 +229,19 @@ def pack_reset(d: dict) -> mg_reset_cfg:
 # C entry points with the same names.
 # ---------------------------------------------------------------------------
 
+TASK_HOVER, TASK_TRACK = 0, 1
+
+
 def mg_create(classes: Sequence[dict], counts: Sequence[int], dt: float, K: int, per_env_params: bool = True,
-              reset: Optional[dict] = None, record_steps: int = 0, ckpt_every: int = 0, mem_budget: int = 0):
+              reset: Optional[dict] = None, record_steps: int = 0, ckpt_every: int = 0, mem_budget: int = 0,
+              task: int = TASK_HOVER):
     L = lib()
     arr = (mg_class_desc * len(classes))(*[pack_class(c) for c in classes])
     cnt = (C.c_int32 * len(counts))(*[int(x) for x in counts])
     cfg = mg_config(n_classes=len(classes), class_counts=cnt, dt=float(dt), K=int(K),
                     per_env_params=int(bool(per_env_params)), reset=pack_reset(reset or {}),
-                    record_steps=int(record_steps), ckpt_every=int(ckpt_every), mem_budget=int(mem_budget))
+                    record_steps=int(record_steps), ckpt_every=int(ckpt_every), mem_budget=int(mem_budget),
+                    task=int(task))
     h = _VP()
     _check(L.mg_create(C.byref(cfg), arr, C.byref(h)), None)
     return h.value
@@ -320,6 +327,20 @@ def mg_set_params(sim, params: np.ndarray):
     return _check(lib().mg_set_params(sim, p.ctypes.data, p.nbytes), sim)
 
 
+TASK_DIM = 16   # c[3], a[3], w[3], phi[3], v[3], step counter
+
+
+def mg_get_task(sim, n_envs: int) -> np.ndarray:
+    out = np.zeros((n_envs, TASK_DIM), np.float64)
+    _check(lib().mg_get_task(sim, out.ctypes.data, out.nbytes), sim)
+    return out
+
+
+def mg_set_task(sim, task: np.ndarray):
+    t = np.ascontiguousarray(task, dtype=np.float64)
+    return _check(lib().mg_set_task(sim, t.ctypes.data, t.nbytes), sim)
+
+
 def mg_status(sim, stream=None):
     return _check(lib().mg_status(sim, _stream(stream)), sim)
 
@@ -385,13 +406,13 @@ class Sim:
     """
 
     def __init__(self, classes, counts, dt=0.01, K=1, per_env_params=True, reset=None, record_steps=0,
-                 ckpt_every=0, mem_budget=0, device="cuda"):
+                 ckpt_every=0, mem_budget=0, task=TASK_HOVER, device="cuda"):
         import torch
         self.classes = list(classes)
         self.counts = [int(c) for c in counts]
         self.dt, self.K = float(dt), int(K)
         self.handle = mg_create(self.classes, self.counts, dt, K, per_env_params, reset, record_steps,
-                                ckpt_every, mem_budget)
+                                ckpt_every, mem_budget, task)
         self.layout = mg_get_layout(self.handle)
         self.n_envs = self.layout.n_envs
         self.n_slots = self.layout.n_slots
@@ -475,6 +496,12 @@ class Sim:
 
     def set_params(self, p):
         mg_set_params(self.handle, p)
+
+    def get_task(self):
+        return mg_get_task(self.handle, self.n_envs)
+
+    def set_task(self, t):
+        mg_set_task(self.handle, t)
 
     def status(self, stream=None):
         return mg_status(self.handle, stream)

@@ -47,6 +47,24 @@ MG_HD float minvsqrt(float x) {
 #endif
 }
 MG_HD double minvsqrt(double x) { return 1.0 / sqrt(x); }
+MG_HD float msin(float x) { return sinf(x); }
+MG_HD double msin(double x) { return sin(x); }
+
+// Reference point of the trajectory-tracking task at step counter k:
+// p*(t) = c + a o sin(w t + phi) + v t, t = k dt. `c` is the target plane
+// (centre; its w lane holds the counter), tr0..tr2 the three trajectory planes
+// (a_x a_y a_z w_x | w_y w_z phi_x phi_y | phi_z v_x v_y v_z).
+template <typename S>
+MG_HD void track_ref(float4 c, float4 tr0, float4 tr1, float4 tr2, S dt, S k, S out[3]) {
+  const S t = k * dt;
+  const S a[3] = {S(tr0.x), S(tr0.y), S(tr0.z)};
+  const S w[3] = {S(tr0.w), S(tr1.x), S(tr1.y)};
+  const S ph[3] = {S(tr1.z), S(tr1.w), S(tr2.x)};
+  const S v[3] = {S(tr2.y), S(tr2.z), S(tr2.w)};
+  const S cc[3] = {S(c.x), S(c.y), S(c.z)};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] = cc[i] + a[i] * msin(w[i] * t + ph[i]) + v[i] * t;
+}
 
 // Actuator table of one (class, substep length).
 template <typename S>

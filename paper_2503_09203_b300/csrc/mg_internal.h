@@ -23,7 +23,9 @@ struct SegDesc {
   int64_t slot_off;     // first slot (obs / reward / parameter planes)
   int64_t env_base;     // global env id of local env 0 (random draws)
   float h;
-  float pad1[3];
+  float dt;             // control step (trajectory time = step counter * dt)
+  int32_t track;        // 1: trajectory-tracking reference, 0: fixed hover target
+  float pad1;
   float alpha[8];
   uint64_t seed;        // serving: action seed
   uint64_t pad2;
@@ -54,7 +56,15 @@ enum { PAR_MINV = 0, PAR_A = 6, PAR_DL = 12, PAR_DQ = 18, PAR_M = 24, PAR_IG = 2
        PAR_B = 29, PAR_RB = 30, PAR_VC = 33, PAR_DIM = 36 };
 
 // Number of float4 parameter planes: 9 for the 36 physical floats + 1 target.
-enum { PAR_PLANES = 9, TGT_PLANE = 9, N_PLANES = 10 };
+// The target plane holds (c_x, c_y, c_z, k): the reference centre and the
+// env's step counter. Tracking runs add 3 planes right after the target:
+// (a_x, a_y, a_z, w_x), (w_y, w_z, phi_x, phi_y), (phi_z, v_x, v_y, v_z) of the
+// reference p*(t) = c + a o sin(w t + phi) + v t, t = k dt.
+enum { PAR_PLANES = 9, TGT_PLANE = 9, N_PLANES = 10, TRAJ_PLANES = 3 };
+// Index of the target plane (per-env runs keep the physics in planes 0..8).
+__host__ __device__ inline int tgt_plane(int per_env) { return per_env ? TGT_PLANE : 0; }
+// Planes of a run.
+inline int n_planes_of(int per_env, int track) { return (per_env ? PAR_PLANES : 0) + 1 + (track ? TRAJ_PLANES : 0); }
 
 // A launch covers the segments [seg_lo, seg_hi) of one thruster count, whose
 // tiles are tile_lo .. tile_lo + n_tiles - 1.
@@ -125,6 +135,7 @@ struct ResetArgs {
   int32_t dr, cur, cur3d, init_mode;
   double mass_lo, mass_hi, added_lo, added_hi, damp_lo, damp_hi, cob_lo, cob_hi, cur_lo, cur_hi;
   double target_half, pos_radius, max_angle;
+  int32_t track, track_kind;
 };
 
 // Arguments of the FP64 finite-difference rollout.
@@ -145,6 +156,7 @@ struct Fp64Args {
   const double* ddl;
   const double* ddq;
   double eps;
+  double dt;                  // control step in FP64 (tracking time)
   double h;                   // dt / K in FP64
   double* reward;
   double* state_out;

@@ -318,10 +318,12 @@ struct Stage {
   static constexpr int SS = 13 + NT, NF4 = SS / 4, REM = SS % 4;
   static constexpr int ACT_OFF = WENV * SS;                     // floats
   static constexpr int TGT_OFF = ACT_OFF + WENV * NT;           // floats (16-byte aligned)
-  static constexpr int FLOATS = TGT_OFF + 4 * WENV;
+  static constexpr int TRJ_OFF = TGT_OFF + 4 * WENV;            // 3 trajectory planes (tracking runs)
+  static constexpr int FLOATS = TRJ_OFF + 12 * WENV;
   static constexpr int OBS = WENV * 13;
   static constexpr int WARP_FLOATS = 2 * FLOATS + OBS;          // per warp
-  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (FLOATS % 4) == 0 && (OBS % 4) == 0,
+  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (FLOATS % 4) == 0 &&
+                    (OBS % 4) == 0,
                 "16-byte aligned sections");
 };
 constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
@@ -336,6 +338,7 @@ __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDes
   unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
   const bool load_act = a.n_steps > 0 && a.act_mode == 0;
   if (load_act) bytes += nvw * NT * 4;
+  if (sd.track) bytes += 3 * nvw * 16;
   mbar_expect_tx(bar, bytes);
   const unsigned b = smem_addr(buf);
 #pragma unroll
@@ -345,7 +348,13 @@ __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDes
     bulk_load(b + 16u * SG::NF4 * WENV + 4u * r * WENV, st + (int64_t)SG::NF4 * 4 * sd.n4 + (int64_t)r * sd.n4 + w0,
               nvw * 4, bar);
   if (load_act) bulk_load(b + 4u * SG::ACT_OFF, a.actions + sd.act_off + w0 * NT, nvw * NT * 4, bar);
-  bulk_load(b + 4u * SG::TGT_OFF, a.planes + (PER_ENV ? TGT_PLANE : 0) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
+  bulk_load(b + 4u * SG::TGT_OFF, a.planes + tgt_plane(PER_ENV) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
+  if (sd.track) {
+#pragma unroll
+    for (int q = 0; q < TRAJ_PLANES; ++q)
+      bulk_load(b + 4u * (SG::TRJ_OFF + 4 * q * WENV),
+                a.planes + (int64_t)(tgt_plane(PER_ENV) + 1 + q) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
+  }
 }
 
 // Envs of warp `warp` in a tile that starts at local env local0 (0 if none).
@@ -379,6 +388,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   St<float, NT> x;
   float c[NT];
   float tgt[3] = {0.0f, 0.0f, 0.0f};
+  float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
   for (int j = 0; j < NT; ++j) c[j] = 0.0f;
   bool have_act0 = false;
@@ -393,7 +403,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 #pragma unroll
     for (int r = 0; r < SG::REM; ++r) f[(SG::NF4 * 4 + r) % (13 + NT)] = buf[SG::NF4 * 4 * WENV + r * WENV + lane];
     fields_to_state<NT>(f, x);
-    const float4 tg = reinterpret_cast<const float4*>(buf + SG::TGT_OFF)[lane];
+    tg = reinterpret_cast<const float4*>(buf + SG::TGT_OFF)[lane];
     tgt[0] = tg.x; tgt[1] = tg.y; tgt[2] = tg.z;
     if (a.n_steps > 0 && a.act_mode == 0) {
 #pragma unroll
@@ -471,7 +481,16 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       float o[13], r = 0.0f;
 #pragma unroll
       for (int j = 0; j < 13; ++j) o[j] = 0.0f;
-      if (valid) observe<float, NT>(x, c, tgt, o, r);
+      if (valid) {
+        if (sd.track) {
+          // Tracking reference at the end of this step (counter k0 + t + 1);
+          // its parameters were staged with the tile.
+          const float4* tp = reinterpret_cast<const float4*>(buf + SG::TRJ_OFF) + lane;
+          const float kk = tg.w + (a.n_steps > 0 ? (float)(t + 1) : 0.0f);
+          track_ref<float>(tg, tp[0], tp[WENV], tp[2 * WENV], sd.dt, kk, tgt);
+        }
+        observe<float, NT>(x, c, tgt, o, r);
+      }
       if (a.obs && nvw > 0) {
         // The warp's previous observation store must have read its buffer.
         if (lane == 0 && n_emit > 0) bulk_wait_read0();
@@ -492,6 +511,11 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   }
   if (valid && a.n_steps > 0) {
     store_state<NT>(st_base, sd.n4, i, x);
+    if (sd.track) {
+      // Advance the env's step counter (w lane of its target plane entry).
+      float* kp = reinterpret_cast<float*>(const_cast<float4*>(a.planes) + (int64_t)tgt_plane(PER_ENV) * a.n_slots + slot);
+      kp[3] = tg.w + (float)a.n_steps;
+    }
     float s = 0.0f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) s += x.p[j];
@@ -659,15 +683,41 @@ __global__ void mg_reset_kernel(const __grid_constant__ ResetArgs a) {
   for (int j = 0; j < 21; ++j) f[j] = 0.0;
   f[3] = 1.0;
   double tgt[3] = {0.0, 0.0, 0.0};
-  if (a.init_mode == 1) {
+  // Tracking reference (stream 2, draws 9..): a, w, phi, v of
+  // p*(t) = c + a o sin(w t + phi) + v t.
+  double ta[3] = {0.0, 0.0, 0.0}, tw[3] = {0.0, 0.0, 0.0}, tph[3] = {0.0, 0.0, 0.0}, tv[3] = {0.0, 0.0, 0.0};
+  if (a.init_mode == 1 || a.track)
     for (int j = 0; j < 3; ++j) tgt[j] = a.target_half * (2.0 * uniform53(seed, STREAM_INIT, id, j) - 1.0);
+  if (a.track) {
+    const double two_pi = 6.283185307179586;
+    if (a.track_kind == 0) {
+      const double R = 1.0 + 2.0 * uniform53(seed, STREAM_INIT, id, 9);
+      const double W = 0.2 + 0.4 * uniform53(seed, STREAM_INIT, id, 10);
+      const double psi = two_pi * uniform53(seed, STREAM_INIT, id, 11);
+      const double vz = -0.2 + 0.4 * uniform53(seed, STREAM_INIT, id, 12);
+      ta[0] = R; ta[1] = R;
+      tw[0] = W; tw[1] = W;
+      tph[0] = psi + 0.5 * 3.141592653589793; tph[1] = psi;
+      tv[2] = vz;
+    } else {
+      for (int j = 0; j < 3; ++j) {
+        ta[j] = 1.0 + 2.0 * uniform53(seed, STREAM_INIT, id, 9 + j);
+        tw[j] = 0.2 + 0.4 * uniform53(seed, STREAM_INIT, id, 12 + j);
+        tph[j] = two_pi * uniform53(seed, STREAM_INIT, id, 15 + j);
+      }
+    }
+  }
+  if (a.init_mode == 1) {
+    // Initial pose around the reference at t = 0.
+    double p0[3];
+    for (int j = 0; j < 3; ++j) p0[j] = tgt[j] + ta[j] * sin(tph[j]);
     const double rad = a.pos_radius * cbrt(uniform53(seed, STREAM_INIT, id, 3));
     const double zd = 2.0 * uniform53(seed, STREAM_INIT, id, 4) - 1.0;
     const double ph = 6.283185307179586 * uniform53(seed, STREAM_INIT, id, 5);
     const double rd = sqrt(1.0 - zd * zd);
-    f[0] = tgt[0] + rad * rd * cos(ph);
-    f[1] = tgt[1] + rad * rd * sin(ph);
-    f[2] = tgt[2] + rad * zd;
+    f[0] = p0[0] + rad * rd * cos(ph);
+    f[1] = p0[1] + rad * rd * sin(ph);
+    f[2] = p0[2] + rad * zd;
     const double za = 2.0 * uniform53(seed, STREAM_INIT, id, 6) - 1.0;
     const double pa = 6.283185307179586 * uniform53(seed, STREAM_INIT, id, 7);
     const double ra = sqrt(1.0 - za * za);
@@ -705,8 +755,13 @@ __global__ void mg_reset_kernel(const __grid_constant__ ResetArgs a) {
     for (int kk = 0; kk < PAR_PLANES; ++kk)
       a.planes[kk * a.n_slots + slot] = make_float4(v[4 * kk], v[4 * kk + 1], v[4 * kk + 2], v[4 * kk + 3]);
   }
-  a.planes[(a.per_env ? TGT_PLANE : 0) * a.n_slots + slot] =
-      make_float4((float)tgt[0], (float)tgt[1], (float)tgt[2], 0.0f);
+  const int tp = tgt_plane(a.per_env);
+  a.planes[tp * a.n_slots + slot] = make_float4((float)tgt[0], (float)tgt[1], (float)tgt[2], 0.0f);
+  if (a.track) {
+    a.planes[(tp + 1) * a.n_slots + slot] = make_float4((float)ta[0], (float)ta[1], (float)ta[2], (float)tw[0]);
+    a.planes[(tp + 2) * a.n_slots + slot] = make_float4((float)tw[1], (float)tw[2], (float)tph[0], (float)tph[1]);
+    a.planes[(tp + 3) * a.n_slots + slot] = make_float4((float)tph[2], (float)tv[0], (float)tv[1], (float)tv[2]);
+  }
 }
 
 // Overwrite added mass / damping planes and recompute M^-1 in FP64.
@@ -756,7 +811,13 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
   Phys<float> P;
   load_phys(a.planes, ns, slot, P);
   const float4 tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
-  const float tgt[3] = {tg.x, tg.y, tg.z};
+  float tgt[3] = {tg.x, tg.y, tg.z};
+  float4 tr[3] = {tg, tg, tg};
+  if (sd.track) {
+    for (int q = 0; q < 3; ++q) tr[q] = __ldg(&a.planes[(TGT_PLANE + 1 + q) * ns + slot]);
+  }
+  // The recorded rollout advanced the counter by T.
+  const float k_start = tg.w - (float)a.T;
   St<float, NT> lam;
 #pragma unroll
   for (int j = 0; j < 3; ++j) lam.p[j] = a.g_state_T ? a.g_state_T[slot * 21 + j] : 0.0f;
@@ -805,6 +866,7 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
         gop = go;
       }
       const float gr = a.g_rew ? a.g_rew[(int64_t)t * ns + slot] : 0.0f;
+      if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
       observe_vjp<float, NT>(xe, c, tgt, gop, gr, lam, lc);
       for (int k = K - 1; k >= 0; --k) {
         St<float, NT> xs;
@@ -895,7 +957,11 @@ __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
   const double Mrb[6] = {P.m, P.m, P.m, P.Ig[0], P.Ig[1], P.Ig[2]};
   for (int j = 0; j < 6; ++j) P.minv[j] = 1.0 / (Mrb[j] + P.A[j]);
   const float4 tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
-  const double tgt[3] = {tg.x, tg.y, tg.z};
+  double tgt[3] = {tg.x, tg.y, tg.z};
+  float4 tr[3] = {tg, tg, tg};
+  if (sd.track) {
+    for (int q = 0; q < 3; ++q) tr[q] = __ldg(&a.planes[(TGT_PLANE + 1 + q) * ns + slot]);
+  }
   St<float, NT> xf;
   load_state<NT>(a.state + sd.st_off, sd.n4, i, xf);
   St<double, NT> x;
@@ -910,6 +976,7 @@ __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
     for (int q = 0; q < NT; ++q) c[q] = raw[q] < -1.0f ? -1.0 : (raw[q] > 1.0f ? 1.0 : (double)raw[q]);
     for (int k = 0; k < sd.K; ++k) substep<double, NT, false>(x, c, P, A, a.h, nullptr);
     double o[13], r;
+    if (sd.track) track_ref<double>(tg, tr[0], tr[1], tr[2], a.dt, (double)tg.w + (double)(t + 1), tgt);
     observe<double, NT>(x, c, tgt, o, r);
     a.reward[(int64_t)t * ns + slot] = r;
   }

@@ -168,6 +168,8 @@ static void build_segs(mg_sim* sim) {
       sd.slot_off = L.slot_off;
       sd.env_base = L.env_off;
       sd.h = (float)sim->h;
+      sd.dt = (float)sim->cfg.dt;
+      sd.track = sim->cfg.task == 1;
       double a[8];
       alpha_of(sim->classes[c], sim->h, a);
       for (int i = 0; i < 8; ++i) sd.alpha[i] = (float)a[i];
@@ -230,6 +232,8 @@ static ResetArgs reset_args(mg_sim* sim, const mg_reset_cfg& r, uint64_t seed) {
   a.cob_lo = r.cob_lo; a.cob_hi = r.cob_hi;
   a.cur_lo = r.cur_lo; a.cur_hi = r.cur_hi;
   a.target_half = r.target_half; a.pos_radius = r.pos_radius; a.max_angle = r.max_angle;
+  a.track = sim->cfg.task == 1;
+  a.track_kind = r.track_kind;
   return a;
 }
 
@@ -270,6 +274,8 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (cfg->record_steps < 0 || cfg->ckpt_every < 0) return bail(MG_ERR_INVALID_ARG);
   if (!cfg->per_env_params && (cfg->reset.dr_enabled || cfg->reset.current_enabled || cfg->record_steps > 0))
     return bail(MG_ERR_INVALID_ARG);
+  if (cfg->task < 0 || cfg->task > 1 || cfg->reset.track_kind < 0 || cfg->reset.track_kind > 1)
+    return bail(MG_ERR_INVALID_ARG);
   sim->n_classes = cfg->n_classes;
   sim->classes.assign(classes, classes + cfg->n_classes);
   sim->counts.assign(cfg->class_counts, cfg->class_counts + cfg->n_classes);
@@ -305,7 +311,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
   cudaDeviceGetAttribute(&sim->num_sms, cudaDevAttrMultiProcessorCount, dev);
 
-  sim->n_planes = cfg->per_env_params ? N_PLANES : 1;
+  sim->n_planes = n_planes_of(cfg->per_env_params, cfg->task == 1);
   int rc;
   if ((rc = dev_alloc(sim, (void**)&sim->d_state, sizeof(float) * st)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_planes, sizeof(float4) * sim->n_planes * slot)) != MG_OK) return bail(rc);
@@ -596,6 +602,7 @@ int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, cons
   a.T = n_steps;
   a.dA = dA; a.ddl = ddl; a.ddq = ddq;
   a.eps = eps;
+  a.dt = sim->cfg.dt;
   a.h = sim->h;
   a.reward = reward_dev;
   a.state_out = state_dev;
@@ -664,7 +671,7 @@ int mg_get_params(const mg_sim* csim, double* host, size_t bytes) {
       const int64_t slot = L.slot_off + i;
       float v[40];
       if (sim->cfg.per_env_params) {
-        for (int k = 0; k < N_PLANES; ++k) {
+        for (int k = 0; k < PAR_PLANES + 1; ++k) {
           const float4 x = pl[(size_t)k * sim->n_slots + slot];
           v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
         }
@@ -721,10 +728,73 @@ int mg_set_params(mg_sim* sim, const double* host, size_t bytes) {
       for (int j = 0; j < 3; ++j) { v[PAR_IG + j] = (float)Ig[j]; v[PAR_RB + j] = (float)s[4 + j]; v[PAR_VC + j] = (float)s[27 + j]; }
       v[PAR_W] = (float)s[7];
       v[PAR_B] = (float)s[8];
-      v[36] = (float)s[30]; v[37] = (float)s[31]; v[38] = (float)s[32]; v[39] = 0.0f;
       const int64_t slot = L.slot_off + i;
-      for (int k = 0; k < N_PLANES; ++k)
+      // The target plane's w lane is the env's step counter: keep it.
+      v[36] = (float)s[30]; v[37] = (float)s[31]; v[38] = (float)s[32];
+      v[39] = pl[(size_t)TGT_PLANE * sim->n_slots + slot].w;
+      for (int k = 0; k < PAR_PLANES + 1; ++k)
         pl[(size_t)k * sim->n_slots + slot] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+  }
+  CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+int mg_get_task(const mg_sim* csim, double* host, size_t bytes) {
+  mg_sim* sim = const_cast<mg_sim*>(csim);
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(double) * 16 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "get_task: buffer too small");
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  const int tp = tgt_plane(sim->cfg.per_env_params);
+  const bool track = sim->cfg.task == 1;
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const int64_t slot = L.slot_off + i;
+      double* o = host + (L.env_off + i) * 16;
+      for (int j = 0; j < 16; ++j) o[j] = 0.0;
+      const float4 g = pl[(size_t)tp * sim->n_slots + slot];
+      o[0] = g.x; o[1] = g.y; o[2] = g.z; o[15] = g.w;
+      if (track) {
+        const float4 t0 = pl[(size_t)(tp + 1) * sim->n_slots + slot];
+        const float4 t1 = pl[(size_t)(tp + 2) * sim->n_slots + slot];
+        const float4 t2 = pl[(size_t)(tp + 3) * sim->n_slots + slot];
+        const float r[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
+        for (int j = 0; j < 12; ++j) o[3 + j] = r[j];
+      }
+    }
+  }
+  return MG_OK;
+}
+
+int mg_set_task(mg_sim* sim, const double* host, size_t bytes) {
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (bytes < sizeof(double) * 16 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "set_task: buffer too small");
+  const bool track = sim->cfg.task == 1;
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  const int tp = tgt_plane(sim->cfg.per_env_params);
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const double* s = host + (L.env_off + i) * 16;
+      for (int j = 0; j < 16; ++j)
+        if (!std::isfinite(s[j])) return fail(sim, MG_ERR_INVALID_ARG, "set_task: env %lld not finite", (long long)(L.env_off + i));
+      if (!track)
+        for (int j = 3; j < 15; ++j)
+          if (s[j] != 0.0) return fail(sim, MG_ERR_INVALID_ARG, "set_task: a, w, phi, v must be 0 without tracking");
+      if (s[15] < 0 || s[15] > 16777216.0 || s[15] != std::floor(s[15]))
+        return fail(sim, MG_ERR_INVALID_ARG, "set_task: step counter must be an integer in [0, 2^24]");
+      const int64_t slot = L.slot_off + i;
+      pl[(size_t)tp * sim->n_slots + slot] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[15]);
+      if (track) {
+        pl[(size_t)(tp + 1) * sim->n_slots + slot] = make_float4((float)s[3], (float)s[4], (float)s[5], (float)s[6]);
+        pl[(size_t)(tp + 2) * sim->n_slots + slot] = make_float4((float)s[7], (float)s[8], (float)s[9], (float)s[10]);
+        pl[(size_t)(tp + 3) * sim->n_slots + slot] = make_float4((float)s[11], (float)s[12], (float)s[13], (float)s[14]);
+      }
     }
   }
   CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));

@@ -209,6 +209,8 @@ static SegDesc seg_of(const Req& q) {
   sd.slot_off = q.slot_off;
   sd.env_base = 0;
   sd.h = q.h;
+  sd.dt = q.h * (float)q.r.K;
+  sd.track = 0;
   for (int i = 0; i < 8; ++i) sd.alpha[i] = q.alpha[i];
   sd.seed = q.r.seed;
   return sd;
@@ -417,7 +419,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   }
   // Per slot: 10 float4 planes + return; per state unit one float. A slot
   // holds at most 21 state floats, so size the spaces in that ratio.
-  const size_t per_slot = sizeof(float4) * N_PLANES + sizeof(float) + 21 * sizeof(float);
+  const size_t per_slot = sizeof(float4) * N_PLANES + sizeof(float) + 21 * sizeof(float);   // hover task: 10 planes
   int64_t S = (int64_t)(budget / per_slot) & ~int64_t(3);
   if (S < 4) { delete s; return MG_ERR_OOM; }
   s->S = S;

@@ -101,3 +101,8 @@ DR_TRAIN = dict(dr_enabled=1, current_enabled=1, current_3d=0, init_mode=0,
 NO_DR = dict(DR_TRAIN, dr_enabled=0, current_enabled=0)
 HOVER = dict(NO_DR, init_mode=1)
 HOVER_DR = dict(DR_TRAIN, init_mode=1)
+# Trajectory tracking (Sec. IV-B): helix or Lissajous references; the oracle
+# reads `track`, the library reads the simulator's task.
+TRACK_HELIX = dict(HOVER, track=1, track_kind=0)
+TRACK_LISSAJOUS = dict(HOVER, track=1, track_kind=1)
+TRACK_HELIX_DR = dict(HOVER_DR, track=1, track_kind=0)

@@ -529,3 +529,35 @@ def test_classes_explicit_step_stable_at_dr_extremes():
         vmax = (-dl * 0.8 / 1.2 + np.sqrt((dl * 0.8 / 1.2) ** 2 + 4 * dq * 0.8 / 1.2 * Fmax)) / (2 * dq * 0.8 / 1.2)
         ratio = 0.01 * (dl + 2 * dq * vmax) / (0.8 * M)
         assert ratio.max() <= 1.0, (c["name"], ratio)
+
+
+# ---------------------------------------------------------------------------
+# Trajectory tracking (Sec. IV-B): helix and Lissajous references.
+# ---------------------------------------------------------------------------
+def test_tracking_reference_helix_and_lissajous_closed_forms():
+    classes = [vehicles.heavy8()]
+    dt, K = 0.01, 1
+    for cfg, kind in ((vehicles.TRACK_HELIX, "helix"), (vehicles.TRACK_LISSAJOUS, "lissajous")):
+        envs, _ = oracle.reset(classes, np.zeros(8, np.int32), dict(cfg, init_mode=0), 21)
+        arr = oracle.envs_to_arrays(envs)
+        if kind == "helix":
+            # p*(t) - c = (R cos(W t + psi), R sin(W t + psi), v_z t)
+            R, W, psi, vz = arr["traj_a"][:, 0], arr["traj_w"][:, 0], arr["traj_phi"][:, 1], arr["traj_v"][:, 2]
+            assert np.all((R >= 1) & (R <= 3) & (W >= 0.2) & (W <= 0.6) & (np.abs(vz) <= 0.2))
+            np.testing.assert_array_equal(arr["traj_a"][:, 2], 0.0)
+        else:
+            assert np.all(arr["traj_v"] == 0.0) and np.all((arr["traj_a"] >= 1) & (arr["traj_a"] <= 3))
+        arr["k0"] = np.full(8, 37.0)
+        envs = oracle.make_envs(arr)
+        # A neutral vehicle at rest at the centre with identity attitude stays put,
+        # so the observation is c - p*(t) with t = (k0 + step + 1) dt.
+        s = np.zeros((8, 21)); s[:, 3] = 1.0; s[:, 0:3] = arr["target"]
+        T = 5
+        _, obs, _ = oracle.rollout(classes, envs, s, np.zeros((T, 8, 8), np.float32), dt, K)
+        for t in range(T):
+            tt = (37.0 + t + 1) * dt
+            if kind == "helix":
+                ref = np.stack([R * np.cos(W * tt + psi), R * np.sin(W * tt + psi), vz * tt], 1)
+            else:
+                ref = arr["traj_a"] * np.sin(arr["traj_w"] * tt + arr["traj_phi"])
+            np.testing.assert_allclose(obs[t, :, 0:3], -ref, atol=1e-12)
