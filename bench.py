@@ -160,13 +160,14 @@ def workload(n_envs, K):
 
 
 def algorithmic(classes, counts, K):
-    """Bytes and FP32 ops per env-step of the hover step (class parameters):
-    state in + out 2*4*(13+n), actions 4n, target 12, observation 52, reward 4."""
+    """Bytes and FP32 ops per env-step of the hover step (class parameters, no
+    current): state in + out 2*4*(13+n), actions 4n, target 12, observation 52,
+    reward 4."""
     from paper_2503_09203_b300 import binding as B
     tot_b = tot_f = 0.0
     for c, n in zip(classes, counts):
         nt = c["n_thr"]
-        sub, obs = B.mg_count_flops(nt)
+        sub, obs = B.mg_count_flops(nt, with_current=False)
         tot_b += n * (2 * 4 * (13 + nt) + 4 * nt + 12 + 52 + 4)
         tot_f += n * (K * sub + obs)
     E = sum(counts)

@@ -285,10 +285,12 @@ int mg_graph_destroy(mg_graph* g);
 
 /* Algorithmic FP32 operations (FMA = 2, divide and square root = 1 each) for
  * a class with n_thr thrusters, counted by running the kernels' own templated
- * arithmetic with a counting scalar on the host: one substep (current terms
- * included), the observation + reward, and one substep's adjoint (its
- * forward recompute included). Any output may be NULL. */
-int mg_count_flops(int32_t n_thr, double* substep_flops, double* observe_flops, double* adjoint_flops);
+ * arithmetic with a counting scalar on the host: one substep (with_current:
+ * including the ocean-current terms, which class-constant runs compile out),
+ * the observation + reward, and one substep's adjoint (its forward recompute
+ * included). Any output may be NULL. */
+int mg_count_flops(int32_t n_thr, int32_t with_current, double* substep_flops, double* observe_flops,
+                   double* adjoint_flops);
 
 const char* mg_last_error(const mg_sim* sim);
 const char* mg_strerror(int code);

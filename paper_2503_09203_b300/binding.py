@@ -132,7 +132,7 @@ _SIGS = {
     "mg_graph_capture": [_VP, _VP, _I32, _VP, _VP, _VP, C.POINTER(_VP)],
     "mg_graph_launch": [_VP, _VP],
     "mg_graph_destroy": [_VP],
-    "mg_count_flops": [_I32, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)],
+    "mg_count_flops": [_I32, _I32, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)],
     "mg_server_create": [C.POINTER(mg_server_config), C.POINTER(mg_class_desc), _I32, C.POINTER(_VP)],
     "mg_server_submit": [_VP, C.POINTER(mg_request), C.POINTER(_I64)],
     "mg_server_poll": [_VP, _I64, C.POINTER(mg_request_result)],
@@ -366,10 +366,11 @@ def mg_graph_destroy(graph):
     return _check(lib().mg_graph_destroy(graph))
 
 
-def mg_count_flops(n_thr: int, adjoint: bool = False):
-    """(substep, observe) FP32 op counts, plus the substep adjoint's if asked."""
+def mg_count_flops(n_thr: int, adjoint: bool = False, with_current: bool = True):
+    """(substep, observe) FP32 op counts, plus the substep adjoint's if asked.
+    with_current=False: the class-constant variant (no current terms)."""
     s, o, a = C.c_double(), C.c_double(), C.c_double()
-    _check(lib().mg_count_flops(int(n_thr), C.byref(s), C.byref(o), C.byref(a)))
+    _check(lib().mg_count_flops(int(n_thr), int(bool(with_current)), C.byref(s), C.byref(o), C.byref(a)))
     return (s.value, o.value, a.value) if adjoint else (s.value, o.value)
 
 

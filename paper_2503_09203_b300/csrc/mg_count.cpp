@@ -41,7 +41,7 @@ using mgcount::minvsqrt;
 }  // namespace mg
 
 template <int NT>
-static void count(double* sub, double* obs, double* adj) {
+static void count(bool with_current, double* sub, double* obs, double* adj) {
   using mg::Cnt;
   mg::St<Cnt, NT> x;
   for (int i = 0; i < 3; ++i) x.p[i] = Cnt(0.1 * (i + 1));
@@ -59,7 +59,10 @@ static void count(double* sub, double* obs, double* adj) {
   for (int k = 0; k < 6; ++k) for (int i = 0; i < 8; ++i) A.alloc[k][i] = Cnt(0.5);
   for (int i = 0; i < 8; ++i) { A.kf[i] = Cnt(40.0); A.dz[i] = Cnt(0.0); A.alpha[i] = Cnt(0.2); }
   mgcount::g_ops = 0;
-  mg::substep<Cnt, NT, false>(x, c, P, A, Cnt(0.01), nullptr);
+  if (with_current)
+    mg::substep<Cnt, NT, false, mg::Act<Cnt>, mg::Phys<Cnt>, true>(x, c, P, A, Cnt(0.01), nullptr);
+  else
+    mg::substep<Cnt, NT, false, mg::Act<Cnt>, mg::Phys<Cnt>, false>(x, c, P, A, Cnt(0.01), nullptr);
   *sub = (double)mgcount::g_ops;
   mgcount::g_ops = 0;
   Cnt tgt[3] = {Cnt(0.0), Cnt(0.0), Cnt(0.0)};
@@ -74,18 +77,18 @@ static void count(double* sub, double* obs, double* adj) {
   *adj = (double)mgcount::g_ops;
 }
 
-extern "C" int mg_count_flops(int32_t n_thr, double* substep_flops, double* observe_flops,
+extern "C" int mg_count_flops(int32_t n_thr, int32_t with_current, double* substep_flops, double* observe_flops,
                               double* adjoint_flops) {
   double s = 0, o = 0, a = 0;
   switch (n_thr) {
-    case 1: count<1>(&s, &o, &a); break;
-    case 2: count<2>(&s, &o, &a); break;
-    case 3: count<3>(&s, &o, &a); break;
-    case 4: count<4>(&s, &o, &a); break;
-    case 5: count<5>(&s, &o, &a); break;
-    case 6: count<6>(&s, &o, &a); break;
-    case 7: count<7>(&s, &o, &a); break;
-    case 8: count<8>(&s, &o, &a); break;
+    case 1: count<1>(with_current != 0, &s, &o, &a); break;
+    case 2: count<2>(with_current != 0, &s, &o, &a); break;
+    case 3: count<3>(with_current != 0, &s, &o, &a); break;
+    case 4: count<4>(with_current != 0, &s, &o, &a); break;
+    case 5: count<5>(with_current != 0, &s, &o, &a); break;
+    case 6: count<6>(with_current != 0, &s, &o, &a); break;
+    case 7: count<7>(with_current != 0, &s, &o, &a); break;
+    case 8: count<8>(with_current != 0, &s, &o, &a); break;
     default: return MG_ERR_INVALID_ARG;
   }
   if (substep_flops) *substep_flops = s;

@@ -141,7 +141,9 @@ struct Tape {
 // keeps the class table in shared memory instead of hoisting it into registers).
 // `P` is a Phys<S> or a view with the same members (arrays minv, A, dl, dq,
 // Ig, rb, Vc and scalars m, W, B) that reads shared memory on use.
-template <typename S, int NT, bool TAPE, typename ActT, typename PhysT>
+// CURRENT = false compiles the ocean-current terms out (parameter sources
+// whose current is zero by construction).
+template <typename S, int NT, bool TAPE, typename ActT, typename PhysT, bool CURRENT = true>
 MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
                    Tape<S, NT>* tp) {
   // a1 + a2
@@ -174,8 +176,8 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   S vc[3], vr[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    vc[j] = R[0][j] * S(P.Vc[0]) + R[1][j] * S(P.Vc[1]) + R[2][j] * S(P.Vc[2]);
-    vr[j] = v[j] - vc[j];
+    vc[j] = CURRENT ? R[0][j] * S(P.Vc[0]) + R[1][j] * S(P.Vc[1]) + R[2][j] * S(P.Vc[2]) : S(0.0f);
+    vr[j] = CURRENT ? v[j] - vc[j] : v[j];
   }
   // a4
   S wxv[3], Iw[3], wxIw[3];
@@ -189,7 +191,11 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   cross3(w, a1, wxa1);
   cross3(vr, a1, vrxa1);
   cross3(w, a2, wxa2);
-  cross3(w, vc, wxvc);
+  if (CURRENT) {
+    cross3(w, vc, wxvc);
+  } else {
+    wxvc[0] = wxvc[1] = wxvc[2] = S(0.0f);
+  }
   // a6 (nu_r = [v_r ; w])
   S dmp[6];
 #pragma unroll
@@ -207,7 +213,8 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   S rhs[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    rhs[j] = tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j];
+    rhs[j] = CURRENT ? tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j]
+                     : tau[j] - S(P.m) * wxv[j] - wxa1[j] - dmp[j] + WmB * e[j];
     rhs[3 + j] = tau[3 + j] - wxIw[j] - vrxa1[j] - wxa2[j] - dmp[3 + j] - mb[j];
   }
 #pragma unroll

@@ -88,7 +88,7 @@ struct StepArgs {
   float* ret;                 // serving: per-slot sum of rewards (or null)
   float* ckpt;                // record: [n_ckpt][21][n_slots] or null
   int32_t ckpt_every;
-  int32_t pad0;
+  int32_t track;              // 1: every segment of the launch is a tracking run
   uint32_t* status;           // bit 0: non-finite state
 };
 

@@ -318,12 +318,13 @@ struct Stage {
   static constexpr int SS = 13 + NT, NF4 = SS / 4, REM = SS % 4;
   static constexpr int ACT_OFF = WENV * SS;                     // floats
   static constexpr int TGT_OFF = ACT_OFF + WENV * NT;           // floats (16-byte aligned)
-  static constexpr int TRJ_OFF = TGT_OFF + 4 * WENV;            // 3 trajectory planes (tracking runs)
-  static constexpr int FLOATS = TRJ_OFF + 12 * WENV;
+  static constexpr int TRJ_OFF = TGT_OFF + 4 * WENV;            // 3 trajectory planes (tracking runs only)
   static constexpr int OBS = WENV * 13;
-  static constexpr int WARP_FLOATS = 2 * FLOATS + OBS;          // per warp
-  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (FLOATS % 4) == 0 &&
-                    (OBS % 4) == 0,
+  // Stage buffer and per-warp sizes (floats); smaller shared memory pays off,
+  // so the trajectory section exists only in tracking runs.
+  static __host__ __device__ constexpr int floats(bool track) { return TRJ_OFF + (track ? 12 * WENV : 0); }
+  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track) + OBS; }
+  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (OBS % 4) == 0,
                 "16-byte aligned sections");
 };
 constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
@@ -338,7 +339,8 @@ __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDes
   unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
   const bool load_act = a.n_steps > 0 && a.act_mode == 0;
   if (load_act) bytes += nvw * NT * 4;
-  if (sd.track) bytes += 3 * nvw * 16;
+  const bool trj = a.track != 0;   // the launch's layout has the trajectory section
+  if (trj) bytes += 3 * nvw * 16;
   mbar_expect_tx(bar, bytes);
   const unsigned b = smem_addr(buf);
 #pragma unroll
@@ -349,7 +351,7 @@ __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDes
               nvw * 4, bar);
   if (load_act) bulk_load(b + 4u * SG::ACT_OFF, a.actions + sd.act_off + w0 * NT, nvw * NT * 4, bar);
   bulk_load(b + 4u * SG::TGT_OFF, a.planes + tgt_plane(PER_ENV) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
-  if (sd.track) {
+  if (trj) {
 #pragma unroll
     for (int q = 0; q < TRAJ_PLANES; ++q)
       bulk_load(b + 4u * (SG::TRJ_OFF + 4 * q * WENV),
@@ -469,10 +471,11 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
         asm volatile("" : "+r"(pb), "+r"(ab));
         const PV Pk(pb);
         const ActSmem Ak{ab};
-        substep<float, NT, false>(x, c, Pk, Ak, sd.h, nullptr);
+        // Class-constant physics carries no current (zero by construction).
+        substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
       }
 #else
-      for (int k = 0; k < sd.K; ++k) substep<float, NT, false>(x, c, P, A, sd.h, nullptr);
+      for (int k = 0; k < sd.K; ++k) substep<float, NT, false, ActSmem, decltype(P), PER_ENV>(x, c, P, A, sd.h, nullptr);
 #endif
     }
     const bool emit = a.obs_every || t == n_out_steps - 1;
@@ -482,7 +485,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 #pragma unroll
       for (int j = 0; j < 13; ++j) o[j] = 0.0f;
       if (valid) {
-        if (sd.track) {
+        if (a.track) {
           // Tracking reference at the end of this step (counter k0 + t + 1);
           // its parameters were staged with the tile.
           const float4* tp = reinterpret_cast<const float4*>(buf + SG::TRJ_OFF) + lane;
@@ -511,7 +514,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   }
   if (valid && a.n_steps > 0) {
     store_state<NT>(st_base, sd.n4, i, x);
-    if (sd.track) {
+    if (a.track) {
       // Advance the env's step counter (w lane of its target plane entry).
       float* kp = reinterpret_cast<float*>(const_cast<float4*>(a.planes) + (int64_t)tgt_plane(PER_ENV) * a.n_slots + slot);
       kp[3] = tg.w + (float)a.n_steps;
@@ -543,11 +546,12 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
   using SG = Stage<NT>;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* const w_base = s_dyn + warp * SG::WARP_FLOATS;
+  const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0);
+  float* const w_base = s_dyn + warp * wfl;
   float* const buf0 = w_base;
-  float* const buf1 = w_base + SG::FLOATS;
-  float* const obs_w = w_base + 2 * SG::FLOATS;
-  float* const s_par = s_dyn + N_WARPS * SG::WARP_FLOATS;
+  float* const buf1 = w_base + fl;
+  float* const obs_w = w_base + 2 * fl;
+  float* const s_par = s_dyn + N_WARPS * wfl;
   __shared__ __align__(16) float s_act[SA_DIM];
   __shared__ __align__(16) float s_phys[PAR_DIM];
   __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
@@ -1018,8 +1022,8 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
 
 // Dynamic shared memory of mg_step_kernel<NT, PER_ENV>.
 template <int NT, bool PER_ENV>
-static size_t step_smem() {
-  return sizeof(float) * (N_WARPS * Stage<NT>::WARP_FLOATS + (PER_ENV ? PAR_DIM * STEP_BLK : 0));
+static size_t step_smem(bool track) {
+  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + (PER_ENV ? PAR_DIM * STEP_BLK : 0));
 }
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
@@ -1027,10 +1031,11 @@ static size_t step_smem() {
 template <int NT, bool PER_ENV>
 static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
   static bool attr_set = false;   // per instantiation, per process (one device)
-  const size_t smem = step_smem<NT, PER_ENV>();
+  const size_t smem = step_smem<NT, PER_ENV>(a.track != 0);
   if (!attr_set) {
+    // The largest layout (tracking) bounds every launch of this instantiation.
     cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)step_smem<NT, PER_ENV>(true));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1090,21 +1095,21 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
 }
 
 template <int NT, bool PER_ENV>
-static cudaError_t occupancy_t(int* blocks_per_sm) {
-  const size_t smem = step_smem<NT, PER_ENV>();
+static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)step_smem<NT, PER_ENV>(true));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PER_ENV>, STEP_BLK, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PER_ENV>, STEP_BLK,
+                                                       step_smem<NT, PER_ENV>(track));
 }
 
-cudaError_t step_kernel_occupancy(int nt, bool per_env, int* blocks_per_sm) {
+cudaError_t step_kernel_occupancy(int nt, bool per_env, bool track, int* blocks_per_sm) {
   if (per_env) {
-#define MG_L(N) return occupancy_t<N, true>(blocks_per_sm)
+#define MG_L(N) return occupancy_t<N, true>(track, blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   } else {
-#define MG_L(N) return occupancy_t<N, false>(blocks_per_sm)
+#define MG_L(N) return occupancy_t<N, false>(track, blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   }

@@ -21,7 +21,7 @@ cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
-cudaError_t step_kernel_occupancy(int nt, bool per_env, int* blocks_per_sm);
+cudaError_t step_kernel_occupancy(int nt, bool per_env, bool track, int* blocks_per_sm);
 }  // namespace mg
 
 namespace mg {
@@ -439,6 +439,7 @@ static StepArgs step_args(mg_sim* sim) {
   a.n_slots = sim->n_slots;
   a.status = sim->d_status;
   a.ckpt_every = sim->ckpt_every;
+  a.track = sim->cfg.task == 1;
   return a;
 }
 
@@ -448,7 +449,7 @@ static int grid_of(mg_sim* sim, const Group& g) {
   int b = sim->blocks_per_sm;
   if (b <= 0) {
     b = 1;
-    step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, &b);
+    step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, sim->cfg.task == 1, &b);
     if (b < 1) b = 1;
   }
   return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
@@ -836,7 +837,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   int occ = 1 << 30;
   for (const Group& g : sim->groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, &o) != cudaSuccess) o = 0;
+    if (step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;
