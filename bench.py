@@ -270,6 +270,41 @@ def tracking_bench(pk, stream, E=1 << 20, K=4, steps=200):
             "hbm_frac": v * bpe / (pk["hbm_gbs"] * 1e9)}
 
 
+def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
+    """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
+    T-step rollout (observation and reward every step) captured once as a CUDA
+    graph after the autotuner chose the persistent grid, then replayed."""
+    import torch
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(E, 5)
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=SEED)
+    acts = (torch.rand(T, sim.action_floats, device="cuda") * 2 - 1)
+    obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        threads, bps = B.mg_autotune(sim.handle, st)
+        g = B.mg_graph_capture(sim.handle, acts, T, obs, rew, st)
+        B.mg_graph_launch(g, st)
+        st.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            B.mg_graph_launch(g, st)
+        e1.record(st)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / reps
+        B.mg_graph_destroy(g)
+    B.mg_status(sim.handle, st)
+    sim.close()
+    return {"envs": E, "K": K, "steps_per_graph": T, "blocks_per_sm": bps, "graph_s": t,
+            "env_steps_per_s": E * T / t}
+
+
 def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
     import torch
     from paper_2503_09203_b300 import binding as B
@@ -503,6 +538,7 @@ def main():
         line["parity"] = parity_sample(classes, counts, K)
         line["sweep"] = sweep(pk, stream)
         line["tracking"] = tracking_bench(pk, stream)
+        line["hetero_graph"] = hetero_graph_bench(stream)
         line["adjoint"] = adjoint_bench(stream)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)
         line["serving"] = serving_bench(plain_substeps)

@@ -311,6 +311,9 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 // float4 planes, then REM float planes, 32 entries each), actions [32][NT],
 // target [32] float4. Each warp of a block owns two stage buffers and one
 // observation buffer [32][13] and runs its own copy pipeline.
+#ifndef MG_OBS_ALIAS
+#define MG_OBS_ALIAS 0
+#endif
 constexpr int WENV = 32;
 constexpr int N_WARPS = STEP_BLK / WENV;
 template <int NT>
@@ -323,7 +326,14 @@ struct Stage {
   // Stage buffer and per-warp sizes (floats); smaller shared memory pays off,
   // so the trajectory section exists only in tracking runs.
   static __host__ __device__ constexpr int floats(bool track) { return TRJ_OFF + (track ? 12 * WENV : 0); }
+#if MG_OBS_ALIAS
+  // The observation tile reuses the tile's own stage buffer once its inputs
+  // are in registers (rows 0..12 per env lie below the trajectory section).
+  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track); }
+  static_assert(OBS <= TRJ_OFF, "observation tile must fit below the trajectory section");
+#else
   static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track) + OBS; }
+#endif
   static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (OBS % 4) == 0,
                 "16-byte aligned sections");
 };
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
   float* const w_base = s_dyn + warp * wfl;
   float* const buf0 = w_base;
   float* const buf1 = w_base + fl;
-  float* const obs_w = w_base + 2 * fl;
+  float* const obs_sep = w_base + 2 * fl;   // separate observation tile (unless aliased)
   float* const s_par = s_dyn + N_WARPS * wfl;
   __shared__ __align__(16) float s_act[SA_DIM];
   __shared__ __align__(16) float s_phys[PAR_DIM];
@@ -601,6 +611,10 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
       const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
       nvw_next = warp_envs(sn, ln, warp);
       if (lane == 0 && nvw_next > 0) {
+#if MG_OBS_ALIAS
+        // The buffer may still be the source of the previous tile's observation store.
+        bulk_wait_read0();
+#endif
         fence_async_smem();
         issue_warp_loads<NT, PER_ENV>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
       }
@@ -627,7 +641,8 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
       }
       use[b]++;
     }
-    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, obs_w, s_par, n_emit);
+    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep,
+                           s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
     nvw_cur = nvw_next;
