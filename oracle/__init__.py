@@ -56,7 +56,8 @@ class or_env(C.Structure):
                 ("W", C.c_double), ("B", C.c_double), ("Ma", C.c_double * 6),
                 ("dl", C.c_double * 6), ("dq", C.c_double * 6), ("Vc", C.c_double * 3),
                 ("target", C.c_double * 3), ("traj_a", C.c_double * 3), ("traj_w", C.c_double * 3),
-                ("traj_phi", C.c_double * 3), ("traj_v", C.c_double * 3), ("k0", C.c_double)]
+                ("traj_phi", C.c_double * 3), ("traj_v", C.c_double * 3), ("k0", C.c_double),
+                ("Ig_off", C.c_double * 3)]
 
 
 class or_reset_cfg(C.Structure):
@@ -68,7 +69,9 @@ class or_reset_cfg(C.Structure):
                 ("cob_lo", C.c_double), ("cob_hi", C.c_double),
                 ("cur_lo", C.c_double), ("cur_hi", C.c_double),
                 ("target_half", C.c_double), ("pos_radius", C.c_double),
-                ("max_angle", C.c_double), ("track", C.c_int32), ("track_kind", C.c_int32)]
+                ("max_angle", C.c_double), ("track", C.c_int32), ("track_kind", C.c_int32),
+                ("payload", C.c_int32), ("pad1", C.c_int32), ("payload_lo", C.c_double),
+                ("payload_hi", C.c_double)]
 
 
 _lib = None
@@ -90,6 +93,8 @@ def lib():
         _lib.or_uniform.restype = C.c_double
         _lib.or_action.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int]
         _lib.or_action.restype = C.c_float
+        _lib.or_attach_payload.argtypes = [C.c_void_p, C.c_double, dp]
+        _lib.or_attach_payload.restype = None
         for name in ("or_rotation", "or_coriolis", "or_mass", "or_restoring", "or_actuator_wrench",
                      "or_acceleration", "or_philox4x64"):
             getattr(_lib, name).restype = C.c_int
@@ -150,7 +155,8 @@ def envs_to_arrays(envs) -> dict:
     out = {k: np.zeros((n,) + s) for k, s in
            (("mass", ()), ("Ig", (3,)), ("rg", (3,)), ("rb", (3,)), ("W", ()), ("B", ()),
             ("Ma", (6,)), ("dl", (6,)), ("dq", (6,)), ("Vc", (3,)), ("target", (3,)),
-            ("traj_a", (3,)), ("traj_w", (3,)), ("traj_phi", (3,)), ("traj_v", (3,)), ("k0", ()))}
+            ("traj_a", (3,)), ("traj_w", (3,)), ("traj_phi", (3,)), ("traj_v", (3,)), ("k0", ()),
+            ("Ig_off", (3,)))}
     out["cls"] = np.zeros(n, dtype=np.int32)
     for i in range(n):
         e = envs[i]
@@ -175,7 +181,8 @@ def make_envs(arrays: dict):
         if "k0" in arrays:
             e.k0 = float(arrays["k0"][i])
         for k, m in (("Ig", 3), ("rg", 3), ("rb", 3), ("Ma", 6), ("dl", 6), ("dq", 6), ("Vc", 3),
-                     ("target", 3), ("traj_a", 3), ("traj_w", 3), ("traj_phi", 3), ("traj_v", 3)):
+                     ("target", 3), ("traj_a", 3), ("traj_w", 3), ("traj_phi", 3), ("traj_v", 3),
+                     ("Ig_off", 3)):
             if k not in arrays:
                 continue
             dst = getattr(e, k)
@@ -208,6 +215,17 @@ def reset(classes, env_class, cfg: dict, seed: int, env_ids=None):
     if rc != 0:
         raise ValueError(f"or_reset failed: {rc}")
     return envs, state
+
+
+def attach_payload(envs, payload):
+    """Attach payloads in place: payload [E, 4] = (m_p, r_p) per env record."""
+    L = lib()
+    p = np.asarray(payload, dtype=np.float64).reshape(-1, 4)
+    assert len(p) == len(envs)
+    for i in range(len(envs)):
+        rp = np.ascontiguousarray(p[i, 1:4])
+        L.or_attach_payload(C.cast(C.byref(envs, i * C.sizeof(or_env)), C.c_void_p), float(p[i, 0]), _dp(rp))
+    return envs
 
 
 def rollout(classes, envs, state, actions, dt, K, obs=True, form=0, threads=0):

@@ -108,6 +108,7 @@ typedef struct {
   double target[3];   // hover target p* (tracking: the reference centre c), NED, m
   double traj_a[3], traj_w[3], traj_phi[3], traj_v[3];   // tracking reference (zeros: hover)
   double k0;          // step counter at the start of the rollout
+  double Ig_off[3];   // products of inertia about the CoG (Ixy, Ixz, Iyz): 0 without payload
 } or_env;
 
 // Reset configuration: domain-randomisation ranges (Table 2 train column
@@ -127,6 +128,9 @@ typedef struct {
   double max_angle;        // initial attitude error angle ~ U[0, max], rad
   int32_t track;           // 1: draw a tracking reference
   int32_t track_kind;      // 0 helix, 1 Lissajous
+  int32_t payload;         // 1: attach a point-mass payload (Sec. III-B payloads, Table 2)
+  int32_t pad1;
+  double payload_lo, payload_hi;   // payload mass / vehicle mass ~ U[lo, hi]
 } or_reset_cfg;
 
 }  // extern "C"
@@ -233,7 +237,7 @@ template <class T> static void rotation(const T q[4], T R[3][3]) {
 // added-mass and damping coefficients can carry tangents.
 // ---------------------------------------------------------------------------
 template <class T> struct EnvT {
-  double mass, Ig[3], rg[3], rb[3], W, B;
+  double mass, Ig[3], Ig_off[3], rg[3], rb[3], W, B;
   T Ma[6], dl[6], dq[6];
   double Vc[3], target[3];
   double ta[3], tw[3], tph[3], tv[3], k0;
@@ -244,6 +248,14 @@ template <class T> struct EnvT {
 // (all of a, w, phi, v zero for station keeping).
 template <class T> static void reference(const EnvT<T>& e, double t, double out[3]) {
   for (int i = 0; i < 3; ++i) out[i] = e.target[i] + e.ta[i] * std::sin(e.tw[i] * t + e.tph[i]) + e.tv[i] * t;
+}
+
+// Inertia tensor about the CoG: principal moments on the diagonal, products
+// of inertia (nonzero once a payload is attached) off it.
+template <class T> static double inertia_cog(const EnvT<T>& e, int i, int j) {
+  if (i == j) return e.Ig[i];
+  const int k = (i + j == 1) ? 0 : (i + j == 2 ? 1 : 2);   // (0,1)->Ixy, (0,2)->Ixz, (1,2)->Iyz
+  return e.Ig_off[k];
 }
 
 // Rigid-body inertia about the body origin with the CoG at r_g:
@@ -263,7 +275,7 @@ template <class T> static void mass_rb(const EnvT<T>& e, T M[6][6]) {
     for (int j = 0; j < 3; ++j) {
       T s2 = T(0.0);
       for (int k = 0; k < 3; ++k) s2 += S[i][k] * S[k][j];
-      M[3 + i][3 + j] = (i == j ? T(e.Ig[i]) : T(0.0)) - T(e.mass) * s2;
+      M[3 + i][3 + j] = T(inertia_cog(e, i, j)) - T(e.mass) * s2;
     }
 }
 
@@ -501,6 +513,7 @@ template <class T> static EnvT<T> env_of(const or_env& in) {
     e.ta[i] = in.traj_a[i]; e.tw[i] = in.traj_w[i]; e.tph[i] = in.traj_phi[i]; e.tv[i] = in.traj_v[i];
   }
   e.k0 = in.k0;
+  for (int i = 0; i < 3; ++i) e.Ig_off[i] = in.Ig_off[i];
   return e;
 }
 
@@ -527,6 +540,34 @@ float or_action(uint64_t seed, uint64_t env, uint64_t step, int thr) {
   philox4x64_10(ctr, key, out);
   double k = (double)(out[thr % 4] >> 40);
   return (float)(k * (1.0 / 8388608.0) - 1.0);
+}
+
+// Attach a point mass m_p at r_p (body frame) to an env whose CoG is at r_g
+// (Sec. III-B mission payloads). The payload's volume is neglected. The
+// combined body has mass m' = m + m_p, CoG r_g' = (m r_g + m_p r_p) / m' and,
+// by the parallel-axis theorem, inertia about r_g'
+// I' = I + m (|d|^2 1 - d d^T) + m_p (|d_p|^2 1 - d_p d_p^T),
+// d = r_g - r_g', d_p = r_p - r_g'; the payload's weight m_p g adds to W.
+void or_attach_payload(or_env* env, double mp, const double* rp) {
+  or_env& e = *env;
+  const double m = e.mass, mt = m + mp;
+  double rg[3], d[3], dp[3];
+  for (int i = 0; i < 3; ++i) rg[i] = (m * e.rg[i] + mp * rp[i]) / mt;
+  for (int i = 0; i < 3; ++i) { d[i] = e.rg[i] - rg[i]; dp[i] = rp[i] - rg[i]; }
+  const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double dp2 = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+  // Current inertia about the CoG as a full tensor (products from Ig_off).
+  const double I0[3][3] = {{e.Ig[0], e.Ig_off[0], e.Ig_off[1]},
+                           {e.Ig_off[0], e.Ig[1], e.Ig_off[2]},
+                           {e.Ig_off[1], e.Ig_off[2], e.Ig[2]}};
+  double I[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      I[i][j] = I0[i][j] + m * ((i == j ? d2 : 0.0) - d[i] * d[j]) + mp * ((i == j ? dp2 : 0.0) - dp[i] * dp[j]);
+  e.mass = mt;
+  for (int i = 0; i < 3; ++i) { e.Ig[i] = I[i][i]; e.rg[i] = rg[i]; }
+  e.Ig_off[0] = I[0][1]; e.Ig_off[1] = I[0][2]; e.Ig_off[2] = I[1][2];
+  e.W += mp * kGravity;
 }
 
 // Reset: domain-randomised parameters (Sec. III-C, Table 2) and initial state.
@@ -562,6 +603,15 @@ int or_reset(const or_class* classes, int n_classes, const int32_t* env_class, i
     for (int i = 0; i < 3; ++i) e.rb[i] = c.rb[i] * fb;
     e.W = e.mass * kGravity;
     e.B = c.buoy_ratio * c.mass * kGravity;   // volume is not randomised
+    if (cfg->payload) {
+      // Payload (stream 1, draws 23-26): mass fraction of the vehicle's mass
+      // U[lo, hi] (Table 2), position x, y ~ U[-0.1, 0.1] m, z ~ U[0.05, 0.15] m.
+      const double mp = e.mass * (cfg->payload_lo + (cfg->payload_hi - cfg->payload_lo) *
+                                                         draw_u(seed, kStreamDR, id, 23));
+      const double rp[3] = {-0.1 + 0.2 * draw_u(seed, kStreamDR, id, 24), -0.1 + 0.2 * draw_u(seed, kStreamDR, id, 25),
+                            0.05 + 0.1 * draw_u(seed, kStreamDR, id, 26)};
+      or_attach_payload(&e, mp, rp);
+    }
     if (cfg->current_enabled) {
       const double speed = cfg->cur_lo + (cfg->cur_hi - cfg->cur_lo) * draw_u(seed, kStreamDR, id, 20);
       const double psi = 2.0 * kPi * draw_u(seed, kStreamDR, id, 21);

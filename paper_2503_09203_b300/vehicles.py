@@ -106,3 +106,7 @@ HOVER_DR = dict(DR_TRAIN, init_mode=1)
 TRACK_HELIX = dict(HOVER, track=1, track_kind=0)
 TRACK_LISSAJOUS = dict(HOVER, track=1, track_kind=1)
 TRACK_HELIX_DR = dict(HOVER_DR, track=1, track_kind=0)
+# Payload disturbance (Sec. III-B; Table 2 payload mass, train range [0, 0.3]
+# of the vehicle mass); the oracle reads `payload`, the library its config.
+PAYLOAD = dict(HOVER, payload=1, payload_lo=0.0, payload_hi=0.3)
+PAYLOAD_DR = dict(HOVER_DR, payload=1, payload_lo=0.0, payload_hi=0.3)
