@@ -270,6 +270,30 @@ def tracking_bench(pk, stream, E=1 << 20, K=4, steps=200):
             "hbm_frac": v * bpe / (pk["hbm_gbs"] * 1e9)}
 
 
+def payload_bench(pk, stream, E=1 << 20, K=4, steps=200):
+    """Payload disturbance (point mass per env, full 6x6 inverse) with per-env
+    DR and current, against the same batch without the payload."""
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(E, 5)
+    bpe, _ = algorithmic(classes, counts, K)
+    out = {"envs": E, "K": K}
+    for name, cfg, pay, planes in (("per_env_dr", vehicles.HOVER_DR, False, 9),
+                                   ("payload_dr", vehicles.PAYLOAD_DR, True, 15)):
+        sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(cfg), payload=pay)
+        sim.reset(seed=SEED)
+        acts = action_pool(sim, 4, 9)
+        t = time_steps(sim, acts, steps, 10, stream)
+        sim.status()
+        sim.close()
+        v = E * steps / t
+        b = bpe + 16 * planes + 4   # parameter planes read per step; full target float4
+        out[name] = {"env_steps_per_s": v, "us_per_step": t / steps * 1e6, "bytes_per_env_step": b,
+                     "hbm_frac": v * b / (pk["hbm_gbs"] * 1e9)}
+    return out
+
+
 def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
     """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
     T-step rollout (observation and reward every step) captured once as a CUDA
@@ -538,6 +562,7 @@ def main():
         line["parity"] = parity_sample(classes, counts, K)
         line["sweep"] = sweep(pk, stream)
         line["tracking"] = tracking_bench(pk, stream)
+        line["payload"] = payload_bench(pk, stream)
         line["hetero_graph"] = hetero_graph_bench(stream)
         line["adjoint"] = adjoint_bench(stream)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)

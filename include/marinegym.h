@@ -69,13 +69,14 @@ enum {
  * coefficients and up to 8 thrusters. FP64 on the host; the library derives
  * the allocation matrix B = [d_i ; r_i x d_i], the rotor factor
  * alpha = 1 - exp(-h/T) and the inverse inertia in FP64 and stores them FP32.
- * Only r_g = 0 and diagonal added mass are supported by the kernels. */
+ * The class's own CoG is the body origin (r_g = 0) and its added mass is
+ * diagonal; an off-origin CoG arises from a payload (see mg_set_payload). */
 typedef struct {
   int32_t n_thr;            /* 1..8 (the workloads use 4, 6, 8) */
   int32_t pad0;
   double mass;              /* kg */
   double Ig[3];             /* principal inertia about the CoG, kg m^2 */
-  double rg[3];             /* CoG in body frame (must be 0) */
+  double rg[3];             /* CoG in body frame (must be 0; payloads move it) */
   double rb[3];             /* CoB in body frame, m */
   double buoy_ratio;        /* B / (mass g) at nominal volume (1 = neutral) */
   double Ma[6];             /* added mass diag (kg, kg m^2) */
@@ -109,6 +110,7 @@ typedef struct {
   double max_angle;         /* attitude error angle ~ U[0, max_angle], rad */
   int32_t track_kind;       /* tracking runs: 0 helix, 1 Lissajous reference */
   int32_t pad0;
+  double payload_lo, payload_hi;   /* payload runs: m_p / m ~ U[lo, hi] (Table 2: [0, 0.3]) */
 } mg_reset_cfg;
 
 typedef struct {
@@ -126,7 +128,8 @@ typedef struct {
                                    MG_ERR_OOM above this many device bytes */
   int32_t task;                 /* 0: station keeping (fixed target p*);
                                    1: trajectory tracking (time-varying p*(t)) */
-  int32_t pad0;
+  int32_t payload;              /* 1: every env carries a point-mass payload
+                                   (needs per_env_params, record_steps = 0) */
 } mg_config;
 
 /* Placement of class c inside the device buffers. */
@@ -195,6 +198,25 @@ int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* ob
  * the rest 0). Both synchronise the device. */
 int mg_get_task(const mg_sim* sim, double* host, size_t bytes);
 int mg_set_task(mg_sim* sim, const double* host, size_t bytes);
+
+/* Payload disturbance (payload = 1; Sec. III-B mission payloads, Table 2
+ * payload mass). A point mass m_p rigidly attached at r_p (body frame, m)
+ * moves the CoG to r_g = m_p r_p / (m + m_p) and couples translation and
+ * rotation: the step then uses the full 6x6 inverse of M_RB + M_A (Eq. 1,
+ * M_RB about the body origin with the S(m r_g) blocks), C_RB with r_g and the
+ * weight (m + m_p) g acting at r_g. The inverse is computed in FP64 (Cholesky)
+ * at reset and whenever the parameters change. Reset draws (stream 1, draws
+ * 23..26): m_p = U[payload_lo, payload_hi] x the env's vehicle mass, r_p with
+ * x, y ~ U[-0.1, 0.1] and z ~ U[0.05, 0.15] (below the vehicle's CoG); drawn
+ * whether or not DR is enabled. The payload's own volume is neglected.
+ * mg_get_payload / mg_set_payload read and write [n_envs][4] doubles
+ * (m_p, r_p x, y, z); mg_get_params / mg_set_params keep describing the
+ * vehicle alone (mg_set_params recomputes the combined body). Both synchronise
+ * the device. Errors: INVALID_ARG (not a payload run, buffer too small,
+ * non-finite values, m_p < 0, an inertia that is not positive definite).
+ * Payload runs reject mg_set_hydro, mg_rollout_fp64 and gradients. */
+int mg_get_payload(const mg_sim* sim, double* host, size_t bytes);
+int mg_set_payload(mg_sim* sim, const double* host, size_t bytes);
 
 /* Observation of the current state (no step): obs_dev [n_slots][13]. */
 int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream);

@@ -62,14 +62,15 @@ class mg_reset_cfg(C.Structure):
                 ("cob_lo", C.c_double), ("cob_hi", C.c_double),
                 ("cur_lo", C.c_double), ("cur_hi", C.c_double),
                 ("target_half", C.c_double), ("pos_radius", C.c_double),
-                ("max_angle", C.c_double), ("track_kind", C.c_int32), ("pad0", C.c_int32)]
+                ("max_angle", C.c_double), ("track_kind", C.c_int32), ("pad0", C.c_int32),
+                ("payload_lo", C.c_double), ("payload_hi", C.c_double)]
 
 
 class mg_config(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("class_counts", C.POINTER(C.c_int32)),
                 ("dt", C.c_double), ("K", C.c_int32), ("per_env_params", C.c_int32),
                 ("reset", mg_reset_cfg), ("record_steps", C.c_int32), ("ckpt_every", C.c_int32),
-                ("mem_budget", C.c_size_t), ("task", C.c_int32), ("pad0", C.c_int32)]
+                ("mem_budget", C.c_size_t), ("task", C.c_int32), ("payload", C.c_int32)]
 
 
 class mg_class_layout(C.Structure):
@@ -126,6 +127,8 @@ _SIGS = {
     "mg_get_params": [_VP, _VP, C.c_size_t],
     "mg_get_task": [_VP, _VP, C.c_size_t],
     "mg_set_task": [_VP, _VP, C.c_size_t],
+    "mg_get_payload": [_VP, _VP, C.c_size_t],
+    "mg_set_payload": [_VP, _VP, C.c_size_t],
     "mg_set_params": [_VP, _VP, C.c_size_t],
     "mg_status": [_VP, _VP],
     "mg_autotune": [_VP, _VP, C.POINTER(_I32), C.POINTER(_I32)],
@@ -234,14 +237,14 @@ TASK_HOVER, TASK_TRACK = 0, 1
 
 def mg_create(classes: Sequence[dict], counts: Sequence[int], dt: float, K: int, per_env_params: bool = True,
               reset: Optional[dict] = None, record_steps: int = 0, ckpt_every: int = 0, mem_budget: int = 0,
-              task: int = TASK_HOVER):
+              task: int = TASK_HOVER, payload: bool = False):
     L = lib()
     arr = (mg_class_desc * len(classes))(*[pack_class(c) for c in classes])
     cnt = (C.c_int32 * len(counts))(*[int(x) for x in counts])
     cfg = mg_config(n_classes=len(classes), class_counts=cnt, dt=float(dt), K=int(K),
                     per_env_params=int(bool(per_env_params)), reset=pack_reset(reset or {}),
                     record_steps=int(record_steps), ckpt_every=int(ckpt_every), mem_budget=int(mem_budget),
-                    task=int(task))
+                    task=int(task), payload=int(bool(payload)))
     h = _VP()
     _check(L.mg_create(C.byref(cfg), arr, C.byref(h)), None)
     return h.value
@@ -341,6 +344,20 @@ def mg_set_task(sim, task: np.ndarray):
     return _check(lib().mg_set_task(sim, t.ctypes.data, t.nbytes), sim)
 
 
+PAYLOAD_DIM = 4   # m_p, r_p (x, y, z)
+
+
+def mg_get_payload(sim, n_envs: int) -> np.ndarray:
+    out = np.zeros((n_envs, PAYLOAD_DIM), np.float64)
+    _check(lib().mg_get_payload(sim, out.ctypes.data, out.nbytes), sim)
+    return out
+
+
+def mg_set_payload(sim, payload: np.ndarray):
+    p = np.ascontiguousarray(payload, dtype=np.float64)
+    return _check(lib().mg_set_payload(sim, p.ctypes.data, p.nbytes), sim)
+
+
 def mg_status(sim, stream=None):
     return _check(lib().mg_status(sim, _stream(stream)), sim)
 
@@ -407,13 +424,13 @@ class Sim:
     """
 
     def __init__(self, classes, counts, dt=0.01, K=1, per_env_params=True, reset=None, record_steps=0,
-                 ckpt_every=0, mem_budget=0, task=TASK_HOVER, device="cuda"):
+                 ckpt_every=0, mem_budget=0, task=TASK_HOVER, payload=False, device="cuda"):
         import torch
         self.classes = list(classes)
         self.counts = [int(c) for c in counts]
         self.dt, self.K = float(dt), int(K)
         self.handle = mg_create(self.classes, self.counts, dt, K, per_env_params, reset, record_steps,
-                                ckpt_every, mem_budget, task)
+                                ckpt_every, mem_budget, task, payload)
         self.layout = mg_get_layout(self.handle)
         self.n_envs = self.layout.n_envs
         self.n_slots = self.layout.n_slots
@@ -503,6 +520,12 @@ class Sim:
 
     def set_task(self, t):
         mg_set_task(self.handle, t)
+
+    def get_payload(self):
+        return mg_get_payload(self.handle, self.n_envs)
+
+    def set_payload(self, p):
+        mg_set_payload(self.handle, p)
 
     def status(self, stream=None):
         return mg_status(self.handle, stream)

@@ -78,9 +78,14 @@ struct Act {
 // Per-env physical parameters (device block of 36 floats in this order).
 template <typename S>
 struct Phys {
+  static constexpr bool kFull = false;   // diagonal inertia, CoG at the origin
   S minv[6], A[6], dl[6], dq[6];
   S m, Ig[3], W, B, rb[3], Vc[3];
 };
+
+// Index of entry (i, j), i <= j, of a symmetric 6x6 matrix stored as its upper
+// triangle row by row (21 entries).
+MG_HD constexpr int sym6(int i, int j) { return i * 6 - (i * (i - 1)) / 2 + (j - i); }
 
 template <typename S, int NT>
 struct St {
@@ -179,10 +184,18 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     vc[j] = CURRENT ? R[0][j] * S(P.Vc[0]) + R[1][j] * S(P.Vc[1]) + R[2][j] * S(P.Vc[2]) : S(0.0f);
     vr[j] = CURRENT ? v[j] - vc[j] : v[j];
   }
-  // a4
+  // a4. With a payload (PhysT::kFull) the body origin is not the CoG: with the
+  // first moment s = m' r_g and the inertia I_o about the origin,
+  // C_RB(nu) nu = [m' w x v + w x (w x s) ; w x (I_o w) + s x (w x v)].
   S wxv[3], Iw[3], wxIw[3];
   cross3(w, v, wxv);
-  Iw[0] = S(P.Ig[0]) * w[0]; Iw[1] = S(P.Ig[1]) * w[1]; Iw[2] = S(P.Ig[2]) * w[2];
+  if constexpr (PhysT::kFull) {
+    Iw[0] = S(P.Io[0]) * w[0] + S(P.Io[1]) * w[1] + S(P.Io[2]) * w[2];
+    Iw[1] = S(P.Io[1]) * w[0] + S(P.Io[3]) * w[1] + S(P.Io[4]) * w[2];
+    Iw[2] = S(P.Io[2]) * w[0] + S(P.Io[4]) * w[1] + S(P.Io[5]) * w[2];
+  } else {
+    Iw[0] = S(P.Ig[0]) * w[0]; Iw[1] = S(P.Ig[1]) * w[1]; Iw[2] = S(P.Ig[2]) * w[2];
+  }
   cross3(w, Iw, wxIw);
   // a5
   S a1[3], a2[3], wxa1[3], vrxa1[3], wxa2[3], wxvc[3];
@@ -208,6 +221,20 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   const S Pw = S(P.W), Pb = S(P.B);
   const S WmB = Pw - Pb;
   S Brb[3] = {Pb * S(P.rb[0]), Pb * S(P.rb[1]), Pb * S(P.rb[2])}, mb[3];
+  S extra_lin[3] = {S(0.0f), S(0.0f), S(0.0f)}, extra_ang[3] = {S(0.0f), S(0.0f), S(0.0f)};
+  if constexpr (PhysT::kFull) {
+    // Weight acts at r_g: the moment arm is B r_b - W r_g = B r_b - (W/m') s.
+    const S sv[3] = {S(P.s[0]), S(P.s[1]), S(P.s[2])};
+    const S wpm = Pw / S(P.m);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Brb[j] = Brb[j] - wpm * sv[j];
+    S wxs[3], wxwxs[3], sxwxv[3];
+    cross3(w, sv, wxs);
+    cross3(w, wxs, wxwxs);
+    cross3(sv, wxv, sxwxv);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { extra_lin[j] = wxwxs[j]; extra_ang[j] = sxwxv[j]; }
+  }
   cross3(Brb, e, mb);
   // a8
   S rhs[6];
@@ -216,9 +243,27 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     rhs[j] = CURRENT ? tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j]
                      : tau[j] - S(P.m) * wxv[j] - wxa1[j] - dmp[j] + WmB * e[j];
     rhs[3 + j] = tau[3 + j] - wxIw[j] - vrxa1[j] - wxa2[j] - dmp[3 + j] - mb[j];
+    if constexpr (PhysT::kFull) {
+      rhs[j] = rhs[j] - extra_lin[j];
+      rhs[3 + j] = rhs[3 + j] - extra_ang[j];
+    }
   }
+  if constexpr (PhysT::kFull) {
+    // nu_dot = M^-1 rhs with the full symmetric inverse.
+    S nd[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (S(P.minv[j]) * rhs[j]);
+    for (int i = 0; i < 6; ++i) {
+      S acc = S(0.0f);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc = acc + S(P.Mi[i <= j ? sym6(i, j) : sym6(j, i)]) * rhs[j];
+      nd[i] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (S(P.minv[j]) * rhs[j]);
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     x.p[i] = x.p[i] + h * (R[i][0] * x.nu[0] + R[i][1] * x.nu[1] + R[i][2] * x.nu[2]);

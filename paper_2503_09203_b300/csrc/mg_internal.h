@@ -60,11 +60,20 @@ enum { PAR_MINV = 0, PAR_A = 6, PAR_DL = 12, PAR_DQ = 18, PAR_M = 24, PAR_IG = 2
 // env's step counter. Tracking runs add 3 planes right after the target:
 // (a_x, a_y, a_z, w_x), (w_y, w_z, phi_x, phi_y), (phi_z, v_x, v_y, v_z) of the
 // reference p*(t) = c + a o sin(w t + phi) + v t, t = k dt.
-enum { PAR_PLANES = 9, TGT_PLANE = 9, N_PLANES = 10, TRAJ_PLANES = 3 };
+enum { PAR_PLANES = 9, TGT_PLANE = 9, N_PLANES = 10, TRAJ_PLANES = 3, PAY_PLANES = 9 };
 // Index of the target plane (per-env runs keep the physics in planes 0..8).
 __host__ __device__ inline int tgt_plane(int per_env) { return per_env ? TGT_PLANE : 0; }
+// Payload runs (per-env only) add 9 planes after the target and trajectory
+// planes: the combined body's inverse inertia (21 floats, upper triangle row
+// by row), its inertia about the body origin I_o (6: xx xy xz yy yz zz), its
+// first moment s = m_p r_p (3), total mass m' (1), total weight W' (1), and the
+// payload itself: m_p (1), r_p (3).
+enum { PAY_MINV = 0, PAY_IO = 21, PAY_S = 27, PAY_M = 30, PAY_W = 31, PAY_MP = 32, PAY_RP = 33, PAY_DIM = 36 };
+__host__ __device__ inline int pay_plane(int track) { return TGT_PLANE + 1 + (track ? TRAJ_PLANES : 0); }
 // Planes of a run.
-inline int n_planes_of(int per_env, int track) { return (per_env ? PAR_PLANES : 0) + 1 + (track ? TRAJ_PLANES : 0); }
+inline int n_planes_of(int per_env, int track, int payload = 0) {
+  return (per_env ? PAR_PLANES : 0) + 1 + (track ? TRAJ_PLANES : 0) + (payload ? PAY_PLANES : 0);
+}
 
 // A launch covers the segments [seg_lo, seg_hi) of one thruster count, whose
 // tiles are tile_lo .. tile_lo + n_tiles - 1.
@@ -80,7 +89,7 @@ struct StepArgs {
   int32_t n_steps;
   int32_t act_mode;           // 0: load actions; 1: Philox actions (serving)
   const float4* planes;       // [N_PLANES][n_slots] (per-env) or target plane only
-  int32_t per_env;            // 1: physical parameters from planes 0..8
+  int32_t per_env;            // 0: class constants; 1: physical parameters from planes 0..8; 2: as 1 plus the payload planes
   int32_t obs_every;          // 1: obs/reward every step; 0: after the last step
   int64_t n_slots;
   float* obs;                 // [*][n_slots][13] or null
@@ -90,6 +99,8 @@ struct StepArgs {
   int32_t ckpt_every;
   int32_t track;              // 1: every segment of the launch is a tracking run
   uint32_t* status;           // bit 0: non-finite state
+  int32_t pay_plane;          // payload runs: first payload plane
+  int32_t pad1;
 };
 
 struct AdjArgs {
@@ -136,6 +147,8 @@ struct ResetArgs {
   double mass_lo, mass_hi, added_lo, added_hi, damp_lo, damp_hi, cob_lo, cob_hi, cur_lo, cur_hi;
   double target_half, pos_radius, max_angle;
   int32_t track, track_kind;
+  int32_t payload, pad1;
+  double payload_lo, payload_hi;
 };
 
 // Arguments of the FP64 finite-difference rollout.

@@ -18,8 +18,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mg_internal.h"
 #include "mg_device.cuh"
+#include "mg_payload.h"
 
 namespace mg {
 
@@ -235,6 +238,7 @@ struct SScl {
 };
 template <int STRIDE>
 struct PhysSmem {
+  static constexpr bool kFull = false;
   SArr<PAR_MINV, STRIDE> minv;
   SArr<PAR_A, STRIDE> A;
   SArr<PAR_DL, STRIDE> dl;
@@ -248,6 +252,35 @@ struct PhysSmem {
   __device__ __forceinline__ explicit PhysSmem(unsigned b)
       : minv{b}, A{b}, dl{b}, dq{b}, m{b}, Ig{b}, W{b}, B{b}, rb{b}, Vc{b} {}
 };
+
+// Payload runs: per-env columns staged from physics planes 1-5, 7, 8 (columns
+// 0-27) and payload planes 0-7 (columns 28-59). The diagonal inverse, the
+// vehicle's own mass and inertia and its weight are not needed: the combined
+// body's full inverse, inertia about the origin, first moment, mass and
+// weight replace them.
+enum { PF_A = 2, PF_DL = 8, PF_DQ = 14, PF_B = 21, PF_RB = 22, PF_VC = 25, PF_PAY = 28, PF_DIM = 60 };
+constexpr int PF_STD_PLANES = 7;                       // physics planes staged
+constexpr int PF_PAY_PLANES = 8;                       // payload planes staged
+__device__ __forceinline__ int pf_std_plane(int k) { return k < 5 ? k + 1 : k + 2; }   // 1..5, 7, 8
+template <int STRIDE>
+struct PhysSmemFull {
+  static constexpr bool kFull = true;
+  SArr<PF_A, STRIDE> A;
+  SArr<PF_DL, STRIDE> dl;
+  SArr<PF_DQ, STRIDE> dq;
+  SScl<PF_B, STRIDE> B;
+  SArr<PF_RB, STRIDE> rb;
+  SArr<PF_VC, STRIDE> Vc;
+  SArr<PF_PAY + PAY_MINV, STRIDE> Mi;
+  SArr<PF_PAY + PAY_IO, STRIDE> Io;
+  SArr<PF_PAY + PAY_S, STRIDE> s;
+  SScl<PF_PAY + PAY_M, STRIDE> m;
+  SScl<PF_PAY + PAY_W, STRIDE> W;
+  __device__ __forceinline__ explicit PhysSmemFull(unsigned b)
+      : A{b}, dl{b}, dq{b}, B{b}, rb{b}, Vc{b}, Mi{b}, Io{b}, s{b}, m{b}, W{b} {}
+};
+static_assert(PF_STD_PLANES * 4 == PF_PAY && PF_PAY + PF_PAY_PLANES * 4 == PF_DIM, "payload column map");
+static_assert(PAY_W < PF_PAY_PLANES * 4, "staged payload planes hold the step's fields");
 
 constexpr int STEP_BLK = 128;
 #ifndef MG_STEP_MIN_BLOCKS
@@ -341,9 +374,10 @@ constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
 
 // Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
 // (a multiple of 4, > 0) envs start at local env index w0 of the segment.
-template <int NT, bool PER_ENV>
+template <int NT, int PM>
 __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDesc& sd, int64_t w0, unsigned nvw,
                                                  float* buf, unsigned bar) {
+  constexpr bool PER_ENV = PM >= 1;
   using SG = Stage<NT>;
   const float* st = a.state + sd.st_off;
   unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
@@ -375,10 +409,11 @@ __device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0,
   return n <= 0 ? 0u : (unsigned)min((int64_t)WENV, n);
 }
 
-template <int NT, bool PER_ENV>
+template <int NT, int PM>
 __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
                                           const float* s_phys, const float* buf, float* obs_w, float* s_par,
                                           int& n_emit) {
+  constexpr bool PER_ENV = PM >= 1;
   using SG = Stage<NT>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t local0 = (int64_t)(tile - sd.tile_begin) * STEP_BLK;
@@ -391,7 +426,13 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   float* st_base = a.state + sd.st_off;
   const ActSmem A{smem_addr(s_act)};
 
-  constexpr bool STAGE_PAR = PER_ENV && !MG_PHYS_REGS;
+#if MG_PHYS_REGS
+  static_assert(PM < 2, "payload runs stage their parameters in shared memory");
+#endif
+  // Per-env parameters: plain per-env runs prefetch their 9 planes into
+  // registers here (their loads overlap the stage reads below); payload runs
+  // copy 15 planes straight to shared memory afterwards.
+  constexpr bool STAGE_PAR = PM == 1 && !MG_PHYS_REGS;
   float4 pv[STAGE_PAR ? PAR_PLANES : 1];
   if (STAGE_PAR && valid) {
 #pragma unroll
@@ -433,6 +474,17 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
     }
   }
+  if (PM == 2 && valid) {
+#pragma unroll
+    for (int k = 0; k < PF_STD_PLANES + PF_PAY_PLANES; ++k) {
+      const int plane = k < PF_STD_PLANES ? pf_std_plane(k) : a.pay_plane + (k - PF_STD_PLANES);
+      const float4 v = __ldg(&a.planes[(int64_t)plane * a.n_slots + slot]);
+      s_par[(4 * k + 0) * STEP_BLK + tid] = v.x;
+      s_par[(4 * k + 1) * STEP_BLK + tid] = v.y;
+      s_par[(4 * k + 2) * STEP_BLK + tid] = v.z;
+      s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
+    }
+  }
 #if MG_PHYS_REGS
   // Parameters held in registers for the whole tile.
   Phys<float> P;
@@ -443,8 +495,9 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   }
 #else
   // Each thread reads only its own parameter column: no barrier needed.
-  using PV = PhysSmem<PER_ENV ? STEP_BLK : 1>;
-  const PV P(PER_ENV ? smem_addr(s_par) + 4u * tid : smem_addr(s_phys));
+  using PV = std::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
+  const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : smem_addr(s_phys);
+  const PV P(p_base);
 #endif
   const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
   for (int t = 0; t < n_out_steps; ++t) {
@@ -477,7 +530,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       // Shared-memory bases made opaque once per substep: loads may be
       // scheduled freely inside a substep but not hoisted out of the loop.
       for (int k = 0; k < sd.K; ++k) {
-        unsigned pb = P.minv.base, ab = A.base;
+        unsigned pb = p_base, ab = A.base;
         asm volatile("" : "+r"(pb), "+r"(ab));
         const PV Pk(pb);
         const ActSmem Ak{ab};
@@ -551,7 +604,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 // a per-warp bulk store. Warps never wait on one another except when the
 // class constants change. Every wait is bounded (2 s); a warp that gives up
 // sets bit 1 of the status word and leaves.
-template <int NT, bool PER_ENV>
+template <int NT, int PM>
 __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(const __grid_constant__ StepArgs a) {
   using SG = Stage<NT>;
   extern __shared__ __align__(16) float s_dyn[];
@@ -593,7 +646,7 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
     const int64_t local0 = (int64_t)(tile0 - s0.tile_begin) * STEP_BLK;
     nvw_cur = warp_envs(s0, local0, warp);
     if (lane == 0 && nvw_cur > 0)
-      issue_warp_loads<NT, PER_ENV>(a, s0, local0 + warp * WENV, nvw_cur, buf0, full0);
+      issue_warp_loads<NT, PM>(a, s0, local0 + warp * WENV, nvw_cur, buf0, full0);
   }
   int prev_seg = -1, n_emit = 0;
   unsigned use[2] = {0u, 0u};   // completed uses of each stage barrier
@@ -616,7 +669,7 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
         bulk_wait_read0();
 #endif
         fence_async_smem();
-        issue_warp_loads<NT, PER_ENV>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
+        issue_warp_loads<NT, PM>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
       }
     }
     const SegDesc& sd = segs[si];
@@ -641,7 +694,7 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
       }
       use[b]++;
     }
-    step_tile<NT, PER_ENV>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep,
+    step_tile<NT, PM>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep,
                            s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
@@ -780,6 +833,21 @@ __global__ void mg_reset_kernel(const __grid_constant__ ResetArgs a) {
     a.planes[(tp + 1) * a.n_slots + slot] = make_float4((float)ta[0], (float)ta[1], (float)ta[2], (float)tw[0]);
     a.planes[(tp + 2) * a.n_slots + slot] = make_float4((float)tw[1], (float)tw[2], (float)tph[0], (float)tph[1]);
     a.planes[(tp + 3) * a.n_slots + slot] = make_float4((float)tph[2], (float)tv[0], (float)tv[1], (float)tv[2]);
+  }
+  if (a.payload) {
+    // Payload (stream 1, draws 23-26): mass m_p = U[lo, hi] x (randomised)
+    // vehicle mass, attachment point r_p with x, y ~ U[-0.1, 0.1] m and
+    // z ~ U[0.05, 0.15] m (below the CoG). Drawn whether or not DR is on.
+    const double mp = m * (a.payload_lo + (a.payload_hi - a.payload_lo) * uniform53(seed, STREAM_DR, id, 23));
+    const double rp[3] = {-0.1 + 0.2 * uniform53(seed, STREAM_DR, id, 24), -0.1 + 0.2 * uniform53(seed, STREAM_DR, id, 25),
+                          0.05 + 0.1 * uniform53(seed, STREAM_DR, id, 26)};
+    float v[PAY_DIM];
+    if (!payload_block(m, Ig, Ma, W, mp, rp, v)) {
+      for (int j = 0; j < PAY_DIM; ++j) v[j] = __int_as_float(0x7fc00000);   // reported as non-finite by the step
+    }
+    const int pp = pay_plane(a.track);
+    for (int kk = 0; kk < PAY_PLANES; ++kk)
+      a.planes[(pp + kk) * a.n_slots + slot] = make_float4(v[4 * kk], v[4 * kk + 1], v[4 * kk + 2], v[4 * kk + 3]);
   }
 }
 
@@ -1035,22 +1103,23 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
     default: return cudaErrorInvalidValue; \
   }
 
-// Dynamic shared memory of mg_step_kernel<NT, PER_ENV>.
-template <int NT, bool PER_ENV>
+// Dynamic shared memory of mg_step_kernel<NT, PM>.
+template <int NT, int PM>
 static size_t step_smem(bool track) {
-  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + (PER_ENV ? PAR_DIM * STEP_BLK : 0));
+  const int cols = PM == 2 ? PF_DIM : (PM == 1 ? PAR_DIM : 0);
+  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
 }
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
-template <int NT, bool PER_ENV>
+template <int NT, int PM>
 static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
   static bool attr_set = false;   // per instantiation, per process (one device)
-  const size_t smem = step_smem<NT, PER_ENV>(a.track != 0);
+  const size_t smem = step_smem<NT, PM>(a.track != 0);
   if (!attr_set) {
     // The largest layout (tracking) bounds every launch of this instantiation.
-    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem<NT, PER_ENV>(true));
+    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem<NT, PM>(true));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1064,17 +1133,21 @@ static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cu
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PER_ENV>, a);
+  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM>, a);
 }
 
 cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
-  if (a.per_env) {
-#define MG_L(N) return launch_step_t<N, true>(a, grid, dependent, st)
+  if (a.per_env == 2) {
+#define MG_L(N) return launch_step_t<N, 2>(a, grid, dependent, st)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  } else if (a.per_env == 1) {
+#define MG_L(N) return launch_step_t<N, 1>(a, grid, dependent, st)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   } else {
-#define MG_L(N) return launch_step_t<N, false>(a, grid, dependent, st)
+#define MG_L(N) return launch_step_t<N, 0>(a, grid, dependent, st)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   }
@@ -1109,22 +1182,26 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int NT, bool PER_ENV>
+template <int NT, int PM>
 static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PER_ENV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem<NT, PER_ENV>(true));
+  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem<NT, PM>(true));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PER_ENV>, STEP_BLK,
-                                                       step_smem<NT, PER_ENV>(track));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PM>, STEP_BLK,
+                                                       step_smem<NT, PM>(track));
 }
 
-cudaError_t step_kernel_occupancy(int nt, bool per_env, bool track, int* blocks_per_sm) {
-  if (per_env) {
-#define MG_L(N) return occupancy_t<N, true>(track, blocks_per_sm)
+cudaError_t step_kernel_occupancy(int nt, int pm, bool track, int* blocks_per_sm) {
+  if (pm == 2) {
+#define MG_L(N) return occupancy_t<N, 2>(track, blocks_per_sm)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  } else if (pm == 1) {
+#define MG_L(N) return occupancy_t<N, 1>(track, blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   } else {
-#define MG_L(N) return occupancy_t<N, false>(track, blocks_per_sm)
+#define MG_L(N) return occupancy_t<N, 0>(track, blocks_per_sm)
     MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   }

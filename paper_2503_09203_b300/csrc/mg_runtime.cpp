@@ -14,6 +14,7 @@
 
 #include "../../include/marinegym.h"
 #include "mg_internal.h"
+#include "mg_payload.h"
 
 namespace mg {
 cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st);
@@ -21,7 +22,7 @@ cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
-cudaError_t step_kernel_occupancy(int nt, bool per_env, bool track, int* blocks_per_sm);
+cudaError_t step_kernel_occupancy(int nt, int pm, bool track, int* blocks_per_sm);
 }  // namespace mg
 
 namespace mg {
@@ -234,6 +235,9 @@ static ResetArgs reset_args(mg_sim* sim, const mg_reset_cfg& r, uint64_t seed) {
   a.target_half = r.target_half; a.pos_radius = r.pos_radius; a.max_angle = r.max_angle;
   a.track = sim->cfg.task == 1;
   a.track_kind = r.track_kind;
+  a.payload = sim->cfg.payload;
+  a.payload_lo = r.payload_lo;
+  a.payload_hi = r.payload_hi;
   return a;
 }
 
@@ -276,6 +280,22 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
     return bail(MG_ERR_INVALID_ARG);
   if (cfg->task < 0 || cfg->task > 1 || cfg->reset.track_kind < 0 || cfg->reset.track_kind > 1)
     return bail(MG_ERR_INVALID_ARG);
+  if (cfg->payload < 0 || cfg->payload > 1) return bail(MG_ERR_INVALID_ARG);
+  if (cfg->payload) {
+    if (!cfg->per_env_params) {
+      sim->err = "payload runs need per_env_params";
+      return bail(MG_ERR_INVALID_ARG);
+    }
+    if (cfg->record_steps > 0) {
+      sim->err = "payload runs have no adjoint (record_steps must be 0)";
+      return bail(MG_ERR_INVALID_ARG);
+    }
+    const double lo = cfg->reset.payload_lo, hi = cfg->reset.payload_hi;
+    if (!(std::isfinite(lo) && std::isfinite(hi) && lo >= 0.0 && hi >= lo)) {
+      sim->err = "payload range must satisfy 0 <= payload_lo <= payload_hi";
+      return bail(MG_ERR_INVALID_ARG);
+    }
+  }
   sim->n_classes = cfg->n_classes;
   sim->classes.assign(classes, classes + cfg->n_classes);
   sim->counts.assign(cfg->class_counts, cfg->class_counts + cfg->n_classes);
@@ -311,7 +331,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
   cudaDeviceGetAttribute(&sim->num_sms, cudaDevAttrMultiProcessorCount, dev);
 
-  sim->n_planes = n_planes_of(cfg->per_env_params, cfg->task == 1);
+  sim->n_planes = n_planes_of(cfg->per_env_params, cfg->task == 1, cfg->payload);
   int rc;
   if ((rc = dev_alloc(sim, (void**)&sim->d_state, sizeof(float) * st)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_planes, sizeof(float4) * sim->n_planes * slot)) != MG_OK) return bail(rc);
@@ -427,6 +447,10 @@ int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, 
   return MG_OK;
 }
 
+// Parameter source of the step kernel: 0 class constants, 1 per-env planes,
+// 2 per-env planes plus the payload planes.
+static int param_mode(const mg_sim* sim) { return sim->cfg.payload ? 2 : (sim->cfg.per_env_params ? 1 : 0); }
+
 static StepArgs step_args(mg_sim* sim) {
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -435,11 +459,12 @@ static StepArgs step_args(mg_sim* sim) {
   a.state = sim->d_state;
   a.act_stride = sim->act_floats;
   a.planes = sim->d_planes;
-  a.per_env = sim->cfg.per_env_params;
+  a.per_env = param_mode(sim);
   a.n_slots = sim->n_slots;
   a.status = sim->d_status;
   a.ckpt_every = sim->ckpt_every;
   a.track = sim->cfg.task == 1;
+  a.pay_plane = pay_plane(a.track);
   return a;
 }
 
@@ -449,7 +474,7 @@ static int grid_of(mg_sim* sim, const Group& g) {
   int b = sim->blocks_per_sm;
   if (b <= 0) {
     b = 1;
-    step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, sim->cfg.task == 1, &b);
+    step_kernel_occupancy(g.nt, param_mode(sim), sim->cfg.task == 1, &b);
     if (b < 1) b = 1;
   }
   return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
@@ -582,6 +607,7 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
 int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const float* dq_dev, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "set_hydro needs per_env_params");
+  if (sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "set_hydro: not available for payload runs (use mg_set_params)");
   CK(launch_set_hydro(sim->d_planes, sim->n_slots, A_dev, dl_dev, dq_dev, (cudaStream_t)stream));
   return MG_OK;
 }
@@ -590,6 +616,7 @@ int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, cons
                     const double* ddq, double eps, double* reward_dev, double* state_dev, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64 needs per_env_params");
+  if (sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: not available for payload runs");
   if (!actions_dev || !reward_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: bad arguments");
   Fp64Args a;
   std::memset(&a, 0, sizeof(a));
@@ -699,6 +726,18 @@ int mg_get_params(const mg_sim* csim, double* host, size_t bytes) {
   return MG_OK;
 }
 
+// Payload planes of one slot from the vehicle parameters and the payload
+// (m_p, r_p), computed in FP64 on the host.
+static int write_payload(mg_sim* sim, std::vector<float4>& pl, int64_t slot, double m, const double Ig[3],
+                         const double Ma[6], double W, double mp, const double rp[3]) {
+  float v[PAY_DIM];
+  if (!payload_block(m, Ig, Ma, W, mp, rp, v)) return MG_ERR_INVALID_ARG;
+  const int pp = pay_plane(sim->cfg.task == 1);
+  for (int k = 0; k < PAY_PLANES; ++k)
+    pl[(size_t)(pp + k) * sim->n_slots + slot] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  return MG_OK;
+}
+
 int mg_set_params(mg_sim* sim, const double* host, size_t bytes) {
   if (!sim || !host) return MG_ERR_INVALID_ARG;
   if (bytes < sizeof(double) * MG_ENV_PARAM_DIM * (size_t)sim->n_envs)
@@ -735,6 +774,66 @@ int mg_set_params(mg_sim* sim, const double* host, size_t bytes) {
       v[39] = pl[(size_t)TGT_PLANE * sim->n_slots + slot].w;
       for (int k = 0; k < PAR_PLANES + 1; ++k)
         pl[(size_t)k * sim->n_slots + slot] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      if (sim->cfg.payload) {
+        // The combined body follows the new vehicle parameters; the payload stays.
+        const float4 q = pl[(size_t)(pay_plane(sim->cfg.task == 1) + PAY_MP / 4) * sim->n_slots + slot];
+        const double Ma[6] = {s[9], s[10], s[11], s[12], s[13], s[14]};
+        const double rp[3] = {q.y, q.z, q.w};
+        if (write_payload(sim, pl, slot, m, Ig, Ma, s[7], q.x, rp) != MG_OK)
+          return fail(sim, MG_ERR_INVALID_ARG, "set_params: env %lld inertia not positive definite", (long long)(L.env_off + i));
+      }
+    }
+  }
+  CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+int mg_get_payload(const mg_sim* csim, double* host, size_t bytes) {
+  mg_sim* sim = const_cast<mg_sim*>(csim);
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (!sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "get_payload: not a payload run");
+  if (bytes < sizeof(double) * 4 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "get_payload: buffer too small");
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  const int qp = pay_plane(sim->cfg.task == 1) + PAY_MP / 4;
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const float4 q = pl[(size_t)qp * sim->n_slots + L.slot_off + i];
+      double* o = host + (L.env_off + i) * 4;
+      o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    }
+  }
+  return MG_OK;
+}
+
+int mg_set_payload(mg_sim* sim, const double* host, size_t bytes) {
+  if (!sim || !host) return MG_ERR_INVALID_ARG;
+  if (!sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "set_payload: not a payload run");
+  if (bytes < sizeof(double) * 4 * (size_t)sim->n_envs) return fail(sim, MG_ERR_INVALID_ARG, "set_payload: buffer too small");
+  std::vector<float4> pl((size_t)sim->n_planes * sim->n_slots);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl.data(), sim->d_planes, sizeof(float4) * pl.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < sim->n_classes; ++c) {
+    const ClassLay& L = sim->lay[c];
+    for (int64_t i = 0; i < L.n_envs; ++i) {
+      const int64_t env = L.env_off + i, slot = L.slot_off + i;
+      const double* q = host + env * 4;
+      for (int j = 0; j < 4; ++j)
+        if (!std::isfinite(q[j])) return fail(sim, MG_ERR_INVALID_ARG, "set_payload: env %lld not finite", (long long)env);
+      if (q[0] < 0.0) return fail(sim, MG_ERR_INVALID_ARG, "set_payload: env %lld payload mass < 0", (long long)env);
+      float v[PAR_DIM];
+      for (int k = 0; k < PAR_PLANES; ++k) {
+        const float4 x = pl[(size_t)k * sim->n_slots + slot];
+        v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+      }
+      const double Ig[3] = {v[PAR_IG], v[PAR_IG + 1], v[PAR_IG + 2]};
+      double Ma[6];
+      for (int j = 0; j < 6; ++j) Ma[j] = v[PAR_A + j];
+      const double rp[3] = {q[1], q[2], q[3]};
+      if (write_payload(sim, pl, slot, v[PAR_M], Ig, Ma, v[PAR_W], q[0], rp) != MG_OK)
+        return fail(sim, MG_ERR_INVALID_ARG, "set_payload: env %lld inertia not positive definite", (long long)env);
     }
   }
   CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
@@ -837,7 +936,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   int occ = 1 << 30;
   for (const Group& g : sim->groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, sim->cfg.per_env_params != 0, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
+    if (step_kernel_occupancy(g.nt, param_mode(sim), sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;

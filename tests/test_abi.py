@@ -77,10 +77,12 @@ def test_flop_count_is_host_only_and_sane(lib):
     assert e.value.code == B.MG_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env"])
+@pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env", "payload_per_env",
+                                 "payload_record", "payload_range"])
 def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
     classes = [vehicles.heavy8()]
     counts, dt, K, per_env, reset = [8], 0.01, 1, True, dict(vehicles.NO_DR)
+    record, payload = 0, False
     if bad == "dt":
         dt = -1.0
     elif bad == "K":
@@ -93,9 +95,17 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
         counts = [-1]
     elif bad == "per_env":
         per_env, reset = False, dict(vehicles.DR_TRAIN)
+    elif bad == "payload_per_env":
+        per_env, payload = False, True
+    elif bad == "payload_record":
+        record, payload = 10, True
+    elif bad == "payload_range":
+        payload, reset = True, dict(vehicles.PAYLOAD, payload_lo=0.3, payload_hi=0.1)
     with pytest.raises(B.MGError) as e:
-        B.mg_create(classes, counts, dt, K, per_env, reset)
+        B.mg_create(classes, counts, dt, K, per_env, reset, record_steps=record, payload=payload)
     assert e.value.code == B.MG_ERR_INVALID_ARG
+    if bad.startswith("payload"):
+        assert "payload" in str(e.value)
 
 
 def test_error_strings(lib):
