@@ -47,7 +47,14 @@ class or_class(C.Structure):
                 ("buoy_ratio", C.c_double), ("Ma", C.c_double * 6), ("dl", C.c_double * 6),
                 ("dq", C.c_double * 6), ("thr_pos", (C.c_double * 3) * 8),
                 ("thr_dir", (C.c_double * 3) * 8), ("k_f", C.c_double * 8),
-                ("T_rotor", C.c_double * 8), ("deadzone", C.c_double * 8)]
+                ("T_rotor", C.c_double * 8), ("deadzone", C.c_double * 8),
+                ("act_kind", C.c_int32 * 8), ("act_link", C.c_int32 * 8),
+                ("act_axis", (C.c_double * 3) * 8), ("act_chord", (C.c_double * 3) * 8),
+                ("act_range", C.c_double * 8), ("fin_area", C.c_double * 8), ("fin_cl", C.c_double * 8),
+                ("fin_cd0", C.c_double * 8), ("fin_cda", C.c_double * 8), ("rho", C.c_double)]
+
+# Actuator kinds (Sec. III-D): propeller, servo, fin, propeller tilted by a servo.
+KIND_PROP, KIND_SERVO, KIND_FIN, KIND_TILT = 0, 1, 2, 3
 
 
 class or_env(C.Structure):
@@ -84,7 +91,7 @@ def lib():
         dp = C.POINTER(C.c_double)
         fp = C.POINTER(C.c_float)
         _lib.or_rollout.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
-                                    fp, dp, dp, dp, C.c_int, C.c_int]
+                                    fp, dp, dp, dp, C.c_int, C.c_int, C.c_int]
         _lib.or_rollout_jvp.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
                                         fp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
         _lib.or_reset.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_int64, C.c_void_p,
@@ -131,6 +138,14 @@ def pack_class(d: dict) -> or_class:
             c.thr_pos[i][k] = float(d["thr_pos"][i][k]); c.thr_dir[i][k] = float(d["thr_dir"][i][k])
         c.k_f[i] = float(d["k_f"][i]); c.T_rotor[i] = float(d["T_rotor"][i])
         c.deadzone[i] = float(d["deadzone"][i])
+        c.act_kind[i] = int(d.get("act_kind", [KIND_PROP] * n)[i])
+        c.act_link[i] = int(d.get("act_link", [0] * n)[i])
+        for k in range(3):
+            c.act_axis[i][k] = float(d.get("act_axis", [(0.0, 0.0, 0.0)] * n)[i][k])
+            c.act_chord[i][k] = float(d.get("act_chord", [(0.0, 0.0, 0.0)] * n)[i][k])
+        for name in ("act_range", "fin_area", "fin_cl", "fin_cd0", "fin_cda"):
+            getattr(c, name)[i] = float(d.get(name, [0.0] * n)[i])
+    c.rho = float(d.get("rho", 0.0))
     return c
 
 
@@ -228,7 +243,7 @@ def attach_payload(envs, payload):
     return envs
 
 
-def rollout(classes, envs, state, actions, dt, K, obs=True, form=0, threads=0):
+def rollout(classes, envs, state, actions, dt, K, obs=True, form=0, threads=0, integ=0):
     """Run actions[T,E,8] (float32) from state[E,21] (FP64, updated in place).
 
     Returns (state, obs[T,E,13] or None, reward[T,E] or None)."""
@@ -241,7 +256,7 @@ def rollout(classes, envs, state, actions, dt, K, obs=True, form=0, threads=0):
     r = np.zeros((T, E)) if obs else None
     cls = pack_classes(classes)
     rc = L.or_rollout(C.cast(cls, C.c_void_p), C.cast(envs, C.c_void_p), E, float(dt), int(K), T,
-                      _fp(actions), _dp(state), _dp(o), _dp(r), int(form), int(threads))
+                      _fp(actions), _dp(state), _dp(o), _dp(r), int(form), int(threads), int(integ))
     if rc != 0:
         raise ValueError(f"or_rollout failed: {rc}")
     return state, o, r
@@ -319,12 +334,14 @@ def restoring(env_arrays: dict, q):
     return g
 
 
-def actuator_wrench(cls: dict, n):
+def actuator_wrench(cls: dict, n, nur=None):
+    """Wrench of actuator states n; nur = body velocity relative to the water (fins)."""
     c = pack_class(cls)
     nn = np.zeros(8)
     nn[:len(n)] = n
     tau = np.zeros(6)
-    lib().or_actuator_wrench(C.byref(c), _dp(nn), _dp(tau))
+    v = None if nur is None else np.ascontiguousarray(nur, dtype=np.float64)
+    lib().or_actuator_wrench(C.byref(c), _dp(nn), _dp(v), _dp(tau))
     return tau
 
 

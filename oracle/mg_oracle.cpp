@@ -63,12 +63,20 @@ inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
 inline Dual fabs(Dual a) { return a.v < 0 ? -a : (a.v > 0 ? a : Dual(0.0, 0.0)); }
+inline Dual sin(Dual a) { return Dual(std::sin(a.v), std::cos(a.v) * a.d); }
+inline Dual cos(Dual a) { return Dual(std::cos(a.v), -std::sin(a.v) * a.d); }
+inline Dual atan2(Dual y, Dual x) {
+  return Dual(std::atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v));
+}
 inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
 inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
 inline double val(double a) { return a; }
 inline double val(Dual a) { return a.v; }
 using std::sqrt;
 using std::fabs;
+using std::sin;
+using std::cos;
+using std::atan2;
 
 // ---------------------------------------------------------------------------
 // C-ABI records (host, FP64).
@@ -79,7 +87,12 @@ extern "C" {
 
 // A vehicle class (Sec. III-D): rigid body, hydrodynamic coefficients as
 // positive magnitudes (added mass diag, linear and quadratic damping diag),
-// and up to 8 thrusters given by position and unit direction in the body frame.
+// and up to 8 actuator channels. Every channel has a first-order state n in
+// [-1, 1] driven by its command (rotor speed, or servo / fin angle n * range).
+// Kinds (Sec. III-D actuator types): 0 propeller with fixed unit direction;
+// 1 servo (no force; tilts the propellers linked to it); 2 fin (control
+// surface: lift and drag from the local flow); 3 propeller whose direction is
+// turned about act_axis by the angle of the servo act_link.
 typedef struct {
   int32_t n_thr;
   int32_t pad0;
@@ -96,6 +109,16 @@ typedef struct {
   double k_f[8];        // N at |n| = 1
   double T_rotor[8];    // s; 0 means zero-order rotor
   double deadzone[8];   // |n| below which thrust is 0
+  int32_t act_kind[8];  // 0 propeller, 1 servo, 2 fin, 3 tilted propeller
+  int32_t act_link[8];  // kind 3: channel index of its servo
+  double act_axis[8][3];   // kind 2: span axis; kind 3: tilt axis (unit, body frame)
+  double act_chord[8][3];  // kind 2: chord direction at zero deflection (unit, normal to the span axis)
+  double act_range[8];     // kinds 1, 2: angle at |n| = 1, rad
+  double fin_area[8];      // kind 2: planform area S, m^2
+  double fin_cl[8];        // kind 2: lift slope C_L_alpha, 1/rad
+  double fin_cd0[8];       // kind 2: drag at zero angle of attack
+  double fin_cda[8];       // kind 2: drag growth C_D_alpha
+  double rho;              // water density, kg/m^3 (fins)
 } or_class;
 
 // Per-environment physical parameters after domain randomisation.
@@ -362,13 +385,74 @@ template <class T> static void restoring(const EnvT<T>& e, const T R[3][3], T gR
 
 // Actuator wrench: each thruster force f_i d_i applied at its frame r_i
 // contributes [f_i d_i ; r_i x f_i d_i] (Sec. III-D, last paragraph).
-template <class T> static void actuator_wrench(const or_class& c, const T n[8], T tau[6]) {
+// Rotation by angle th about the unit axis a (Rodrigues):
+// Rot = cos th 1 + sin th S(a) + (1 - cos th) a a^T.
+template <class T> static void axis_rotation(const double a[3], T th, T Rm[3][3]) {
+  const T ct = cos(th), st = sin(th);
+  T S[3][3];
+  const T aa[3] = {T(a[0]), T(a[1]), T(a[2])};
+  skew(aa, S);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Rm[i][j] = (i == j ? ct : T(0.0)) + st * S[i][j] + (T(1.0) - ct) * aa[i] * aa[j];
+}
+
+// Actuator wrench at the body origin (Sec. III-D: every actuator force acts
+// at its own frame). Propellers: thrust k n|n| (0 inside the dead zone) along
+// their direction, turned by the linked servo's angle for kind 3. Fins: the
+// fin moves through the water with u = v_r + w x r; in the plane normal to
+// the span axis a the angle of attack alpha is the angle of u from the
+// deflected chord c (towards the fin normal a x c); lift
+// 1/2 rho S U^2 C_L(alpha) acts along -(a x u)/U and drag
+// 1/2 rho S U^2 C_D(alpha) along -u/U, with C_L = C_L_alpha sin(alpha) cos(alpha),
+// C_D = C_D0 + C_D_alpha sin^2(alpha) (reading R18).
+template <class T>
+static void actuator_wrench(const or_class& c, const T n[8], const T nur[6], T tau[6]) {
   for (int k = 0; k < 6; ++k) tau[k] = T(0.0);
   for (int i = 0; i < c.n_thr; ++i) {
-    T f = T(0.0);
-    if (!(fabs(n[i]) < T(c.deadzone[i]))) f = T(c.k_f[i]) * n[i] * fabs(n[i]);
-    T F[3], r[3], m[3];
-    for (int k = 0; k < 3; ++k) { F[k] = f * T(c.thr_dir[i][k]); r[k] = T(c.thr_pos[i][k]); }
+    const int kind = c.act_kind[i];
+    T F[3] = {T(0.0), T(0.0), T(0.0)}, r[3], m[3];
+    for (int k = 0; k < 3; ++k) r[k] = T(c.thr_pos[i][k]);
+    if (kind == 0 || kind == 3) {
+      T f = T(0.0);
+      if (!(fabs(n[i]) < T(c.deadzone[i]))) f = T(c.k_f[i]) * n[i] * fabs(n[i]);
+      T d[3] = {T(c.thr_dir[i][0]), T(c.thr_dir[i][1]), T(c.thr_dir[i][2])};
+      if (kind == 3) {
+        const int j = c.act_link[i];
+        T Rm[3][3];
+        axis_rotation(c.act_axis[i], n[j] * T(c.act_range[j]), Rm);
+        T d0[3] = {d[0], d[1], d[2]};
+        for (int a = 0; a < 3; ++a) d[a] = Rm[a][0] * d0[0] + Rm[a][1] * d0[1] + Rm[a][2] * d0[2];
+      }
+      for (int k = 0; k < 3; ++k) F[k] = f * d[k];
+    } else if (kind == 2) {
+      const T w[3] = {nur[3], nur[4], nur[5]};
+      T wxr[3], u[3];
+      cross(w, r, wxr);
+      for (int k = 0; k < 3; ++k) u[k] = nur[k] + wxr[k];
+      const T ax[3] = {T(c.act_axis[i][0]), T(c.act_axis[i][1]), T(c.act_axis[i][2])};
+      const T ua = u[0] * ax[0] + u[1] * ax[1] + u[2] * ax[2];
+      T up[3];
+      for (int k = 0; k < 3; ++k) up[k] = u[k] - ua * ax[k];
+      const T U2 = up[0] * up[0] + up[1] * up[1] + up[2] * up[2];
+      if (val(U2) > 0.0) {
+        const T U = sqrt(U2);
+        T Rm[3][3];
+        axis_rotation(c.act_axis[i], n[i] * T(c.act_range[i]), Rm);
+        T ch[3], nrm[3];
+        for (int a = 0; a < 3; ++a)
+          ch[a] = Rm[a][0] * T(c.act_chord[i][0]) + Rm[a][1] * T(c.act_chord[i][1]) + Rm[a][2] * T(c.act_chord[i][2]);
+        cross(ax, ch, nrm);
+        const T alpha = atan2(up[0] * nrm[0] + up[1] * nrm[1] + up[2] * nrm[2],
+                              up[0] * ch[0] + up[1] * ch[1] + up[2] * ch[2]);
+        const T sa = sin(alpha), ca = cos(alpha);
+        const T CL = T(c.fin_cl[i]) * sa * ca;
+        const T CD = T(c.fin_cd0[i]) + T(c.fin_cda[i]) * sa * sa;
+        const T qS = T(0.5 * c.rho * c.fin_area[i]) * U2;
+        T axu[3];
+        cross(ax, up, axu);
+        for (int k = 0; k < 3; ++k) F[k] = -qS * CL * axu[k] / U - qS * CD * up[k] / U;
+      }
+    }
     cross(r, F, m);
     for (int k = 0; k < 3; ++k) { tau[k] += F[k]; tau[3 + k] += m[k]; }
   }
@@ -440,19 +524,34 @@ static void acceleration(const EnvT<T>& e, const T q[4], const T nu[6], const T 
 // State layout [21]: p[3] NED, q[4] (w,x,y,z), nu[6] = (u,v,w,p,q,r), n[8].
 enum { SP = 0, SQ = 3, SNU = 7, SN = 13, SDIM = 21 };
 
-// One substep of the discrete map (reading R6).
+// Relative velocity nu_r = nu - [R^T V_c ; 0] (Sec. III-B current).
+template <class T> static void relative_velocity(const EnvT<T>& e, const T q[4], const T nu[6], T nur[6]) {
+  T R[3][3];
+  rotation(q, R);
+  for (int i = 0; i < 3; ++i)
+    nur[i] = nu[i] - (R[0][i] * T(e.Vc[0]) + R[1][i] * T(e.Vc[1]) + R[2][i] * T(e.Vc[2]));
+  for (int i = 3; i < 6; ++i) nur[i] = nu[i];
+}
+
+// q (x) (0, w): the quaternion kinematics q_dot = 1/2 q (x) (0, w).
+template <class T> static void quat_rate(const T q[4], const T nu[6], T qd[4]) {
+  const T w = q[0], x = q[1], y = q[2], z = q[3];
+  const T P = nu[3], Q = nu[4], Rr = nu[5];
+  qd[0] = -x * P - y * Q - z * Rr;
+  qd[1] = w * P + y * Rr - z * Q;
+  qd[2] = w * Q - x * Rr + z * P;
+  qd[3] = w * Rr + x * Q - y * P;
+}
+
+// One substep of the discrete map (reading R6: semi-implicit Euler).
 template <class T>
-static void substep(const or_class& c, const EnvT<T>& e, const double alpha[8], double h, const T cmd[8],
-                    int form, T s[SDIM]) {
-  // Rotor dynamics: n <- n + alpha (c - n).
-  T n[8];
-  for (int i = 0; i < 8; ++i) n[i] = s[SN + i];
-  for (int i = 0; i < c.n_thr; ++i) n[i] = n[i] + T(alpha[i]) * (cmd[i] - n[i]);
-  T tau[6];
-  actuator_wrench(c, n, tau);
+static void substep_euler(const or_class& c, const EnvT<T>& e, double h, const T n[8], int form, T s[SDIM]) {
   T q[4] = {s[SQ], s[SQ + 1], s[SQ + 2], s[SQ + 3]};
   T nu[6];
   for (int i = 0; i < 6; ++i) nu[i] = s[SNU + i];
+  T nur[6], tau[6];
+  relative_velocity(e, q, nu, nur);
+  actuator_wrench(c, n, nur, tau);
   T nu_dot[6];
   acceleration(e, q, nu, tau, form, nu_dot);
   for (int i = 0; i < 6; ++i) nu[i] = nu[i] + T(h) * nu_dot[i];
@@ -461,14 +560,64 @@ static void substep(const or_class& c, const EnvT<T>& e, const double alpha[8], 
   for (int i = 0; i < 3; ++i)
     s[SP + i] = s[SP + i] + T(h) * (R[i][0] * nu[0] + R[i][1] * nu[1] + R[i][2] * nu[2]);
   // q <- normalise(q + h/2 q (x) (0, w+)).
-  const T w = q[0], x = q[1], y = q[2], z = q[3];
-  const T P = nu[3], Q = nu[4], Rr = nu[5];
-  T qd[4] = {-x * P - y * Q - z * Rr, w * P + y * Rr - z * Q, w * Q - x * Rr + z * P, w * Rr + x * Q - y * P};
-  T qn[4];
+  T qd[4], qn[4];
+  quat_rate(q, nu, qd);
   for (int i = 0; i < 4; ++i) qn[i] = q[i] + T(0.5 * h) * qd[i];
   T norm = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
   for (int i = 0; i < 4; ++i) s[SQ + i] = qn[i] / norm;
   for (int i = 0; i < 6; ++i) s[SNU + i] = nu[i];
+}
+
+// Time derivative of y = (p, q, nu) with the actuator states held (reading
+// R19): the attitude of a stage is that of its normalised quaternion.
+template <class T>
+static void derivative(const or_class& c, const EnvT<T>& e, const T n[8], int form, const T y[13], T dy[13]) {
+  const T* q = y + 3;
+  const T* nu = y + 7;
+  const T qq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const T qh[4] = {q[0] / qq, q[1] / qq, q[2] / qq, q[3] / qq};
+  T R[3][3];
+  rotation(qh, R);
+  for (int i = 0; i < 3; ++i) dy[i] = R[i][0] * nu[0] + R[i][1] * nu[1] + R[i][2] * nu[2];
+  T qd[4];
+  quat_rate(q, nu, qd);
+  for (int i = 0; i < 4; ++i) dy[3 + i] = T(0.5) * qd[i];
+  T nur[6], tau[6];
+  relative_velocity(e, qh, nu, nur);
+  actuator_wrench(c, n, nur, tau);
+  acceleration(e, qh, nu, tau, form, dy + 7);
+}
+
+// One substep of the classical fourth-order Runge-Kutta variant (reading R19):
+// RK4 on (p, q, nu) over h with the actuator states n held, then q normalised.
+template <class T>
+static void substep_rk4(const or_class& c, const EnvT<T>& e, double h, const T n[8], int form, T s[SDIM]) {
+  T y0[13], y[13], k1[13], k2[13], k3[13], k4[13];
+  for (int i = 0; i < 13; ++i) y0[i] = s[i];
+  derivative(c, e, n, form, y0, k1);
+  for (int i = 0; i < 13; ++i) y[i] = y0[i] + T(0.5 * h) * k1[i];
+  derivative(c, e, n, form, y, k2);
+  for (int i = 0; i < 13; ++i) y[i] = y0[i] + T(0.5 * h) * k2[i];
+  derivative(c, e, n, form, y, k3);
+  for (int i = 0; i < 13; ++i) y[i] = y0[i] + T(h) * k3[i];
+  derivative(c, e, n, form, y, k4);
+  for (int i = 0; i < 13; ++i) s[i] = y0[i] + T(h / 6.0) * (k1[i] + T(2.0) * k2[i] + T(2.0) * k3[i] + k4[i]);
+  T norm = sqrt(s[SQ] * s[SQ] + s[SQ + 1] * s[SQ + 1] + s[SQ + 2] * s[SQ + 2] + s[SQ + 3] * s[SQ + 3]);
+  for (int i = 0; i < 4; ++i) s[SQ + i] = s[SQ + i] / norm;
+}
+
+// One substep: actuator states first (n <- n + alpha (c - n), rotor or servo
+// lag), then the rigid body with integrator `integ` (0 Euler, 1 RK4).
+template <class T>
+static void substep(const or_class& c, const EnvT<T>& e, const double alpha[8], double h, const T cmd[8],
+                    int form, T s[SDIM], int integ = 0) {
+  T n[8];
+  for (int i = 0; i < 8; ++i) n[i] = s[SN + i];
+  for (int i = 0; i < c.n_thr; ++i) n[i] = n[i] + T(alpha[i]) * (cmd[i] - n[i]);
+  if (integ == 1)
+    substep_rk4(c, e, h, n, form, s);
+  else
+    substep_euler(c, e, h, n, form, s);
   for (int i = 0; i < 8; ++i) s[SN + i] = n[i];
 }
 
@@ -675,7 +824,8 @@ int or_reset(const or_class* classes, int n_classes, const int32_t* env_class, i
 // class's thruster count are ignored). state: [n_envs][21] in/out.
 // obs: [n_steps][n_envs][13] or NULL; reward: [n_steps][n_envs] or NULL.
 int or_rollout(const or_class* classes, const or_env* envs, int64_t n_envs, double dt, int K, int n_steps,
-               const float* actions, double* state, double* obs, double* reward, int form, int n_threads) {
+               const float* actions, double* state, double* obs, double* reward, int form, int n_threads,
+               int integ) {
   if (K < 1 || dt <= 0.0) return -1;
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(static)
@@ -691,7 +841,7 @@ int or_rollout(const or_class* classes, const or_env* envs, int64_t n_envs, doub
       double cmd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       const float* a = actions + ((int64_t)t * n_envs + ei) * 8;
       for (int i = 0; i < c.n_thr; ++i) cmd[i] = clamp1((double)a[i]);
-      for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, form, s);
+      for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, form, s, integ);
       if (obs || reward) {
         double o[13], r;
         observe(c, e, (e.k0 + t + 1) * dt, s, cmd, o, &r);
@@ -792,9 +942,10 @@ int or_restoring(const or_env* env, const double* q, double* g6) {
   return 0;
 }
 
-// Actuator wrench for rotor speeds n[8].
-int or_actuator_wrench(const or_class* c, const double* n, double* tau6) {
-  actuator_wrench(*c, n, tau6);
+// Actuator wrench for actuator states n[8] and relative velocity nu_r (NULL: at rest).
+int or_actuator_wrench(const or_class* c, const double* n, const double* nur6, double* tau6) {
+  const double zero[6] = {0, 0, 0, 0, 0, 0};
+  actuator_wrench(*c, n, nur6 ? nur6 : zero, tau6);
   return 0;
 }
 

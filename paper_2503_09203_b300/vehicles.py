@@ -83,6 +83,63 @@ def scaled(name: str, mass: float, n_thr: int) -> dict:
     )
 
 
+# Actuator kinds (Sec. III-D): propeller, servo, fin (control surface),
+# propeller tilted by a servo.
+KIND_PROP, KIND_SERVO, KIND_FIN, KIND_TILT = 0, 1, 2, 3
+RHO_WATER = 1025.0
+
+
+def lauv() -> dict:
+    """Rudder-propeller class (Sec. III-D, LAUV/iAUV type): one stern propeller
+    and a cruciform tail of four independently driven fins (channels: propeller,
+    top and bottom rudders with span axis z, port and starboard elevators with
+    span axis y; chord along x). 18 kg torpedo body; underactuated."""
+    fins_pos = [(-0.8, 0.0, -0.1), (-0.8, 0.0, 0.1), (-0.8, -0.1, 0.0), (-0.8, 0.1, 0.0)]
+    fins_axis = [(0.0, 0.0, 1.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0), (0.0, 1.0, 0.0)]
+    return dict(
+        name="lauv5", n_thr=5, mass=18.0, Ig=(0.08, 1.6, 1.6), rg=(0.0, 0.0, 0.0),
+        rb=(0.0, 0.0, -0.01), buoy_ratio=1.0,
+        Ma=(1.0, 16.0, 16.0, 0.02, 1.6, 1.6),
+        dl=(2.0, 20.0, 20.0, 0.2, 4.0, 4.0),
+        dq=(4.0, 60.0, 60.0, 0.1, 8.0, 8.0),
+        thr_pos=[(-0.95, 0.0, 0.0)] + fins_pos,
+        thr_dir=[(1.0, 0.0, 0.0)] + [(0.0, 0.0, 0.0)] * 4,
+        k_f=[30.0] + [0.0] * 4, T_rotor=[0.1] + [0.05] * 4, deadzone=[0.0] * 5,
+        act_kind=[KIND_PROP] + [KIND_FIN] * 4, act_link=[0] * 5,
+        act_axis=[(0.0, 0.0, 0.0)] + fins_axis, act_chord=[(0.0, 0.0, 0.0)] + [(1.0, 0.0, 0.0)] * 4,
+        act_range=[0.0] + [0.35] * 4, fin_area=[0.0] + [0.012] * 4, fin_cl=[0.0] + [3.0] * 4,
+        fin_cd0=[0.0] + [0.05] * 4, fin_cda=[0.0] + [1.2] * 4, rho=RHO_WATER,
+    )
+
+
+def tilt_hauv() -> dict:
+    """Tiltrotor class (Sec. III-D, hybrid aerial-underwater type): four rotors
+    at the ends of diagonal arms, thrust along -z at zero tilt, each turned
+    about its own arm by a servo (channels 0-3 rotors, 4-7 servos, +-90 deg)."""
+    s2 = math.sqrt(0.5)
+    pos = [(0.18, 0.18, 0.0), (0.18, -0.18, 0.0), (-0.18, 0.18, 0.0), (-0.18, -0.18, 0.0)]
+    arms = [(s2, s2, 0.0), (s2, -s2, 0.0), (-s2, s2, 0.0), (-s2, -s2, 0.0)]
+    return dict(
+        name="tilt8", n_thr=8, mass=2.8, Ig=(0.035, 0.035, 0.06), rg=(0.0, 0.0, 0.0),
+        rb=(0.0, 0.0, -0.01), buoy_ratio=1.0,
+        Ma=(1.2, 1.2, 2.5, 0.01, 0.01, 0.015),
+        dl=(2.5, 2.5, 5.0, 0.04, 0.04, 0.03),
+        dq=(5.0, 5.0, 10.0, 0.08, 0.08, 0.06),
+        thr_pos=pos + pos, thr_dir=[(0.0, 0.0, -1.0)] * 4 + [(0.0, 0.0, 0.0)] * 4,
+        k_f=[15.0] * 4 + [0.0] * 4, T_rotor=[0.05] * 4 + [0.08] * 4, deadzone=[0.0] * 8,
+        act_kind=[KIND_TILT] * 4 + [KIND_SERVO] * 4, act_link=[4, 5, 6, 7] + [0] * 4,
+        act_axis=arms + [(0.0, 0.0, 0.0)] * 4, act_chord=[(0.0, 0.0, 0.0)] * 8,
+        act_range=[0.0] * 4 + [0.5 * math.pi] * 4, fin_area=[0.0] * 8, fin_cl=[0.0] * 8,
+        fin_cd0=[0.0] * 8, fin_cda=[0.0] * 8, rho=RHO_WATER,
+    )
+
+
+def actuated_classes() -> list:
+    """The three propulsion types of the model library side by side:
+    multirotor (class 0), rudder-propeller, tiltrotor."""
+    return [heavy8(), lauv(), tilt_hauv()]
+
+
 def five_classes() -> list:
     """The five classes of the heterogeneous workloads (4/6/8 thrusters, 10-200 kg)."""
     return [heavy8(), scaled("quad4", 10.0, 4), scaled("rov6", 25.0, 6),
