@@ -294,6 +294,26 @@ def payload_bench(pk, stream, E=1 << 20, K=4, steps=200):
     return out
 
 
+def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
+    """The three propulsion types (multirotor, rudder-propeller with fins,
+    tiltrotor with servos) with per-env DR and current, Euler and RK4."""
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles, workloads
+    classes = vehicles.actuated_classes()
+    counts = workloads.class_counts(E, 3)
+    out = {"envs": E, "K": K, "classes": [c["name"] for c in classes]}
+    for name, integ in (("euler", B.MG_INTEG_EULER), ("rk4", B.MG_INTEG_RK4)):
+        sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR),
+                    integrator=integ)
+        sim.reset(seed=SEED)
+        acts = action_pool(sim, 4, 9)
+        t = time_steps(sim, acts, steps, 10, stream)
+        sim.status()
+        sim.close()
+        out[name] = {"env_steps_per_s": E * steps / t, "us_per_step": t / steps * 1e6}
+    return out
+
+
 def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
     """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
     T-step rollout (observation and reward every step) captured once as a CUDA
@@ -563,6 +583,7 @@ def main():
         line["sweep"] = sweep(pk, stream)
         line["tracking"] = tracking_bench(pk, stream)
         line["payload"] = payload_bench(pk, stream)
+        line["actuated"] = actuated_bench(pk, stream)
         line["hetero_graph"] = hetero_graph_bench(stream)
         line["adjoint"] = adjoint_bench(stream)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)

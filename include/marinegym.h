@@ -65,12 +65,37 @@ enum {
 #define MG_OBS_DIM 13     /* hover observation: R^T(p-p*) 3, q 4 (w>=0), v 3, w 3 */
 #define MG_ENV_PARAM_DIM 34 /* canonical host per-env parameter record (doubles) */
 
+/* Actuator kinds (Sec. III-D: multirotor, rudder-propeller and tiltrotor
+ * types). Every channel has a first-order state n in [-1, 1] driven by its
+ * command with alpha = 1 - exp(-h/T_rotor) (rotor speed, or a servo / fin
+ * angle n * act_range).
+ * MG_ACT_PROP  propeller: thrust k_f n|n| (0 inside the dead zone) along thr_dir
+ *              at thr_pos.
+ * MG_ACT_SERVO servo: no force; tilts the MG_ACT_TILT propellers linked to it.
+ * MG_ACT_FIN   fin at thr_pos with span axis act_axis and chord act_chord at
+ *              zero deflection (unit, orthogonal), deflected by n * act_range
+ *              about the span. With u = v_r + w x r (v_r relative to the water)
+ *              projected on the plane normal to the span, U = |u|, and the
+ *              angle of attack a of u from the deflected chord towards
+ *              act_axis x chord: lift 1/2 rho S U^2 C_L(a) along -(act_axis x u)/U,
+ *              drag 1/2 rho S U^2 C_D(a) along -u/U, C_L = fin_cl sin a cos a,
+ *              C_D = fin_cd0 + fin_cda sin^2 a, S = fin_area.
+ * MG_ACT_TILT  propeller whose direction thr_dir is turned about act_axis by
+ *              the angle of servo channel act_link (Rodrigues). */
+#define MG_ACT_PROP 0
+#define MG_ACT_SERVO 1
+#define MG_ACT_FIN 2
+#define MG_ACT_TILT 3
+
 /* A vehicle class (Sec. III-D model library): rigid body, hydrodynamic
- * coefficients and up to 8 thrusters. FP64 on the host; the library derives
- * the allocation matrix B = [d_i ; r_i x d_i], the rotor factor
- * alpha = 1 - exp(-h/T) and the inverse inertia in FP64 and stores them FP32.
- * The class's own CoG is the body origin (r_g = 0) and its added mass is
- * diagonal; an off-origin CoG arises from a payload (see mg_set_payload). */
+ * coefficients and up to 8 actuator channels. FP64 on the host; the library
+ * derives the allocation matrix B = [d_i ; r_i x d_i] of the fixed
+ * propellers, the fin and tilt tables, the lag factor alpha = 1 - exp(-h/T)
+ * and the inverse inertia in FP64 and stores them FP32. The class's own CoG
+ * is the body origin (r_g = 0) and its added mass is diagonal; an off-origin
+ * CoG arises from a payload (see mg_set_payload). A class with any channel
+ * other than MG_ACT_PROP (a "generic" class) runs the step only: no adjoint,
+ * FP64 check path, payload or serving. */
 typedef struct {
   int32_t n_thr;            /* 1..8 (the workloads use 4, 6, 8) */
   int32_t pad0;
@@ -87,6 +112,16 @@ typedef struct {
   double k_f[8];            /* thrust at |n| = 1, N */
   double T_rotor[8];        /* rotor time constant, s; 0 = zero-order model */
   double deadzone[8];       /* |n| below which the thrust is 0 */
+  int32_t act_kind[8];      /* MG_ACT_* (all 0: a propeller-only class) */
+  int32_t act_link[8];      /* MG_ACT_TILT: its servo channel */
+  double act_axis[8][3];    /* fin span axis / tilt axis (unit, body frame) */
+  double act_chord[8][3];   /* fin chord at zero deflection (unit, normal to the axis) */
+  double act_range[8];      /* servo / fin angle at |n| = 1, rad (> 0) */
+  double fin_area[8];       /* m^2 */
+  double fin_cl[8];         /* lift slope, 1/rad */
+  double fin_cd0[8];        /* drag at zero angle of attack */
+  double fin_cda[8];        /* drag growth with sin^2 of the angle of attack */
+  double rho;               /* water density, kg/m^3 (> 0 with fins) */
 } mg_class_desc;
 
 /* Reset configuration: domain randomisation (Sec. III-C, Table 2 train
@@ -130,7 +165,15 @@ typedef struct {
                                    1: trajectory tracking (time-varying p*(t)) */
   int32_t payload;              /* 1: every env carries a point-mass payload
                                    (needs per_env_params, record_steps = 0) */
+  int32_t integrator;           /* MG_INTEG_EULER (semi-implicit Euler per
+                                   substep) or MG_INTEG_RK4 (classical RK4 on
+                                   p, q, nu with the actuator states held over
+                                   the substep; step only, no adjoint) */
+  int32_t pad1;
 } mg_config;
+
+#define MG_INTEG_EULER 0
+#define MG_INTEG_RK4 1
 
 /* Placement of class c inside the device buffers. */
 typedef struct {
@@ -363,6 +406,8 @@ typedef struct {
   double tick_p50, tick_p99;                   /* s, device time of one shared launch */
 } mg_server_stats;
 
+/* Errors of mg_server_create: INVALID_ARG (bad config, a class that is not
+ * propeller-only or has r_g != 0), OOM. */
 int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, int32_t n_classes,
                      mg_server** out);
 int mg_server_submit(mg_server* srv, const mg_request* req, int64_t* id_out);

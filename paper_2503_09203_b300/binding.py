@@ -31,6 +31,8 @@ MG_ERR_TIMEOUT = -5
 MG_ERR_ADMISSION_REFUSED = -6
 MG_ERR_STATE = -7
 MG_MAX_THR = 8
+MG_ACT_PROP, MG_ACT_SERVO, MG_ACT_FIN, MG_ACT_TILT = 0, 1, 2, 3   # actuator kinds
+MG_INTEG_EULER, MG_INTEG_RK4 = 0, 1
 MG_MAX_CLASSES = 16
 MG_STATE_DIM = 21
 MG_OBS_DIM = 13
@@ -50,7 +52,11 @@ class mg_class_desc(C.Structure):
                 ("buoy_ratio", C.c_double), ("Ma", C.c_double * 6), ("dl", C.c_double * 6),
                 ("dq", C.c_double * 6), ("thr_pos", (C.c_double * 3) * 8),
                 ("thr_dir", (C.c_double * 3) * 8), ("k_f", C.c_double * 8),
-                ("T_rotor", C.c_double * 8), ("deadzone", C.c_double * 8)]
+                ("T_rotor", C.c_double * 8), ("deadzone", C.c_double * 8),
+                ("act_kind", C.c_int32 * 8), ("act_link", C.c_int32 * 8),
+                ("act_axis", (C.c_double * 3) * 8), ("act_chord", (C.c_double * 3) * 8),
+                ("act_range", C.c_double * 8), ("fin_area", C.c_double * 8), ("fin_cl", C.c_double * 8),
+                ("fin_cd0", C.c_double * 8), ("fin_cda", C.c_double * 8), ("rho", C.c_double)]
 
 
 class mg_reset_cfg(C.Structure):
@@ -70,7 +76,8 @@ class mg_config(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("class_counts", C.POINTER(C.c_int32)),
                 ("dt", C.c_double), ("K", C.c_int32), ("per_env_params", C.c_int32),
                 ("reset", mg_reset_cfg), ("record_steps", C.c_int32), ("ckpt_every", C.c_int32),
-                ("mem_budget", C.c_size_t), ("task", C.c_int32), ("payload", C.c_int32)]
+                ("mem_budget", C.c_size_t), ("task", C.c_int32), ("payload", C.c_int32),
+                ("integrator", C.c_int32), ("pad1", C.c_int32)]
 
 
 class mg_class_layout(C.Structure):
@@ -217,6 +224,15 @@ def pack_class(d: dict) -> mg_class_desc:
         for k in range(3):
             c.thr_pos[i][k] = float(d["thr_pos"][i][k]); c.thr_dir[i][k] = float(d["thr_dir"][i][k])
         c.k_f[i] = float(d["k_f"][i]); c.T_rotor[i] = float(d["T_rotor"][i]); c.deadzone[i] = float(d["deadzone"][i])
+        # Actuator kinds (absent: every channel a fixed propeller).
+        c.act_kind[i] = int(d.get("act_kind", [MG_ACT_PROP] * n)[i])
+        c.act_link[i] = int(d.get("act_link", [0] * n)[i])
+        for k in range(3):
+            c.act_axis[i][k] = float(d.get("act_axis", [(0.0, 0.0, 0.0)] * n)[i][k])
+            c.act_chord[i][k] = float(d.get("act_chord", [(0.0, 0.0, 0.0)] * n)[i][k])
+        for name in ("act_range", "fin_area", "fin_cl", "fin_cd0", "fin_cda"):
+            getattr(c, name)[i] = float(d.get(name, [0.0] * n)[i])
+    c.rho = float(d.get("rho", 0.0))
     return c
 
 
@@ -237,14 +253,14 @@ TASK_HOVER, TASK_TRACK = 0, 1
 
 def mg_create(classes: Sequence[dict], counts: Sequence[int], dt: float, K: int, per_env_params: bool = True,
               reset: Optional[dict] = None, record_steps: int = 0, ckpt_every: int = 0, mem_budget: int = 0,
-              task: int = TASK_HOVER, payload: bool = False):
+              task: int = TASK_HOVER, payload: bool = False, integrator: int = MG_INTEG_EULER):
     L = lib()
     arr = (mg_class_desc * len(classes))(*[pack_class(c) for c in classes])
     cnt = (C.c_int32 * len(counts))(*[int(x) for x in counts])
     cfg = mg_config(n_classes=len(classes), class_counts=cnt, dt=float(dt), K=int(K),
                     per_env_params=int(bool(per_env_params)), reset=pack_reset(reset or {}),
                     record_steps=int(record_steps), ckpt_every=int(ckpt_every), mem_budget=int(mem_budget),
-                    task=int(task), payload=int(bool(payload)))
+                    task=int(task), payload=int(bool(payload)), integrator=int(integrator))
     h = _VP()
     _check(L.mg_create(C.byref(cfg), arr, C.byref(h)), None)
     return h.value
@@ -424,13 +440,14 @@ class Sim:
     """
 
     def __init__(self, classes, counts, dt=0.01, K=1, per_env_params=True, reset=None, record_steps=0,
-                 ckpt_every=0, mem_budget=0, task=TASK_HOVER, payload=False, device="cuda"):
+                 ckpt_every=0, mem_budget=0, task=TASK_HOVER, payload=False, integrator=MG_INTEG_EULER,
+                 device="cuda"):
         import torch
         self.classes = list(classes)
         self.counts = [int(c) for c in counts]
         self.dt, self.K = float(dt), int(K)
         self.handle = mg_create(self.classes, self.counts, dt, K, per_env_params, reset, record_steps,
-                                ckpt_every, mem_budget, task, payload)
+                                ckpt_every, mem_budget, task, payload, integrator)
         self.layout = mg_get_layout(self.handle)
         self.n_envs = self.layout.n_envs
         self.n_slots = self.layout.n_slots

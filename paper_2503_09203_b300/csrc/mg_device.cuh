@@ -4,7 +4,8 @@
 //
 // One substep (h = dt/K) of the discrete map, in the order a1..a8:
 //   a1 rotor lag      n <- n + alpha (c - n)                 (Sec. III-D)
-//   a2 thrust/alloc   f_i = k_i n_i |n_i| (0 in dead zone), tau = B f
+//   a2 thrust/alloc   f_i = k_i n_i |n_i| (0 in dead zone), tau = B f; generic
+//                     tables add fins (lift/drag) and servo-tilted propellers
 //   a3 kinematics     R(q), v_c = R^T V_c, v_r = v - v_c     (Sec. III-B, current)
 //   a4 C_RB(nu) nu  = [m w x v ; w x (I_g w)]                 (Eq. 2, r_g = 0)
 //   a5 C_A(nu_r)nu_r= [w x a1 ; v_r x a1 + w x a2], a1 = A_lin v_r, a2 = A_ang w,
@@ -12,6 +13,7 @@
 //   a6 D(nu_r)nu_r  = d_l o nu_r + d_q o |nu_r| o nu_r
 //   a7 g(q)         = [-(W-B) e ; B r_b x e], e = R^T e_3    (Eq. 1-2, r_g = 0)
 //   a8 nu += h M^-1 (tau - a4 - a5 - a6 - a7); p += h R v; q <- |q + h/2 q(x)(0,w)|
+//      (or the RK4 variant over a3-a8 with the actuator states held)
 // The hover observation / reward (Sec. IV-B station keeping) and the exact
 // vector-Jacobian products of both are here too.
 #pragma once
@@ -19,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #define MG_HD __host__ __device__ __forceinline__
 
@@ -141,18 +145,35 @@ struct Tape {
   S n1[NT], R[3][3], vc[3], vr[3], w[3], rhs[6], nu1[6], qn[4], inv;
 };
 
-// a1-a8. `x` is updated in place; `c` is the clamped command (zero-order hold).
-// `A` is an Act<S> or a volatile view of one in shared memory (a volatile view
-// keeps the class table in shared memory instead of hoisting it into registers).
-// `P` is a Phys<S> or a view with the same members (arrays minv, A, dl, dq,
-// Ig, rb, Vc and scalars m, W, B) that reads shared memory on use.
-// CURRENT = false compiles the ocean-current terms out (parameter sources
-// whose current is zero by construction).
-template <typename S, int NT, bool TAPE, typename ActT, typename PhysT, bool CURRENT = true>
-MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
-                   Tape<S, NT>* tp) {
-  // a1 + a2
-  S f[NT];
+// Actuator kinds (Sec. III-D): propeller with a fixed direction (its column
+// of the allocation matrix), servo (no force), fin, propeller tilted by a servo.
+enum { KIND_PROP = 0, KIND_SERVO = 1, KIND_FIN = 2, KIND_TILT = 3 };
+
+// No generic actuators: every channel is a fixed propeller.
+struct NoGen {};
+
+// Per-channel values of a generic actuator table (20 floats per channel):
+// fin  : e1 = chord at zero deflection (0..2), e2 = a x e1 (3..5), r x e1
+//        (6..8), r x e2 (9..11), kL = rho S C_L_alpha / 2 (12), kD0 (13),
+//        kDa (14), deflection range (15);
+// tilt : B0 = [d ; r x d] (0..5), B1 = [a x d ; r x (a x d)] (6..11),
+//        B2 = (a . d) [a ; r x a] (12..17), servo channel (18), its range (19).
+enum { GEN_VALS = 20 };
+
+MG_HD void msincos(float x, float* s, float* c) {
+#if defined(__CUDA_ARCH__)
+  sincosf(x, s, c);
+#else
+  *s = sinf(x); *c = cosf(x);
+#endif
+}
+MG_HD void msincos(double x, double* s, double* c) { *s = sin(x); *c = cos(x); }
+
+// a1 + a2: actuator states (rotor speed or servo / fin angle, first-order
+// lag), propeller thrust f = k n|n| (0 in the dead zone; k = 0 for servos and
+// fins) and the fixed-direction part of the wrench tau = B f.
+template <typename S, int NT, typename ActT>
+MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S tau[6]) {
   {
     S kf[NT], dz[NT], al[NT];
     act_rotor<S, NT>(A, kf, dz, al);
@@ -163,7 +184,6 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
       f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
     }
   }
-  S tau[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     S r[NT];
@@ -173,17 +193,79 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     for (int i = 1; i < NT; ++i) s = s + r[i] * f[i];
     tau[k] = s;
   }
-  // a3
-  S R[3][3];
-  rot(x.q, R);
-  const S v[3] = {x.nu[0], x.nu[1], x.nu[2]};
-  const S w[3] = {x.nu[3], x.nu[4], x.nu[5]};
-  S vc[3], vr[3];
+}
+
+// Wrench of the propellers tilted by servos (depends on the actuator states only):
+// f_i [cos th B0 + sin th B1 + (1 - cos th) B2], th = n_servo * range (Rodrigues).
+template <typename S, int NT, typename GenT>
+MG_HD void tilt_wrench(const GenT& G, const S (&n)[NT], const S (&f)[NT], S tau[6]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    if (G.kind(i) != KIND_TILT) continue;
+    const int link = (int)G.v(i, 18);
+    S nl = S(0.0f);
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (j == link) nl = n[j];
+    S sn, cs;
+    msincos(nl * S(G.v(i, 19)), &sn, &cs);
+    const S omc = S(1.0f) - cs;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tau[k] = tau[k] + f[i] * (cs * S(G.v(i, k)) + sn * S(G.v(i, 6 + k)) + omc * S(G.v(i, 12 + k)));
+  }
+}
+
+// Wrench of the fins. With x = u . e1, y = u . e2 the components of the fin's
+// velocity through the water u = v_r + w x r in the plane normal to the span,
+// deflection th, u_c = cos th x + sin th y (along the chord), u_n = cos th y -
+// sin th x (along the fin normal) and U^2 = x^2 + y^2: lift
+// -kL (u_n u_c / U) (a x u) = kL g (y e1 - x e2), g = u_n u_c / U, and drag
+// -(kD0 U + kDa u_n^2 / U) u (the lift and drag of C_L = C_L_alpha sin a cos a,
+// C_D = C_D0 + C_D_alpha sin^2 a at angle of attack a, written in x and y).
+template <typename S, int NT, typename GenT>
+MG_HD void fin_wrench(const GenT& G, const S (&n)[NT], const S vr[3], const S w[3], S tau[6]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    if (G.kind(i) != KIND_FIN) continue;
+    S e1[3], e2[3], re1[3], re2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = S(G.v(i, k)); e2[k] = S(G.v(i, 3 + k)); re1[k] = S(G.v(i, 6 + k)); re2[k] = S(G.v(i, 9 + k));
+    }
+    const S xx = vr[0] * e1[0] + vr[1] * e1[1] + vr[2] * e1[2] + w[0] * re1[0] + w[1] * re1[1] + w[2] * re1[2];
+    const S yy = vr[0] * e2[0] + vr[1] * e2[1] + vr[2] * e2[2] + w[0] * re2[0] + w[1] * re2[1] + w[2] * re2[2];
+    const S U2 = xx * xx + yy * yy;
+    if (!(U2 > S(0.0f))) continue;
+    S sn, cs;
+    msincos(n[i] * S(G.v(i, 15)), &sn, &cs);
+    const S uc = cs * xx + sn * yy, un = cs * yy - sn * xx;
+    const S iU = minvsqrt(U2);
+    const S U = U2 * iU;
+    const S g = un * uc * iU;
+    const S kL = S(G.v(i, 12)), D = S(G.v(i, 13)) * U + S(G.v(i, 14)) * un * un * iU;
+    const S F1 = kL * g * yy - D * xx, F2 = -(kL * g * xx) - D * yy;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      tau[k] = tau[k] + F1 * e1[k] + F2 * e2[k];
+      tau[3 + k] = tau[3 + k] + F1 * re1[k] + F2 * re2[k];
+    }
+  }
+}
+
+// a3: body-frame current v_c = R^T V_c and relative velocity v_r = v - v_c.
+template <typename S, typename PhysT, bool CURRENT>
+MG_HD void rel_velocity(const S R[3][3], const S v[3], const PhysT& P, S vc[3], S vr[3]) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     vc[j] = CURRENT ? R[0][j] * S(P.Vc[0]) + R[1][j] * S(P.Vc[1]) + R[2][j] * S(P.Vc[2]) : S(0.0f);
     vr[j] = CURRENT ? v[j] - vc[j] : v[j];
   }
+}
+
+// a4-a7: rhs = tau - C_RB(nu) nu - C_A(nu_r) nu_r - M_A [w x v_c ; 0] - D(nu_r) nu_r - g(q).
+template <typename S, typename PhysT, bool CURRENT>
+MG_HD void body_rhs(const S R[3][3], const S v[3], const S w[3], const S vc[3], const S vr[3], const S tau[6],
+                    const PhysT& P, S rhs[6]) {
   // a4. With a payload (PhysT::kFull) the body origin is not the CoG: with the
   // first moment s = m' r_g and the inertia I_o about the origin,
   // C_RB(nu) nu = [m' w x v + w x (w x s) ; w x (I_o w) + s x (w x v)].
@@ -236,8 +318,6 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     for (int j = 0; j < 3; ++j) { extra_lin[j] = wxwxs[j]; extra_ang[j] = sxwxv[j]; }
   }
   cross3(Brb, e, mb);
-  // a8
-  S rhs[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     rhs[j] = CURRENT ? tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j]
@@ -248,9 +328,12 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
       rhs[3 + j] = rhs[3 + j] - extra_ang[j];
     }
   }
+}
+
+// a8 (first half): nu_dot = M^-1 rhs (diagonal, or the full symmetric inverse).
+template <typename S, typename PhysT>
+MG_HD void apply_minv(const PhysT& P, const S rhs[6], S nd[6]) {
   if constexpr (PhysT::kFull) {
-    // nu_dot = M^-1 rhs with the full symmetric inverse.
-    S nd[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       S acc = S(0.0f);
@@ -258,23 +341,59 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
       for (int j = 0; j < 6; ++j) acc = acc + S(P.Mi[i <= j ? sym6(i, j) : sym6(j, i)]) * rhs[j];
       nd[i] = acc;
     }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
   } else {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * (S(P.minv[j]) * rhs[j]);
+    for (int j = 0; j < 6; ++j) nd[j] = S(P.minv[j]) * rhs[j];
   }
+}
+
+// q (x) (0, w) for the quaternion kinematics q_dot = 1/2 q (x) (0, w).
+template <typename S>
+MG_HD void quat_rate(const S q[4], const S w[3], S qd[4]) {
+  qd[0] = -q[1] * w[0] - q[2] * w[1] - q[3] * w[2];
+  qd[1] = q[0] * w[0] + q[2] * w[2] - q[3] * w[1];
+  qd[2] = q[0] * w[1] - q[1] * w[2] + q[3] * w[0];
+  qd[3] = q[0] * w[2] + q[1] * w[1] - q[2] * w[0];
+}
+
+// a1-a8. `x` is updated in place; `c` is the clamped command (zero-order hold).
+// `A` is an Act<S> or a volatile view of one in shared memory (a volatile view
+// keeps the class table in shared memory instead of hoisting it into registers).
+// `P` is a Phys<S> or a view with the same members (arrays minv, A, dl, dq,
+// Ig, rb, Vc and scalars m, W, B) that reads shared memory on use.
+// CURRENT = false compiles the ocean-current terms out (parameter sources
+// whose current is zero by construction). `G` is NoGen (propellers only) or a
+// generic actuator table (fins, servo-tilted propellers).
+template <typename S, int NT, bool TAPE, typename ActT, typename PhysT, bool CURRENT = true,
+          typename GenT = NoGen>
+MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
+                   Tape<S, NT>* tp, const GenT& G = GenT()) {
+  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  S f[NT], tau[6];
+  actuate<S, NT>(x, c, A, f, tau);
+  if constexpr (GEN) tilt_wrench<S, NT>(G, x.n, f, tau);
+  // a3
+  S R[3][3];
+  rot(x.q, R);
+  const S v[3] = {x.nu[0], x.nu[1], x.nu[2]};
+  const S w[3] = {x.nu[3], x.nu[4], x.nu[5]};
+  S vc[3], vr[3];
+  rel_velocity<S, PhysT, CURRENT>(R, v, P, vc, vr);
+  if constexpr (GEN) fin_wrench<S, NT>(G, x.n, vr, w, tau);
+  S rhs[6], nd[6];
+  body_rhs<S, PhysT, CURRENT>(R, v, w, vc, vr, tau, P, rhs);
+  apply_minv<S>(P, rhs, nd);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     x.p[i] = x.p[i] + h * (R[i][0] * x.nu[0] + R[i][1] * x.nu[1] + R[i][2] * x.nu[2]);
-  const S qw = x.q[0], qx = x.q[1], qy = x.q[2], qz = x.q[3];
-  const S P_ = x.nu[3], Q_ = x.nu[4], R_ = x.nu[5];
   const S hh = S(0.5f) * h;
-  S qn[4];
-  qn[0] = qw + hh * (-qx * P_ - qy * Q_ - qz * R_);
-  qn[1] = qx + hh * (qw * P_ + qy * R_ - qz * Q_);
-  qn[2] = qy + hh * (qw * Q_ - qx * R_ + qz * P_);
-  qn[3] = qz + hh * (qw * R_ + qx * Q_ - qy * P_);
+  const S wn[3] = {x.nu[3], x.nu[4], x.nu[5]};
+  S qd[4], qn[4];
+  quat_rate(x.q, wn, qd);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) qn[i] = x.q[i] + hh * qd[i];
   const S inv = minvsqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.q[i] = qn[i] * inv;
@@ -293,6 +412,74 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     for (int i = 0; i < 4; ++i) tp->qn[i] = qn[i];
     tp->inv = inv;
   }
+}
+
+// Time derivative of (p, q, nu) for the RK4 variant, with the actuator states
+// and the state-independent part of the actuator wrench (tau_n) held over the
+// substep; the attitude of a stage is that of its normalised quaternion.
+template <typename S, int NT, typename PhysT, bool CURRENT, typename GenT>
+MG_HD void rk4_stage(const S q[4], const S nu[6], const S (&n)[NT], const S tau_n[6], const PhysT& P,
+                     const GenT& G, S dp[3], S dq[4], S dnu[6]) {
+  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  const S iq = minvsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const S qh[4] = {q[0] * iq, q[1] * iq, q[2] * iq, q[3] * iq};
+  S R[3][3];
+  rot(qh, R);
+  const S v[3] = {nu[0], nu[1], nu[2]};
+  const S w[3] = {nu[3], nu[4], nu[5]};
+  S vc[3], vr[3], tau[6];
+  rel_velocity<S, PhysT, CURRENT>(R, v, P, vc, vr);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) tau[k] = tau_n[k];
+  if constexpr (GEN) fin_wrench<S, NT>(G, n, vr, w, tau);
+  S rhs[6];
+  body_rhs<S, PhysT, CURRENT>(R, v, w, vc, vr, tau, P, rhs);
+  apply_minv<S>(P, rhs, dnu);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dp[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
+  S qd[4];
+  quat_rate(q, w, qd);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dq[i] = S(0.5f) * qd[i];
+}
+
+// One substep of the classical fourth-order Runge-Kutta variant: actuator
+// states first (as a1), then RK4 on (p, q, nu) over h with them held, then q
+// normalised. Stage sums are accumulated in place to bound register use.
+template <typename S, int NT, typename ActT, typename PhysT, bool CURRENT = true, typename GenT = NoGen>
+MG_HD void substep_rk4(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
+                       const GenT& G = GenT()) {
+  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  S f[NT], tau_n[6];
+  actuate<S, NT>(x, c, A, f, tau_n);
+  if constexpr (GEN) tilt_wrench<S, NT>(G, x.n, f, tau_n);
+  S q0[4], nu0[6];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q0[i] = x.q[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) nu0[i] = x.nu[i];
+  // x holds the running sum y0 + h/6 (k1 + 2 k2 + 2 k3 + k4); ys the stage point.
+  S ys_q[4], ys_nu[6], dp[3], dq[4], dnu[6];
+  const S h2 = S(0.5f) * h, h6 = h / S(6.0f), h3 = h / S(3.0f);
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    if (st == 0) {
+      rk4_stage<S, NT, PhysT, CURRENT>(q0, nu0, x.n, tau_n, P, G, dp, dq, dnu);
+    } else {
+      rk4_stage<S, NT, PhysT, CURRENT>(ys_q, ys_nu, x.n, tau_n, P, G, dp, dq, dnu);
+    }
+    const S wsum = (st == 0 || st == 3) ? h6 : h3;
+    const S hs = (st == 2) ? h : h2;   // step to the next stage point
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x.p[i] = x.p[i] + wsum * dp[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { x.q[i] = x.q[i] + wsum * dq[i]; ys_q[i] = q0[i] + hs * dq[i]; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { x.nu[i] = x.nu[i] + wsum * dnu[i]; ys_nu[i] = nu0[i] + hs * dnu[i]; }
+  }
+  const S inv = minvsqrt(x.q[0] * x.q[0] + x.q[1] * x.q[1] + x.q[2] * x.q[2] + x.q[3] * x.q[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.q[i] = x.q[i] * inv;
 }
 
 // Hover observation and reward after a control step.

@@ -42,6 +42,16 @@ struct ClassF {
 };
 static_assert(sizeof(ClassF) == 104 * 4, "ClassF layout");
 
+// Generic actuator table of a class (fins, servo-tilted propellers): the kind
+// of each channel (as the bits of a float, so that the table stages into
+// shared memory as one float array) and 20 values per channel (layout in the
+// step arithmetic's header).
+struct ClassG {
+  int32_t kind[8];
+  float v[8][20];
+};
+static_assert(sizeof(ClassG) == (8 + 160) * 4, "ClassG layout");
+
 // Per-class constants in FP64 for the finite-difference check path.
 struct ClassD {
   double alloc[6][8];
@@ -101,6 +111,7 @@ struct StepArgs {
   uint32_t* status;           // bit 0: non-finite state
   int32_t pay_plane;          // payload runs: first payload plane
   int32_t pad1;
+  const ClassG* gen;          // generic actuator tables (launches of generic classes)
 };
 
 struct AdjArgs {

@@ -20,6 +20,7 @@
 
 #include <type_traits>
 
+#include "marinegym.h"
 #include "mg_internal.h"
 #include "mg_device.cuh"
 #include "mg_payload.h"
@@ -282,6 +283,20 @@ struct PhysSmemFull {
 static_assert(PF_STD_PLANES * 4 == PF_PAY && PF_PAY + PF_PAY_PLANES * 4 == PF_DIM, "payload column map");
 static_assert(PAY_W < PF_PAY_PLANES * 4, "staged payload planes hold the step's fields");
 
+// Generic actuator table in shared memory: 8 kinds (float bits), then
+// GEN_VALS values per channel (a copy of the class's ClassG).
+constexpr int GEN_FLOATS = 8 + 8 * GEN_VALS;
+static_assert(sizeof(ClassG) == GEN_FLOATS * sizeof(float), "generic table layout");
+static_assert(KIND_PROP == MG_ACT_PROP && KIND_SERVO == MG_ACT_SERVO && KIND_FIN == MG_ACT_FIN &&
+                  KIND_TILT == MG_ACT_TILT, "actuator kinds");
+struct GenSmem {
+  unsigned base;
+  __device__ __forceinline__ int kind(int i) const { return __float_as_int(lds1(base + 4u * (unsigned)i)); }
+  __device__ __forceinline__ float v(int i, int k) const {
+    return lds1(base + 4u * (unsigned)(8 + i * GEN_VALS + k));
+  }
+};
+
 constexpr int STEP_BLK = 128;
 #ifndef MG_STEP_MIN_BLOCKS
 #define MG_STEP_MIN_BLOCKS 4
@@ -409,10 +424,10 @@ __device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0,
   return n <= 0 ? 0u : (unsigned)min((int64_t)WENV, n);
 }
 
-template <int NT, int PM>
+template <int NT, int PM, int VAR>
 __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
-                                          const float* s_phys, const float* buf, float* obs_w, float* s_par,
-                                          int& n_emit) {
+                                          const float* s_phys, const float* s_gen, const float* buf, float* obs_w,
+                                          float* s_par, int& n_emit) {
   constexpr bool PER_ENV = PM >= 1;
   using SG = Stage<NT>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -497,6 +512,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   // Each thread reads only its own parameter column: no barrier needed.
   using PV = std::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
   const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : smem_addr(s_phys);
+  const unsigned g_base = smem_addr(s_gen);
   const PV P(p_base);
 #endif
   const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
@@ -530,14 +546,21 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       // Shared-memory bases made opaque once per substep: loads may be
       // scheduled freely inside a substep but not hoisted out of the loop.
       for (int k = 0; k < sd.K; ++k) {
-        unsigned pb = p_base, ab = A.base;
-        asm volatile("" : "+r"(pb), "+r"(ab));
+        unsigned pb = p_base, ab = A.base, gb = g_base;
+        asm volatile("" : "+r"(pb), "+r"(ab), "+r"(gb));
         const PV Pk(pb);
         const ActSmem Ak{ab};
         // Class-constant physics carries no current (zero by construction).
-        substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
+        if constexpr (VAR == 0) {
+          substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
+        } else if constexpr (VAR == 1) {
+          substep<float, NT, false, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, nullptr, GenSmem{gb});
+        } else {
+          substep_rk4<float, NT, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, GenSmem{gb});
+        }
       }
 #else
+      static_assert(VAR == 0, "generic actuators and RK4 read their tables from shared memory");
       for (int k = 0; k < sd.K; ++k) substep<float, NT, false, ActSmem, decltype(P), PER_ENV>(x, c, P, A, sd.h, nullptr);
 #endif
     }
@@ -604,8 +627,16 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 // a per-warp bulk store. Warps never wait on one another except when the
 // class constants change. Every wait is bounded (2 s); a warp that gives up
 // sets bit 1 of the status word and leaves.
-template <int NT, int PM>
-__global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(const __grid_constant__ StepArgs a) {
+// The RK4 variant keeps the stage point, the running sum and the substep's
+// start state live at once: it is compiled for 2 resident blocks per SM (up to
+// 255 registers) instead of spilling.
+template <int VAR>
+struct StepMinBlocks {
+  static constexpr int value = VAR == 2 ? 2 : MG_STEP_MIN_BLOCKS;
+};
+
+template <int NT, int PM, int VAR>
+__global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_kernel(const __grid_constant__ StepArgs a) {
   using SG = Stage<NT>;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -617,6 +648,7 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
   float* const s_par = s_dyn + N_WARPS * wfl;
   __shared__ __align__(16) float s_act[SA_DIM];
   __shared__ __align__(16) float s_phys[PAR_DIM];
+  __shared__ __align__(16) float s_gen[VAR ? GEN_FLOATS : 4];
   __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
   __shared__ SegDesc s_seg[SEG_CACHE];
   // The next launch of a step (another thruster count, disjoint envs) may
@@ -684,6 +716,10 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
         else if (k < 72) s_act[k] = sd.alpha[k - 64];
         else s_phys[k - 72] = cf.phys[k - 72];
       }
+      if (VAR) {
+        const float* g = reinterpret_cast<const float*>(a.gen + sd.cls);
+        for (int k = tid; k < GEN_FLOATS; k += STEP_BLK) s_gen[k % (VAR ? GEN_FLOATS : 4)] = g[k];
+      }
       __syncthreads();
       prev_seg = si;
     }
@@ -694,8 +730,8 @@ __global__ void __launch_bounds__(STEP_BLK, MG_STEP_MIN_BLOCKS) mg_step_kernel(c
       }
       use[b]++;
     }
-    step_tile<NT, PM>(a, sd, tile, s_act, s_phys, b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep,
-                           s_par, n_emit);
+    step_tile<NT, PM, VAR>(a, sd, tile, s_act, s_phys, s_gen, b ? buf1 : buf0,
+                           MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
     nvw_cur = nvw_next;
@@ -1103,7 +1139,7 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
     default: return cudaErrorInvalidValue; \
   }
 
-// Dynamic shared memory of mg_step_kernel<NT, PM>.
+// Dynamic shared memory of mg_step_kernel<NT, PM, *>.
 template <int NT, int PM>
 static size_t step_smem(bool track) {
   const int cols = PM == 2 ? PF_DIM : (PM == 1 ? PAR_DIM : 0);
@@ -1112,13 +1148,13 @@ static size_t step_smem(bool track) {
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
-template <int NT, int PM>
+template <int NT, int PM, int VAR>
 static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
   static bool attr_set = false;   // per instantiation, per process (one device)
   const size_t smem = step_smem<NT, PM>(a.track != 0);
   if (!attr_set) {
     // The largest layout (tracking) bounds every launch of this instantiation.
-    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_smem<NT, PM>(true));
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -1133,25 +1169,34 @@ static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cu
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM>, a);
+  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a);
 }
 
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st) {
-  if (a.n_tiles <= 0) return cudaSuccess;
-  if (a.per_env == 2) {
-#define MG_L(N) return launch_step_t<N, 2>(a, grid, dependent, st)
-    MG_NT_SWITCH(nt, MG_L)
+template <int PM, int VAR>
+static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st) {
+#define MG_L(N) return launch_step_t<N, PM, VAR>(a, grid, dependent, st)
+  MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
-  } else if (a.per_env == 1) {
-#define MG_L(N) return launch_step_t<N, 1>(a, grid, dependent, st)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  } else {
-#define MG_L(N) return launch_step_t<N, 0>(a, grid, dependent, st)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  }
   return cudaErrorInvalidValue;
+}
+
+// Step launch of one class group: thruster count nt, parameter source
+// a.per_env (0 class, 1 per-env, 2 payload), variant var (0 propellers with
+// Euler, 1 generic actuators with Euler, 2 RK4).
+cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  switch (a.per_env * 3 + var) {
+    case 0: return launch_step_pv<0, 0>(a, nt, grid, dependent, st);
+    case 1: return launch_step_pv<0, 1>(a, nt, grid, dependent, st);
+    case 2: return launch_step_pv<0, 2>(a, nt, grid, dependent, st);
+    case 3: return launch_step_pv<1, 0>(a, nt, grid, dependent, st);
+    case 4: return launch_step_pv<1, 1>(a, nt, grid, dependent, st);
+    case 5: return launch_step_pv<1, 2>(a, nt, grid, dependent, st);
+    case 6: return launch_step_pv<2, 0>(a, nt, grid, dependent, st);
+    case 7: return launch_step_pv<2, 1>(a, nt, grid, dependent, st);
+    case 8: return launch_step_pv<2, 2>(a, nt, grid, dependent, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st) {
@@ -1182,30 +1227,36 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int NT, int PM>
+template <int NT, int PM, int VAR>
 static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<NT, PM>(true));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PM>, STEP_BLK,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PM, VAR>, STEP_BLK,
                                                        step_smem<NT, PM>(track));
 }
 
-cudaError_t step_kernel_occupancy(int nt, int pm, bool track, int* blocks_per_sm) {
-  if (pm == 2) {
-#define MG_L(N) return occupancy_t<N, 2>(track, blocks_per_sm)
-    MG_NT_SWITCH(nt, MG_L)
+template <int PM, int VAR>
+static cudaError_t occupancy_pv(int nt, bool track, int* blocks_per_sm) {
+#define MG_L(N) return occupancy_t<N, PM, VAR>(track, blocks_per_sm)
+  MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
-  } else if (pm == 1) {
-#define MG_L(N) return occupancy_t<N, 1>(track, blocks_per_sm)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  } else {
-#define MG_L(N) return occupancy_t<N, 0>(track, blocks_per_sm)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm) {
+  switch (pm * 3 + var) {
+    case 0: return occupancy_pv<0, 0>(nt, track, blocks_per_sm);
+    case 1: return occupancy_pv<0, 1>(nt, track, blocks_per_sm);
+    case 2: return occupancy_pv<0, 2>(nt, track, blocks_per_sm);
+    case 3: return occupancy_pv<1, 0>(nt, track, blocks_per_sm);
+    case 4: return occupancy_pv<1, 1>(nt, track, blocks_per_sm);
+    case 5: return occupancy_pv<1, 2>(nt, track, blocks_per_sm);
+    case 6: return occupancy_pv<2, 0>(nt, track, blocks_per_sm);
+    case 7: return occupancy_pv<2, 1>(nt, track, blocks_per_sm);
+    case 8: return occupancy_pv<2, 2>(nt, track, blocks_per_sm);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace mg

@@ -17,12 +17,12 @@
 #include "mg_payload.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
-cudaError_t step_kernel_occupancy(int nt, int pm, bool track, int* blocks_per_sm);
+cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm);
 }  // namespace mg
 
 namespace mg {
@@ -39,9 +39,11 @@ struct ClassLay {
   int64_t st_off, act_off;
 };
 
-// Segments with the same thruster count, launched by one kernel instantiation.
+// Segments with the same thruster count and step variant (0 propellers with
+// Euler, 1 generic actuators with Euler, 2 RK4), launched by one kernel
+// instantiation.
 struct Group {
-  int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles;
+  int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles, var;
 };
 
 struct mg_sim {
@@ -63,6 +65,7 @@ struct mg_sim {
   float4* d_planes = nullptr;
   int32_t n_planes = 0;
   ClassF* d_cls = nullptr;
+  ClassG* d_gen = nullptr;
   ClassD* d_cls64 = nullptr;
   ClassNominal* d_nominal = nullptr;
   SegDesc* d_segs = nullptr;
@@ -118,10 +121,90 @@ static int validate_class(mg_sim* sim, const mg_class_desc& c, int ci) {
     if (!finite_nonneg(c.k_f[i]) || !finite_nonneg(c.T_rotor[i]) || !finite_nonneg(c.deadzone[i]))
       return fail(sim, MG_ERR_INVALID_ARG, "class %d thruster %d: k_f, T_rotor, deadzone must be >= 0", ci, i);
     for (int k = 0; k < 3; ++k)
-      if (!std::isfinite(c.thr_pos[i][k]) || !std::isfinite(c.thr_dir[i][k]))
+      if (!std::isfinite(c.thr_pos[i][k]) || !std::isfinite(c.thr_dir[i][k]) || !std::isfinite(c.act_axis[i][k]) ||
+          !std::isfinite(c.act_chord[i][k]))
         return fail(sim, MG_ERR_INVALID_ARG, "class %d thruster %d: geometry not finite", ci, i);
+    const int kind = c.act_kind[i];
+    if (kind < MG_ACT_PROP || kind > MG_ACT_TILT)
+      return fail(sim, MG_ERR_INVALID_ARG, "class %d channel %d: unknown actuator kind %d", ci, i, kind);
+    auto norm = [](const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); };
+    auto unit = [&](const double* v) { return std::fabs(norm(v) - 1.0) <= 1e-9; };
+    if (kind == MG_ACT_SERVO || kind == MG_ACT_FIN)
+      if (!(std::isfinite(c.act_range[i]) && c.act_range[i] > 0.0))
+        return fail(sim, MG_ERR_INVALID_ARG, "class %d channel %d: act_range must be > 0", ci, i);
+    if (kind == MG_ACT_FIN) {
+      const double* a = c.act_axis[i];
+      const double* ch = c.act_chord[i];
+      if (!unit(a) || !unit(ch) || std::fabs(a[0] * ch[0] + a[1] * ch[1] + a[2] * ch[2]) > 1e-9)
+        return fail(sim, MG_ERR_INVALID_ARG, "class %d fin %d: span axis and chord must be orthogonal unit vectors", ci, i);
+      if (!finite_nonneg(c.fin_area[i]) || !std::isfinite(c.fin_cl[i]) || !finite_nonneg(c.fin_cd0[i]) ||
+          !finite_nonneg(c.fin_cda[i]) || !(std::isfinite(c.rho) && c.rho > 0.0))
+        return fail(sim, MG_ERR_INVALID_ARG, "class %d fin %d: area, drag >= 0, lift slope finite, rho > 0", ci, i);
+    }
+    if (kind == MG_ACT_TILT) {
+      const int j = c.act_link[i];
+      if (j < 0 || j >= c.n_thr || c.act_kind[j] != MG_ACT_SERVO)
+        return fail(sim, MG_ERR_INVALID_ARG, "class %d channel %d: act_link must name a servo channel", ci, i);
+      if (!unit(c.act_axis[i])) return fail(sim, MG_ERR_INVALID_ARG, "class %d channel %d: tilt axis must be a unit vector", ci, i);
+    }
   }
   return MG_OK;
+}
+
+// A class with any channel other than a fixed propeller.
+static bool generic_class(const mg_class_desc& c) {
+  for (int i = 0; i < c.n_thr; ++i)
+    if (c.act_kind[i] != MG_ACT_PROP) return true;
+  return false;
+}
+
+// Generic actuator table of a class (FP64 geometry, stored FP32): fins
+// e1, e2 = a x e1, r x e1, r x e2, 1/2 rho S (C_L_alpha, C_D0, C_D_alpha),
+// range; tilted propellers B0 = [d ; r x d], B1 = [a x d ; r x (a x d)],
+// B2 = (a . d) [a ; r x a], servo channel, servo range.
+static ClassG generic_table(const mg_class_desc& c) {
+  ClassG g;
+  std::memset(&g, 0, sizeof(g));
+  auto crs = [](const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1]; o[1] = a[2] * b[0] - a[0] * b[2]; o[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  for (int i = 0; i < c.n_thr; ++i) {
+    g.kind[i] = c.act_kind[i];
+    const double* r = c.thr_pos[i];
+    const double* a = c.act_axis[i];
+    if (c.act_kind[i] == MG_ACT_FIN) {
+      const double* e1 = c.act_chord[i];
+      double e2[3], re1[3], re2[3];
+      crs(a, e1, e2);
+      crs(r, e1, re1);
+      crs(r, e2, re2);
+      for (int k = 0; k < 3; ++k) {
+        g.v[i][k] = (float)e1[k]; g.v[i][3 + k] = (float)e2[k];
+        g.v[i][6 + k] = (float)re1[k]; g.v[i][9 + k] = (float)re2[k];
+      }
+      const double qS = 0.5 * c.rho * c.fin_area[i];
+      g.v[i][12] = (float)(qS * c.fin_cl[i]);
+      g.v[i][13] = (float)(qS * c.fin_cd0[i]);
+      g.v[i][14] = (float)(qS * c.fin_cda[i]);
+      g.v[i][15] = (float)c.act_range[i];
+    } else if (c.act_kind[i] == MG_ACT_TILT) {
+      const double* d = c.thr_dir[i];
+      double rd[3], ad[3], rad[3], ra[3];
+      crs(r, d, rd);
+      crs(a, d, ad);
+      crs(r, ad, rad);
+      crs(r, a, ra);
+      const double adot = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
+      for (int k = 0; k < 3; ++k) {
+        g.v[i][k] = (float)d[k]; g.v[i][3 + k] = (float)rd[k];
+        g.v[i][6 + k] = (float)ad[k]; g.v[i][9 + k] = (float)rad[k];
+        g.v[i][12 + k] = (float)(adot * a[k]); g.v[i][15 + k] = (float)(adot * ra[k]);
+      }
+      g.v[i][18] = (float)c.act_link[i];
+      g.v[i][19] = (float)c.act_range[c.act_link[i]];
+    }
+  }
+  return g;
 }
 
 static void alpha_of(const mg_class_desc& c, double h, double* a) {
@@ -129,10 +212,12 @@ static void alpha_of(const mg_class_desc& c, double h, double* a) {
   for (int i = 0; i < c.n_thr; ++i) a[i] = c.T_rotor[i] > 0.0 ? 1.0 - std::exp(-h / c.T_rotor[i]) : 1.0;
 }
 
-// Allocation matrix B = [d_i ; r_i x d_i] (FP64).
+// Allocation matrix B = [d_i ; r_i x d_i] of the fixed propellers (FP64);
+// the columns of other channels are zero.
 static void alloc_of(const mg_class_desc& c, double B[6][8]) {
   for (int k = 0; k < 6; ++k) for (int i = 0; i < 8; ++i) B[k][i] = 0.0;
   for (int i = 0; i < c.n_thr; ++i) {
+    if (c.act_kind[i] != MG_ACT_PROP) continue;
     const double* r = c.thr_pos[i];
     const double* d = c.thr_dir[i];
     B[0][i] = d[0]; B[1][i] = d[1]; B[2][i] = d[2];
@@ -142,20 +227,29 @@ static void alloc_of(const mg_class_desc& c, double B[6][8]) {
   }
 }
 
-// Segments ordered by thruster count (then class); tiles are numbered in that
-// order so that each thruster count owns one contiguous tile range.
+// Step variant of a class: 2 with the RK4 integrator, else 1 for a generic
+// class, 0 for a propeller-only class.
+static int class_var(const mg_sim* sim, int c) {
+  if (sim->cfg.integrator == MG_INTEG_RK4) return 2;
+  return generic_class(sim->classes[c]) ? 1 : 0;
+}
+
+// Segments ordered by step variant, then thruster count (then class); tiles
+// are numbered in that order so that each group owns one contiguous tile range.
 static void build_segs(mg_sim* sim) {
   sim->segs.clear();
   sim->groups.clear();
   int tiles = 0;
+  for (int var = 0; var < 3; ++var)
   for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
     Group g;
     g.nt = nt;
+    g.var = var;
     g.seg_lo = (int32_t)sim->segs.size();
     g.tile_lo = tiles;
     for (int c = 0; c < sim->n_classes; ++c) {
       const ClassLay& L = sim->lay[c];
-      if (L.n_envs == 0 || L.n_thr != nt) continue;
+      if (L.n_envs == 0 || L.n_thr != nt || class_var(sim, c) != var) continue;
       SegDesc sd;
       std::memset(&sd, 0, sizeof(sd));
       sd.tile_begin = tiles;
@@ -206,7 +300,7 @@ static int dev_alloc(mg_sim* sim, void** p, size_t bytes) {
 }
 
 static void free_all(mg_sim* sim) {
-  void* ps[] = {sim->d_state, sim->d_planes, sim->d_cls, sim->d_cls64, sim->d_nominal,
+  void* ps[] = {sim->d_state, sim->d_planes, sim->d_cls, sim->d_gen, sim->d_cls64, sim->d_nominal,
                 sim->d_segs, sim->d_status, sim->d_ckpt, sim->d_scratch, sim->d_stage};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -281,6 +375,10 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (cfg->task < 0 || cfg->task > 1 || cfg->reset.track_kind < 0 || cfg->reset.track_kind > 1)
     return bail(MG_ERR_INVALID_ARG);
   if (cfg->payload < 0 || cfg->payload > 1) return bail(MG_ERR_INVALID_ARG);
+  if (cfg->integrator != MG_INTEG_EULER && cfg->integrator != MG_INTEG_RK4) {
+    sim->err = "integrator must be MG_INTEG_EULER or MG_INTEG_RK4";
+    return bail(MG_ERR_INVALID_ARG);
+  }
   if (cfg->payload) {
     if (!cfg->per_env_params) {
       sim->err = "payload runs need per_env_params";
@@ -302,6 +400,10 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   for (int c = 0; c < sim->n_classes; ++c) {
     if (validate_class(sim, sim->classes[c], c) != MG_OK) return bail(MG_ERR_INVALID_ARG);
     if (sim->counts[c] < 0) return bail(MG_ERR_INVALID_ARG);
+    if (cfg->record_steps > 0 && (generic_class(sim->classes[c]) || cfg->integrator != MG_INTEG_EULER)) {
+      sim->err = "gradients need propeller-only classes and the Euler integrator (record_steps must be 0)";
+      return bail(MG_ERR_INVALID_ARG);
+    }
   }
   sim->h = cfg->dt / cfg->K;
   sim->ckpt_every = cfg->ckpt_every > 0 ? cfg->ckpt_every : 20;
@@ -336,6 +438,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if ((rc = dev_alloc(sim, (void**)&sim->d_state, sizeof(float) * st)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_planes, sizeof(float4) * sim->n_planes * slot)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_cls, sizeof(ClassF) * sim->n_classes)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_gen, sizeof(ClassG) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_cls64, sizeof(ClassD) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_nominal, sizeof(ClassNominal) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_segs, sizeof(SegDesc) * MG_MAX_CLASSES)) != MG_OK) return bail(rc);
@@ -359,8 +462,10 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   std::vector<ClassF> cf(sim->n_classes);
   std::vector<ClassD> cd(sim->n_classes);
   std::vector<ClassNominal> cn(sim->n_classes);
+  std::vector<ClassG> cg(sim->n_classes);
   for (int c = 0; c < sim->n_classes; ++c) {
     const mg_class_desc& d = sim->classes[c];
+    cg[c] = generic_table(d);
     double B[6][8], al[8];
     alloc_of(d, B);
     alpha_of(d, sim->h, al);
@@ -397,6 +502,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   ce = cudaMemcpy(sim->d_cls, cf.data(), sizeof(ClassF) * cf.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_cls64, cd.data(), sizeof(ClassD) * cd.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_nominal, cn.data(), sizeof(ClassNominal) * cn.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_gen, cg.data(), sizeof(ClassG) * cg.size(), cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "class upload: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
   if ((rc = upload_segs(sim)) != MG_OK) return bail(rc);
   // Rest state with nominal parameters.
@@ -465,6 +571,7 @@ static StepArgs step_args(mg_sim* sim) {
   a.ckpt_every = sim->ckpt_every;
   a.track = sim->cfg.task == 1;
   a.pay_plane = pay_plane(a.track);
+  a.gen = sim->d_gen;
   return a;
 }
 
@@ -474,7 +581,7 @@ static int grid_of(mg_sim* sim, const Group& g) {
   int b = sim->blocks_per_sm;
   if (b <= 0) {
     b = 1;
-    step_kernel_occupancy(g.nt, param_mode(sim), sim->cfg.task == 1, &b);
+    step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b);
     if (b < 1) b = 1;
   }
   return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
@@ -493,7 +600,7 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    CK(launch_step(a, g.nt, grid_of(sim, g), !first, st));
+    CK(launch_step(a, g.nt, g.var, grid_of(sim, g), !first, st));
     first = false;
   }
   return MG_OK;
@@ -617,6 +724,9 @@ int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, cons
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64 needs per_env_params");
   if (sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: not available for payload runs");
+  for (const Group& g : sim->groups)
+    if (g.var != 0)
+      return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: needs propeller-only classes and the Euler integrator");
   if (!actions_dev || !reward_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: bad arguments");
   Fp64Args a;
   std::memset(&a, 0, sizeof(a));
@@ -936,7 +1046,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   int occ = 1 << 30;
   for (const Group& g : sim->groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, param_mode(sim), sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
+    if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;

@@ -36,7 +36,7 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 }  // namespace mg
 
@@ -301,7 +301,7 @@ static bool tick_once(mg_server* s) {
   bool first = true;
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
-    launch_step(a, g.nt, std::min(g.tiles, 4 * s->num_sms), !first, st);
+    launch_step(a, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, st);
     first = false;
   }
   cudaEventRecord(s->ev1, st);
@@ -405,6 +405,8 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     const mg_class_desc& d = classes[c];
     if (d.n_thr < 1 || d.n_thr > 8 || !(d.mass > 0) || d.rg[0] != 0 || d.rg[1] != 0 || d.rg[2] != 0)
       return MG_ERR_INVALID_ARG;
+    for (int i = 0; i < d.n_thr; ++i)
+      if (d.act_kind[i] != MG_ACT_PROP) return MG_ERR_INVALID_ARG;   // serving runs propeller-only classes
   }
   mg_server* s = new mg_server();
   s->cfg = *cfg;

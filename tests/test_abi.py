@@ -111,3 +111,34 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
 def test_error_strings(lib):
     for code in (B.MG_OK, B.MG_ERR_INVALID_ARG, B.MG_ERR_OOM, B.MG_ERR_NONFINITE, B.MG_ERR_STATE):
         assert lib.mg_strerror(code)
+
+
+@pytest.mark.parametrize("bad", ["record_generic", "record_rk4", "integrator", "fin_chord", "tilt_link", "kind",
+                                 "fin_rho"])
+def test_create_rejects_bad_actuators_before_touching_the_device(lib, bad):
+    classes = [vehicles.lauv(), vehicles.tilt_hauv()]
+    counts, record, integ = [4, 4], 0, B.MG_INTEG_EULER
+    if bad == "record_generic":
+        record = 10
+    elif bad == "record_rk4":
+        classes, counts, record, integ = [vehicles.heavy8()], [4], 10, B.MG_INTEG_RK4
+    elif bad == "integrator":
+        integ = 7
+    elif bad == "fin_chord":
+        classes[0]["act_chord"] = [(0.0, 0.0, 0.0)] + [(0.0, 0.6, 0.8)] * 4   # not normal to the y/z span axes
+    elif bad == "tilt_link":
+        classes[1]["act_link"] = [0, 5, 6, 7, 0, 0, 0, 0]                    # a propeller, not a servo
+    elif bad == "kind":
+        classes[1]["act_kind"] = [3, 3, 3, 3, 1, 1, 1, 9]
+    elif bad == "fin_rho":
+        classes[0]["rho"] = 0.0
+    with pytest.raises(B.MGError) as e:
+        B.mg_create(classes, counts, 0.01, 1, True, dict(vehicles.HOVER), record_steps=record, integrator=integ)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+
+
+def test_server_refuses_generic_classes(lib):
+    with pytest.raises(B.MGError) as e:
+        B.mg_server_create([vehicles.heavy8(), vehicles.lauv()], dt=0.01, max_requests=4, max_queue=4)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+
