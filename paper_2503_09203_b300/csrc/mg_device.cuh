@@ -137,6 +137,11 @@ MG_HD void act_rotor(const ActT& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) { kf[i] = S(A.kf[i]); dz[i] = S(A.dz[i]); al[i] = S(A.alpha[i]); }
 }
+template <typename S, int NT, typename ActT>
+MG_HD void act_rotor_nodz(const ActT& A, S (&kf)[NT], S (&al)[NT]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) { kf[i] = S(A.kf[i]); al[i] = S(A.alpha[i]); }
+}
 
 
 // Intermediates of one substep kept for the vector-Jacobian product.
@@ -172,9 +177,14 @@ MG_HD void msincos(double x, double* s, double* c) { *s = sin(x); *c = cos(x); }
 // a1 + a2: actuator states (rotor speed or servo / fin angle, first-order
 // lag), propeller thrust f = k n|n| (0 in the dead zone; k = 0 for servos and
 // fins) and the fixed-direction part of the wrench tau = B f.
+// Whether the actuator table may hold a nonzero dead zone (the hot kernel's
+// shared-memory view knows per class; other tables are always tested).
+template <typename ActT>
+MG_HD bool dz_active(const ActT&) { return true; }
+
 template <typename S, int NT, typename ActT>
 MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S tau[6]) {
-  {
+  if (dz_active(A)) {
     S kf[NT], dz[NT], al[NT];
     act_rotor<S, NT>(A, kf, dz, al);
 #pragma unroll
@@ -182,6 +192,15 @@ MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S 
       x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
       const S an = mabs(x.n[i]);
       f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
+    }
+  } else {
+    // No dead zone in this class: |n| < 0 never holds.
+    S kf[NT], al[NT];
+    act_rotor_nodz<S, NT>(A, kf, al);
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+      f[i] = kf[i] * x.n[i] * mabs(x.n[i]);
     }
   }
 #pragma unroll

@@ -17,7 +17,7 @@ struct SegDesc {
   int32_t K;
   int32_t step0;        // serving: step counter of the request at launch
   int32_t n4;           // slots of the segment's storage (n_envs rounded up to 4)
-  int32_t pad0;
+  int32_t flags;        // bit 0: the class has a nonzero dead zone
   int64_t st_off;       // float offset of the segment's state planes
   int64_t act_off;      // float offset of the segment's [n4][n_thr] actions
   int64_t slot_off;     // first slot (obs / reward / parameter planes)
@@ -110,7 +110,7 @@ struct StepArgs {
   int32_t track;              // 1: every segment of the launch is a tracking run
   uint32_t* status;           // bit 0: non-finite state
   int32_t pay_plane;          // payload runs: first payload plane
-  int32_t pad1;
+  int32_t wait_first;         // 1: launched as a programmatic dependent of unrelated work; wait before reading
   const ClassG* gen;          // generic actuator tables (launches of generic classes)
 };
 

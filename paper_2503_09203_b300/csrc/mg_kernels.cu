@@ -197,9 +197,15 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
 #endif
 
 // Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
+// dz_on = 0: the class has no dead zone (the thrust skips the test).
+#ifndef MG_DZ_FLAG
+#define MG_DZ_FLAG 1
+#endif
 struct ActSmem {
   unsigned base;
+  unsigned dz_on;
 };
+__device__ __forceinline__ bool dz_active(const ActSmem& A) { return !MG_DZ_FLAG || A.dz_on != 0u; }
 enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
 
 template <int NT>
@@ -221,6 +227,11 @@ template <typename S, int NT>
 __device__ __forceinline__ void act_rotor(const ActSmem& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_DZ, dz);
+  lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
+}
+template <typename S, int NT>
+__device__ __forceinline__ void act_rotor_nodz(const ActSmem& A, S (&kf)[NT], S (&al)[NT]) {
+  lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
 
@@ -439,7 +450,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   const unsigned nvw = warp_envs(sd, local0, warp);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
-  const ActSmem A{smem_addr(s_act)};
+  const ActSmem A{smem_addr(s_act), (unsigned)(sd.flags & 1)};
 
 #if MG_PHYS_REGS
   static_assert(PM < 2, "payload runs stage their parameters in shared memory");
@@ -548,9 +559,9 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       for (int k = 0; k < sd.K; ++k) {
         unsigned pb = p_base, ab = A.base, gb = g_base;
         asm volatile("" : "+r"(pb), "+r"(ab), "+r"(gb));
-        const PV Pk(pb);
-        const ActSmem Ak{ab};
+        const ActSmem Ak{ab, A.dz_on};
         // Class-constant physics carries no current (zero by construction).
+        const PV Pk(pb);
         if constexpr (VAR == 0) {
           substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
         } else if constexpr (VAR == 1) {
@@ -653,6 +664,11 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
   __shared__ SegDesc s_seg[SEG_CACHE];
   // The next launch of a step (another thruster count, disjoint envs) may
   // start filling SMs as soon as this grid's blocks are resident.
+  // The first launch of a step may become resident while the previous step
+  // (same envs) finishes: it waits for that work to complete before it reads
+  // anything or lets its own dependents start, so that every later launch of
+  // the step also follows the whole previous step.
+  if (a.wait_first) asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if ((int)blockIdx.x >= a.n_tiles) return;
   const int n_seg = a.seg_hi - a.seg_lo;

@@ -265,6 +265,9 @@ static void build_segs(mg_sim* sim) {
       sd.h = (float)sim->h;
       sd.dt = (float)sim->cfg.dt;
       sd.track = sim->cfg.task == 1;
+      sd.flags = 0;
+      for (int i = 0; i < L.n_thr; ++i)
+        if (sim->classes[c].deadzone[i] != 0.0) sd.flags |= 1;
       double a[8];
       alpha_of(sim->classes[c], sim->h, a);
       for (int i = 0; i < 8; ++i) sd.alpha[i] = (float)a[i];
@@ -593,14 +596,34 @@ static bool misaligned(const void* p) { return p && ((uintptr_t)p & 15u) != 0; }
 // The first group is an ordinary launch (it waits for everything before it in
 // the stream); later groups touch disjoint envs and are programmatic
 // dependents, so they fill the SMs that the previous group's tail leaves idle.
+#ifndef MG_USE_PDL
+#define MG_USE_PDL 1
+#endif
+// When the whole step fits in one wave of resident blocks, the first group is
+// a programmatic dependent too: its blocks become resident while the previous
+// kernel drains and wait for it to complete before reading anything (the
+// launch latency is hidden). Larger steps launch it normally: its waiting
+// blocks would take SM slots from the previous step's pending blocks.
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
+  bool pdl_first = false;
+  if (MG_USE_PDL) {
+    int64_t tiles = 0, resident = INT64_MAX;
+    for (const Group& g : sim->groups) {
+      tiles += g.n_tiles;
+      int b = sim->blocks_per_sm;
+      if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
+      resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
+    }
+    pdl_first = tiles <= resident;
+  }
   bool first = true;
   for (const Group& g : sim->groups) {
     a.seg_lo = g.seg_lo;
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    CK(launch_step(a, g.nt, g.var, grid_of(sim, g), !first, st));
+    a.wait_first = first && pdl_first;
+    CK(launch_step(a, g.nt, g.var, grid_of(sim, g), !first || pdl_first, st));
     first = false;
   }
   return MG_OK;

@@ -211,6 +211,7 @@ static SegDesc seg_of(const Req& q) {
   sd.h = q.h;
   sd.dt = q.h * (float)q.r.K;
   sd.track = 0;
+  sd.flags = 1;   // dead zones always tested in serving
   for (int i = 0; i < 8; ++i) sd.alpha[i] = q.alpha[i];
   sd.seed = q.r.seed;
   return sd;
