@@ -1162,19 +1162,32 @@ static size_t step_smem(bool track) {
   return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
 }
 
+// Kernel attributes of a step instantiation: the largest dynamic shared
+// memory of its layouts (tracking), and the same shared-memory carveout for
+// every instantiation so that blocks of different launches can share an SM.
+#ifndef MG_CARVEOUT_MAX
+#define MG_CARVEOUT_MAX 1
+#endif
+template <int NT, int PM, int VAR>
+static cudaError_t step_attrs() {
+  static bool done = false;   // per instantiation, per process (one device)
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem<NT, PM>(true));
+  if (e == cudaSuccess && MG_CARVEOUT_MAX)
+    e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
 template <int NT, int PM, int VAR>
 static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
-  static bool attr_set = false;   // per instantiation, per process (one device)
   const size_t smem = step_smem<NT, PM>(a.track != 0);
-  if (!attr_set) {
-    // The largest layout (tracking) bounds every launch of this instantiation.
-    cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem<NT, PM>(true));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = step_attrs<NT, PM, VAR>();
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(STEP_BLK);
@@ -1245,8 +1258,7 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
 
 template <int NT, int PM, int VAR>
 static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem<NT, PM>(true));
+  cudaError_t e = step_attrs<NT, PM, VAR>();
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PM, VAR>, STEP_BLK,
                                                        step_smem<NT, PM>(track));

@@ -599,31 +599,82 @@ static bool misaligned(const void* p) { return p && ((uintptr_t)p & 15u) != 0; }
 #ifndef MG_USE_PDL
 #define MG_USE_PDL 1
 #endif
-// When the whole step fits in one wave of resident blocks, the first group is
-// a programmatic dependent too: its blocks become resident while the previous
-// kernel drains and wait for it to complete before reading anything (the
-// launch latency is hidden). Larger steps launch it normally: its waiting
-// blocks would take SM slots from the previous step's pending blocks.
-static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
-  bool pdl_first = false;
-  if (MG_USE_PDL) {
-    int64_t tiles = 0, resident = INT64_MAX;
-    for (const Group& g : sim->groups) {
-      tiles += g.n_tiles;
-      int b = sim->blocks_per_sm;
-      if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
-      resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
-    }
-    pdl_first = tiles <= resident;
+// Up to this many waves of tiles per step, the groups of a step (one kernel
+// per thruster count and variant) share one wave of resident blocks: group g
+// gets a grid proportional to its estimated work (tiles x FLOPs per
+// env-step; one block per tile when all tiles fit), every launch is a
+// programmatic dependent of the one before, so the groups run side by side
+// and finish together; the first launch waits for the previous kernel of the
+// stream (the previous step, same envs) before it reads anything or lets the
+// step's other launches start. Larger steps launch the groups one after the
+// other with full persistent grids (each group alone on the SMs runs faster
+// than three interleaved), later groups as programmatic dependents that fill
+// the previous group's tail.
+#ifndef MG_CORESIDENT_WAVES
+#define MG_CORESIDENT_WAVES 6
+#endif
+static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
+  const int n = (int)sim->groups.size();
+  grid.assign(n, 1);
+  int64_t resident = INT64_MAX, tiles = 0;
+  std::vector<double> w(n);
+  double wsum = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const Group& g = sim->groups[i];
+    int b = sim->blocks_per_sm;
+    if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
+    resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
+    double sub = 0.0, obs = 0.0;
+    mg_count_flops(g.nt, sim->cfg.per_env_params, &sub, &obs, nullptr);
+    w[i] = (double)g.n_tiles * ((g.var == 2 ? 4.0 : 1.0) * sim->cfg.K * sub + obs);
+    wsum += w[i];
+    tiles += g.n_tiles;
   }
+  if (!MG_USE_PDL || resident < n || tiles > MG_CORESIDENT_WAVES * resident) return false;
+  if (tiles <= resident) {
+    for (int i = 0; i < n; ++i) grid[i] = sim->groups[i].n_tiles;
+    return true;
+  }
+  int64_t used = 0;
+  for (int i = 0; i < n; ++i) {
+    grid[i] = std::max(1, std::min(sim->groups[i].n_tiles, (int)(resident * w[i] / wsum)));
+    used += grid[i];
+  }
+  // Hand out what rounding left (or take back what the minimum of one added)
+  // by the estimated time of each group: tile rounds x work per tile.
+  auto cost = [&](int i, int blocks) {
+    const Group& g = sim->groups[i];
+    return (double)((g.n_tiles + blocks - 1) / blocks) * (w[i] / g.n_tiles);
+  };
+  while (used > resident) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (grid[i] > 1 && (best < 0 || cost(i, grid[i] - 1) < cost(best, grid[best] - 1))) best = i;
+    if (best < 0) break;
+    grid[best]--; used--;
+  }
+  while (used < resident) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (grid[i] < sim->groups[i].n_tiles && (best < 0 || cost(i, grid[i]) > cost(best, grid[best]))) best = i;
+    if (best < 0) break;
+    grid[best]++; used++;
+  }
+  return true;
+}
+
+static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
+  std::vector<int> grid;
+  const bool cores = coresident_grids(sim, grid);
   bool first = true;
-  for (const Group& g : sim->groups) {
+  for (size_t i = 0; i < sim->groups.size(); ++i) {
+    const Group& g = sim->groups[i];
     a.seg_lo = g.seg_lo;
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    a.wait_first = first && pdl_first;
-    CK(launch_step(a, g.nt, g.var, grid_of(sim, g), !first || pdl_first, st));
+    a.wait_first = first && cores;
+    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores, st));
     first = false;
   }
   return MG_OK;
