@@ -266,7 +266,11 @@ int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream);
 
 /* Host-buffer variant of mg_step for callers without device memory: copies
  * actions (host, as for mg_step) in, steps, copies obs/reward (host, may be
- * NULL) out, all on `stream`, and synchronises it. Host buffers should be
+ * NULL) out, and returns when all of it is done. The envs are cut into chunks
+ * of consecutive tiles: actions of chunk c are copied in on a library stream
+ * while chunk c-1 steps on `stream` and chunk c-2's results are copied out on
+ * another library stream, so that copies in both directions overlap. Work
+ * queued on `stream` before the call completes first. Host buffers should be
  * pinned for asynchronous copies. */
 int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float* obs_host, float* reward_host,
                  mg_stream_t stream);

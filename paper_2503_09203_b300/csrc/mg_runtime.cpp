@@ -78,6 +78,9 @@ struct mg_sim {
   int32_t rec_T = 0;           // steps of the last recorded rollout (0: none)
   size_t bytes = 0;
   std::string err;
+  // mg_step_host: copy streams and events of the chunked pipeline.
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> host_ev;
 };
 
 struct mg_graph {
@@ -523,6 +526,9 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
 int mg_destroy(mg_sim* sim) {
   if (!sim) return MG_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
+  for (cudaEvent_t e : sim->host_ev) cudaEventDestroy(e);
+  if (sim->s_in) cudaStreamDestroy(sim->s_in);
+  if (sim->s_out) cudaStreamDestroy(sim->s_out);
   free_all(sim);
   delete sim;
   return MG_OK;
@@ -726,6 +732,15 @@ int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream) {
   return launch_groups(sim, a, (cudaStream_t)stream);
 }
 
+// mg_step_host pipeline: the step is cut into chunks of at most this many
+// tiles (one thruster-count group, contiguous tiles); chunk c's actions are
+// copied in on one stream while chunk c-1 steps on the caller's stream and
+// chunk c-2's observations are copied out on a third (host-to-device and
+// device-to-host copies overlap on the link).
+#ifndef MG_HOST_CHUNK_TILES
+#define MG_HOST_CHUNK_TILES 512
+#endif
+
 int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float* obs_host, float* reward_host,
                  mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
@@ -742,11 +757,72 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   float* d_obs = d_act + (size_t)n_steps * sim->act_floats;
   float* d_rew = d_obs + (size_t)sim->n_slots * 13;
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(d_act, actions_host, sizeof(float) * n_steps * sim->act_floats, cudaMemcpyHostToDevice, st));
-  int rc = mg_step(sim, d_act, n_steps, obs_host ? d_obs : nullptr, reward_host ? d_rew : nullptr, stream);
-  if (rc != MG_OK) return rc;
-  if (obs_host) CK(cudaMemcpyAsync(obs_host, d_obs, sizeof(float) * sim->n_slots * 13, cudaMemcpyDeviceToHost, st));
-  if (reward_host) CK(cudaMemcpyAsync(reward_host, d_rew, sizeof(float) * sim->n_slots, cudaMemcpyDeviceToHost, st));
+  if (!sim->s_in) CK(cudaStreamCreateWithFlags(&sim->s_in, cudaStreamNonBlocking));
+  if (!sim->s_out) CK(cudaStreamCreateWithFlags(&sim->s_out, cudaStreamNonBlocking));
+  // Chunks: (group, first tile, tiles).
+  struct Chunk { int g, t0, nt; };
+  std::vector<Chunk> chunks;
+  for (int gi = 0; gi < (int)sim->groups.size(); ++gi)
+    for (int t = 0; t < sim->groups[gi].n_tiles; t += MG_HOST_CHUNK_TILES)
+      chunks.push_back({gi, t, std::min(MG_HOST_CHUNK_TILES, sim->groups[gi].n_tiles - t)});
+  const size_t n_ev = 2 * chunks.size() + 1;
+  while (sim->host_ev.size() < n_ev) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    sim->host_ev.push_back(e);
+  }
+  cudaEvent_t ev_entry = sim->host_ev[0];
+  CK(cudaEventRecord(ev_entry, st));   // earlier work on the caller's stream
+  CK(cudaStreamWaitEvent(sim->s_in, ev_entry, 0));
+  CK(cudaStreamWaitEvent(sim->s_out, ev_entry, 0));
+  const size_t pitch = sizeof(float) * (size_t)sim->act_floats;
+  StepArgs a = step_args(sim);
+  a.actions = d_act;
+  a.n_steps = n_steps;
+  a.obs = obs_host ? d_obs : nullptr;
+  a.reward = reward_host ? d_rew : nullptr;
+  a.act_stride = sim->act_floats;
+  for (size_t c = 0; c < chunks.size(); ++c) {
+    const Chunk& ch = chunks[c];
+    const Group& g = sim->groups[ch.g];
+    const int tile_lo = g.tile_lo + ch.t0, tile_hi = tile_lo + ch.nt;
+    cudaEvent_t ev_in = sim->host_ev[1 + 2 * c], ev_done = sim->host_ev[2 + 2 * c];
+    // Env ranges of the chunk, per segment of the group.
+    struct Range { int64_t act0, nact, slot0, nslot; };
+    std::vector<Range> ranges;
+    for (int si = g.seg_lo; si < g.seg_hi; ++si) {
+      const SegDesc& sd = sim->segs[si];
+      const int seg_tiles = (sd.n4 + sim->threads - 1) / sim->threads;
+      const int lo = std::max(tile_lo, sd.tile_begin), hi = std::min(tile_hi, sd.tile_begin + seg_tiles);
+      if (lo >= hi) continue;
+      const int64_t s0 = (int64_t)(lo - sd.tile_begin) * sim->threads;
+      const int64_t s1 = std::min<int64_t>((int64_t)(hi - sd.tile_begin) * sim->threads, sd.n4);
+      ranges.push_back({sd.act_off + s0 * sd.n_thr, (s1 - s0) * sd.n_thr, sd.slot_off + s0, s1 - s0});
+    }
+    for (const Range& r : ranges)
+      CK(cudaMemcpy2DAsync(d_act + r.act0, pitch, actions_host + r.act0, pitch, sizeof(float) * r.nact, n_steps,
+                           cudaMemcpyHostToDevice, sim->s_in));
+    CK(cudaEventRecord(ev_in, sim->s_in));
+    CK(cudaStreamWaitEvent(st, ev_in, 0));
+    a.seg_lo = g.seg_lo;
+    a.seg_hi = g.seg_hi;
+    a.tile_lo = tile_lo;
+    a.n_tiles = ch.nt;
+    a.wait_first = 0;
+    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, grid_of(sim, g))), false, st));
+    CK(cudaEventRecord(ev_done, st));
+    CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
+    for (const Range& r : ranges) {
+      if (obs_host)
+        CK(cudaMemcpyAsync(obs_host + r.slot0 * 13, d_obs + r.slot0 * 13, sizeof(float) * r.nslot * 13,
+                           cudaMemcpyDeviceToHost, sim->s_out));
+      if (reward_host)
+        CK(cudaMemcpyAsync(reward_host + r.slot0, d_rew + r.slot0, sizeof(float) * r.nslot,
+                           cudaMemcpyDeviceToHost, sim->s_out));
+    }
+  }
+  sim->rec_T = 0;
+  CK(cudaStreamSynchronize(sim->s_out));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
 }

@@ -288,6 +288,29 @@ def test_host_buffer_step_equals_device_step():
     sim.close()
 
 
+def test_host_buffer_step_chunked_multi_step_equals_device_step():
+    """Sizes that cut every group into several copy/step chunks, 3 steps per call."""
+    classes = vehicles.five_classes()
+    counts = [70001, 3, 140001, 5, 9]
+    sim = make_sim(classes, counts, K=1, reset=dict(vehicles.HOVER_DR))
+    sim.reset(seed=3)
+    s0 = sim.get_state()
+    a_dev = (torch.rand(3, sim.action_floats, device="cuda") * 2 - 1).contiguous()
+    B.mg_step(sim.handle, a_dev, 3, sim.obs, sim.reward)
+    torch.cuda.synchronize()
+    s_dev, o_dev, r_dev = sim.get_state(), sim.obs.cpu().numpy().copy(), sim.reward.cpu().numpy().copy()
+    sim.set_state(s0)
+    a_host = a_dev.cpu().pin_memory()
+    o_host = torch.full((sim.n_slots, 13), 7.0).pin_memory()
+    r_host = torch.full((sim.n_slots,), 7.0).pin_memory()
+    B.mg_step_host(sim.handle, a_host, 3, o_host, r_host)
+    assert np.array_equal(sim.get_state(), s_dev)
+    assert np.array_equal(o_host.numpy(), o_dev)
+    assert np.array_equal(r_host.numpy(), r_dev)
+    sim.status()
+    sim.close()
+
+
 def test_graph_replay_and_autotune_keep_results():
     classes = vehicles.five_classes()
     counts = [100, 50, 60, 70, 80]
