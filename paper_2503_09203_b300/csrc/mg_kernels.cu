@@ -201,11 +201,15 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
 #ifndef MG_DZ_FLAG
 #define MG_DZ_FLAG 1
 #endif
-struct ActSmem {
+// DZF: the kernel carries a dead-zone-free thrust path (class-constant
+// propellers only: in the other variants the second path costs registers).
+template <bool DZF>
+struct ActSmemT {
   unsigned base;
   unsigned dz_on;
 };
-__device__ __forceinline__ bool dz_active(const ActSmem& A) { return !MG_DZ_FLAG || A.dz_on != 0u; }
+template <bool DZF>
+__device__ __forceinline__ bool dz_active(const ActSmemT<DZF>& A) { return !(MG_DZ_FLAG && DZF) || A.dz_on != 0u; }
 enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
 
 template <int NT>
@@ -219,18 +223,18 @@ __device__ __forceinline__ void lds_vec(unsigned a, float (&r)[NT]) {
     if (4 * q + 3 < NT) r[(4 * q + 3) % NT] = v.w;
   }
 }
-template <typename S, int NT>
-__device__ __forceinline__ void act_row(const ActSmem& A, int k, S (&r)[NT]) {
+template <typename S, int NT, bool DZF>
+__device__ __forceinline__ void act_row(const ActSmemT<DZF>& A, int k, S (&r)[NT]) {
   lds_vec<NT>(A.base + 4 * (SA_ALLOC + 8 * k), r);
 }
-template <typename S, int NT>
-__device__ __forceinline__ void act_rotor(const ActSmem& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF>
+__device__ __forceinline__ void act_rotor(const ActSmemT<DZF>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_DZ, dz);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
-template <typename S, int NT>
-__device__ __forceinline__ void act_rotor_nodz(const ActSmem& A, S (&kf)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF>
+__device__ __forceinline__ void act_rotor_nodz(const ActSmemT<DZF>& A, S (&kf)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
@@ -450,6 +454,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   const unsigned nvw = warp_envs(sd, local0, warp);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
+  using ActSmem = ActSmemT<PM == 0 && VAR == 0>;
   const ActSmem A{smem_addr(s_act), (unsigned)(sd.flags & 1)};
 
 #if MG_PHYS_REGS
@@ -1163,30 +1168,37 @@ static size_t step_smem(bool track) {
 }
 
 // Kernel attributes of a step instantiation: the largest dynamic shared
-// memory of its layouts (tracking), and the same shared-memory carveout for
-// every instantiation so that blocks of different launches can share an SM.
-#ifndef MG_CARVEOUT_MAX
-#define MG_CARVEOUT_MAX 1
-#endif
+// memory of its layouts (tracking).
 template <int NT, int PM, int VAR>
 static cudaError_t step_attrs() {
   static bool done = false;   // per instantiation, per process (one device)
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<NT, PM>(true));
-  if (e == cudaSuccess && MG_CARVEOUT_MAX)
-    e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// Shared-memory carveout of the next launch of an instantiation: the largest
+// (`shared_sm`) or the driver's default; set only when it changes.
+template <int NT, int PM, int VAR>
+static cudaError_t step_carveout(bool shared_sm) {
+  static int current = -2;   // per instantiation, per process (one device)
+  const int want = shared_sm ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault;
+  if (want == current) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributePreferredSharedMemoryCarveout, want);
+  if (e == cudaSuccess) current = want;
   return e;
 }
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
 template <int NT, int PM, int VAR>
-static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cudaStream_t st) {
+static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, bool shared_sm, cudaStream_t st) {
   const size_t smem = step_smem<NT, PM>(a.track != 0);
   cudaError_t e = step_attrs<NT, PM, VAR>();
+  if (e == cudaSuccess) e = step_carveout<NT, PM, VAR>(shared_sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1202,8 +1214,9 @@ static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, cu
 }
 
 template <int PM, int VAR>
-static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool dependent, cudaStream_t st) {
-#define MG_L(N) return launch_step_t<N, PM, VAR>(a, grid, dependent, st)
+static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool dependent, bool shared_sm,
+                                  cudaStream_t st) {
+#define MG_L(N) return launch_step_t<N, PM, VAR>(a, grid, dependent, shared_sm, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;
@@ -1212,18 +1225,19 @@ static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool depe
 // Step launch of one class group: thruster count nt, parameter source
 // a.per_env (0 class, 1 per-env, 2 payload), variant var (0 propellers with
 // Euler, 1 generic actuators with Euler, 2 RK4).
-cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, cudaStream_t st) {
+cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, bool shared_sm,
+                        cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
   switch (a.per_env * 3 + var) {
-    case 0: return launch_step_pv<0, 0>(a, nt, grid, dependent, st);
-    case 1: return launch_step_pv<0, 1>(a, nt, grid, dependent, st);
-    case 2: return launch_step_pv<0, 2>(a, nt, grid, dependent, st);
-    case 3: return launch_step_pv<1, 0>(a, nt, grid, dependent, st);
-    case 4: return launch_step_pv<1, 1>(a, nt, grid, dependent, st);
-    case 5: return launch_step_pv<1, 2>(a, nt, grid, dependent, st);
-    case 6: return launch_step_pv<2, 0>(a, nt, grid, dependent, st);
-    case 7: return launch_step_pv<2, 1>(a, nt, grid, dependent, st);
-    case 8: return launch_step_pv<2, 2>(a, nt, grid, dependent, st);
+    case 0: return launch_step_pv<0, 0>(a, nt, grid, dependent, shared_sm, st);
+    case 1: return launch_step_pv<0, 1>(a, nt, grid, dependent, shared_sm, st);
+    case 2: return launch_step_pv<0, 2>(a, nt, grid, dependent, shared_sm, st);
+    case 3: return launch_step_pv<1, 0>(a, nt, grid, dependent, shared_sm, st);
+    case 4: return launch_step_pv<1, 1>(a, nt, grid, dependent, shared_sm, st);
+    case 5: return launch_step_pv<1, 2>(a, nt, grid, dependent, shared_sm, st);
+    case 6: return launch_step_pv<2, 0>(a, nt, grid, dependent, shared_sm, st);
+    case 7: return launch_step_pv<2, 1>(a, nt, grid, dependent, shared_sm, st);
+    case 8: return launch_step_pv<2, 2>(a, nt, grid, dependent, shared_sm, st);
     default: return cudaErrorInvalidValue;
   }
 }

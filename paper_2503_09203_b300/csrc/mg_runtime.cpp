@@ -17,7 +17,8 @@
 #include "mg_payload.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, bool shared_sm,
+                        cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
@@ -669,6 +670,15 @@ static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
   return true;
 }
 
+// Shared-memory carveout of a launch: the largest when the step's groups share
+// SMs (blocks of different launches must fit one SM configuration) and for
+// class-constant propeller steps without tracking (measured faster: their
+// class-group launches overlap at the tails); the driver's default otherwise
+// (measured faster for per-env, tracking and generic-actuator steps).
+static bool carveout_max(const mg_sim* sim, const Group& g, bool cores) {
+  return cores || (param_mode(sim) == 0 && g.var == 0 && sim->cfg.task != 1);
+}
+
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
   std::vector<int> grid;
   const bool cores = coresident_grids(sim, grid);
@@ -680,7 +690,8 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
     a.wait_first = first && cores;
-    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores, st));
+    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores, carveout_max(sim, g, cores),
+                   st));
     first = false;
   }
   return MG_OK;
@@ -809,7 +820,8 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     a.tile_lo = tile_lo;
     a.n_tiles = ch.nt;
     a.wait_first = 0;
-    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, grid_of(sim, g))), false, st));
+    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, grid_of(sim, g))), false,
+                   carveout_max(sim, g, false), st));
     CK(cudaEventRecord(ev_done, st));
     CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
     for (const Range& r : ranges) {
