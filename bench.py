@@ -383,7 +383,7 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
             "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb}
 
 
-def serving_bench(plain_rate, n_req=300, load=0.7, seed=11, horizon_max=200):
+def serving_bench(plain_rate, n_req=10000, load=0.7, seed=11, horizon_max=1000):
     from paper_2503_09203_b300 import binding as B
     from paper_2503_09203_b300 import vehicles
     rng = np.random.default_rng(seed)
@@ -396,7 +396,7 @@ def serving_bench(plain_rate, n_req=300, load=0.7, seed=11, horizon_max=200):
     mean_work = np.mean([r[1] * r[2] * r[3] for r in reqs])  # env-substeps per request
     # Offered load: `load` x the plain path's substep throughput.
     lam = load * plain_rate / mean_work
-    srv = B.mg_server_create(classes, 0.01, budget_bytes=2 << 30, max_requests=1024, reset=dict(vehicles.HOVER))
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=8 << 30, max_requests=4096, reset=dict(vehicles.HOVER))
     t0 = time.perf_counter()
     ids = []
     t_next = t0
@@ -408,6 +408,8 @@ def serving_bench(plain_rate, n_req=300, load=0.7, seed=11, horizon_max=200):
     B.mg_server_wait_idle(srv, 600.0)
     wall = time.perf_counter() - t0
     st = B.mg_server_stats_get(srv)
+    for i in ids:
+        B.mg_server_release(srv, i)
     B.mg_server_destroy(srv)
     return {"requests": n_req, "offered_load": load, "arrival_rate_per_s": lam, "wall_s": wall,
             "env_steps_per_s": st["env_steps"] / wall, "busy_env_steps_per_s": st["env_steps"] / max(st["busy_seconds"], 1e-9),
@@ -587,7 +589,7 @@ def main():
         line["hetero_graph"] = hetero_graph_bench(stream)
         line["adjoint"] = adjoint_bench(stream)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)
-        line["serving"] = serving_bench(plain_substeps)
+        line["serving"] = [serving_bench(plain_substeps, load=0.7), serving_bench(plain_substeps, load=0.9)]
     else:
         sim.close()
     print(json.dumps(line))
