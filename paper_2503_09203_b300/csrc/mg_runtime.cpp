@@ -671,17 +671,21 @@ static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
 }
 
 // Shared-memory carveout of a launch: the largest when the step's groups share
-// SMs (blocks of different launches must fit one SM configuration) and for
-// class-constant propeller steps without tracking (measured faster: their
-// class-group launches overlap at the tails); the driver's default otherwise
-// (measured faster for per-env, tracking and generic-actuator steps).
-static bool carveout_max(const mg_sim* sim, const Group& g, bool cores) {
-  return cores || (param_mode(sim) == 0 && g.var == 0 && sim->cfg.task != 1);
+// SMs (side-by-side launches with more blocks than SMs: blocks of different
+// launches must fit one SM configuration) and for class-constant propeller
+// steps without tracking (measured faster: their class-group launches overlap
+// at the tails); the driver's default otherwise (measured faster for per-env,
+// tracking and generic-actuator steps).
+static bool carveout_max(const mg_sim* sim, const Group& g, bool shared_sm) {
+  return shared_sm || (param_mode(sim) == 0 && g.var == 0 && sim->cfg.task != 1);
 }
 
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
   std::vector<int> grid;
   const bool cores = coresident_grids(sim, grid);
+  int64_t blocks = 0;
+  for (int b : grid) blocks += b;
+  const bool shared_sm = cores && blocks > sim->num_sms;
   bool first = true;
   for (size_t i = 0; i < sim->groups.size(); ++i) {
     const Group& g = sim->groups[i];
@@ -690,8 +694,8 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
     a.wait_first = first && cores;
-    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores, carveout_max(sim, g, cores),
-                   st));
+    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores,
+                   carveout_max(sim, g, shared_sm), st));
     first = false;
   }
   return MG_OK;
