@@ -103,17 +103,6 @@ __device__ __forceinline__ void load_phys(const float4* planes, int64_t n_slots,
   P.W = v[PAR_W]; P.B = v[PAR_B];
 }
 
-__device__ __forceinline__ void phys_from_array(const float* v, Phys<float>& P) {
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    P.minv[j] = v[PAR_MINV + j]; P.A[j] = v[PAR_A + j]; P.dl[j] = v[PAR_DL + j]; P.dq[j] = v[PAR_DQ + j];
-  }
-  P.m = v[PAR_M];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) { P.Ig[j] = v[PAR_IG + j]; P.rb[j] = v[PAR_RB + j]; P.Vc[j] = v[PAR_VC + j]; }
-  P.W = v[PAR_W]; P.B = v[PAR_B];
-}
-
 // Segment of a tile: binary search over tile_begin (segments sorted). The
 // table may live in global or in shared memory, so the loads are generic.
 __device__ __forceinline__ int find_seg(const SegDesc* segs, int n_segs, int tile) {
@@ -156,23 +145,15 @@ __device__ __forceinline__ void load_actions(const float* base, float (&a)[NT]) 
 // ---------------------------------------------------------------------------
 // Shared-memory views read at the point of use. Class constants and per-env
 // parameters stay in shared memory (vector loads for the actuator table)
-// instead of occupying registers across the substep loop; the loads are
-// volatile so that they are not hoisted out of the loop.
+// instead of occupying registers across the substep loop. The loads are plain
+// (non-volatile) inline PTX, free to be scheduled within a substep; the step
+// loop passes them a base address made opaque once per substep, so that they
+// are neither hoisted out of the loop nor moved above the barrier that
+// follows a table rewrite.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
-#ifndef MG_SMEM_LAUNDER
-#define MG_SMEM_LAUNDER 1
-#endif
-#ifndef MG_SMEM_PLAIN
-#define MG_SMEM_PLAIN MG_SMEM_LAUNDER
-#endif
-#ifndef MG_PHYS_REGS
-#define MG_PHYS_REGS 0
-#endif
-#if MG_SMEM_PLAIN
-// Plain (non-volatile) shared loads: the compiler may schedule or hoist them.
 __device__ __forceinline__ float lds1(unsigned a) {
   float v;
   asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
@@ -183,18 +164,6 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
   asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
 }
-#else
-__device__ __forceinline__ float lds1(unsigned a) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ float4 lds4(unsigned a) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-  return v;
-}
-#endif
 
 // Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
 // dz_on = 0: the class has no dead zone (the thrust skips the test).
@@ -402,6 +371,25 @@ struct Stage {
 };
 constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
 
+// Class tables of segment `sd` into act (SA_DIM) and phys (PAR_DIM), and its
+// generic actuator table into gen (generic variants), by the block's threads.
+template <int VAR>
+__device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& sd, float* act, float* phys,
+                                             float* gen, int tid) {
+  const ClassF& cf = a.classes[sd.cls];
+  for (int k = tid; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
+    if (k < 48) act[k] = cf.alloc[k / 8][k % 8];
+    else if (k < 56) act[k] = cf.kf[k - 48];
+    else if (k < 64) act[k] = cf.dz[k - 56];
+    else if (k < 72) act[k] = sd.alpha[k - 64];
+    else phys[k - 72] = cf.phys[k - 72];
+  }
+  if (VAR) {
+    const float* g = reinterpret_cast<const float*>(a.gen + sd.cls);
+    for (int k = tid; k < GEN_FLOATS; k += STEP_BLK) gen[k] = g[k];
+  }
+}
+
 // Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
 // (a multiple of 4, > 0) envs start at local env index w0 of the segment.
 template <int NT, int PM>
@@ -440,8 +428,8 @@ __device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0,
 }
 
 template <int NT, int PM, int VAR>
-__device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, const float* s_act,
-                                          const float* s_phys, const float* s_gen, const float* buf, float* obs_w,
+__device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, unsigned s_act,
+                                          unsigned s_phys, unsigned s_gen, const float* buf, float* obs_w,
                                           float* s_par, int& n_emit) {
   constexpr bool PER_ENV = PM >= 1;
   using SG = Stage<NT>;
@@ -455,15 +443,12 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
   using ActSmem = ActSmemT<PM == 0 && VAR == 0>;
-  const ActSmem A{smem_addr(s_act), (unsigned)(sd.flags & 1)};
+  const ActSmem A{s_act, (unsigned)(sd.flags & 1)};
 
-#if MG_PHYS_REGS
-  static_assert(PM < 2, "payload runs stage their parameters in shared memory");
-#endif
   // Per-env parameters: plain per-env runs prefetch their 9 planes into
   // registers here (their loads overlap the stage reads below); payload runs
   // copy 15 planes straight to shared memory afterwards.
-  constexpr bool STAGE_PAR = PM == 1 && !MG_PHYS_REGS;
+  constexpr bool STAGE_PAR = PM == 1;
   float4 pv[STAGE_PAR ? PAR_PLANES : 1];
   if (STAGE_PAR && valid) {
 #pragma unroll
@@ -516,21 +501,10 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
     }
   }
-#if MG_PHYS_REGS
-  // Parameters held in registers for the whole tile.
-  Phys<float> P;
-  if (PER_ENV) {
-    if (valid) load_phys(a.planes, a.n_slots, slot, P);
-  } else {
-    phys_from_array(s_phys, P);
-  }
-#else
   // Each thread reads only its own parameter column: no barrier needed.
   using PV = std::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
-  const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : smem_addr(s_phys);
-  const unsigned g_base = smem_addr(s_gen);
-  const PV P(p_base);
-#endif
+  const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : s_phys;
+  const unsigned g_base = s_gen;
   const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
   for (int t = 0; t < n_out_steps; ++t) {
     if (valid && a.n_steps > 0) {
@@ -558,7 +532,6 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 #pragma unroll
         for (int j = 0; j < 21; ++j) ck[j * a.n_slots] = (j < 13 + NT) ? f[j % (13 + NT)] : 0.0f;
       }
-#if MG_SMEM_LAUNDER && !MG_PHYS_REGS
       // Shared-memory bases made opaque once per substep: loads may be
       // scheduled freely inside a substep but not hoisted out of the loop.
       for (int k = 0; k < sd.K; ++k) {
@@ -575,10 +548,6 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
           substep_rk4<float, NT, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, GenSmem{gb});
         }
       }
-#else
-      static_assert(VAR == 0, "generic actuators and RK4 read their tables from shared memory");
-      for (int k = 0; k < sd.K; ++k) substep<float, NT, false, ActSmem, decltype(P), PER_ENV>(x, c, P, A, sd.h, nullptr);
-#endif
     }
     const bool emit = a.obs_every || t == n_out_steps - 1;
     if (emit) {
@@ -727,20 +696,10 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
     }
     const SegDesc& sd = segs[si];
     if (si != prev_seg) {
-      // Class constants change: rewrite them between two block barriers.
+      // Class constants change: rewrite them between two block barriers
+      // (every warp of the block walks the same tiles).
       __syncthreads();
-      const ClassF& cf = a.classes[sd.cls];
-      for (int k = tid; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
-        if (k < 48) s_act[k] = cf.alloc[k / 8][k % 8];
-        else if (k < 56) s_act[k] = cf.kf[k - 48];
-        else if (k < 64) s_act[k] = cf.dz[k - 56];
-        else if (k < 72) s_act[k] = sd.alpha[k - 64];
-        else s_phys[k - 72] = cf.phys[k - 72];
-      }
-      if (VAR) {
-        const float* g = reinterpret_cast<const float*>(a.gen + sd.cls);
-        for (int k = tid; k < GEN_FLOATS; k += STEP_BLK) s_gen[k % (VAR ? GEN_FLOATS : 4)] = g[k];
-      }
+      stage_tables<VAR>(a, sd, s_act, s_phys, s_gen, tid);
       __syncthreads();
       prev_seg = si;
     }
@@ -751,7 +710,7 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
       }
       use[b]++;
     }
-    step_tile<NT, PM, VAR>(a, sd, tile, s_act, s_phys, s_gen, b ? buf1 : buf0,
+    step_tile<NT, PM, VAR>(a, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
                            MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
