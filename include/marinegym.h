@@ -335,9 +335,19 @@ int mg_set_state(mg_sim* sim, const float* host, size_t bytes);
 int mg_get_params(const mg_sim* sim, double* host, size_t bytes);
 int mg_set_params(mg_sim* sim, const double* host, size_t bytes);
 
-/* Synchronise `stream`; return MG_ERR_NONFINITE (and clear the flag) if any
- * step since the last call produced a non-finite state, else MG_OK. */
+/* Synchronise `stream`; return MG_ERR_TIMEOUT if a bounded wait of a step
+ * kernel gave up (its results are invalid), else MG_ERR_NONFINITE if any step
+ * since the last call produced a non-finite state, else MG_OK; the flags are
+ * cleared. Every wait of the step kernel on its own copies gives up after 2 s,
+ * so a stalled copy ends the kernel with an error instead of a hang. */
 int mg_status(mg_sim* sim, mg_stream_t stream);
+
+/* Test hook for the failure path (no counterpart in the paper): one step
+ * launch in which no copies are issued, so every warp's wait runs out after
+ * limit_ns (0 < limit_ns <= 2 s) and the warp leaves with the timeout flag
+ * set; the state is not touched. The next mg_status returns MG_ERR_TIMEOUT and
+ * the simulator stays usable. Synchronises `stream`. */
+int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream);
 
 /* Choose threads per block and the number of resident blocks per SM of the
  * persistent rollout by timing candidates on `stream` (state is saved and

@@ -138,6 +138,7 @@ _SIGS = {
     "mg_set_payload": [_VP, _VP, C.c_size_t],
     "mg_set_params": [_VP, _VP, C.c_size_t],
     "mg_status": [_VP, _VP],
+    "mg_test_wait_timeout": [_VP, _U64, _VP],
     "mg_autotune": [_VP, _VP, C.POINTER(_I32), C.POINTER(_I32)],
     "mg_graph_capture": [_VP, _VP, _I32, _VP, _VP, _VP, C.POINTER(_VP)],
     "mg_graph_launch": [_VP, _VP],
@@ -376,6 +377,10 @@ def mg_set_payload(sim, payload: np.ndarray):
 
 def mg_status(sim, stream=None):
     return _check(lib().mg_status(sim, _stream(stream)), sim)
+
+
+def mg_test_wait_timeout(sim, limit_ns: int, stream=None):
+    return _check(lib().mg_test_wait_timeout(sim, int(limit_ns), _stream(stream)), sim)
 
 
 def mg_autotune(sim, stream=None):

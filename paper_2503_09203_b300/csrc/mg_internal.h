@@ -17,7 +17,7 @@ struct SegDesc {
   int32_t K;
   int32_t step0;        // serving: step counter of the request at launch
   int32_t n4;           // slots of the segment's storage (n_envs rounded up to 4)
-  int32_t flags;        // bit 0: the class has a nonzero dead zone
+  int32_t flags;        // bit 0: the class has a nonzero dead zone; bit 1: failure-path test, issue no copies
   int64_t st_off;       // float offset of the segment's state planes
   int64_t act_off;      // float offset of the segment's [n4][n_thr] actions
   int64_t slot_off;     // first slot (obs / reward / parameter planes)
@@ -28,7 +28,7 @@ struct SegDesc {
   float pad1;
   float alpha[8];
   uint64_t seed;        // serving: action seed
-  uint64_t pad2;
+  uint64_t wait_limit_ns;   // bound of the waits on this segment's copies (0: 2 s)
 };
 static_assert(sizeof(SegDesc) == 128, "SegDesc layout");
 

@@ -611,7 +611,8 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
 // tile into the warp's other stage buffer, and observation rows leave through
 // a per-warp bulk store. Warps never wait on one another except when the
 // class constants change. Every wait is bounded (2 s); a warp that gives up
-// sets bit 1 of the status word and leaves.
+// sets bit 1 of the status word and skips the rest of its tiles (it keeps
+// walking them, so every block barrier is still reached).
 // The RK4 variant keeps the stage point, the running sum and the substep's
 // start state live at once: it is compiled for 2 resident blocks per SM (up to
 // 255 registers) instead of spilling.
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
     const SegDesc& s0 = segs[find_seg(segs, n_seg, tile0)];
     const int64_t local0 = (int64_t)(tile0 - s0.tile_begin) * STEP_BLK;
     nvw_cur = warp_envs(s0, local0, warp);
-    if (lane == 0 && nvw_cur > 0)
+    if (lane == 0 && nvw_cur > 0 && !(s0.flags & 2))
       issue_warp_loads<NT, PM>(a, s0, local0 + warp * WENV, nvw_cur, buf0, full0);
   }
   int prev_seg = -1, n_emit = 0;
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
       const SegDesc& sn = segs[find_seg(segs, n_seg, tile_n)];
       const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
       nvw_next = warp_envs(sn, ln, warp);
-      if (lane == 0 && nvw_next > 0) {
+      if (lane == 0 && nvw_next > 0 && !failed && !(sn.flags & 2)) {
 #if MG_OBS_ALIAS
         // The buffer may still be the source of the previous tile's observation store.
         bulk_wait_read0();
@@ -703,15 +704,17 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
       __syncthreads();
       prev_seg = si;
     }
-    if (nvw_cur > 0) {
-      if (!mbar_wait_bounded(b ? full1 : full0, use[b] & 1u, kWaitLimitNs)) {
+    // A warp whose wait ran out stops computing and copying but stays in the
+    // loop, so that it still reaches every block barrier of the launch.
+    if (nvw_cur > 0 && !failed) {
+      if (mbar_wait_bounded(b ? full1 : full0, use[b] & 1u, sd.wait_limit_ns ? sd.wait_limit_ns : kWaitLimitNs))
+        use[b]++;
+      else
         failed = true;
-        break;
-      }
-      use[b]++;
     }
-    step_tile<NT, PM, VAR>(a, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
-                           MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
+    if (!failed)
+      step_tile<NT, PM, VAR>(a, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
+                             MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
     nvw_cur = nvw_next;

@@ -1177,6 +1177,35 @@ int mg_set_task(mg_sim* sim, const double* host, size_t bytes) {
   return MG_OK;
 }
 
+// Failure-path test: one step launch in which no copies are issued, so every
+// warp's first wait runs out after limit_ns and the warp leaves with bit 1 of
+// the status word set; no state is touched.
+int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (limit_ns == 0 || limit_ns > 2000000000ull) return fail(sim, MG_ERR_INVALID_ARG, "test_wait_timeout: limit in (0, 2 s]");
+  const size_t need = (size_t)sim->act_floats;
+  if (need > sim->stage_floats) {
+    if (sim->d_stage) { cudaFree(sim->d_stage); sim->bytes -= sim->stage_floats * sizeof(float); sim->d_stage = nullptr; }
+    sim->stage_floats = 0;
+    int rc = dev_alloc(sim, (void**)&sim->d_stage, need * sizeof(float));
+    if (rc != MG_OK) return rc;
+    sim->stage_floats = need;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // The segment table of this one launch marks every segment "issue no
+  // copies" with the given bound; the simulator's own table is put back after.
+  std::vector<SegDesc> test = sim->segs;
+  for (SegDesc& sd : test) { sd.flags |= 2; sd.wait_limit_ns = limit_ns; }
+  CK(cudaMemcpyAsync(sim->d_segs, test.data(), sizeof(SegDesc) * test.size(), cudaMemcpyHostToDevice, st));
+  StepArgs a = step_args(sim);
+  a.actions = sim->d_stage;
+  a.n_steps = 1;
+  int rc = launch_groups(sim, a, st);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice));
+  return rc;
+}
+
 int mg_status(mg_sim* sim, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize((cudaStream_t)stream));

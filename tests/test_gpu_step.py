@@ -6,6 +6,7 @@ an identical FP32 state, and trajectory-relative error <= 1e-3 over 1000 steps
 (error = ||x_gpu - x_ref|| / max(||x_ref||, 1), quaternion sign-aligned).
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -229,6 +230,35 @@ def test_nonfinite_state_is_reported_and_cleared():
     assert e.value.code == B.MG_ERR_NONFINITE
     sim.status()  # cleared
     sim.close()
+
+
+def test_wait_that_runs_out_is_reported_and_the_simulator_stays_usable():
+    """A step launch whose copies are never issued: every warp's bounded wait
+    gives up after 20 ms, the status reports a timeout, the state is untouched
+    and the next normal step matches a simulator that never saw the failure."""
+    classes = vehicles.five_classes()
+    counts = [300, 5, 130, 0, 64]
+    sims = [make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER_DR)) for _ in range(2)]
+    for s in sims:
+        s.reset(seed=8)
+    s0 = sims[0].get_state()
+    t0 = time.perf_counter()
+    B.mg_test_wait_timeout(sims[0].handle, 20_000_000)
+    assert time.perf_counter() - t0 < 10.0
+    with pytest.raises(B.MGError) as e:
+        sims[0].status()
+    assert e.value.code == B.MG_ERR_TIMEOUT
+    sims[0].status()   # cleared
+    assert np.array_equal(sims[0].get_state(), s0)
+    a = sims[0].pack_actions(workloads.actions(4, 1, sims[0].n_envs))
+    for s in sims:
+        s.step(a)
+    torch.cuda.synchronize()
+    assert np.array_equal(sims[0].get_state(), sims[1].get_state())
+    assert torch.equal(sims[0].obs, sims[1].obs)
+    for s in sims:
+        s.status()
+        s.close()
 
 
 def test_state_and_params_roundtrip_byte_exact():
