@@ -135,6 +135,8 @@ struct AdjArgs {
   float* g_A;                 // [n_slots][6] or null
   float* g_D;                 // [n_slots][12] or null
   float* g_state0;            // [n_slots][21] or null
+  int32_t tile_envs;          // envs per tile (the launch's blocks cover a tile in tile_envs / blockDim parts)
+  int32_t pad0;
 };
 
 // Class nominal record for the reset kernel (FP64).

@@ -1007,34 +1007,45 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
   }
 }
 
+// One warp-sized block per part of a tile: a few thousand envs (the adjoint
+// workload) then spread over all SMs instead of a few dozen. Class groups are
+// launched as programmatic dependents of one another (disjoint envs and
+// outputs) so that they run side by side.
+constexpr int ADJ_BLK = 32;
 template <int NT>
-__global__ void __launch_bounds__(128) mg_adjoint_kernel(const __grid_constant__ AdjArgs a) {
+__global__ void __launch_bounds__(ADJ_BLK) mg_adjoint_kernel(const __grid_constant__ AdjArgs a) {
   __shared__ Act<float> act;
-  if ((int)blockIdx.x >= a.n_tiles) return;
-  const int tile = a.tile_lo + blockIdx.x;
-  const int si = a.seg_lo + find_seg(a.segs + a.seg_lo, a.seg_hi - a.seg_lo, tile);
-  const SegDesc& sd = a.segs[si];
-  const ClassF& cf = a.classes[sd.cls];
-  for (int k = threadIdx.x; k < 72; k += blockDim.x) {
-    if (k < 48) (&act.alloc[0][0])[k] = cf.alloc[k / 8][k % 8];
-    else if (k < 56) act.kf[k - 48] = cf.kf[k - 48];
-    else if (k < 64) act.dz[k - 56] = cf.dz[k - 56];
-    else act.alpha[k - 64] = sd.alpha[k - 64];
-  }
-  __syncthreads();
-  const int64_t i = (int64_t)(tile - sd.tile_begin) * blockDim.x + threadIdx.x;
-  if (i >= sd.n_envs) {
-    // Padding slots of the segment: zero gradients.
-    if (i < sd.n4) {
-      const int64_t slot = sd.slot_off + i;
-      if (a.g_A) for (int j = 0; j < 6; ++j) a.g_A[slot * 6 + j] = 0.0f;
-      if (a.g_D) for (int j = 0; j < 12; ++j) a.g_D[slot * 12 + j] = 0.0f;
-      if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int parts = a.tile_envs / (int)blockDim.x;
+  const int tile = a.tile_lo + (int)blockIdx.x / parts;
+  if (tile < a.tile_lo + a.n_tiles) {
+    const int si = a.seg_lo + find_seg(a.segs + a.seg_lo, a.seg_hi - a.seg_lo, tile);
+    const SegDesc& sd = a.segs[si];
+    const ClassF& cf = a.classes[sd.cls];
+    for (int k = threadIdx.x; k < 72; k += blockDim.x) {
+      if (k < 48) (&act.alloc[0][0])[k] = cf.alloc[k / 8][k % 8];
+      else if (k < 56) act.kf[k - 48] = cf.kf[k - 48];
+      else if (k < 64) act.dz[k - 56] = cf.dz[k - 56];
+      else act.alpha[k - 64] = sd.alpha[k - 64];
     }
-    return;
+    __syncthreads();
+    const int64_t i = (int64_t)(tile - sd.tile_begin) * a.tile_envs + ((int)blockIdx.x % parts) * blockDim.x +
+                      threadIdx.x;
+    if (i >= sd.n_envs) {
+      // Padding slots of the segment: zero gradients.
+      if (i < sd.n4) {
+        const int64_t slot = sd.slot_off + i;
+        if (a.g_A) for (int j = 0; j < 6; ++j) a.g_A[slot * 6 + j] = 0.0f;
+        if (a.g_D) for (int j = 0; j < 12; ++j) a.g_D[slot * 12 + j] = 0.0f;
+        if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
+      }
+    } else {
+      const volatile Act<float>& va = act;
+      adjoint_env<NT>(a, sd, va, i);
+    }
   }
-  const volatile Act<float>& va = act;
-  adjoint_env<NT>(a, sd, va, i);
+  // Completion stays ordered along the stream (see the step kernel).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1216,12 +1227,30 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st) {
+// Adjoint launch of one class group (tiles of a.tile_envs envs, a multiple
+// of ADJ_BLK); `dependent`: programmatic dependent of the previous launch.
+template <int NT>
+static cudaError_t launch_adjoint_t(const AdjArgs& a, bool dependent, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_tiles * (a.tile_envs / ADJ_BLK)));
+  cfg.blockDim = dim3(ADJ_BLK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, mg_adjoint_kernel<NT>, a);
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
-#define MG_L(N) mg_adjoint_kernel<N><<<a.n_tiles, block, 0, st>>>(a)
+  if (a.tile_envs <= 0 || a.tile_envs % ADJ_BLK != 0) return cudaErrorInvalidValue;
+#define MG_L(N) return launch_adjoint_t<N>(a, dependent, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {

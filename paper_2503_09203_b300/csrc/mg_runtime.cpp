@@ -22,7 +22,7 @@ cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool depen
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
-cudaError_t launch_adjoint(const AdjArgs& a, int nt, int block, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm);
 }  // namespace mg
 
@@ -870,9 +870,12 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
   a.g_state0 = g_state0;
   cudaStream_t st = (cudaStream_t)stream;
   if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
+  a.tile_envs = sim->threads;
+  bool first = true;
   for (const Group& g : sim->groups) {
     a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-    CK(launch_adjoint(a, g.nt, sim->threads, st));
+    CK(launch_adjoint(a, g.nt, !first, st));
+    first = false;
   }
   return MG_OK;
 }
@@ -1360,9 +1363,12 @@ extern "C" int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, c
   a.g_state0 = g_state0;
   cudaStream_t st = (cudaStream_t)stream;
   if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
+  a.tile_envs = sim->threads;
+  bool first = true;
   for (const Group& g : sim->groups) {
     a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-    CK(launch_adjoint(a, g.nt, sim->threads, st));
+    CK(launch_adjoint(a, g.nt, !first, st));
+    first = false;
   }
   return MG_OK;
 }
