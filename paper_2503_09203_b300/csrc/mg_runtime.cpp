@@ -753,7 +753,7 @@ int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream) {
 // chunk c-2's observations are copied out on a third (host-to-device and
 // device-to-host copies overlap on the link).
 #ifndef MG_HOST_CHUNK_TILES
-#define MG_HOST_CHUNK_TILES 512
+#define MG_HOST_CHUNK_TILES 2048
 #endif
 
 int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float* obs_host, float* reward_host,
