@@ -321,7 +321,7 @@ def test_host_buffer_step_equals_device_step():
 def test_host_buffer_step_chunked_multi_step_equals_device_step():
     """Sizes that cut every group into several copy/step chunks, 3 steps per call."""
     classes = vehicles.five_classes()
-    counts = [70001, 3, 140001, 5, 9]
+    counts = [300001, 3, 140001, 5, 9]   # the 8-thruster group spans two 2048-tile chunks
     sim = make_sim(classes, counts, K=1, reset=dict(vehicles.HOVER_DR))
     sim.reset(seed=3)
     s0 = sim.get_state()
