@@ -458,8 +458,15 @@ def main():
     ap.add_argument("--substeps", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint workload (8k envs, T=200, K=4) and print its line (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.adjoint_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"adjoint": adjoint_bench(torch.cuda.current_stream())}))
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
