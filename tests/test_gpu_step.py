@@ -220,6 +220,33 @@ def test_env_result_independent_of_co_resident_classes():
     solo.close()
 
 
+def test_env_result_independent_of_env_order():
+    """Permuting the envs of a class (their parameters, states and actions)
+    permutes the results bit-exactly: no env sees another."""
+    classes = vehicles.five_classes()
+    counts = [300, 7, 140, 0, 65]
+    sims = [make_sim(classes, counts, K=4) for _ in range(2)]
+    n = sims[0].n_envs
+    p, s0 = set_inputs(sims[0], classes, counts, 31, n_thr_of(classes, counts))
+    a = workloads.actions(32, 3, n)
+    perm = np.arange(n)
+    rng = np.random.default_rng(33)
+    lo = 0
+    for c in counts:   # shuffle within each class block
+        perm[lo:lo + c] = lo + rng.permutation(c)
+        lo += c
+    pp = {k: np.asarray(v)[perm] for k, v in p.items()}
+    sims[1].set_params(B.dict_to_params(pp, n))
+    sims[1].set_state(s0[perm])
+    sims[0].rollout(sims[0].pack_actions(a), 3)
+    sims[1].rollout(sims[1].pack_actions(a[:, perm]), 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(sims[1].get_state(), sims[0].get_state()[perm])
+    for s in sims:
+        s.status()
+        s.close()
+
+
 def test_nonfinite_state_is_reported_and_cleared():
     sim = make_sim([vehicles.heavy8()], [64], K=1)
     a = np.zeros((1, 64, 8), np.float32)
