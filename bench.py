@@ -159,6 +159,16 @@ def workload(n_envs, K):
     return classes, counts, dict(vehicles.HOVER)
 
 
+def bench_config(E, K, world):
+    """The workload description shared by both arms of the benchmark."""
+    classes, counts, _ = workload(E, K)
+    state_io = sum(n * (2 * 4 * (13 + c["n_thr"]) + 4 * c["n_thr"] + 12 + 52 + 4) for c, n in zip(classes, counts))
+    return {"workload": f"hover step, {E} envs per GPU, 5 classes (4/6/8 thr), K={K}, dt=0.01",
+            "envs_per_gpu": E, "K": K, "classes": [c["name"] for c in classes], "counts": counts,
+            "l2": f"inputs larger than L2 ({state_io / 1e6:.0f} MB touched per step)",
+            "parallelism": f"replicas x{world} (independent envs per GPU)"}
+
+
 def algorithmic(classes, counts, K):
     """Bytes and FP32 ops per env-step of the hover step (class parameters, no
     current): state in + out 2*4*(13+n), actions 4n, target 12, observation 52,
@@ -480,7 +490,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"hover step, {E} envs, 5 classes, K={K}", "envs": E, "K": K},
+                "config": bench_config(E, K, world),
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -579,10 +589,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"hover step, {E} envs per GPU, 5 classes (4/6/8 thr), K={K}, dt=0.01",
-                       "envs_per_gpu": E, "K": K, "classes": [c["name"] for c in classes], "counts": counts,
-                       "l2": f"inputs larger than L2 ({E * bpe / 1e6:.0f} MB touched per step)",
-                       "parallelism": f"replicas x{world} (independent envs per GPU)"},
+            "config": bench_config(E, K, world),
             "e2e": e2e, "gpu_launches": args.steps * n_groups, "roofline": roof,
             "clocks": clocks.summary(tw0, tw1)}
     if world == 1 and not args.no_extras:
