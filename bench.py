@@ -213,7 +213,7 @@ def action_pool(sim, n_pool, seed):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload.
 # ---------------------------------------------------------------------------
-def cpu_baseline(n_envs, K, budget_s=12.0, sample_envs=4096):
+def cpu_baseline(n_envs, K, budget_s=12.0, sample_envs=4096, threads=None):
     import oracle
     from paper_2503_09203_b300 import workloads
     classes, counts, cfg = workload(n_envs, K)
@@ -221,7 +221,7 @@ def cpu_baseline(n_envs, K, budget_s=12.0, sample_envs=4096):
     ids = np.sort(rng.choice(n_envs, min(sample_envs, n_envs), replace=False))
     ec = workloads.env_classes(counts)[ids]
     envs, s = oracle.reset(classes, ec, cfg, SEED, env_ids=ids)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     a = workloads.actions(3, 1, len(ids))
     oracle.rollout(classes, envs, s.copy(), a, 0.01, K, threads=threads)  # warm-up
     t0 = time.perf_counter()
@@ -241,7 +241,7 @@ def cpu_baseline(n_envs, K, budget_s=12.0, sample_envs=4096):
 # ---------------------------------------------------------------------------
 # Extras: sweep, adjoint, serving, parity (N=1 only).
 # ---------------------------------------------------------------------------
-def sweep(pk, stream, sizes=(65536, 262144, 1048576), Ks=(1, 4, 8), steps=200):
+def sweep(pk, stream, sizes=(65536, 131072, 262144, 524288, 1048576), Ks=(1, 4, 8), steps=200):
     from paper_2503_09203_b300 import binding as B
     out = []
     for E in sizes:
@@ -259,6 +259,31 @@ def sweep(pk, stream, sizes=(65536, 262144, 1048576), Ks=(1, 4, 8), steps=200):
                         "l2_resident": E * bpe < 126e6})
             sim.close()
     return out
+
+
+def plain_bench(stream, E=1024, K=1, steps=1000):
+    """The plain workload: 1024 envs of class 0, no DR, K=1, 1000 steps
+    (launch-latency bound: reported as us per step), one launch per step and
+    the same steps as one 1000-step launch."""
+    from paper_2503_09203_b300 import binding as B
+    from paper_2503_09203_b300 import vehicles
+    import torch
+    sim = B.Sim([vehicles.heavy8()], [E], dt=0.01, K=K, per_env_params=False, reset=dict(vehicles.NO_DR))
+    sim.reset(seed=SEED)
+    acts = action_pool(sim, 4, 5)
+    t = time_steps(sim, acts, steps, 50, stream)
+    a_all = torch.rand(steps, sim.action_floats, device="cuda") * 2 - 1
+    B.mg_step(sim.handle, a_all, steps, sim.obs, sim.reward, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.mg_step(sim.handle, a_all, steps, sim.obs, sim.reward, stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_fused = e0.elapsed_time(e1) * 1e-3
+    sim.status()
+    sim.close()
+    return {"envs": E, "K": K, "steps": steps, "us_per_step": t / steps * 1e6,
+            "us_per_step_one_launch": t_fused / steps * 1e6}
 
 
 def tracking_bench(pk, stream, E=1 << 20, K=4, steps=200):
@@ -359,7 +384,7 @@ def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
             "env_steps_per_s": E * T / t}
 
 
-def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
+def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):
     import torch
     from paper_2503_09203_b300 import binding as B
     from paper_2503_09203_b300 import vehicles, workloads
@@ -389,11 +414,23 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20):
         times.append((e0.elapsed_time(e1) * 1e-3, e1.elapsed_time(e2) * 1e-3))
     tf, tb = np.median([t[0] for t in times]), np.median([t[1] for t in times])
     sim.close()
-    return {"envs": E, "horizon": T, "K": K, "ckpt_every": ckpt, "forward_s": tf, "backward_s": tb,
-            "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb}
+    # FP32 work: the recording rollout (K substeps + observation per step) and
+    # the reverse pass (per substep: recompute + vector-Jacobian product).
+    f_fwd = f_bwd = 0.0
+    for c, n in zip(classes, counts):
+        sub, obs, adj = B.mg_count_flops(c["n_thr"], adjoint=True, with_current=True)
+        f_fwd += n * T * (K * sub + obs)
+        f_bwd += n * T * K * adj
+    out = {"envs": E, "horizon": T, "K": K, "ckpt_every": ckpt, "forward_s": tf, "backward_s": tb,
+           "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb,
+           "fp32_tflops": (f_fwd + f_bwd) / (tf + tb) / 1e12}
+    if pk:
+        out["alu_frac"] = out["fp32_tflops"] * 1e12 / (2 * 128 * 148 * pk["sm_max_mhz"] * 1e6)
+        out["roofline_note"] = "FP32-issue and latency bound (256 warps at 8192 envs); FMA = 2"
+    return out
 
 
-def serving_bench(plain_rate, n_req=10000, load=0.7, seed=11, horizon_max=1000):
+def serving_bench(plain_rate, n_req=10000, load=0.7, seed=11, horizon_max=1000, pk=None):
     from paper_2503_09203_b300 import binding as B
     from paper_2503_09203_b300 import vehicles
     rng = np.random.default_rng(seed)
@@ -421,12 +458,26 @@ def serving_bench(plain_rate, n_req=10000, load=0.7, seed=11, horizon_max=1000):
     for i in ids:
         B.mg_server_release(srv, i)
     B.mg_server_destroy(srv)
+    # Work per env-step of the mix (weights: envs x horizon): FP32 ops of K
+    # substeps + observation, and bytes of a device step (state in + out,
+    # 10 per-env parameter planes, return read + write; actions drawn on the device).
+    w = np.array([r[1] * r[2] for r in reqs], dtype=np.float64)
+    per_nt = {c["n_thr"]: B.mg_count_flops(c["n_thr"]) for c in classes}
+    flops = np.array([r[3] * per_nt[classes[r[0]]["n_thr"]][0] + per_nt[classes[r[0]]["n_thr"]][1] for r in reqs])
+    nbytes = np.array([2 * 4 * (13 + classes[r[0]]["n_thr"]) + 160 + 8 for r in reqs], dtype=np.float64)
+    busy = st["env_steps"] / max(st["busy_seconds"], 1e-9)
+    roof = {"flops_per_env_step": float(np.sum(w * flops) / np.sum(w)),
+            "bytes_per_env_step": float(np.sum(w * nbytes) / np.sum(w))}
+    if pk:
+        roof["busy_alu_frac"] = busy * roof["flops_per_env_step"] / (2 * 128 * 148 * pk["sm_max_mhz"] * 1e6)
+        roof["busy_hbm_frac"] = busy * roof["bytes_per_env_step"] / (pk["hbm_gbs"] * 1e9)
     return {"requests": n_req, "offered_load": load, "arrival_rate_per_s": lam, "wall_s": wall,
             "env_steps_per_s": st["env_steps"] / wall, "busy_env_steps_per_s": st["env_steps"] / max(st["busy_seconds"], 1e-9),
             "step_latency_p50_ms": st["step_latency_p50"] * 1e3, "step_latency_p99_ms": st["step_latency_p99"] * 1e3,
             "queue_delay_p50_ms": st["queue_delay_p50"] * 1e3, "queue_delay_p99_ms": st["queue_delay_p99"] * 1e3,
             "tick_p50_ms": st["tick_p50"] * 1e3, "tick_p99_ms": st["tick_p99"] * 1e3, "ticks": st["ticks"],
-            "request_mix": "class U{0..4}, envs log-uniform [1,16384], horizon U{1..%d}, K U{1..8}" % horizon_max}
+            "request_mix": "class U{0..4}, envs log-uniform [1,16384], horizon U{1..%d}, K U{1..8}" % horizon_max,
+            "roofline_while_busy": roof}
 
 
 def parity_sample(sim_classes, counts, K, n=512):
@@ -594,6 +645,8 @@ def main():
             "clocks": clocks.summary(tw0, tw1)}
     if world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(E, K)
+        line["cpu_baseline_1core"] = cpu_baseline(E, K, budget_s=4.0, sample_envs=1024, threads=1)
+        line["plain"] = plain_bench(stream)
         sim.close()
         line["parity"] = parity_sample(classes, counts, K)
         line["sweep"] = sweep(pk, stream)
@@ -601,9 +654,9 @@ def main():
         line["payload"] = payload_bench(pk, stream)
         line["actuated"] = actuated_bench(pk, stream)
         line["hetero_graph"] = hetero_graph_bench(stream)
-        line["adjoint"] = adjoint_bench(stream)
+        line["adjoint"] = adjoint_bench(stream, pk=pk)
         plain_substeps = max(r["env_steps_per_s"] * r["K"] for r in line["sweep"] if r["envs"] == 65536)
-        line["serving"] = [serving_bench(plain_substeps, load=0.7), serving_bench(plain_substeps, load=0.9)]
+        line["serving"] = [serving_bench(plain_substeps, load=0.7, pk=pk), serving_bench(plain_substeps, load=0.9, pk=pk)]
     else:
         sim.close()
     print(json.dumps(line))
