@@ -79,6 +79,16 @@ struct mg_sim {
   int32_t rec_T = 0;           // steps of the last recorded rollout (0: none)
   size_t bytes = 0;
   std::string err;
+  // Launch plan of a step (grids, launch shape, carveouts), computed once per
+  // segment layout and blocks_per_sm setting: a step only reads it.
+  struct Plan {
+    bool valid = false;
+    int bps = -1;
+    bool cores = false;
+    std::vector<int> grid;
+    std::vector<int> full_grid;   // persistent grid of each group launched alone
+    std::vector<char> carve_max;
+  } plan;
   // mg_step_host: copy streams and events of the chunked pipeline.
   cudaStream_t s_in = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> host_ev;
@@ -243,6 +253,7 @@ static int class_var(const mg_sim* sim, int c) {
 static void build_segs(mg_sim* sim) {
   sim->segs.clear();
   sim->groups.clear();
+  sim->plan.valid = false;
   int tiles = 0;
   for (int var = 0; var < 3; ++var)
   for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
@@ -680,12 +691,30 @@ static bool carveout_max(const mg_sim* sim, const Group& g, bool shared_sm) {
   return shared_sm || (param_mode(sim) == 0 && g.var == 0 && sim->cfg.task != 1);
 }
 
-static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
-  std::vector<int> grid;
-  const bool cores = coresident_grids(sim, grid);
+// The launch plan of the current segment layout and blocks_per_sm setting
+// (occupancy queries and FLOP counts stay off the per-step path).
+static const mg_sim::Plan& step_plan(mg_sim* sim) {
+  mg_sim::Plan& p = sim->plan;
+  if (p.valid && p.bps == sim->blocks_per_sm) return p;
+  p.cores = coresident_grids(sim, p.grid);
   int64_t blocks = 0;
-  for (int b : grid) blocks += b;
-  const bool shared_sm = cores && blocks > sim->num_sms;
+  for (int b : p.grid) blocks += b;
+  const bool shared_sm = p.cores && blocks > sim->num_sms;
+  p.carve_max.assign(sim->groups.size(), 0);
+  p.full_grid.assign(sim->groups.size(), 1);
+  for (size_t i = 0; i < sim->groups.size(); ++i) {
+    const Group& g = sim->groups[i];
+    p.full_grid[i] = grid_of(sim, g);
+    if (!p.cores) p.grid[i] = p.full_grid[i];
+    p.carve_max[i] = carveout_max(sim, g, shared_sm) ? 1 : 0;
+  }
+  p.bps = sim->blocks_per_sm;
+  p.valid = true;
+  return p;
+}
+
+static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
+  const mg_sim::Plan& p = step_plan(sim);
   bool first = true;
   for (size_t i = 0; i < sim->groups.size(); ++i) {
     const Group& g = sim->groups[i];
@@ -693,9 +722,8 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    a.wait_first = first && cores;
-    CK(launch_step(a, g.nt, g.var, cores ? grid[i] : grid_of(sim, g), !first || cores,
-                   carveout_max(sim, g, shared_sm), st));
+    a.wait_first = first && p.cores;
+    CK(launch_step(a, g.nt, g.var, p.grid[i], !first || p.cores, p.carve_max[i] != 0, st));
     first = false;
   }
   return MG_OK;
@@ -791,6 +819,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   CK(cudaStreamWaitEvent(sim->s_in, ev_entry, 0));
   CK(cudaStreamWaitEvent(sim->s_out, ev_entry, 0));
   const size_t pitch = sizeof(float) * (size_t)sim->act_floats;
+  const mg_sim::Plan& plan = step_plan(sim);
   StepArgs a = step_args(sim);
   a.actions = d_act;
   a.n_steps = n_steps;
@@ -824,7 +853,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     a.tile_lo = tile_lo;
     a.n_tiles = ch.nt;
     a.wait_first = 0;
-    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, grid_of(sim, g))), false,
+    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false,
                    carveout_max(sim, g, false), st));
     CK(cudaEventRecord(ev_done, st));
     CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
