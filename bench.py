@@ -337,6 +337,8 @@ def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
     classes = vehicles.actuated_classes()
     counts = workloads.class_counts(E, 3)
     out = {"envs": E, "K": K, "classes": [c["name"] for c in classes]}
+    bpe, _ = algorithmic(classes, counts, K)
+    b = bpe + 16 * 9 + 4   # parameter planes read per step; full target float4
     for name, integ in (("euler", B.MG_INTEG_EULER), ("rk4", B.MG_INTEG_RK4)):
         sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR),
                     integrator=integ)
@@ -345,7 +347,9 @@ def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
         t = time_steps(sim, acts, steps, 10, stream)
         sim.status()
         sim.close()
-        out[name] = {"env_steps_per_s": E * steps / t, "us_per_step": t / steps * 1e6}
+        v = E * steps / t
+        out[name] = {"env_steps_per_s": v, "us_per_step": t / steps * 1e6, "bytes_per_env_step": b,
+                     "hbm_frac": v * b / (pk["hbm_gbs"] * 1e9)}
     return out
 
 
