@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace mg {
@@ -42,6 +43,24 @@ struct ClassF {
 };
 static_assert(sizeof(ClassF) == 104 * 4, "ClassF layout");
 
+// One class's constants passed by value as a kernel parameter (propeller
+// steps with class constants launch one class at a time): the kernel reads
+// them as constant-bank operands, with no shared-memory load and no register
+// to hold them. Members as the actuator table (alloc, kf, dz, alpha) and the
+// nominal physical block (minv .. Vc; current 0) that the step reads.
+struct ClassK {
+  static constexpr bool kFull = false;   // diagonal inertia, CoG at the origin
+  float alloc[6][8];
+  float kf[8];
+  float dz[8];
+  float alpha[8];
+  float minv[6], A[6], dl[6], dq[6];
+  float m, Ig[3], W, B, rb[3], Vc[3];
+  uint32_t dz_on;       // 0: no channel has a dead zone
+  uint32_t pad[3];
+};
+static_assert(sizeof(ClassK) == 112 * 4, "ClassK layout");
+
 // Generic actuator table of a class (fins, servo-tilted propellers): the kind
 // of each channel (as the bits of a float, so that the table stages into
 // shared memory as one float array) and 20 values per channel (layout in the
@@ -64,6 +83,9 @@ struct ClassD {
 // Per-env physical parameter block (36 floats, 9 float4 planes) field offsets.
 enum { PAR_MINV = 0, PAR_A = 6, PAR_DL = 12, PAR_DQ = 18, PAR_M = 24, PAR_IG = 25, PAR_W = 28,
        PAR_B = 29, PAR_RB = 30, PAR_VC = 33, PAR_DIM = 36 };
+static_assert(offsetof(ClassK, minv) == 4 * (72 + PAR_MINV) && offsetof(ClassK, m) == 4 * (72 + PAR_M) &&
+                  offsetof(ClassK, Vc) == 4 * (72 + PAR_VC),
+              "ClassK physical block follows the parameter block layout");
 
 // Number of float4 parameter planes: 9 for the 36 physical floats + 1 target.
 // The target plane holds (c_x, c_y, c_z, k): the reference centre and the

@@ -179,6 +179,9 @@ struct ActSmemT {
 };
 template <bool DZF>
 __device__ __forceinline__ bool dz_active(const ActSmemT<DZF>& A) { return !(MG_DZ_FLAG && DZF) || A.dz_on != 0u; }
+// Class constants as a kernel parameter: the dead-zone test is skipped for
+// classes without one.
+__device__ __forceinline__ bool dz_active(const ClassK& k) { return !MG_DZ_FLAG || k.dz_on != 0u; }
 enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
 
 template <int NT>
@@ -395,7 +398,7 @@ __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& s
 template <int NT, int PM>
 __device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDesc& sd, int64_t w0, unsigned nvw,
                                                  float* buf, unsigned bar) {
-  constexpr bool PER_ENV = PM >= 1;
+  constexpr bool PER_ENV = PM == 1 || PM == 2;
   using SG = Stage<NT>;
   const float* st = a.state + sd.st_off;
   unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
@@ -428,10 +431,10 @@ __device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0,
 }
 
 template <int NT, int PM, int VAR>
-__device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, int tile, unsigned s_act,
-                                          unsigned s_phys, unsigned s_gen, const float* buf, float* obs_w,
-                                          float* s_par, int& n_emit) {
-  constexpr bool PER_ENV = PM >= 1;
+__device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, const SegDesc& sd, int tile,
+                                          unsigned s_act, unsigned s_phys, unsigned s_gen, const float* buf,
+                                          float* obs_w, float* s_par, int& n_emit) {
+  constexpr bool PER_ENV = PM == 1 || PM == 2;
   using SG = Stage<NT>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t local0 = (int64_t)(tile - sd.tile_begin) * STEP_BLK;
@@ -535,17 +538,22 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const SegDesc& sd, 
       // Shared-memory bases made opaque once per substep: loads may be
       // scheduled freely inside a substep but not hoisted out of the loop.
       for (int k = 0; k < sd.K; ++k) {
-        unsigned pb = p_base, ab = A.base, gb = g_base;
-        asm volatile("" : "+r"(pb), "+r"(ab), "+r"(gb));
-        const ActSmem Ak{ab, A.dz_on};
-        // Class-constant physics carries no current (zero by construction).
-        const PV Pk(pb);
-        if constexpr (VAR == 0) {
-          substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
-        } else if constexpr (VAR == 1) {
-          substep<float, NT, false, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, nullptr, GenSmem{gb});
+        if constexpr (PM == 3) {
+          // Class constants are kernel parameters: read as operands.
+          substep<float, NT, false, ClassK, ClassK, false>(x, c, *kc, *kc, sd.h, nullptr);
         } else {
-          substep_rk4<float, NT, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, GenSmem{gb});
+          unsigned pb = p_base, ab = A.base, gb = g_base;
+          asm volatile("" : "+r"(pb), "+r"(ab), "+r"(gb));
+          const ActSmem Ak{ab, A.dz_on};
+          // Class-constant physics carries no current (zero by construction).
+          const PV Pk(pb);
+          if constexpr (VAR == 0) {
+            substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
+          } else if constexpr (VAR == 1) {
+            substep<float, NT, false, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, nullptr, GenSmem{gb});
+          } else {
+            substep_rk4<float, NT, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, GenSmem{gb});
+          }
         }
       }
     }
@@ -631,8 +639,11 @@ struct StepMinBlocks {
   static constexpr int value = VAR == 2 ? MG_RK4_MIN_BLOCKS : (VAR == 1 ? MG_GEN_MIN_BLOCKS : MG_STEP_MIN_BLOCKS);
 };
 
+// PM: parameter source (0 class constants staged in shared memory, 1 per-env
+// planes, 2 per-env planes with the payload, 3 class constants passed as the
+// kernel parameter `kc`: one class per launch).
 template <int NT, int PM, int VAR>
-__global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_kernel(const __grid_constant__ StepArgs a) {
+__device__ __forceinline__ void step_body(const StepArgs& a, const ClassK* kc) {
   using SG = Stage<NT>;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -706,7 +717,7 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
       }
     }
     const SegDesc& sd = segs[si];
-    if (si != prev_seg) {
+    if (PM != 3 && si != prev_seg) {
       // Class constants change: rewrite them between two block barriers
       // (every warp of the block walks the same tiles).
       __syncthreads();
@@ -723,8 +734,8 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
         failed = true;
     }
     if (!failed)
-      step_tile<NT, PM, VAR>(a, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
-                             MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
+      step_tile<NT, PM, VAR>(a, kc, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen),
+                             b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
     nvw_cur = nvw_next;
@@ -735,6 +746,21 @@ __global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_k
   // A grid launched as a programmatic dependent completes only after the grid
   // it depends on, so that completion stays ordered along the stream.
   asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <int NT, int PM, int VAR>
+__global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_kernel(const __grid_constant__ StepArgs a) {
+  step_body<NT, PM, VAR>(a, nullptr);
+}
+
+// Propeller step of one class whose constants travel in the kernel parameters.
+#ifndef MG_KSTEP_MIN_BLOCKS
+#define MG_KSTEP_MIN_BLOCKS MG_STEP_MIN_BLOCKS
+#endif
+template <int NT>
+__global__ void __launch_bounds__(STEP_BLK, MG_KSTEP_MIN_BLOCKS)
+    mg_step_kernel_k(const __grid_constant__ StepArgs a, const __grid_constant__ ClassK kc) {
+  step_body<NT, 3, 0>(a, &kc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1150,13 +1176,20 @@ static size_t step_smem(bool track) {
   return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
 }
 
+// Entry point of a step instantiation (PM 3: class constants as parameters).
+template <int NT, int PM, int VAR>
+static const void* step_fn() {
+  if constexpr (PM == 3) return reinterpret_cast<const void*>(&mg_step_kernel_k<NT>);
+  else return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR>);
+}
+
 // Kernel attributes of a step instantiation: the largest dynamic shared
 // memory of its layouts (tracking).
 template <int NT, int PM, int VAR>
 static cudaError_t step_attrs() {
   static bool done = false;   // per instantiation, per process (one device)
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<NT, PM>(true));
   if (e == cudaSuccess) done = true;
   return e;
@@ -1169,8 +1202,7 @@ static cudaError_t step_carveout(bool shared_sm) {
   static int current = -2;   // per instantiation, per process (one device)
   const int want = shared_sm ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault;
   if (want == current) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(mg_step_kernel<NT, PM, VAR>, cudaFuncAttributePreferredSharedMemoryCarveout, want);
+  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR>(), cudaFuncAttributePreferredSharedMemoryCarveout, want);
   if (e == cudaSuccess) current = want;
   return e;
 }
@@ -1178,7 +1210,8 @@ static cudaError_t step_carveout(bool shared_sm) {
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
 template <int NT, int PM, int VAR>
-static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, bool shared_sm, cudaStream_t st) {
+static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, int grid, bool dependent, bool shared_sm,
+                                 cudaStream_t st) {
   const size_t smem = step_smem<NT, PM>(a.track != 0);
   cudaError_t e = step_attrs<NT, PM, VAR>();
   if (e == cudaSuccess) e = step_carveout<NT, PM, VAR>(shared_sm);
@@ -1193,13 +1226,14 @@ static cudaError_t launch_step_t(const StepArgs& a, int grid, bool dependent, bo
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a);
+  if constexpr (PM == 3) return cudaLaunchKernelEx(&cfg, mg_step_kernel_k<NT>, a, *kc);
+  else return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a);
 }
 
 template <int PM, int VAR>
-static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool dependent, bool shared_sm,
-                                  cudaStream_t st) {
-#define MG_L(N) return launch_step_t<N, PM, VAR>(a, grid, dependent, shared_sm, st)
+static cudaError_t launch_step_pv(const StepArgs& a, const ClassK* kc, int nt, int grid, bool dependent,
+                                  bool shared_sm, cudaStream_t st) {
+#define MG_L(N) return launch_step_t<N, PM, VAR>(a, kc, grid, dependent, shared_sm, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;
@@ -1207,20 +1241,26 @@ static cudaError_t launch_step_pv(const StepArgs& a, int nt, int grid, bool depe
 
 // Step launch of one class group: thruster count nt, parameter source
 // a.per_env (0 class, 1 per-env, 2 payload), variant var (0 propellers with
-// Euler, 1 generic actuators with Euler, 2 RK4).
-cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, bool shared_sm,
-                        cudaStream_t st) {
+// Euler, 1 generic actuators with Euler, 2 RK4). `kc` (class-constant
+// propeller steps whose segments are all of one class, else null): that
+// class's constants, passed as a kernel parameter.
+cudaError_t launch_step(const StepArgs& a, const ClassK* kc, int nt, int var, int grid, bool dependent,
+                        bool shared_sm, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
+  if (kc) {
+    if (a.per_env != 0 || var != 0) return cudaErrorInvalidValue;
+    return launch_step_pv<3, 0>(a, kc, nt, grid, dependent, shared_sm, st);
+  }
   switch (a.per_env * 3 + var) {
-    case 0: return launch_step_pv<0, 0>(a, nt, grid, dependent, shared_sm, st);
-    case 1: return launch_step_pv<0, 1>(a, nt, grid, dependent, shared_sm, st);
-    case 2: return launch_step_pv<0, 2>(a, nt, grid, dependent, shared_sm, st);
-    case 3: return launch_step_pv<1, 0>(a, nt, grid, dependent, shared_sm, st);
-    case 4: return launch_step_pv<1, 1>(a, nt, grid, dependent, shared_sm, st);
-    case 5: return launch_step_pv<1, 2>(a, nt, grid, dependent, shared_sm, st);
-    case 6: return launch_step_pv<2, 0>(a, nt, grid, dependent, shared_sm, st);
-    case 7: return launch_step_pv<2, 1>(a, nt, grid, dependent, shared_sm, st);
-    case 8: return launch_step_pv<2, 2>(a, nt, grid, dependent, shared_sm, st);
+    case 0: return launch_step_pv<0, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 1: return launch_step_pv<0, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 2: return launch_step_pv<0, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 3: return launch_step_pv<1, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 4: return launch_step_pv<1, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 5: return launch_step_pv<1, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 6: return launch_step_pv<2, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 7: return launch_step_pv<2, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
+    case 8: return launch_step_pv<2, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1275,7 +1315,7 @@ template <int NT, int PM, int VAR>
 static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
   cudaError_t e = step_attrs<NT, PM, VAR>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mg_step_kernel<NT, PM, VAR>, STEP_BLK,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_fn<NT, PM, VAR>(), STEP_BLK,
                                                        step_smem<NT, PM>(track));
 }
 
@@ -1287,6 +1327,7 @@ static cudaError_t occupancy_pv(int nt, bool track, int* blocks_per_sm) {
   return cudaErrorInvalidValue;
 }
 
+// pm 3: class constants as kernel parameters (var 0 only).
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm) {
   switch (pm * 3 + var) {
     case 0: return occupancy_pv<0, 0>(nt, track, blocks_per_sm);
@@ -1298,6 +1339,7 @@ cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* bloc
     case 6: return occupancy_pv<2, 0>(nt, track, blocks_per_sm);
     case 7: return occupancy_pv<2, 1>(nt, track, blocks_per_sm);
     case 8: return occupancy_pv<2, 2>(nt, track, blocks_per_sm);
+    case 9: return occupancy_pv<3, 0>(nt, track, blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }
 }

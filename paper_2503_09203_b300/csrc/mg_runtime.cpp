@@ -17,8 +17,8 @@
 #include "mg_payload.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, int nt, int var, int grid, bool dependent, bool shared_sm,
-                        cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, const ClassK* kc, int nt, int var, int grid, bool dependent,
+                        bool shared_sm, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
@@ -42,9 +42,11 @@ struct ClassLay {
 
 // Segments with the same thruster count and step variant (0 propellers with
 // Euler, 1 generic actuators with Euler, 2 RK4), launched by one kernel
-// instantiation.
+// instantiation. A launch of the step plan with cls >= 0 holds envs of that
+// one class and passes its constants as the kernel parameter (the groups of
+// the segment layout have cls = -1).
 struct Group {
-  int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles, var;
+  int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles, var, cls;
 };
 
 struct mg_sim {
@@ -88,7 +90,10 @@ struct mg_sim {
     std::vector<int> grid;
     std::vector<int> full_grid;   // persistent grid of each group launched alone
     std::vector<char> carve_max;
+    std::vector<Group> groups;     // the launches of a step
+    std::vector<ClassK> kc;        // constants of each launch with cls >= 0
   } plan;
+  std::vector<ClassF> h_cls;       // host copy of the class tables
   // mg_step_host: copy streams and events of the chunked pipeline.
   cudaStream_t s_in = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> host_ev;
@@ -250,6 +255,12 @@ static int class_var(const mg_sim* sim, int c) {
 
 // Segments ordered by step variant, then thruster count (then class); tiles
 // are numbered in that order so that each group owns one contiguous tile range.
+// Class-constant propeller launches of a single class pass its constants as
+// the kernel parameter (0: always staged in shared memory).
+#ifndef MG_CLASS_PARAMS
+#define MG_CLASS_PARAMS 1
+#endif
+
 static void build_segs(mg_sim* sim) {
   sim->segs.clear();
   sim->groups.clear();
@@ -291,6 +302,7 @@ static void build_segs(mg_sim* sim) {
     }
     g.seg_hi = (int32_t)sim->segs.size();
     g.n_tiles = tiles - g.tile_lo;
+    g.cls = -1;
     if (g.seg_hi > g.seg_lo) sim->groups.push_back(g);
   }
   sim->n_tiles = tiles;
@@ -517,6 +529,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
     n.B = d.buoy_ratio * d.mass * kG;
     for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
   }
+  sim->h_cls = cf;
   ce = cudaMemcpy(sim->d_cls, cf.data(), sizeof(ClassF) * cf.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_cls64, cd.data(), sizeof(ClassD) * cd.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_nominal, cn.data(), sizeof(ClassNominal) * cn.size(), cudaMemcpyHostToDevice);
@@ -577,6 +590,25 @@ int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, 
 // Parameter source of the step kernel: 0 class constants, 1 per-env planes,
 // 2 per-env planes plus the payload planes.
 static int param_mode(const mg_sim* sim) { return sim->cfg.payload ? 2 : (sim->cfg.per_env_params ? 1 : 0); }
+// Parameter source of a group's kernel (3: class constants as the kernel parameter).
+static int group_pm(const mg_sim* sim, const Group& g) { return g.cls >= 0 ? 3 : param_mode(sim); }
+
+// Kernel-parameter constants of a one-class group: the class table, the lag
+// coefficients and dead-zone flag of its segment, no current.
+static ClassK class_k(const mg_sim* sim, const Group& g) {
+  ClassK k;
+  std::memset(&k, 0, sizeof(k));
+  const ClassF& f = sim->h_cls[g.cls];
+  const SegDesc& sd = sim->segs[g.seg_lo];
+  std::memcpy(k.alloc, f.alloc, sizeof(k.alloc));
+  std::memcpy(k.kf, f.kf, sizeof(k.kf));
+  std::memcpy(k.dz, f.dz, sizeof(k.dz));
+  std::memcpy(k.alpha, sd.alpha, sizeof(k.alpha));
+  std::memcpy(k.minv, f.phys, sizeof(float) * PAR_DIM);
+  for (int j = 0; j < 3; ++j) k.Vc[j] = 0.0f;
+  k.dz_on = (uint32_t)(sd.flags & 1);
+  return k;
+}
 
 static StepArgs step_args(mg_sim* sim) {
   StepArgs a;
@@ -602,7 +634,7 @@ static int grid_of(mg_sim* sim, const Group& g) {
   int b = sim->blocks_per_sm;
   if (b <= 0) {
     b = 1;
-    step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b);
+    step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &b);
     if (b < 1) b = 1;
   }
   return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
@@ -640,7 +672,7 @@ static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
   for (int i = 0; i < n; ++i) {
     const Group& g = sim->groups[i];
     int b = sim->blocks_per_sm;
-    if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
+    if (b <= 0 && step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
     resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
     double sub = 0.0, obs = 0.0;
     mg_count_flops(g.nt, sim->cfg.per_env_params, &sub, &obs, nullptr);
@@ -693,6 +725,13 @@ static bool carveout_max(const mg_sim* sim, const Group& g, bool shared_sm) {
 
 // The launch plan of the current segment layout and blocks_per_sm setting
 // (occupancy queries and FLOP counts stay off the per-step path).
+// Launches run one after the other (the larger steps) split the class groups
+// of class-constant propeller steps into one launch per class, which takes
+// its constants as the kernel parameter (1M envs, K=4: 77.0 -> 69.8 us;
+// 512k: 42.9 -> 39.1 us). Side-by-side launches keep one launch per group
+// with the constants in shared memory: their grids are split by estimated
+// work, which a faster one-class kernel unbalances (262k envs: 23.1 -> 23.6
+// us), and five launches instead of three cost 4 us at 65k envs.
 static const mg_sim::Plan& step_plan(mg_sim* sim) {
   mg_sim::Plan& p = sim->plan;
   if (p.valid && p.bps == sim->blocks_per_sm) return p;
@@ -700,10 +739,28 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
   int64_t blocks = 0;
   for (int b : p.grid) blocks += b;
   const bool shared_sm = p.cores && blocks > sim->num_sms;
-  p.carve_max.assign(sim->groups.size(), 0);
-  p.full_grid.assign(sim->groups.size(), 1);
-  for (size_t i = 0; i < sim->groups.size(); ++i) {
-    const Group& g = sim->groups[i];
+  p.groups.clear();
+  for (const Group& g : sim->groups) {
+    const bool split = !p.cores && MG_CLASS_PARAMS && !sim->cfg.per_env_params && !sim->cfg.payload && g.var == 0;
+    if (!split) { p.groups.push_back(g); continue; }
+    for (int s = g.seg_lo; s < g.seg_hi; ++s) {   // a segment holds envs of one class
+      Group h = g;
+      h.seg_lo = s;
+      h.seg_hi = s + 1;
+      h.tile_lo = sim->segs[s].tile_begin;
+      h.n_tiles = (s + 1 < g.seg_hi ? sim->segs[s + 1].tile_begin : g.tile_lo + g.n_tiles) - h.tile_lo;
+      h.cls = sim->segs[s].cls;
+      if (h.n_tiles > 0) p.groups.push_back(h);
+    }
+  }
+  const size_t n = p.groups.size();
+  if (!p.cores) p.grid.assign(n, 1);
+  p.carve_max.assign(n, 0);
+  p.full_grid.assign(n, 1);
+  p.kc.assign(n, ClassK());
+  for (size_t i = 0; i < n; ++i) {
+    const Group& g = p.groups[i];
+    if (g.cls >= 0) p.kc[i] = class_k(sim, g);
     p.full_grid[i] = grid_of(sim, g);
     if (!p.cores) p.grid[i] = p.full_grid[i];
     p.carve_max[i] = carveout_max(sim, g, shared_sm) ? 1 : 0;
@@ -716,14 +773,15 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
   const mg_sim::Plan& p = step_plan(sim);
   bool first = true;
-  for (size_t i = 0; i < sim->groups.size(); ++i) {
-    const Group& g = sim->groups[i];
+  for (size_t i = 0; i < p.groups.size(); ++i) {
+    const Group& g = p.groups[i];
     a.seg_lo = g.seg_lo;
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
     a.wait_first = first && p.cores;
-    CK(launch_step(a, g.nt, g.var, p.grid[i], !first || p.cores, p.carve_max[i] != 0, st));
+    CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.nt, g.var, p.grid[i], !first || p.cores,
+                   p.carve_max[i] != 0, st));
     first = false;
   }
   return MG_OK;
@@ -802,12 +860,13 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   cudaStream_t st = (cudaStream_t)stream;
   if (!sim->s_in) CK(cudaStreamCreateWithFlags(&sim->s_in, cudaStreamNonBlocking));
   if (!sim->s_out) CK(cudaStreamCreateWithFlags(&sim->s_out, cudaStreamNonBlocking));
-  // Chunks: (group, first tile, tiles).
+  // Chunks: (launch of the step plan, first tile, tiles).
+  const mg_sim::Plan& plan = step_plan(sim);
   struct Chunk { int g, t0, nt; };
   std::vector<Chunk> chunks;
-  for (int gi = 0; gi < (int)sim->groups.size(); ++gi)
-    for (int t = 0; t < sim->groups[gi].n_tiles; t += MG_HOST_CHUNK_TILES)
-      chunks.push_back({gi, t, std::min(MG_HOST_CHUNK_TILES, sim->groups[gi].n_tiles - t)});
+  for (int gi = 0; gi < (int)plan.groups.size(); ++gi)
+    for (int t = 0; t < plan.groups[gi].n_tiles; t += MG_HOST_CHUNK_TILES)
+      chunks.push_back({gi, t, std::min(MG_HOST_CHUNK_TILES, plan.groups[gi].n_tiles - t)});
   const size_t n_ev = 2 * chunks.size() + 1;
   while (sim->host_ev.size() < n_ev) {
     cudaEvent_t e;
@@ -819,7 +878,6 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   CK(cudaStreamWaitEvent(sim->s_in, ev_entry, 0));
   CK(cudaStreamWaitEvent(sim->s_out, ev_entry, 0));
   const size_t pitch = sizeof(float) * (size_t)sim->act_floats;
-  const mg_sim::Plan& plan = step_plan(sim);
   StepArgs a = step_args(sim);
   a.actions = d_act;
   a.n_steps = n_steps;
@@ -828,7 +886,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   a.act_stride = sim->act_floats;
   for (size_t c = 0; c < chunks.size(); ++c) {
     const Chunk& ch = chunks[c];
-    const Group& g = sim->groups[ch.g];
+    const Group& g = plan.groups[ch.g];
     const int tile_lo = g.tile_lo + ch.t0, tile_hi = tile_lo + ch.nt;
     cudaEvent_t ev_in = sim->host_ev[1 + 2 * c], ev_done = sim->host_ev[2 + 2 * c];
     // Env ranges of the chunk, per segment of the group.
@@ -853,8 +911,8 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     a.tile_lo = tile_lo;
     a.n_tiles = ch.nt;
     a.wait_first = 0;
-    CK(launch_step(a, g.nt, g.var, std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false,
-                   carveout_max(sim, g, false), st));
+    CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.nt, g.var,
+                   std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false, carveout_max(sim, g, false), st));
     CK(cudaEventRecord(ev_done, st));
     CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
     for (const Range& r : ranges) {
@@ -1273,7 +1331,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   int occ = 1 << 30;
   for (const Group& g : sim->groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
+    if (step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;
