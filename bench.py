@@ -567,7 +567,7 @@ def main():
     stream = torch.cuda.current_stream()
     acts = action_pool(sim, 8, 100 + rank)
     bpe, fpe = algorithmic(classes, counts, K)
-    n_groups = len({c["n_thr"] for c in classes})
+    n_launches = sim.launches_per_step()
 
     clocks = ClockSampler(local)
     if rank == 0:
@@ -635,17 +635,17 @@ def main():
                 "peak_src": "2 x 128 FP32 lanes x 148 SMs x max SM clock"}
     traffic = profiled_traffic() if (E == 1 << 20 and K == 4) else None
     roof["traffic"] = traffic
-    roof["traffic_note"] = ("DRAM read+write bytes per step (3 launches) from profiles/step_kernel_full_hover_1M_K4.md "
+    roof["traffic_note"] = (f"DRAM read+write bytes per step ({n_launches} launches) from profiles/step_kernel_full_hover_1M_K4.md "
                             "(ncu serialised replay: reads = algorithmic, writes partly deferred in L2)"
                             if traffic else "null: no ncu capture of these kernel sources at this workload")
-    roof.update({"kernel": "mg_step_kernel<4,6,8> (one launch per thruster count, per step)",
+    roof.update({"kernel": f"mg_step_kernel<NT, 3, 0> (class constants as the kernel parameter), {n_launches} launches per step",
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
                  "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": bench_config(E, K, world),
-            "e2e": e2e, "gpu_launches": args.steps * n_groups, "roofline": roof,
+            "e2e": e2e, "gpu_launches": args.steps * n_launches, "roofline": roof,
             "clocks": clocks.summary(tw0, tw1)}
     if world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(E, K)

@@ -185,7 +185,10 @@ typedef struct {
 } mg_class_layout;
 
 typedef struct {
-  int32_t n_classes, n_envs, n_slots, pad0;
+  int32_t n_classes, n_envs, n_slots;
+  int32_t launches_per_step;  /* kernel launches one mg_step call makes (one per
+                               * thruster count and step variant; large steps of
+                               * class-constant propeller classes: one per class) */
   int64_t action_floats;  /* floats per control step in an actions buffer */
   int64_t state_floats;
   mg_class_layout cls[MG_MAX_CLASSES];

@@ -88,7 +88,7 @@ class mg_class_layout(C.Structure):
 
 class mg_layout(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("n_envs", C.c_int32), ("n_slots", C.c_int32),
-                ("pad0", C.c_int32), ("action_floats", C.c_int64), ("state_floats", C.c_int64),
+                ("launches_per_step", C.c_int32), ("action_floats", C.c_int64), ("state_floats", C.c_int64),
                 ("cls", mg_class_layout * MG_MAX_CLASSES)]
 
 
@@ -462,6 +462,10 @@ class Sim:
         self.reward = torch.zeros(self.n_slots, device=self.device)
 
     # -- layout helpers ------------------------------------------------------
+    def launches_per_step(self) -> int:
+        """Kernel launches one step call makes (current launch plan)."""
+        return int(mg_get_layout(self.handle).launches_per_step)
+
     def cls(self, c):
         return self.layout.cls[c]
 

@@ -634,17 +634,33 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
 #ifndef MG_GEN_MIN_BLOCKS
 #define MG_GEN_MIN_BLOCKS 3
 #endif
-template <int VAR>
+#ifndef MG_KSTEP_MIN_BLOCKS
+#define MG_KSTEP_MIN_BLOCKS MG_STEP_MIN_BLOCKS
+#endif
+template <int PM, int VAR>
 struct StepMinBlocks {
-  static constexpr int value = VAR == 2 ? MG_RK4_MIN_BLOCKS : (VAR == 1 ? MG_GEN_MIN_BLOCKS : MG_STEP_MIN_BLOCKS);
+  static constexpr int value = VAR == 2 ? MG_RK4_MIN_BLOCKS
+                               : VAR == 1 ? MG_GEN_MIN_BLOCKS
+                               : PM == 3  ? MG_KSTEP_MIN_BLOCKS
+                                          : MG_STEP_MIN_BLOCKS;
 };
+
+// Second kernel parameter: the class constants (PM 3), else nothing.
+struct NoClassK {};
+template <int PM>
+using KParam = std::conditional_t<PM == 3, ClassK, NoClassK>;
 
 // PM: parameter source (0 class constants staged in shared memory, 1 per-env
 // planes, 2 per-env planes with the payload, 3 class constants passed as the
-// kernel parameter `kc`: one class per launch).
+// kernel parameter `kp`: one class per launch). The body stays in the kernel
+// itself: moved into a function taking the parameters by reference, the
+// per-env and payload instantiations spilled.
 template <int NT, int PM, int VAR>
-__device__ __forceinline__ void step_body(const StepArgs& a, const ClassK* kc) {
+__global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR>::value))
+    mg_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ KParam<PM> kp) {
   using SG = Stage<NT>;
+  const ClassK* kc = nullptr;
+  if constexpr (PM == 3) kc = &kp;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0);
@@ -746,21 +762,6 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const ClassK* kc) {
   // A grid launched as a programmatic dependent completes only after the grid
   // it depends on, so that completion stays ordered along the stream.
   asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-template <int NT, int PM, int VAR>
-__global__ void __launch_bounds__(STEP_BLK, StepMinBlocks<VAR>::value) mg_step_kernel(const __grid_constant__ StepArgs a) {
-  step_body<NT, PM, VAR>(a, nullptr);
-}
-
-// Propeller step of one class whose constants travel in the kernel parameters.
-#ifndef MG_KSTEP_MIN_BLOCKS
-#define MG_KSTEP_MIN_BLOCKS MG_STEP_MIN_BLOCKS
-#endif
-template <int NT>
-__global__ void __launch_bounds__(STEP_BLK, MG_KSTEP_MIN_BLOCKS)
-    mg_step_kernel_k(const __grid_constant__ StepArgs a, const __grid_constant__ ClassK kc) {
-  step_body<NT, 3, 0>(a, &kc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1176,11 +1177,9 @@ static size_t step_smem(bool track) {
   return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
 }
 
-// Entry point of a step instantiation (PM 3: class constants as parameters).
 template <int NT, int PM, int VAR>
 static const void* step_fn() {
-  if constexpr (PM == 3) return reinterpret_cast<const void*>(&mg_step_kernel_k<NT>);
-  else return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR>);
+  return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR>);
 }
 
 // Kernel attributes of a step instantiation: the largest dynamic shared
@@ -1226,8 +1225,8 @@ static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, int grid, 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  if constexpr (PM == 3) return cudaLaunchKernelEx(&cfg, mg_step_kernel_k<NT>, a, *kc);
-  else return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a);
+  if constexpr (PM == 3) return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a, *kc);
+  else return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a, NoClassK{});
 }
 
 template <int PM, int VAR>

@@ -559,12 +559,15 @@ int mg_destroy(mg_sim* sim) {
   return MG_OK;
 }
 
+static const mg_sim::Plan& step_plan(mg_sim* sim);
+
 int mg_get_layout(const mg_sim* sim, mg_layout* out) {
   if (!sim || !out) return MG_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
   out->n_classes = sim->n_classes;
   out->n_envs = sim->n_envs;
   out->n_slots = sim->n_slots;
+  out->launches_per_step = (int32_t)step_plan(const_cast<mg_sim*>(sim)).groups.size();
   out->action_floats = sim->act_floats;
   out->state_floats = sim->state_floats;
   for (int c = 0; c < sim->n_classes; ++c) {

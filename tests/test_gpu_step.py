@@ -113,6 +113,39 @@ def test_reset_subset_and_full_size_sampled():
     sim.close()
 
 
+@pytest.mark.parametrize("E,launches", [(1 << 20, 5), (65536, 3)])
+def test_class_constant_step_in_both_launch_shapes(E, launches):
+    """Class-constant hover step, 5 classes, K=4, sampled envs after reset +
+    one step against the oracle. At 1,048,576 envs (the benchmark workload)
+    the step runs one launch per class with the class constants as the kernel
+    parameter; at 65,536 envs one side-by-side launch per thruster count with
+    the constants in shared memory."""
+    classes = vehicles.five_classes()
+    counts = workloads.class_counts(E, 5)
+    sim = make_sim(classes, counts, K=4, reset=dict(vehicles.HOVER), per_env=False)
+    assert sim.launches_per_step() == launches
+    sim.reset(seed=7)
+    rng = np.random.default_rng(8)
+    bounds = np.cumsum(counts)
+    ids = np.sort(rng.choice(E, 1024, replace=False))
+    ids = np.unique(np.concatenate([ids, [0, E - 1], bounds[:-1], bounds[:-1] - 1]))
+    a_s = workloads.actions(11, 1, len(ids))
+    a_env = np.zeros((1, E, 8), np.float32)
+    a_env[:, ids] = a_s
+    sim.step(sim.pack_actions(a_env))
+    torch.cuda.synchronize()
+    gpu = sim.get_state()[ids]
+    envs, s0 = oracle.reset(classes, workloads.env_classes(counts)[ids], vehicles.HOVER, 7, env_ids=ids)
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0, a_s, 0.01, 4)
+    err = rel_state_err(gpu, ref)
+    assert err.max() <= ONE_STEP_TOL, (err.max(), int(ids[np.argmax(err)]))
+    slots = sim.slots_of_envs()[ids]
+    np.testing.assert_allclose(sim.obs.cpu().numpy()[slots], o_ref[0], rtol=2e-5, atol=2e-5)
+    np.testing.assert_allclose(sim.reward.cpu().numpy()[slots], r_ref[0], rtol=1e-5, atol=1e-4)
+    sim.status()
+    sim.close()
+
+
 def test_thousand_step_trajectory_plain_workload():
     """Plain workload: 1024 envs of class 0, no DR, zero current, K=1, dt=0.01,
     1000 steps of uniform actions from rest."""
@@ -345,11 +378,15 @@ def test_host_buffer_step_equals_device_step():
     sim.close()
 
 
-def test_host_buffer_step_chunked_multi_step_equals_device_step():
-    """Sizes that cut every group into several copy/step chunks, 3 steps per call."""
+@pytest.mark.parametrize("per_env", [True, False])
+def test_host_buffer_step_chunked_multi_step_equals_device_step(per_env):
+    """Sizes that cut the launches into several copy/step chunks, 3 steps per
+    call; with class constants the step runs one launch per class."""
     classes = vehicles.five_classes()
-    counts = [300001, 3, 140001, 5, 9]   # the 8-thruster group spans two 2048-tile chunks
-    sim = make_sim(classes, counts, K=1, reset=dict(vehicles.HOVER_DR))
+    counts = [300001, 3, 240001, 5, 9]   # class 0 spans two 2048-tile chunks
+    sim = make_sim(classes, counts, K=1, reset=dict(vehicles.HOVER_DR if per_env else vehicles.HOVER),
+                   per_env=per_env)
+    assert sim.launches_per_step() == (3 if per_env else 5)
     sim.reset(seed=3)
     s0 = sim.get_state()
     a_dev = (torch.rand(3, sim.action_floats, device="cuda") * 2 - 1).contiguous()
