@@ -71,6 +71,12 @@ struct ClassG {
 };
 static_assert(sizeof(ClassG) == (8 + 160) * 4, "ClassG layout");
 
+// Kernel parameter of a one-class launch of a generic-actuator or RK4 step.
+struct ClassKG {
+  ClassK k;
+  ClassG g;
+};
+
 // Per-class constants in FP64 for the finite-difference check path.
 struct ClassD {
   double alloc[6][8];

@@ -1,20 +1,6 @@
-// CUDA kernels of libmarinegym for sm_103a (B300).
-//
-// Data layout in HBM (one GPU, all resident):
-//   * state: per class segment, SoA planes over the segment's n4 slots: the
-//     13 + n_thr fields (p3 q4 nu6 n[n_thr]) grouped as float4 planes plus up
-//     to three scalar planes for the remainder, so one env-step moves exactly
-//     4 (13 + n_thr) bytes each way with 512-byte coalesced warp accesses;
-//   * parameters: 10 float4 planes over all slots (9 planes = 36 physical
-//     floats, 1 plane = hover target); class-constant runs read only the
-//     target plane and take the physics from the class table;
-//   * actions: per class, row-major [n4][n_thr] (a policy's natural output);
-//   * observations: [slot][13] row-major, written through a shared-memory
-//     tile so that global stores are full 16-byte vectors.
-// One thread advances one env through all K substeps (and all steps of a
-// multi-step launch) with the state in registers; class constants live in
-// shared memory and are read as warp-uniform broadcasts. Nothing here is a
-// dense contraction, so there are no tensor-core paths.
+// CUDA kernels of libmarinegym for sm_103a (B300) other than the step kernel
+// (mg_step.cuh): reset with domain randomisation, set_hydro, the adjoint and
+// the FP64 check path, and the launch dispatchers the runtime calls.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,745 +10,9 @@
 #include "mg_internal.h"
 #include "mg_device.cuh"
 #include "mg_payload.h"
+#include "mg_step.cuh"
 
 namespace mg {
-
-template <int NT>
-struct Lay {
-  static constexpr int SS = 13 + NT;
-  static constexpr int NF4 = SS / 4;
-  static constexpr int REM = SS % 4;
-};
-
-template <int NT>
-__device__ __forceinline__ void fields_to_state(const float (&f)[13 + NT], St<float, NT>& x) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) x.p[i] = f[i];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) x.q[i] = f[3 + i];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) x.nu[i] = f[7 + i];
-#pragma unroll
-  for (int i = 0; i < NT; ++i) x.n[i] = f[13 + i];
-}
-
-template <int NT>
-__device__ __forceinline__ void state_to_fields(const St<float, NT>& x, float (&f)[13 + NT]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) f[i] = x.p[i];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) f[3 + i] = x.q[i];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) f[7 + i] = x.nu[i];
-#pragma unroll
-  for (int i = 0; i < NT; ++i) f[13 + i] = x.n[i];
-}
-
-template <int NT>
-__device__ __forceinline__ void load_state(const float* base, int64_t n4, int64_t i, St<float, NT>& x) {
-  float f[13 + NT];
-  const float4* p4 = reinterpret_cast<const float4*>(base);
-#pragma unroll
-  for (int k = 0; k < Lay<NT>::NF4; ++k) {
-    const float4 v = p4[k * n4 + i];
-    f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
-  }
-  const float* pr = base + (int64_t)Lay<NT>::NF4 * 4 * n4;
-#pragma unroll
-  for (int r = 0; r < Lay<NT>::REM; ++r) f[Lay<NT>::NF4 * 4 + r] = pr[r * n4 + i];
-  fields_to_state<NT>(f, x);
-}
-
-template <int NT>
-__device__ __forceinline__ void store_state(float* base, int64_t n4, int64_t i, const St<float, NT>& x) {
-  float f[13 + NT];
-  state_to_fields<NT>(x, f);
-  float4* p4 = reinterpret_cast<float4*>(base);
-#pragma unroll
-  for (int k = 0; k < Lay<NT>::NF4; ++k)
-    p4[k * n4 + i] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
-  float* pr = base + (int64_t)Lay<NT>::NF4 * 4 * n4;
-#pragma unroll
-  for (int r = 0; r < Lay<NT>::REM; ++r) pr[r * n4 + i] = f[Lay<NT>::NF4 * 4 + r];
-}
-
-__device__ __forceinline__ void load_phys(const float4* planes, int64_t n_slots, int64_t slot, Phys<float>& P) {
-  float v[36];
-#pragma unroll
-  for (int k = 0; k < PAR_PLANES; ++k) {
-    const float4 a = __ldg(&planes[k * n_slots + slot]);
-    v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
-  }
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    P.minv[j] = v[PAR_MINV + j]; P.A[j] = v[PAR_A + j]; P.dl[j] = v[PAR_DL + j]; P.dq[j] = v[PAR_DQ + j];
-  }
-  P.m = v[PAR_M];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) { P.Ig[j] = v[PAR_IG + j]; P.rb[j] = v[PAR_RB + j]; P.Vc[j] = v[PAR_VC + j]; }
-  P.W = v[PAR_W]; P.B = v[PAR_B];
-}
-
-// Segment of a tile: binary search over tile_begin (segments sorted). The
-// table may live in global or in shared memory, so the loads are generic.
-__device__ __forceinline__ int find_seg(const SegDesc* segs, int n_segs, int tile) {
-  int lo = 0, hi = n_segs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ float clamp1(float a) { return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a); }
-
-// Serving action from one 64-bit Philox output: top 24 bits k -> k 2^-23 - 1,
-// exact in FP32, on [-1, 1).
-__device__ __forceinline__ float action_of_bits(uint64_t bits) {
-  return (float)(int)(bits >> 40) * (1.0f / 8388608.0f) - 1.0f;
-}
-
-template <int NT>
-__device__ __forceinline__ void load_actions(const float* base, float (&a)[NT]) {
-  if constexpr (NT % 4 == 0) {
-#pragma unroll
-    for (int k = 0; k < NT / 4; ++k) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(base) + k);
-      a[4 * k] = v.x; a[4 * k + 1] = v.y; a[4 * k + 2] = v.z; a[4 * k + 3] = v.w;
-    }
-  } else if constexpr (NT % 2 == 0) {
-#pragma unroll
-    for (int k = 0; k < NT / 2; ++k) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(base) + k);
-      a[2 * k] = v.x; a[2 * k + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NT; ++k) a[k] = __ldg(base + k);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Shared-memory views read at the point of use. Class constants and per-env
-// parameters stay in shared memory (vector loads for the actuator table)
-// instead of occupying registers across the substep loop. The loads are plain
-// (non-volatile) inline PTX, free to be scheduled within a substep; the step
-// loop passes them a base address made opaque once per substep, so that they
-// are neither hoisted out of the loop nor moved above the barrier that
-// follows a table rewrite.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ float lds1(unsigned a) {
-  float v;
-  asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ float4 lds4(unsigned a) {
-  float4 v;
-  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-  return v;
-}
-
-// Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
-// dz_on = 0: the class has no dead zone (the thrust skips the test).
-#ifndef MG_DZ_FLAG
-#define MG_DZ_FLAG 1
-#endif
-// DZF: the kernel carries a dead-zone-free thrust path (class-constant
-// propellers only: in the other variants the second path costs registers).
-template <bool DZF>
-struct ActSmemT {
-  unsigned base;
-  unsigned dz_on;
-};
-template <bool DZF>
-__device__ __forceinline__ bool dz_active(const ActSmemT<DZF>& A) { return !(MG_DZ_FLAG && DZF) || A.dz_on != 0u; }
-// Class constants as a kernel parameter: the dead-zone test is skipped for
-// classes without one.
-__device__ __forceinline__ bool dz_active(const ClassK& k) { return !MG_DZ_FLAG || k.dz_on != 0u; }
-enum { SA_ALLOC = 0, SA_KF = 48, SA_DZ = 56, SA_ALPHA = 64, SA_DIM = 72 };
-
-template <int NT>
-__device__ __forceinline__ void lds_vec(unsigned a, float (&r)[NT]) {
-#pragma unroll
-  for (int q = 0; q < (NT + 3) / 4; ++q) {
-    const float4 v = lds4(a + 16 * q);
-    if (4 * q + 0 < NT) r[(4 * q + 0) % NT] = v.x;
-    if (4 * q + 1 < NT) r[(4 * q + 1) % NT] = v.y;
-    if (4 * q + 2 < NT) r[(4 * q + 2) % NT] = v.z;
-    if (4 * q + 3 < NT) r[(4 * q + 3) % NT] = v.w;
-  }
-}
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_row(const ActSmemT<DZF>& A, int k, S (&r)[NT]) {
-  lds_vec<NT>(A.base + 4 * (SA_ALLOC + 8 * k), r);
-}
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor(const ActSmemT<DZF>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
-  lds_vec<NT>(A.base + 4 * SA_KF, kf);
-  lds_vec<NT>(A.base + 4 * SA_DZ, dz);
-  lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
-}
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor_nodz(const ActSmemT<DZF>& A, S (&kf)[NT], S (&al)[NT]) {
-  lds_vec<NT>(A.base + 4 * SA_KF, kf);
-  lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
-}
-
-// Physical parameters in shared memory, field f at base + 4 * f * STRIDE
-// (STRIDE = 1: class block read as a broadcast; STRIDE = tile width: per-env
-// columns, one per thread, bank-conflict free).
-template <int OFF, int STRIDE>
-struct SArr {
-  unsigned base;
-  __device__ __forceinline__ float operator[](int j) const { return lds1(base + 4u * (unsigned)((OFF + j) * STRIDE)); }
-};
-template <int OFF, int STRIDE>
-struct SScl {
-  unsigned base;
-  __device__ __forceinline__ operator float() const { return lds1(base + 4u * (unsigned)(OFF * STRIDE)); }
-};
-template <int STRIDE>
-struct PhysSmem {
-  static constexpr bool kFull = false;
-  SArr<PAR_MINV, STRIDE> minv;
-  SArr<PAR_A, STRIDE> A;
-  SArr<PAR_DL, STRIDE> dl;
-  SArr<PAR_DQ, STRIDE> dq;
-  SScl<PAR_M, STRIDE> m;
-  SArr<PAR_IG, STRIDE> Ig;
-  SScl<PAR_W, STRIDE> W;
-  SScl<PAR_B, STRIDE> B;
-  SArr<PAR_RB, STRIDE> rb;
-  SArr<PAR_VC, STRIDE> Vc;
-  __device__ __forceinline__ explicit PhysSmem(unsigned b)
-      : minv{b}, A{b}, dl{b}, dq{b}, m{b}, Ig{b}, W{b}, B{b}, rb{b}, Vc{b} {}
-};
-
-// Payload runs: per-env columns staged from physics planes 1-5, 7, 8 (columns
-// 0-27) and payload planes 0-7 (columns 28-59). The diagonal inverse, the
-// vehicle's own mass and inertia and its weight are not needed: the combined
-// body's full inverse, inertia about the origin, first moment, mass and
-// weight replace them.
-enum { PF_A = 2, PF_DL = 8, PF_DQ = 14, PF_B = 21, PF_RB = 22, PF_VC = 25, PF_PAY = 28, PF_DIM = 60 };
-constexpr int PF_STD_PLANES = 7;                       // physics planes staged
-constexpr int PF_PAY_PLANES = 8;                       // payload planes staged
-__device__ __forceinline__ int pf_std_plane(int k) { return k < 5 ? k + 1 : k + 2; }   // 1..5, 7, 8
-template <int STRIDE>
-struct PhysSmemFull {
-  static constexpr bool kFull = true;
-  SArr<PF_A, STRIDE> A;
-  SArr<PF_DL, STRIDE> dl;
-  SArr<PF_DQ, STRIDE> dq;
-  SScl<PF_B, STRIDE> B;
-  SArr<PF_RB, STRIDE> rb;
-  SArr<PF_VC, STRIDE> Vc;
-  SArr<PF_PAY + PAY_MINV, STRIDE> Mi;
-  SArr<PF_PAY + PAY_IO, STRIDE> Io;
-  SArr<PF_PAY + PAY_S, STRIDE> s;
-  SScl<PF_PAY + PAY_M, STRIDE> m;
-  SScl<PF_PAY + PAY_W, STRIDE> W;
-  __device__ __forceinline__ explicit PhysSmemFull(unsigned b)
-      : A{b}, dl{b}, dq{b}, B{b}, rb{b}, Vc{b}, Mi{b}, Io{b}, s{b}, m{b}, W{b} {}
-};
-static_assert(PF_STD_PLANES * 4 == PF_PAY && PF_PAY + PF_PAY_PLANES * 4 == PF_DIM, "payload column map");
-static_assert(PAY_W < PF_PAY_PLANES * 4, "staged payload planes hold the step's fields");
-
-// Generic actuator table in shared memory: 8 kinds (float bits), then
-// GEN_VALS values per channel (a copy of the class's ClassG).
-constexpr int GEN_FLOATS = 8 + 8 * GEN_VALS;
-static_assert(sizeof(ClassG) == GEN_FLOATS * sizeof(float), "generic table layout");
-static_assert(KIND_PROP == MG_ACT_PROP && KIND_SERVO == MG_ACT_SERVO && KIND_FIN == MG_ACT_FIN &&
-                  KIND_TILT == MG_ACT_TILT, "actuator kinds");
-struct GenSmem {
-  unsigned base;
-  __device__ __forceinline__ int kind(int i) const { return __float_as_int(lds1(base + 4u * (unsigned)i)); }
-  __device__ __forceinline__ float v(int i, int k) const {
-    return lds1(base + 4u * (unsigned)(8 + i * GEN_VALS + k));
-  }
-};
-
-constexpr int STEP_BLK = 128;
-#ifndef MG_STEP_MIN_BLOCKS
-#define MG_STEP_MIN_BLOCKS 4
-#endif
-
-
-// ---------------------------------------------------------------------------
-// Bulk-copy (1-D TMA) and mbarrier helpers.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// Global -> shared bulk copy completing on `bar` (addresses 16-byte aligned,
-// size a multiple of 16).
-__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// Shared -> global bulk copy in the current bulk group.
-__device__ __forceinline__ void bulk_store(void* dst, unsigned src, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Bounded wait on an mbarrier phase: gives up after `limit_ns` and reports it.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-  return true;
-}
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
-
-// Per-warp stage buffer: the warp's 32 envs of one tile. State planes (NF4
-// float4 planes, then REM float planes, 32 entries each), actions [32][NT],
-// target [32] float4. Each warp of a block owns two stage buffers and one
-// observation buffer [32][13] and runs its own copy pipeline.
-#ifndef MG_OBS_ALIAS
-#define MG_OBS_ALIAS 0
-#endif
-constexpr int WENV = 32;
-constexpr int N_WARPS = STEP_BLK / WENV;
-template <int NT>
-struct Stage {
-  static constexpr int SS = 13 + NT, NF4 = SS / 4, REM = SS % 4;
-  static constexpr int ACT_OFF = WENV * SS;                     // floats
-  static constexpr int TGT_OFF = ACT_OFF + WENV * NT;           // floats (16-byte aligned)
-  static constexpr int TRJ_OFF = TGT_OFF + 4 * WENV;            // 3 trajectory planes (tracking runs only)
-  static constexpr int OBS = WENV * 13;
-  // Stage buffer and per-warp sizes (floats); smaller shared memory pays off,
-  // so the trajectory section exists only in tracking runs.
-  static __host__ __device__ constexpr int floats(bool track) { return TRJ_OFF + (track ? 12 * WENV : 0); }
-#if MG_OBS_ALIAS
-  // The observation tile reuses the tile's own stage buffer once its inputs
-  // are in registers (rows 0..12 per env lie below the trajectory section).
-  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track); }
-  static_assert(OBS <= TRJ_OFF, "observation tile must fit below the trajectory section");
-#else
-  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track) + OBS; }
-#endif
-  static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (OBS % 4) == 0,
-                "16-byte aligned sections");
-};
-constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
-
-// Class tables of segment `sd` into act (SA_DIM) and phys (PAR_DIM), and its
-// generic actuator table into gen (generic variants), by the block's threads.
-template <int VAR>
-__device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& sd, float* act, float* phys,
-                                             float* gen, int tid) {
-  const ClassF& cf = a.classes[sd.cls];
-  for (int k = tid; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
-    if (k < 48) act[k] = cf.alloc[k / 8][k % 8];
-    else if (k < 56) act[k] = cf.kf[k - 48];
-    else if (k < 64) act[k] = cf.dz[k - 56];
-    else if (k < 72) act[k] = sd.alpha[k - 64];
-    else phys[k - 72] = cf.phys[k - 72];
-  }
-  if (VAR) {
-    const float* g = reinterpret_cast<const float*>(a.gen + sd.cls);
-    for (int k = tid; k < GEN_FLOATS; k += STEP_BLK) gen[k] = g[k];
-  }
-}
-
-// Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
-// (a multiple of 4, > 0) envs start at local env index w0 of the segment.
-template <int NT, int PM>
-__device__ __forceinline__ void issue_warp_loads(const StepArgs& a, const SegDesc& sd, int64_t w0, unsigned nvw,
-                                                 float* buf, unsigned bar) {
-  constexpr bool PER_ENV = PM == 1 || PM == 2;
-  using SG = Stage<NT>;
-  const float* st = a.state + sd.st_off;
-  unsigned bytes = SG::NF4 * nvw * 16 + SG::REM * nvw * 4 + nvw * 16;
-  const bool load_act = a.n_steps > 0 && a.act_mode == 0;
-  if (load_act) bytes += nvw * NT * 4;
-  const bool trj = a.track != 0;   // the launch's layout has the trajectory section
-  if (trj) bytes += 3 * nvw * 16;
-  mbar_expect_tx(bar, bytes);
-  const unsigned b = smem_addr(buf);
-#pragma unroll
-  for (int k = 0; k < SG::NF4; ++k) bulk_load(b + 16u * k * WENV, st + ((int64_t)k * sd.n4 + w0) * 4, nvw * 16, bar);
-#pragma unroll
-  for (int r = 0; r < SG::REM; ++r)
-    bulk_load(b + 16u * SG::NF4 * WENV + 4u * r * WENV, st + (int64_t)SG::NF4 * 4 * sd.n4 + (int64_t)r * sd.n4 + w0,
-              nvw * 4, bar);
-  if (load_act) bulk_load(b + 4u * SG::ACT_OFF, a.actions + sd.act_off + w0 * NT, nvw * NT * 4, bar);
-  bulk_load(b + 4u * SG::TGT_OFF, a.planes + tgt_plane(PER_ENV) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
-  if (trj) {
-#pragma unroll
-    for (int q = 0; q < TRAJ_PLANES; ++q)
-      bulk_load(b + 4u * (SG::TRJ_OFF + 4 * q * WENV),
-                a.planes + (int64_t)(tgt_plane(PER_ENV) + 1 + q) * a.n_slots + sd.slot_off + w0, nvw * 16, bar);
-  }
-}
-
-// Envs of warp `warp` in a tile that starts at local env local0 (0 if none).
-__device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0, int warp) {
-  const int64_t n = (int64_t)sd.n4 - local0 - (int64_t)warp * WENV;
-  return n <= 0 ? 0u : (unsigned)min((int64_t)WENV, n);
-}
-
-template <int NT, int PM, int VAR>
-__device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, const SegDesc& sd, int tile,
-                                          unsigned s_act, unsigned s_phys, unsigned s_gen, const float* buf,
-                                          float* obs_w, float* s_par, int& n_emit) {
-  constexpr bool PER_ENV = PM == 1 || PM == 2;
-  using SG = Stage<NT>;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t local0 = (int64_t)(tile - sd.tile_begin) * STEP_BLK;
-  const int64_t w0 = local0 + warp * WENV;
-  const int64_t i = w0 + lane;
-  const bool valid = i < sd.n_envs;
-  const bool in_storage = i < sd.n4;
-  const unsigned nvw = warp_envs(sd, local0, warp);
-  const int64_t slot = sd.slot_off + i;
-  float* st_base = a.state + sd.st_off;
-  using ActSmem = ActSmemT<PM == 0 && VAR == 0>;
-  const ActSmem A{s_act, (unsigned)(sd.flags & 1)};
-
-  // Per-env parameters: plain per-env runs prefetch their 9 planes into
-  // registers here (their loads overlap the stage reads below); payload runs
-  // copy 15 planes straight to shared memory afterwards.
-  constexpr bool STAGE_PAR = PM == 1;
-  float4 pv[STAGE_PAR ? PAR_PLANES : 1];
-  if (STAGE_PAR && valid) {
-#pragma unroll
-    for (int k = 0; k < PAR_PLANES; ++k) pv[k % (STAGE_PAR ? PAR_PLANES : 1)] = __ldg(&a.planes[k * a.n_slots + slot]);
-  }
-  St<float, NT> x;
-  float c[NT];
-  float tgt[3] = {0.0f, 0.0f, 0.0f};
-  float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-  for (int j = 0; j < NT; ++j) c[j] = 0.0f;
-  bool have_act0 = false;
-  if (valid) {
-    float f[13 + NT];
-    const float4* p4 = reinterpret_cast<const float4*>(buf);
-#pragma unroll
-    for (int k = 0; k < SG::NF4; ++k) {
-      const float4 v = p4[k * WENV + lane];
-      f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
-    }
-#pragma unroll
-    for (int r = 0; r < SG::REM; ++r) f[(SG::NF4 * 4 + r) % (13 + NT)] = buf[SG::NF4 * 4 * WENV + r * WENV + lane];
-    fields_to_state<NT>(f, x);
-    tg = reinterpret_cast<const float4*>(buf + SG::TGT_OFF)[lane];
-    tgt[0] = tg.x; tgt[1] = tg.y; tgt[2] = tg.z;
-    if (a.n_steps > 0 && a.act_mode == 0) {
-#pragma unroll
-      for (int j = 0; j < NT; ++j) c[j] = clamp1(buf[SG::ACT_OFF + lane * NT + j]);
-      have_act0 = true;
-    }
-  }
-  if (STAGE_PAR && valid) {
-#pragma unroll
-    for (int k = 0; k < PAR_PLANES; ++k) {
-      const float4 v = pv[k % (STAGE_PAR ? PAR_PLANES : 1)];
-      s_par[(4 * k + 0) * STEP_BLK + tid] = v.x;
-      s_par[(4 * k + 1) * STEP_BLK + tid] = v.y;
-      s_par[(4 * k + 2) * STEP_BLK + tid] = v.z;
-      s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
-    }
-  }
-  if (PM == 2 && valid) {
-#pragma unroll
-    for (int k = 0; k < PF_STD_PLANES + PF_PAY_PLANES; ++k) {
-      const int plane = k < PF_STD_PLANES ? pf_std_plane(k) : a.pay_plane + (k - PF_STD_PLANES);
-      const float4 v = __ldg(&a.planes[(int64_t)plane * a.n_slots + slot]);
-      s_par[(4 * k + 0) * STEP_BLK + tid] = v.x;
-      s_par[(4 * k + 1) * STEP_BLK + tid] = v.y;
-      s_par[(4 * k + 2) * STEP_BLK + tid] = v.z;
-      s_par[(4 * k + 3) * STEP_BLK + tid] = v.w;
-    }
-  }
-  // Each thread reads only its own parameter column: no barrier needed.
-  using PV = std::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
-  const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : s_phys;
-  const unsigned g_base = s_gen;
-  const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
-  for (int t = 0; t < n_out_steps; ++t) {
-    if (valid && a.n_steps > 0) {
-      if (a.act_mode == 0) {
-        if (!(t == 0 && have_act0)) {
-          float raw[NT];
-          load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
-#pragma unroll
-          for (int j = 0; j < NT; ++j) c[j] = clamp1(raw[j]);
-        }
-      } else {
-#pragma unroll
-        for (int g = 0; g < (NT + 3) / 4; ++g) {
-          uint64_t o[4];
-          philox4x64((uint64_t)i, (uint64_t)(sd.step0 + t), (uint64_t)g, 0, sd.seed, STREAM_ACTION, o);
-#pragma unroll
-          for (int l = 0; l < 4; ++l)
-            if (4 * g + l < NT) c[(4 * g + l) % NT] = clamp1(action_of_bits(o[l]));
-        }
-      }
-      if (a.ckpt && (t % a.ckpt_every) == 0) {
-        float f[13 + NT];
-        state_to_fields<NT>(x, f);
-        float* ck = a.ckpt + (int64_t)(t / a.ckpt_every) * 21 * a.n_slots + slot;
-#pragma unroll
-        for (int j = 0; j < 21; ++j) ck[j * a.n_slots] = (j < 13 + NT) ? f[j % (13 + NT)] : 0.0f;
-      }
-      // Shared-memory bases made opaque once per substep: loads may be
-      // scheduled freely inside a substep but not hoisted out of the loop.
-      for (int k = 0; k < sd.K; ++k) {
-        if constexpr (PM == 3) {
-          // Class constants are kernel parameters: read as operands.
-          substep<float, NT, false, ClassK, ClassK, false>(x, c, *kc, *kc, sd.h, nullptr);
-        } else {
-          unsigned pb = p_base, ab = A.base, gb = g_base;
-          asm volatile("" : "+r"(pb), "+r"(ab), "+r"(gb));
-          const ActSmem Ak{ab, A.dz_on};
-          // Class-constant physics carries no current (zero by construction).
-          const PV Pk(pb);
-          if constexpr (VAR == 0) {
-            substep<float, NT, false, ActSmem, PV, PER_ENV>(x, c, Pk, Ak, sd.h, nullptr);
-          } else if constexpr (VAR == 1) {
-            substep<float, NT, false, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, nullptr, GenSmem{gb});
-          } else {
-            substep_rk4<float, NT, ActSmem, PV, PER_ENV, GenSmem>(x, c, Pk, Ak, sd.h, GenSmem{gb});
-          }
-        }
-      }
-    }
-    const bool emit = a.obs_every || t == n_out_steps - 1;
-    if (emit) {
-      const int64_t out = a.obs_every ? t : 0;
-      float o[13], r = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 13; ++j) o[j] = 0.0f;
-      if (valid) {
-        if (a.track) {
-          // Tracking reference at the end of this step (counter k0 + t + 1);
-          // its parameters were staged with the tile.
-          const float4* tp = reinterpret_cast<const float4*>(buf + SG::TRJ_OFF) + lane;
-          const float kk = tg.w + (a.n_steps > 0 ? (float)(t + 1) : 0.0f);
-          track_ref<float>(tg, tp[0], tp[WENV], tp[2 * WENV], sd.dt, kk, tgt);
-        }
-        observe<float, NT>(x, c, tgt, o, r);
-      }
-      if (a.obs && nvw > 0) {
-        // The warp's previous observation store must have read its buffer.
-        if (lane == 0 && n_emit > 0) bulk_wait_read0();
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 13; ++j) obs_w[lane * 13 + j] = o[j];
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          bulk_store(a.obs + (out * a.n_slots + sd.slot_off + w0) * 13, smem_addr(obs_w), nvw * 52u);
-          bulk_commit();
-        }
-        ++n_emit;
-      }
-      if (a.reward && in_storage) a.reward[out * a.n_slots + slot] = valid ? r : 0.0f;
-      if (a.ret && valid && a.n_steps > 0) a.ret[slot] += r;
-    }
-  }
-  if (valid && a.n_steps > 0) {
-    store_state<NT>(st_base, sd.n4, i, x);
-    if (a.track) {
-      // Advance the env's step counter (w lane of its target plane entry).
-      float* kp = reinterpret_cast<float*>(const_cast<float4*>(a.planes) + (int64_t)tgt_plane(PER_ENV) * a.n_slots + slot);
-      kp[3] = tg.w + (float)a.n_steps;
-    }
-    float s = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) s += x.p[j];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) s += x.q[j];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) s += x.nu[j];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) s += x.n[j];
-    if (!isfinite(s)) atomicOr(a.status, 1u);
-  }
-  return true;
-}
-
-// Persistent step kernel for envs with NT thrusters. Block b walks the tiles
-// tile_lo + b, + gridDim.x, ...; a tile is 128 envs of one segment, 32 per
-// warp. Every warp runs its own pipeline: while it computes its slice of tile
-// j, its lane 0 has already issued the bulk copies of its slice of the next
-// tile into the warp's other stage buffer, and observation rows leave through
-// a per-warp bulk store. Warps never wait on one another except when the
-// class constants change. Every wait is bounded (2 s); a warp that gives up
-// sets bit 1 of the status word and skips the rest of its tiles (it keeps
-// walking them, so every block barrier is still reached).
-// The RK4 variant keeps the stage point, the running sum and the substep's
-// start state live at once. It is compiled for 3 resident blocks per SM (168
-// registers): measured at 1M envs, K=4, that beats both 4 blocks (heavy
-// spills) and 2 blocks (too few warps to hide latency), although the tracking
-// and per-env kernels still spill a few hundred bytes. The generic-actuator
-// variant (fins, servo tilt) is also compiled for 3 blocks per SM: its extra
-// live state otherwise costs 3% at K=4 and 8% at K=1.
-#ifndef MG_RK4_MIN_BLOCKS
-#define MG_RK4_MIN_BLOCKS 3
-#endif
-#ifndef MG_GEN_MIN_BLOCKS
-#define MG_GEN_MIN_BLOCKS 3
-#endif
-#ifndef MG_KSTEP_MIN_BLOCKS
-#define MG_KSTEP_MIN_BLOCKS MG_STEP_MIN_BLOCKS
-#endif
-template <int PM, int VAR>
-struct StepMinBlocks {
-  static constexpr int value = VAR == 2 ? MG_RK4_MIN_BLOCKS
-                               : VAR == 1 ? MG_GEN_MIN_BLOCKS
-                               : PM == 3  ? MG_KSTEP_MIN_BLOCKS
-                                          : MG_STEP_MIN_BLOCKS;
-};
-
-// Second kernel parameter: the class constants (PM 3), else nothing.
-struct NoClassK {};
-template <int PM>
-using KParam = std::conditional_t<PM == 3, ClassK, NoClassK>;
-
-// PM: parameter source (0 class constants staged in shared memory, 1 per-env
-// planes, 2 per-env planes with the payload, 3 class constants passed as the
-// kernel parameter `kp`: one class per launch). The body stays in the kernel
-// itself: moved into a function taking the parameters by reference, the
-// per-env and payload instantiations spilled.
-template <int NT, int PM, int VAR>
-__global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR>::value))
-    mg_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ KParam<PM> kp) {
-  using SG = Stage<NT>;
-  const ClassK* kc = nullptr;
-  if constexpr (PM == 3) kc = &kp;
-  extern __shared__ __align__(16) float s_dyn[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0);
-  float* const w_base = s_dyn + warp * wfl;
-  float* const buf0 = w_base;
-  float* const buf1 = w_base + fl;
-  float* const obs_sep = w_base + 2 * fl;   // separate observation tile (unless aliased)
-  float* const s_par = s_dyn + N_WARPS * wfl;
-  __shared__ __align__(16) float s_act[SA_DIM];
-  __shared__ __align__(16) float s_phys[PAR_DIM];
-  __shared__ __align__(16) float s_gen[VAR ? GEN_FLOATS : 4];
-  __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
-  __shared__ SegDesc s_seg[SEG_CACHE];
-  // The next launch of a step (another thruster count, disjoint envs) may
-  // start filling SMs as soon as this grid's blocks are resident.
-  // The first launch of a step may become resident while the previous step
-  // (same envs) finishes: it waits for that work to complete before it reads
-  // anything or lets its own dependents start, so that every later launch of
-  // the step also follows the whole previous step.
-  if (a.wait_first) asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if ((int)blockIdx.x >= a.n_tiles) return;
-  const int n_seg = a.seg_hi - a.seg_lo;
-  const bool cached = n_seg <= SEG_CACHE;
-  if (cached) {
-    const int32_t* src = reinterpret_cast<const int32_t*>(a.segs + a.seg_lo);
-    int32_t* dst = reinterpret_cast<int32_t*>(s_seg);
-    for (int k = tid; k < n_seg * (int)(sizeof(SegDesc) / 4); k += STEP_BLK) dst[k] = src[k];
-  }
-  const SegDesc* segs = cached ? s_seg : a.segs + a.seg_lo;
-  const unsigned full0 = smem_addr(&s_bar[warp][0]), full1 = smem_addr(&s_bar[warp][1]);
-  if (lane == 0) {
-    mbar_init(full0, 1);
-    mbar_init(full1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // Prologue: this warp's slice of the first tile.
-  unsigned nvw_cur = 0;
-  {
-    const int tile0 = a.tile_lo + blockIdx.x;
-    const SegDesc& s0 = segs[find_seg(segs, n_seg, tile0)];
-    const int64_t local0 = (int64_t)(tile0 - s0.tile_begin) * STEP_BLK;
-    nvw_cur = warp_envs(s0, local0, warp);
-    if (lane == 0 && nvw_cur > 0 && !(s0.flags & 2))
-      issue_warp_loads<NT, PM>(a, s0, local0 + warp * WENV, nvw_cur, buf0, full0);
-  }
-  int prev_seg = -1, n_emit = 0;
-  unsigned use[2] = {0u, 0u};   // completed uses of each stage barrier
-  bool failed = false;
-  for (int j = 0, tt = blockIdx.x; tt < a.n_tiles; ++j, tt += gridDim.x) {
-    const int tile = a.tile_lo + tt;
-    const int b = j & 1;
-    const int si = find_seg(segs, n_seg, tile);
-    // Refill the other buffer (read during tile j - 1) with the next slice.
-    const int tt_next = tt + gridDim.x;
-    unsigned nvw_next = 0;
-    if (tt_next < a.n_tiles) {
-      const int tile_n = a.tile_lo + tt_next;
-      const SegDesc& sn = segs[find_seg(segs, n_seg, tile_n)];
-      const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
-      nvw_next = warp_envs(sn, ln, warp);
-      if (lane == 0 && nvw_next > 0 && !failed && !(sn.flags & 2)) {
-#if MG_OBS_ALIAS
-        // The buffer may still be the source of the previous tile's observation store.
-        bulk_wait_read0();
-#endif
-        fence_async_smem();
-        issue_warp_loads<NT, PM>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
-      }
-    }
-    const SegDesc& sd = segs[si];
-    if (PM != 3 && si != prev_seg) {
-      // Class constants change: rewrite them between two block barriers
-      // (every warp of the block walks the same tiles).
-      __syncthreads();
-      stage_tables<VAR>(a, sd, s_act, s_phys, s_gen, tid);
-      __syncthreads();
-      prev_seg = si;
-    }
-    // A warp whose wait ran out stops computing and copying but stays in the
-    // loop, so that it still reaches every block barrier of the launch.
-    if (nvw_cur > 0 && !failed) {
-      if (mbar_wait_bounded(b ? full1 : full0, use[b] & 1u, sd.wait_limit_ns ? sd.wait_limit_ns : kWaitLimitNs))
-        use[b]++;
-      else
-        failed = true;
-    }
-    if (!failed)
-      step_tile<NT, PM, VAR>(a, kc, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen),
-                             b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
-    // The warp has read its stage buffer b; lane 0 may refill it next round.
-    __syncwarp();
-    nvw_cur = nvw_next;
-  }
-  if (failed && lane == 0) atomicOr(a.status, 2u);
-  // Observation stores must finish reading shared memory before the warp exits.
-  if (lane == 0) bulk_wait0();
-  // A grid launched as a programmatic dependent completes only after the grid
-  // it depends on, so that completion stays ordered along the stream.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
 
 // ---------------------------------------------------------------------------
 // Reset: domain randomisation draws and initial state (FP64 arithmetic).
@@ -1157,113 +407,6 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
 // ---------------------------------------------------------------------------
 // Host-side launchers (called by the runtime).
 // ---------------------------------------------------------------------------
-#define MG_NT_SWITCH(nt, CALL) \
-  switch (nt) {                   \
-    case 1: CALL(1); break;       \
-    case 2: CALL(2); break;       \
-    case 3: CALL(3); break;       \
-    case 4: CALL(4); break;       \
-    case 5: CALL(5); break;       \
-    case 6: CALL(6); break;       \
-    case 7: CALL(7); break;       \
-    case 8: CALL(8); break;       \
-    default: return cudaErrorInvalidValue; \
-  }
-
-// Dynamic shared memory of mg_step_kernel<NT, PM, *>.
-template <int NT, int PM>
-static size_t step_smem(bool track) {
-  const int cols = PM == 2 ? PF_DIM : (PM == 1 ? PAR_DIM : 0);
-  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
-}
-
-template <int NT, int PM, int VAR>
-static const void* step_fn() {
-  return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR>);
-}
-
-// Kernel attributes of a step instantiation: the largest dynamic shared
-// memory of its layouts (tracking).
-template <int NT, int PM, int VAR>
-static cudaError_t step_attrs() {
-  static bool done = false;   // per instantiation, per process (one device)
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem<NT, PM>(true));
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
-// Shared-memory carveout of the next launch of an instantiation: the largest
-// (`shared_sm`) or the driver's default; set only when it changes.
-template <int NT, int PM, int VAR>
-static cudaError_t step_carveout(bool shared_sm) {
-  static int current = -2;   // per instantiation, per process (one device)
-  const int want = shared_sm ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault;
-  if (want == current) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR>(), cudaFuncAttributePreferredSharedMemoryCarveout, want);
-  if (e == cudaSuccess) current = want;
-  return e;
-}
-
-// `dependent`: launch as a programmatic dependent of the previous kernel in
-// the stream (the previous launch of the same step, on disjoint envs).
-template <int NT, int PM, int VAR>
-static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, int grid, bool dependent, bool shared_sm,
-                                 cudaStream_t st) {
-  const size_t smem = step_smem<NT, PM>(a.track != 0);
-  cudaError_t e = step_attrs<NT, PM, VAR>();
-  if (e == cudaSuccess) e = step_carveout<NT, PM, VAR>(shared_sm);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(STEP_BLK);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  if constexpr (PM == 3) return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a, *kc);
-  else return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR>, a, NoClassK{});
-}
-
-template <int PM, int VAR>
-static cudaError_t launch_step_pv(const StepArgs& a, const ClassK* kc, int nt, int grid, bool dependent,
-                                  bool shared_sm, cudaStream_t st) {
-#define MG_L(N) return launch_step_t<N, PM, VAR>(a, kc, grid, dependent, shared_sm, st)
-  MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  return cudaErrorInvalidValue;
-}
-
-// Step launch of one class group: thruster count nt, parameter source
-// a.per_env (0 class, 1 per-env, 2 payload), variant var (0 propellers with
-// Euler, 1 generic actuators with Euler, 2 RK4). `kc` (class-constant
-// propeller steps whose segments are all of one class, else null): that
-// class's constants, passed as a kernel parameter.
-cudaError_t launch_step(const StepArgs& a, const ClassK* kc, int nt, int var, int grid, bool dependent,
-                        bool shared_sm, cudaStream_t st) {
-  if (a.n_tiles <= 0) return cudaSuccess;
-  if (kc) {
-    if (a.per_env != 0 || var != 0) return cudaErrorInvalidValue;
-    return launch_step_pv<3, 0>(a, kc, nt, grid, dependent, shared_sm, st);
-  }
-  switch (a.per_env * 3 + var) {
-    case 0: return launch_step_pv<0, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 1: return launch_step_pv<0, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 2: return launch_step_pv<0, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 3: return launch_step_pv<1, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 4: return launch_step_pv<1, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 5: return launch_step_pv<1, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 6: return launch_step_pv<2, 0>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 7: return launch_step_pv<2, 1>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    case 8: return launch_step_pv<2, 2>(a, nullptr, nt, grid, dependent, shared_sm, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st) {
   if (a.n_sel <= 0) return cudaSuccess;
   mg_reset_kernel<<<(a.n_sel + 127) / 128, 128, 0, st>>>(a);
@@ -1310,35 +453,39 @@ cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int NT, int PM, int VAR>
-static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
-  cudaError_t e = step_attrs<NT, PM, VAR>();
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_fn<NT, PM, VAR>(), STEP_BLK,
-                                                       step_smem<NT, PM>(track));
+cudaError_t launch_step_pm0(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                            bool dependent, bool shared_sm, cudaStream_t st);
+cudaError_t launch_step_pm1(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                            bool dependent, bool shared_sm, cudaStream_t st);
+cudaError_t launch_step_pm2(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                            bool dependent, bool shared_sm, cudaStream_t st);
+cudaError_t occupancy_pm0(int nt, int var, bool kp, bool track, int* blocks_per_sm);
+cudaError_t occupancy_pm1(int nt, int var, bool kp, bool track, int* blocks_per_sm);
+cudaError_t occupancy_pm2(int nt, int var, bool kp, bool track, int* blocks_per_sm);
+
+// Step launch of one class group: thruster count nt, parameter source
+// a.per_env (0 class, 1 per-env, 2 payload), variant var (0 propellers with
+// Euler, 1 generic actuators with Euler, 2 RK4). kc (launches whose segments
+// are all of one class, else null): that class's constants, and kg its
+// generic actuator table (var >= 1), passed as the kernel parameter.
+cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                        bool dependent, bool shared_sm, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  switch (a.per_env) {
+    case 0: return launch_step_pm0(a, kc, kg, nt, var, grid, dependent, shared_sm, st);
+    case 1: return launch_step_pm1(a, kc, kg, nt, var, grid, dependent, shared_sm, st);
+    case 2: return launch_step_pm2(a, kc, kg, nt, var, grid, dependent, shared_sm, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-template <int PM, int VAR>
-static cudaError_t occupancy_pv(int nt, bool track, int* blocks_per_sm) {
-#define MG_L(N) return occupancy_t<N, PM, VAR>(track, blocks_per_sm)
-  MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  return cudaErrorInvalidValue;
-}
-
-// pm 3: class constants as kernel parameters (var 0 only).
-cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm) {
-  switch (pm * 3 + var) {
-    case 0: return occupancy_pv<0, 0>(nt, track, blocks_per_sm);
-    case 1: return occupancy_pv<0, 1>(nt, track, blocks_per_sm);
-    case 2: return occupancy_pv<0, 2>(nt, track, blocks_per_sm);
-    case 3: return occupancy_pv<1, 0>(nt, track, blocks_per_sm);
-    case 4: return occupancy_pv<1, 1>(nt, track, blocks_per_sm);
-    case 5: return occupancy_pv<1, 2>(nt, track, blocks_per_sm);
-    case 6: return occupancy_pv<2, 0>(nt, track, blocks_per_sm);
-    case 7: return occupancy_pv<2, 1>(nt, track, blocks_per_sm);
-    case 8: return occupancy_pv<2, 2>(nt, track, blocks_per_sm);
-    case 9: return occupancy_pv<3, 0>(nt, track, blocks_per_sm);
+// Resident blocks per SM of a step instantiation (kp: class tables as the
+// kernel parameter).
+cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm) {
+  switch (pm) {
+    case 0: return occupancy_pm0(nt, var, kp, track, blocks_per_sm);
+    case 1: return occupancy_pm1(nt, var, kp, track, blocks_per_sm);
+    case 2: return occupancy_pm2(nt, var, kp, track, blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -17,13 +17,13 @@
 #include "mg_payload.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, const ClassK* kc, int nt, int var, int grid, bool dependent,
-                        bool shared_sm, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                        bool dependent, bool shared_sm, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st);
-cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool track, int* blocks_per_sm);
+cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 }  // namespace mg
 
 namespace mg {
@@ -43,8 +43,8 @@ struct ClassLay {
 // Segments with the same thruster count and step variant (0 propellers with
 // Euler, 1 generic actuators with Euler, 2 RK4), launched by one kernel
 // instantiation. A launch of the step plan with cls >= 0 holds envs of that
-// one class and passes its constants as the kernel parameter (the groups of
-// the segment layout have cls = -1).
+// one class and passes its class tables as the kernel parameter (the groups
+// of the segment layout have cls = -1).
 struct Group {
   int32_t nt, seg_lo, seg_hi, tile_lo, n_tiles, var, cls;
 };
@@ -93,7 +93,8 @@ struct mg_sim {
     std::vector<Group> groups;     // the launches of a step
     std::vector<ClassK> kc;        // constants of each launch with cls >= 0
   } plan;
-  std::vector<ClassF> h_cls;       // host copy of the class tables
+  std::vector<ClassF> h_cls;       // host copies of the class tables
+  std::vector<ClassG> h_gen;
   // mg_step_host: copy streams and events of the chunked pipeline.
   cudaStream_t s_in = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> host_ev;
@@ -255,8 +256,8 @@ static int class_var(const mg_sim* sim, int c) {
 
 // Segments ordered by step variant, then thruster count (then class); tiles
 // are numbered in that order so that each group owns one contiguous tile range.
-// Class-constant propeller launches of a single class pass its constants as
-// the kernel parameter (0: always staged in shared memory).
+// Launches of a single class pass its class tables as the kernel parameter
+// (0: always staged in shared memory).
 #ifndef MG_CLASS_PARAMS
 #define MG_CLASS_PARAMS 1
 #endif
@@ -530,6 +531,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
     for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
   }
   sim->h_cls = cf;
+  sim->h_gen = cg;
   ce = cudaMemcpy(sim->d_cls, cf.data(), sizeof(ClassF) * cf.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_cls64, cd.data(), sizeof(ClassD) * cd.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_nominal, cn.data(), sizeof(ClassNominal) * cn.size(), cudaMemcpyHostToDevice);
@@ -593,8 +595,6 @@ int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, 
 // Parameter source of the step kernel: 0 class constants, 1 per-env planes,
 // 2 per-env planes plus the payload planes.
 static int param_mode(const mg_sim* sim) { return sim->cfg.payload ? 2 : (sim->cfg.per_env_params ? 1 : 0); }
-// Parameter source of a group's kernel (3: class constants as the kernel parameter).
-static int group_pm(const mg_sim* sim, const Group& g) { return g.cls >= 0 ? 3 : param_mode(sim); }
 
 // Kernel-parameter constants of a one-class group: the class table, the lag
 // coefficients and dead-zone flag of its segment, no current.
@@ -637,7 +637,7 @@ static int grid_of(mg_sim* sim, const Group& g) {
   int b = sim->blocks_per_sm;
   if (b <= 0) {
     b = 1;
-    step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &b);
+    step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &b);
     if (b < 1) b = 1;
   }
   return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
@@ -675,7 +675,7 @@ static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
   for (int i = 0; i < n; ++i) {
     const Group& g = sim->groups[i];
     int b = sim->blocks_per_sm;
-    if (b <= 0 && step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
+    if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
     resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
     double sub = 0.0, obs = 0.0;
     mg_count_flops(g.nt, sim->cfg.per_env_params, &sub, &obs, nullptr);
@@ -729,12 +729,12 @@ static bool carveout_max(const mg_sim* sim, const Group& g, bool shared_sm) {
 // The launch plan of the current segment layout and blocks_per_sm setting
 // (occupancy queries and FLOP counts stay off the per-step path).
 // Launches run one after the other (the larger steps) split the class groups
-// of class-constant propeller steps into one launch per class, which takes
-// its constants as the kernel parameter (1M envs, K=4: 77.0 -> 69.8 us;
-// 512k: 42.9 -> 39.1 us). Side-by-side launches keep one launch per group
-// with the constants in shared memory: their grids are split by estimated
-// work, which a faster one-class kernel unbalances (262k envs: 23.1 -> 23.6
-// us), and five launches instead of three cost 4 us at 65k envs.
+// into one launch per class, which takes its class tables as the kernel
+// parameter (class-constant hover, 1M envs, K=4: 77.0 -> 69.8 us; 512k: 42.9
+// -> 39.1 us). Side-by-side launches keep one launch per group with the
+// tables in shared memory: their grids are split by estimated work, which a
+// faster one-class kernel unbalances (262k envs: 23.1 -> 23.6 us), and five
+// launches instead of three cost 4 us at 65k envs.
 static const mg_sim::Plan& step_plan(mg_sim* sim) {
   mg_sim::Plan& p = sim->plan;
   if (p.valid && p.bps == sim->blocks_per_sm) return p;
@@ -744,7 +744,7 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
   const bool shared_sm = p.cores && blocks > sim->num_sms;
   p.groups.clear();
   for (const Group& g : sim->groups) {
-    const bool split = !p.cores && MG_CLASS_PARAMS && !sim->cfg.per_env_params && !sim->cfg.payload && g.var == 0;
+    const bool split = !p.cores && MG_CLASS_PARAMS;
     if (!split) { p.groups.push_back(g); continue; }
     for (int s = g.seg_lo; s < g.seg_hi; ++s) {   // a segment holds envs of one class
       Group h = g;
@@ -783,8 +783,8 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
     a.wait_first = first && p.cores;
-    CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.nt, g.var, p.grid[i], !first || p.cores,
-                   p.carve_max[i] != 0, st));
+    CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
+                   p.grid[i], !first || p.cores, p.carve_max[i] != 0, st));
     first = false;
   }
   return MG_OK;
@@ -914,8 +914,9 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     a.tile_lo = tile_lo;
     a.n_tiles = ch.nt;
     a.wait_first = 0;
-    CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.nt, g.var,
-                   std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false, carveout_max(sim, g, false), st));
+    CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt,
+                   g.var, std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false, carveout_max(sim, g, false),
+                   st));
     CK(cudaEventRecord(ev_done, st));
     CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
     for (const Range& r : ranges) {
@@ -1334,7 +1335,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   int occ = 1 << 30;
   for (const Group& g : sim->groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, group_pm(sim, g), g.var, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
+    if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
     occ = std::min(occ, o);
   }
   if (occ == (1 << 30)) occ = 0;

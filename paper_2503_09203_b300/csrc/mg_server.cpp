@@ -36,8 +36,8 @@
 #include "mg_internal.h"
 
 namespace mg {
-cudaError_t launch_step(const StepArgs& a, const ClassK* kc, int nt, int var, int grid, bool dependent,
-                        bool shared_sm, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
+                        bool dependent, bool shared_sm, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 }  // namespace mg
 
@@ -303,7 +303,7 @@ static bool tick_once(mg_server* s) {
   bool first = true;
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
-    launch_step(a, nullptr, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
+    launch_step(a, nullptr, nullptr, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
     first = false;
   }
   cudaEventRecord(s->ev1, st);

@@ -381,12 +381,13 @@ def test_host_buffer_step_equals_device_step():
 @pytest.mark.parametrize("per_env", [True, False])
 def test_host_buffer_step_chunked_multi_step_equals_device_step(per_env):
     """Sizes that cut the launches into several copy/step chunks, 3 steps per
-    call; with class constants the step runs one launch per class."""
+    call; at this size the step runs one launch per class (class tables as the
+    kernel parameter)."""
     classes = vehicles.five_classes()
     counts = [300001, 3, 240001, 5, 9]   # class 0 spans two 2048-tile chunks
     sim = make_sim(classes, counts, K=1, reset=dict(vehicles.HOVER_DR if per_env else vehicles.HOVER),
                    per_env=per_env)
-    assert sim.launches_per_step() == (3 if per_env else 5)
+    assert sim.launches_per_step() == 5
     sim.reset(seed=3)
     s0 = sim.get_state()
     a_dev = (torch.rand(3, sim.action_floats, device="cuda") * 2 - 1).contiguous()
