@@ -184,6 +184,28 @@ def algorithmic(classes, counts, K):
     return tot_b / E, tot_f / E
 
 
+def link_bound(h2d_bytes, d2h_bytes, steps=50):
+    """Seconds per step of the end-to-end path's copies alone: the same bytes
+    host->device and device->host between pinned buffers, one copy each way
+    per step on two streams (overlapped), no step kernel."""
+    import torch
+    h_in = torch.empty(h2d_bytes // 4, dtype=torch.float32).pin_memory()
+    d_in = torch.empty_like(h_in, device="cuda")
+    d_out = torch.zeros(d2h_bytes // 4, dtype=torch.float32, device="cuda")
+    h_out = torch.empty(d2h_bytes // 4, dtype=torch.float32).pin_memory()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    for it in range(steps + 3):
+        if it == 3:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        with torch.cuda.stream(s_in):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps
+
+
 def time_steps(sim, acts, steps, warmup, stream):
     """Device time of `steps` mg_step calls (events on the launching stream)."""
     import torch
@@ -353,7 +375,7 @@ def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
     return out
 
 
-def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
+def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20):
     """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
     T-step rollout (observation and reward every step) captured once as a CUDA
     graph after the autotuner chose the persistent grid, then replayed."""
@@ -371,7 +393,8 @@ def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=5):
     with torch.cuda.stream(st):
         threads, bps = B.mg_autotune(sim.handle, st)
         g = B.mg_graph_capture(sim.handle, acts, T, obs, rew, st)
-        B.mg_graph_launch(g, st)
+        for _ in range(3):
+            B.mg_graph_launch(g, st)
         st.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -613,6 +636,9 @@ def main():
     e2e = {"value": whole_job_rate(E, world, args.e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": int(sim.action_floats * 4), "d2h_bytes_per_step": int(sim.n_slots * 14 * 4),
            "steps": args.e2e_steps, "api": "mg_step_host"}
+    t_link = link_bound(e2e["h2d_bytes_per_step"], e2e["d2h_bytes_per_step"])
+    e2e["link_bound"] = {"env_steps_per_s": E / t_link, "frac": e2e["value"] / world / (E / t_link),
+                         "note": "the same bytes as plain pinned copies, one each way per step on two streams"}
 
     if rank != 0:
         sim.close()

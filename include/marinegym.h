@@ -357,6 +357,12 @@ int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream);
  * restored). Writes the choice into *threads / *blocks_per_sm if not NULL. */
 int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads, int32_t* blocks_per_sm);
 
+/* Fix the persistent grid: blocks_per_sm resident blocks of each step launch
+ * per SM (0: the kernel's occupancy limit, the default; values above it are
+ * capped by it). Takes effect from the next launch on any stream; a captured
+ * graph keeps the grid it was captured with. Errors: INVALID_ARG (negative). */
+int mg_set_blocks_per_sm(mg_sim* sim, int32_t blocks_per_sm);
+
 /* CUDA-graph capture of mg_rollout(actions, n_steps, obs, reward, record=0)
  * on `stream`; mg_graph_launch replays it. Buffers are bound at capture. */
 typedef struct mg_graph mg_graph;

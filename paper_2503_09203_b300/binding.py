@@ -140,6 +140,7 @@ _SIGS = {
     "mg_status": [_VP, _VP],
     "mg_test_wait_timeout": [_VP, _U64, _VP],
     "mg_autotune": [_VP, _VP, C.POINTER(_I32), C.POINTER(_I32)],
+    "mg_set_blocks_per_sm": [_VP, _I32],
     "mg_graph_capture": [_VP, _VP, _I32, _VP, _VP, _VP, C.POINTER(_VP)],
     "mg_graph_launch": [_VP, _VP],
     "mg_graph_destroy": [_VP],
@@ -387,6 +388,10 @@ def mg_autotune(sim, stream=None):
     t, b = C.c_int32(), C.c_int32()
     _check(lib().mg_autotune(sim, _stream(stream), C.byref(t), C.byref(b)), sim)
     return t.value, b.value
+
+
+def mg_set_blocks_per_sm(sim, blocks_per_sm: int):
+    return _check(lib().mg_set_blocks_per_sm(sim, int(blocks_per_sm)), sim)
 
 
 def mg_graph_capture(sim, actions, n_steps, obs=None, reward=None, stream=None):

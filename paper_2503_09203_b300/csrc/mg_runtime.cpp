@@ -633,14 +633,18 @@ static StepArgs step_args(mg_sim* sim) {
 
 // Persistent grid: blocks_per_sm resident blocks per SM (0: the kernel's
 // occupancy limit), never more blocks than tiles.
+// Resident blocks per SM of a group's launches: blocks_per_sm, capped by the
+// kernel's occupancy limit (which is the default).
+static int blocks_of(const mg_sim* sim, const Group& g) {
+  int occ = 1;
+  if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &occ) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return sim->blocks_per_sm > 0 ? std::min(sim->blocks_per_sm, occ) : occ;
+}
+
 static int grid_of(mg_sim* sim, const Group& g) {
-  int b = sim->blocks_per_sm;
-  if (b <= 0) {
-    b = 1;
-    step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &b);
-    if (b < 1) b = 1;
-  }
-  return std::max(1, std::min(g.n_tiles, b * sim->num_sms));
+  return std::max(1, std::min(g.n_tiles, blocks_of(sim, g) * sim->num_sms));
 }
 
 static bool misaligned(const void* p) { return p && ((uintptr_t)p & 15u) != 0; }
@@ -674,9 +678,7 @@ static bool coresident_grids(mg_sim* sim, std::vector<int>& grid) {
   double wsum = 0.0;
   for (int i = 0; i < n; ++i) {
     const Group& g = sim->groups[i];
-    int b = sim->blocks_per_sm;
-    if (b <= 0 && step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &b) != cudaSuccess) b = 1;
-    resident = std::min<int64_t>(resident, (int64_t)std::max(b, 1) * sim->num_sms);
+    resident = std::min<int64_t>(resident, (int64_t)blocks_of(sim, g) * sim->num_sms);
     double sub = 0.0, obs = 0.0;
     mg_count_flops(g.nt, sim->cfg.per_env_params, &sub, &obs, nullptr);
     w[i] = (double)g.n_tiles * ((g.var == 2 ? 4.0 : 1.0) * sim->cfg.K * sub + obs);
@@ -1368,6 +1370,13 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   CK(cudaGetLastError());
   if (threads_out) *threads_out = best_t;
   if (bps_out) *bps_out = best_b;
+  return MG_OK;
+}
+
+int mg_set_blocks_per_sm(mg_sim* sim, int32_t blocks_per_sm) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (blocks_per_sm < 0) return fail(sim, MG_ERR_INVALID_ARG, "set_blocks_per_sm: negative count %d", blocks_per_sm);
+  sim->blocks_per_sm = blocks_per_sm;   // the step plan is rebuilt for the new value
   return MG_OK;
 }
 
