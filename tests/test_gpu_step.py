@@ -435,6 +435,35 @@ def test_graph_replay_and_autotune_keep_results():
     sim.close()
 
 
+@pytest.mark.parametrize("per_env", [True, False])
+@pytest.mark.parametrize("counts", [[70001, 3, 60001, 5, 9],      # groups side by side
+                                    [300001, 3, 240001, 5, 9]])   # one launch per class
+def test_fixed_grid_keeps_results(per_env, counts):
+    """A fixed persistent grid (1 block per SM, above the occupancy limit, the
+    default) leaves every result bit-identical: each env is computed by one
+    thread whatever block walks its tile; negative counts are refused."""
+    classes = vehicles.five_classes()
+    sim = make_sim(classes, counts, K=2, reset=dict(vehicles.HOVER_DR if per_env else vehicles.HOVER),
+                   per_env=per_env)
+    sim.reset(seed=4)
+    s0 = sim.get_state()
+    a_dev = sim.pack_actions(workloads.actions(6, 2, sim.n_envs))
+    out = []
+    for b in (0, 1, 64):
+        B.mg_set_blocks_per_sm(sim.handle, b)
+        sim.set_state(s0)
+        sim.step(a_dev, n_steps=2)
+        torch.cuda.synchronize()
+        out.append((sim.get_state(), sim.obs.cpu().numpy().copy(), sim.reward.cpu().numpy().copy()))
+    for st, ob, rw in out[1:]:
+        assert np.array_equal(st, out[0][0]) and np.array_equal(ob, out[0][1]) and np.array_equal(rw, out[0][2])
+    with pytest.raises(B.MGError) as e:
+        B.mg_set_blocks_per_sm(sim.handle, -1)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
+    sim.status()
+    sim.close()
+
+
 def test_flop_count_matches_hand_count():
     """The counted substep of the 8-thruster class: rotor 3/thr, thrust 2/thr,
     allocation 6 x (8 mul + 7 add) = 90; the remaining terms are fixed."""
