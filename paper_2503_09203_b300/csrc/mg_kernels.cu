@@ -471,6 +471,7 @@ cudaError_t occupancy_pm2(int nt, int var, bool kp, bool track, int* blocks_per_
 cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                         bool dependent, bool shared_sm, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
+  if (kc && a.seg_hi - a.seg_lo != 1) return cudaErrorInvalidValue;   // one class, one segment
   switch (a.per_env) {
     case 0: return launch_step_pm0(a, kc, kg, nt, var, grid, dependent, shared_sm, st);
     case 1: return launch_step_pm1(a, kc, kg, nt, var, grid, dependent, shared_sm, st);

@@ -139,7 +139,13 @@ struct mg_server {
   float* d_ret = nullptr;        // [S]
   float* d_state = nullptr;      // state space (floats)
   uint32_t* d_status = nullptr;
-  SegDesc* h_segs = nullptr;     // pinned
+  SegDesc* h_segs = nullptr;     // pinned tick segment table
+  SegDesc* h_rsegs = nullptr;    // pinned reset segment table
+  int32_t* d_tile_seg = nullptr; // tick: segment of each tile
+  int32_t* h_tile_seg = nullptr; // pinned
+  int64_t tile_cap = 0;
+  float* h_stage = nullptr;      // pinned: final states and returns of retiring requests
+  size_t stage_floats = 0;
   int64_t S = 0, state_cap = 0;
   RangeAlloc slots, states;
   cudaStream_t stream = nullptr;
@@ -221,26 +227,27 @@ static SegDesc seg_of(const Req& q) {
 // One scheduler tick. Returns false when there is nothing to do.
 static bool tick_once(mg_server* s) {
   std::vector<int64_t> admitted;
-  std::vector<SegDesc> segs;
+  std::vector<Req*> act;   // active requests of this tick (stable: only done requests are erased)
   {
     std::lock_guard<std::mutex> lk(s->mu);
     admit_locked(s, admitted);
     if (s->active.empty()) return false;
-    // Reset table for new requests.
-    if (!admitted.empty()) {
-      for (size_t k = 0; k < admitted.size(); ++k) segs.push_back(seg_of(s->reqs[admitted[k]]));
-    }
+    for (size_t k = 0; k < admitted.size(); ++k) s->h_rsegs[k] = seg_of(s->reqs[admitted[k]]);
+    act.reserve(s->active.size());
+    for (int64_t id : s->active) act.push_back(&s->reqs[id]);
   }
   cudaStream_t st = s->stream;
-  if (!segs.empty()) {
-    // Reset each admitted request: one launch per request over its envs.
-    cudaMemcpyAsync(s->d_rsegs, segs.data(), sizeof(SegDesc) * segs.size(), cudaMemcpyHostToDevice, st);
-    for (size_t k = 0; k < segs.size(); ++k) {
+  if (!admitted.empty()) {
+    // Reset each admitted request: one launch per request over its envs. The
+    // pinned reset table is rewritten only after this tick's completion wait.
+    cudaMemcpyAsync(s->d_rsegs, s->h_rsegs, sizeof(SegDesc) * admitted.size(), cudaMemcpyHostToDevice, st);
+    for (size_t k = 0; k < admitted.size(); ++k) {
+      const SegDesc& sd = s->h_rsegs[k];
       ResetArgs a;
       std::memset(&a, 0, sizeof(a));
       a.segs = s->d_rsegs + k;
       a.n_segs = 1;
-      a.n_sel = segs[k].n_envs;
+      a.n_sel = sd.n_envs;
       a.nominal = s->d_nominal;
       a.per_env = 1;
       a.serving = 1;
@@ -254,37 +261,38 @@ static bool tick_once(mg_server* s) {
       a.cur_lo = r.cur_lo; a.cur_hi = r.cur_hi; a.target_half = r.target_half; a.pos_radius = r.pos_radius;
       a.max_angle = r.max_angle;
       launch_reset(a, st);
-      cudaMemsetAsync(s->d_ret + segs[k].slot_off, 0, sizeof(float) * segs[k].n4, st);
+      cudaMemsetAsync(s->d_ret + sd.slot_off, 0, sizeof(float) * sd.n4, st);
     }
-    // The reset table must not be overwritten before the resets ran.
-    cudaStreamSynchronize(st);
   }
-  // Tick table: active requests grouped by thruster count.
-  std::vector<SegDesc> tab;
+  // Tick table in one pass: active requests grouped by thruster count, and
+  // the segment (within its group) of every tile.
   struct G { int nt, lo, hi, tile_lo, tiles; };
   std::vector<G> groups;
+  std::vector<const Req*> by_nt[MG_MAX_THR + 1];
   int64_t envs = 0;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    int tiles = 0;
-    for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
-      G g{nt, (int)tab.size(), 0, tiles, 0};
-      for (int64_t id : s->active) {
-        const Req& q = s->reqs[id];
-        if (q.n_thr != nt) continue;
-        SegDesc sd = seg_of(q);
-        sd.tile_begin = tiles;
-        tiles += (q.n4 + kThreads - 1) / kThreads;
-        tab.push_back(sd);
-        envs += q.r.n_envs;
-      }
-      g.hi = (int)tab.size();
-      g.tiles = tiles - g.tile_lo;
-      if (g.hi > g.lo) groups.push_back(g);
-    }
+  for (const Req* q : act) {
+    by_nt[q->n_thr].push_back(q);
+    envs += q->r.n_envs;
   }
-  std::memcpy(s->h_segs, tab.data(), sizeof(SegDesc) * tab.size());
-  cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(SegDesc) * tab.size(), cudaMemcpyHostToDevice, st);
+  int n_seg = 0, tiles = 0;
+  for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
+    if (by_nt[nt].empty()) continue;
+    G g{nt, n_seg, 0, tiles, 0};
+    for (const Req* q : by_nt[nt]) {
+      SegDesc& sd = s->h_segs[n_seg];
+      sd = seg_of(*q);
+      sd.tile_begin = tiles;
+      const int qt = (q->n4 + kThreads - 1) / kThreads;
+      for (int k = 0; k < qt; ++k) s->h_tile_seg[tiles + k] = n_seg - g.lo;
+      tiles += qt;
+      ++n_seg;
+    }
+    g.hi = n_seg;
+    g.tiles = tiles - g.tile_lo;
+    groups.push_back(g);
+  }
+  cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(SegDesc) * n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s->d_tile_seg, s->h_tile_seg, sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, st);
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.segs = s->d_segs;
@@ -303,22 +311,76 @@ static bool tick_once(mg_server* s) {
   bool first = true;
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
+    a.tile_seg = s->d_tile_seg + g.tile_lo;
     launch_step(a, nullptr, nullptr, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
     first = false;
   }
   cudaEventRecord(s->ev1, st);
+  // Requests that finish with this tick: their final states and returns are
+  // copied into one pinned staging buffer behind the tick's launches.
+  std::vector<Req*> done;
+  size_t stage = 0;
+  for (Req* q : act)
+    if (q->steps_done + 1 >= q->r.horizon) {
+      done.push_back(q);
+      stage += (size_t)q->n4 * (14 + q->n_thr);
+    }
+  if (stage > s->stage_floats) {
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->h_stage = nullptr;
+    s->stage_floats = 0;
+    if (cudaMallocHost(&s->h_stage, sizeof(float) * stage * 2) != cudaSuccess) {
+      cudaGetLastError();
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->fatal = MG_ERR_OOM;
+      s->err = "tick: pinned staging allocation failed";
+      return false;
+    }
+    s->stage_floats = stage * 2;
+  }
+  {
+    size_t off = 0;
+    for (Req* q : done) {
+      const size_t n = (size_t)q->n4 * (13 + q->n_thr);
+      cudaMemcpyAsync(s->h_stage + off, s->d_state + q->st_off, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(s->h_stage + off + n, s->d_ret + q->slot_off, sizeof(float) * q->n4, cudaMemcpyDeviceToHost,
+                      st);
+      off += n + q->n4;
+    }
+  }
   cudaError_t e = cudaEventSynchronize(s->ev1);
   const double t_end = now_s();
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+  if (e == cudaSuccess && !done.empty()) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->fatal = MG_ERR_CUDA;
     s->err = std::string("tick: ") + cudaGetErrorString(e);
     return false;
   }
+  // Unpack the finished requests (env-major, 21 floats per env).
+  std::vector<std::vector<float>> states(done.size()), rets(done.size());
+  {
+    size_t off = 0;
+    for (size_t d = 0; d < done.size(); ++d) {
+      const Req& q = *done[d];
+      const int SS = 13 + q.n_thr, NF4 = SS / 4;
+      const float* buf = s->h_stage + off;
+      std::vector<float>& fs = states[d];
+      fs.assign((size_t)q.r.n_envs * 21, 0.0f);
+      for (int64_t i = 0; i < q.r.n_envs; ++i)
+        for (int j = 0; j < SS; ++j) {
+          const int64_t o = (j < NF4 * 4) ? ((int64_t)(j / 4) * q.n4 + i) * 4 + (j % 4)
+                                          : (int64_t)NF4 * 4 * q.n4 + (int64_t)(j - NF4 * 4) * q.n4 + i;
+          fs[i * 21 + j] = buf[o];
+        }
+      const float* r = buf + (size_t)q.n4 * SS;
+      rets[d].assign(r, r + q.r.n_envs);
+      off += (size_t)q.n4 * (SS + 1);
+    }
+  }
   // Book-keeping and retirement.
-  std::vector<int64_t> done;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     const double spacing = s->last_tick_end > 0 ? t_end - s->last_tick_end : ms * 1e-3;
@@ -328,46 +390,31 @@ static bool tick_once(mg_server* s) {
     s->busy += ms * 1e-3;
     s->tick.push_back({ms * 1e-3, 1.0});
     int n_cont = 0;
-    for (int64_t id : s->active) {
-      Req& q = s->reqs[id];
+    for (Req* q : act) {
       // First step of a request admitted this tick is measured from admission.
-      const bool fresh = std::find(admitted.begin(), admitted.end(), id) != admitted.end();
-      if (fresh) s->lat.push_back({t_end - q.t_admit, 1.0});
+      if (q->steps_done == 0) s->lat.push_back({t_end - q->t_admit, 1.0});
       else ++n_cont;
-      q.steps_done++;
-      if (q.steps_done >= q.r.horizon) done.push_back(id);
+      q->steps_done++;
     }
     if (n_cont > 0) s->lat.push_back({spacing, (double)n_cont});
-  }
-  for (int64_t id : done) {
-    Req* qp;
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      qp = &s->reqs[id];
+    for (size_t d = 0; d < done.size(); ++d) {
+      Req& q = *done[d];
+      q.final_state.swap(states[d]);
+      q.returns.swap(rets[d]);
+      q.t_done = now_s();
+      q.status = MG_REQ_DONE;
+      s->slots.release(q.slot_off, q.n4);
+      s->states.release(q.st_off, state_units(q.n_thr, q.n4));
+      s->requests_done++;
     }
-    Req& q = *qp;
-    const int SS = 13 + q.n_thr, NF4 = SS / 4;
-    std::vector<float> buf((size_t)q.n4 * SS);
-    cudaMemcpyAsync(buf.data(), s->d_state + q.st_off, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, st);
-    std::vector<float> ret(q.n4);
-    cudaMemcpyAsync(ret.data(), s->d_ret + q.slot_off, sizeof(float) * q.n4, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    std::vector<float> fs((size_t)q.r.n_envs * 21, 0.0f);
-    for (int64_t i = 0; i < q.r.n_envs; ++i)
-      for (int j = 0; j < SS; ++j) {
-        const int64_t off = (j < NF4 * 4) ? ((int64_t)(j / 4) * q.n4 + i) * 4 + (j % 4)
-                                          : (int64_t)NF4 * 4 * q.n4 + (int64_t)(j - NF4 * 4) * q.n4 + i;
-        fs[i * 21 + j] = buf[off];
-      }
-    std::lock_guard<std::mutex> lk(s->mu);
-    q.final_state.swap(fs);
-    q.returns.assign(ret.begin(), ret.begin() + q.r.n_envs);
-    q.t_done = now_s();
-    q.status = MG_REQ_DONE;
-    s->slots.release(q.slot_off, q.n4);
-    s->states.release(q.st_off, state_units(q.n_thr, q.n4));
-    s->active.erase(std::find(s->active.begin(), s->active.end(), id));
-    s->requests_done++;
+    if (!done.empty()) {
+      // `act` lists s->active in order (only this thread changes it).
+      std::vector<int64_t> keep;
+      keep.reserve(act.size());
+      for (const Req* q : act)
+        if (q->status != MG_REQ_DONE) keep.push_back(q->id);
+      s->active.swap(keep);
+    }
   }
   if (!done.empty()) s->cv.notify_all();
   return true;
@@ -437,6 +484,9 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     if (s->d_rsegs) cudaFree(s->d_rsegs);
     if (s->d_status) cudaFree(s->d_status);
     if (s->h_segs) cudaFreeHost(s->h_segs);
+    if (s->h_rsegs) cudaFreeHost(s->h_rsegs);
+    if (s->d_tile_seg) cudaFree(s->d_tile_seg);
+    if (s->h_tile_seg) cudaFreeHost(s->h_tile_seg);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
@@ -449,12 +499,17 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   s->d_state = s->d_ret + S;
   s->slots.reset(S);
   s->states.reset(s->state_cap);
-  if (cudaMalloc(&s->d_cls, sizeof(ClassF) * n_classes) != cudaSuccess ||
+  // Tiles of a tick: each request's slots rounded up to whole tiles.
+  s->tile_cap = S / kThreads + cfg->max_requests;
+  if (cudaMalloc(&s->d_tile_seg, sizeof(int32_t) * s->tile_cap) != cudaSuccess ||
+      cudaMallocHost(&s->h_tile_seg, sizeof(int32_t) * s->tile_cap) != cudaSuccess ||
+      cudaMalloc(&s->d_cls, sizeof(ClassF) * n_classes) != cudaSuccess ||
       cudaMalloc(&s->d_nominal, sizeof(ClassNominal) * n_classes) != cudaSuccess ||
       cudaMalloc(&s->d_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
       cudaMalloc(&s->d_rsegs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
       cudaMalloc(&s->d_status, sizeof(uint32_t)) != cudaSuccess ||
-      cudaMallocHost(&s->h_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess) {
+      cudaMallocHost(&s->h_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
+      cudaMallocHost(&s->h_rsegs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(MG_ERR_OOM);
   }
@@ -599,6 +654,10 @@ int mg_server_destroy(mg_server* s) {
   cudaFree(s->d_rsegs);
   cudaFree(s->d_status);
   cudaFreeHost(s->h_segs);
+  cudaFreeHost(s->h_rsegs);
+  cudaFree(s->d_tile_seg);
+  cudaFreeHost(s->h_tile_seg);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
   cudaEventDestroy(s->ev0);
   cudaEventDestroy(s->ev1);
   cudaStreamDestroy(s->stream);

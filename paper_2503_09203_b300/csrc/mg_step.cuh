@@ -117,6 +117,14 @@ __device__ __forceinline__ int find_seg(const SegDesc* segs, int n_segs, int til
   }
   return lo;
 }
+// Segment of launch tile `tile`: from the launch's tile map (TM: serving ticks
+// with thousands of segments, one load instead of a search of dependent
+// loads), else by binary search (a few segments, cached in shared memory).
+template <bool TM>
+__device__ __forceinline__ int seg_of_tile(const StepArgs& a, const SegDesc* segs, int n_segs, int tile) {
+  if constexpr (TM) return __ldg(a.tile_seg + (tile - a.tile_lo));
+  else return find_seg(segs, n_segs, tile);
+}
 
 __device__ __forceinline__ float clamp1(float a) { return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a); }
 
@@ -700,10 +708,11 @@ using KParam = std::conditional_t<!KP, NoClassK, std::conditional_t<VAR == 0, Cl
 
 // PM: parameter source (0 class constants, 1 per-env planes, 2 per-env planes
 // with the payload). KP: the launch holds one class and its tables travel as
-// the kernel parameter `kp` (otherwise they are staged in shared memory). The
+// the kernel parameter `kp` (otherwise they are staged in shared memory). TM:
+// tiles find their segment through the launch's tile map (serving). The
 // body stays in the kernel itself: moved into a function taking the
 // parameters by reference, the per-env and payload instantiations spilled.
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP>::value))
     mg_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ KParam<KP, VAR> kp) {
   using SG = Stage<NT>;
@@ -752,7 +761,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP>::value))
   unsigned nvw_cur = 0;
   {
     const int tile0 = a.tile_lo + blockIdx.x;
-    const SegDesc& s0 = segs[find_seg(segs, n_seg, tile0)];
+    const SegDesc& s0 = segs[seg_of_tile<TM>(a, segs, n_seg, tile0)];
     const int64_t local0 = (int64_t)(tile0 - s0.tile_begin) * STEP_BLK;
     nvw_cur = warp_envs(s0, local0, warp);
     if (lane == 0 && nvw_cur > 0 && !(s0.flags & 2))
@@ -764,13 +773,13 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP>::value))
   for (int j = 0, tt = blockIdx.x; tt < a.n_tiles; ++j, tt += gridDim.x) {
     const int tile = a.tile_lo + tt;
     const int b = j & 1;
-    const int si = find_seg(segs, n_seg, tile);
+    const int si = seg_of_tile<TM>(a, segs, n_seg, tile);
     // Refill the other buffer (read during tile j - 1) with the next slice.
     const int tt_next = tt + gridDim.x;
     unsigned nvw_next = 0;
     if (tt_next < a.n_tiles) {
       const int tile_n = a.tile_lo + tt_next;
-      const SegDesc& sn = segs[find_seg(segs, n_seg, tile_n)];
+      const SegDesc& sn = segs[seg_of_tile<TM>(a, segs, n_seg, tile_n)];
       const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
       nvw_next = warp_envs(sn, ln, warp);
       if (lane == 0 && nvw_next > 0 && !failed && !(sn.flags & 2)) {
@@ -839,18 +848,18 @@ static size_t step_smem(bool track) {
   return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
 }
 
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 static const void* step_fn() {
-  return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR, KP>);
+  return reinterpret_cast<const void*>(&mg_step_kernel<NT, PM, VAR, KP, TM>);
 }
 
 // Kernel attributes of a step instantiation: the largest dynamic shared
 // memory of its layouts (tracking).
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 static cudaError_t step_attrs() {
   static bool done = false;   // per instantiation, per process (one device)
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<NT, PM>(true));
   if (e == cudaSuccess) done = true;
   return e;
@@ -858,24 +867,24 @@ static cudaError_t step_attrs() {
 
 // Shared-memory carveout of the next launch of an instantiation: the largest
 // (`shared_sm`) or the driver's default; set only when it changes.
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 static cudaError_t step_carveout(bool shared_sm) {
   static int current = -2;   // per instantiation, per process (one device)
   const int want = shared_sm ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault;
   if (want == current) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP>(), cudaFuncAttributePreferredSharedMemoryCarveout, want);
+  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM>(), cudaFuncAttributePreferredSharedMemoryCarveout, want);
   if (e == cudaSuccess) current = want;
   return e;
 }
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, const ClassG* kg, int grid, bool dependent,
                                  bool shared_sm, cudaStream_t st) {
   const size_t smem = step_smem<NT, PM>(a.track != 0);
-  cudaError_t e = step_attrs<NT, PM, VAR, KP>();
-  if (e == cudaSuccess) e = step_carveout<NT, PM, VAR, KP>(shared_sm);
+  cudaError_t e = step_attrs<NT, PM, VAR, KP, TM>();
+  if (e == cudaSuccess) e = step_carveout<NT, PM, VAR, KP, TM>(shared_sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -888,32 +897,42 @@ static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, const Clas
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
   if constexpr (!KP) {
-    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP>, a, NoClassK{});
+    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP, TM>, a, NoClassK{});
   } else if constexpr (VAR == 0) {
-    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP>, a, *kc);
+    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP, TM>, a, *kc);
   } else {
     ClassKG t;
     t.k = *kc;
     t.g = *kg;
-    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP>, a, t);
+    return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP, TM>, a, t);
   }
 }
 
-template <int PM, int VAR, bool KP>
+template <int PM, int VAR, bool KP, bool TM = false>
 static cudaError_t launch_step_pv(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int grid,
                                   bool dependent, bool shared_sm, cudaStream_t st) {
-#define MG_L(N) return launch_step_t<N, PM, VAR, KP>(a, kc, kg, grid, dependent, shared_sm, st)
+#define MG_L(N) return launch_step_t<N, PM, VAR, KP, TM>(a, kc, kg, grid, dependent, shared_sm, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;
 }
 
 // Step launch with parameter source PM: variant var, class tables from the
-// kernel parameter when kc is given (and kg for var >= 1).
+// kernel parameter when kc is given (and kg for var >= 1). A serving tick
+// (act_mode 1: per-env propeller steps with a tile map) has its own
+// instantiation.
 template <int PM>
 static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                                   bool dependent, bool shared_sm, cudaStream_t st) {
   if (kc && var != 0 && !kg) return cudaErrorInvalidValue;
+  if (a.act_mode == 1 && var == 0) {
+    if constexpr (PM == 1) {
+      if (kc) return cudaErrorInvalidValue;
+      return launch_step_pv<PM, 0, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   switch (var * 2 + (kc ? 1 : 0)) {
     case 0: return launch_step_pv<PM, 0, false>(a, kc, kg, nt, grid, dependent, shared_sm, st);
     case 1: return launch_step_pv<PM, 0, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
@@ -925,17 +944,17 @@ static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const Cla
   }
 }
 
-template <int NT, int PM, int VAR, bool KP>
+template <int NT, int PM, int VAR, bool KP, bool TM>
 static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
-  cudaError_t e = step_attrs<NT, PM, VAR, KP>();
+  cudaError_t e = step_attrs<NT, PM, VAR, KP, TM>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_fn<NT, PM, VAR, KP>(), STEP_BLK,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_fn<NT, PM, VAR, KP, TM>(), STEP_BLK,
                                                        step_smem<NT, PM>(track));
 }
 
 template <int PM, int VAR, bool KP>
 static cudaError_t occupancy_pv(int nt, bool track, int* blocks_per_sm) {
-#define MG_L(N) return occupancy_t<N, PM, VAR, KP>(track, blocks_per_sm)
+#define MG_L(N) return occupancy_t<N, PM, VAR, KP, false>(track, blocks_per_sm)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;

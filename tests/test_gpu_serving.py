@@ -54,12 +54,15 @@ def test_request_alone_equals_in_mix_and_matches_oracle():
     assert alone["status"] == B.MG_REQ_DONE and alone["steps_done"] == 40
     srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=CFG)
     rng = np.random.default_rng(0)
-    others = [(int(rng.integers(0, 5)), int(rng.integers(1, 3000)), int(rng.integers(5, 80)),
-               int(rng.integers(1, 9)), int(rng.integers(1 << 40))) for _ in range(24)]
-    ids = [B.mg_server_submit(srv, *r) for r in others[:12]]
+    # 60 others: each thruster-count group of a tick holds more segments than
+    # the kernel keeps in shared memory, so tiles find theirs through the
+    # tick's tile map.
+    others = [(int(rng.integers(0, 5)), int(rng.integers(1, 3000)), int(rng.integers(5, 60)),
+               int(rng.integers(1, 9)), int(rng.integers(1 << 40))) for _ in range(60)]
+    ids = [B.mg_server_submit(srv, *r) for r in others[:30]]
     time.sleep(0.02)                      # the probe arrives while others run
     pid = B.mg_server_submit(srv, *probe)
-    for r in others[12:]:
+    for r in others[30:]:
         ids.append(B.mg_server_submit(srv, *r))
         time.sleep(0.002)
     B.mg_server_wait_idle(srv, 300)
