@@ -2,18 +2,22 @@
 //
 // A server owns one device arena split into a slot space (per-env parameter
 // planes, hover target and return accumulators, indexed by slot) and a state
-// space (per-request SoA state planes). A scheduler thread repeats ticks:
-//   1. admit pending requests in FIFO order while both spaces have room
-//      (first-fit allocators) and reset their envs on the device;
-//   2. advance every admitted request by one control step in one shared launch
-//      per thruster count (segments = requests, each with its own class, K,
-//      seed and step counter; actions drawn on the device);
-//   3. wait for the tick's completion event, retire finished requests (copy
-//      final state and returns to host memory) and free their space.
-// Requests that arrive while others run are admitted at the next tick, so
-// their work shares launches with the running ones. Nothing on the device
-// waits on the host or on another kernel: every device call is an ordinary
-// launch or copy on the server's stream.
+// space (per-request SoA state planes). A scheduler thread runs ticks; each
+//   1. admits pending requests in FIFO order while both spaces have room
+//      (first-fit allocators) and resets their envs on the device;
+//   2. advances every admitted request by one control step in one shared
+//      launch per thruster count (segments = requests, each with its own
+//      class, K, seed and step counter; actions drawn on the device);
+//   3. copies the final state and returns of the requests whose last step it
+//      ran to pinned host memory.
+// Ticks are pipelined: while tick t runs, the host prepares and enqueues tick
+// t+1 (which requests finish with tick t is known in advance, and the space
+// they free may be reused at once: the stream orders t+1's resets after t's
+// copies), then waits for tick t and publishes its results. Requests that
+// arrive while others run join the next tick, so their work shares launches
+// with the running ones. Nothing on the device waits on the host or on
+// another kernel: every device call is an ordinary launch or copy on the
+// server's stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -100,7 +104,8 @@ struct Req {
   mg_request r{};
   int32_t status = MG_REQ_PENDING;
   double t_submit = 0, t_admit = 0, t_done = 0;
-  int64_t steps_done = 0;
+  int64_t steps_done = 0;    // completed ticks (published)
+  int64_t steps_sched = 0;   // ticks enqueued
   int32_t n_thr = 0, n4 = 0;
   int64_t slot_off = -1, st_off = -1;
   float h = 0;
@@ -124,6 +129,26 @@ double wquantile(std::vector<std::pair<double, double>> v, double q) {
 
 }  // namespace
 
+// Host side of one tick in flight; two alternate, so that the next tick is
+// prepared and enqueued while the current one runs.
+struct TickBuf {
+  SegDesc* h_segs = nullptr;      // pinned tick segment table
+  SegDesc* h_rsegs = nullptr;     // pinned reset segment table
+  int32_t* h_tile_seg = nullptr;  // pinned tile map
+  float* h_stage = nullptr;       // pinned: final states and returns of retiring requests
+  size_t stage_floats = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+};
+
+// One tick: the requests it steps, those it admitted (first step) and those
+// whose last step it runs.
+struct Tick {
+  bool valid = false;
+  int par = 0;
+  std::vector<Req*> act, fresh, done;
+  int64_t envs = 0;
+};
+
 struct mg_server {
   mg_server_config cfg{};
   std::vector<mg_class_desc> classes;
@@ -139,17 +164,12 @@ struct mg_server {
   float* d_ret = nullptr;        // [S]
   float* d_state = nullptr;      // state space (floats)
   uint32_t* d_status = nullptr;
-  SegDesc* h_segs = nullptr;     // pinned tick segment table
-  SegDesc* h_rsegs = nullptr;    // pinned reset segment table
   int32_t* d_tile_seg = nullptr; // tick: segment of each tile
-  int32_t* h_tile_seg = nullptr; // pinned
   int64_t tile_cap = 0;
-  float* h_stage = nullptr;      // pinned: final states and returns of retiring requests
-  size_t stage_floats = 0;
+  TickBuf buf[2];                // host side of the two ticks in flight
   int64_t S = 0, state_cap = 0;
   RangeAlloc slots, states;
   cudaStream_t stream = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // scheduler
   std::thread th;
   std::mutex mu;
@@ -210,7 +230,7 @@ static SegDesc seg_of(const Req& q) {
   sd.cls = q.r.cls;
   sd.n_thr = q.n_thr;
   sd.K = q.r.K;
-  sd.step0 = (int32_t)q.steps_done;
+  sd.step0 = (int32_t)q.steps_sched;
   sd.n4 = q.n4;
   sd.st_off = q.st_off;
   sd.slot_off = q.slot_off;
@@ -224,25 +244,40 @@ static SegDesc seg_of(const Req& q) {
   return sd;
 }
 
-// One scheduler tick. Returns false when there is nothing to do.
-static bool tick_once(mg_server* s) {
+// Prepare the tick after `prev` (still running) into buffer `par`: free the
+// space of the requests that finish with `prev`, admit pending requests, and
+// list the requests this tick steps.
+static Tick prepare_tick(mg_server* s, const Tick& prev, int par) {
+  Tick t;
+  t.par = par;
   std::vector<int64_t> admitted;
-  std::vector<Req*> act;   // active requests of this tick (stable: only done requests are erased)
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    admit_locked(s, admitted);
-    if (s->active.empty()) return false;
-    for (size_t k = 0; k < admitted.size(); ++k) s->h_rsegs[k] = seg_of(s->reqs[admitted[k]]);
-    act.reserve(s->active.size());
-    for (int64_t id : s->active) act.push_back(&s->reqs[id]);
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Req* q : prev.done) {
+    s->slots.release(q->slot_off, q->n4);
+    s->states.release(q->st_off, state_units(q->n_thr, q->n4));
   }
+  if (s->stop || s->fatal != MG_OK) return t;
+  admit_locked(s, admitted);
+  for (int64_t id : admitted) t.fresh.push_back(&s->reqs[id]);
+  for (int64_t id : s->active) {
+    Req& q = s->reqs[id];
+    if (q.steps_sched < q.r.horizon) t.act.push_back(&q);
+  }
+  t.valid = !t.act.empty();
+  return t;
+}
+
+// Enqueue tick t on the server's stream: resets of its admitted requests,
+// its tables, one launch per thruster count, and the copies of the finishing
+// requests' results. Returns false (fatal set) if pinned staging is short.
+static bool enqueue_tick(mg_server* s, Tick& t) {
+  TickBuf& b = s->buf[t.par];
   cudaStream_t st = s->stream;
-  if (!admitted.empty()) {
-    // Reset each admitted request: one launch per request over its envs. The
-    // pinned reset table is rewritten only after this tick's completion wait.
-    cudaMemcpyAsync(s->d_rsegs, s->h_rsegs, sizeof(SegDesc) * admitted.size(), cudaMemcpyHostToDevice, st);
-    for (size_t k = 0; k < admitted.size(); ++k) {
-      const SegDesc& sd = s->h_rsegs[k];
+  if (!t.fresh.empty()) {
+    for (size_t k = 0; k < t.fresh.size(); ++k) b.h_rsegs[k] = seg_of(*t.fresh[k]);
+    cudaMemcpyAsync(s->d_rsegs, b.h_rsegs, sizeof(SegDesc) * t.fresh.size(), cudaMemcpyHostToDevice, st);
+    for (size_t k = 0; k < t.fresh.size(); ++k) {
+      const SegDesc& sd = b.h_rsegs[k];
       ResetArgs a;
       std::memset(&a, 0, sizeof(a));
       a.segs = s->d_rsegs + k;
@@ -264,26 +299,25 @@ static bool tick_once(mg_server* s) {
       cudaMemsetAsync(s->d_ret + sd.slot_off, 0, sizeof(float) * sd.n4, st);
     }
   }
-  // Tick table in one pass: active requests grouped by thruster count, and
-  // the segment (within its group) of every tile.
+  // Tick table in one pass: requests grouped by thruster count, and the
+  // segment (within its group) of every tile.
   struct G { int nt, lo, hi, tile_lo, tiles; };
   std::vector<G> groups;
   std::vector<const Req*> by_nt[MG_MAX_THR + 1];
-  int64_t envs = 0;
-  for (const Req* q : act) {
+  for (const Req* q : t.act) {
     by_nt[q->n_thr].push_back(q);
-    envs += q->r.n_envs;
+    t.envs += q->r.n_envs;
   }
   int n_seg = 0, tiles = 0;
   for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
     if (by_nt[nt].empty()) continue;
     G g{nt, n_seg, 0, tiles, 0};
     for (const Req* q : by_nt[nt]) {
-      SegDesc& sd = s->h_segs[n_seg];
+      SegDesc& sd = b.h_segs[n_seg];
       sd = seg_of(*q);
       sd.tile_begin = tiles;
       const int qt = (q->n4 + kThreads - 1) / kThreads;
-      for (int k = 0; k < qt; ++k) s->h_tile_seg[tiles + k] = n_seg - g.lo;
+      for (int k = 0; k < qt; ++k) b.h_tile_seg[tiles + k] = n_seg - g.lo;
       tiles += qt;
       ++n_seg;
     }
@@ -291,8 +325,8 @@ static bool tick_once(mg_server* s) {
     g.tiles = tiles - g.tile_lo;
     groups.push_back(g);
   }
-  cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(SegDesc) * n_seg, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(s->d_tile_seg, s->h_tile_seg, sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s->d_segs, b.h_segs, sizeof(SegDesc) * n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s->d_tile_seg, b.h_tile_seg, sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, st);
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.segs = s->d_segs;
@@ -307,7 +341,7 @@ static bool tick_once(mg_server* s) {
   a.ret = s->d_ret;
   a.status = s->d_status;
   a.ckpt_every = 1;
-  cudaEventRecord(s->ev0, st);
+  cudaEventRecord(b.ev0, st);
   bool first = true;
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
@@ -315,44 +349,49 @@ static bool tick_once(mg_server* s) {
     launch_step(a, nullptr, nullptr, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
     first = false;
   }
-  cudaEventRecord(s->ev1, st);
-  // Requests that finish with this tick: their final states and returns are
-  // copied into one pinned staging buffer behind the tick's launches.
-  std::vector<Req*> done;
+  cudaEventRecord(b.ev1, st);
+  // Requests whose last step this is: results into the pinned staging buffer.
   size_t stage = 0;
-  for (Req* q : act)
-    if (q->steps_done + 1 >= q->r.horizon) {
-      done.push_back(q);
+  for (Req* q : t.act) {
+    q->steps_sched++;
+    if (q->steps_sched >= q->r.horizon) {
+      t.done.push_back(q);
       stage += (size_t)q->n4 * (14 + q->n_thr);
     }
-  if (stage > s->stage_floats) {
-    if (s->h_stage) cudaFreeHost(s->h_stage);
-    s->h_stage = nullptr;
-    s->stage_floats = 0;
-    if (cudaMallocHost(&s->h_stage, sizeof(float) * stage * 2) != cudaSuccess) {
+  }
+  if (stage > b.stage_floats) {
+    if (b.h_stage) cudaFreeHost(b.h_stage);   // its last copies were waited for with this buffer's tick
+    b.h_stage = nullptr;
+    b.stage_floats = 0;
+    if (cudaMallocHost(&b.h_stage, sizeof(float) * stage * 2) != cudaSuccess) {
       cudaGetLastError();
       std::lock_guard<std::mutex> lk(s->mu);
       s->fatal = MG_ERR_OOM;
       s->err = "tick: pinned staging allocation failed";
       return false;
     }
-    s->stage_floats = stage * 2;
+    b.stage_floats = stage * 2;
   }
-  {
-    size_t off = 0;
-    for (Req* q : done) {
-      const size_t n = (size_t)q->n4 * (13 + q->n_thr);
-      cudaMemcpyAsync(s->h_stage + off, s->d_state + q->st_off, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(s->h_stage + off + n, s->d_ret + q->slot_off, sizeof(float) * q->n4, cudaMemcpyDeviceToHost,
-                      st);
-      off += n + q->n4;
-    }
+  size_t off = 0;
+  for (Req* q : t.done) {
+    const size_t n = (size_t)q->n4 * (13 + q->n_thr);
+    cudaMemcpyAsync(b.h_stage + off, s->d_state + q->st_off, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(b.h_stage + off + n, s->d_ret + q->slot_off, sizeof(float) * q->n4, cudaMemcpyDeviceToHost, st);
+    off += n + q->n4;
   }
-  cudaError_t e = cudaEventSynchronize(s->ev1);
+  cudaEventRecord(b.ev_done, st);
+  return true;
+}
+
+// Wait for tick t and publish it: step counts, latency samples, and the
+// results of the requests it finished.
+static bool finish_tick(mg_server* s, const Tick& t) {
+  TickBuf& b = s->buf[t.par];
+  cudaError_t e = cudaEventSynchronize(b.ev1);
   const double t_end = now_s();
   float ms = 0.0f;
-  cudaEventElapsedTime(&ms, s->ev0, s->ev1);
-  if (e == cudaSuccess && !done.empty()) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b.ev0, b.ev1);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b.ev_done);
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->fatal = MG_ERR_CUDA;
@@ -360,83 +399,107 @@ static bool tick_once(mg_server* s) {
     return false;
   }
   // Unpack the finished requests (env-major, 21 floats per env).
-  std::vector<std::vector<float>> states(done.size()), rets(done.size());
-  {
-    size_t off = 0;
-    for (size_t d = 0; d < done.size(); ++d) {
-      const Req& q = *done[d];
-      const int SS = 13 + q.n_thr, NF4 = SS / 4;
-      const float* buf = s->h_stage + off;
-      std::vector<float>& fs = states[d];
-      fs.assign((size_t)q.r.n_envs * 21, 0.0f);
-      for (int64_t i = 0; i < q.r.n_envs; ++i)
-        for (int j = 0; j < SS; ++j) {
-          const int64_t o = (j < NF4 * 4) ? ((int64_t)(j / 4) * q.n4 + i) * 4 + (j % 4)
-                                          : (int64_t)NF4 * 4 * q.n4 + (int64_t)(j - NF4 * 4) * q.n4 + i;
-          fs[i * 21 + j] = buf[o];
-        }
-      const float* r = buf + (size_t)q.n4 * SS;
-      rets[d].assign(r, r + q.r.n_envs);
-      off += (size_t)q.n4 * (SS + 1);
-    }
+  std::vector<std::vector<float>> states(t.done.size()), rets(t.done.size());
+  size_t off = 0;
+  for (size_t d = 0; d < t.done.size(); ++d) {
+    const Req& q = *t.done[d];
+    const int SS = 13 + q.n_thr, NF4 = SS / 4;
+    const float* src = b.h_stage + off;
+    std::vector<float>& fs = states[d];
+    fs.assign((size_t)q.r.n_envs * 21, 0.0f);
+    for (int64_t i = 0; i < q.r.n_envs; ++i)
+      for (int j = 0; j < SS; ++j) {
+        const int64_t o = (j < NF4 * 4) ? ((int64_t)(j / 4) * q.n4 + i) * 4 + (j % 4)
+                                        : (int64_t)NF4 * 4 * q.n4 + (int64_t)(j - NF4 * 4) * q.n4 + i;
+        fs[i * 21 + j] = src[o];
+      }
+    const float* r = src + (size_t)q.n4 * SS;
+    rets[d].assign(r, r + q.r.n_envs);
+    off += (size_t)q.n4 * (SS + 1);
   }
-  // Book-keeping and retirement.
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    const double spacing = s->last_tick_end > 0 ? t_end - s->last_tick_end : ms * 1e-3;
-    s->last_tick_end = t_end;
-    s->ticks++;
-    s->env_steps += envs;
-    s->busy += ms * 1e-3;
-    s->tick.push_back({ms * 1e-3, 1.0});
-    int n_cont = 0;
-    for (Req* q : act) {
-      // First step of a request admitted this tick is measured from admission.
-      if (q->steps_done == 0) s->lat.push_back({t_end - q->t_admit, 1.0});
-      else ++n_cont;
-      q->steps_done++;
-    }
-    if (n_cont > 0) s->lat.push_back({spacing, (double)n_cont});
-    for (size_t d = 0; d < done.size(); ++d) {
-      Req& q = *done[d];
-      q.final_state.swap(states[d]);
-      q.returns.swap(rets[d]);
-      q.t_done = now_s();
-      q.status = MG_REQ_DONE;
-      s->slots.release(q.slot_off, q.n4);
-      s->states.release(q.st_off, state_units(q.n_thr, q.n4));
-      s->requests_done++;
-    }
-    if (!done.empty()) {
-      // `act` lists s->active in order (only this thread changes it).
-      std::vector<int64_t> keep;
-      keep.reserve(act.size());
-      for (const Req* q : act)
-        if (q->status != MG_REQ_DONE) keep.push_back(q->id);
-      s->active.swap(keep);
-    }
+  std::lock_guard<std::mutex> lk(s->mu);
+  const double spacing = s->last_tick_end > 0 ? t_end - s->last_tick_end : ms * 1e-3;
+  s->last_tick_end = t_end;
+  s->ticks++;
+  s->env_steps += t.envs;
+  s->busy += ms * 1e-3;
+  s->tick.push_back({ms * 1e-3, 1.0});
+  int n_cont = 0;
+  for (Req* q : t.act) {
+    // First step of a request admitted with this tick is measured from admission.
+    if (q->steps_done == 0) s->lat.push_back({t_end - q->t_admit, 1.0});
+    else ++n_cont;
+    q->steps_done++;
   }
-  if (!done.empty()) s->cv.notify_all();
+  if (n_cont > 0) s->lat.push_back({spacing, (double)n_cont});
+  for (size_t d = 0; d < t.done.size(); ++d) {
+    Req& q = *t.done[d];
+    q.final_state.swap(states[d]);
+    q.returns.swap(rets[d]);
+    q.t_done = now_s();
+    q.status = MG_REQ_DONE;
+    s->requests_done++;
+  }
+  if (!t.done.empty()) {
+    std::vector<int64_t> keep;
+    keep.reserve(s->active.size());
+    for (int64_t id : s->active)
+      if (s->reqs[id].status != MG_REQ_DONE) keep.push_back(id);
+    s->active.swap(keep);
+  }
   return true;
 }
 
 static void scheduler(mg_server* s) {
   cudaSetDevice(s->device);
+  Tick cur;   // the tick in flight
+  int par = 0;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
-      if (s->stop) return;
+      s->cv.wait(lk, [&] { return s->stop || cur.valid || !s->pending.empty() || !s->active.empty(); });
       if (s->fatal != MG_OK) return;
+      if (s->stop && !cur.valid) return;
     }
-    if (!tick_once(s)) {
+    // Prepare and enqueue the next tick while the current one runs.
+    Tick nxt = prepare_tick(s, cur, par);
+    if (nxt.valid && !enqueue_tick(s, nxt)) { s->cv.notify_all(); return; }
+    if (cur.valid && !finish_tick(s, cur)) { s->cv.notify_all(); return; }
+    cur = nxt;
+    if (nxt.valid) par ^= 1;
+    if (!cur.valid) {
+      // Nothing in flight: wait for a submission (or a timeout to retry admission).
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->fatal != MG_OK) { s->cv.notify_all(); return; }
-      // Nothing admitted and nothing active: wait for a submission or a release.
       if (s->active.empty()) s->last_tick_end = 0;
+      s->cv.notify_all();
       s->cv.wait_for(lk, std::chrono::milliseconds(1));
     }
     s->cv.notify_all();
+  }
+}
+
+// Pinned tables, staging and events of the two tick buffers.
+static bool alloc_tick_bufs(mg_server* s) {
+  for (TickBuf& b : s->buf) {
+    if (cudaMallocHost(&b.h_segs, sizeof(SegDesc) * s->cfg.max_requests) != cudaSuccess ||
+        cudaMallocHost(&b.h_rsegs, sizeof(SegDesc) * s->cfg.max_requests) != cudaSuccess ||
+        cudaMallocHost(&b.h_tile_seg, sizeof(int32_t) * s->tile_cap) != cudaSuccess ||
+        cudaEventCreate(&b.ev0) != cudaSuccess || cudaEventCreate(&b.ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+static void free_tick_bufs(mg_server* s) {
+  for (TickBuf& b : s->buf) {
+    if (b.h_segs) cudaFreeHost(b.h_segs);
+    if (b.h_rsegs) cudaFreeHost(b.h_rsegs);
+    if (b.h_tile_seg) cudaFreeHost(b.h_tile_seg);
+    if (b.h_stage) cudaFreeHost(b.h_stage);
+    if (b.ev0) cudaEventDestroy(b.ev0);
+    if (b.ev1) cudaEventDestroy(b.ev1);
+    if (b.ev_done) cudaEventDestroy(b.ev_done);
+    b = TickBuf();
   }
 }
 
@@ -483,13 +546,9 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     if (s->d_segs) cudaFree(s->d_segs);
     if (s->d_rsegs) cudaFree(s->d_rsegs);
     if (s->d_status) cudaFree(s->d_status);
-    if (s->h_segs) cudaFreeHost(s->h_segs);
-    if (s->h_rsegs) cudaFreeHost(s->h_rsegs);
+    free_tick_bufs(s);
     if (s->d_tile_seg) cudaFree(s->d_tile_seg);
-    if (s->h_tile_seg) cudaFreeHost(s->h_tile_seg);
     if (s->stream) cudaStreamDestroy(s->stream);
-    if (s->ev0) cudaEventDestroy(s->ev0);
-    if (s->ev1) cudaEventDestroy(s->ev1);
     delete s;
     return code;
   };
@@ -502,14 +561,12 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   // Tiles of a tick: each request's slots rounded up to whole tiles.
   s->tile_cap = S / kThreads + cfg->max_requests;
   if (cudaMalloc(&s->d_tile_seg, sizeof(int32_t) * s->tile_cap) != cudaSuccess ||
-      cudaMallocHost(&s->h_tile_seg, sizeof(int32_t) * s->tile_cap) != cudaSuccess ||
       cudaMalloc(&s->d_cls, sizeof(ClassF) * n_classes) != cudaSuccess ||
       cudaMalloc(&s->d_nominal, sizeof(ClassNominal) * n_classes) != cudaSuccess ||
       cudaMalloc(&s->d_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
       cudaMalloc(&s->d_rsegs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
       cudaMalloc(&s->d_status, sizeof(uint32_t)) != cudaSuccess ||
-      cudaMallocHost(&s->h_segs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess ||
-      cudaMallocHost(&s->h_rsegs, sizeof(SegDesc) * cfg->max_requests) != cudaSuccess) {
+      !alloc_tick_bufs(s)) {
     cudaGetLastError();
     return cleanup(MG_ERR_OOM);
   }
@@ -537,8 +594,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   if (cudaMemcpy(s->d_cls, cf.data(), sizeof(ClassF) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_nominal, cn.data(), sizeof(ClassNominal) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(MG_ERR_CUDA);
   }
@@ -653,13 +709,8 @@ int mg_server_destroy(mg_server* s) {
   cudaFree(s->d_segs);
   cudaFree(s->d_rsegs);
   cudaFree(s->d_status);
-  cudaFreeHost(s->h_segs);
-  cudaFreeHost(s->h_rsegs);
+  free_tick_bufs(s);
   cudaFree(s->d_tile_seg);
-  cudaFreeHost(s->h_tile_seg);
-  if (s->h_stage) cudaFreeHost(s->h_stage);
-  cudaEventDestroy(s->ev0);
-  cudaEventDestroy(s->ev1);
   cudaStreamDestroy(s->stream);
   delete s;
   return MG_OK;
