@@ -692,10 +692,17 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
 #ifndef MG_KSTEP_MIN_BLOCKS
 #define MG_KSTEP_MIN_BLOCKS MG_STEP_MIN_BLOCKS
 #endif
-template <int PM, int VAR, bool KP>
+// Serving-tick kernels (TM) are compiled for 3 blocks per SM: at 4 their
+// 8-thruster instantiation spilled, and shared memory held it to 3 blocks
+// anyway (10^4-request serving run: 5.66e9 -> 6.19e9 env-steps/s while busy).
+#ifndef MG_TM_MIN_BLOCKS
+#define MG_TM_MIN_BLOCKS 3
+#endif
+template <int PM, int VAR, bool KP, bool TM>
 struct StepMinBlocks {
   static constexpr int value = VAR == 2               ? MG_RK4_MIN_BLOCKS
                                : VAR == 1             ? MG_GEN_MIN_BLOCKS
+                               : TM                   ? MG_TM_MIN_BLOCKS
                                : (KP && PM == 0)      ? MG_KSTEP_MIN_BLOCKS
                                                       : MG_STEP_MIN_BLOCKS;
 };
@@ -713,7 +720,7 @@ using KParam = std::conditional_t<!KP, NoClassK, std::conditional_t<VAR == 0, Cl
 // body stays in the kernel itself: moved into a function taking the
 // parameters by reference, the per-env and payload instantiations spilled.
 template <int NT, int PM, int VAR, bool KP, bool TM>
-__global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP>::value))
+__global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::value))
     mg_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ KParam<KP, VAR> kp) {
   using SG = Stage<NT>;
   const ClassK* kc = nullptr;
