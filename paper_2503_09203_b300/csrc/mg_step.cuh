@@ -431,6 +431,17 @@ __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& s
   }
 }
 
+// Actuator table of segment `sd` into one warp's copy (lanes of that warp).
+__device__ __forceinline__ void stage_act_warp(const StepArgs& a, const SegDesc& sd, float* act, int lane) {
+  const ClassF& cf = a.classes[sd.cls];
+  for (int k = lane; k < SA_DIM; k += WENV) {
+    if (k < 48) act[k] = cf.alloc[k / 8][k % 8];
+    else if (k < 56) act[k] = cf.kf[k - 48];
+    else if (k < 64) act[k] = cf.dz[k - 56];
+    else act[k] = sd.alpha[k - 64];
+  }
+}
+
 // Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
 // (a multiple of 4, > 0) envs start at local env index w0 of the segment.
 template <int NT, int PM>
@@ -735,7 +746,9 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   float* const buf1 = w_base + fl;
   float* const obs_sep = w_base + 2 * fl;   // separate observation tile (unless aliased)
   float* const s_par = s_dyn + N_WARPS * wfl;
-  __shared__ __align__(16) float s_act[SA_DIM];
+  // Serving ticks (TM) keep one actuator table per warp (their tiles change
+  // segment almost every time); other launches one per block.
+  __shared__ __align__(16) float s_act[TM ? N_WARPS * SA_DIM : SA_DIM];
   __shared__ __align__(16) float s_phys[PAR_DIM];
   __shared__ __align__(16) float s_gen[VAR ? GEN_FLOATS : 4];
   __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
@@ -799,7 +812,15 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       }
     }
     const SegDesc& sd = segs[si];
-    if (!KP && si != prev_seg) {
+    if constexpr (TM) {
+      // Per-env physics; the warp rewrites its own actuator table (its lanes
+      // finished the previous tile at the warp barrier that ends each round).
+      if (si != prev_seg) {
+        stage_act_warp(a, sd, s_act + warp * SA_DIM, lane);
+        __syncwarp();
+        prev_seg = si;
+      }
+    } else if (!KP && si != prev_seg) {
       // Class constants change: rewrite them between two block barriers
       // (every warp of the block walks the same tiles).
       __syncthreads();
@@ -816,8 +837,9 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
         failed = true;
     }
     if (!failed)
-      step_tile<NT, PM, VAR, KP>(a, kc, kg, sd, tile, smem_addr(s_act), smem_addr(s_phys), smem_addr(s_gen),
-                             b ? buf1 : buf0, MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
+      step_tile<NT, PM, VAR, KP>(a, kc, kg, sd, tile, smem_addr(s_act + (TM ? warp * SA_DIM : 0)),
+                                 smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
+                                 MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     // The warp has read its stage buffer b; lane 0 may refill it next round.
     __syncwarp();
     nvw_cur = nvw_next;
