@@ -91,6 +91,7 @@ struct mg_sim {
     std::vector<int> full_grid;   // persistent grid of each group launched alone
     std::vector<char> carve_max;
     std::vector<Group> groups;     // the launches of a step
+    bool first_pdl = false;        // the first launch is a programmatic dependent too
     std::vector<ClassK> kc;        // constants of each launch with cls >= 0
   } plan;
   std::vector<ClassF> h_cls;       // host copies of the class tables
@@ -770,6 +771,14 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
     if (!p.cores) p.grid[i] = p.full_grid[i];
     p.carve_max[i] = carveout_max(sim, g, shared_sm) ? 1 : 0;
   }
+  // Measured: a programmatic first launch helps side-by-side steps and
+  // propeller steps run one launch after the other (1M envs K=4 70.0 -> 67.6
+  // us, K=1 52.4 -> 50.5 us, per-env DR 106.0 -> 104.3 us) but slows a step
+  // that mixes propeller and generic-actuator launches (184 -> 196 us).
+  p.first_pdl = true;
+  if (!p.cores)
+    for (const Group& g : p.groups)
+      if (g.var != 0) p.first_pdl = false;
   p.bps = sim->blocks_per_sm;
   p.valid = true;
   return p;
@@ -784,9 +793,14 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     a.seg_hi = g.seg_hi;
     a.tile_lo = g.tile_lo;
     a.n_tiles = g.n_tiles;
-    a.wait_first = first && p.cores;
+    // Later launches are programmatic dependents of the one before. With
+    // p.first_pdl the first is too: it waits for the kernel before it (the
+    // previous step, or unrelated work) before it reads anything or lets the
+    // step's other launches start, so its blocks only become resident and set
+    // up early.
+    a.wait_first = first && p.first_pdl;
     CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
-                   p.grid[i], !first || p.cores, p.carve_max[i] != 0, st));
+                   p.grid[i], !first || p.first_pdl, p.carve_max[i] != 0, st));
     first = false;
   }
   return MG_OK;
