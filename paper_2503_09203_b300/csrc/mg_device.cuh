@@ -182,8 +182,16 @@ MG_HD void msincos(double x, double* s, double* c) { *s = sin(x); *c = cos(x); }
 template <typename ActT>
 MG_HD bool dz_active(const ActT&) { return true; }
 
+// Whether a table's allocation rows already carry the thrust constants
+// (rows of B diag(k)): then f below is n|n| and tau = (B diag(k)) f.
+template <typename ActT>
+struct ActPremul {
+  static constexpr bool value = false;
+};
+
 template <typename S, int NT, typename ActT>
 MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S tau[6]) {
+  constexpr bool PRE = ActPremul<ActT>::value;
   if (dz_active(A)) {
     S kf[NT], dz[NT], al[NT];
     act_rotor<S, NT>(A, kf, dz, al);
@@ -191,7 +199,7 @@ MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S 
     for (int i = 0; i < NT; ++i) {
       x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
       const S an = mabs(x.n[i]);
-      f[i] = (an < dz[i]) ? S(0.0f) : kf[i] * x.n[i] * an;
+      f[i] = (an < dz[i]) ? S(0.0f) : (PRE ? x.n[i] * an : kf[i] * x.n[i] * an);
     }
   } else {
     // No dead zone in this class: |n| < 0 never holds.
@@ -200,7 +208,7 @@ MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S 
 #pragma unroll
     for (int i = 0; i < NT; ++i) {
       x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
-      f[i] = kf[i] * x.n[i] * mabs(x.n[i]);
+      f[i] = PRE ? x.n[i] * mabs(x.n[i]) : kf[i] * x.n[i] * mabs(x.n[i]);
     }
   }
 #pragma unroll

@@ -43,6 +43,13 @@ struct ClassF {
 };
 static_assert(sizeof(ClassF) == 104 * 4, "ClassF layout");
 
+// Propeller steps with class-constant or payload parameters take allocation
+// rows premultiplied by the thrust constants (rows of B diag(k)): the thrust
+// per channel is then n|n|, one multiply less per thruster and substep.
+#ifndef MG_PREMUL
+#define MG_PREMUL 1
+#endif
+
 // One class's constants passed by value as a kernel parameter (propeller
 // steps with class constants launch one class at a time): the kernel reads
 // them as constant-bank operands, with no shared-memory load and no register

@@ -605,6 +605,9 @@ static ClassK class_k(const mg_sim* sim, const Group& g) {
   const ClassF& f = sim->h_cls[g.cls];
   const SegDesc& sd = sim->segs[g.seg_lo];
   std::memcpy(k.alloc, f.alloc, sizeof(k.alloc));
+  if (MG_PREMUL && g.var == 0 && param_mode(sim) != 1)   // as the kernels' Premul: rows of B diag(k)
+    for (int r = 0; r < 6; ++r)
+      for (int i = 0; i < 8; ++i) k.alloc[r][i] = f.alloc[r][i] * f.kf[i];
   std::memcpy(k.kf, f.kf, sizeof(k.kf));
   std::memcpy(k.dz, f.dz, sizeof(k.dz));
   std::memcpy(k.alpha, sd.alpha, sizeof(k.alpha));

@@ -177,6 +177,18 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
   return v;
 }
 
+// Whether propeller launches of parameter source PM take allocation rows
+// premultiplied by the thrust constants (MG_PREMUL). Not for per-env steps
+// (PM 1, serving included): there the 8-thruster kernel spilled and the step
+// measured slower (104.0 -> 106.4 us at 1M envs); class-constant and payload
+// steps gained (1M envs K=4 67.6 -> 66.9 us, K=8 96.8 -> 95.0 us). Every
+// table source of a launch kind does the same, so results do not depend on
+// the launch shape.
+template <int PM, int VAR>
+struct Premul {
+  static constexpr bool value = MG_PREMUL && VAR == 0 && PM != 1;
+};
+
 // Actuator table in shared memory: alloc[6][8] | kf[8] | dz[8] | alpha[8].
 // dz_on = 0: the class has no dead zone (the thrust skips the test).
 #ifndef MG_DZ_FLAG
@@ -184,33 +196,46 @@ __device__ __forceinline__ float4 lds4(unsigned a) {
 #endif
 // DZF: the kernel carries a dead-zone-free thrust path (class-constant
 // propellers only: in the other variants the second path costs registers).
-template <bool DZF>
+// PRE: the staged rows carry the thrust constants (Premul).
+template <bool DZF, bool PRE>
 struct ActSmemT {
   unsigned base;
   unsigned dz_on;
 };
 template <bool DZF>
-__device__ __forceinline__ bool dz_active(const ActSmemT<DZF>& A) { return !(MG_DZ_FLAG && DZF) || A.dz_on != 0u; }
+struct ActPremul<ActSmemT<DZF, true>> {
+  static constexpr bool value = true;
+};
+template <bool DZF, bool PRE>
+__device__ __forceinline__ bool dz_active(const ActSmemT<DZF, PRE>& A) {
+  return !(MG_DZ_FLAG && DZF) || A.dz_on != 0u;
+}
 // Actuator table passed as the kernel parameter (KP launches): read as
-// constant-bank operands. DZF as for the shared-memory view.
-template <bool DZF>
+// constant-bank operands. DZF and PRE as for the shared-memory view.
+template <bool DZF, bool PRE>
 struct ActK {
   const ClassK& k;
 };
 template <bool DZF>
-__device__ __forceinline__ bool dz_active(const ActK<DZF>& A) { return !(MG_DZ_FLAG && DZF) || A.k.dz_on != 0u; }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_row(const ActK<DZF>& A, int k, S (&r)[NT]) {
+struct ActPremul<ActK<DZF, true>> {
+  static constexpr bool value = true;
+};
+template <bool DZF, bool PRE>
+__device__ __forceinline__ bool dz_active(const ActK<DZF, PRE>& A) {
+  return !(MG_DZ_FLAG && DZF) || A.k.dz_on != 0u;
+}
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_row(const ActK<DZF, PRE>& A, int k, S (&r)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) r[i] = A.k.alloc[k][i];
 }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor(const ActK<DZF>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_rotor(const ActK<DZF, PRE>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) { kf[i] = A.k.kf[i]; dz[i] = A.k.dz[i]; al[i] = A.k.alpha[i]; }
 }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor_nodz(const ActK<DZF>& A, S (&kf)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_rotor_nodz(const ActK<DZF, PRE>& A, S (&kf)[NT], S (&al)[NT]) {
 #pragma unroll
   for (int i = 0; i < NT; ++i) { kf[i] = A.k.kf[i]; al[i] = A.k.alpha[i]; }
 }
@@ -227,18 +252,18 @@ __device__ __forceinline__ void lds_vec(unsigned a, float (&r)[NT]) {
     if (4 * q + 3 < NT) r[(4 * q + 3) % NT] = v.w;
   }
 }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_row(const ActSmemT<DZF>& A, int k, S (&r)[NT]) {
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_row(const ActSmemT<DZF, PRE>& A, int k, S (&r)[NT]) {
   lds_vec<NT>(A.base + 4 * (SA_ALLOC + 8 * k), r);
 }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor(const ActSmemT<DZF>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_rotor(const ActSmemT<DZF, PRE>& A, S (&kf)[NT], S (&dz)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_DZ, dz);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
-template <typename S, int NT, bool DZF>
-__device__ __forceinline__ void act_rotor_nodz(const ActSmemT<DZF>& A, S (&kf)[NT], S (&al)[NT]) {
+template <typename S, int NT, bool DZF, bool PRE>
+__device__ __forceinline__ void act_rotor_nodz(const ActSmemT<DZF, PRE>& A, S (&kf)[NT], S (&al)[NT]) {
   lds_vec<NT>(A.base + 4 * SA_KF, kf);
   lds_vec<NT>(A.base + 4 * SA_ALPHA, al);
 }
@@ -414,12 +439,12 @@ constexpr int SEG_CACHE = 16;   // segments of a launch kept in shared memory
 
 // Class tables of segment `sd` into act (SA_DIM) and phys (PAR_DIM), and its
 // generic actuator table into gen (generic variants), by the block's threads.
-template <int VAR>
+template <int PM, int VAR>
 __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& sd, float* act, float* phys,
                                              float* gen, int tid) {
   const ClassF& cf = a.classes[sd.cls];
   for (int k = tid; k < SA_DIM + PAR_DIM; k += STEP_BLK) {
-    if (k < 48) act[k] = cf.alloc[k / 8][k % 8];
+    if (k < 48) act[k] = Premul<PM, VAR>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
     else if (k < 56) act[k] = cf.kf[k - 48];
     else if (k < 64) act[k] = cf.dz[k - 56];
     else if (k < 72) act[k] = sd.alpha[k - 64];
@@ -434,8 +459,8 @@ __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& s
 // Actuator table of segment `sd` into one warp's copy (lanes of that warp).
 __device__ __forceinline__ void stage_act_warp(const StepArgs& a, const SegDesc& sd, float* act, int lane) {
   const ClassF& cf = a.classes[sd.cls];
-  for (int k = lane; k < SA_DIM; k += WENV) {
-    if (k < 48) act[k] = cf.alloc[k / 8][k % 8];
+  for (int k = lane; k < SA_DIM; k += WENV) {   // serving: per-env propeller steps, rows as staged above
+    if (k < 48) act[k] = Premul<1, 0>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
     else if (k < 56) act[k] = cf.kf[k - 48];
     else if (k < 64) act[k] = cf.dz[k - 56];
     else act[k] = sd.alpha[k - 64];
@@ -497,7 +522,8 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
   const unsigned nvw = warp_envs(sd, local0, warp);
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
-  using ActSmem = ActSmemT<DZF>;
+  constexpr bool PRE = Premul<PM, VAR>::value;
+  using ActSmem = ActSmemT<DZF, PRE>;
   const ActSmem A{s_act, (unsigned)(sd.flags & 1)};
 
   // Per-env parameters: plain per-env runs prefetch their 9 planes into
@@ -602,7 +628,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
       // Kernel-parameter tables are read as operands where they are used.
       for (int k = 0; k < sd.K; ++k) {
         if constexpr (KP) {
-          const ActK<DZF> Av{*kc};
+          const ActK<DZF, PRE> Av{*kc};
           if constexpr (PM == 0) {
             if constexpr (VAR == 0) sub(*kc, Av, NoGen{});
             else sub(*kc, Av, GenK{*kg});
@@ -824,7 +850,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       // Class constants change: rewrite them between two block barriers
       // (every warp of the block walks the same tiles).
       __syncthreads();
-      stage_tables<VAR>(a, sd, s_act, s_phys, s_gen, tid);
+      stage_tables<PM, VAR>(a, sd, s_act, s_phys, s_gen, tid);
       __syncthreads();
       prev_seg = si;
     }
