@@ -464,6 +464,41 @@ def test_fixed_grid_keeps_results(per_env, counts):
     sim.close()
 
 
+@pytest.mark.parametrize("per_env", [True, False])
+def test_graph_of_per_class_launches_equals_direct_rollout(per_env):
+    """A size that takes the one-launch-per-class plan (class tables as the
+    kernel parameter, every launch a programmatic dependent): a captured
+    4-step rollout replays to the same states, observations and rewards as
+    the direct rollout, bit for bit."""
+    classes = vehicles.five_classes()
+    counts = [300001, 3, 240001, 5, 9]
+    sim = make_sim(classes, counts, K=2, reset=dict(vehicles.HOVER_DR if per_env else vehicles.HOVER),
+                   per_env=per_env)
+    assert sim.launches_per_step() == 5
+    sim.reset(seed=12)
+    s0 = sim.get_state()
+    T = 4
+    a_dev = sim.pack_actions(workloads.actions(13, T, sim.n_envs))
+    obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    sim.rollout(a_dev, T, obs, rew)
+    torch.cuda.synchronize()
+    s_ref, o_ref, r_ref = sim.get_state(), obs.clone(), rew.clone()
+    sim.set_state(s0)
+    obs.zero_()
+    rew.zero_()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = B.mg_graph_capture(sim.handle, a_dev, T, obs, rew, stream=st)
+        B.mg_graph_launch(g, stream=st)
+    st.synchronize()
+    assert np.array_equal(sim.get_state(), s_ref)
+    assert torch.equal(obs, o_ref) and torch.equal(rew, r_ref)
+    B.mg_graph_destroy(g)
+    sim.status()
+    sim.close()
+
+
 def test_flop_count_matches_hand_count():
     """The counted substep of the 8-thruster class: rotor 3/thr, thrust 2/thr,
     allocation 6 x (8 mul + 7 add) = 90; the remaining terms are fixed."""
