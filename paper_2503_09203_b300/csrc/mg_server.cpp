@@ -177,7 +177,7 @@ struct mg_server {
   bool stop = false;
   int64_t next_id = 1;
   std::deque<int64_t> pending;
-  std::vector<int64_t> active;
+  std::vector<Req*> active;   // admitted, not yet published as done (map nodes are stable)
   std::unordered_map<int64_t, Req> reqs;
   // stats
   int64_t requests_done = 0, env_steps = 0, ticks = 0;
@@ -202,7 +202,7 @@ static int sfail(mg_server* s, int code, const char* fmt, ...) {
 static int64_t state_units(int n_thr, int n4) { return (int64_t)n4 * (13 + n_thr); }
 
 // Admit pending requests in FIFO order while they fit; reset their envs.
-static void admit_locked(mg_server* s, std::vector<int64_t>& admitted) {
+static void admit_locked(mg_server* s, std::vector<Req*>& admitted) {
   while (!s->pending.empty() && (int)s->active.size() < s->cfg.max_requests) {
     Req& q = s->reqs[s->pending.front()];
     const int64_t so = s->slots.alloc(q.n4);
@@ -217,8 +217,8 @@ static void admit_locked(mg_server* s, std::vector<int64_t>& admitted) {
     q.status = MG_REQ_RUNNING;
     q.t_admit = now_s();
     s->qdel.push_back({q.t_admit - q.t_submit, 1.0});
-    s->active.push_back(q.id);
-    admitted.push_back(q.id);
+    s->active.push_back(&q);
+    admitted.push_back(&q);
     s->pending.pop_front();
   }
 }
@@ -250,19 +250,15 @@ static SegDesc seg_of(const Req& q) {
 static Tick prepare_tick(mg_server* s, const Tick& prev, int par) {
   Tick t;
   t.par = par;
-  std::vector<int64_t> admitted;
   std::lock_guard<std::mutex> lk(s->mu);
   for (Req* q : prev.done) {
     s->slots.release(q->slot_off, q->n4);
     s->states.release(q->st_off, state_units(q->n_thr, q->n4));
   }
   if (s->stop || s->fatal != MG_OK) return t;
-  admit_locked(s, admitted);
-  for (int64_t id : admitted) t.fresh.push_back(&s->reqs[id]);
-  for (int64_t id : s->active) {
-    Req& q = s->reqs[id];
-    if (q.steps_sched < q.r.horizon) t.act.push_back(&q);
-  }
+  admit_locked(s, t.fresh);
+  for (Req* q : s->active)
+    if (q->steps_sched < q->r.horizon) t.act.push_back(q);
   t.valid = !t.act.empty();
   return t;
 }
@@ -441,10 +437,10 @@ static bool finish_tick(mg_server* s, const Tick& t) {
     s->requests_done++;
   }
   if (!t.done.empty()) {
-    std::vector<int64_t> keep;
+    std::vector<Req*> keep;
     keep.reserve(s->active.size());
-    for (int64_t id : s->active)
-      if (s->reqs[id].status != MG_REQ_DONE) keep.push_back(id);
+    for (Req* q : s->active)
+      if (q->status != MG_REQ_DONE) keep.push_back(q);
     s->active.swap(keep);
   }
   return true;
