@@ -197,8 +197,45 @@ __device__ __forceinline__ void st21(float* base, int64_t stride, const St<float
   for (int j = 0; j < 13 + NT; ++j) base[j * stride] = f[j];
 }
 
+// Backward-pass state reads: the recomputed states of a segment are read in
+// reverse order, each into a per-thread shared-memory slot by cp.async one
+// substep ahead, so the read of the next state overlaps the current
+// vector-Jacobian product instead of stalling it.
+constexpr int ADJ_BLK = 32;   // adjoint blocks: one warp
+struct StatePrefetch {
+  float* buf;          // [2][21][ADJ_BLK] floats of this block
+  int lane, cur;
+  __device__ __forceinline__ float* slot(int b) const { return buf + b * 21 * ADJ_BLK + lane; }
+  template <int NT>
+  __device__ __forceinline__ void issue(const float* base, int64_t stride, int b) const {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot(b));
+#pragma unroll
+    for (int j = 0; j < 13 + NT; ++j)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * ADJ_BLK * j), "l"(base + j * stride)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  template <int NT>
+  __device__ __forceinline__ void read(int b, St<float, NT>& x) const {
+    float f[13 + NT];
+    const float* p = slot(b);
+#pragma unroll
+    for (int j = 0; j < 13 + NT; ++j) f[j] = p[ADJ_BLK * j];
+    fields_to_state<NT>(f, x);
+  }
+  // Wait for the state in the current slot, read it, start the copy of the
+  // state at `next` (if any) into the other slot.
+  template <int NT>
+  __device__ __forceinline__ void advance(St<float, NT>& x, const float* next, int64_t stride) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    read<NT>(cur, x);
+    if (next) issue<NT>(next, stride, cur ^ 1);
+    cur ^= 1;
+  }
+};
+
 template <int NT, typename ActT>
-__device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, int64_t i) {
+__device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, int64_t i, float* pf_buf) {
   const int64_t slot = sd.slot_off + i;
   const int64_t ns = a.n_slots;
   Phys<float> P;
@@ -243,14 +280,27 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
       }
     }
     st21<NT>(scr + (int64_t)j * 21 * ns, ns, x);
+    // The states are read back in reverse: index j (the segment's end), j-1,
+    // ..., 0; the state at a step boundary serves both steps.
+    __threadfence_block();
+    StatePrefetch pf{pf_buf, (int)threadIdx.x, 0};
+    pf.issue<NT>(scr + (int64_t)j * 21 * ns, ns, 0);
+    int next = j - 1;
+    auto next_ptr = [&]() -> const float* { return next >= 0 ? scr + (int64_t)next * 21 * ns : nullptr; };
     for (int t = t1 - 1; t >= t0; --t) {
       float raw[NT], c[NT], lc[NT];
       load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
 #pragma unroll
       for (int q = 0; q < NT; ++q) { c[q] = clamp1(raw[q]); lc[q] = 0.0f; }
-      const int jb = (t - t0) * K;
+      // State at the end of step t: the segment's end (first step back), else
+      // the state the previous step's last substep read (still in its slot).
       St<float, NT> xe;
-      ld21<NT>(scr + (int64_t)(jb + K) * 21 * ns, ns, xe);
+      if (t == t1 - 1) {
+        pf.advance<NT>(xe, next_ptr(), ns);
+        --next;
+      } else {
+        pf.read<NT>(pf.cur ^ 1, xe);
+      }
       float go[13];
       const float* gop = nullptr;
       if (a.g_obs) {
@@ -263,7 +313,8 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
       observe_vjp<float, NT>(xe, c, tgt, gop, gr, lam, lc);
       for (int k = K - 1; k >= 0; --k) {
         St<float, NT> xs;
-        ld21<NT>(scr + (int64_t)(jb + k) * 21 * ns, ns, xs);
+        pf.advance<NT>(xs, next_ptr(), ns);
+        --next;
         substep_vjp<float, NT>(xs, c, P, A, sd.h, lam, lc, g);
       }
       if (a.g_actions) {
@@ -298,10 +349,10 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
 // workload) then spread over all SMs instead of a few dozen. Class groups are
 // launched as programmatic dependents of one another (disjoint envs and
 // outputs) so that they run side by side.
-constexpr int ADJ_BLK = 32;
 template <int NT>
 __global__ void __launch_bounds__(ADJ_BLK) mg_adjoint_kernel(const __grid_constant__ AdjArgs a) {
   __shared__ Act<float> act;
+  __shared__ __align__(16) float pf_buf[2 * 21 * ADJ_BLK];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int parts = a.tile_envs / (int)blockDim.x;
   const int tile = a.tile_lo + (int)blockIdx.x / parts;
@@ -328,7 +379,7 @@ __global__ void __launch_bounds__(ADJ_BLK) mg_adjoint_kernel(const __grid_consta
       }
     } else {
       const volatile Act<float>& va = act;
-      adjoint_env<NT>(a, sd, va, i);
+      adjoint_env<NT>(a, sd, va, i, pf_buf);
     }
   }
   // Completion stays ordered along the stream (see the step kernel).
