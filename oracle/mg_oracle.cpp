@@ -682,12 +682,14 @@ double or_uniform(uint64_t seed, uint64_t stream, uint64_t env, uint64_t j) {
 }
 
 // Serving-loop action: a(seed, env, step, thr) in [-1, 1), 24-bit grid, from
-// Philox4x64-10 under key (seed, 3), counter (env, step, thr/4, 0), lane thr%4,
-// top 24 bits: a = k/2^23 - 1.
+// one Philox4x64-10 block under key (seed, 3), counter (env, step, 0, 0):
+// word thr % 4, its top 24 bits for thr < 4 and bits 31..8 for thr = 4..7;
+// a = k/2^23 - 1.
 float or_action(uint64_t seed, uint64_t env, uint64_t step, int thr) {
-  uint64_t ctr[4] = {env, step, (uint64_t)(thr / 4), 0}, key[2] = {seed, kStreamAction}, out[4];
+  uint64_t ctr[4] = {env, step, 0, 0}, key[2] = {seed, kStreamAction}, out[4];
   philox4x64_10(ctr, key, out);
-  double k = (double)(out[thr % 4] >> 40);
+  const uint64_t w = out[thr % 4];
+  double k = (double)(thr < 4 ? (w >> 40) : ((w >> 8) & 0xFFFFFFull));
   return (float)(k * (1.0 / 8388608.0) - 1.0);
 }
 

@@ -128,10 +128,13 @@ __device__ __forceinline__ int seg_of_tile(const StepArgs& a, const SegDesc* seg
 
 __device__ __forceinline__ float clamp1(float a) { return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a); }
 
-// Serving action from one 64-bit Philox output: top 24 bits k -> k 2^-23 - 1,
-// exact in FP32, on [-1, 1).
-__device__ __forceinline__ float action_of_bits(uint64_t bits) {
-  return (float)(int)(bits >> 40) * (1.0f / 8388608.0f) - 1.0f;
+// Serving action j of one Philox4x64 block: 24 bits k of word j % 4 (its top
+// bits for j < 4, bits 31..8 for j = 4..7) -> k 2^-23 - 1, exact in FP32, on
+// [-1, 1). One block serves up to 8 thrusters.
+__device__ __forceinline__ float action_of_block(const uint64_t (&o)[4], int j) {
+  const uint64_t w = o[j & 3];
+  const unsigned k = j < 4 ? (unsigned)(w >> 40) : (unsigned)((w >> 8) & 0xFFFFFFull);
+  return (float)(int)k * (1.0f / 8388608.0f) - 1.0f;
 }
 
 template <int NT>
@@ -597,14 +600,11 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
           for (int j = 0; j < NT; ++j) c[j] = clamp1(raw[j]);
         }
       } else {
+        static_assert(NT <= 8, "one Philox block holds 8 actions");
+        uint64_t o[4];
+        philox4x64((uint64_t)i, (uint64_t)(sd.step0 + t), 0, 0, sd.seed, STREAM_ACTION, o);
 #pragma unroll
-        for (int g = 0; g < (NT + 3) / 4; ++g) {
-          uint64_t o[4];
-          philox4x64((uint64_t)i, (uint64_t)(sd.step0 + t), (uint64_t)g, 0, sd.seed, STREAM_ACTION, o);
-#pragma unroll
-          for (int l = 0; l < 4; ++l)
-            if (4 * g + l < NT) c[(4 * g + l) % NT] = clamp1(action_of_bits(o[l]));
-        }
+        for (int j = 0; j < NT; ++j) c[j] = clamp1(action_of_block(o, j));
       }
       if (a.ckpt && (t % a.ckpt_every) == 0) {
         float f[13 + NT];

@@ -73,6 +73,20 @@ def test_philox_matches_numpy(key, ctr):
     assert oracle.philox4x64(ctr, key) == ref
 
 
+def test_action_bits_from_numpy_philox():
+    # Serving actions: one Philox4x64-10 block per (env, step) under key
+    # (seed, 3); thruster j takes 24 bits of word j % 4 (top bits for j < 4,
+    # bits 31..8 for j >= 4). The block comes from numpy's generator here.
+    for seed, env, step in ((7, 1, 0), (123456789, 5, 17), (2**63 + 5, 4095, 999)):
+        # numpy's Philox(counter=c) emits the block of counter c + 1 (env >= 1 here).
+        g = np.random.Philox(key=np.array((seed, 3), dtype=np.uint64),
+                             counter=np.array((env - 1, step, 0, 0), dtype=np.uint64))
+        w = [int(v) for v in g.random_raw(4)]
+        for j in range(8):
+            k = (w[j % 4] >> 40) if j < 4 else ((w[j % 4] >> 8) & 0xFFFFFF)
+            assert oracle.action(seed, env, step, j) == np.float32(k / 2.0 ** 23 - 1.0)
+
+
 def test_action_grid():
     vals = np.array([oracle.action(7, e, t, i) for e in range(3) for t in range(5) for i in range(8)])
     assert np.all(vals >= -1.0) and np.all(vals < 1.0)
