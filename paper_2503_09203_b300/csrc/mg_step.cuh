@@ -517,7 +517,8 @@ __device__ __forceinline__ unsigned warp_envs(const SegDesc& sd, int64_t local0,
 // registers hold the next tile's parameters, so the per-env kernels stopped
 // spilling); 16k-env rollout graph 6.87e9 -> 9.25e9 env-steps/s. Serving
 // ticks (short tiles) keep vector loads: 36 four-byte copies per thread cost
-// them 4-6%.
+// them 4-6%; payload steps (60 copies) measured slower too (131.4 -> 133.9
+// us) and keep their direct staging.
 #ifndef MG_PAR_ASYNC
 #define MG_PAR_ASYNC 1
 #endif
