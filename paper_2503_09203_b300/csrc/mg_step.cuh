@@ -763,15 +763,17 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
 // warp. Every warp runs its own pipeline: while it computes its slice of tile
 // j, its lane 0 has already issued the bulk copies of its slice of the next
 // tile into the warp's other stage buffer, and observation rows leave through
-// a per-warp bulk store. Warps never wait on one another except when the
-// class constants change. Every wait is bounded (2 s); a warp that gives up
+// a per-warp bulk store. Warps never wait on one another except when a
+// block's shared class table changes (not in launches with the tables as the
+// kernel parameter, nor in serving ticks, whose warps keep their own table).
+// Every wait is bounded (2 s); a warp that gives up
 // sets bit 1 of the status word and skips the rest of its tiles (it keeps
 // walking them, so every block barrier is still reached).
 // The RK4 variant keeps the stage point, the running sum and the substep's
 // start state live at once. It is compiled for 3 resident blocks per SM (168
 // registers): measured at 1M envs, K=4, that beats both 4 blocks (heavy
-// spills) and 2 blocks (too few warps to hide latency), although the tracking
-// and per-env kernels still spill a few hundred bytes. The generic-actuator
+// spills) and 2 blocks (too few warps to hide latency), although the payload
+// instantiations still spill 52-160 bytes. The generic-actuator
 // variant (fins, servo tilt) is also compiled for 3 blocks per SM: its extra
 // live state otherwise costs 3% at K=4 and 8% at K=1.
 #ifndef MG_RK4_MIN_BLOCKS
