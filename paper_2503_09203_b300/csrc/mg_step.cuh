@@ -873,7 +873,9 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
     if (PA) issue_par_copies(a, s0, local0, warp, lane, s_par, tid);
   }
   int prev_seg = -1, n_emit = 0;
-  unsigned use[2] = {0u, 0u};   // completed uses of each stage barrier
+  // Completed uses of each stage barrier (two scalars: an array indexed by
+  // the stage parity would live in local memory).
+  unsigned use0 = 0u, use1 = 0u;
   bool failed = false;
   for (int j = 0, tt = blockIdx.x; tt < a.n_tiles; ++j, tt += gridDim.x) {
     const int tile = a.tile_lo + tt;
@@ -916,8 +918,11 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
     // A warp whose wait ran out stops computing and copying but stays in the
     // loop, so that it still reaches every block barrier of the launch.
     if (nvw_cur > 0 && !failed) {
-      if (mbar_wait_bounded(b ? full1 : full0, use[b] & 1u, sd.wait_limit_ns ? sd.wait_limit_ns : kWaitLimitNs))
-        use[b]++;
+      if (mbar_wait_bounded(b ? full1 : full0, (b ? use1 : use0) & 1u,
+                            sd.wait_limit_ns ? sd.wait_limit_ns : kWaitLimitNs)) {
+        if (b) ++use1;
+        else ++use0;
+      }
       else
         failed = true;
     }
