@@ -666,7 +666,7 @@ def main():
     roof["traffic_note"] = (f"DRAM read+write bytes per step ({n_launches} launches) from profiles/step_kernel_full_hover_1M_K4.md "
                             "(ncu serialised replay: reads = algorithmic, writes partly deferred in L2)"
                             if traffic else "null: no ncu capture of these kernel sources at this workload")
-    roof.update({"kernel": f"mg_step_kernel<NT, 3, 0> (class constants as the kernel parameter), {n_launches} launches per step",
+    roof.update({"kernel": f"mg_step_kernel<NT, 0, 0, 1, 0, 0> (class constants, propellers, Euler, class tables as the kernel parameter), {n_launches} launches per step",
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
                  "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -110,17 +110,21 @@ MG_HD void cross3(const S a[3], const S b[3], S o[3]) {
 
 template <typename S>
 MG_HD void rot(const S q[4], S R[3][3]) {
+  // Products with the doubled components: each off-diagonal entry is one sum
+  // and each diagonal entry two fused multiply-adds.
   const S w = q[0], x = q[1], y = q[2], z = q[3];
-  const S two = S(2.0f), one = S(1.0f);
-  R[0][0] = one - two * (y * y + z * z);
-  R[0][1] = two * (x * y - w * z);
-  R[0][2] = two * (x * z + w * y);
-  R[1][0] = two * (x * y + w * z);
-  R[1][1] = one - two * (x * x + z * z);
-  R[1][2] = two * (y * z - w * x);
-  R[2][0] = two * (x * z - w * y);
-  R[2][1] = two * (y * z + w * x);
-  R[2][2] = one - two * (x * x + y * y);
+  const S one = S(1.0f);
+  const S x2 = x + x, y2 = y + y, z2 = z + z;
+  const S xy = x * y2, xz = x * z2, yz = y * z2, wx = w * x2, wy = w * y2, wz = w * z2;
+  R[0][0] = one - y * y2 - z * z2;
+  R[0][1] = xy - wz;
+  R[0][2] = xz + wy;
+  R[1][0] = xy + wz;
+  R[1][1] = one - x * x2 - z * z2;
+  R[1][2] = yz - wx;
+  R[2][0] = xz - wy;
+  R[2][1] = yz + wx;
+  R[2][2] = one - x * x2 - y * y2;
 }
 
 // Actuator-table access: row k of the allocation matrix, and the thrust
@@ -296,8 +300,7 @@ MG_HD void body_rhs(const S R[3][3], const S v[3], const S w[3], const S vc[3], 
   // a4. With a payload (PhysT::kFull) the body origin is not the CoG: with the
   // first moment s = m' r_g and the inertia I_o about the origin,
   // C_RB(nu) nu = [m' w x v + w x (w x s) ; w x (I_o w) + s x (w x v)].
-  S wxv[3], Iw[3], wxIw[3];
-  cross3(w, v, wxv);
+  S Iw[3];
   if constexpr (PhysT::kFull) {
     Iw[0] = S(P.Io[0]) * w[0] + S(P.Io[1]) * w[1] + S(P.Io[2]) * w[2];
     Iw[1] = S(P.Io[1]) * w[0] + S(P.Io[3]) * w[1] + S(P.Io[4]) * w[2];
@@ -305,14 +308,19 @@ MG_HD void body_rhs(const S R[3][3], const S v[3], const S w[3], const S vc[3], 
   } else {
     Iw[0] = S(P.Ig[0]) * w[0]; Iw[1] = S(P.Ig[1]) * w[1]; Iw[2] = S(P.Ig[2]) * w[2];
   }
-  cross3(w, Iw, wxIw);
-  // a5
-  S a1[3], a2[3], wxa1[3], vrxa1[3], wxa2[3], wxvc[3];
+  // a5: a1 = A_lin v_r, a2 = A_ang w. The terms with w on the left share one
+  // cross product each: m w x v + w x a1 = w x (m v + a1) (linear) and
+  // w x (I w) + w x a2 = w x (I w + a2) (angular); v_r x a1 stays apart.
+  S a1[3], bl[3], ba[3], wxbl[3], wxba[3], vrxa1[3], wxvc[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) { a1[j] = S(P.A[j]) * vr[j]; a2[j] = S(P.A[3 + j]) * w[j]; }
-  cross3(w, a1, wxa1);
+  for (int j = 0; j < 3; ++j) {
+    a1[j] = S(P.A[j]) * vr[j];
+    bl[j] = S(P.m) * v[j] + a1[j];
+    ba[j] = S(P.A[3 + j]) * w[j] + Iw[j];
+  }
+  cross3(w, bl, wxbl);
+  cross3(w, ba, wxba);
   cross3(vr, a1, vrxa1);
-  cross3(w, a2, wxa2);
   if (CURRENT) {
     cross3(w, vc, wxvc);
   } else {
@@ -337,7 +345,8 @@ MG_HD void body_rhs(const S R[3][3], const S v[3], const S w[3], const S vc[3], 
     const S wpm = Pw / S(P.m);
 #pragma unroll
     for (int j = 0; j < 3; ++j) Brb[j] = Brb[j] - wpm * sv[j];
-    S wxs[3], wxwxs[3], sxwxv[3];
+    S wxv[3], wxs[3], wxwxs[3], sxwxv[3];
+    cross3(w, v, wxv);
     cross3(w, sv, wxs);
     cross3(w, wxs, wxwxs);
     cross3(sv, wxv, sxwxv);
@@ -347,9 +356,9 @@ MG_HD void body_rhs(const S R[3][3], const S v[3], const S w[3], const S vc[3], 
   cross3(Brb, e, mb);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    rhs[j] = CURRENT ? tau[j] - S(P.m) * wxv[j] - wxa1[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j]
-                     : tau[j] - S(P.m) * wxv[j] - wxa1[j] - dmp[j] + WmB * e[j];
-    rhs[3 + j] = tau[3 + j] - wxIw[j] - vrxa1[j] - wxa2[j] - dmp[3 + j] - mb[j];
+    rhs[j] = CURRENT ? tau[j] - wxbl[j] - S(P.A[j]) * wxvc[j] - dmp[j] + WmB * e[j]
+                     : tau[j] - wxbl[j] - dmp[j] + WmB * e[j];
+    rhs[3 + j] = tau[3 + j] - wxba[j] - vrxa1[j] - dmp[3 + j] - mb[j];
     if constexpr (PhysT::kFull) {
       rhs[j] = rhs[j] - extra_lin[j];
       rhs[3 + j] = rhs[3 + j] - extra_ang[j];
