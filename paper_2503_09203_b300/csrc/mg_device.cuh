@@ -416,11 +416,19 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
   S vc[3], vr[3];
   rel_velocity<S, PhysT, CURRENT>(R, v, P, vc, vr);
   if constexpr (GEN) fin_wrench<S, NT>(G, x.n, vr, w, tau);
-  S rhs[6], nd[6];
+  S rhs[6];
   body_rhs<S, PhysT, CURRENT>(R, v, w, vc, vr, tau, P, rhs);
-  apply_minv<S>(P, rhs, nd);
+  if constexpr (PhysT::kFull) {
+    S nd[6];
+    apply_minv<S>(P, rhs, nd);
 #pragma unroll
-  for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
+    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
+  } else {
+    // Diagonal M^-1: nu += (h M^-1_jj) rhs_j; h M^-1 is the same for every
+    // substep of the step loop, so the compiler can keep it in registers.
+#pragma unroll
+    for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + (h * S(P.minv[j])) * rhs[j];
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     x.p[i] = x.p[i] + h * (R[i][0] * x.nu[0] + R[i][1] * x.nu[1] + R[i][2] * x.nu[2]);
