@@ -804,8 +804,10 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
       kp[3] = tg.w + (float)a.n_steps;
     }
     // Non-finite state check. The last step's reward -|d|^2 - 0.1|nu|^2 -
-    // 0.01|c|^2 (c clamped, finite) is a sum of non-positive terms, so it is
-    // finite exactly when p and nu are: lean kernels add only q and n to it.
+    // 0.01|c|^2 is a sum of non-positive terms (no inf - inf), so it is finite
+    // exactly when p, nu and c are; c is clamped to [-1, 1], so only a NaN
+    // command is non-finite, and it makes n NaN as well. Lean kernels
+    // therefore add only q and n to it.
     float s = LEAN ? r_last : 0.0f;
     if constexpr (!LEAN) {
 #pragma unroll
