@@ -550,8 +550,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint workload (8k envs, T=200, K=4) and print its line (profiling)")
+    ap.add_argument("--hetero-only", action="store_true",
+                    help="run only the heterogeneous CUDA-graph workload (16k envs, 5 classes, K=4, 100 steps) "
+                         "and print its line (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.hetero_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"hetero_graph": hetero_graph_bench(torch.cuda.current_stream())}))
+        return
     if args.adjoint_only:
         import torch
         torch.cuda.set_device(0)

@@ -93,7 +93,7 @@ struct mg_sim {
     std::vector<Group> groups;     // the launches of a step
     bool first_pdl = false;        // the first launch is a programmatic dependent too
     std::vector<ClassK> kc;        // constants of each launch with cls >= 0
-  } plan;
+  } plan, plan_ms;                 // single-step launches; multi-step launches
   std::vector<ClassF> h_cls;       // host copies of the class tables
   std::vector<ClassG> h_gen;
   // mg_step_host: copy streams and events of the chunked pipeline.
@@ -267,6 +267,7 @@ static void build_segs(mg_sim* sim) {
   sim->segs.clear();
   sim->groups.clear();
   sim->plan.valid = false;
+  sim->plan_ms.valid = false;
   int tiles = 0;
   for (int var = 0; var < 3; ++var)
   for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
@@ -562,7 +563,7 @@ int mg_destroy(mg_sim* sim) {
   return MG_OK;
 }
 
-static const mg_sim::Plan& step_plan(mg_sim* sim);
+static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms = false);
 
 int mg_get_layout(const mg_sim* sim, mg_layout* out) {
   if (!sim || !out) return MG_ERR_INVALID_ARG;
@@ -742,16 +743,22 @@ static bool carveout_max(const mg_sim* sim, const Group& g, bool shared_sm) {
 // tables in shared memory: their grids are split by estimated work, which a
 // faster one-class kernel unbalances (262k envs: 23.1 -> 23.6 us), and five
 // launches instead of three cost 4 us at 65k envs.
-static const mg_sim::Plan& step_plan(mg_sim* sim) {
-  mg_sim::Plan& p = sim->plan;
+static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
+  mg_sim::Plan& p = ms ? sim->plan_ms : sim->plan;
   if (p.valid && p.bps == sim->blocks_per_sm) return p;
   p.cores = coresident_grids(sim, p.grid);
-  int64_t blocks = 0;
+  int64_t blocks = 0, tiles = 0;
   for (int b : p.grid) blocks += b;
+  for (const Group& g : sim->groups) tiles += g.n_tiles;
+  // Multi-step launches whose tiles all fit one wave (one tile per block) are
+  // latency bound: every step is a chain of dependent arithmetic per warp, and
+  // class tables read as constant-bank operands instead of shared-memory loads
+  // shorten it. They too take one launch per class.
+  const bool one_wave = p.cores && blocks == tiles;
+  const bool split = MG_CLASS_PARAMS && (!p.cores || (ms && one_wave));
   const bool shared_sm = p.cores && blocks > sim->num_sms;
   p.groups.clear();
   for (const Group& g : sim->groups) {
-    const bool split = !p.cores && MG_CLASS_PARAMS;
     if (!split) { p.groups.push_back(g); continue; }
     for (int s = g.seg_lo; s < g.seg_hi; ++s) {   // a segment holds envs of one class
       Group h = g;
@@ -764,7 +771,7 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
     }
   }
   const size_t n = p.groups.size();
-  if (!p.cores) p.grid.assign(n, 1);
+  if (!p.cores || split) p.grid.assign(n, 1);
   p.carve_max.assign(n, 0);
   p.full_grid.assign(n, 1);
   p.kc.assign(n, ClassK());
@@ -773,6 +780,7 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
     if (g.cls >= 0) p.kc[i] = class_k(sim, g);
     p.full_grid[i] = grid_of(sim, g);
     if (!p.cores) p.grid[i] = p.full_grid[i];
+    else if (split) p.grid[i] = g.n_tiles;   // one wave: a block per tile
     p.carve_max[i] = carveout_max(sim, g, shared_sm) ? 1 : 0;
   }
   // Measured: a programmatic first launch helps side-by-side steps and
@@ -788,8 +796,13 @@ static const mg_sim::Plan& step_plan(mg_sim* sim) {
   return p;
 }
 
+// Launches of at least this many steps use the multi-step plan.
+#ifndef MG_SPLIT_MIN_STEPS
+#define MG_SPLIT_MIN_STEPS 8
+#endif
+
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
-  const mg_sim::Plan& p = step_plan(sim);
+  const mg_sim::Plan& p = step_plan(sim, a.n_steps >= MG_SPLIT_MIN_STEPS);
   bool first = true;
   for (size_t i = 0; i < p.groups.size(); ++i) {
     const Group& g = p.groups[i];
