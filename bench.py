@@ -49,18 +49,41 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name="step_kernel_full_hover_1M_K4.md"):
-    """DRAM bytes per step from the committed ncu summary, if it measured these sources."""
-    p = os.path.join(ROOT, "profiles", name)
-    if not os.path.exists(p):
-        return None
-    sha = traffic = None
-    for line in open(p):
-        if line.startswith("source_sha:"):
-            sha = line.split(":", 1)[1].strip()
-        if line.startswith("traffic_bytes_per_step:"):
-            traffic = float(line.split(":", 1)[1])
-    return traffic if sha == kernel_sha() else None
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "step_kernel_dram_hover_1M_K4.json")
+
+
+def profiled_traffic(E, K):
+    """DRAM bytes (read + write) per step of the workload, from the committed
+    machine-readable ncu record, if it measured these kernel sources at this
+    workload; else None. Returns (bytes per step, record)."""
+    if not os.path.exists(TRAFFIC_RECORD):
+        return None, None
+    rec = json.load(open(TRAFFIC_RECORD))
+    if rec.get("source_sha") != kernel_sha() or rec.get("envs") != E or rec.get("K") != K:
+        return None, rec
+    return float(rec["dram_bytes_per_step"]), rec
+
+
+def num_sms() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def fp32_peak(pk) -> float:
+    """FP32 FLOP/s of this device: 2 (FMA) x 128 FP32 lanes per SM x SMs x the
+    maximum SM clock."""
+    return 2 * 128 * num_sms() * pk["sm_max_mhz"] * 1e6
+
+
+def spin(seconds: float):
+    """Keep this thread busy for `seconds` (no sleep): a host thread that
+    sleeps comes back with its launch path several times slower for tens of
+    milliseconds, which a short timed region would measure."""
+    t0 = time.perf_counter()
+    x = 0
+    while time.perf_counter() - t0 < seconds:
+        x += 1
+    return x
 
 
 def dist_max(x: float, device="cuda") -> float:
@@ -277,7 +300,7 @@ def sweep(pk, stream, sizes=(65536, 131072, 262144, 524288, 1048576), Ks=(1, 4, 
             t = time_steps(sim, acts, steps, 10, stream)
             bpe, fpe = algorithmic(classes, counts, K)
             v = E * steps / t
-            alu_peak = 2 * 128 * 148 * pk["sm_max_mhz"] * 1e6
+            alu_peak = fp32_peak(pk)
             out.append({"envs": E, "K": K, "env_steps_per_s": v, "us_per_step": t / steps * 1e6,
                         "hbm_frac": v * bpe / (pk["hbm_gbs"] * 1e9), "alu_frac": v * fpe / alu_peak,
                         "l2_resident": E * bpe < 126e6})
@@ -454,7 +477,7 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):
            "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb,
            "fp32_tflops": (f_fwd + f_bwd) / (tf + tb) / 1e12}
     if pk:
-        out["alu_frac"] = out["fp32_tflops"] * 1e12 / (2 * 128 * 148 * pk["sm_max_mhz"] * 1e6)
+        out["alu_frac"] = out["fp32_tflops"] * 1e12 / fp32_peak(pk)
         out["roofline_note"] = "FP32-issue and latency bound (256 warps at 8192 envs); FMA = 2"
     return out
 
@@ -498,7 +521,7 @@ def serving_bench(plain_rate, n_req=10000, load=0.7, seed=11, horizon_max=1000, 
     roof = {"flops_per_env_step": float(np.sum(w * flops) / np.sum(w)),
             "bytes_per_env_step": float(np.sum(w * nbytes) / np.sum(w))}
     if pk:
-        roof["busy_alu_frac"] = busy * roof["flops_per_env_step"] / (2 * 128 * 148 * pk["sm_max_mhz"] * 1e6)
+        roof["busy_alu_frac"] = busy * roof["flops_per_env_step"] / fp32_peak(pk)
         roof["busy_hbm_frac"] = busy * roof["bytes_per_env_step"] / (pk["hbm_gbs"] * 1e9)
     return {"requests": n_req, "offered_load": load, "arrival_rate_per_s": lam, "wall_s": wall,
             "env_steps_per_s": st["env_steps"] / wall, "busy_env_steps_per_s": st["env_steps"] / max(st["busy_seconds"], 1e-9),
@@ -550,6 +573,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint workload (8k envs, T=200, K=4) and print its line (profiling)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="after the warm-up, run --steps steps of the headline workload between "
+                         "cudaProfilerStart/Stop and exit (for an ncu range replay of DRAM traffic)")
     ap.add_argument("--hetero-only", action="store_true",
                     help="run only the heterogeneous CUDA-graph workload (16k envs, 5 classes, K=4, 100 steps) "
                          "and print its line (profiling)")
@@ -605,11 +631,23 @@ def main():
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
-        time.sleep(0.5)
+    spin(0.5)   # the sampler starts; the host thread stays busy (see spin)
     # Warm-up, then exactly `steps` timed steps between barriers.
     for i in range(args.warmup):
         B.mg_step(sim.handle, acts[i % 8], 1, sim.obs, sim.reward, stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        clocks.stop()
+        torch.cuda.profiler.start()
+        for i in range(args.steps):
+            B.mg_step(sim.handle, acts[i % 8], 1, sim.obs, sim.reward, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        B.mg_status(sim.handle, stream)
+        print(json.dumps({"profile_range": {"envs": E, "K": K, "steps": args.steps,
+                                            "launches": args.steps * n_launches, "source_sha": kernel_sha()}}))
+        sim.close()
+        return
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -630,6 +668,17 @@ def main():
         clocks.stop()
     B.mg_status(sim.handle, stream)
     value = whole_job_rate(E, world, args.steps, t)
+    # Per-step device times of the same steps run again with an event after
+    # each one (kept out of the timed region: an event between two steps ends
+    # the programmatic overlap of their launches, about 3 us a step).
+    n_ev = min(args.steps, 100)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev + 1)]
+    ev[0].record(stream)
+    for i in range(n_ev):
+        B.mg_step(sim.handle, acts[i % 8], 1, sim.obs, sim.reward, stream)
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    step_us = [round(ev[i].elapsed_time(ev[i + 1]) * 1e3, 2) for i in range(n_ev)]
 
     # End to end through the host-buffer entry point (pinned buffers).
     a_host = acts[0].cpu().pin_memory()
@@ -658,7 +707,7 @@ def main():
 
     per_step = t / args.steps
     achieved_gbs = E * bpe / per_step / 1e9
-    alu_peak = 2 * 128 * 148 * pk["sm_max_mhz"] * 1e6
+    alu_peak = fp32_peak(pk)
     achieved_flops = E * fpe / per_step
     t_mem, t_alu = E * bpe / (pk["hbm_gbs"] * 1e9), E * fpe / alu_peak
     if t_mem >= t_alu:
@@ -668,12 +717,12 @@ def main():
     else:
         roof = {"bound": "alu", "achieved": achieved_flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved_flops / alu_peak, "traffic": None,
-                "peak_src": "2 x 128 FP32 lanes x 148 SMs x max SM clock"}
-    traffic = profiled_traffic() if (E == 1 << 20 and K == 4) else None
+                "peak_src": f"2 x 128 FP32 lanes x {num_sms()} SMs x max SM clock"}
+    traffic, trec = profiled_traffic(E, K)
     roof["traffic"] = traffic
-    roof["traffic_note"] = (f"DRAM read+write bytes per step ({n_launches} launches) from profiles/step_kernel_full_hover_1M_K4.md "
-                            "(ncu serialised replay: reads = algorithmic, writes partly deferred in L2)"
-                            if traffic else "null: no ncu capture of these kernel sources at this workload")
+    roof["traffic_note"] = (f"DRAM read+write bytes per step from an ncu range replay of {trec['steps']} consecutive "
+                            f"steps ({trec['launches']} launches, write-backs included): {os.path.relpath(TRAFFIC_RECORD, ROOT)}"
+                            if traffic else "null: no ncu record of these kernel sources at this workload")
     roof.update({"kernel": f"mg_step_kernel<NT, 0, 0, 1, 0, 0> (class constants, propellers, Euler, class tables as the kernel parameter), {n_launches} launches per step",
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
                  "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
@@ -682,6 +731,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": bench_config(E, K, world),
             "e2e": e2e, "gpu_launches": args.steps * n_launches, "roofline": roof,
+            "step_us": {"per_step": step_us, "median": float(np.median(step_us)),
+                        "note": "a second pass of the timed steps with an event after each step"},
             "clocks": clocks.summary(tw0, tw1)}
     if world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(E, K)

@@ -34,7 +34,12 @@
  * (observations, rewards) are indexed by *slot*: each class's first slot is a
  * multiple of 4, so class c occupies slots [slot_offset_c, slot_offset_c +
  * n_c) and up to 3 padding slots may follow it. mg_get_layout() reports all
- * offsets.
+ * offsets. Grouping by class lets one kernel instantiation (one thruster
+ * count, one class table) walk contiguous, 16-byte aligned SoA planes; a
+ * caller whose environments carry an arbitrary class map env_class[i] gets
+ * the library's order from mg_env_order() (a stable sort by class: library
+ * env index lib_env[i] of its env i) and passes the resulting class_counts to
+ * mg_create.
  */
 #ifndef MARINEGYM_H
 #define MARINEGYM_H
@@ -264,8 +269,23 @@ int mg_set_task(mg_sim* sim, const double* host, size_t bytes);
 int mg_get_payload(const mg_sim* sim, double* host, size_t bytes);
 int mg_set_payload(mg_sim* sim, const double* host, size_t bytes);
 
-/* Observation of the current state (no step): obs_dev [n_slots][13]. */
-int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream);
+/* Observation of the current state (no step): obs_dev [n_slots][13] and
+ * reward_dev [n_slots] (either may be NULL, not both). The reward is the hover
+ * reward of the current state without a command term:
+ * r = -|p - p*|^2 - 0.1 |nu|^2 (Sec. IV-B station keeping; the command term of
+ * mg_step's reward belongs to the step that applied it). */
+int mg_observe(mg_sim* sim, float* obs_dev, float* reward_dev, mg_stream_t stream);
+
+/* Library order of an arbitrary env -> class map (no device work, no
+ * simulator needed): class_counts [n_classes] receives the number of envs of
+ * each class (the mg_config.class_counts to create the simulator with) and
+ * lib_env [n_envs] the library env index of env i (envs sorted by class,
+ * stable: envs of one class keep their order). Per-env data of env i lives at
+ * library env lib_env[i] (slot: that env's class slot_offset + its index
+ * within the class). Errors: INVALID_ARG (a class outside [0, n_classes), null
+ * buffers); the message is read with mg_last_error(NULL). */
+int mg_env_order(const int32_t* env_class, int32_t n_envs, int32_t n_classes, int32_t* class_counts,
+                 int32_t* lib_env);
 
 /* Host-buffer variant of mg_step for callers without device memory: copies
  * actions (host, as for mg_step) in, steps, copies obs/reward (host, may be
@@ -281,13 +301,21 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
 /* Reverse-mode gradient of the last recorded mg_rollout (discretise-then-
  * differentiate: the exact adjoint of the discrete map, including the clamp,
  * rotor lag, quaternion renormalisation, and M^-1 = (M_RB + M_A)^-1 through
- * the added mass). Inputs: the same actions_dev, cotangents g_obs
- * [T][n_slots][13] and g_rew [T][n_slots] (either may be NULL = 0) and
- * g_state_T [n_slots][21] on the final state (NULL = 0). Outputs (each may be
- * NULL): g_actions [T][action_floats], g_added_mass [n_slots][6],
- * g_damping [n_slots][12] (6 linear then 6 quadratic), g_state0
- * [n_slots][21]. Segments between checkpoints are recomputed into
- * library-owned scratch. Errors: STATE if nothing was recorded. */
+ * the added mass). Inputs: the same actions_dev (the library keeps no copy of
+ * the caller's actions; the segments between checkpoints are recomputed from
+ * them), cotangents g_obs [T][n_slots][13] and g_rew [T][n_slots] (either may
+ * be NULL = 0) and g_state_T [n_slots][21] on the final state (NULL = 0).
+ * Outputs (each may be NULL): g_actions [T][action_floats], g_added_mass
+ * [n_slots][6], g_damping [n_slots][12] (6 linear then 6 quadratic),
+ * g_state0 [n_slots][21] (the cotangent of the rollout's initial state, so
+ * that a long rollout cut into recorded pieces chains its gradients through
+ * g_state_T of the previous piece). Segments between checkpoints are
+ * recomputed into library-owned scratch.
+ * A recording stays valid only until the simulator changes: mg_step,
+ * mg_rollout, mg_step_host, mg_reset, mg_set_state, mg_set_params,
+ * mg_set_hydro, mg_set_task, mg_set_payload, mg_autotune, mg_graph_capture
+ * and mg_graph_launch of a graph of this simulator all discard it.
+ * Errors: STATE if nothing is recorded (never recorded, or discarded). */
 int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
                      const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
                      float* g_state0, mg_stream_t stream);
@@ -307,11 +335,20 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
  * needs clearing between calls; the array keeps the last call's contents.
  * All calls share the one array: calls that overlap on the GPU (for example on
  * two streams) race. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture. */
+ * address (cudaGetSymbolAddress) and caches it with the current context; make
+ * that first call before any stream capture. A call in a new context of the
+ * device (after cudaDeviceReset) looks the address up again, so it too should
+ * come before any capture. Also a backward pass: the recording rules of
+ * mg_step_backward apply. */
 int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
                              const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
                              float* g_state0, mg_stream_t stream);
+
+/* The current recording: *steps = its length T (0: none) and *id = a
+ * process-unique identity (0: none), which changes with every new recording.
+ * A caller that keeps a recording across other work (an autograd graph)
+ * stores the id and checks it before mg_step_backward. Either may be NULL. */
+int mg_recording(const mg_sim* sim, int32_t* steps, uint64_t* id);
 
 /* Overwrite the added-mass (A [n_slots][6]), linear damping (dl) and quadratic
  * damping (dq) of every env from device arrays (each may be NULL = keep) and
@@ -427,6 +464,11 @@ typedef struct {
   double step_latency_p50, step_latency_p99;   /* s, per request step (tick completion spacing) */
   double queue_delay_p50, queue_delay_p99;     /* s, submit -> admit */
   double tick_p50, tick_p99;                   /* s, device time of one shared launch */
+  size_t budget_bytes;          /* the arena budget the server was created with */
+  size_t peak_resident_bytes;   /* most device bytes ever held by admitted requests at once
+                                   (their slot planes, returns and states); <= budget_bytes */
+  int32_t peak_requests;        /* most requests ever holding arena space at once */
+  int32_t pad0;
 } mg_server_stats;
 
 /* Errors of mg_server_create: INVALID_ARG (bad config, a class that is not

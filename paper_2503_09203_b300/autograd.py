@@ -6,6 +6,12 @@ simulator's current state and returns per-step observations and rewards.
 Backward calls mg_step_backward, the hand-written adjoint of the discrete map
 (checkpoints every `ckpt_every` steps, segments recomputed on the GPU), and
 returns gradients for the actions, the added mass and the damping.
+
+The checkpoints live in the simulator, which holds one recording at a time.
+Forward keeps the identity of the recording it made; backward refuses (raises)
+when the simulator no longer holds that recording, for example after a second
+forward on the same simulator, a step, a reset or a parameter change, instead
+of differentiating another rollout.
 """
 from __future__ import annotations
 
@@ -25,6 +31,7 @@ class RolloutFn(torch.autograd.Function):
         rew = torch.zeros(T, sim.n_slots, device=actions.device)
         B.mg_rollout(sim.handle, actions, T, obs, rew, True, stream)
         ctx.sim = sim
+        ctx.rec_id = B.mg_recording(sim.handle)[1]
         ctx.save_for_backward(actions)
         return obs, rew
 
@@ -32,6 +39,11 @@ class RolloutFn(torch.autograd.Function):
     def backward(ctx, g_obs, g_rew):
         (actions,) = ctx.saved_tensors
         sim = ctx.sim
+        steps, rec_id = B.mg_recording(sim.handle)
+        if rec_id != ctx.rec_id:
+            raise RuntimeError("marinegym rollout backward: the simulator no longer holds this forward's "
+                               "recording (a later forward, step, reset or parameter change replaced or "
+                               "discarded it); run backward before reusing the simulator")
         T = actions.shape[0]
         stream = torch.cuda.current_stream()
         g_act = torch.zeros_like(actions)

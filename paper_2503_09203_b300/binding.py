@@ -112,7 +112,9 @@ class mg_server_stats(C.Structure):
     _fields_ = [("requests_done", C.c_int64), ("env_steps", C.c_int64), ("ticks", C.c_int64),
                 ("busy_seconds", C.c_double), ("step_latency_p50", C.c_double),
                 ("step_latency_p99", C.c_double), ("queue_delay_p50", C.c_double),
-                ("queue_delay_p99", C.c_double), ("tick_p50", C.c_double), ("tick_p99", C.c_double)]
+                ("queue_delay_p99", C.c_double), ("tick_p50", C.c_double), ("tick_p99", C.c_double),
+                ("budget_bytes", C.c_size_t), ("peak_resident_bytes", C.c_size_t), ("peak_requests", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 _VP, _I32, _I64, _U64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
@@ -123,7 +125,9 @@ _SIGS = {
     "mg_reset": [_VP, _VP, _I32, _U64, _VP],
     "mg_step": [_VP, _VP, _I32, _VP, _VP, _VP],
     "mg_rollout": [_VP, _VP, _I32, _VP, _VP, _I32, _VP],
-    "mg_observe": [_VP, _VP, _VP],
+    "mg_observe": [_VP, _VP, _VP, _VP],
+    "mg_recording": [_VP, C.POINTER(_I32), C.POINTER(_U64)],
+    "mg_env_order": [_VP, _I32, _I32, _VP, _VP],
     "mg_step_host": [_VP, _VP, _I32, _VP, _VP, _VP],
     "mg_step_backward": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "mg_step_backward_noalloc": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -291,8 +295,25 @@ def mg_rollout(sim, actions, n_steps: int, obs=None, reward=None, record: bool =
                                    _stream(stream)), sim)
 
 
-def mg_observe(sim, obs, stream=None):
-    return _check(lib().mg_observe(sim, _ptr(obs), _stream(stream)), sim)
+def mg_observe(sim, obs=None, reward=None, stream=None):
+    return _check(lib().mg_observe(sim, _ptr(obs), _ptr(reward), _stream(stream)), sim)
+
+
+def mg_recording(sim):
+    """(steps, id) of the simulator's current recording ((0, 0): none)."""
+    n, i = _I32(), _U64()
+    _check(lib().mg_recording(sim, C.byref(n), C.byref(i)), sim)
+    return n.value, i.value
+
+
+def mg_env_order(env_class, n_classes: int):
+    """Library order of an env -> class map: (class_counts [n_classes],
+    lib_env [n_envs]) with lib_env[i] the library env index of env i."""
+    ec = np.ascontiguousarray(env_class, dtype=np.int32)
+    counts = np.zeros(int(n_classes), np.int32)
+    lib_env = np.zeros(len(ec), np.int32)
+    _check(lib().mg_env_order(ec.ctypes.data, len(ec), int(n_classes), counts.ctypes.data, lib_env.ctypes.data))
+    return counts, lib_env
 
 
 def mg_step_host(sim, actions_host, n_steps: int = 1, obs_host=None, reward_host=None, stream=None):
@@ -531,7 +552,7 @@ class Sim:
         mg_rollout(self.handle, actions, n_steps, obs, reward, record, stream)
 
     def observe(self, stream=None):
-        mg_observe(self.handle, self.obs, stream)
+        mg_observe(self.handle, self.obs, self.reward, stream)
         return self.obs
 
     def get_state(self):

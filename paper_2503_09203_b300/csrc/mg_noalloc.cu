@@ -23,25 +23,53 @@ static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-float* g_ptr[kMaxDevices] = {};
+struct Cached {
+  void* ctx = nullptr;   // context the address belongs to
+  float* ptr = nullptr;
+};
+Cached g_cache[kMaxDevices];
+
+// The current driver context (null if it cannot be read). Reached through the
+// runtime's driver entry point, so the library does not link the driver
+// library directly (it still loads on machines without a GPU driver).
+void* current_context() {
+  using Fn = int (*)(void**);
+  static Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<Fn>(f);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 }  // namespace
 
 // Device address of the scratch array on the current device. In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// with the device current and cached together with the context it belongs
+// to; a new context on the same device (after cudaDeviceReset, or after the
+// primary context was released and created again, which reloads the module)
+// makes the next call look it up again.
 cudaError_t noalloc_scratch(float** ptr, size_t* capacity_floats) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
+  void* ctx = current_context();
+  Cached& c = g_cache[dev];
+  if (!c.ptr || !ctx || ctx != c.ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_ptr[dev] = static_cast<float*>(p);
+    c.ptr = static_cast<float*>(p);
+    c.ctx = current_context();   // the lookup may have made the primary context current
   }
-  *ptr = g_ptr[dev];
+  *ptr = c.ptr;
   *capacity_floats = kNoAllocScratchFloats;
   return cudaSuccess;
 }

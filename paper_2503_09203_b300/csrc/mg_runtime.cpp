@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,6 +80,7 @@ struct mg_sim {
   size_t stage_floats = 0;
   int32_t ckpt_every = 20;
   int32_t rec_T = 0;           // steps of the last recorded rollout (0: none)
+  uint64_t rec_id = 0;         // identity of that recording (0: none)
   size_t bytes = 0;
   std::string err;
   // Launch plan of a step (grids, launch shape, carveouts), computed once per
@@ -104,7 +106,20 @@ struct mg_sim {
 struct mg_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  mg_sim* sim = nullptr;        // a replay advances this simulator's envs
 };
+
+// Recordings for mg_step_backward. A recording is valid only while the
+// simulator still holds what produced it: every call that changes the state,
+// the per-env parameters, the task or the payload (or runs a step, a reset or
+// a graph replay) discards it, so that a backward pass never differentiates
+// old checkpoints with new parameters. Each recording gets a process-unique
+// identity that callers (the autograd wrapper) keep to detect a newer one.
+static std::atomic<uint64_t> g_next_rec_id{1};
+static void drop_recording(mg_sim* sim) {
+  sim->rec_T = 0;
+  sim->rec_id = 0;
+}
 
 static int fail(mg_sim* s, int code, const char* fmt, ...) {
   if (s) {
@@ -590,7 +605,7 @@ int mg_reset(mg_sim* sim, const int32_t* env_ids_dev, int32_t n, uint64_t seed, 
   a.env_ids = env_ids_dev;
   a.n_sel = env_ids_dev ? n : sim->n_envs;
   CK(launch_reset(a, (cudaStream_t)stream));
-  sim->rec_T = 0;
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -838,9 +853,8 @@ int mg_step(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_d
   a.obs = obs_dev;
   a.reward = reward_dev;
   a.obs_every = 0;
-  int rc = launch_groups(sim, a, (cudaStream_t)stream);
-  sim->rec_T = 0;
-  return rc;
+  drop_recording(sim);
+  return launch_groups(sim, a, (cudaStream_t)stream);
 }
 
 int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* obs_dev, float* reward_dev,
@@ -858,18 +872,55 @@ int mg_rollout(mg_sim* sim, const float* actions_dev, int32_t n_steps, float* ob
   a.reward = reward_dev;
   a.obs_every = 1;
   a.ckpt = record ? sim->d_ckpt : nullptr;
+  drop_recording(sim);
   int rc = launch_groups(sim, a, (cudaStream_t)stream);
-  sim->rec_T = (record && rc == MG_OK) ? n_steps : 0;
+  if (record && rc == MG_OK) {
+    sim->rec_T = n_steps;
+    sim->rec_id = g_next_rec_id.fetch_add(1);
+  }
   return rc;
 }
 
-int mg_observe(mg_sim* sim, float* obs_dev, mg_stream_t stream) {
-  if (!sim || !obs_dev) return sim ? fail(sim, MG_ERR_INVALID_ARG, "observe: null obs") : MG_ERR_INVALID_ARG;
+int mg_observe(mg_sim* sim, float* obs_dev, float* reward_dev, mg_stream_t stream) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (!obs_dev && !reward_dev) return fail(sim, MG_ERR_INVALID_ARG, "observe: obs and reward are both null");
   if (misaligned(obs_dev)) return fail(sim, MG_ERR_INVALID_ARG, "observe: obs buffer must be 16-byte aligned");
   StepArgs a = step_args(sim);
   a.n_steps = 0;
   a.obs = obs_dev;
+  a.reward = reward_dev;
   return launch_groups(sim, a, (cudaStream_t)stream);
+}
+
+int mg_recording(const mg_sim* sim, int32_t* steps, uint64_t* id) {
+  if (!sim) return MG_ERR_INVALID_ARG;
+  if (steps) *steps = sim->rec_T;
+  if (id) *id = sim->rec_id;
+  return MG_OK;
+}
+
+int mg_env_order(const int32_t* env_class, int32_t n_envs, int32_t n_classes, int32_t* class_counts,
+                 int32_t* lib_env) {
+  if (!env_class || !class_counts || !lib_env || n_envs < 0 || n_classes < 1 || n_classes > MG_MAX_CLASSES) {
+    g_create_err = "env_order: null buffer or bad sizes";
+    return MG_ERR_INVALID_ARG;
+  }
+  std::vector<int64_t> start(n_classes + 1, 0);
+  for (int32_t i = 0; i < n_envs; ++i) {
+    const int32_t c = env_class[i];
+    if (c < 0 || c >= n_classes) {
+      g_create_err = "env_order: env " + std::to_string(i) + " has class " + std::to_string(c) + " outside [0, n_classes)";
+      return MG_ERR_INVALID_ARG;
+    }
+    ++start[c + 1];
+  }
+  for (int c = 0; c < n_classes; ++c) {
+    class_counts[c] = (int32_t)start[c + 1];
+    start[c + 1] += start[c];
+  }
+  // Stable: envs of one class keep their relative order.
+  for (int32_t i = 0; i < n_envs; ++i) lib_env[i] = (int32_t)start[env_class[i]]++;
+  return MG_OK;
 }
 
 // mg_step_host pipeline: the step is cut into chunks of at most this many
@@ -978,7 +1029,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
                            cudaMemcpyDeviceToHost, sim->s_out));
     }
   }
-  sim->rec_T = 0;
+  drop_recording(sim);
   CK(cudaStreamSynchronize(sim->s_out));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
@@ -988,7 +1039,10 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
                      const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
                      float* g_state0, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
-  if (sim->rec_T <= 0) return fail(sim, MG_ERR_STATE, "backward: no recorded rollout (call mg_rollout with record=1)");
+  if (sim->rec_T <= 0)
+    return fail(sim, MG_ERR_STATE,
+                "backward: no recorded rollout (call mg_rollout with record=1; a later step, reset, graph replay "
+                "or state / parameter / task / payload change discards the recording)");
   if (!actions_dev) return fail(sim, MG_ERR_INVALID_ARG, "backward: actions required");
   AdjArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1026,6 +1080,7 @@ int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const flo
   if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "set_hydro needs per_env_params");
   if (sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "set_hydro: not available for payload runs (use mg_set_params)");
   CK(launch_set_hydro(sim->d_planes, sim->n_slots, A_dev, dl_dev, dq_dev, (cudaStream_t)stream));
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -1099,7 +1154,7 @@ int mg_set_state(mg_sim* sim, const float* host, size_t bytes) {
     }
   }
   CK(cudaMemcpy(sim->d_state, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice));
-  sim->rec_T = 0;
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -1205,6 +1260,7 @@ int mg_set_params(mg_sim* sim, const double* host, size_t bytes) {
     }
   }
   CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -1257,6 +1313,7 @@ int mg_set_payload(mg_sim* sim, const double* host, size_t bytes) {
     }
   }
   CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -1318,6 +1375,7 @@ int mg_set_task(mg_sim* sim, const double* host, size_t bytes) {
     }
   }
   CK(cudaMemcpy(sim->d_planes, pl.data(), sizeof(float4) * pl.size(), cudaMemcpyHostToDevice));
+  drop_recording(sim);
   return MG_OK;
 }
 
@@ -1347,6 +1405,7 @@ int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream) {
   int rc = launch_groups(sim, a, st);
   CK(cudaStreamSynchronize(st));
   CK(cudaMemcpy(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice));
+  drop_recording(sim);
   return rc;
 }
 
@@ -1414,7 +1473,7 @@ int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* 
   cudaEventDestroy(e1);
   cudaFree(d_save);
   cudaFree(d_act);
-  sim->rec_T = 0;
+  drop_recording(sim);
   CK(cudaGetLastError());
   if (threads_out) *threads_out = best_t;
   if (bps_out) *bps_out = best_b;
@@ -1441,6 +1500,7 @@ int mg_graph_capture(mg_sim* sim, const float* actions_dev, int32_t n_steps, flo
   if (e != cudaSuccess) return fail(sim, MG_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
   mg_graph* G = new mg_graph();
   G->graph = g;
+  G->sim = sim;
   e = cudaGraphInstantiate(&G->exec, g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -1453,6 +1513,7 @@ int mg_graph_capture(mg_sim* sim, const float* actions_dev, int32_t n_steps, flo
 
 int mg_graph_launch(mg_graph* g, mg_stream_t stream) {
   if (!g) return MG_ERR_INVALID_ARG;
+  if (g->sim) drop_recording(g->sim);
   return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
@@ -1479,7 +1540,10 @@ extern "C" int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, c
                                         float* g_added_mass, float* g_damping, float* g_state0,
                                         mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
-  if (sim->rec_T <= 0) return fail(sim, MG_ERR_STATE, "backward: no recorded rollout (call mg_rollout with record=1)");
+  if (sim->rec_T <= 0)
+    return fail(sim, MG_ERR_STATE,
+                "backward: no recorded rollout (call mg_rollout with record=1; a later step, reset, graph replay "
+                "or state / parameter / task / payload change discards the recording)");
   if (!actions_dev) return fail(sim, MG_ERR_INVALID_ARG, "backward: actions required");
   float* scratch = nullptr;
   size_t cap = 0;

@@ -168,7 +168,13 @@ struct mg_server {
   int64_t tile_cap = 0;
   TickBuf buf[2];                // host side of the two ticks in flight
   int64_t S = 0, state_cap = 0;
+  size_t budget = 0;             // arena budget (bytes)
   RangeAlloc slots, states;
+  // Device bytes held by admitted requests (slot planes, return and state
+  // of their envs), and the most ever held at once: the admission rule keeps
+  // it within the arena, and the statistic lets a caller check that.
+  size_t resident = 0, peak_resident = 0;
+  int32_t held = 0, peak_requests = 0;   // requests holding arena space
   cudaStream_t stream = nullptr;
   // scheduler
   std::thread th;
@@ -201,6 +207,12 @@ static int sfail(mg_server* s, int code, const char* fmt, ...) {
 
 static int64_t state_units(int n_thr, int n4) { return (int64_t)n4 * (13 + n_thr); }
 
+// Device bytes of an admitted request: its slots' parameter planes and return
+// accumulator, and its state planes.
+static size_t request_bytes(const Req& q) {
+  return (size_t)q.n4 * (sizeof(float4) * N_PLANES + sizeof(float)) + sizeof(float) * (size_t)state_units(q.n_thr, q.n4);
+}
+
 // Admit pending requests in FIFO order while they fit; reset their envs.
 static void admit_locked(mg_server* s, std::vector<Req*>& admitted) {
   while (!s->pending.empty() && (int)s->active.size() < s->cfg.max_requests) {
@@ -214,6 +226,9 @@ static void admit_locked(mg_server* s, std::vector<Req*>& admitted) {
     }
     q.slot_off = so;
     q.st_off = st;
+    s->resident += request_bytes(q);
+    s->peak_resident = std::max(s->peak_resident, s->resident);
+    s->peak_requests = std::max(s->peak_requests, ++s->held);
     q.status = MG_REQ_RUNNING;
     q.t_admit = now_s();
     s->qdel.push_back({q.t_admit - q.t_submit, 1.0});
@@ -254,6 +269,8 @@ static Tick prepare_tick(mg_server* s, const Tick& prev, int par) {
   for (Req* q : prev.done) {
     s->slots.release(q->slot_off, q->n4);
     s->states.release(q->st_off, state_units(q->n_thr, q->n4));
+    s->resident -= request_bytes(*q);
+    --s->held;
   }
   if (s->stop || s->fatal != MG_OK) return t;
   admit_locked(s, t.fresh);
@@ -534,6 +551,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   if (S < 4) { delete s; return MG_ERR_OOM; }
   s->S = S;
   s->state_cap = S * 21;
+  s->budget = budget;
   const size_t bytes = sizeof(float4) * N_PLANES * S + sizeof(float) * S + sizeof(float) * s->state_cap;
   auto cleanup = [&](int code) {
     if (s->arena) cudaFree(s->arena);
@@ -687,6 +705,9 @@ int mg_server_stats_get(mg_server* s, mg_server_stats* out) {
   out->queue_delay_p99 = wquantile(s->qdel, 0.99);
   out->tick_p50 = wquantile(s->tick, 0.50);
   out->tick_p99 = wquantile(s->tick, 0.99);
+  out->budget_bytes = s->budget;
+  out->peak_resident_bytes = s->peak_resident;
+  out->peak_requests = s->peak_requests;
   return MG_OK;
 }
 

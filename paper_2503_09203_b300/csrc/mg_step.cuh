@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "marinegym.h"
@@ -1045,48 +1046,55 @@ static const void* step_fn() {
 }
 
 // Kernel attributes of a step instantiation: the largest dynamic shared
-// memory of its layouts (tracking).
+// memory of its layouts (tracking). A function attribute belongs to the
+// function on each device, so it is set once per instantiation and device
+// (bit d of `done`; devices beyond 63 set it on every launch); concurrent
+// callers may both set it, which is harmless.
 template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>
 static cudaError_t step_attrs() {
-  static bool done = false;   // per instantiation, per process (one device)
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM, MS>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem<NT, PM>(true));
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
-// Shared-memory carveout of the next launch of an instantiation: the largest
-// (`shared_sm`) or the driver's default; set only when it changes.
-template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>
-static cudaError_t step_carveout(bool shared_sm) {
-  static int current = -2;   // per instantiation, per process (one device)
-  const int want = shared_sm ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault;
-  if (want == current) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM, MS>(), cudaFuncAttributePreferredSharedMemoryCarveout, want);
-  if (e == cudaSuccess) current = want;
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM, MS>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_smem<NT, PM>(true));
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
 
 // `dependent`: launch as a programmatic dependent of the previous kernel in
 // the stream (the previous launch of the same step, on disjoint envs).
+// `shared_sm`: the largest shared-memory carveout for this launch, else the
+// driver's default preference; a launch attribute, so launches of the same kernel with
+// different carveouts (two simulators, two devices, two threads) never
+// rewrite a shared function attribute.
 template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>
 static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, const ClassG* kg, int grid, bool dependent,
                                  bool shared_sm, cudaStream_t st) {
   const size_t smem = step_smem<NT, PM>(a.track != 0);
   cudaError_t e = step_attrs<NT, PM, VAR, KP, TM, MS>();
-  if (e == cudaSuccess) e = step_carveout<NT, PM, VAR, KP, TM, MS>(shared_sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(STEP_BLK);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (shared_sm) {   // otherwise the function's own (default) preference
+    attr[na].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[na].val.sharedMemCarveout = (unsigned)cudaSharedmemCarveoutMaxShared;
+    ++na;
+  }
+  if (MG_USE_PDL && dependent) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
+  cfg.numAttrs = na;
   if constexpr (!KP) {
     return cudaLaunchKernelEx(&cfg, mg_step_kernel<NT, PM, VAR, KP, TM, MS>, a, NoClassK{});
   } else if constexpr (VAR == 0) {

@@ -142,3 +142,24 @@ def test_server_refuses_generic_classes(lib):
         B.mg_server_create([vehicles.heavy8(), vehicles.lauv()], dt=0.01, max_requests=4, max_queue=4)
     assert e.value.code == B.MG_ERR_INVALID_ARG
 
+
+
+def test_env_order_is_a_stable_sort_by_class(lib):
+    """mg_env_order: per-class counts, and lib_env[i] places env i in the
+    library's class-grouped order (stable within a class); host only."""
+    import numpy as np
+    rng = np.random.default_rng(4)
+    env_class = rng.integers(0, 5, size=1000).astype(np.int32)
+    env_class[:7] = [4, 0, 4, 2, 2, 0, 1]
+    counts, lib_env = B.mg_env_order(env_class, 5)
+    assert counts.tolist() == np.bincount(env_class, minlength=5).tolist()
+    assert sorted(lib_env.tolist()) == list(range(1000))           # a permutation
+    order = np.argsort(env_class, kind="stable")                     # library env k holds user env order[k]
+    assert np.array_equal(lib_env[order], np.arange(1000))
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    for c in range(5):                                               # class c owns [start_c, start_c + n_c)
+        idx = lib_env[env_class == c]
+        assert np.all(np.diff(idx) == 1) and (len(idx) == 0 or idx[0] == starts[c])
+    with pytest.raises(B.MGError) as e:
+        B.mg_env_order(np.array([0, 5, 1], np.int32), 5)
+    assert e.value.code == B.MG_ERR_INVALID_ARG and "class 5" in str(e.value)

@@ -196,5 +196,90 @@ def test_autograd_function_matches_direct_call():
     g = gpu_gradients(sim, a, T, np.zeros((T, E, 13)), -np.ones((T, E)), np.zeros((E, 21)))
     np.testing.assert_allclose(sim.unpack_actions(acts.grad), g["act"], rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(A.grad.cpu().numpy()[slots], g["A"], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(dl.grad.cpu().numpy()[slots], g["dl"], rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(dq.grad.cpu().numpy()[slots], g["dq"], rtol=1e-6, atol=1e-7)
+    sim.close()
+
+
+def test_backward_refuses_a_discarded_recording():
+    """Every call that changes what produced a recording (parameters, state,
+    task, a step, a reset, a graph replay) discards it: backward then returns
+    MG_ERR_STATE instead of differentiating old checkpoints with new values."""
+    counts, T, K = [2, 2, 2, 2, 2], 6, 2
+    classes, sim, p, s0, a, nthr = setup(counts, T, K, 3, seed=17)
+    a_dev = sim.pack_actions(a)
+    n_slots = sim.n_slots
+    A = torch.ones(n_slots, 6, device="cuda")
+    params = sim.get_params()
+    task = sim.get_task()
+
+    def record():
+        sim.set_state(s0)
+        B.mg_rollout(sim.handle, a_dev, T, None, None, True)
+        steps, rid = B.mg_recording(sim.handle)
+        assert steps == T and rid != 0
+        return rid
+
+    changes = {
+        "set_hydro": lambda: B.mg_set_hydro(sim.handle, A, None, None),
+        "set_params": lambda: sim.set_params(params),
+        "set_task": lambda: sim.set_task(task),
+        "set_state": lambda: sim.set_state(s0),
+        "step": lambda: sim.step(a_dev[:1]),
+        "rollout": lambda: B.mg_rollout(sim.handle, a_dev, 2, None, None, False),
+        "reset": lambda: sim.reset(seed=3),
+    }
+    ids = set()
+    for name, change in changes.items():
+        rid = record()
+        assert rid not in ids
+        ids.add(rid)
+        B.mg_step_backward(sim.handle, a_dev)          # valid right after recording
+        change()
+        assert B.mg_recording(sim.handle) == (0, 0), name
+        for fn in (B.mg_step_backward, B.mg_step_backward_noalloc):
+            with pytest.raises(B.MGError) as e:
+                fn(sim.handle, a_dev)
+            assert e.value.code == B.MG_ERR_STATE, name
+    # A replayed graph advances the same envs: it discards the recording too.
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = B.mg_graph_capture(sim.handle, a_dev, 2, None, None, stream=st)
+    st.synchronize()
+    record()
+    with torch.cuda.stream(st):
+        B.mg_graph_launch(g, stream=st)
+    st.synchronize()
+    with pytest.raises(B.MGError) as e:
+        B.mg_step_backward(sim.handle, a_dev)
+    assert e.value.code == B.MG_ERR_STATE
+    B.mg_graph_destroy(g)
+    torch.cuda.synchronize()
+    sim.close()
+
+
+def test_autograd_backward_after_another_forward_raises():
+    """The simulator holds one recording: the first graph's backward after a
+    second forward on the same simulator raises instead of returning the
+    second rollout's gradients (the shapes would match)."""
+    counts, T, K = [2, 2, 2, 2, 2], 5, 2
+    classes, sim, p, s0, a, nthr = setup(counts, T, K, 5, seed=19)
+    n_slots = sim.n_slots
+    slots = sim.slots_of_envs()
+    A = torch.ones(n_slots, 6)
+    A[slots] = torch.from_numpy(p["Ma"]).float()
+    dl = torch.zeros(n_slots, 6)
+    dl[slots] = torch.from_numpy(p["dl"]).float()
+    dq = torch.zeros(n_slots, 6)
+    dq[slots] = torch.from_numpy(p["dq"]).float()
+    A, dl, dq = (x.cuda().requires_grad_(True) for x in (A, dl, dq))
+    acts = sim.pack_actions(a).requires_grad_(True)
+    _, rew1 = AG.rollout(sim, acts, A, dl, dq)
+    sim.set_state(s0)
+    _, rew2 = AG.rollout(sim, acts, A, dl, dq)
+    with pytest.raises(RuntimeError, match="no longer holds"):
+        (-rew1.sum()).backward()
+    (-rew2.sum()).backward()          # the current recording still differentiates
+    torch.cuda.synchronize()
+    assert torch.isfinite(acts.grad).all() and torch.isfinite(dl.grad).all()
     sim.close()

@@ -505,3 +505,51 @@ def test_flop_count_matches_hand_count():
     s8, o8 = B.mg_count_flops(8)
     s4, _ = B.mg_count_flops(4)
     assert s8 - s4 == 4 * (3 + 2) + 6 * 4 * 2
+
+
+def test_interleaved_class_map_through_env_order():
+    """A caller whose envs carry an arbitrary class map (interleaved here)
+    builds the simulator from mg_env_order's class counts and moves each env's
+    data to library env lib_env[i]; every env's result, read back through the
+    same map, equals the oracle run on that env in the caller's order. Then
+    mg_observe of the final state gives the rollout's last observation and
+    its reward without the command term."""
+    classes = vehicles.five_classes()
+    rng = np.random.default_rng(50)
+    env_class = rng.integers(0, 5, 700).astype(np.int32)
+    env_class[:10] = [3, 0, 4, 0, 1, 2, 2, 4, 3, 1]
+    counts, lib_env = B.mg_env_order(env_class, 5)
+    sim = make_sim(classes, counts.tolist(), K=4)
+    n, T = sim.n_envs, 3
+    # The caller's data, in the caller's order (env i of class env_class[i]).
+    grouped = workloads.random_params(51, classes, counts.tolist())
+    p_user = {k: np.asarray(v)[lib_env] for k, v in grouped.items()}
+    assert np.array_equal(p_user["cls"], env_class)
+    nthr_user = np.array([classes[c]["n_thr"] for c in env_class])
+    s_user = workloads.random_states(52, n, nthr_user)
+    a_user = workloads.actions(53, T, n)
+    # Into the library's order: library env lib_env[i] holds the caller's env i.
+    order = np.argsort(lib_env)
+    sim.set_params(B.dict_to_params({k: v[order] for k, v in p_user.items()}, n))
+    sim.set_state(s_user[order])
+    obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
+    rew = torch.zeros(T, sim.n_slots, device="cuda")
+    sim.rollout(sim.pack_actions(a_user[:, order]), T, obs, rew)
+    o_now = torch.zeros(sim.n_slots, 13, device="cuda")
+    r_now = torch.zeros(sim.n_slots, device="cuda")
+    B.mg_observe(sim.handle, o_now, r_now)
+    torch.cuda.synchronize()
+    got = sim.get_state()[lib_env]          # back in the caller's order
+    slots = sim.slots_of_envs()[lib_env]
+    envs = oracle.make_envs(oracle_env_arrays(p_user))
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s_user.astype(np.float64), a_user, 0.01, 4)
+    err = rel_state_err(got, ref)
+    assert err.max() <= 3 * ONE_STEP_TOL, err.max()
+    np.testing.assert_allclose(obs.cpu().numpy()[:, slots], o_ref, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(rew.cpu().numpy()[:, slots], r_ref, rtol=1e-4, atol=1e-3)
+    np.testing.assert_allclose(o_now.cpu().numpy(), obs[-1].cpu().numpy(), rtol=1e-6, atol=1e-6)
+    c = np.clip(a_user[-1].astype(np.float64), -1, 1) * (np.arange(8)[None, :] < nthr_user[:, None])
+    np.testing.assert_allclose(r_now.cpu().numpy()[slots], rew[-1].cpu().numpy()[slots] + 0.01 * (c * c).sum(1),
+                               rtol=1e-6, atol=1e-5)
+    sim.status()
+    sim.close()
