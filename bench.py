@@ -720,8 +720,9 @@ def main():
                 "peak_src": f"2 x 128 FP32 lanes x {num_sms()} SMs x max SM clock"}
     traffic, trec = profiled_traffic(E, K)
     roof["traffic"] = traffic
-    roof["traffic_note"] = (f"DRAM read+write bytes per step from an ncu range replay of {trec['steps']} consecutive "
-                            f"steps ({trec['launches']} launches, write-backs included): {os.path.relpath(TRAFFIC_RECORD, ROOT)}"
+    roof["traffic_note"] = (f"DRAM read+write bytes per step, difference of two ncu range replays of 2 and 6 "
+                            f"consecutive steps ({trec['launches_per_step']} launches a step, write-backs included): "
+                            f"{os.path.relpath(TRAFFIC_RECORD, ROOT)}"
                             if traffic else "null: no ncu record of these kernel sources at this workload")
     roof.update({"kernel": f"mg_step_kernel<NT, 0, 0, 1, 0, 0> (class constants, propellers, Euler, class tables as the kernel parameter), {n_launches} launches per step",
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
