@@ -403,7 +403,9 @@ def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
 def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20):
     """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
     T-step rollout (observation and reward every step) captured once as a CUDA
-    graph after the autotuner chose the persistent grid, then replayed."""
+    graph after the autotuner chose the launch shape (lanes per env, envs per
+    block, resident blocks per SM), then replayed. The same graph with one
+    lane per env is timed beside it."""
     import torch
     from paper_2503_09203_b300 import binding as B
     from paper_2503_09203_b300 import vehicles, workloads
@@ -415,25 +417,35 @@ def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20):
     obs = torch.zeros(T, sim.n_slots, 13, device="cuda")
     rew = torch.zeros(T, sim.n_slots, device="cuda")
     st = torch.cuda.Stream()
+    out = {"envs": E, "K": K, "steps_per_graph": T}
+
+    def time_graph():
+        with torch.cuda.stream(st):
+            g = B.mg_graph_capture(sim.handle, acts, T, obs, rew, st)
+            for _ in range(3):
+                B.mg_graph_launch(g, st)
+            st.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                B.mg_graph_launch(g, st)
+            e1.record(st)
+            e1.synchronize()
+            B.mg_graph_destroy(g)
+        return e0.elapsed_time(e1) * 1e-3 / reps
+
     with torch.cuda.stream(st):
-        threads, bps = B.mg_autotune(sim.handle, st)
-        g = B.mg_graph_capture(sim.handle, acts, T, obs, rew, st)
-        for _ in range(3):
-            B.mg_graph_launch(g, st)
-        st.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps):
-            B.mg_graph_launch(g, st)
-        e1.record(st)
-        e1.synchronize()
-        t = e0.elapsed_time(e1) * 1e-3 / reps
-        B.mg_graph_destroy(g)
+        shape = B.mg_autotune(sim.handle, T, st)
+    t = time_graph()
+    out.update({"launch_shape": shape, "graph_s": t, "env_steps_per_s": E * T / t})
+    if shape["lanes_per_env"] != 1:
+        B.mg_set_launch_shape(sim.handle, 1, 0)
+        t1 = time_graph()
+        out["one_lane"] = {"graph_s": t1, "env_steps_per_s": E * T / t1}
     B.mg_status(sim.handle, st)
     sim.close()
-    return {"envs": E, "K": K, "steps_per_graph": T, "blocks_per_sm": bps, "graph_s": t,
-            "env_steps_per_s": E * T / t}
+    return out
 
 
 def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):

@@ -389,10 +389,43 @@ int mg_status(mg_sim* sim, mg_stream_t stream);
  * the simulator stays usable. Synchronises `stream`. */
 int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream);
 
-/* Choose threads per block and the number of resident blocks per SM of the
- * persistent rollout by timing candidates on `stream` (state is saved and
- * restored). Writes the choice into *threads / *blocks_per_sm if not NULL. */
-int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads, int32_t* blocks_per_sm);
+/* Launch shape of the step launches (no counterpart in the paper: how the
+ * batched step maps onto the GPU).
+ * lanes_per_env 1: one env per thread, tiles of 128 envs per block, each
+ *   launch a persistent grid of blocks_per_sm resident blocks per SM (0: the
+ *   kernels' occupancy limit).
+ * lanes_per_env 2: a lane pair per env (the linear-momentum and the
+ *   angular-momentum rows of the equation of motion on two lanes), 64 envs
+ *   per block, one block per half tile. It serves the launches of one class
+ *   (those of large steps and of long rollouts) of propeller classes with the
+ *   Euler substep, class-constant or per-env parameters, the hover task and
+ *   no checkpoint recording; every other launch keeps one lane per env.
+ *   Results agree with the one-lane kernel to rounding (the rows are summed
+ *   in another order), not bit for bit.
+ * The K substeps of a step (and the steps of a multi-step launch) always stay
+ * in one launch with the state in registers: splitting them over launches
+ * would only add state traffic. */
+typedef struct {
+  int32_t lanes_per_env;    /* 1 or 2 */
+  int32_t envs_per_block;   /* 128 / lanes_per_env (output only) */
+  int32_t blocks_per_sm;    /* one-lane launches: resident blocks per SM (0: occupancy limit) */
+  int32_t pad0;
+  double us_per_step;       /* mg_autotune: the chosen shape's measured time per step */
+} mg_launch_shape;
+
+/* Choose the launch shape by timing candidates on `stream`: one lane per env
+ * with every persistent grid from 1 resident block per SM to the occupancy
+ * limit, and a lane pair per env when a launch can take it. Each candidate
+ * runs a rollout of n_steps steps (0: 20) with observations and rewards every
+ * step, the shape of the rollouts and graphs it will serve, from the current
+ * state, which is restored afterwards (a recording is discarded). Allocates
+ * scratch of about n_steps * n_slots * 56 bytes plus the state and the
+ * actions of n_steps steps. Writes the choice into *out if not NULL. */
+int mg_autotune(mg_sim* sim, int32_t n_steps, mg_stream_t stream, mg_launch_shape* out);
+int mg_get_launch_shape(const mg_sim* sim, mg_launch_shape* out);
+/* Fix the launch shape by hand (lanes_per_env 1 or 2, blocks_per_sm >= 0);
+ * takes effect from the next launch. Errors: INVALID_ARG. */
+int mg_set_launch_shape(mg_sim* sim, const mg_launch_shape* shape);
 
 /* Fix the persistent grid: blocks_per_sm resident blocks of each step launch
  * per SM (0: the kernel's occupancy limit, the default; values above it are

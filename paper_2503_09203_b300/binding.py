@@ -92,6 +92,11 @@ class mg_layout(C.Structure):
                 ("cls", mg_class_layout * MG_MAX_CLASSES)]
 
 
+class mg_launch_shape(C.Structure):
+    _fields_ = [("lanes_per_env", C.c_int32), ("envs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("pad0", C.c_int32), ("us_per_step", C.c_double)]
+
+
 class mg_server_config(C.Structure):
     _fields_ = [("dt", C.c_double), ("budget_bytes", C.c_size_t), ("max_requests", C.c_int32),
                 ("max_queue", C.c_int32), ("reset", mg_reset_cfg)]
@@ -143,7 +148,9 @@ _SIGS = {
     "mg_set_params": [_VP, _VP, C.c_size_t],
     "mg_status": [_VP, _VP],
     "mg_test_wait_timeout": [_VP, _U64, _VP],
-    "mg_autotune": [_VP, _VP, C.POINTER(_I32), C.POINTER(_I32)],
+    "mg_autotune": [_VP, _I32, _VP, C.POINTER(mg_launch_shape)],
+    "mg_get_launch_shape": [_VP, C.POINTER(mg_launch_shape)],
+    "mg_set_launch_shape": [_VP, C.POINTER(mg_launch_shape)],
     "mg_set_blocks_per_sm": [_VP, _I32],
     "mg_graph_capture": [_VP, _VP, _I32, _VP, _VP, _VP, C.POINTER(_VP)],
     "mg_graph_launch": [_VP, _VP],
@@ -405,10 +412,27 @@ def mg_test_wait_timeout(sim, limit_ns: int, stream=None):
     return _check(lib().mg_test_wait_timeout(sim, int(limit_ns), _stream(stream)), sim)
 
 
-def mg_autotune(sim, stream=None):
-    t, b = C.c_int32(), C.c_int32()
-    _check(lib().mg_autotune(sim, _stream(stream), C.byref(t), C.byref(b)), sim)
-    return t.value, b.value
+def _shape_dict(sh: "mg_launch_shape") -> dict:
+    return {name: getattr(sh, name) for name, _ in mg_launch_shape._fields_ if name != "pad0"}
+
+
+def mg_autotune(sim, n_steps: int = 0, stream=None) -> dict:
+    """Time the launch-shape candidates on a rollout of n_steps steps (0: 20)
+    and keep the fastest; returns the chosen shape."""
+    sh = mg_launch_shape()
+    _check(lib().mg_autotune(sim, int(n_steps), _stream(stream), C.byref(sh)), sim)
+    return _shape_dict(sh)
+
+
+def mg_get_launch_shape(sim) -> dict:
+    sh = mg_launch_shape()
+    _check(lib().mg_get_launch_shape(sim, C.byref(sh)), sim)
+    return _shape_dict(sh)
+
+
+def mg_set_launch_shape(sim, lanes_per_env: int = 1, blocks_per_sm: int = 0):
+    sh = mg_launch_shape(lanes_per_env=int(lanes_per_env), blocks_per_sm=int(blocks_per_sm))
+    return _check(lib().mg_set_launch_shape(sim, C.byref(sh)), sim)
 
 
 def mg_set_blocks_per_sm(sim, blocks_per_sm: int):

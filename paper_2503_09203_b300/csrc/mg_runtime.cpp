@@ -25,6 +25,7 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
                              cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
+cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
 }  // namespace mg
 
 namespace mg {
@@ -59,6 +60,7 @@ struct mg_sim {
   int64_t act_floats = 0, state_floats = 0;
   int32_t threads = 128;
   int32_t blocks_per_sm = 0;   // persistent blocks per SM (0: occupancy limit)
+  int32_t lanes = 1;           // lanes per env of eligible launches (1 or 2)
   int32_t num_sms = 148;
   int32_t n_tiles = 0, n_segs = 0;
   double h = 0.0;
@@ -819,6 +821,15 @@ static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
 #define MG_SPLIT_MIN_STEPS 16
 #endif
 
+// Whether a launch of the plan may run on the lane-pair kernel: one class
+// (class tables as the kernel parameter), propellers with the Euler substep,
+// class-constant or per-env parameters, the hover task, actions from memory,
+// no checkpoint recording.
+static bool pair_eligible(const mg_sim* sim, const Group& g, const StepArgs& a) {
+  return g.cls >= 0 && g.var == 0 && param_mode(sim) <= 1 && sim->cfg.task == 0 && !a.ckpt && !a.ret &&
+         a.act_mode == 0 && a.n_steps >= 1;
+}
+
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
   const mg_sim::Plan& p = step_plan(sim, a.n_steps >= MG_SPLIT_MIN_STEPS);
   bool first = true;
@@ -834,8 +845,11 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     // step's other launches start, so its blocks only become resident and set
     // up early.
     a.wait_first = first && p.first_pdl;
-    CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
-                   p.grid[i], !first || p.first_pdl, p.carve_max[i] != 0, st));
+    if (sim->lanes == 2 && pair_eligible(sim, g, a))
+      CK(launch_pair(a, p.kc[i], g.nt, !first || p.first_pdl, st));
+    else
+      CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
+                     p.grid[i], !first || p.first_pdl, p.carve_max[i] != 0, st));
     first = false;
   }
   return MG_OK;
@@ -1420,63 +1434,108 @@ int mg_status(mg_sim* sim, mg_stream_t stream) {
   return MG_OK;
 }
 
-int mg_autotune(mg_sim* sim, mg_stream_t stream, int32_t* threads_out, int32_t* bps_out) {
+// Launch-shape autotuner. Candidates: one lane per env (128-env blocks) with
+// every persistent grid from 1 resident block per SM to the kernels'
+// occupancy limit, and, when some launch of the rollout can take it, a lane
+// pair per env (64-env blocks, one block per half tile). Each candidate
+// times the rollout shape it will serve: n_steps steps with the observation
+// and reward of every step (one warm-up, then the best of three), from the
+// same saved state, which is put back afterwards.
+int mg_autotune(mg_sim* sim, int32_t n_steps, mg_stream_t stream, mg_launch_shape* out) {
   if (!sim) return MG_ERR_INVALID_ARG;
+  if (n_steps < 0 || n_steps > 4096) return fail(sim, MG_ERR_INVALID_ARG, "autotune: n_steps %d not in 0..4096", n_steps);
+  const int steps = n_steps > 0 ? n_steps : 20;
   cudaStream_t st = (cudaStream_t)stream;
-  const int steps = 4;
-  float* d_save = nullptr;
-  float* d_act = nullptr;
-  CK(cudaMalloc(&d_save, sizeof(float) * sim->state_floats));
-  if (cudaMalloc(&d_act, sizeof(float) * sim->act_floats * steps) != cudaSuccess) {
-    cudaFree(d_save);
+  float *d_save = nullptr, *d_act = nullptr, *d_obs = nullptr;
+  const size_t obs_floats = (size_t)steps * sim->n_slots * 14;
+  auto release = [&]() {
+    if (d_save) cudaFree(d_save);
+    if (d_act) cudaFree(d_act);
+    if (d_obs) cudaFree(d_obs);
+  };
+  if (cudaMalloc(&d_save, sizeof(float) * sim->state_floats) != cudaSuccess ||
+      cudaMalloc(&d_act, sizeof(float) * sim->act_floats * steps) != cudaSuccess ||
+      cudaMalloc(&d_obs, sizeof(float) * obs_floats) != cudaSuccess) {
+    cudaGetLastError();
+    release();
     return fail(sim, MG_ERR_OOM, "autotune: scratch allocation failed");
   }
-  cudaMemcpyAsync(d_save, sim->d_state, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st);
-  cudaMemsetAsync(d_act, 0, sizeof(float) * sim->act_floats * steps, st);
+  CK(cudaMemcpyAsync(d_save, sim->d_state, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(d_act, 0, sizeof(float) * sim->act_floats * steps, st));
   cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  // Tiles are 128 envs (the kernels' fixed block); the tuned knob is the
-  // persistent grid: b resident blocks per SM.
-  int best_t = sim->threads, best_b = sim->blocks_per_sm;
-  float best = 1e30f;
-  const int old_t = sim->threads, old_b = sim->blocks_per_sm;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int old_lanes = sim->lanes, old_bps = sim->blocks_per_sm;
   int occ = 1 << 30;
-  for (const Group& g : sim->groups) {
+  bool pair_any = false;
+  StepArgs probe = step_args(sim);
+  probe.n_steps = steps;
+  probe.obs_every = 1;
+  for (const Group& g : step_plan(sim, steps >= MG_SPLIT_MIN_STEPS).groups) {
     int o = 0;
-    if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &o) != cudaSuccess) o = 0;
-    occ = std::min(occ, o);
+    if (step_kernel_occupancy(g.nt, param_mode(sim), g.var, g.cls >= 0, sim->cfg.task == 1, &o) != cudaSuccess) o = 1;
+    occ = std::min(occ, std::max(o, 1));
+    pair_any = pair_any || pair_eligible(sim, g, probe);
   }
-  if (occ == (1 << 30)) occ = 0;
-  for (int b = 1; b <= occ; ++b) {
-    sim->blocks_per_sm = b;
-    float ms = 0.0f;
-    for (int rep = 0; rep < 3; ++rep) {
+  if (occ == (1 << 30)) occ = 1;
+  std::vector<std::pair<int, int>> cand;   // (lanes, blocks per SM)
+  for (int b = 1; b <= occ; ++b) cand.push_back({1, b});
+  if (pair_any) cand.push_back({2, 0});
+  float best = 1e30f;
+  int best_lanes = 1, best_bps = 0;
+  int rc = MG_OK;
+  for (const auto& c : cand) {
+    sim->lanes = c.first;
+    sim->blocks_per_sm = c.second;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 4 && rc == MG_OK; ++rep) {
+      cudaMemcpyAsync(sim->d_state, d_save, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st);
       cudaEventRecord(e0, st);
-      mg_rollout(sim, d_act, steps, nullptr, nullptr, 0, stream);
+      rc = mg_rollout(sim, d_act, steps, d_obs, d_obs + (size_t)steps * sim->n_slots * 13, 0, stream);
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float x = 0.0f;
       cudaEventElapsedTime(&x, e0, e1);
-      if (rep > 0) ms += x;
+      if (rep > 0) ms = std::min(ms, x);
     }
-    if (ms < best) { best = ms; best_b = b; }
+    if (rc != MG_OK) break;
+    if (ms < best) { best = ms; best_lanes = c.first; best_bps = c.second; }
   }
-  (void)old_t; (void)old_b;
-  sim->threads = best_t;
-  sim->blocks_per_sm = best_b;
-  build_segs(sim);
-  cudaMemcpyAsync(sim->d_segs, sim->segs.data(), sizeof(SegDesc) * sim->segs.size(), cudaMemcpyHostToDevice, st);
+  sim->lanes = rc == MG_OK ? best_lanes : old_lanes;
+  sim->blocks_per_sm = rc == MG_OK ? best_bps : old_bps;
   cudaMemcpyAsync(sim->d_state, d_save, sizeof(float) * sim->state_floats, cudaMemcpyDeviceToDevice, st);
-  cudaStreamSynchronize(st);
+  cudaError_t e = cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(d_save);
-  cudaFree(d_act);
+  release();
   drop_recording(sim);
+  if (rc != MG_OK) return rc;
+  if (e != cudaSuccess) return fail(sim, MG_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
   CK(cudaGetLastError());
-  if (threads_out) *threads_out = best_t;
-  if (bps_out) *bps_out = best_b;
+  if (out) {
+    mg_get_launch_shape(sim, out);
+    out->us_per_step = 1e3 * best / steps;
+  }
+  return MG_OK;
+}
+
+int mg_get_launch_shape(const mg_sim* sim, mg_launch_shape* out) {
+  if (!sim || !out) return MG_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->lanes_per_env = sim->lanes;
+  out->envs_per_block = sim->threads / sim->lanes;
+  out->blocks_per_sm = sim->blocks_per_sm;
+  return MG_OK;
+}
+
+int mg_set_launch_shape(mg_sim* sim, const mg_launch_shape* shape) {
+  if (!sim || !shape) return MG_ERR_INVALID_ARG;
+  if (shape->lanes_per_env != 1 && shape->lanes_per_env != 2)
+    return fail(sim, MG_ERR_INVALID_ARG, "set_launch_shape: lanes_per_env %d not 1 or 2", shape->lanes_per_env);
+  if (shape->blocks_per_sm < 0)
+    return fail(sim, MG_ERR_INVALID_ARG, "set_launch_shape: negative blocks_per_sm %d", shape->blocks_per_sm);
+  sim->lanes = shape->lanes_per_env;
+  sim->blocks_per_sm = shape->blocks_per_sm;
   return MG_OK;
 }
 

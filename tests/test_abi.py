@@ -45,7 +45,7 @@ def test_binding_covers_header(lib):
 
 def test_record_layouts_match_header(tmp_path):
     structs = ["mg_class_desc", "mg_reset_cfg", "mg_config", "mg_class_layout", "mg_layout",
-               "mg_server_config", "mg_request", "mg_request_result", "mg_server_stats"]
+               "mg_server_config", "mg_request", "mg_request_result", "mg_server_stats", "mg_launch_shape"]
     prog = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){"]
     for s in structs:
         prog.append(f'printf("{s} %zu\\n", sizeof({s}));')

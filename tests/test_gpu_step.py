@@ -419,9 +419,12 @@ def test_graph_replay_and_autotune_keep_results():
     sim.rollout(a_dev, T, obs, rew)
     torch.cuda.synchronize()
     s_ref, o_ref = sim.get_state(), obs.clone()
-    threads, bps = B.mg_autotune(sim.handle)
-    assert threads in (64, 128, 256) and bps >= 0
+    shape = B.mg_autotune(sim.handle, T)
+    assert shape["lanes_per_env"] in (1, 2) and shape["envs_per_block"] == 128 // shape["lanes_per_env"]
+    assert shape["blocks_per_sm"] >= 0 and shape["us_per_step"] > 0
+    assert shape == dict(B.mg_get_launch_shape(sim.handle), us_per_step=shape["us_per_step"])
     assert np.array_equal(sim.get_state(), s_ref)   # autotune restores the state
+    B.mg_set_launch_shape(sim.handle, 1, shape["blocks_per_sm"])   # the one-lane kernels of s_ref
     sim.set_state(s0)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
