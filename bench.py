@@ -400,7 +400,7 @@ def actuated_bench(pk, stream, E=1 << 20, K=4, steps=100):
     return out
 
 
-def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20):
+def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20, lanes=0):
     """Heterogeneous batch: 5 classes, per-env DR + current, K substeps; a
     T-step rollout (observation and reward every step) captured once as a CUDA
     graph after the autotuner chose the launch shape (lanes per env, envs per
@@ -435,11 +435,15 @@ def hetero_graph_bench(stream, E=16384, K=4, T=100, reps=20):
             B.mg_graph_destroy(g)
         return e0.elapsed_time(e1) * 1e-3 / reps
 
-    with torch.cuda.stream(st):
-        shape = B.mg_autotune(sim.handle, T, st)
+    if lanes:   # a fixed shape (profiling: timings under a profiler would mislead the autotuner)
+        B.mg_set_launch_shape(sim.handle, lanes, 0)
+        shape = B.mg_get_launch_shape(sim.handle)
+    else:
+        with torch.cuda.stream(st):
+            shape = B.mg_autotune(sim.handle, T, st)
     t = time_graph()
     out.update({"launch_shape": shape, "graph_s": t, "env_steps_per_s": E * T / t})
-    if shape["lanes_per_env"] != 1:
+    if shape["lanes_per_env"] != 1 and not lanes:
         B.mg_set_launch_shape(sim.handle, 1, 0)
         t1 = time_graph()
         out["one_lane"] = {"graph_s": t1, "env_steps_per_s": E * T / t1}
@@ -588,6 +592,8 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="after the warm-up, run --steps steps of the headline workload between "
                          "cudaProfilerStart/Stop and exit (for an ncu range replay of DRAM traffic)")
+    ap.add_argument("--hetero-lanes", type=int, default=0,
+                    help="with --hetero-only: fix the launch shape to this many lanes per env instead of autotuning")
     ap.add_argument("--hetero-only", action="store_true",
                     help="run only the heterogeneous CUDA-graph workload (16k envs, 5 classes, K=4, 100 steps) "
                          "and print its line (profiling)")
@@ -596,7 +602,7 @@ def main():
     if args.hetero_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"hetero_graph": hetero_graph_bench(torch.cuda.current_stream())}))
+        print(json.dumps({"hetero_graph": hetero_graph_bench(torch.cuda.current_stream(), lanes=args.hetero_lanes)}))
         return
     if args.adjoint_only:
         import torch

@@ -329,7 +329,7 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
  * recompute scratch is a fixed 32 MiB array compiled into the library (held
  * by every GPU that loads it until the process exits) instead of the
  * simulator's own scratch buffer; the call allocates nothing.
- * Limit: (ckpt_every * K + 1) * 21 * n_slots <= 8,388,608 floats, else
+ * Limit: 2 * (ckpt_every * K + 1) * 28 * n_slots <= 8,388,608 floats, else
  * MG_ERR_INVALID_ARG with the sizes in mg_last_error(). Every entry of the
  * scratch that the kernel reads it writes earlier in the same call, so nothing
  * needs clearing between calls; the array keeps the last call's contents.
@@ -445,8 +445,10 @@ int mg_graph_destroy(mg_graph* g);
  * a class with n_thr thrusters, counted by running the kernels' own templated
  * arithmetic with a counting scalar on the host: one substep (with_current:
  * including the ocean-current terms, which class-constant runs compile out),
- * the observation + reward, and one substep's adjoint (its forward recompute
- * included). Any output may be NULL. */
+ * the observation + reward, and one substep's adjoint as the reverse pass
+ * runs it (the forward recompute that records the right-hand side, the tape
+ * rebuilt from that record, and the vector-Jacobian product). Any output may
+ * be NULL. */
 int mg_count_flops(int32_t n_thr, int32_t with_current, double* substep_flops, double* observe_flops,
                    double* adjoint_flops);
 

@@ -620,22 +620,53 @@ MG_HD void observe_vjp(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], con
   for (int i = 0; i < NT; ++i) lc[i] = lc[i] - S(0.02) * c[i] * g_rew;
 }
 
-// Adjoint of one substep. x0 is the substep's start state; `lx` holds the
-// adjoint of its end state on entry and of its start state on exit. The
-// command adjoint and the hydrodynamic-coefficient adjoints accumulate.
+// Tape of one substep rebuilt from its start state x0 and its right-hand side
+// rhs (M nu_dot of a4-a7, which the forward recompute stores with the state):
+// the rest of the tape (rotor states, R, current, relative velocity, the new
+// velocity and the quaternion update) is cheap to recompute, in the same
+// operations as the substep. q1 receives the end attitude.
+template <typename S, int NT, typename ActT, typename PhysT>
+MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
+                         const S rhs[6], Tape<S, NT>& tp, S q1[4]) {
+  S kf[NT], dz[NT], al[NT];
+  act_rotor<S, NT>(A, kf, dz, al);
+#pragma unroll
+  for (int i = 0; i < NT; ++i) tp.n1[i] = x0.n[i] + al[i] * (c[i] - x0.n[i]);
+  rot(x0.q, tp.R);
+  const S v[3] = {x0.nu[0], x0.nu[1], x0.nu[2]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tp.w[i] = x0.nu[3 + i];
+  rel_velocity<S, PhysT, true>(tp.R, v, P, tp.vc, tp.vr);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    tp.rhs[j] = rhs[j];
+    tp.nu1[j] = x0.nu[j] + (h * S(P.minv[j])) * rhs[j];
+  }
+  const S hh = S(0.5f) * h;
+  const S wn[3] = {tp.nu1[3], tp.nu1[4], tp.nu1[5]};
+  S qd[4];
+  quat_rate(x0.q, wn, qd);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tp.qn[i] = x0.q[i] + hh * qd[i];
+  tp.inv = minvsqrt(tp.qn[0] * tp.qn[0] + tp.qn[1] * tp.qn[1] + tp.qn[2] * tp.qn[2] + tp.qn[3] * tp.qn[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q1[i] = tp.qn[i] * tp.inv;
+}
+
+// Adjoint of one substep from its tape. x0 is the substep's start state and
+// q1 its end attitude; `lx` holds the adjoint of its end state on entry and
+// of its start state on exit. The command adjoint and the
+// hydrodynamic-coefficient adjoints accumulate.
 template <typename S, int NT, typename ActT>
-MG_HD void substep_vjp(const St<S, NT>& x0, const S (&c)[NT], const Phys<S>& P, const ActT& A, S h,
-                       St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
-  St<S, NT> x = x0;
-  Tape<S, NT> tp;
-  substep<S, NT, true>(x, c, P, A, h, &tp);
+MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& tp, const S (&c)[NT],
+                         const Phys<S>& P, const ActT& A, S h, St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
   const S z0 = S(0.0f);
 
   // q1 = qn * inv
-  S dot = x.q[0] * lx.q[0] + x.q[1] * lx.q[1] + x.q[2] * lx.q[2] + x.q[3] * lx.q[3];
+  S dot = q1[0] * lx.q[0] + q1[1] * lx.q[1] + q1[2] * lx.q[2] + q1[3] * lx.q[3];
   S lqn[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) lqn[i] = tp.inv * (lx.q[i] - x.q[i] * dot);
+  for (int i = 0; i < 4; ++i) lqn[i] = tp.inv * (lx.q[i] - q1[i] * dot);
   // qn = q + hh * W(w1) q ; W(w) q = q (x) (0, w)
   const S hh = S(0.5f) * h;
   const S qw = x0.q[0], qx = x0.q[1], qy = x0.q[2], qz = x0.q[3];
@@ -785,6 +816,16 @@ MG_HD void substep_vjp(const St<S, NT>& x0, const S (&c)[NT], const Phys<S>& P, 
 #pragma unroll
   for (int i = 0; i < 4; ++i) lx.q[i] = lq[i];
   // lx.p: identity through p1 = p + ...
+}
+
+// Adjoint of one substep with its forward recomputed in full.
+template <typename S, int NT, typename ActT>
+MG_HD void substep_vjp(const St<S, NT>& x0, const S (&c)[NT], const Phys<S>& P, const ActT& A, S h,
+                       St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
+  St<S, NT> x = x0;
+  Tape<S, NT> tp;
+  substep<S, NT, true>(x, c, P, A, h, &tp);
+  vjp_from_tape<S, NT>(x0, x.q, tp, c, P, A, h, lx, lc, g);
 }
 
 // ---------------------------------------------------------------------------

@@ -179,7 +179,23 @@ __global__ void mg_set_hydro_kernel(float4* planes, int64_t n_slots, const float
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint of a recorded rollout (one env per thread).
+// Adjoint of a recorded rollout: a block of two warps per 32 envs, one launch
+// per class with the class tables as the kernel parameter (constant-bank
+// operands in the vector-Jacobian product).
+//
+// The reverse pass walks the checkpoint segments from the last to the first.
+// Warp 1 (the producer) recomputes segment s - 1 from its checkpoint while
+// warp 0 (the consumer) runs the vector-Jacobian products of segment s, so
+// the forward recompute leaves the consumer's dependent chain. Per substep
+// and env the producer stores one record: the start state and the
+// right-hand side M nu_dot of a4-a7 (ADJ_REC floats, seven 16-byte vectors);
+// the consumer rebuilds the rest of the substep's tape from it (rotor
+// states, R, current, the new velocity and attitude: a few dozen operations
+// instead of the full substep) and applies its VJP. Two scratch buffers
+// alternate between the warps, with one block barrier per segment. Each
+// consumer lane prefetches its next record (and the next step's cotangents
+// and actions) into shared memory by cp.async while it computes the current
+// substep; record copies go through L2 only (the producer wrote them).
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ __forceinline__ void ld21(const float* base, int64_t stride, St<float, NT>& x) {
@@ -197,133 +213,214 @@ __device__ __forceinline__ void st21(float* base, int64_t stride, const St<float
   for (int j = 0; j < 13 + NT; ++j) base[j * stride] = f[j];
 }
 
-// Backward-pass state reads: the recomputed states of a segment are read in
-// reverse order, each into a per-thread shared-memory slot by cp.async one
-// substep ahead, so the read of the next state overlaps the current
-// vector-Jacobian product instead of stalling it.
-constexpr int ADJ_BLK = 32;   // adjoint blocks: one warp
-struct StatePrefetch {
-  float* buf;          // [2][21][ADJ_BLK] floats of this block
-  int lane, cur;
-  __device__ __forceinline__ float* slot(int b) const { return buf + b * 21 * ADJ_BLK + lane; }
-  template <int NT>
-  __device__ __forceinline__ void issue(const float* base, int64_t stride, int b) const {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot(b));
+constexpr int ADJ_ENVS = 32;                 // envs per block
+constexpr int ADJ_THREADS = 2 * ADJ_ENVS;    // warp 0: reverse pass, warp 1: forward recompute
+constexpr int ADJ_STEPF = 14 + 8;            // per-step slot: g_obs 13, g_rew 1, actions 8
+static_assert(ADJ_REC % 4 == 0 && ADJ_REC >= 27, "record of whole 16-byte vectors");
+
+__device__ __forceinline__ void cp4(unsigned dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp16_l2(unsigned dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Record of one env: state fields (canonical order p3 q4 nu6 n[NT]), rhs at 21.
+template <int NT>
+__device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x, const float* rhs) {
+  float sf[13 + NT], f[ADJ_REC];
+  state_to_fields<NT>(x, sf);
 #pragma unroll
-    for (int j = 0; j < 13 + NT; ++j)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * ADJ_BLK * j), "l"(base + j * stride)
-                   : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int j = 0; j < 21; ++j) f[j] = j < 13 + NT ? sf[j % (13 + NT)] : 0.0f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) f[21 + j] = rhs ? rhs[j] : 0.0f;
+#pragma unroll
+  for (int j = 27; j < ADJ_REC; ++j) f[j] = 0.0f;
+  float4* r4 = reinterpret_cast<float4*>(rec);
+#pragma unroll
+  for (int k = 0; k < ADJ_REC / 4; ++k) r4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+
+// Consumer-side prefetch slots of one lane: records [2][32][ADJ_REC] and
+// per-step data [2][ADJ_STEPF][32] of the block.
+struct AdjPrefetch {
+  float* rec;
+  float* stp;
+  int lane, cur, scur;
+  __device__ __forceinline__ float* rslot(int b) const { return rec + (b * ADJ_ENVS + lane) * ADJ_REC; }
+  __device__ __forceinline__ float* sslot(int b) const { return stp + b * ADJ_STEPF * ADJ_ENVS + lane; }
+  __device__ __forceinline__ void issue_rec(const float* src, int b) const {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(rslot(b));
+#pragma unroll
+    for (int k = 0; k < ADJ_REC / 4; ++k) cp16_l2(dst + 16u * k, src + 4 * k);
+    cp_commit();
   }
   template <int NT>
-  __device__ __forceinline__ void read(int b, St<float, NT>& x) const {
-    float f[13 + NT];
-    const float* p = slot(b);
+  __device__ __forceinline__ void read(int b, St<float, NT>& x, float rhs[6]) const {
+    float f[ADJ_REC];
+    const float4* p = reinterpret_cast<const float4*>(rslot(b));
 #pragma unroll
-    for (int j = 0; j < 13 + NT; ++j) f[j] = p[ADJ_BLK * j];
-    fields_to_state<NT>(f, x);
+    for (int k = 0; k < ADJ_REC / 4; ++k) {
+      const float4 v = p[k];
+      f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+    }
+    float sf[13 + NT];
+#pragma unroll
+    for (int j = 0; j < 13 + NT; ++j) sf[j] = f[j];
+    fields_to_state<NT>(sf, x);
+    if (rhs) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) rhs[j] = f[21 + j];
+    }
   }
-  // Wait for the state in the current slot, read it, start the copy of the
-  // state at `next` (if any) into the other slot.
+  // Step t's cotangents and actions into per-step slot b.
   template <int NT>
-  __device__ __forceinline__ void advance(St<float, NT>& x, const float* next, int64_t stride) {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    read<NT>(cur, x);
-    if (next) issue<NT>(next, stride, cur ^ 1);
-    cur ^= 1;
+  __device__ __forceinline__ void issue_step(const AdjArgs& a, const SegDesc& sd, int64_t i, int t, int b) const {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sslot(b));
+    const int64_t slot = sd.slot_off + i;
+    if (a.g_obs) {
+      const float* go = a.g_obs + ((int64_t)t * a.n_slots + slot) * 13;
+#pragma unroll
+      for (int q = 0; q < 13; ++q) cp4(dst + 4u * ADJ_ENVS * q, go + q);
+    }
+    if (a.g_rew) cp4(dst + 4u * ADJ_ENVS * 13, a.g_rew + (int64_t)t * a.n_slots + slot);
+    const float* ac = a.actions + (int64_t)t * a.act_stride + sd.act_off + i * NT;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) cp4(dst + 4u * ADJ_ENVS * (14 + q), ac + q);
+    cp_commit();
   }
 };
 
+// Producer: recompute segment s from its checkpoint into the records of
+// buffer `buf` (record j of this env at buf + (j * n_slots + slot) * ADJ_REC).
 template <int NT, typename ActT>
-__device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, int64_t i, float* pf_buf) {
+__device__ __forceinline__ void adj_produce(const AdjArgs& a, const SegDesc& sd, const ActT& A, const Phys<float>& P,
+                                            int64_t i, int s, float* buf) {
+  const int64_t ns = a.n_slots, slot = sd.slot_off + i;
+  const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
+  St<float, NT> x;
+  ld21<NT>(a.ckpt + (int64_t)s * 21 * ns + slot, ns, x);
+  float* rec = buf + slot * ADJ_REC;
+  const int64_t rstride = ns * ADJ_REC;
+  for (int t = t0; t < t1; ++t) {
+    float raw[NT], c[NT];
+    load_actions<NT>(a.actions + (int64_t)t * a.act_stride + sd.act_off + i * NT, raw);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) c[q] = clamp1(raw[q]);
+    for (int k = 0; k < sd.K; ++k) {
+      St<float, NT> x0 = x;
+      Tape<float, NT> tp;
+      substep<float, NT, true>(x, c, P, A, sd.h, &tp);
+      store_record<NT>(rec, x0, tp.rhs);
+      rec += rstride;
+    }
+  }
+  store_record<NT>(rec, x, nullptr);
+}
+
+template <int NT, typename ActT>
+__device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, int64_t i, bool valid,
+                            float* s_rec, float* s_step) {
+  const int role = threadIdx.x / ADJ_ENVS;   // 0: reverse pass, 1: forward recompute
+  const int lane = threadIdx.x % ADJ_ENVS;
   const int64_t slot = sd.slot_off + i;
   const int64_t ns = a.n_slots;
   Phys<float> P;
-  load_phys(a.planes, ns, slot, P);
-  const float4 tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
-  float tgt[3] = {tg.x, tg.y, tg.z};
-  float4 tr[3] = {tg, tg, tg};
-  if (sd.track) {
-    for (int q = 0; q < 3; ++q) tr[q] = __ldg(&a.planes[(TGT_PLANE + 1 + q) * ns + slot]);
-  }
-  // The recorded rollout advanced the counter by T.
-  const float k_start = tg.w - (float)a.T;
-  St<float, NT> lam;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) lam.p[j] = a.g_state_T ? a.g_state_T[slot * 21 + j] : 0.0f;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) lam.q[j] = a.g_state_T ? a.g_state_T[slot * 21 + 3 + j] : 0.0f;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) lam.nu[j] = a.g_state_T ? a.g_state_T[slot * 21 + 7 + j] : 0.0f;
-#pragma unroll
-  for (int j = 0; j < NT; ++j) lam.n[j] = a.g_state_T ? a.g_state_T[slot * 21 + 13 + j] : 0.0f;
-  HydroGrad<float> g;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) { g.A[j] = 0.0f; g.dl[j] = 0.0f; g.dq[j] = 0.0f; }
+  if (valid) load_phys(a.planes, ns, slot, P);
   const int K = sd.K;
   const int n_seg = (a.T + a.ckpt_every - 1) / a.ckpt_every;
-  float* scr = a.scratch + slot;
-  for (int s = n_seg - 1; s >= 0; --s) {
-    const int t0 = s * a.ckpt_every;
-    const int t1 = min(a.T, t0 + a.ckpt_every);
-    St<float, NT> x;
-    ld21<NT>(a.ckpt + (int64_t)s * 21 * ns + slot, ns, x);
-    int j = 0;
-    for (int t = t0; t < t1; ++t) {
-      float raw[NT], c[NT];
-      load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
-#pragma unroll
-      for (int q = 0; q < NT; ++q) c[q] = clamp1(raw[q]);
-      for (int k = 0; k < K; ++k, ++j) {
-        st21<NT>(scr + (int64_t)j * 21 * ns, ns, x);
-        substep<float, NT, false>(x, c, P, A, sd.h, nullptr);
-      }
+  const int64_t buf_floats = (int64_t)(a.ckpt_every * K + 1) * ns * ADJ_REC;
+  const int64_t rstride = ns * ADJ_REC;
+
+  // Consumer state.
+  St<float, NT> lam;
+  HydroGrad<float> g;
+  float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float4 tr[3] = {tg, tg, tg};
+  float k_start = 0.0f;
+  AdjPrefetch pf{s_rec, s_step, lane, 0, 0};
+  if (role == 0 && valid) {
+    tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
+    if (sd.track) {
+      for (int q = 0; q < 3; ++q) tr[q] = __ldg(&a.planes[(TGT_PLANE + 1 + q) * ns + slot]);
     }
-    st21<NT>(scr + (int64_t)j * 21 * ns, ns, x);
-    // The states are read back in reverse: index j (the segment's end), j-1,
-    // ..., 0; the state at a step boundary serves both steps.
-    __threadfence_block();
-    StatePrefetch pf{pf_buf, (int)threadIdx.x, 0};
-    pf.issue<NT>(scr + (int64_t)j * 21 * ns, ns, 0);
-    int next = j - 1;
-    auto next_ptr = [&]() -> const float* { return next >= 0 ? scr + (int64_t)next * 21 * ns : nullptr; };
-    for (int t = t1 - 1; t >= t0; --t) {
-      float raw[NT], c[NT], lc[NT];
-      load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
+    k_start = tg.w - (float)a.T;   // the recorded rollout advanced the counter by T
 #pragma unroll
-      for (int q = 0; q < NT; ++q) { c[q] = clamp1(raw[q]); lc[q] = 0.0f; }
-      // State at the end of step t: the segment's end (first step back), else
-      // the state the previous step's last substep read (still in its slot).
-      St<float, NT> xe;
-      if (t == t1 - 1) {
-        pf.advance<NT>(xe, next_ptr(), ns);
-        --next;
-      } else {
-        pf.read<NT>(pf.cur ^ 1, xe);
-      }
-      float go[13];
-      const float* gop = nullptr;
-      if (a.g_obs) {
+    for (int j = 0; j < 3; ++j) lam.p[j] = a.g_state_T ? a.g_state_T[slot * 21 + j] : 0.0f;
 #pragma unroll
-        for (int q = 0; q < 13; ++q) go[q] = a.g_obs[((int64_t)t * ns + slot) * 13 + q];
-        gop = go;
-      }
-      const float gr = a.g_rew ? a.g_rew[(int64_t)t * ns + slot] : 0.0f;
-      if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
-      observe_vjp<float, NT>(xe, c, tgt, gop, gr, lam, lc);
-      for (int k = K - 1; k >= 0; --k) {
-        St<float, NT> xs;
-        pf.advance<NT>(xs, next_ptr(), ns);
-        --next;
-        substep_vjp<float, NT>(xs, c, P, A, sd.h, lam, lc, g);
-      }
-      if (a.g_actions) {
-        float* ga = a.g_actions + t * a.act_stride + sd.act_off + i * NT;
+    for (int j = 0; j < 4; ++j) lam.q[j] = a.g_state_T ? a.g_state_T[slot * 21 + 3 + j] : 0.0f;
 #pragma unroll
-        for (int q = 0; q < NT; ++q) ga[q] = (raw[q] >= -1.0f && raw[q] <= 1.0f) ? lc[q] : 0.0f;
-      }
-    }
+    for (int j = 0; j < 6; ++j) lam.nu[j] = a.g_state_T ? a.g_state_T[slot * 21 + 7 + j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) lam.n[j] = a.g_state_T ? a.g_state_T[slot * 21 + 13 + j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) { g.A[j] = 0.0f; g.dl[j] = 0.0f; g.dq[j] = 0.0f; }
+    // The first step back (the last step of the rollout): its cotangents and actions.
+    pf.issue_step<NT>(a, sd, i, a.T - 1, 0);
   }
+  float tgt[3] = {tg.x, tg.y, tg.z};
+
+  for (int it = 0; it <= n_seg; ++it) {
+    if (role == 1 && it < n_seg && valid)
+      adj_produce<NT>(a, sd, A, P, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
+    if (role == 0 && it >= 1 && valid) {
+      const int s = n_seg - it;
+      const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
+      const float* rec0 = a.scratch + (int64_t)((it - 1) & 1) * buf_floats + slot * ADJ_REC;
+      int j = (t1 - t0) * K;   // record of the segment's end state
+      pf.issue_rec(rec0 + (int64_t)j * rstride, pf.cur);
+      cp_wait_all();
+      pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, pf.cur ^ 1);
+      for (int t = t1 - 1; t >= t0; --t) {
+        // Step t's cotangents and actions (issued one step ahead) and the
+        // next record are in shared memory after this wait.
+        cp_wait_all();
+        float go[13], raw[NT], c[NT], lc[NT];
+        const float* sp = pf.sslot(pf.scur);
+#pragma unroll
+        for (int q = 0; q < 13; ++q) go[q] = a.g_obs ? sp[ADJ_ENVS * q] : 0.0f;
+        const float gr = a.g_rew ? sp[ADJ_ENVS * 13] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+          raw[q] = sp[ADJ_ENVS * (14 + q)];
+          c[q] = clamp1(raw[q]);
+          lc[q] = 0.0f;
+        }
+        pf.scur ^= 1;
+        if (t > 0) pf.issue_step<NT>(a, sd, i, t - 1, pf.scur);
+        // State at the end of step t: record j (the segment's end on the
+        // first step back, else the first substep record of step t + 1).
+        St<float, NT> xe;
+        pf.read<NT>(pf.cur, xe, nullptr);
+        if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
+        observe_vjp<float, NT>(xe, c, tgt, a.g_obs ? go : nullptr, gr, lam, lc);
+        for (int k = K - 1; k >= 0; --k) {
+          if (k != K - 1) cp_wait_all();
+          pf.cur ^= 1;
+          --j;
+          St<float, NT> xs;
+          float rhs[6], q1[4];
+          pf.read<NT>(pf.cur, xs, rhs);
+          // Record j - 1 streams in while this substep's product runs.
+          if (j > 0) pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, pf.cur ^ 1);
+          Tape<float, NT> tp;
+          tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
+          vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g);
+        }
+        if (a.g_actions) {
+          float* ga = a.g_actions + (int64_t)t * a.act_stride + sd.act_off + i * NT;
+#pragma unroll
+          for (int q = 0; q < NT; ++q) ga[q] = (raw[q] >= -1.0f && raw[q] <= 1.0f) ? lc[q] : 0.0f;
+        }
+      }
+    }
+    // The producer's records of this round are complete and the consumer is
+    // done with the buffer the producer fills next.
+    __syncthreads();
+  }
+  if (role != 0 || !valid) return;
   if (a.g_state0) {
     float* o = a.g_state0 + slot * 21;
 #pragma unroll
@@ -345,42 +442,32 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
   }
 }
 
-// One warp-sized block per part of a tile: a few thousand envs (the adjoint
-// workload) then spread over all SMs instead of a few dozen. Class groups are
-// launched as programmatic dependents of one another (disjoint envs and
-// outputs) so that they run side by side.
+// One block of two warps per 32 envs of a class segment (one segment per
+// launch): a few thousand envs (the adjoint workload) then spread over all
+// SMs. The launches of a backward pass are programmatic dependents of one
+// another (disjoint envs and outputs) so that they run side by side.
 template <int NT>
-__global__ void __launch_bounds__(ADJ_BLK) mg_adjoint_kernel(const __grid_constant__ AdjArgs a) {
-  __shared__ Act<float> act;
-  __shared__ __align__(16) float pf_buf[2 * 21 * ADJ_BLK];
+__global__ void __launch_bounds__(ADJ_THREADS)
+    mg_adjoint_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ ClassK kc) {
+  __shared__ __align__(16) float s_rec[2 * ADJ_ENVS * ADJ_REC];
+  __shared__ __align__(16) float s_step[2 * ADJ_STEPF * ADJ_ENVS];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int parts = a.tile_envs / (int)blockDim.x;
+  const int parts = a.tile_envs / ADJ_ENVS;
   const int tile = a.tile_lo + (int)blockIdx.x / parts;
   if (tile < a.tile_lo + a.n_tiles) {
-    const int si = a.seg_lo + find_seg(a.segs + a.seg_lo, a.seg_hi - a.seg_lo, tile);
-    const SegDesc& sd = a.segs[si];
-    const ClassF& cf = a.classes[sd.cls];
-    for (int k = threadIdx.x; k < 72; k += blockDim.x) {
-      if (k < 48) (&act.alloc[0][0])[k] = cf.alloc[k / 8][k % 8];
-      else if (k < 56) act.kf[k - 48] = cf.kf[k - 48];
-      else if (k < 64) act.dz[k - 56] = cf.dz[k - 56];
-      else act.alpha[k - 64] = sd.alpha[k - 64];
-    }
-    __syncthreads();
-    const int64_t i = (int64_t)(tile - sd.tile_begin) * a.tile_envs + ((int)blockIdx.x % parts) * blockDim.x +
-                      threadIdx.x;
-    if (i >= sd.n_envs) {
+    const SegDesc& sd = a.segs[a.seg_lo];
+    const int64_t i = (int64_t)(tile - sd.tile_begin) * a.tile_envs + ((int)blockIdx.x % parts) * ADJ_ENVS +
+                      (threadIdx.x % ADJ_ENVS);
+    const bool valid = i < sd.n_envs;
+    if (!valid && i < sd.n4 && threadIdx.x < ADJ_ENVS) {
       // Padding slots of the segment: zero gradients.
-      if (i < sd.n4) {
-        const int64_t slot = sd.slot_off + i;
-        if (a.g_A) for (int j = 0; j < 6; ++j) a.g_A[slot * 6 + j] = 0.0f;
-        if (a.g_D) for (int j = 0; j < 12; ++j) a.g_D[slot * 12 + j] = 0.0f;
-        if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
-      }
-    } else {
-      const volatile Act<float>& va = act;
-      adjoint_env<NT>(a, sd, va, i, pf_buf);
+      const int64_t slot = sd.slot_off + i;
+      if (a.g_A) for (int j = 0; j < 6; ++j) a.g_A[slot * 6 + j] = 0.0f;
+      if (a.g_D) for (int j = 0; j < 12; ++j) a.g_D[slot * 12 + j] = 0.0f;
+      if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
     }
+    // Every thread of the block takes part in the per-segment barriers.
+    adjoint_env<NT>(a, sd, kc, i, valid, s_rec, s_step);
   }
   // Completion stays ordered along the stream (see the step kernel).
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -470,13 +557,14 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
   return cudaGetLastError();
 }
 
-// Adjoint launch of one class group (tiles of a.tile_envs envs, a multiple
-// of ADJ_BLK); `dependent`: programmatic dependent of the previous launch.
+// Adjoint launch of one class segment (a.seg_hi == a.seg_lo + 1; tiles of
+// a.tile_envs envs, a multiple of ADJ_ENVS) with that class's tables kc;
+// `dependent`: programmatic dependent of the previous launch.
 template <int NT>
-static cudaError_t launch_adjoint_t(const AdjArgs& a, bool dependent, cudaStream_t st) {
+static cudaError_t launch_adjoint_t(const AdjArgs& a, const ClassK& kc, bool dependent, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_tiles * (a.tile_envs / ADJ_BLK)));
-  cfg.blockDim = dim3(ADJ_BLK);
+  cfg.gridDim = dim3((unsigned)(a.n_tiles * (a.tile_envs / ADJ_ENVS)));
+  cfg.blockDim = dim3(ADJ_THREADS);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -484,13 +572,13 @@ static cudaError_t launch_adjoint_t(const AdjArgs& a, bool dependent, cudaStream
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, mg_adjoint_kernel<NT>, a);
+  return cudaLaunchKernelEx(&cfg, mg_adjoint_kernel<NT>, a, kc);
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st) {
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
-  if (a.tile_envs <= 0 || a.tile_envs % ADJ_BLK != 0) return cudaErrorInvalidValue;
-#define MG_L(N) return launch_adjoint_t<N>(a, dependent, st)
+  if (a.tile_envs <= 0 || a.tile_envs % ADJ_ENVS != 0 || a.seg_hi - a.seg_lo != 1) return cudaErrorInvalidValue;
+#define MG_L(N) return launch_adjoint_t<N>(a, kc, dependent, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;

@@ -23,7 +23,7 @@ cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, i
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
-cudaError_t launch_adjoint(const AdjArgs& a, int nt, bool dependent, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
 }  // namespace mg
@@ -496,8 +496,8 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (cfg->record_steps > 0) {
     const int64_t n_ck = (cfg->record_steps + sim->ckpt_every - 1) / sim->ckpt_every;
     if ((rc = dev_alloc(sim, (void**)&sim->d_ckpt, sizeof(float) * n_ck * 21 * slot)) != MG_OK) return bail(rc);
-    const int64_t n_scr = (int64_t)sim->ckpt_every * cfg->K + 1;
-    if ((rc = dev_alloc(sim, (void**)&sim->d_scratch, sizeof(float) * n_scr * 21 * slot)) != MG_OK) return bail(rc);
+    const size_t n_scr = adjoint_scratch_floats(sim->ckpt_every, cfg->K, slot);
+    if ((rc = dev_alloc(sim, (void**)&sim->d_scratch, sizeof(float) * n_scr)) != MG_OK) return bail(rc);
   }
   {
     cudaError_t e1 = cudaMemset(sim->d_state, 0, sizeof(float) * st);
@@ -1049,6 +1049,30 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
   return MG_OK;
 }
 
+// The adjoint launches of a backward pass: one per class segment, with that
+// class's tables as the kernel parameter, each a programmatic dependent of
+// the previous one so that they run side by side.
+static int launch_backward(mg_sim* sim, AdjArgs a, cudaStream_t st) {
+  a.tile_envs = sim->threads;
+  bool first = true;
+  for (const Group& grp : sim->groups) {
+    for (int s = grp.seg_lo; s < grp.seg_hi; ++s) {
+      const SegDesc& sd = sim->segs[s];
+      Group g = grp;
+      g.seg_lo = s;
+      g.seg_hi = s + 1;
+      g.tile_lo = sd.tile_begin;
+      g.n_tiles = (sd.n4 + sim->threads - 1) / sim->threads;
+      g.cls = sd.cls;
+      const ClassK kc = class_k(sim, g);
+      a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
+      CK(launch_adjoint(a, kc, g.nt, !first, st));
+      first = false;
+    }
+  }
+  return MG_OK;
+}
+
 int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, const float* g_rew,
                      const float* g_state_T, float* g_actions, float* g_added_mass, float* g_damping,
                      float* g_state0, mg_stream_t stream) {
@@ -1079,14 +1103,7 @@ int mg_step_backward(mg_sim* sim, const float* actions_dev, const float* g_obs, 
   a.g_state0 = g_state0;
   cudaStream_t st = (cudaStream_t)stream;
   if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
-  a.tile_envs = sim->threads;
-  bool first = true;
-  for (const Group& g : sim->groups) {
-    a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-    CK(launch_adjoint(a, g.nt, !first, st));
-    first = false;
-  }
-  return MG_OK;
+  return launch_backward(sim, a, st);
 }
 
 int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const float* dq_dev, mg_stream_t stream) {
@@ -1607,10 +1624,10 @@ extern "C" int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, c
   float* scratch = nullptr;
   size_t cap = 0;
   CK(noalloc_scratch(&scratch, &cap));
-  const size_t need = ((size_t)sim->ckpt_every * (size_t)sim->cfg.K + 1) * 21 * (size_t)sim->n_slots;
+  const size_t need = adjoint_scratch_floats(sim->ckpt_every, sim->cfg.K, sim->n_slots);
   if (need > cap)
     return fail(sim, MG_ERR_INVALID_ARG,
-                "backward_noalloc: scratch of %zu floats needed ((ckpt_every*K+1)*21*n_slots), the fixed array "
+                "backward_noalloc: scratch of %zu floats needed (2*(ckpt_every*K+1)*28*n_slots), the fixed array "
                 "holds %zu; lower ckpt_every or the env count",
                 need, cap);
   AdjArgs a;
@@ -1634,12 +1651,5 @@ extern "C" int mg_step_backward_noalloc(mg_sim* sim, const float* actions_dev, c
   a.g_state0 = g_state0;
   cudaStream_t st = (cudaStream_t)stream;
   if (g_actions) CK(cudaMemsetAsync(g_actions, 0, sizeof(float) * sim->rec_T * sim->act_floats, st));
-  a.tile_envs = sim->threads;
-  bool first = true;
-  for (const Group& g : sim->groups) {
-    a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-    CK(launch_adjoint(a, g.nt, !first, st));
-    first = false;
-  }
-  return MG_OK;
+  return launch_backward(sim, a, st);
 }
