@@ -461,6 +461,7 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):
     sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR),
                 record_steps=T, ckpt_every=ckpt)
     sim.reset(seed=SEED)
+    shape = B.mg_autotune(sim.handle, T, stream)   # launch shape of the recording rollout
     s0 = sim.get_state()
     acts = (torch.rand(T, sim.action_floats, device="cuda") * 2 - 1) * 0.99
     rew = torch.zeros(T, sim.n_slots, device="cuda")
@@ -489,7 +490,7 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):
         sub, obs, adj = B.mg_count_flops(c["n_thr"], adjoint=True, with_current=True)
         f_fwd += n * T * (K * sub + obs)
         f_bwd += n * T * K * adj
-    out = {"envs": E, "horizon": T, "K": K, "ckpt_every": ckpt, "forward_s": tf, "backward_s": tb,
+    out = {"envs": E, "horizon": T, "K": K, "ckpt_every": ckpt, "launch_shape": shape, "forward_s": tf, "backward_s": tb,
            "env_steps_per_s": E * T / (tf + tb), "backward_env_steps_per_s": E * T / tb,
            "fp32_tflops": (f_fwd + f_bwd) / (tf + tb) / 1e12}
     if pk:

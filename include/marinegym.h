@@ -398,8 +398,8 @@ int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream);
  *   angular-momentum rows of the equation of motion on two lanes), 64 envs
  *   per block, one block per half tile. It serves the launches of one class
  *   (those of large steps and of long rollouts) of propeller classes with the
- *   Euler substep, class-constant or per-env parameters, the hover task and
- *   no checkpoint recording; every other launch keeps one lane per env.
+ *   Euler substep, class-constant or per-env parameters and the hover task
+ *   (recorded rollouts included); every other launch keeps one lane per env.
  *   Results agree with the one-lane kernel to rounding (the rows are summed
  *   in another order), not bit for bit.
  * The K substeps of a step (and the steps of a multi-step launch) always stay

@@ -19,12 +19,10 @@
 // Scope: propeller classes with the semi-implicit Euler substep, class
 // tables as the kernel parameter (one class per launch), class-constant
 // (PM = 0) or per-env (PM = 1) parameters, hover observation and reward
-// after every step or after the last, actions from memory. Other launches
-// use the one-lane kernel.
+// after every step or after the last, actions from memory, and the
+// checkpoints of a recorded rollout. Other launches use the one-lane kernel.
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <atomic>
 
 #include "marinegym.h"
 #include "mg_internal.h"
@@ -152,7 +150,6 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const int r = 3 * hsel + j;
 #pragma unroll
     for (int q = 0; q < NT; ++q) Q.rows[j][q] = hsel ? kc.alloc[3 + j][q] : kc.alloc[j][q];
     Q.hminv[j] = h * (hsel ? minv6[3 + j] : minv6[j]);
@@ -163,7 +160,6 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
     Q.dq[j] = hsel ? dq6[3 + j] : dq6[j];
     Q.y2[j] = hsel ? -(Bf * rb[j]) : 0.0f;
     Q.Al[j] = A6[j];
-    (void)r;
   }
   Q.alpha = hsel ? 0.0f : W - Bf;
 
@@ -184,6 +180,18 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
   if (valid) pair_actions<NT>(a.actions + sd.act_off + i * NT, cn);
   float r_last = 0.0f;
   for (int t = 0; t < a.n_steps; ++t) {
+    if (a.ckpt && (t % a.ckpt_every) == 0 && valid && hsel == 0) {
+      // Recorded rollout: the state before step t into checkpoint t / ckpt_every.
+      float* ck = a.ckpt + (int64_t)(t / a.ckpt_every) * 21 * a.n_slots + slot;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) ck[j * a.n_slots] = x.p[j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ck[(3 + j) * a.n_slots] = x.q[j];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) ck[(7 + j) * a.n_slots] = x.nu[j];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ck[(13 + j) * a.n_slots] = j < NT ? x.n[j % NT] : 0.0f;
+    }
 #pragma unroll
     for (int j = 0; j < NT; ++j) c[j] = pclamp(cn[j]);
     // The next step's actions are in flight while this step computes.
@@ -321,7 +329,7 @@ static cudaError_t launch_pair_t(const StepArgs& a, const ClassK& kc, bool depen
 // kernel does not cover.
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st) {
   if (a.n_tiles <= 0) return cudaSuccess;
-  if (a.seg_hi - a.seg_lo != 1 || a.act_mode != 0 || a.track || a.ckpt || a.ret || a.n_steps < 1 ||
+  if (a.seg_hi - a.seg_lo != 1 || a.act_mode != 0 || a.track || a.ret || a.n_steps < 1 ||
       (a.per_env != 0 && a.per_env != 1))
     return cudaErrorInvalidValue;
 #define MG_P(N)                                                                              \

@@ -823,11 +823,10 @@ static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
 
 // Whether a launch of the plan may run on the lane-pair kernel: one class
 // (class tables as the kernel parameter), propellers with the Euler substep,
-// class-constant or per-env parameters, the hover task, actions from memory,
-// no checkpoint recording.
+// class-constant or per-env parameters, the hover task, actions from memory.
 static bool pair_eligible(const mg_sim* sim, const Group& g, const StepArgs& a) {
-  return g.cls >= 0 && g.var == 0 && param_mode(sim) <= 1 && sim->cfg.task == 0 && !a.ckpt && !a.ret &&
-         a.act_mode == 0 && a.n_steps >= 1;
+  return g.cls >= 0 && g.var == 0 && param_mode(sim) <= 1 && sim->cfg.task == 0 && !a.ret && a.act_mode == 0 &&
+         a.n_steps >= 1;
 }
 
 static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {

@@ -127,3 +127,46 @@ def test_autotune_shape_keeps_results_within_rounding():
     assert e.value.code == B.MG_ERR_INVALID_ARG
     sim.status()
     sim.close()
+
+
+def test_gradients_of_a_rollout_recorded_on_the_pair_kernel():
+    """A rollout recorded with two lanes per env (its checkpoints come from
+    the lane-pair kernel) differentiates to the oracle's tangents."""
+    from tests.test_gpu_adjoint import gpu_gradients
+    from tests.helpers import oracle_env_arrays
+    classes = vehicles.five_classes()
+    counts = [5, 4, 6, 3, 4]
+    T, K = 24, 4
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(vehicles.HOVER_DR),
+                record_steps=T, ckpt_every=8)
+    B.mg_set_launch_shape(sim.handle, 2, 0)
+    p = workloads.random_params(71, classes, counts)
+    sim.set_params(B.dict_to_params(p, sim.n_envs))
+    nthr = np.array([classes[c]["n_thr"] for c in workloads.env_classes(counts)])
+    s0 = workloads.random_states(72, sim.n_envs, nthr, pos_scale=2.0, vel_scale=0.3, rate_scale=0.4)
+    sim.set_state(s0)
+    a = workloads.actions(73, T, sim.n_envs, lo=-0.99, hi=0.99)
+    E = sim.n_envs
+    rng = np.random.default_rng(74)
+    g_rew = -np.ones((T, E))
+    g = gpu_gradients(sim, a, T, np.zeros((T, E, 13)), g_rew, np.zeros((E, 21)))
+    envs = oracle.make_envs(oracle_env_arrays(p))
+    thr_mask = (np.arange(8)[None, :] < nthr[:, None]).astype(np.float64)
+    for name in ("act", "A", "dq"):
+        got, want = [], []
+        for _ in range(3):
+            if name == "act":
+                d = dict(d_actions=rng.normal(size=(T, E, 8)) * thr_mask[None])
+            elif name == "A":
+                d = dict(d_Ma=rng.normal(size=(E, 6)))
+            else:
+                d = dict(d_dq=rng.normal(size=(E, 6)))
+            j = oracle.rollout_jvp(classes, envs, s0.astype(np.float64), a, 0.01, K, **d)
+            want.append(np.einsum("te,te->e", g_rew, j["d_reward"]))
+            key = {"act": "d_actions", "A": "d_Ma", "dq": "d_dq"}[name]
+            got.append(np.einsum("tek,tek->e", g[name], d[key]) if name == "act"
+                       else np.einsum("ek,ek->e", g[name], d[key]))
+        gv, rv = np.stack(got, 1), np.stack(want, 1)
+        err = np.linalg.norm(gv - rv, axis=1) / np.maximum(np.linalg.norm(rv, axis=1), 1e-6)
+        assert err.max() <= 1e-3, (name, err.max())
+    sim.close()
