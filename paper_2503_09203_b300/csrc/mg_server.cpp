@@ -43,6 +43,8 @@ namespace mg {
 cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                         bool dependent, bool shared_sm, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
+cudaError_t prepare_tick_pm0(int nt);
+cudaError_t prepare_tick_pm1(int nt);
 }  // namespace mg
 
 using namespace mg;
@@ -107,6 +109,7 @@ struct Req {
   int64_t steps_done = 0;    // completed ticks (published)
   int64_t steps_sched = 0;   // ticks enqueued
   int32_t n_thr = 0, n4 = 0;
+  int32_t dz = 0;            // the class has a nonzero dead zone
   int64_t slot_off = -1, st_off = -1;
   float h = 0;
   float alpha[8] = {0};
@@ -169,6 +172,10 @@ struct mg_server {
   TickBuf buf[2];                // host side of the two ticks in flight
   int64_t S = 0, state_cap = 0;
   size_t budget = 0;             // arena budget (bytes)
+  // Without DR and current every env of a class has the class's nominal
+  // physics: ticks then read the class tables instead of per-env parameter
+  // planes (the target plane only), and resets write only the target.
+  bool class_const = false;
   RangeAlloc slots, states;
   // Device bytes held by admitted requests (slot planes, return and state
   // of their envs), and the most ever held at once: the admission rule keeps
@@ -253,7 +260,7 @@ static SegDesc seg_of(const Req& q) {
   sd.h = q.h;
   sd.dt = q.h * (float)q.r.K;
   sd.track = 0;
-  sd.flags = 1;   // dead zones always tested in serving
+  sd.flags = q.dz ? 1 : 0;   // bit 0: the class has a dead zone
   for (int i = 0; i < 8; ++i) sd.alpha[i] = q.alpha[i];
   sd.seed = q.r.seed;
   return sd;
@@ -297,10 +304,10 @@ static bool enqueue_tick(mg_server* s, Tick& t) {
       a.n_segs = 1;
       a.n_sel = sd.n_envs;
       a.nominal = s->d_nominal;
-      a.per_env = 1;
+      a.per_env = s->class_const ? 0 : 1;
       a.serving = 1;
       a.state = s->d_state;
-      a.planes = s->d_planes;
+      a.planes = s->class_const ? s->d_planes + (size_t)TGT_PLANE * s->S : s->d_planes;
       a.n_slots = s->S;
       const mg_reset_cfg& r = s->cfg.reset;
       a.dr = r.dr_enabled; a.cur = r.current_enabled; a.cur3d = r.current_3d; a.init_mode = r.init_mode;
@@ -347,8 +354,8 @@ static bool enqueue_tick(mg_server* s, Tick& t) {
   a.state = s->d_state;
   a.n_steps = 1;
   a.act_mode = 1;
-  a.planes = s->d_planes;
-  a.per_env = 1;
+  a.planes = s->class_const ? s->d_planes + (size_t)TGT_PLANE * s->S : s->d_planes;
+  a.per_env = s->class_const ? 0 : 1;
   a.obs_every = 0;
   a.n_slots = s->S;
   a.ret = s->d_ret;
@@ -552,6 +559,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   s->S = S;
   s->state_cap = S * 21;
   s->budget = budget;
+  s->class_const = !cfg->reset.dr_enabled && !cfg->reset.current_enabled;
   const size_t bytes = sizeof(float4) * N_PLANES * S + sizeof(float) * S + sizeof(float) * s->state_cap;
   auto cleanup = [&](int code) {
     if (s->arena) cudaFree(s->arena);
@@ -599,11 +607,31 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
       f.kf[i] = (float)d.k_f[i];
       f.dz[i] = (float)d.deadzone[i];
     }
+    // Nominal physics block (class-constant ticks), in the order of the
+    // per-env parameter block; no current.
+    const double Mrb[6] = {d.mass, d.mass, d.mass, d.Ig[0], d.Ig[1], d.Ig[2]};
+    for (int j = 0; j < 6; ++j) {
+      f.phys[PAR_MINV + j] = (float)(1.0 / (Mrb[j] + d.Ma[j]));
+      f.phys[PAR_A + j] = (float)d.Ma[j];
+      f.phys[PAR_DL + j] = (float)d.dl[j];
+      f.phys[PAR_DQ + j] = (float)d.dq[j];
+    }
+    f.phys[PAR_M] = (float)d.mass;
+    for (int j = 0; j < 3; ++j) { f.phys[PAR_IG + j] = (float)d.Ig[j]; f.phys[PAR_RB + j] = (float)d.rb[j]; }
+    f.phys[PAR_W] = (float)(d.mass * kG);
+    f.phys[PAR_B] = (float)(d.buoy_ratio * d.mass * kG);
     ClassNominal& n = cn[c];
     n.mass = d.mass;
     for (int j = 0; j < 3; ++j) { n.Ig[j] = d.Ig[j]; n.rb[j] = d.rb[j]; }
     n.B = d.buoy_ratio * d.mass * kG;
     for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
+  }
+  for (int c = 0; c < n_classes; ++c) {   // tick kernels loaded before the first request
+    const cudaError_t e = s->class_const ? prepare_tick_pm0(classes[c].n_thr) : prepare_tick_pm1(classes[c].n_thr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(MG_ERR_CUDA);
+    }
   }
   if (cudaMemcpy(s->d_cls, cf.data(), sizeof(ClassF) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_nominal, cn.data(), sizeof(ClassNominal) * n_classes, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -632,6 +660,8 @@ int mg_server_submit(mg_server* s, const mg_request* r, int64_t* id_out) {
   const double h = s->cfg.dt / r->K;
   q.h = (float)h;
   const mg_class_desc& d = s->classes[r->cls];
+  for (int i = 0; i < d.n_thr; ++i)
+    if (d.deadzone[i] != 0.0) q.dz = 1;
   for (int i = 0; i < 8; ++i)
     q.alpha[i] = (i < d.n_thr && d.T_rotor[i] > 0) ? (float)(1.0 - std::exp(-h / d.T_rotor[i])) : 1.0f;
   q.t_submit = now_s();

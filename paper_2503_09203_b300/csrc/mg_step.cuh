@@ -498,15 +498,21 @@ __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& s
   }
 }
 
-// Actuator table of segment `sd` into one warp's copy (lanes of that warp).
-__device__ __forceinline__ void stage_act_warp(const StepArgs& a, const SegDesc& sd, float* act, int lane) {
+// Class tables of segment `sd` into one warp's copies (lanes of that warp):
+// the actuator table, and for class-constant ticks (PM = 0) the nominal
+// physics block. Serving ticks: propeller steps, rows as staged above.
+template <int PM>
+__device__ __forceinline__ void stage_tables_warp(const StepArgs& a, const SegDesc& sd, float* act, float* phys,
+                                                  int lane) {
   const ClassF& cf = a.classes[sd.cls];
-  for (int k = lane; k < SA_DIM; k += WENV) {   // serving: per-env propeller steps, rows as staged above
-    if (k < 48) act[k] = Premul<1, 0>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
+  for (int k = lane; k < SA_DIM; k += WENV) {
+    if (k < 48) act[k] = Premul<PM, 0>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
     else if (k < 56) act[k] = cf.kf[k - 48];
     else if (k < 64) act[k] = cf.dz[k - 56];
     else act[k] = sd.alpha[k - 64];
   }
+  if (PM == 0)
+    for (int k = lane; k < PAR_DIM; k += WENV) phys[k] = cf.phys[k];
 }
 
 // Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
@@ -897,10 +903,11 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   float* const buf1 = w_base + fl;
   float* const obs_sep = w_base + 2 * fl;   // separate observation tile (unless aliased)
   float* const s_par = s_dyn + N_WARPS * wfl;
-  // Serving ticks (TM) keep one actuator table per warp (their tiles change
-  // segment almost every time); other launches one per block.
+  // Serving ticks (TM) keep one actuator table (and, with class constants,
+  // one physics block) per warp: their tiles change segment almost every
+  // time. Other launches keep one per block.
   __shared__ __align__(16) float s_act[TM ? N_WARPS * SA_DIM : SA_DIM];
-  __shared__ __align__(16) float s_phys[PAR_DIM];
+  __shared__ __align__(16) float s_phys[TM ? N_WARPS * PAR_DIM : PAR_DIM];
   __shared__ __align__(16) float s_gen[VAR ? GEN_FLOATS : 4];
   __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
   __shared__ SegDesc s_seg[SEG_CACHE];
@@ -970,7 +977,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       // Per-env physics; the warp rewrites its own actuator table (its lanes
       // finished the previous tile at the warp barrier that ends each round).
       if (si != prev_seg) {
-        stage_act_warp(a, sd, s_act + warp * SA_DIM, lane);
+        stage_tables_warp<PM>(a, sd, s_act + warp * SA_DIM, s_phys + warp * PAR_DIM, lane);
         __syncwarp();
         prev_seg = si;
       }
@@ -995,7 +1002,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
     }
     if (!failed)
       step_tile<NT, PM, VAR, KP, MS, PA>(a, kc, kg, sd, tile, smem_addr(s_act + (TM ? warp * SA_DIM : 0)),
-                                 smem_addr(s_phys), smem_addr(s_gen), b ? buf1 : buf0,
+                                 smem_addr(s_phys + (TM ? warp * PAR_DIM : 0)), smem_addr(s_gen), b ? buf1 : buf0,
                                  MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     if (PA && !failed && tt_next < a.n_tiles) {
       // This thread is done with its parameter column: bring in the next tile's.
@@ -1125,7 +1132,8 @@ static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const Cla
                                   bool dependent, bool shared_sm, cudaStream_t st) {
   if (kc && var != 0 && !kg) return cudaErrorInvalidValue;
   if (a.act_mode == 1 && var == 0) {
-    if constexpr (PM == 1) {
+    // Serving ticks: per-env parameters (DR or current on), or class constants.
+    if constexpr (PM <= 1) {
       if (kc) return cudaErrorInvalidValue;
       return launch_step_pv<PM, 0, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
     } else {
@@ -1149,6 +1157,17 @@ static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const Cla
     case 5: return launch_step_pv<PM, 2, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Load the serving-tick kernel of thruster count nt (and set its attributes)
+// ahead of the first tick: with lazy module loading the first launch of each
+// kernel otherwise pays the load, and early requests queue behind it.
+template <int PM>
+static cudaError_t prepare_tick_pm(int nt) {
+#define MG_L(N) return step_attrs<N, PM, 0, false, true, false>()
+  MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  return cudaErrorInvalidValue;
 }
 
 template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>

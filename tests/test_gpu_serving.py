@@ -25,8 +25,8 @@ pytestmark = pytest.mark.gpu
 CFG = dict(vehicles.HOVER_DR)
 
 
-def run_alone(classes, req, budget=256 << 20):
-    srv = B.mg_server_create(classes, 0.01, budget_bytes=budget, max_requests=64, reset=CFG)
+def run_alone(classes, req, budget=256 << 20, cfg=CFG):
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=budget, max_requests=64, reset=cfg)
     rid = B.mg_server_submit(srv, *req)
     B.mg_server_wait_idle(srv, 120)
     out = B.mg_server_poll(srv, rid)
@@ -34,9 +34,9 @@ def run_alone(classes, req, budget=256 << 20):
     return out
 
 
-def oracle_request(classes, req):
+def oracle_request(classes, req, cfg=CFG):
     cls, n, horizon, K, seed = req
-    envs, s = oracle.reset(classes, np.full(n, cls, np.int32), CFG, seed)
+    envs, s = oracle.reset(classes, np.full(n, cls, np.int32), cfg, seed)
     a = np.zeros((horizon, n, 8), np.float32)
     nt = classes[cls]["n_thr"]
     for t in range(horizon):
@@ -47,12 +47,17 @@ def oracle_request(classes, req):
     return s, r.sum(0)
 
 
-def test_request_alone_equals_in_mix_and_matches_oracle():
+@pytest.mark.parametrize("cfg", [CFG, dict(vehicles.HOVER)], ids=["per_env_dr", "class_constants"])
+def test_request_alone_equals_in_mix_and_matches_oracle(cfg):
+    """Per-env DR and current (ticks read per-env parameter planes), or
+    neither (ticks read the class tables; the probe's class has a dead zone)."""
     classes = vehicles.five_classes()
+    if not cfg["dr_enabled"]:
+        classes[2] = dict(classes[2], deadzone=[0.25] * 6)
     probe = (2, 37, 40, 3, 1234567)
-    alone = run_alone(classes, probe)
+    alone = run_alone(classes, probe, cfg=cfg)
     assert alone["status"] == B.MG_REQ_DONE and alone["steps_done"] == 40
-    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=CFG)
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=cfg)
     rng = np.random.default_rng(0)
     # 60 others: each thruster-count group of a tick holds more segments than
     # the kernel keeps in shared memory, so tiles find theirs through the
@@ -74,7 +79,7 @@ def test_request_alone_equals_in_mix_and_matches_oracle():
     assert np.array_equal(mixed["returns"], alone["returns"])
     # Shared launches actually happened: fewer ticks than total request steps.
     assert st["ticks"] < sum(r[2] for r in others) + probe[2]
-    s_ref, ret_ref = oracle_request(classes, probe)
+    s_ref, ret_ref = oracle_request(classes, probe, cfg=cfg)
     err = rel_state_err(alone["final_state"].astype(np.float64), s_ref)
     assert err.max() <= 1e-3, err.max()
     np.testing.assert_allclose(alone["returns"], ret_ref, rtol=1e-4, atol=1e-3)
