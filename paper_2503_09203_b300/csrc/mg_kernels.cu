@@ -226,6 +226,8 @@ __device__ __forceinline__ void cp16_l2(unsigned dst, const float* src) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// All but the most recent group complete.
+__device__ __forceinline__ void cp_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Record of one env: state fields (canonical order p3 q4 nu6 n[NT]), rhs at 21.
 template <int NT>
@@ -243,12 +245,16 @@ __device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x,
   for (int k = 0; k < ADJ_REC / 4; ++k) r4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
-// Consumer-side prefetch slots of one lane: records [2][32][ADJ_REC] and
-// per-step data [2][ADJ_STEPF][32] of the block.
+// Consumer-side prefetch slots of one lane: a ring of ADJ_RING records
+// [ADJ_RING][32][ADJ_REC] (record j in slot j % ADJ_RING: while the reverse
+// pass works on record j, records j - 1 and j - 2 stream in) and a ring of
+// per-step data [ADJ_RING][ADJ_STEPF][32] (step t in slot t % ADJ_RING,
+// issued two steps ahead). Every issue is its own cp.async group.
+constexpr int ADJ_RING = 3;
 struct AdjPrefetch {
   float* rec;
   float* stp;
-  int lane, cur, scur;
+  int lane;
   __device__ __forceinline__ float* rslot(int b) const { return rec + (b * ADJ_ENVS + lane) * ADJ_REC; }
   __device__ __forceinline__ float* sslot(int b) const { return stp + b * ADJ_STEPF * ADJ_ENVS + lane; }
   __device__ __forceinline__ void issue_rec(const float* src, int b) const {
@@ -340,7 +346,7 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
   float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 tr[3] = {tg, tg, tg};
   float k_start = 0.0f;
-  AdjPrefetch pf{s_rec, s_step, lane, 0, 0};
+  AdjPrefetch pf{s_rec, s_step, lane};
   if (role == 0 && valid) {
     tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
     if (sd.track) {
@@ -357,8 +363,10 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
     for (int j = 0; j < NT; ++j) lam.n[j] = a.g_state_T ? a.g_state_T[slot * 21 + 13 + j] : 0.0f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) { g.A[j] = 0.0f; g.dl[j] = 0.0f; g.dq[j] = 0.0f; }
-    // The first step back (the last step of the rollout): its cotangents and actions.
-    pf.issue_step<NT>(a, sd, i, a.T - 1, 0);
+    // The first two steps back (the last steps of the rollout): their
+    // cotangents and actions.
+    pf.issue_step<NT>(a, sd, i, a.T - 1, (a.T - 1) % ADJ_RING);
+    if (a.T >= 2) pf.issue_step<NT>(a, sd, i, a.T - 2, (a.T - 2) % ADJ_RING);
   }
   float tgt[3] = {tg.x, tg.y, tg.z};
 
@@ -369,16 +377,15 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
       const float* rec0 = a.scratch + (int64_t)((it - 1) & 1) * buf_floats + slot * ADJ_REC;
-      int j = (t1 - t0) * K;   // record of the segment's end state
-      pf.issue_rec(rec0 + (int64_t)j * rstride, pf.cur);
-      cp_wait_all();
-      pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, pf.cur ^ 1);
+      int j = (t1 - t0) * K;   // record of the segment's end state (j >= 1)
+      pf.issue_rec(rec0 + (int64_t)j * rstride, j % ADJ_RING);
+      pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, (j - 1) % ADJ_RING);
+      cp_wait_but1();   // record j (record j - 1 was committed after it)
       for (int t = t1 - 1; t >= t0; --t) {
-        // Step t's cotangents and actions (issued one step ahead) and the
-        // next record are in shared memory after this wait.
-        cp_wait_all();
+        // Step t's cotangents and actions, issued two steps ahead: complete
+        // after the last wait (at least one record group followed them).
         float go[13], raw[NT], c[NT], lc[NT];
-        const float* sp = pf.sslot(pf.scur);
+        const float* sp = pf.sslot(t % ADJ_RING);
 #pragma unroll
         for (int q = 0; q < 13; ++q) go[q] = a.g_obs ? sp[ADJ_ENVS * q] : 0.0f;
         const float gr = a.g_rew ? sp[ADJ_ENVS * 13] : 0.0f;
@@ -388,23 +395,26 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
           c[q] = clamp1(raw[q]);
           lc[q] = 0.0f;
         }
-        pf.scur ^= 1;
-        if (t > 0) pf.issue_step<NT>(a, sd, i, t - 1, pf.scur);
+        if (t >= 2) pf.issue_step<NT>(a, sd, i, t - 2, (t - 2) % ADJ_RING);
         // State at the end of step t: record j (the segment's end on the
         // first step back, else the first substep record of step t + 1).
         St<float, NT> xe;
-        pf.read<NT>(pf.cur, xe, nullptr);
+        pf.read<NT>(j % ADJ_RING, xe, nullptr);
+        // After reading record j, record j - 2 is issued (records j and
+        // j - 1 were issued before): every record once, two ahead.
+        if (t == t1 - 1 && j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
         if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
         observe_vjp<float, NT>(xe, c, tgt, a.g_obs ? go : nullptr, gr, lam, lc);
         for (int k = K - 1; k >= 0; --k) {
-          if (k != K - 1) cp_wait_all();
-          pf.cur ^= 1;
           --j;
+          // Record j: record j - 1 was committed after it, except for j = 0.
+          if (j >= 1) cp_wait_but1();
+          else cp_wait_all();
           St<float, NT> xs;
           float rhs[6], q1[4];
-          pf.read<NT>(pf.cur, xs, rhs);
-          // Record j - 1 streams in while this substep's product runs.
-          if (j > 0) pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, pf.cur ^ 1);
+          pf.read<NT>(j % ADJ_RING, xs, rhs);
+          // Records j - 1 and j - 2 stream in while this substep's product runs.
+          if (j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
           Tape<float, NT> tp;
           tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
           vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g);
@@ -449,8 +459,8 @@ __device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, 
 template <int NT>
 __global__ void __launch_bounds__(ADJ_THREADS)
     mg_adjoint_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ ClassK kc) {
-  __shared__ __align__(16) float s_rec[2 * ADJ_ENVS * ADJ_REC];
-  __shared__ __align__(16) float s_step[2 * ADJ_STEPF * ADJ_ENVS];
+  __shared__ __align__(16) float s_rec[ADJ_RING * ADJ_ENVS * ADJ_REC];
+  __shared__ __align__(16) float s_step[ADJ_RING * ADJ_STEPF * ADJ_ENVS];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int parts = a.tile_envs / ADJ_ENVS;
   const int tile = a.tile_lo + (int)blockIdx.x / parts;
