@@ -743,7 +743,11 @@ def main():
                             f"consecutive steps ({trec['launches_per_step']} launches a step, write-backs included): "
                             f"{os.path.relpath(TRAFFIC_RECORD, ROOT)}"
                             if traffic else "null: no ncu record of these kernel sources at this workload")
-    roof.update({"kernel": f"mg_step_kernel<NT, 0, 0, 1, 0, 0> (class constants, propellers, Euler, class tables as the kernel parameter), {n_launches} launches per step",
+    shape = B.mg_get_launch_shape(sim.handle)
+    kname = ("mg_step_kernel<NT, 0, 0, 1, 0, 0, JitLit> (class constants as literals: one kernel per class compiled "
+             "at run time with NVRTC)" if shape["specialised_launches"] == n_launches else
+             "mg_step_kernel<NT, 0, 0, 1, 0, 0> (class tables as the kernel parameter)")
+    roof.update({"kernel": f"{kname}; propellers, Euler; {n_launches} launches per step", "launch_shape": shape,
                  "bytes_per_env_step": bpe, "flops_per_env_step": fpe,
                  "hbm_frac": achieved_gbs / pk["hbm_gbs"], "alu_frac": achieved_flops / alu_peak})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -402,6 +402,12 @@ int mg_test_wait_timeout(mg_sim* sim, uint64_t limit_ns, mg_stream_t stream);
  *   (recorded rollouts included); every other launch keeps one lane per env.
  *   Results agree with the one-lane kernel to rounding (the rows are summed
  *   in another order), not bit for bit.
+ * specialised: the class-specialised kernels are the one-lane step kernel
+ *   compiled again with the class's constants as literals, so that zero
+ *   allocation entries, a restoring arm on the body axis and W = B fold away;
+ *   the first launch of a class compiles its kernel (about half a second;
+ *   kept for the process). Results agree with the library-built kernel to
+ *   rounding.
  * The K substeps of a step (and the steps of a multi-step launch) always stay
  * in one launch with the state in registers: splitting them over launches
  * would only add state traffic. */
@@ -409,8 +415,13 @@ typedef struct {
   int32_t lanes_per_env;    /* 1 or 2 */
   int32_t envs_per_block;   /* 128 / lanes_per_env (output only) */
   int32_t blocks_per_sm;    /* one-lane launches: resident blocks per SM (0: occupancy limit) */
+  int32_t specialised;      /* 1 (default): one-lane launches of one class with class-constant
+                               parameters (propellers, Euler, hover task) run a kernel compiled at
+                               run time (NVRTC) with that class's constants as literals, when NVRTC
+                               is available; 0: the kernels built with the library */
+  double us_per_step;       /* mg_autotune: the chosen shape's measured time per step (output only) */
+  int32_t specialised_launches; /* output: launches of one step that run specialised kernels */
   int32_t pad0;
-  double us_per_step;       /* mg_autotune: the chosen shape's measured time per step */
 } mg_launch_shape;
 
 /* Choose the launch shape by timing candidates on `stream`: one lane per env
@@ -423,8 +434,10 @@ typedef struct {
  * actions of n_steps steps. Writes the choice into *out if not NULL. */
 int mg_autotune(mg_sim* sim, int32_t n_steps, mg_stream_t stream, mg_launch_shape* out);
 int mg_get_launch_shape(const mg_sim* sim, mg_launch_shape* out);
-/* Fix the launch shape by hand (lanes_per_env 1 or 2, blocks_per_sm >= 0);
- * takes effect from the next launch. Errors: INVALID_ARG. */
+/* Fix the launch shape by hand (lanes_per_env 1 or 2, blocks_per_sm >= 0,
+ * specialised 0 or 1); takes effect from the next launch. Errors:
+ * INVALID_ARG. mg_get_launch_shape compiles the specialised kernels of the
+ * current plan if they were not yet, to report specialised_launches. */
 int mg_set_launch_shape(mg_sim* sim, const mg_launch_shape* shape);
 
 /* Fix the persistent grid: blocks_per_sm resident blocks of each step launch

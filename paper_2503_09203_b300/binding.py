@@ -94,7 +94,8 @@ class mg_layout(C.Structure):
 
 class mg_launch_shape(C.Structure):
     _fields_ = [("lanes_per_env", C.c_int32), ("envs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("pad0", C.c_int32), ("us_per_step", C.c_double)]
+                ("specialised", C.c_int32), ("us_per_step", C.c_double), ("specialised_launches", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 class mg_server_config(C.Structure):
@@ -430,8 +431,9 @@ def mg_get_launch_shape(sim) -> dict:
     return _shape_dict(sh)
 
 
-def mg_set_launch_shape(sim, lanes_per_env: int = 1, blocks_per_sm: int = 0):
-    sh = mg_launch_shape(lanes_per_env=int(lanes_per_env), blocks_per_sm=int(blocks_per_sm))
+def mg_set_launch_shape(sim, lanes_per_env: int = 1, blocks_per_sm: int = 0, specialised: int = 1):
+    sh = mg_launch_shape(lanes_per_env=int(lanes_per_env), blocks_per_sm=int(blocks_per_sm),
+                         specialised=int(specialised))
     return _check(lib().mg_set_launch_shape(sim, C.byref(sh)), sim)
 
 

@@ -42,10 +42,36 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+# Kernel headers the library compiles again at run time (class-specialised
+# step kernels, NVRTC); embedded as strings in the library.
+JIT_HEADERS = ("mg_rtc.h", "mg_internal.h", "mg_device.cuh", "mg_step.cuh")
+
+
+def write_jit_sources(out_dir: str) -> None:
+    bodies = []
+    for name in JIT_HEADERS:
+        text = open(os.path.join(CSRC, name)).read()
+        if ")MGJIT" in text:
+            raise RuntimeError(f"{name} contains the raw-string delimiter")
+        bodies.append(text)
+    lines = ["// Generated by build.py: the kernel headers for the run-time compiler.",
+             f"static const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "static const char* const kJitHeaderNames[] = {" + ", ".join(f'"{n}"' for n in JIT_HEADERS) + "};",
+             "static const char* const kJitHeaderBodies[] = {"]
+    lines += [f'R"MGJIT({b})MGJIT",' for b in bodies]
+    lines.append("};")
+    path = os.path.join(out_dir, "mg_jit_sources.inc")
+    new = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != new:
+        with open(path, "w") as f:
+            f.write(new)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
+    write_jit_sources(BUILD_DIR)
     nvcc = _nvcc()
     objs = []
     procs = []
@@ -55,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         else:
-            cmd = [nvcc] + NVFLAGS + ["-x", "c++", "-c", src, "-o", obj]
+            cmd = [nvcc] + NVFLAGS + ["-I", BUILD_DIR, "-x", "c++", "-c", src, "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(obj)
     failed = False
@@ -69,7 +95,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("libmarinegym build failed")
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
+    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

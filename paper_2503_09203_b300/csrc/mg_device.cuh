@@ -18,11 +18,7 @@
 // vector-Jacobian products of both are here too.
 #pragma once
 
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdint.h>
-
-#include <type_traits>
+#include "mg_rtc.h"
 
 #define MG_HD __host__ __device__ __forceinline__
 
@@ -404,7 +400,7 @@ template <typename S, int NT, bool TAPE, typename ActT, typename PhysT, bool CUR
           typename GenT = NoGen>
 MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
                    Tape<S, NT>* tp, const GenT& G = GenT()) {
-  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
   S f[NT], tau[6];
   actuate<S, NT>(x, c, A, f, tau);
   if constexpr (GEN) tilt_wrench<S, NT>(G, x.n, f, tau);
@@ -464,7 +460,7 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
 template <typename S, int NT, typename PhysT, bool CURRENT, typename GenT>
 MG_HD void rk4_stage(const S q[4], const S nu[6], const S (&n)[NT], const S tau_n[6], const PhysT& P,
                      const GenT& G, S dp[3], S dq[4], S dnu[6]) {
-  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
   const S iq = minvsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   const S qh[4] = {q[0] * iq, q[1] * iq, q[2] * iq, q[3] * iq};
   S R[3][3];
@@ -493,7 +489,7 @@ MG_HD void rk4_stage(const S q[4], const S nu[6], const S (&n)[NT], const S tau_
 template <typename S, int NT, typename ActT, typename PhysT, bool CURRENT = true, typename GenT = NoGen>
 MG_HD void substep_rk4(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
                        const GenT& G = GenT()) {
-  constexpr bool GEN = !std::is_same<GenT, NoGen>::value;
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
   S f[NT], tau_n[6];
   actuate<S, NT>(x, c, A, f, tau_n);
   if constexpr (GEN) tilt_wrench<S, NT>(G, x.n, f, tau_n);

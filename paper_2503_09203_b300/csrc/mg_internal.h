@@ -1,9 +1,7 @@
 // Shared host/device records of libmarinegym (not part of the public C-ABI).
 #pragma once
 
-#include <cuda_runtime.h>
-#include <stddef.h>
-#include <stdint.h>
+#include "mg_rtc.h"
 
 namespace mg {
 
@@ -96,9 +94,11 @@ struct ClassD {
 // Per-env physical parameter block (36 floats, 9 float4 planes) field offsets.
 enum { PAR_MINV = 0, PAR_A = 6, PAR_DL = 12, PAR_DQ = 18, PAR_M = 24, PAR_IG = 25, PAR_W = 28,
        PAR_B = 29, PAR_RB = 30, PAR_VC = 33, PAR_DIM = 36 };
+#ifndef __CUDACC_RTC__
 static_assert(offsetof(ClassK, minv) == 4 * (72 + PAR_MINV) && offsetof(ClassK, m) == 4 * (72 + PAR_M) &&
                   offsetof(ClassK, Vc) == 4 * (72 + PAR_VC),
               "ClassK physical block follows the parameter block layout");
+#endif
 
 // Number of float4 parameter planes: 9 for the 36 physical floats + 1 target.
 // The target plane holds (c_x, c_y, c_z, k): the reference centre and the

@@ -26,6 +26,10 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
 cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err);
+cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
+                            bool shared_sm, cudaStream_t st);
+size_t step_kernel_smem(int nt, int pm, bool track);
 }  // namespace mg
 
 namespace mg {
@@ -61,6 +65,7 @@ struct mg_sim {
   int32_t threads = 128;
   int32_t blocks_per_sm = 0;   // persistent blocks per SM (0: occupancy limit)
   int32_t lanes = 1;           // lanes per env of eligible launches (1 or 2)
+  int32_t specialise = 1;      // class-specialised kernels for class-constant launches (when available)
   int32_t num_sms = 148;
   int32_t n_tiles = 0, n_segs = 0;
   double h = 0.0;
@@ -97,7 +102,13 @@ struct mg_sim {
     std::vector<Group> groups;     // the launches of a step
     bool first_pdl = false;        // the first launch is a programmatic dependent too
     std::vector<ClassK> kc;        // constants of each launch with cls >= 0
+    // Class-specialised kernels of each launch ([0] single-step, [1]
+    // multi-step instantiation), compiled on first use; null: none.
+    std::vector<const void*> jit[2];
+    std::vector<char> jit_tried[2];
+    std::vector<int> jit_grid[2];
   } plan, plan_ms;                 // single-step launches; multi-step launches
+  std::string jit_err;             // why the last specialised kernel could not be had
   std::vector<ClassF> h_cls;       // host copies of the class tables
   std::vector<ClassG> h_gen;
   // mg_step_host: copy streams and events of the chunked pipeline.
@@ -808,9 +819,53 @@ static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
   if (!p.cores)
     for (const Group& g : p.groups)
       if (g.var != 0) p.first_pdl = false;
+  for (int v = 0; v < 2; ++v) {
+    p.jit[v].assign(n, nullptr);
+    p.jit_tried[v].assign(n, 0);
+    p.jit_grid[v].assign(n, 1);
+  }
   p.bps = sim->blocks_per_sm;
   p.valid = true;
   return p;
+}
+
+// Whether launch i of a plan may run a class-specialised kernel: one class
+// with class-constant parameters, propellers with the Euler substep, the
+// hover task.
+static bool jit_eligible(const mg_sim* sim, const Group& g) {
+  return sim->specialise && g.cls >= 0 && g.var == 0 && param_mode(sim) == 0 && sim->cfg.task == 0;
+}
+
+// The class-specialised kernel of launch i (single- or multi-step
+// instantiation), compiled on first use, and its persistent grid; null if
+// there is none (not eligible, NVRTC missing, compile failed).
+static const void* plan_jit(mg_sim* sim, mg_sim::Plan& p, size_t i, bool ms) {
+  const Group& g = p.groups[i];
+  const int v = ms ? 1 : 0;
+  if (!jit_eligible(sim, g)) return nullptr;
+  if (!p.jit_tried[v][i]) {
+    p.jit_tried[v][i] = 1;
+    std::string err;
+    const void* k = jit_step_kernel(p.kc[i], g.nt, ms, &err);
+    if (!k) sim->jit_err = err;
+    int occ = 0;
+    if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem(g.nt, 0, false)) !=
+                 cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
+    if (k && occ >= 1) {
+      const int bps = sim->blocks_per_sm > 0 ? std::min(sim->blocks_per_sm, occ) : occ;
+      p.jit[v][i] = k;
+      // Same launch shape as the kernel it replaces: a persistent grid, or
+      // (one-wave plans) a block per tile.
+      p.jit_grid[v][i] = p.grid[i] == p.full_grid[i] ? std::max(1, std::min(g.n_tiles, bps * sim->num_sms))
+                                                      : p.grid[i];
+    } else if (k) {
+      sim->jit_err = "specialised kernel does not fit an SM";
+    }
+  }
+  return p.jit[v][i];
 }
 
 // Launches of at least this many steps use the multi-step plan. Measured:
@@ -844,8 +899,13 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     // step's other launches start, so its blocks only become resident and set
     // up early.
     a.wait_first = first && p.first_pdl;
+    const bool ms = g.var == 0 && a.act_mode == 0 && a.n_steps > 1;   // the kernels' multi-step instantiation
+    const void* jk = nullptr;
     if (sim->lanes == 2 && pair_eligible(sim, g, a))
       CK(launch_pair(a, p.kc[i], g.nt, !first || p.first_pdl, st));
+    else if ((jk = plan_jit(sim, const_cast<mg_sim::Plan&>(p), i, ms)) != nullptr)
+      CK(launch_step_jit(jk, a, p.kc[i], g.nt, p.jit_grid[ms ? 1 : 0][i], !first || p.first_pdl, p.carve_max[i] != 0,
+                         st));
     else
       CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
                      p.grid[i], !first || p.first_pdl, p.carve_max[i] != 0, st));
@@ -1028,9 +1088,15 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     a.tile_lo = tile_lo;
     a.n_tiles = ch.nt;
     a.wait_first = 0;
-    CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt,
-                   g.var, std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false, carveout_max(sim, g, false),
-                   st));
+    const bool ms = g.var == 0 && n_steps > 1;
+    const void* jk = plan_jit(sim, const_cast<mg_sim::Plan&>(plan), ch.g, ms);
+    if (jk)
+      CK(launch_step_jit(jk, a, plan.kc[ch.g], g.nt, std::max(1, std::min(ch.nt, plan.jit_grid[ms ? 1 : 0][ch.g])), false,
+                         carveout_max(sim, g, false), st));
+    else
+      CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt,
+                     g.var, std::max(1, std::min(ch.nt, plan.full_grid[ch.g])), false, carveout_max(sim, g, false),
+                     st));
     CK(cudaEventRecord(ev_done, st));
     CK(cudaStreamWaitEvent(sim->s_out, ev_done, 0));
     for (const Range& r : ranges) {
@@ -1541,6 +1607,13 @@ int mg_get_launch_shape(const mg_sim* sim, mg_launch_shape* out) {
   out->lanes_per_env = sim->lanes;
   out->envs_per_block = sim->threads / sim->lanes;
   out->blocks_per_sm = sim->blocks_per_sm;
+  out->specialised = sim->specialise;
+  // Launches of a single step that run class-specialised kernels (compiled
+  // here if they were not yet).
+  mg_sim* s = const_cast<mg_sim*>(sim);
+  mg_sim::Plan& p = const_cast<mg_sim::Plan&>(step_plan(s));
+  for (size_t i = 0; i < p.groups.size(); ++i)
+    if (plan_jit(s, p, i, false)) out->specialised_launches++;
   return MG_OK;
 }
 
@@ -1550,8 +1623,14 @@ int mg_set_launch_shape(mg_sim* sim, const mg_launch_shape* shape) {
     return fail(sim, MG_ERR_INVALID_ARG, "set_launch_shape: lanes_per_env %d not 1 or 2", shape->lanes_per_env);
   if (shape->blocks_per_sm < 0)
     return fail(sim, MG_ERR_INVALID_ARG, "set_launch_shape: negative blocks_per_sm %d", shape->blocks_per_sm);
+  if (shape->specialised != 0 && shape->specialised != 1)
+    return fail(sim, MG_ERR_INVALID_ARG, "set_launch_shape: specialised %d not 0 or 1", shape->specialised);
   sim->lanes = shape->lanes_per_env;
   sim->blocks_per_sm = shape->blocks_per_sm;
+  if (sim->specialise != shape->specialised) {
+    sim->specialise = shape->specialised;
+    sim->plan.valid = sim->plan_ms.valid = false;
+  }
   return MG_OK;
 }
 

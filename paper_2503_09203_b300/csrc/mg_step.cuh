@@ -20,13 +20,12 @@
 // tensor-core paths.
 #pragma once
 
-#include <cuda_runtime.h>
-#include <stdint.h>
-
+#include "mg_rtc.h"
+#ifndef __CUDACC_RTC__
 #include <atomic>
-#include <type_traits>
 
 #include "marinegym.h"
+#endif
 #include "mg_internal.h"
 #include "mg_device.cuh"
 
@@ -373,8 +372,10 @@ static_assert(PAY_W < PF_PAY_PLANES * 4, "staged payload planes hold the step's 
 // GEN_VALS values per channel (a copy of the class's ClassG).
 constexpr int GEN_FLOATS = 8 + 8 * GEN_VALS;
 static_assert(sizeof(ClassG) == GEN_FLOATS * sizeof(float), "generic table layout");
+#ifndef __CUDACC_RTC__
 static_assert(KIND_PROP == MG_ACT_PROP && KIND_SERVO == MG_ACT_SERVO && KIND_FIN == MG_ACT_FIN &&
                   KIND_TILT == MG_ACT_TILT, "actuator kinds");
+#endif
 // Generic actuator table passed as the kernel parameter (KP launches).
 struct GenK {
   const ClassG& g;
@@ -674,7 +675,7 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
     }
   }
   // Each thread reads only its own parameter column: no barrier needed.
-  using PV = std::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
+  using PV = tt::conditional_t<PM == 2, PhysSmemFull<STEP_BLK>, PhysSmem<PER_ENV ? STEP_BLK : 1>>;
   const unsigned p_base = PER_ENV ? smem_addr(s_par) + 4u * tid : s_phys;
   const unsigned g_base = s_gen;
   const int n_out_steps = a.n_steps == 0 ? 1 : a.n_steps;
@@ -736,9 +737,9 @@ __device__ __forceinline__ bool step_tile(const StepArgs& a, const ClassK* kc, c
       // (generic table). Class-constant physics carries no current (zero by
       // construction): CURRENT = PER_ENV.
       auto sub = [&](const auto& P, const auto& Av, const auto& G) {
-        using PT = std::decay_t<decltype(P)>;
-        using AT = std::decay_t<decltype(Av)>;
-        using GT = std::decay_t<decltype(G)>;
+        using PT = tt::decay_t<decltype(P)>;
+        using AT = tt::decay_t<decltype(Av)>;
+        using GT = tt::decay_t<decltype(G)>;
         if constexpr (VAR == 2) substep_rk4<float, NT, AT, PT, PER_ENV, GT>(x, c, P, Av, sd.h, G);
         else substep<float, NT, false, AT, PT, PER_ENV, GT>(x, c, P, Av, sd.h, nullptr, G);
       };
@@ -876,8 +877,18 @@ struct StepMinBlocks {
 // Second kernel parameter: the class tables of a KP launch (ClassK, plus the
 // generic table for VAR >= 1), else nothing.
 struct NoClassK {};
+
+// Class constants known when the kernel is compiled: the class-specialised
+// step kernels that the library compiles at run time (NVRTC) for
+// class-constant launches take a type whose make() returns the class's
+// ClassK, so that the arithmetic sees literals (zero allocation entries, a
+// zero restoring arm, W = B drop out). NoLit: the constants come from the
+// kernel parameter.
+struct NoLit {
+  MG_HD static constexpr ClassK make() { return ClassK{}; }
+};
 template <bool KP, int VAR>
-using KParam = std::conditional_t<!KP, NoClassK, std::conditional_t<VAR == 0, ClassK, ClassKG>>;
+using KParam = tt::conditional_t<!KP, NoClassK, tt::conditional_t<VAR == 0, ClassK, ClassKG>>;
 
 // PM: parameter source (0 class constants, 1 per-env planes, 2 per-env planes
 // with the payload). KP: the launch holds one class and its tables travel as
@@ -886,15 +897,19 @@ using KParam = std::conditional_t<!KP, NoClassK, std::conditional_t<VAR == 0, Cl
 // launch of several steps prefetches each next step's actions. The
 // body stays in the kernel itself: moved into a function taking the
 // parameters by reference, the per-env and payload instantiations spilled.
-template <int NT, int PM, int VAR, bool KP, bool TM, bool MS>
+template <int NT, int PM, int VAR, bool KP, bool TM, bool MS, class LIT = NoLit>
 __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::value))
     mg_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ KParam<KP, VAR> kp) {
   using SG = Stage<NT>;
   constexpr bool PA = PM == 1 && !TM && MG_PAR_ASYNC;
+  constexpr bool HAS_LIT = !tt::is_same<LIT, NoLit>::value;
+  static_assert(!HAS_LIT || (KP && PM == 0 && VAR == 0 && !TM), "literal class constants: one-class propeller launches");
   const ClassK* kc = nullptr;
   const ClassG* kg = nullptr;
   if constexpr (KP && VAR == 0) kc = &kp;
   if constexpr (KP && VAR != 0) { kc = &kp.k; kg = &kp.g; }
+  [[maybe_unused]] constexpr ClassK klit = LIT::make();
+  if constexpr (HAS_LIT) kc = &klit;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0);
@@ -1022,6 +1037,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------
 // Host-side launch templates of the step kernel. Each parameter source is
 // instantiated in its own translation unit (mg_step_pm0/1/2.cu) so that the
@@ -1198,5 +1214,7 @@ static cudaError_t occupancy_pm(int nt, int var, bool kp, bool track, int* block
     default: return cudaErrorInvalidValue;
   }
 }
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace mg
