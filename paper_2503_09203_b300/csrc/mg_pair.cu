@@ -117,6 +117,11 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
   const int64_t slot = sd.slot_off + i;
   float* st_base = a.state + sd.st_off;
   const float h = sd.h;
+  // Per-step fields in registers (a reference into global memory would be
+  // read again after every observation store).
+  const int K = sd.K;
+  const int64_t n4 = sd.n4;
+  const float* act_env = a.actions + sd.act_off + i * NT;
 
   // Parameters of this lane's half.
   PairHalf<NT> Q;
@@ -171,13 +176,13 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
   for (int j = 0; j < 6; ++j) x.nu[j] = 0.0f;
 #pragma unroll
   for (int j = 0; j < NT; ++j) x.n[j] = 0.0f;
-  if (valid) pair_load_state<NT>(st_base, sd.n4, i, x);
+  if (valid) pair_load_state<NT>(st_base, n4, i, x);
   const float tgt[3] = {tg.x, tg.y, tg.z};
 
   float c[NT], cn[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) c[j] = cn[j] = 0.0f;
-  if (valid) pair_actions<NT>(a.actions + sd.act_off + i * NT, cn);
+  if (valid) pair_actions<NT>(act_env, cn);
   float r_last = 0.0f;
   for (int t = 0; t < a.n_steps; ++t) {
     if (a.ckpt && (t % a.ckpt_every) == 0 && valid && hsel == 0) {
@@ -195,8 +200,8 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
 #pragma unroll
     for (int j = 0; j < NT; ++j) c[j] = pclamp(cn[j]);
     // The next step's actions are in flight while this step computes.
-    if (valid && t + 1 < a.n_steps) pair_actions<NT>(a.actions + (int64_t)(t + 1) * a.act_stride + sd.act_off + i * NT, cn);
-    for (int k = 0; k < sd.K; ++k) {
+    if (valid && t + 1 < a.n_steps) pair_actions<NT>(act_env + (int64_t)(t + 1) * a.act_stride, cn);
+    for (int k = 0; k < K; ++k) {
       // a1 + a2: every rotor in both lanes; the lane's three wrench rows.
       float f[NT];
       if (kc.dz_on) {
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
     }
   }
   if (valid && hsel == 0 && a.n_steps > 0) {
-    pair_store_state<NT>(st_base, sd.n4, i, x);
+    pair_store_state<NT>(st_base, n4, i, x);
     // Finite exactly when the last reward (p, nu, c) and q, n are.
     float s = r_last;
 #pragma unroll
