@@ -213,8 +213,21 @@ __device__ __forceinline__ void st21(float* base, int64_t stride, const St<float
   for (int j = 0; j < 13 + NT; ++j) base[j * stride] = f[j];
 }
 
-constexpr int ADJ_ENVS = 32;                 // envs per block
-constexpr int ADJ_THREADS = 2 * ADJ_ENVS;    // warp 0: reverse pass, warp 1: forward recompute
+#ifndef MG_ADJ_ENVS
+#define MG_ADJ_ENVS 32
+#endif
+constexpr int ADJ_ENVS = MG_ADJ_ENVS;        // envs per block
+constexpr int ADJ_THREADS = 2 * ADJ_ENVS;    // first half: reverse pass, second half: forward recompute
+static_assert(ADJ_ENVS % 32 == 0, "whole warps per role");
+
+// The fields of the launch's segment that the adjoint reads, held in
+// registers: read through a reference into global memory, each use after a
+// global store (records, action gradients) would be a fresh dependent load.
+struct AdjSeg {
+  int64_t act_off, slot_off;
+  float h, dt;
+  int K, track;
+};
 constexpr int ADJ_STEPF = 14 + 8;            // per-step slot: g_obs 13, g_rew 1, actions 8
 static_assert(ADJ_REC % 4 == 0 && ADJ_REC >= 27, "record of whole 16-byte vectors");
 
@@ -283,7 +296,7 @@ struct AdjPrefetch {
   }
   // Step t's cotangents and actions into per-step slot b.
   template <int NT>
-  __device__ __forceinline__ void issue_step(const AdjArgs& a, const SegDesc& sd, int64_t i, int t, int b) const {
+  __device__ __forceinline__ void issue_step(const AdjArgs& a, const AdjSeg& sd, int64_t i, int t, int b) const {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(sslot(b));
     const int64_t slot = sd.slot_off + i;
     if (a.g_obs) {
@@ -302,7 +315,7 @@ struct AdjPrefetch {
 // Producer: recompute segment s from its checkpoint into the records of
 // buffer `buf` (record j of this env at buf + (j * n_slots + slot) * ADJ_REC).
 template <int NT, typename ActT>
-__device__ __forceinline__ void adj_produce(const AdjArgs& a, const SegDesc& sd, const ActT& A, const Phys<float>& P,
+__device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const Phys<float>& P,
                                             int64_t i, int s, float* buf) {
   const int64_t ns = a.n_slots, slot = sd.slot_off + i;
   const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
@@ -327,8 +340,8 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const SegDesc& sd,
 }
 
 template <int NT, typename ActT>
-__device__ void adjoint_env(const AdjArgs& a, const SegDesc& sd, const ActT& A, int64_t i, bool valid,
-                            float* s_rec, float* s_step) {
+__device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, const ActT& A, int64_t i, bool valid,
+                                            float* s_rec, float* s_step) {
   const int role = threadIdx.x / ADJ_ENVS;   // 0: reverse pass, 1: forward recompute
   const int lane = threadIdx.x % ADJ_ENVS;
   const int64_t slot = sd.slot_off + i;
@@ -477,7 +490,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
       if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
     }
     // Every thread of the block takes part in the per-segment barriers.
-    adjoint_env<NT>(a, sd, kc, i, valid, s_rec, s_step);
+    const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track};
+    adjoint_env<NT>(a, sr, kc, i, valid, s_rec, s_step);
   }
   // Completion stays ordered along the stream (see the step kernel).
   asm volatile("griddepcontrol.wait;" ::: "memory");
