@@ -188,7 +188,10 @@ __global__ void mg_set_hydro_kernel(float4* planes, int64_t n_slots, const float
 // warp 0 (the consumer) runs the vector-Jacobian products of segment s, so
 // the forward recompute leaves the consumer's dependent chain. Per substep
 // and env the producer stores one record: the start state and the
-// right-hand side M nu_dot of a4-a7 (ADJ_REC floats, seven 16-byte vectors);
+// right-hand side M nu_dot of a4-a7 (ADJ_REC floats, seven 16-byte vectors;
+// in the scratch buffer the records of four consecutive slots interleave by
+// vector, so that a warp's stores and copies of one vector touch whole 64-byte
+// runs);
 // the consumer rebuilds the rest of the substep's tape from it (rotor
 // states, R, current, the new velocity and attitude: a few dozen operations
 // instead of the full substep) and applies its VJP. Two scratch buffers
@@ -242,7 +245,10 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_grou
 // All but the most recent group complete.
 __device__ __forceinline__ void cp_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Record of one env: state fields (canonical order p3 q4 nu6 n[NT]), rhs at 21.
+// Record of one env: state fields (canonical order p3 q4 nu6 n[NT]), rhs at
+// 21. In the scratch buffer, record j of slot s starts at
+// j * n_slots * ADJ_REC + rec_off(s) and its vector k lies 16 k floats further.
+__device__ __forceinline__ int64_t rec_off(int64_t s) { return (s >> 2) * (4 * ADJ_REC) + (s & 3) * 4; }
 template <int NT>
 __device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x, const float* rhs) {
   float sf[13 + NT], f[ADJ_REC];
@@ -255,7 +261,7 @@ __device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x,
   for (int j = 27; j < ADJ_REC; ++j) f[j] = 0.0f;
   float4* r4 = reinterpret_cast<float4*>(rec);
 #pragma unroll
-  for (int k = 0; k < ADJ_REC / 4; ++k) r4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+  for (int k = 0; k < ADJ_REC / 4; ++k) r4[4 * k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
 // Consumer-side prefetch slots of one lane: a ring of ADJ_RING records
@@ -273,7 +279,7 @@ struct AdjPrefetch {
   __device__ __forceinline__ void issue_rec(const float* src, int b) const {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(rslot(b));
 #pragma unroll
-    for (int k = 0; k < ADJ_REC / 4; ++k) cp16_l2(dst + 16u * k, src + 4 * k);
+    for (int k = 0; k < ADJ_REC / 4; ++k) cp16_l2(dst + 16u * k, src + 16 * k);
     cp_commit();
   }
   template <int NT>
@@ -313,7 +319,7 @@ struct AdjPrefetch {
 };
 
 // Producer: recompute segment s from its checkpoint into the records of
-// buffer `buf` (record j of this env at buf + (j * n_slots + slot) * ADJ_REC).
+// buffer `buf`.
 template <int NT, typename ActT>
 __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const Phys<float>& P,
                                             int64_t i, int s, float* buf) {
@@ -321,7 +327,7 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
   const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
   St<float, NT> x;
   ld21<NT>(a.ckpt + (int64_t)s * 21 * ns + slot, ns, x);
-  float* rec = buf + slot * ADJ_REC;
+  float* rec = buf + rec_off(slot);
   const int64_t rstride = ns * ADJ_REC;
   for (int t = t0; t < t1; ++t) {
     float raw[NT], c[NT];
@@ -389,7 +395,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
     if (role == 0 && it >= 1 && valid) {
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
-      const float* rec0 = a.scratch + (int64_t)((it - 1) & 1) * buf_floats + slot * ADJ_REC;
+      const float* rec0 = a.scratch + (int64_t)((it - 1) & 1) * buf_floats + rec_off(slot);
       int j = (t1 - t0) * K;   // record of the segment's end state (j >= 1)
       pf.issue_rec(rec0 + (int64_t)j * rstride, j % ADJ_RING);
       pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, (j - 1) % ADJ_RING);
