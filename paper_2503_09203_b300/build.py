@@ -44,7 +44,7 @@ def _stale() -> bool:
 
 # Kernel headers the library compiles again at run time (class-specialised
 # step kernels, NVRTC); embedded as strings in the library.
-JIT_HEADERS = ("mg_rtc.h", "mg_internal.h", "mg_device.cuh", "mg_step.cuh")
+JIT_HEADERS = ("mg_rtc.h", "mg_internal.h", "mg_device.cuh", "mg_step.cuh", "mg_adjoint.cuh")
 
 
 def write_jit_sources(out_dir: str) -> None:

@@ -696,8 +696,9 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     lrhs[j] = h * P.minv[j] * lnu1[j];
-    // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2
-    g.A[j] = g.A[j] - h * tp.rhs[j] * lnu1[j] * P.minv[j] * P.minv[j];
+    // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2, and
+    // h minv^2 lnu1 rhs = minv lrhs rhs.
+    g.A[j] = g.A[j] - tp.rhs[j] * lrhs[j] * P.minv[j];
   }
   S lnu[6];
 #pragma unroll
@@ -714,10 +715,9 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
   const S WmB = P.W - P.B;
   const S Brb[3] = {P.B * P.rb[0], P.B * P.rb[1], P.B * P.rb[2]};
   {
-    S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
-    S dummy[3] = {z0, z0, z0};
-    S e[3] = {tp.R[2][0], tp.R[2][1], tp.R[2][2]};
-    cross_vjp(Brb, e, nl, dummy, le);
+    // d/de of -(B rb) x e contracted with lrhs_ang: (-lrhs_ang) x (B rb).
+    const S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    cross3(nl, Brb, le);
 #pragma unroll
     for (int j = 0; j < 3; ++j) le[j] = le[j] + WmB * lrhs[j];
   }
@@ -735,33 +735,31 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
     g.dl[3 + j] = g.dl[3 + j] + ldw * w[j];
     g.dq[3 + j] = g.dq[3 + j] + ldw * b * w[j];
   }
-  // C_RB: m w x v ; w x (Ig o w)
+  // C_RB + C_A in the forward's merged form: rhs_lin -= w x bl with
+  // bl = m v + a1; rhs_ang -= w x ba + vr x a1 with ba = A_ang o w + Ig o w;
+  // a1 = A_lin o vr.
   {
-    S ly[3] = {-P.m * lrhs[0], -P.m * lrhs[1], -P.m * lrhs[2]};
-    cross_vjp(w, v, ly, lw, lv);
-    S Iw[3] = {P.Ig[0] * w[0], P.Ig[1] * w[1], P.Ig[2] * w[2]};
-    S ly2[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
-    S lIw[3] = {z0, z0, z0};
-    cross_vjp(w, Iw, ly2, lw, lIw);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) lw[j] = lw[j] + P.Ig[j] * lIw[j];
-  }
-  // C_A: w x a1 ; vr x a1 + w x a2, a1 = A_lin vr, a2 = A_ang w
-  {
-    S a1[3] = {P.A[0] * vr[0], P.A[1] * vr[1], P.A[2] * vr[2]};
-    S a2[3] = {P.A[3] * w[0], P.A[4] * w[1], P.A[5] * w[2]};
-    S la1[3] = {z0, z0, z0}, la2[3] = {z0, z0, z0};
-    S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
-    S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
-    cross_vjp(w, a1, nl, lw, la1);
-    cross_vjp(vr, a1, na, lvr, la1);
-    cross_vjp(w, a2, na, lw, la2);
+    S a1[3], bl[3], ba[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
+      a1[j] = P.A[j] * vr[j];
+      bl[j] = P.m * v[j] + a1[j];
+      ba[j] = P.A[3 + j] * w[j] + P.Ig[j] * w[j];
+    }
+    S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
+    S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    S lbl[3] = {z0, z0, z0}, lba[3] = {z0, z0, z0}, la1[3] = {z0, z0, z0};
+    cross_vjp(w, bl, nl, lw, lbl);
+    cross_vjp(w, ba, na, lw, lba);
+    cross_vjp(vr, a1, na, lvr, la1);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lv[j] = lv[j] + P.m * lbl[j];
+      la1[j] = la1[j] + lbl[j];
+      lw[j] = lw[j] + P.A[3 + j] * lba[j] + P.Ig[j] * lba[j];
+      g.A[3 + j] = g.A[3 + j] + lba[j] * w[j];
       g.A[j] = g.A[j] + la1[j] * vr[j];
       lvr[j] = lvr[j] + la1[j] * P.A[j];
-      g.A[3 + j] = g.A[3 + j] + la2[j] * w[j];
-      lw[j] = lw[j] + la2[j] * P.A[3 + j];
     }
     // current-acceleration term A_lin o (w x vc)
     S wxvc[3];

@@ -1,4 +1,4 @@
-// Class-specialised step kernels compiled at run time (NVRTC).
+// Class-specialised step and adjoint kernels compiled at run time (NVRTC).
 //
 // A class-constant launch (one class, propellers, Euler, hover task) reads
 // its class tables as constant-bank operands: the arithmetic cannot know that
@@ -7,11 +7,13 @@
 // lies on the body z axis, or that a neutral vehicle has W = B. Compiled with
 // the class's values as literals, those terms fold away. This file builds
 // such kernels from the library's own kernel headers (embedded at build
-// time): one NVRTC program per (device architecture, thruster count,
+// time): one NVRTC program per (device architecture, kernel, thruster count,
 // single- or multi-step launch, class table), compiled to a cubin for the
 // device and loaded as a CUDA library; compiled kernels are kept for the
-// process. NVRTC is loaded with dlopen: without it (or if a compile fails)
-// the launches keep the kernels built with the library.
+// process. The adjoint kernel takes only the actuator tables as literals
+// (its physical parameters are per env). NVRTC is loaded with dlopen:
+// without it (or if a compile fails) the launches keep the kernels built
+// with the library.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -94,8 +96,9 @@ std::string lit(float v) {
   return b;
 }
 
-std::string class_source(const ClassK& k) {
-  std::string s = "#include \"mg_step.cuh\"\nnamespace mg {\nstruct JitLit {\n  MG_HD static constexpr ClassK make() {\n    ClassK k{};\n";
+std::string class_source(const ClassK& k, const char* header) {
+  std::string s = std::string("#include \"") + header +
+                  "\"\nnamespace mg {\nstruct JitLit {\n  MG_HD static constexpr ClassK make() {\n    ClassK k{};\n";
   auto arr = [&](const char* name, const float* v, int n) {
     for (int i = 0; i < n; ++i) s += std::string("    k.") + name + "[" + std::to_string(i) + "] = " + lit(v[i]) + ";\n";
   };
@@ -118,22 +121,25 @@ std::string class_source(const ClassK& k) {
   return s;
 }
 
-std::string kernel_name(int nt, bool ms) {
+enum Kind { STEP = 0, ADJOINT = 1 };
+
+std::string kernel_name(Kind kind, int nt, bool ms) {
+  if (kind == ADJOINT) return "mg::mg_adjoint_kernel<" + std::to_string(nt) + ", mg::JitLit>";
   return "mg::mg_step_kernel<" + std::to_string(nt) + ", 0, 0, true, false, " + (ms ? "true" : "false") +
          ", mg::JitLit>";
 }
 
 // Compile and load one specialised kernel (caller holds g_mu).
-void build(Entry& e, const ClassK& k, int nt, bool ms, int arch) {
+void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) { e.failed = true; e.err = "NVRTC not available"; return; }
-  const std::string src = class_source(k);
+  const std::string src = class_source(k, kind == ADJOINT ? "mg_adjoint.cuh" : "mg_step.cuh");
   nvrtcProgram prog = nullptr;
   if (n.create(&prog, src.c_str(), "mg_jit_step.cu", kJitHeaderCount, kJitHeaderBodies, kJitHeaderNames) !=
       NVRTC_SUCCESS) {
     e.failed = true; e.err = "nvrtcCreateProgram failed"; return;
   }
-  const std::string name = kernel_name(nt, ms);
+  const std::string name = kernel_name(kind, nt, ms);
   n.add_name(prog, name.c_str());
   const std::string arch_opt = "--gpu-architecture=sm_" + std::to_string(arch) + "a";
   const char* opts[] = {arch_opt.c_str(), "-std=c++17", "-default-device", "-lineinfo"};
@@ -165,6 +171,7 @@ void build(Entry& e, const ClassK& k, int nt, bool ms, int arch) {
     e.kern = nullptr;
     return;
   }
+  if (kind == ADJOINT) return;   // static shared memory only
   const int smem = (int)step_kernel_smem(nt, 0, false);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess) {
@@ -175,12 +182,7 @@ void build(Entry& e, const ClassK& k, int nt, bool ms, int arch) {
   }
 }
 
-}  // namespace
-
-// The class-specialised one-class propeller step kernel for class table k
-// (nt thrusters; ms: the multi-step instantiation) on the current device, or
-// null if it cannot be had (err says why).
-const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err) {
+const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, std::string* err) {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) !=
                                                 cudaSuccess ||
@@ -191,15 +193,30 @@ const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err) 
   }
   const int arch = major * 10 + minor;
   std::string key(reinterpret_cast<const char*>(&k), sizeof(k));
-  key += ":" + std::to_string(dev) + ":" + std::to_string(arch) + ":" + std::to_string(nt) + (ms ? ":ms" : ":1");
+  key += ":" + std::to_string((int)kind) + ":" + std::to_string(dev) + ":" + std::to_string(arch) + ":" +
+         std::to_string(nt) + (ms ? ":ms" : ":1");
   std::lock_guard<std::mutex> lk(g_mu);
   Entry& e = g_cache[key];
-  if (!e.kern && !e.failed) build(e, k, nt, ms, arch);
+  if (!e.kern && !e.failed) build(e, kind, k, nt, ms, arch);
   if (e.failed) {
     if (err) *err = e.err;
     return nullptr;
   }
   return reinterpret_cast<const void*>(e.kern);
+}
+
+}  // namespace
+
+// The class-specialised one-class propeller step kernel for class table k
+// (nt thrusters; ms: the multi-step instantiation) on the current device, or
+// null if it cannot be had (err says why).
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err) {
+  return jit_kernel(STEP, k, nt, ms, err);
+}
+
+// The class-specialised adjoint kernel for class table k (nt thrusters).
+const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err) {
+  return jit_kernel(ADJOINT, k, nt, false, err);
 }
 
 // Launch of a class-specialised kernel (same arguments and launch shape as

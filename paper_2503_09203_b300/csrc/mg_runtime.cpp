@@ -23,10 +23,12 @@ cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, i
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
-cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st,
+                           const void* jit_kernel);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
 const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err);
+const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err);
 cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st);
 size_t step_kernel_smem(int nt, int pm, bool track);
@@ -1131,7 +1133,15 @@ static int launch_backward(mg_sim* sim, AdjArgs a, cudaStream_t st) {
       g.cls = sd.cls;
       const ClassK kc = class_k(sim, g);
       a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-      CK(launch_adjoint(a, kc, g.nt, !first, st));
+      // The class-specialised kernel (its actuator tables as literals) when
+      // it can be had; the library's otherwise.
+      const void* jk = nullptr;
+      if (sim->specialise) {
+        std::string err;
+        jk = jit_adjoint_kernel(kc, g.nt, &err);
+        if (!jk) sim->jit_err = err;
+      }
+      CK(launch_adjoint(a, kc, g.nt, !first, st, jk));
       first = false;
     }
   }
