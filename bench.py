@@ -495,7 +495,7 @@ def adjoint_bench(stream, E=8192, T=200, K=4, ckpt=20, pk=None):
            "fp32_tflops": (f_fwd + f_bwd) / (tf + tb) / 1e12}
     if pk:
         out["alu_frac"] = out["fp32_tflops"] * 1e12 / fp32_peak(pk)
-        out["roofline_note"] = "FP32-issue and latency bound (256 warps at 8192 envs); FMA = 2"
+        out["roofline_note"] = "latency bound: the reverse warps' dependent chain (130 four-warp blocks at 8192 envs); FMA = 2"
     return out
 
 
