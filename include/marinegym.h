@@ -169,7 +169,7 @@ typedef struct {
   int32_t task;                 /* 0: station keeping (fixed target p*);
                                    1: trajectory tracking (time-varying p*(t)) */
   int32_t payload;              /* 1: every env carries a point-mass payload
-                                   (needs per_env_params, record_steps = 0) */
+                                   (needs per_env_params) */
   int32_t integrator;           /* MG_INTEG_EULER (semi-implicit Euler per
                                    substep) or MG_INTEG_RK4 (classical RK4 on
                                    p, q, nu with the actuator states held over
@@ -301,7 +301,10 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
 /* Reverse-mode gradient of the last recorded mg_rollout (discretise-then-
  * differentiate: the exact adjoint of the discrete map, including the clamp,
  * rotor lag, quaternion renormalisation, and M^-1 = (M_RB + M_A)^-1 through
- * the added mass). Inputs: the same actions_dev (the library keeps no copy of
+ * the added mass; in payload runs the combined body's full inverse, its
+ * inertia about the origin and the off-origin centre-of-gravity terms, with
+ * g_added_mass the gradient with respect to the diagonal added mass M_A).
+ * Inputs: the same actions_dev (the library keeps no copy of
  * the caller's actions; the segments between checkpoints are recomputed from
  * them), cotangents g_obs [T][n_slots][13] and g_rew [T][n_slots] (either may
  * be NULL = 0) and g_state_T [n_slots][21] on the final state (NULL = 0).

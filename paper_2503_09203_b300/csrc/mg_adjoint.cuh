@@ -63,6 +63,12 @@ struct AdjSeg {
   float h, dt;
   int K, track;
 };
+
+// Payload runs: the env's combined-body parameters in a shared-memory
+// column [PF_DIM][ADJ_ENVS] (too many to hold in registers next to the
+// product).
+using AdjPhysPay = PhysSmemFull<ADJ_ENVS>;
+constexpr int ADJ_PAY_SMEM = PF_DIM * ADJ_ENVS * 4;
 constexpr int ADJ_STEPF = 14 + 8;            // per-step slot: g_obs 13, g_rew 1, actions 8
 static_assert(ADJ_REC % 4 == 0 && ADJ_REC >= 27, "record of whole 16-byte vectors");
 
@@ -152,9 +158,9 @@ struct AdjPrefetch {
 
 // Producer: recompute segment s from its checkpoint into the records of
 // buffer `buf`.
-template <int NT, typename ActT>
+template <int NT, bool PAY, typename ActT>
 __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const Phys<float>& P,
-                                            int64_t i, int s, float* buf) {
+                                            unsigned p_base, int64_t i, int s, float* buf) {
   const int64_t ns = a.n_slots, slot = sd.slot_off + i;
   const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
   St<float, NT> x;
@@ -169,7 +175,13 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
     for (int k = 0; k < sd.K; ++k) {
       St<float, NT> x0 = x;
       Tape<float, NT> tp;
-      substep<float, NT, true>(x, c, P, A, sd.h, &tp);
+      if constexpr (PAY) {
+        unsigned pb = p_base;
+        asm volatile("" : "+r"(pb));
+        substep<float, NT, true>(x, c, AdjPhysPay(pb), A, sd.h, &tp);
+      } else {
+        substep<float, NT, true>(x, c, P, A, sd.h, &tp);
+      }
       store_record<NT>(rec, x0, tp.rhs);
       rec += rstride;
     }
@@ -177,15 +189,34 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
   store_record<NT>(rec, x, nullptr);
 }
 
-template <int NT, typename ActT>
+template <int NT, bool PAY, typename ActT>
 __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, const ActT& A, int64_t i, bool valid,
-                                            float* s_rec, float* s_step) {
+                                            float* s_rec, float* s_step, float* s_par) {
   const int role = threadIdx.x / ADJ_ENVS;   // 0: reverse pass, 1: forward recompute
   const int lane = threadIdx.x % ADJ_ENVS;
   const int64_t slot = sd.slot_off + i;
   const int64_t ns = a.n_slots;
   Phys<float> P;
-  if (valid) load_phys(a.planes, ns, slot, P);
+  unsigned p_base = 0;
+  if constexpr (PAY) {
+    // The combined body's parameters (vehicle planes 1-5, 7, 8 and the
+    // payload planes) into the env's shared-memory column, read where used.
+    if (role == 0 && valid) {
+#pragma unroll
+      for (int k = 0; k < PF_STD_PLANES + PF_PAY_PLANES; ++k) {
+        const int plane = k < PF_STD_PLANES ? pf_std_plane(k) : a.pay_plane + (k - PF_STD_PLANES);
+        const float4 v = __ldg(&a.planes[(int64_t)plane * ns + slot]);
+        s_par[(4 * k + 0) * ADJ_ENVS + lane] = v.x;
+        s_par[(4 * k + 1) * ADJ_ENVS + lane] = v.y;
+        s_par[(4 * k + 2) * ADJ_ENVS + lane] = v.z;
+        s_par[(4 * k + 3) * ADJ_ENVS + lane] = v.w;
+      }
+    }
+    __syncthreads();
+    p_base = smem_addr(s_par) + 4u * (unsigned)lane;
+  } else {
+    if (valid) load_phys(a.planes, ns, slot, P);
+  }
   const int K = sd.K;
   const int n_seg = (a.T + a.ckpt_every - 1) / a.ckpt_every;
   const int64_t buf_floats = (int64_t)(a.ckpt_every * K + 1) * ns * ADJ_REC;
@@ -223,7 +254,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 
   for (int it = 0; it <= n_seg; ++it) {
     if (role == 1 && it < n_seg && valid)
-      adj_produce<NT>(a, sd, A, P, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
+      adj_produce<NT, PAY>(a, sd, A, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
     if (role == 0 && it >= 1 && valid) {
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
@@ -267,8 +298,16 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
           // Records j - 1 and j - 2 stream in while this substep's product runs.
           if (j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
           Tape<float, NT> tp;
-          tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
-          vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g);
+          if constexpr (PAY) {
+            unsigned pb = p_base;
+            asm volatile("" : "+r"(pb));
+            const AdjPhysPay Pv(pb);
+            tape_from_rhs<float, NT>(xs, c, Pv, A, sd.h, rhs, tp, q1);
+            vjp_from_tape<float, NT>(xs, q1, tp, c, Pv, A, sd.h, lam, lc, g);
+          } else {
+            tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
+            vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g);
+          }
         }
         if (a.g_actions) {
           float* ga = a.g_actions + (int64_t)t * a.act_stride + sd.act_off + i * NT;
@@ -311,7 +350,10 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 // LIT: NoLit (the class tables of the kernel parameter) or, for the kernels
 // compiled at run time, a type whose make() returns the class's tables
 // (literal operands: zero allocation entries and a zero dead zone drop out).
-template <int NT, class LIT = NoLit>
+// PAY: payload runs (the combined body's full inverse and inertia, read
+// from a shared-memory column per env: ADJ_PAY_SMEM bytes of dynamic shared
+// memory).
+template <int NT, bool PAY = false, class LIT = NoLit>
 __global__ void __launch_bounds__(ADJ_THREADS)
     mg_adjoint_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ ClassK kc) {
   constexpr bool HAS_LIT = !tt::is_same<LIT, NoLit>::value;
@@ -320,6 +362,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
   if constexpr (HAS_LIT) kt = &klit;
   __shared__ __align__(16) float s_rec[ADJ_RING * ADJ_ENVS * ADJ_REC];
   __shared__ __align__(16) float s_step[ADJ_RING * ADJ_STEPF * ADJ_ENVS];
+  extern __shared__ __align__(16) float s_dyn[];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int parts = a.tile_envs / ADJ_ENVS;
   const int tile = a.tile_lo + (int)blockIdx.x / parts;
@@ -337,7 +380,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
     // Every thread of the block takes part in the per-segment barriers.
     const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track};
-    adjoint_env<NT>(a, sr, *kt, i, valid, s_rec, s_step);
+    adjoint_env<NT, PAY>(a, sr, *kt, i, valid, s_rec, s_step, s_dyn);
   }
   // Completion stays ordered along the stream (see the step kernel).
   asm volatile("griddepcontrol.wait;" ::: "memory");

@@ -633,10 +633,20 @@ MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, 
 #pragma unroll
   for (int i = 0; i < 3; ++i) tp.w[i] = x0.nu[3 + i];
   rel_velocity<S, PhysT, true>(tp.R, v, P, tp.vc, tp.vr);
+  if constexpr (PhysT::kFull) {
+    S nd[6];
+    apply_minv<S>(P, rhs, nd);
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    tp.rhs[j] = rhs[j];
-    tp.nu1[j] = x0.nu[j] + (h * S(P.minv[j])) * rhs[j];
+    for (int j = 0; j < 6; ++j) {
+      tp.rhs[j] = rhs[j];
+      tp.nu1[j] = x0.nu[j] + h * nd[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      tp.rhs[j] = rhs[j];
+      tp.nu1[j] = x0.nu[j] + (h * S(P.minv[j])) * rhs[j];
+    }
   }
   const S hh = S(0.5f) * h;
   const S wn[3] = {tp.nu1[3], tp.nu1[4], tp.nu1[5]};
@@ -652,10 +662,13 @@ MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, 
 // Adjoint of one substep from its tape. x0 is the substep's start state and
 // q1 its end attitude; `lx` holds the adjoint of its end state on entry and
 // of its start state on exit. The command adjoint and the
-// hydrodynamic-coefficient adjoints accumulate.
-template <typename S, int NT, typename ActT>
+// hydrodynamic-coefficient adjoints accumulate. `P` is a Phys<S> or a view
+// with its members, or (PhysT::kFull, payload runs) a view of the combined
+// body: full inverse Mi, inertia about the origin Io, first moment s, mass m
+// and weight W of vehicle and payload.
+template <typename S, int NT, typename ActT, typename PhysT>
 MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& tp, const S (&c)[NT],
-                         const Phys<S>& P, const ActT& A, S h, St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
+                         const PhysT& P, const ActT& A, S h, St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
   const S z0 = S(0.0f);
 
   // q1 = qn * inv
@@ -693,12 +706,26 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
   // lp unchanged (identity).
   // nu1 = nu + h minv o rhs
   S lrhs[6];
+  if constexpr (PhysT::kFull) {
+    // nu1 = nu + h Mi rhs with Mi = (M_RB + diag(A))^-1 symmetric:
+    // lrhs = h Mi lnu1, and d(Mi rhs)/dA_j = -Mi e_j (Mi rhs)_j, so
+    // g.A_j -= lrhs_j (Mi rhs)_j.
+    S t[6], nd[6];
+    apply_minv<S>(P, lnu1, t);
+    apply_minv<S>(P, tp.rhs, nd);
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    lrhs[j] = h * P.minv[j] * lnu1[j];
-    // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2, and
-    // h minv^2 lnu1 rhs = minv lrhs rhs.
-    g.A[j] = g.A[j] - tp.rhs[j] * lrhs[j] * P.minv[j];
+    for (int j = 0; j < 6; ++j) {
+      lrhs[j] = h * t[j];
+      g.A[j] = g.A[j] - lrhs[j] * nd[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      lrhs[j] = h * P.minv[j] * lnu1[j];
+      // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2, and
+      // h minv^2 lnu1 rhs = minv lrhs rhs.
+      g.A[j] = g.A[j] - tp.rhs[j] * lrhs[j] * P.minv[j];
+    }
   }
   S lnu[6];
 #pragma unroll
@@ -712,8 +739,14 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
   S lv[3] = {z0, z0, z0}, lw[3] = {z0, z0, z0}, lvr[3] = {z0, z0, z0}, lvc[3] = {z0, z0, z0};
   S le[3] = {z0, z0, z0};
   // (W-B) e  and  -(B rb) x e
-  const S WmB = P.W - P.B;
-  const S Brb[3] = {P.B * P.rb[0], P.B * P.rb[1], P.B * P.rb[2]};
+  const S WmB = S(P.W) - S(P.B);
+  S Brb[3] = {S(P.B) * S(P.rb[0]), S(P.B) * S(P.rb[1]), S(P.B) * S(P.rb[2])};
+  if constexpr (PhysT::kFull) {
+    // Weight at r_g = s / m: the moment arm is B r_b - (W / m) s.
+    const S wpm = S(P.W) / S(P.m);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Brb[j] = Brb[j] - wpm * S(P.s[j]);
+  }
   {
     // d/de of -(B rb) x e contracted with lrhs_ang: (-lrhs_ang) x (B rb).
     const S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
@@ -736,15 +769,23 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
     g.dq[3 + j] = g.dq[3 + j] + ldw * b * w[j];
   }
   // C_RB + C_A in the forward's merged form: rhs_lin -= w x bl with
-  // bl = m v + a1; rhs_ang -= w x ba + vr x a1 with ba = A_ang o w + Ig o w;
-  // a1 = A_lin o vr.
+  // bl = m v + a1; rhs_ang -= w x ba + vr x a1 with ba = A_ang o w + Iw
+  // (Iw = Ig o w, or Io w about the origin with a payload); a1 = A_lin o vr.
   {
-    S a1[3], bl[3], ba[3];
+    S a1[3], bl[3], ba[3], Iw[3];
+    if constexpr (PhysT::kFull) {
+      Iw[0] = S(P.Io[0]) * w[0] + S(P.Io[1]) * w[1] + S(P.Io[2]) * w[2];
+      Iw[1] = S(P.Io[1]) * w[0] + S(P.Io[3]) * w[1] + S(P.Io[4]) * w[2];
+      Iw[2] = S(P.Io[2]) * w[0] + S(P.Io[4]) * w[1] + S(P.Io[5]) * w[2];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Iw[j] = S(P.Ig[j]) * w[j];
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      a1[j] = P.A[j] * vr[j];
-      bl[j] = P.m * v[j] + a1[j];
-      ba[j] = P.A[3 + j] * w[j] + P.Ig[j] * w[j];
+      a1[j] = S(P.A[j]) * vr[j];
+      bl[j] = S(P.m) * v[j] + a1[j];
+      ba[j] = S(P.A[3 + j]) * w[j] + Iw[j];
     }
     S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
     S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
@@ -752,14 +793,37 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
     cross_vjp(w, bl, nl, lw, lbl);
     cross_vjp(w, ba, na, lw, lba);
     cross_vjp(vr, a1, na, lvr, la1);
+    // d(Iw)/dw contracted with lba: Ig o lba, or Io lba (symmetric).
+    S lIw[3];
+    if constexpr (PhysT::kFull) {
+      lIw[0] = S(P.Io[0]) * lba[0] + S(P.Io[1]) * lba[1] + S(P.Io[2]) * lba[2];
+      lIw[1] = S(P.Io[1]) * lba[0] + S(P.Io[3]) * lba[1] + S(P.Io[4]) * lba[2];
+      lIw[2] = S(P.Io[2]) * lba[0] + S(P.Io[4]) * lba[1] + S(P.Io[5]) * lba[2];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) lIw[j] = S(P.Ig[j]) * lba[j];
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      lv[j] = lv[j] + P.m * lbl[j];
+      lv[j] = lv[j] + S(P.m) * lbl[j];
       la1[j] = la1[j] + lbl[j];
-      lw[j] = lw[j] + P.A[3 + j] * lba[j] + P.Ig[j] * lba[j];
+      lw[j] = lw[j] + S(P.A[3 + j]) * lba[j] + lIw[j];
       g.A[3 + j] = g.A[3 + j] + lba[j] * w[j];
       g.A[j] = g.A[j] + la1[j] * vr[j];
-      lvr[j] = lvr[j] + la1[j] * P.A[j];
+      lvr[j] = lvr[j] + la1[j] * S(P.A[j]);
+    }
+    if constexpr (PhysT::kFull) {
+      // Off-origin centre of gravity: rhs_lin -= w x (w x s),
+      // rhs_ang -= s x (w x v).
+      const S sv[3] = {S(P.s[0]), S(P.s[1]), S(P.s[2])};
+      S wxs[3], lwxs[3] = {z0, z0, z0}, t[3], lz[3];
+      cross3(w, sv, wxs);
+      cross_vjp(w, wxs, nl, lw, lwxs);
+      cross3(sv, lwxs, t);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) lw[j] = lw[j] + t[j];
+      cross3(na, sv, lz);
+      cross_vjp(w, v, lz, lw, lv);
     }
     // current-acceleration term A_lin o (w x vc)
     S wxvc[3];
@@ -768,7 +832,7 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       g.A[j] = g.A[j] - lrhs[j] * wxvc[j];
-      lwv[j] = -lrhs[j] * P.A[j];
+      lwv[j] = -lrhs[j] * S(P.A[j]);
     }
     cross_vjp(w, vc, lwv, lw, lvc);
   }

@@ -190,7 +190,7 @@ struct AdjArgs {
   float* g_D;                 // [n_slots][12] or null
   float* g_state0;            // [n_slots][21] or null
   int32_t tile_envs;          // envs per tile (the launch's blocks cover a tile in tile_envs / blockDim parts)
-  int32_t pad0;
+  int32_t pay_plane;          // payload runs: first payload plane; 0: no payload
 };
 
 // Class nominal record for the reset kernel (FP64).

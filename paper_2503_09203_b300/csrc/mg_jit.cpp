@@ -124,7 +124,7 @@ std::string class_source(const ClassK& k, const char* header) {
 enum Kind { STEP = 0, ADJOINT = 1 };
 
 std::string kernel_name(Kind kind, int nt, bool ms) {
-  if (kind == ADJOINT) return "mg::mg_adjoint_kernel<" + std::to_string(nt) + ", mg::JitLit>";
+  if (kind == ADJOINT) return "mg::mg_adjoint_kernel<" + std::to_string(nt) + ", false, mg::JitLit>";
   return "mg::mg_step_kernel<" + std::to_string(nt) + ", 0, 0, true, false, " + (ms ? "true" : "false") +
          ", mg::JitLit>";
 }

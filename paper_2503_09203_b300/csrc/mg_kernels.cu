@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "marinegym.h"
@@ -268,11 +269,11 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
 // `dependent`: programmatic dependent of the previous launch; kern: the
 // kernel (the library's, or one compiled at run time for this class).
 static cudaError_t launch_adjoint_k(const void* kern, const AdjArgs& a, const ClassK& kc, bool dependent,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, size_t dyn_smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.n_tiles * (a.tile_envs / ADJ_ENVS)));
   cfg.blockDim = dim3(ADJ_THREADS);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -291,6 +292,25 @@ cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool depe
                            const void* jit_kernel) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (a.tile_envs <= 0 || a.tile_envs % ADJ_ENVS != 0 || a.seg_hi - a.seg_lo != 1) return cudaErrorInvalidValue;
+  if (a.pay_plane > 0) {
+    // Payload runs: the library's kernel with the parameter column in
+    // dynamic shared memory (above the default 48 KB with the static part:
+    // the attribute is set once per device and kernel).
+    static std::atomic<uint32_t> attr_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    const void* k = nullptr;
+#define MG_L(N) k = reinterpret_cast<const void*>(&mg_adjoint_kernel<N, true>)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+    const uint32_t bit = 1u << nt;
+    if (dev >= 0 && dev < 64 && !(attr_set[dev].load() & bit)) {
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_PAY_SMEM);
+      if (e != cudaSuccess) return e;
+      attr_set[dev].fetch_or(bit);
+    }
+    return launch_adjoint_k(k, a, kc, dependent, st, ADJ_PAY_SMEM);
+  }
   if (jit_kernel) return launch_adjoint_k(jit_kernel, a, kc, dependent, st);
 #define MG_L(N) return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N>), a, kc, dependent, st)
   MG_NT_SWITCH(nt, MG_L)

@@ -447,10 +447,6 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
       sim->err = "payload runs need per_env_params";
       return bail(MG_ERR_INVALID_ARG);
     }
-    if (cfg->record_steps > 0) {
-      sim->err = "payload runs have no adjoint (record_steps must be 0)";
-      return bail(MG_ERR_INVALID_ARG);
-    }
     const double lo = cfg->reset.payload_lo, hi = cfg->reset.payload_hi;
     if (!(std::isfinite(lo) && std::isfinite(hi) && lo >= 0.0 && hi >= lo)) {
       sim->err = "payload range must satisfy 0 <= payload_lo <= payload_hi";
@@ -630,13 +626,17 @@ static int param_mode(const mg_sim* sim) { return sim->cfg.payload ? 2 : (sim->c
 
 // Kernel-parameter constants of a one-class group: the class table, the lag
 // coefficients and dead-zone flag of its segment, no current.
-static ClassK class_k(const mg_sim* sim, const Group& g) {
+// Class tables of group g as the kernel parameter. Step kernels of
+// class-constant and payload runs take allocation rows premultiplied by the
+// thrust constants (as their Premul); the adjoint (for_adjoint) always takes
+// plain rows, its product applies k itself.
+static ClassK class_k(const mg_sim* sim, const Group& g, bool for_adjoint = false) {
   ClassK k;
   std::memset(&k, 0, sizeof(k));
   const ClassF& f = sim->h_cls[g.cls];
   const SegDesc& sd = sim->segs[g.seg_lo];
   std::memcpy(k.alloc, f.alloc, sizeof(k.alloc));
-  if (MG_PREMUL && g.var == 0 && param_mode(sim) != 1)   // as the kernels' Premul: rows of B diag(k)
+  if (!for_adjoint && MG_PREMUL && g.var == 0 && param_mode(sim) != 1)   // as the kernels' Premul: rows of B diag(k)
     for (int r = 0; r < 6; ++r)
       for (int i = 0; i < 8; ++i) k.alloc[r][i] = f.alloc[r][i] * f.kf[i];
   std::memcpy(k.kf, f.kf, sizeof(k.kf));
@@ -1121,6 +1121,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
 // the previous one so that they run side by side.
 static int launch_backward(mg_sim* sim, AdjArgs a, cudaStream_t st) {
   a.tile_envs = sim->threads;
+  a.pay_plane = sim->cfg.payload ? pay_plane(sim->cfg.task == 1) : 0;
   bool first = true;
   for (const Group& grp : sim->groups) {
     for (int s = grp.seg_lo; s < grp.seg_hi; ++s) {
@@ -1131,12 +1132,12 @@ static int launch_backward(mg_sim* sim, AdjArgs a, cudaStream_t st) {
       g.tile_lo = sd.tile_begin;
       g.n_tiles = (sd.n4 + sim->threads - 1) / sim->threads;
       g.cls = sd.cls;
-      const ClassK kc = class_k(sim, g);
+      const ClassK kc = class_k(sim, g, true);
       a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
       // The class-specialised kernel (its actuator tables as literals) when
       // it can be had; the library's otherwise.
       const void* jk = nullptr;
-      if (sim->specialise) {
+      if (sim->specialise && !sim->cfg.payload) {
         std::string err;
         jk = jit_adjoint_kernel(kc, g.nt, &err);
         if (!jk) sim->jit_err = err;

@@ -6,8 +6,10 @@
 // and damping coefficients (the inverse mass matrix follows the added mass).
 // Prints the worst relative difference and, with a nonzero argument, the
 // same for a product whose added-mass gradient is scaled by 1.01 (the check
-// must see that).
+// must see that). Both for the vehicle alone and with a point-mass payload.
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <random>
 #include "mg_device.cuh"
 using namespace mg;
@@ -74,13 +76,132 @@ double run(std::mt19937_64& rng) {
   for (int j = 0; j < 6; ++j) an += g_scale * g.A[j] * d.A[j] + g.dl[j] * d.dl[j] + g.dq[j] * d.dq[j];
   return std::fabs(fd - an) / std::max(1.0, std::fabs(fd));
 }
+
+// Payload runs: the combined body (vehicle + point mass) about the body
+// origin, with its full inverse recomputed from M_RB + diag(A) for every
+// perturbation of the added mass.
+template <typename S>
+struct PhysPay {
+  static constexpr bool kFull = true;
+  S A[6], dl[6], dq[6], B, rb[3], Vc[3], Mi[21], Io[6], s[3], m, W;
+};
+
+static bool invert6(double M[6][6], double Mi[6][6]) {
+  double a[6][12];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 12; ++j) a[i][j] = j < 6 ? M[i][j] : (j - 6 == i ? 1.0 : 0.0);
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 6; ++r)
+      if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+    if (std::fabs(a[piv][c]) < 1e-300) return false;
+    for (int j = 0; j < 12; ++j) std::swap(a[c][j], a[piv][j]);
+    const double d = a[c][c];
+    for (int j = 0; j < 12; ++j) a[c][j] /= d;
+    for (int r = 0; r < 6; ++r)
+      if (r != c) {
+        const double f = a[r][c];
+        for (int j = 0; j < 12; ++j) a[r][j] -= f * a[c][j];
+      }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) Mi[i][j] = a[i][6 + j];
+  return true;
+}
+
+static void pay_fill(PhysPay<double>& P, const double A[6]) {
+  const double Ss[3][3] = {{0, -P.s[2], P.s[1]}, {P.s[2], 0, -P.s[0]}, {-P.s[1], P.s[0], 0}};
+  const double Io[3][3] = {{P.Io[0], P.Io[1], P.Io[2]}, {P.Io[1], P.Io[3], P.Io[4]}, {P.Io[2], P.Io[4], P.Io[5]}};
+  double M[6][6], Mi[6][6];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      M[i][j] = (i == j) ? P.m + A[i] : 0.0;
+      M[i][3 + j] = -Ss[i][j];
+      M[3 + i][j] = Ss[i][j];
+      M[3 + i][3 + j] = Io[i][j] + (i == j ? A[3 + i] : 0.0);
+    }
+  invert6(M, Mi);
+  int q = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) P.Mi[q++] = 0.5 * (Mi[i][j] + Mi[j][i]);
+  for (int j = 0; j < 6; ++j) P.A[j] = A[j];
+}
+
+template <int NT>
+double run_pay(std::mt19937_64& rng) {
+  std::uniform_real_distribution<double> U(-1, 1), P01(0.2, 2.0);
+  PhysPay<double> P; Act<double> Ac; In<NT> in;
+  const double mp = 3.0, rp[3] = {U(rng) * 0.3, U(rng) * 0.3, U(rng) * 0.3};
+  const double m = 12, Ig[3] = {P01(rng), P01(rng), P01(rng)};
+  P.m = m + mp; P.W = 110 + mp * 9.81; P.B = 113;
+  for (int j = 0; j < 3; ++j) { P.s[j] = mp * rp[j]; P.rb[j] = U(rng) * 0.05; P.Vc[j] = U(rng) * 0.4; }
+  const double rp2 = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
+  P.Io[0] = Ig[0] + mp * (rp2 - rp[0] * rp[0]); P.Io[1] = -mp * rp[0] * rp[1]; P.Io[2] = -mp * rp[0] * rp[2];
+  P.Io[3] = Ig[1] + mp * (rp2 - rp[1] * rp[1]); P.Io[4] = -mp * rp[1] * rp[2]; P.Io[5] = Ig[2] + mp * (rp2 - rp[2] * rp[2]);
+  for (int j = 0; j < 6; ++j) { in.A[j] = P01(rng) * 3; in.dl[j] = P01(rng) * 5; in.dq[j] = P01(rng) * 10; }
+  for (int r = 0; r < 6; ++r) for (int i = 0; i < 8; ++i) Ac.alloc[r][i] = i < NT ? U(rng) : 0;
+  for (int i = 0; i < 8; ++i) { Ac.kf[i] = P01(rng) * 20; Ac.dz[i] = 0.0; Ac.alpha[i] = P01(rng) * 0.4; }
+  const double h = 0.0025;
+  for (int j = 0; j < 3; ++j) in.x.p[j] = U(rng);
+  for (int j = 0; j < 4; ++j) in.x.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) in.x.nu[j] = U(rng);
+  for (int j = 0; j < NT; ++j) in.x.n[j] = U(rng);
+  for (int j = 0; j < NT; ++j) in.c[j] = U(rng);
+  auto fwd_pay = [&](const In<NT>& i2, St<double, NT>& out) {
+    PhysPay<double> Q = P;
+    pay_fill(Q, i2.A);
+    for (int j = 0; j < 6; ++j) { Q.dl[j] = i2.dl[j]; Q.dq[j] = i2.dq[j]; }
+    out = i2.x;
+    double c[NT]; for (int k = 0; k < NT; ++k) c[k] = i2.c[k];
+    substep<double, NT, false>(out, c, Q, Ac, h, nullptr);
+  };
+  PhysPay<double> Pb = P;
+  pay_fill(Pb, in.A);
+  for (int j = 0; j < 6; ++j) { Pb.dl[j] = in.dl[j]; Pb.dq[j] = in.dq[j]; }
+  St<double, NT> x = in.x; Tape<double, NT> tp;
+  substep<double, NT, true>(x, in.c, Pb, Ac, h, &tp);
+  St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
+  // The reverse pass rebuilds the tape from the start state and rhs.
+  Tape<double, NT> tr; double q1[4];
+  tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
+  St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
+  vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g);
+  In<NT> d;
+  for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
+  for (int j = 0; j < NT; ++j) d.c[j] = U(rng);
+  for (int j = 0; j < 6; ++j) { d.A[j] = U(rng); d.dl[j] = U(rng); d.dq[j] = U(rng); }
+  const double eps = 1e-6;
+  auto shift = [&](double sc) { In<NT> o = in;
+    for (int j = 0; j < 3; ++j) o.x.p[j] += sc * d.x.p[j]; for (int j = 0; j < 4; ++j) o.x.q[j] += sc * d.x.q[j];
+    for (int j = 0; j < 6; ++j) o.x.nu[j] += sc * d.x.nu[j]; for (int j = 0; j < NT; ++j) o.x.n[j] += sc * d.x.n[j];
+    for (int j = 0; j < NT; ++j) o.c[j] += sc * d.c[j];
+    for (int j = 0; j < 6; ++j) { o.A[j] += sc * d.A[j]; o.dl[j] += sc * d.dl[j]; o.dq[j] += sc * d.dq[j]; }
+    return o; };
+  St<double, NT> yp, ym; fwd_pay(shift(eps), yp); fwd_pay(shift(-eps), ym);
+  double fd = 0;
+  for (int j = 0; j < 3; ++j) fd += lam.p[j] * (yp.p[j] - ym.p[j]); for (int j = 0; j < 4; ++j) fd += lam.q[j] * (yp.q[j] - ym.q[j]);
+  for (int j = 0; j < 6; ++j) fd += lam.nu[j] * (yp.nu[j] - ym.nu[j]); for (int j = 0; j < NT; ++j) fd += lam.n[j] * (yp.n[j] - ym.n[j]);
+  fd /= 2 * eps;
+  double an = 0;
+  for (int j = 0; j < 3; ++j) an += lx.p[j] * d.x.p[j]; for (int j = 0; j < 4; ++j) an += lx.q[j] * d.x.q[j];
+  for (int j = 0; j < 6; ++j) an += lx.nu[j] * d.x.nu[j]; for (int j = 0; j < NT; ++j) an += lx.n[j] * d.x.n[j];
+  for (int j = 0; j < NT; ++j) an += lc[j] * d.c[j];
+  for (int j = 0; j < 6; ++j) an += g_scale * g.A[j] * d.A[j] + g.dl[j] * d.dl[j] + g.dq[j] * d.dq[j];
+  return std::fabs(fd - an) / std::max(1.0, std::fabs(fd));
+}
+
 int main(int argc, char** argv) {
   for (int pass = 0; pass < (argc > 1 ? 2 : 1); ++pass) {
     g_scale = pass ? 1.01 : 1.0;
     std::mt19937_64 rng(11);
     double w = 0;
+    double wp = 0;
     for (int k = 0; k < 300; ++k) { w = std::max(w, run<8>(rng)); w = std::max(w, run<5>(rng)); w = std::max(w, run<3>(rng)); }
+    for (int k = 0; k < 300; ++k) { wp = std::max(wp, run_pay<8>(rng)); wp = std::max(wp, run_pay<4>(rng)); }
     printf("%s %.6e\n", pass ? "scaled" : "worst", w);
+    printf("%s %.6e\n", pass ? "scaled_payload" : "worst_payload", wp);
   }
   return 0;
 }

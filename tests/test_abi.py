@@ -78,11 +78,11 @@ def test_flop_count_is_host_only_and_sane(lib):
 
 
 @pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env", "payload_per_env",
-                                 "payload_record", "payload_range"])
+                                 "rk4_record", "payload_range"])
 def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
     classes = [vehicles.heavy8()]
     counts, dt, K, per_env, reset = [8], 0.01, 1, True, dict(vehicles.NO_DR)
-    record, payload = 0, False
+    record, payload, integ = 0, False, 0
     if bad == "dt":
         dt = -1.0
     elif bad == "K":
@@ -97,12 +97,12 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
         per_env, reset = False, dict(vehicles.DR_TRAIN)
     elif bad == "payload_per_env":
         per_env, payload = False, True
-    elif bad == "payload_record":
-        record, payload = 10, True
+    elif bad == "rk4_record":
+        record, integ = 10, 1   # RK4 runs have no adjoint
     elif bad == "payload_range":
         payload, reset = True, dict(vehicles.PAYLOAD, payload_lo=0.3, payload_hi=0.1)
     with pytest.raises(B.MGError) as e:
-        B.mg_create(classes, counts, dt, K, per_env, reset, record_steps=record, payload=payload)
+        B.mg_create(classes, counts, dt, K, per_env, reset, record_steps=record, payload=payload, integrator=integ)
     assert e.value.code == B.MG_ERR_INVALID_ARG
     if bad.startswith("payload"):
         assert "payload" in str(e.value)

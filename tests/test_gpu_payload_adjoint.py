@@ -1,0 +1,128 @@
+"""GPU adjoint of payload runs (Sec. III-B mission payloads with current and
+domain randomisation: the combined body's full inverse, its inertia about the
+origin and the off-origin centre of gravity) against the oracle's
+forward-mode tangents, for gradients with respect to the actions, the
+added-mass and damping coefficients and the initial state.
+
+Tolerance as for the vehicle alone: FP32 adjoint vs oracle tangents <= 1e-3
+relative per env over random directions.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle
+from paper_2503_09203_b300 import binding as B
+from paper_2503_09203_b300 import vehicles, workloads
+from tests.test_gpu_adjoint import gpu_gradients
+
+pytestmark = pytest.mark.gpu
+
+DT = 0.01
+TOL = 1e-3
+
+
+def payload_sim(counts, T, K, ckpt, seed):
+    classes = vehicles.five_classes()[:len(counts)]
+    cfg = dict(vehicles.PAYLOAD_DR)
+    sim = B.Sim(classes, counts, dt=DT, K=K, per_env_params=True, reset=cfg, payload=True,
+                record_steps=T, ckpt_every=ckpt)
+    sim.reset(seed=seed)
+    envs, _ = oracle.reset(classes, workloads.env_classes(counts), cfg, seed)
+    nthr = np.array([classes[c]["n_thr"] for c in workloads.env_classes(counts)])
+    s0 = workloads.random_states(seed + 1, sim.n_envs, nthr, pos_scale=2.0, vel_scale=0.3, rate_scale=0.4)
+    sim.set_state(s0)
+    return classes, sim, envs, s0, nthr
+
+
+def check_directions(classes, sub_envs, s0, a, K, g, go, gr, nthr, ids, rng):
+    """Per env: <gpu gradient, d> against the oracle's tangent of
+    sum_t <g_obs, obs_t> + <g_rew, rew_t> along d, for three directions per
+    gradient group."""
+    n = len(ids)
+    T = a.shape[0]
+    thr_mask = (np.arange(8)[None, :] < nthr[ids][:, None]).astype(np.float64)
+    st_mask = (np.arange(21)[None, :] < (13 + nthr[ids])[:, None]).astype(np.float64)
+    groups = {"act": lambda: dict(d_actions=rng.normal(size=(T, n, 8)) * thr_mask[None]),
+              "A": lambda: dict(d_Ma=rng.normal(size=(n, 6))),
+              "dl": lambda: dict(d_dl=rng.normal(size=(n, 6))),
+              "dq": lambda: dict(d_dq=rng.normal(size=(n, 6))),
+              "s0": lambda: dict(d_state0=rng.normal(size=(n, 21)) * st_mask * 0.1)}
+    for name, mk in groups.items():
+        got, want = [], []
+        for _ in range(3):
+            d = mk()
+            j = oracle.rollout_jvp(classes, sub_envs, s0[ids].astype(np.float64), a[:, ids], DT, K, **d)
+            want.append(np.einsum("te,te->e", gr[:, ids], j["d_reward"]) +
+                        np.einsum("tek,tek->e", go[:, ids], j["d_obs"]))
+            if name == "act":
+                got.append(np.einsum("tek,tek->e", g["act"][:, ids], d["d_actions"]))
+            elif name == "s0":
+                got.append(np.einsum("ek,ek->e", g["s0"][ids], d["d_state0"]))
+            else:
+                key = {"A": "d_Ma", "dl": "d_dl", "dq": "d_dq"}[name]
+                got.append(np.einsum("ek,ek->e", g[name][ids], d[key]))
+        gv, rv = np.stack(got, 1), np.stack(want, 1)
+        err = np.linalg.norm(gv - rv, axis=1) / np.maximum(np.linalg.norm(rv, axis=1), 1e-6)
+        assert err.max() <= TOL, (name, err.max(), int(ids[np.argmax(err)]))
+
+
+def test_payload_adjoint_matches_oracle_tangents():
+    """Five classes, a few envs each, T = 24, K = 4, a checkpoint every 8
+    steps; cotangents on every observation and reward."""
+    counts = [3, 2, 2, 3, 2]
+    T, K = 24, 4
+    classes, sim, envs, s0, nthr = payload_sim(counts, T, K, 8, seed=51)
+    E = sim.n_envs
+    rng = np.random.default_rng(52)
+    a = workloads.actions(53, T, E, lo=-0.99, hi=0.99)
+    go = rng.normal(size=(T, E, 13)) * 0.1
+    gr = -1.0 + 0.2 * rng.normal(size=(T, E))
+    g = gpu_gradients(sim, a, T, go, gr, np.zeros((E, 21)))
+    assert sim.get_payload()[:, 0].min() > 0
+    sim.close()
+    check_directions(classes, envs, s0, a, K, g, go, gr, nthr, np.arange(E), rng)
+
+
+def test_payload_adjoint_sampled_at_4096_envs():
+    """4096 envs over the five classes, T = 60, K = 4, a checkpoint every 20
+    steps (the launch shape of a full-size backward): 72 sampled envs, every
+    class boundary included."""
+    counts = workloads.class_counts(4096, 5)
+    T, K = 60, 4
+    classes, sim, envs, s0, nthr = payload_sim(counts, T, K, 20, seed=61)
+    E = sim.n_envs
+    rng = np.random.default_rng(62)
+    a = workloads.actions(63, T, E, lo=-0.99, hi=0.99)
+    go = (rng.normal(size=(T, E, 13)) * 0.1).astype(np.float32)
+    gr = (-1.0 + 0.2 * rng.normal(size=(T, E))).astype(np.float32)
+    g = gpu_gradients(sim, a, T, go, gr, np.zeros((E, 21)))
+    sim.close()
+    bounds = np.cumsum(counts)
+    ids = np.unique(np.concatenate([rng.choice(E, 56, replace=False), [0, E - 1], bounds[:-1], bounds[:-1] - 1]))
+    # The sampled envs' records, drawn with their own env ids.
+    sub, _ = oracle.reset(classes, workloads.env_classes(counts)[ids], dict(vehicles.PAYLOAD_DR), 61, env_ids=ids)
+    check_directions(classes, sub, s0, a, K, g, go.astype(np.float64), gr.astype(np.float64), nthr, ids, rng)
+
+
+def test_set_payload_discards_the_recording():
+    """A backward after the payload changed would differentiate the old
+    rollout with the new body: the recording is discarded instead."""
+    counts = [4, 4]
+    T = 10
+    classes, sim, envs, s0, nthr = payload_sim(counts, T, 2, 5, seed=71)
+    a_dev = sim.pack_actions(workloads.actions(72, T, sim.n_envs))
+    B.mg_rollout(sim.handle, a_dev, T, None, None, True)
+    steps, _ = B.mg_recording(sim.handle)
+    assert steps == T
+    sim.set_payload(sim.get_payload())
+    steps, _ = B.mg_recording(sim.handle)
+    assert steps == 0
+    g_act = torch.zeros(T, sim.action_floats, device="cuda")
+    with pytest.raises(B.MGError) as e:
+        B.mg_step_backward(sim.handle, a_dev, None, None, None, g_act, None, None, None)
+    assert e.value.code == B.MG_ERR_STATE
+    sim.close()
