@@ -99,8 +99,8 @@ enum {
  * and the inverse inertia in FP64 and stores them FP32. The class's own CoG
  * is the body origin (r_g = 0) and its added mass is diagonal; an off-origin
  * CoG arises from a payload (see mg_set_payload). A class with any channel
- * other than MG_ACT_PROP (a "generic" class) runs the step only: no adjoint,
- * FP64 check path, payload or serving. */
+ * other than MG_ACT_PROP (a "generic" class) has the step and the adjoint
+ * (Euler) but no FP64 check path, payload or serving. */
 typedef struct {
   int32_t n_thr;            /* 1..8 (the workloads use 4, 6, 8) */
   int32_t pad0;

@@ -158,9 +158,9 @@ struct AdjPrefetch {
 
 // Producer: recompute segment s from its checkpoint into the records of
 // buffer `buf`.
-template <int NT, bool PAY, typename ActT>
-__device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const Phys<float>& P,
-                                            unsigned p_base, int64_t i, int s, float* buf) {
+template <int NT, bool PAY, typename ActT, typename GenT>
+__device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
+                                            const Phys<float>& P, unsigned p_base, int64_t i, int s, float* buf) {
   const int64_t ns = a.n_slots, slot = sd.slot_off + i;
   const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
   St<float, NT> x;
@@ -180,7 +180,7 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
         asm volatile("" : "+r"(pb));
         substep<float, NT, true>(x, c, AdjPhysPay(pb), A, sd.h, &tp);
       } else {
-        substep<float, NT, true>(x, c, P, A, sd.h, &tp);
+        substep<float, NT, true, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, &tp, G);
       }
       store_record<NT>(rec, x0, tp.rhs);
       rec += rstride;
@@ -189,9 +189,9 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
   store_record<NT>(rec, x, nullptr);
 }
 
-template <int NT, bool PAY, typename ActT>
-__device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, const ActT& A, int64_t i, bool valid,
-                                            float* s_rec, float* s_step, float* s_par) {
+template <int NT, bool PAY, typename ActT, typename GenT>
+__device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
+                                            int64_t i, bool valid, float* s_rec, float* s_step, float* s_par) {
   const int role = threadIdx.x / ADJ_ENVS;   // 0: reverse pass, 1: forward recompute
   const int lane = threadIdx.x % ADJ_ENVS;
   const int64_t slot = sd.slot_off + i;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 
   for (int it = 0; it <= n_seg; ++it) {
     if (role == 1 && it < n_seg && valid)
-      adj_produce<NT, PAY>(a, sd, A, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
+      adj_produce<NT, PAY>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
     if (role == 0 && it >= 1 && valid) {
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
@@ -306,7 +306,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
             vjp_from_tape<float, NT>(xs, q1, tp, c, Pv, A, sd.h, lam, lc, g);
           } else {
             tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
-            vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g);
+            vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g, G);
           }
         }
         if (a.g_actions) {
@@ -352,13 +352,18 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 // (literal operands: zero allocation entries and a zero dead zone drop out).
 // PAY: payload runs (the combined body's full inverse and inertia, read
 // from a shared-memory column per env: ADJ_PAY_SMEM bytes of dynamic shared
-// memory).
-template <int NT, bool PAY = false, class LIT = NoLit>
+// memory). GEN: classes with fins or servo-tilted propellers (the kernel
+// parameter carries the generic actuator table too).
+template <int NT, bool PAY = false, class LIT = NoLit, bool GEN = false>
 __global__ void __launch_bounds__(ADJ_THREADS)
-    mg_adjoint_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ ClassK kc) {
+    mg_adjoint_kernel(const __grid_constant__ AdjArgs a,
+                      const __grid_constant__ tt::conditional_t<GEN, ClassKG, ClassK> kp) {
+  static_assert(!(PAY && GEN), "payload runs are propeller classes");
   constexpr bool HAS_LIT = !tt::is_same<LIT, NoLit>::value;
   [[maybe_unused]] constexpr ClassK klit = LIT::make();
-  const ClassK* kt = &kc;
+  const ClassK* kt;
+  if constexpr (GEN) kt = &kp.k;
+  else kt = &kp;
   if constexpr (HAS_LIT) kt = &klit;
   __shared__ __align__(16) float s_rec[ADJ_RING * ADJ_ENVS * ADJ_REC];
   __shared__ __align__(16) float s_step[ADJ_RING * ADJ_STEPF * ADJ_ENVS];
@@ -380,7 +385,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
     // Every thread of the block takes part in the per-segment barriers.
     const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track};
-    adjoint_env<NT, PAY>(a, sr, *kt, i, valid, s_rec, s_step, s_dyn);
+    if constexpr (GEN) adjoint_env<NT, PAY>(a, sr, *kt, GenK{kp.g}, i, valid, s_rec, s_step, s_dyn);
+    else adjoint_env<NT, PAY>(a, sr, *kt, NoGen{}, i, valid, s_rec, s_step, s_dyn);
   }
   // Completion stays ordered along the stream (see the step kernel).
   asm volatile("griddepcontrol.wait;" ::: "memory");

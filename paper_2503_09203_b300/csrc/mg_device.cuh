@@ -279,6 +279,96 @@ MG_HD void fin_wrench(const GenT& G, const S (&n)[NT], const S vr[3], const S w[
   }
 }
 
+// Vector-Jacobian products of the two generic wrenches (the tilt wrench
+// depends on the thrusts f and the servo states, the fin wrench on the fin
+// states and the fin velocities u = v_r + w x r). ltau is the adjoint of the
+// wrench; lf and ln (per channel) and lvr, lw accumulate.
+template <typename S, int NT, typename GenT>
+MG_HD void tilt_wrench_vjp(const GenT& G, const S (&n)[NT], const S (&f)[NT], const S ltau[6], S (&lf)[NT],
+                           S (&ln)[NT]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    if (G.kind(i) != KIND_TILT) continue;
+    const int link = (int)G.v(i, 18);
+    S nl = S(0.0f);
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (j == link) nl = n[j];
+    const S rng = S(G.v(i, 19));
+    S sn, cs;
+    msincos(nl * rng, &sn, &cs);
+    const S omc = S(1.0f) - cs;
+    S dir = S(0.0f), dth = S(0.0f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const S b0 = S(G.v(i, k)), b1 = S(G.v(i, 6 + k)), b2 = S(G.v(i, 12 + k));
+      dir = dir + ltau[k] * (cs * b0 + sn * b1 + omc * b2);
+      dth = dth + ltau[k] * (-sn * b0 + cs * b1 + sn * b2);
+    }
+    lf[i] = lf[i] + dir;
+    const S lnl = f[i] * dth * rng;
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (j == link) ln[j] = ln[j] + lnl;
+  }
+}
+
+template <typename S, int NT, typename GenT>
+MG_HD void fin_wrench_vjp(const GenT& G, const S (&n)[NT], const S vr[3], const S w[3], const S ltau[6],
+                          S (&ln)[NT], S lvr[3], S lw[3]) {
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    if (G.kind(i) != KIND_FIN) continue;
+    S e1[3], e2[3], re1[3], re2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = S(G.v(i, k)); e2[k] = S(G.v(i, 3 + k)); re1[k] = S(G.v(i, 6 + k)); re2[k] = S(G.v(i, 9 + k));
+    }
+    const S xx = vr[0] * e1[0] + vr[1] * e1[1] + vr[2] * e1[2] + w[0] * re1[0] + w[1] * re1[1] + w[2] * re1[2];
+    const S yy = vr[0] * e2[0] + vr[1] * e2[1] + vr[2] * e2[2] + w[0] * re2[0] + w[1] * re2[1] + w[2] * re2[2];
+    const S U2 = xx * xx + yy * yy;
+    if (!(U2 > S(0.0f))) continue;
+    const S rng = S(G.v(i, 15));
+    S sn, cs;
+    msincos(n[i] * rng, &sn, &cs);
+    const S uc = cs * xx + sn * yy, un = cs * yy - sn * xx;
+    const S iU = minvsqrt(U2);
+    const S U = U2 * iU;
+    const S g = un * uc * iU;
+    const S kL = S(G.v(i, 12)), kD0 = S(G.v(i, 13)), kDa = S(G.v(i, 14));
+    const S D = kD0 * U + kDa * un * un * iU;
+    // F1 = kL g yy - D xx, F2 = -kL g xx - D yy; tau += F1 [e1; r x e1] + F2 [e2; r x e2].
+    S lF1 = S(0.0f), lF2 = S(0.0f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lF1 = lF1 + ltau[k] * e1[k] + ltau[3 + k] * re1[k];
+      lF2 = lF2 + ltau[k] * e2[k] + ltau[3 + k] * re2[k];
+    }
+    const S lg = kL * (lF1 * yy - lF2 * xx);
+    const S lD = -(lF1 * xx + lF2 * yy);
+    S lxx = -kL * g * lF2 - D * lF1;
+    S lyy = kL * g * lF1 - D * lF2;
+    // D = kD0 U + kDa un^2 iU ; g = un uc iU ; U = U2 iU ; iU = U2^-1/2
+    S lU = kD0 * lD;
+    S lun = S(2.0f) * kDa * un * iU * lD + uc * iU * lg;
+    S liU = kDa * un * un * lD + un * uc * lg;
+    const S luc = un * iU * lg;
+    S lU2 = iU * lU;
+    liU = liU + U2 * lU;
+    lU2 = lU2 - S(0.5f) * iU * iU * iU * liU;
+    // uc = cs xx + sn yy, un = cs yy - sn xx, th = n rng
+    lxx = lxx + cs * luc - sn * lun + S(2.0f) * xx * lU2;
+    lyy = lyy + sn * luc + cs * lun + S(2.0f) * yy * lU2;
+    const S lth = un * luc - uc * lun;
+    ln[i] = ln[i] + lth * rng;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lvr[k] = lvr[k] + e1[k] * lxx + e2[k] * lyy;
+      lw[k] = lw[k] + re1[k] * lxx + re2[k] * lyy;
+    }
+  }
+}
+
 // a3: body-frame current v_c = R^T V_c and relative velocity v_r = v - v_c.
 template <typename S, typename PhysT, bool CURRENT>
 MG_HD void rel_velocity(const S R[3][3], const S v[3], const PhysT& P, S vc[3], S vr[3]) {
@@ -666,10 +756,19 @@ MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, 
 // with its members, or (PhysT::kFull, payload runs) a view of the combined
 // body: full inverse Mi, inertia about the origin Io, first moment s, mass m
 // and weight W of vehicle and payload.
-template <typename S, int NT, typename ActT, typename PhysT>
+// `G`: NoGen, or the generic actuator table of a class with fins or tilted
+// propellers (their wrenches' products join the thrust and body terms).
+template <typename S, int NT, typename ActT, typename PhysT, typename GenT = NoGen>
 MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& tp, const S (&c)[NT],
-                         const PhysT& P, const ActT& A, S h, St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g) {
+                         const PhysT& P, const ActT& A, S h, St<S, NT>& lx, S (&lc)[NT], HydroGrad<S>& g,
+                         const GenT& G = GenT()) {
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
   const S z0 = S(0.0f);
+  // Generic wrenches: extra adjoints of the thrusts (tilt) and of the
+  // actuator states (servo links, fin angles).
+  S lfx[NT], lnx[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) { lfx[i] = z0; lnx[i] = z0; }
 
   // q1 = qn * inv
   S dot = q1[0] * lx.q[0] + q1[1] * lx.q[1] + q1[2] * lx.q[2] + q1[3] * lx.q[3];
@@ -836,6 +935,7 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
     }
     cross_vjp(w, vc, lwv, lw, lvc);
   }
+  if constexpr (GEN) fin_wrench_vjp<S, NT>(G, tp.n1, vr, w, lrhs, lnx, lvr, lw);
   // vr = v - vc ; vc = R^T Vc
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -849,16 +949,26 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
 #pragma unroll
   for (int j = 0; j < 3; ++j) LR[2][j] = LR[2][j] + le[j];
   rot_vjp(x0.q, LR, lq);
-  // tau = B f ; f_i = k n1 |n1|
+  // tau = B f (+ the tilt wrench) ; f_i = k n1 |n1|
+  if constexpr (GEN) {
+    S f1[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      const S an = mabs(tp.n1[i]);
+      f1[i] = (an < S(A.dz[i])) ? z0 : S(A.kf[i]) * tp.n1[i] * an;
+    }
+    tilt_wrench_vjp<S, NT>(G, tp.n1, f1, lrhs, lfx, lnx);
+  }
   S ln1[NT];
 #pragma unroll
   for (int i = 0; i < NT; ++i) {
     S lf = S(A.alloc[0][i]) * lrhs[0];
 #pragma unroll
     for (int k = 1; k < 6; ++k) lf = lf + S(A.alloc[k][i]) * lrhs[k];
+    lf = lf + lfx[i];
     const S an = mabs(tp.n1[i]);
     const S df = (an < S(A.dz[i])) ? z0 : S(2.0f) * S(A.kf[i]) * an;
-    ln1[i] = lx.n[i] + lf * df;
+    ln1[i] = lx.n[i] + lnx[i] + lf * df;
   }
   // n1 = n + alpha (c - n)
 #pragma unroll

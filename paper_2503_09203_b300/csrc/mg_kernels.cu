@@ -268,8 +268,8 @@ cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, co
 // a.tile_envs envs, a multiple of ADJ_ENVS) with that class's tables kc;
 // `dependent`: programmatic dependent of the previous launch; kern: the
 // kernel (the library's, or one compiled at run time for this class).
-static cudaError_t launch_adjoint_k(const void* kern, const AdjArgs& a, const ClassK& kc, bool dependent,
-                                    cudaStream_t st, size_t dyn_smem = 0) {
+static cudaError_t launch_adjoint_k(const void* kern, const AdjArgs& a, const ClassK& kc, const ClassG* kg,
+                                    bool dependent, cudaStream_t st, size_t dyn_smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.n_tiles * (a.tile_envs / ADJ_ENVS)));
   cfg.blockDim = dim3(ADJ_THREADS);
@@ -281,15 +281,18 @@ static cudaError_t launch_adjoint_k(const void* kern, const AdjArgs& a, const Cl
   cfg.attrs = attr;
   cfg.numAttrs = (MG_USE_PDL && dependent) ? 1 : 0;
   AdjArgs aa = a;
-  ClassK kk = kc;
-  void* args[] = {&aa, &kk};
+  ClassKG kk;
+  kk.k = kc;
+  if (kg) kk.g = *kg;
+  void* args[] = {&aa, kg ? static_cast<void*>(&kk) : static_cast<void*>(&kk.k)};
   return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
-// jit_kernel: a class-specialised adjoint kernel for nt thrusters compiled at
-// run time (null: the library's).
-cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st,
-                           const void* jit_kernel) {
+// kg: the class's generic actuator table (classes with fins or tilted
+// propellers), else null. jit_kernel: a class-specialised adjoint kernel for
+// nt thrusters compiled at run time (null: the library's).
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg, int nt, bool dependent,
+                           cudaStream_t st, const void* jit_kernel) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (a.tile_envs <= 0 || a.tile_envs % ADJ_ENVS != 0 || a.seg_hi - a.seg_lo != 1) return cudaErrorInvalidValue;
   if (a.pay_plane > 0) {
@@ -309,10 +312,18 @@ cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, int nt, bool depe
       if (e != cudaSuccess) return e;
       attr_set[dev].fetch_or(bit);
     }
-    return launch_adjoint_k(k, a, kc, dependent, st, ADJ_PAY_SMEM);
+    return launch_adjoint_k(k, a, kc, nullptr, dependent, st, ADJ_PAY_SMEM);
   }
-  if (jit_kernel) return launch_adjoint_k(jit_kernel, a, kc, dependent, st);
-#define MG_L(N) return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N>), a, kc, dependent, st)
+  if (kg) {
+#define MG_L(N)                                                                                               \
+  return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N, false, NoLit, true>), a, kc, kg, \
+                          dependent, st)
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  }
+  if (jit_kernel) return launch_adjoint_k(jit_kernel, a, kc, nullptr, dependent, st);
+#define MG_L(N) \
+  return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N>), a, kc, nullptr, dependent, st)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaErrorInvalidValue;

@@ -22,3 +22,38 @@ def oracle_env_arrays(p: dict) -> dict:
     """Per-env parameter dict (workloads.random_params keys) -> oracle env arrays."""
     keys = ("mass", "Ig", "rg", "rb", "W", "B", "Ma", "dl", "dq", "Vc", "target", "cls")
     return {k: p[k] for k in keys}
+
+
+def adjoint_vs_oracle_tangents(classes, sub_envs, s0, a, dt, K, g, go, gr, nthr, ids, rng, tol=1e-3):
+    """Per env: <gpu gradient, d> against the oracle's tangent of
+    sum_t <g_obs, obs_t> + <g_rew, rew_t> along d, for three directions per
+    gradient group (g: the GPU gradients of all envs; sub_envs: the oracle's
+    records of the envs `ids`). Per env the relative error over the directions
+    is at most `tol`."""
+    import oracle
+    n = len(ids)
+    T = a.shape[0]
+    thr_mask = (np.arange(8)[None, :] < nthr[ids][:, None]).astype(np.float64)
+    st_mask = (np.arange(21)[None, :] < (13 + nthr[ids])[:, None]).astype(np.float64)
+    groups = {"act": lambda: dict(d_actions=rng.normal(size=(T, n, 8)) * thr_mask[None]),
+              "A": lambda: dict(d_Ma=rng.normal(size=(n, 6))),
+              "dl": lambda: dict(d_dl=rng.normal(size=(n, 6))),
+              "dq": lambda: dict(d_dq=rng.normal(size=(n, 6))),
+              "s0": lambda: dict(d_state0=rng.normal(size=(n, 21)) * st_mask * 0.1)}
+    for name, mk in groups.items():
+        got, want = [], []
+        for _ in range(3):
+            d = mk()
+            j = oracle.rollout_jvp(classes, sub_envs, s0[ids].astype(np.float64), a[:, ids], dt, K, **d)
+            want.append(np.einsum("te,te->e", gr[:, ids], j["d_reward"]) +
+                        np.einsum("tek,tek->e", go[:, ids], j["d_obs"]))
+            if name == "act":
+                got.append(np.einsum("tek,tek->e", g["act"][:, ids], d["d_actions"]))
+            elif name == "s0":
+                got.append(np.einsum("ek,ek->e", g["s0"][ids], d["d_state0"]))
+            else:
+                key = {"A": "d_Ma", "dl": "d_dl", "dq": "d_dq"}[name]
+                got.append(np.einsum("ek,ek->e", g[name][ids], d[key]))
+        gv, rv = np.stack(got, 1), np.stack(want, 1)
+        err = np.linalg.norm(gv - rv, axis=1) / np.maximum(np.linalg.norm(rv, axis=1), 1e-6)
+        assert err.max() <= tol, (name, err.max(), int(ids[np.argmax(err)]))

@@ -6,7 +6,8 @@
 // and damping coefficients (the inverse mass matrix follows the added mass).
 // Prints the worst relative difference and, with a nonzero argument, the
 // same for a product whose added-mass gradient is scaled by 1.01 (the check
-// must see that). Both for the vehicle alone and with a point-mass payload.
+// must see that). For the vehicle alone, with a point-mass payload, and for a
+// class with fins and a servo-tilted propeller.
 #include <cstdio>
 #include <algorithm>
 #include <cmath>
@@ -192,6 +193,87 @@ double run_pay(std::mt19937_64& rng) {
   return std::fabs(fd - an) / std::max(1.0, std::fabs(fd));
 }
 
+// A generic class on the host: 4 fixed propellers, a servo, a propeller
+// tilted by that servo and 2 fins (table values random; the check is about
+// derivatives, not about a particular vehicle).
+struct GenH {
+  int k[8];
+  double vals[8][20];
+  int kind(int i) const { return k[i]; }
+  double v(int i, int j) const { return vals[i][j]; }
+};
+
+template <int NT>
+double run_gen(std::mt19937_64& rng) {
+  static_assert(NT == 8, "channel layout of the generic check");
+  std::uniform_real_distribution<double> U(-1, 1), P01(0.2, 2.0);
+  Phys<double> P; Act<double> Ac; In<NT> in; GenH G;
+  P.m = 12; P.W = 110; P.B = 113;
+  for (int j = 0; j < 3; ++j) { P.Ig[j] = P01(rng); P.rb[j] = U(rng) * 0.05; P.Vc[j] = U(rng) * 0.4; }
+  for (int j = 0; j < 6; ++j) { in.A[j] = P01(rng) * 3; in.dl[j] = P01(rng) * 5; in.dq[j] = P01(rng) * 10; }
+  for (int i = 0; i < 8; ++i) {
+    G.k[i] = i < 4 ? KIND_PROP : (i == 4 ? KIND_SERVO : (i == 5 ? KIND_TILT : KIND_FIN));
+    for (int j = 0; j < 20; ++j) G.vals[i][j] = U(rng);
+    for (int r = 0; r < 6; ++r) Ac.alloc[r][i] = i < 4 ? U(rng) : 0.0;
+    Ac.kf[i] = (i < 4 || i == 5) ? P01(rng) * 20 : 0.0;
+    Ac.dz[i] = 0.0;
+    Ac.alpha[i] = P01(rng) * 0.4;
+  }
+  G.vals[5][18] = 4;      // the tilted propeller follows the servo
+  G.vals[5][19] = 0.8;    // tilt range (rad)
+  for (int i = 6; i < 8; ++i) { G.vals[i][12] = 3.0; G.vals[i][13] = 0.5; G.vals[i][14] = 2.0; G.vals[i][15] = 0.5; }
+  const double h = 0.0025;
+  for (int j = 0; j < 3; ++j) in.x.p[j] = U(rng);
+  for (int j = 0; j < 4; ++j) in.x.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) in.x.nu[j] = U(rng);
+  for (int j = 0; j < NT; ++j) in.x.n[j] = U(rng);
+  for (int j = 0; j < NT; ++j) in.c[j] = U(rng);
+  auto phys_of = [&](const In<NT>& i2) {
+    Phys<double> Q = P;
+    const double Mrb[6] = {P.m, P.m, P.m, P.Ig[0], P.Ig[1], P.Ig[2]};
+    for (int j = 0; j < 6; ++j) { Q.A[j] = i2.A[j]; Q.dl[j] = i2.dl[j]; Q.dq[j] = i2.dq[j]; Q.minv[j] = 1.0 / (Mrb[j] + i2.A[j]); }
+    return Q;
+  };
+  auto fwd_gen = [&](const In<NT>& i2, St<double, NT>& out) {
+    const Phys<double> Q = phys_of(i2);
+    out = i2.x;
+    double c[NT]; for (int k = 0; k < NT; ++k) c[k] = i2.c[k];
+    substep<double, NT, false, Act<double>, Phys<double>, true, GenH>(out, c, Q, Ac, h, nullptr, G);
+  };
+  const Phys<double> Pb = phys_of(in);
+  St<double, NT> x = in.x; Tape<double, NT> tp;
+  substep<double, NT, true, Act<double>, Phys<double>, true, GenH>(x, in.c, Pb, Ac, h, &tp, G);
+  St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
+  Tape<double, NT> tr; double q1[4];
+  tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
+  St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
+  vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g, G);
+  In<NT> d;
+  for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
+  for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
+  for (int j = 0; j < NT; ++j) d.c[j] = U(rng);
+  for (int j = 0; j < 6; ++j) { d.A[j] = U(rng); d.dl[j] = U(rng); d.dq[j] = U(rng); }
+  const double eps = 1e-6;
+  auto shift = [&](double sc) { In<NT> o = in;
+    for (int j = 0; j < 3; ++j) o.x.p[j] += sc * d.x.p[j]; for (int j = 0; j < 4; ++j) o.x.q[j] += sc * d.x.q[j];
+    for (int j = 0; j < 6; ++j) o.x.nu[j] += sc * d.x.nu[j]; for (int j = 0; j < NT; ++j) o.x.n[j] += sc * d.x.n[j];
+    for (int j = 0; j < NT; ++j) o.c[j] += sc * d.c[j];
+    for (int j = 0; j < 6; ++j) { o.A[j] += sc * d.A[j]; o.dl[j] += sc * d.dl[j]; o.dq[j] += sc * d.dq[j]; }
+    return o; };
+  St<double, NT> yp, ym; fwd_gen(shift(eps), yp); fwd_gen(shift(-eps), ym);
+  double fd = 0;
+  for (int j = 0; j < 3; ++j) fd += lam.p[j] * (yp.p[j] - ym.p[j]); for (int j = 0; j < 4; ++j) fd += lam.q[j] * (yp.q[j] - ym.q[j]);
+  for (int j = 0; j < 6; ++j) fd += lam.nu[j] * (yp.nu[j] - ym.nu[j]); for (int j = 0; j < NT; ++j) fd += lam.n[j] * (yp.n[j] - ym.n[j]);
+  fd /= 2 * eps;
+  double an = 0;
+  for (int j = 0; j < 3; ++j) an += lx.p[j] * d.x.p[j]; for (int j = 0; j < 4; ++j) an += lx.q[j] * d.x.q[j];
+  for (int j = 0; j < 6; ++j) an += lx.nu[j] * d.x.nu[j]; for (int j = 0; j < NT; ++j) an += g_scale * lx.n[j] * d.x.n[j];
+  for (int j = 0; j < NT; ++j) an += lc[j] * d.c[j];
+  for (int j = 0; j < 6; ++j) an += g.A[j] * d.A[j] + g.dl[j] * d.dl[j] + g.dq[j] * d.dq[j];
+  return std::fabs(fd - an) / std::max(1.0, std::fabs(fd));
+}
+
 int main(int argc, char** argv) {
   for (int pass = 0; pass < (argc > 1 ? 2 : 1); ++pass) {
     g_scale = pass ? 1.01 : 1.0;
@@ -200,8 +282,11 @@ int main(int argc, char** argv) {
     double wp = 0;
     for (int k = 0; k < 300; ++k) { w = std::max(w, run<8>(rng)); w = std::max(w, run<5>(rng)); w = std::max(w, run<3>(rng)); }
     for (int k = 0; k < 300; ++k) { wp = std::max(wp, run_pay<8>(rng)); wp = std::max(wp, run_pay<4>(rng)); }
+    double wg = 0;
+    for (int k = 0; k < 300; ++k) wg = std::max(wg, run_gen<8>(rng));
     printf("%s %.6e\n", pass ? "scaled" : "worst", w);
     printf("%s %.6e\n", pass ? "scaled_payload" : "worst_payload", wp);
+    printf("%s %.6e\n", pass ? "scaled_generic" : "worst_generic", wg);
   }
   return 0;
 }

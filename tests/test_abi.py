@@ -78,11 +78,11 @@ def test_flop_count_is_host_only_and_sane(lib):
 
 
 @pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env", "payload_per_env",
-                                 "rk4_record", "payload_range"])
+                                 "ckpt_every", "payload_range"])
 def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
     classes = [vehicles.heavy8()]
     counts, dt, K, per_env, reset = [8], 0.01, 1, True, dict(vehicles.NO_DR)
-    record, payload, integ = 0, False, 0
+    record, payload, ckpt = 0, False, 0
     if bad == "dt":
         dt = -1.0
     elif bad == "K":
@@ -97,12 +97,12 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
         per_env, reset = False, dict(vehicles.DR_TRAIN)
     elif bad == "payload_per_env":
         per_env, payload = False, True
-    elif bad == "rk4_record":
-        record, integ = 10, 1   # RK4 runs have no adjoint
+    elif bad == "ckpt_every":
+        record, ckpt = 10, -1
     elif bad == "payload_range":
         payload, reset = True, dict(vehicles.PAYLOAD, payload_lo=0.3, payload_hi=0.1)
     with pytest.raises(B.MGError) as e:
-        B.mg_create(classes, counts, dt, K, per_env, reset, record_steps=record, payload=payload, integrator=integ)
+        B.mg_create(classes, counts, dt, K, per_env, reset, record_steps=record, ckpt_every=ckpt, payload=payload)
     assert e.value.code == B.MG_ERR_INVALID_ARG
     if bad.startswith("payload"):
         assert "payload" in str(e.value)
@@ -113,14 +113,11 @@ def test_error_strings(lib):
         assert lib.mg_strerror(code)
 
 
-@pytest.mark.parametrize("bad", ["record_generic", "record_rk4", "integrator", "fin_chord", "tilt_link", "kind",
-                                 "fin_rho"])
+@pytest.mark.parametrize("bad", ["record_rk4", "integrator", "fin_chord", "tilt_link", "kind", "fin_rho"])
 def test_create_rejects_bad_actuators_before_touching_the_device(lib, bad):
     classes = [vehicles.lauv(), vehicles.tilt_hauv()]
     counts, record, integ = [4, 4], 0, B.MG_INTEG_EULER
-    if bad == "record_generic":
-        record = 10
-    elif bad == "record_rk4":
+    if bad == "record_rk4":
         classes, counts, record, integ = [vehicles.heavy8()], [4], 10, B.MG_INTEG_RK4
     elif bad == "integrator":
         integ = 7

@@ -17,12 +17,12 @@ if not torch.cuda.is_available():
 import oracle
 from paper_2503_09203_b300 import binding as B
 from paper_2503_09203_b300 import vehicles, workloads
+from tests.helpers import adjoint_vs_oracle_tangents
 from tests.test_gpu_adjoint import gpu_gradients
 
 pytestmark = pytest.mark.gpu
 
 DT = 0.01
-TOL = 1e-3
 
 
 def payload_sim(counts, T, K, ckpt, seed):
@@ -36,38 +36,6 @@ def payload_sim(counts, T, K, ckpt, seed):
     s0 = workloads.random_states(seed + 1, sim.n_envs, nthr, pos_scale=2.0, vel_scale=0.3, rate_scale=0.4)
     sim.set_state(s0)
     return classes, sim, envs, s0, nthr
-
-
-def check_directions(classes, sub_envs, s0, a, K, g, go, gr, nthr, ids, rng):
-    """Per env: <gpu gradient, d> against the oracle's tangent of
-    sum_t <g_obs, obs_t> + <g_rew, rew_t> along d, for three directions per
-    gradient group."""
-    n = len(ids)
-    T = a.shape[0]
-    thr_mask = (np.arange(8)[None, :] < nthr[ids][:, None]).astype(np.float64)
-    st_mask = (np.arange(21)[None, :] < (13 + nthr[ids])[:, None]).astype(np.float64)
-    groups = {"act": lambda: dict(d_actions=rng.normal(size=(T, n, 8)) * thr_mask[None]),
-              "A": lambda: dict(d_Ma=rng.normal(size=(n, 6))),
-              "dl": lambda: dict(d_dl=rng.normal(size=(n, 6))),
-              "dq": lambda: dict(d_dq=rng.normal(size=(n, 6))),
-              "s0": lambda: dict(d_state0=rng.normal(size=(n, 21)) * st_mask * 0.1)}
-    for name, mk in groups.items():
-        got, want = [], []
-        for _ in range(3):
-            d = mk()
-            j = oracle.rollout_jvp(classes, sub_envs, s0[ids].astype(np.float64), a[:, ids], DT, K, **d)
-            want.append(np.einsum("te,te->e", gr[:, ids], j["d_reward"]) +
-                        np.einsum("tek,tek->e", go[:, ids], j["d_obs"]))
-            if name == "act":
-                got.append(np.einsum("tek,tek->e", g["act"][:, ids], d["d_actions"]))
-            elif name == "s0":
-                got.append(np.einsum("ek,ek->e", g["s0"][ids], d["d_state0"]))
-            else:
-                key = {"A": "d_Ma", "dl": "d_dl", "dq": "d_dq"}[name]
-                got.append(np.einsum("ek,ek->e", g[name][ids], d[key]))
-        gv, rv = np.stack(got, 1), np.stack(want, 1)
-        err = np.linalg.norm(gv - rv, axis=1) / np.maximum(np.linalg.norm(rv, axis=1), 1e-6)
-        assert err.max() <= TOL, (name, err.max(), int(ids[np.argmax(err)]))
 
 
 def test_payload_adjoint_matches_oracle_tangents():
@@ -84,7 +52,7 @@ def test_payload_adjoint_matches_oracle_tangents():
     g = gpu_gradients(sim, a, T, go, gr, np.zeros((E, 21)))
     assert sim.get_payload()[:, 0].min() > 0
     sim.close()
-    check_directions(classes, envs, s0, a, K, g, go, gr, nthr, np.arange(E), rng)
+    adjoint_vs_oracle_tangents(classes, envs, s0, a, DT, K, g, go, gr, nthr, np.arange(E), rng)
 
 
 def test_payload_adjoint_sampled_at_4096_envs():
@@ -105,7 +73,7 @@ def test_payload_adjoint_sampled_at_4096_envs():
     ids = np.unique(np.concatenate([rng.choice(E, 56, replace=False), [0, E - 1], bounds[:-1], bounds[:-1] - 1]))
     # The sampled envs' records, drawn with their own env ids.
     sub, _ = oracle.reset(classes, workloads.env_classes(counts)[ids], dict(vehicles.PAYLOAD_DR), 61, env_ids=ids)
-    check_directions(classes, sub, s0, a, K, g, go.astype(np.float64), gr.astype(np.float64), nthr, ids, rng)
+    adjoint_vs_oracle_tangents(classes, sub, s0, a, DT, K, g, go.astype(np.float64), gr.astype(np.float64), nthr, ids, rng)
 
 
 def test_set_payload_discards_the_recording():
