@@ -265,7 +265,7 @@ int mg_set_task(mg_sim* sim, const double* host, size_t bytes);
  * vehicle alone (mg_set_params recomputes the combined body). Both synchronise
  * the device. Errors: INVALID_ARG (not a payload run, buffer too small,
  * non-finite values, m_p < 0, an inertia that is not positive definite).
- * Payload runs reject mg_set_hydro, mg_rollout_fp64 and gradients. */
+ * Payload runs reject mg_set_hydro (use mg_set_params). */
 int mg_get_payload(const mg_sim* sim, double* host, size_t bytes);
 int mg_set_payload(mg_sim* sim, const double* host, size_t bytes);
 
@@ -363,7 +363,9 @@ int mg_set_hydro(mg_sim* sim, const float* A_dev, const float* dl_dev, const flo
  * current parameters, the added mass and damping optionally perturbed by
  * eps * (dA, ddl, ddq) (device doubles [n_slots][6] each, NULL = 0), and writes
  * reward_dev [n_steps][n_slots] (double) and, if not NULL, the final state
- * state_dev [n_slots][21] (double). Inverse inertia is recomputed in FP64. */
+ * state_dev [n_slots][21] (double). Inverse inertia is recomputed in FP64
+ * (payload runs: the combined body's full inverse, by Cholesky). Every class
+ * and integrator: fins and tilted propellers with their FP64 tables, RK4. */
 int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, const double* dA,
                     const double* ddl, const double* ddq, double eps, double* reward_dev, double* state_dev,
                     mg_stream_t stream);

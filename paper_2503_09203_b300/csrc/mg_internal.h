@@ -76,6 +76,12 @@ struct ClassG {
 };
 static_assert(sizeof(ClassG) == (8 + 160) * 4, "ClassG layout");
 
+// The same table in FP64 (the finite-difference check path).
+struct ClassGD {
+  int32_t kind[8];
+  double v[8][20];
+};
+
 // Kernel parameter of a one-class launch of a generic-actuator or RK4 step.
 struct ClassKG {
   ClassK k;
@@ -231,7 +237,7 @@ struct Fp64Args {
   const float* actions;
   int64_t act_stride;
   int32_t T;
-  int32_t pad0;
+  int32_t pay_plane;          // payload runs: first payload plane; 0: no payload
   const double* dA;
   const double* ddl;
   const double* ddq;
@@ -240,6 +246,7 @@ struct Fp64Args {
   double h;                   // dt / K in FP64
   double* reward;
   double* state_out;
+  const ClassGD* gen;         // generic actuator tables per class in FP64 (variants 1 and 2)
 };
 
 }  // namespace mg

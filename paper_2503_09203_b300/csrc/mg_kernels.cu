@@ -184,7 +184,25 @@ __global__ void mg_set_hydro_kernel(float4* planes, int64_t n_slots, const float
 // FP64 rollout for finite-difference checks (one env per thread).
 // ---------------------------------------------------------------------------
 
-template <int NT>
+// A class's generic actuator table in FP64 (fins, tilted propellers).
+struct GenD {
+  const ClassGD& g;
+  __device__ __forceinline__ int kind(int i) const { return g.kind[i]; }
+  __device__ __forceinline__ double v(int i, int k) const { return g.v[i][k]; }
+};
+
+// The combined body of a payload run in FP64 (the members the full-inertia
+// step reads): recomputed per env from the vehicle's parameters, the
+// perturbed added mass and the payload, so that a finite difference in the
+// added mass moves the full inverse.
+struct PhysPayD {
+  static constexpr bool kFull = true;
+  double A[6], dl[6], dq[6], B, rb[3], Vc[3], Mi[21], Io[6], s[3], m, W;
+};
+
+// VAR: 0 propellers with Euler, 1 generic actuators with Euler, 2 RK4.
+// PAY: payload runs.
+template <int NT, int VAR, bool PAY>
 __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
   const int64_t slot = sd.slot_off + i;
   const int64_t ns = a.n_slots;
@@ -205,6 +223,24 @@ __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
   for (int j = 0; j < 3; ++j) { P.Ig[j] = Pf.Ig[j]; P.rb[j] = Pf.rb[j]; P.Vc[j] = Pf.Vc[j]; }
   const double Mrb[6] = {P.m, P.m, P.m, P.Ig[0], P.Ig[1], P.Ig[2]};
   for (int j = 0; j < 6; ++j) P.minv[j] = 1.0 / (Mrb[j] + P.A[j]);
+  PhysPayD Q;
+  if constexpr (PAY) {
+    // Payload mass and position: plane PAY_MP / 4 of the payload block.
+    const float4 pv = __ldg(&a.planes[(int64_t)(a.pay_plane + PAY_MP / 4) * ns + slot]);
+    const double mp = pv.x, rp[3] = {pv.y, pv.z, pv.w};
+    double mt, sv[3], Io[3][3], Wt, Mi[6][6];
+    payload_body(P.m, P.Ig, P.A, P.W, mp, rp, &mt, sv, Io, &Wt, Mi);
+    for (int j = 0; j < 6; ++j) { Q.A[j] = P.A[j]; Q.dl[j] = P.dl[j]; Q.dq[j] = P.dq[j]; }
+    Q.B = P.B;
+    for (int j = 0; j < 3; ++j) { Q.rb[j] = P.rb[j]; Q.Vc[j] = P.Vc[j]; Q.s[j] = sv[j]; }
+    int q = 0;
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) Q.Mi[q++] = 0.5 * (Mi[r][c] + Mi[c][r]);
+    Q.Io[0] = Io[0][0]; Q.Io[1] = Io[0][1]; Q.Io[2] = Io[0][2];
+    Q.Io[3] = Io[1][1]; Q.Io[4] = Io[1][2]; Q.Io[5] = Io[2][2];
+    Q.m = mt;
+    Q.W = Wt;
+  }
   const float4 tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
   double tgt[3] = {tg.x, tg.y, tg.z};
   float4 tr[3] = {tg, tg, tg};
@@ -218,12 +254,24 @@ __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
   for (int j = 0; j < 4; ++j) x.q[j] = xf.q[j];
   for (int j = 0; j < 6; ++j) x.nu[j] = xf.nu[j];
   for (int j = 0; j < NT; ++j) x.n[j] = xf.n[j];
+  auto sub = [&](const auto& PP, const double (&c)[NT]) {
+    using PT = tt::decay_t<decltype(PP)>;
+    if constexpr (VAR == 2)
+      substep_rk4<double, NT, Act<double>, PT, true, GenD>(x, c, PP, A, a.h, GenD{a.gen[sd.cls]});
+    else if constexpr (VAR == 1)
+      substep<double, NT, false, Act<double>, PT, true, GenD>(x, c, PP, A, a.h, nullptr, GenD{a.gen[sd.cls]});
+    else
+      substep<double, NT, false>(x, c, PP, A, a.h, nullptr);
+  };
   for (int t = 0; t < a.T; ++t) {
     float raw[NT];
     load_actions<NT>(a.actions + t * a.act_stride + sd.act_off + i * NT, raw);
     double c[NT];
     for (int q = 0; q < NT; ++q) c[q] = raw[q] < -1.0f ? -1.0 : (raw[q] > 1.0f ? 1.0 : (double)raw[q]);
-    for (int k = 0; k < sd.K; ++k) substep<double, NT, false>(x, c, P, A, a.h, nullptr);
+    for (int k = 0; k < sd.K; ++k) {
+      if constexpr (PAY) sub(Q, c);
+      else sub(P, c);
+    }
     double o[13], r;
     if (sd.track) track_ref<double>(tg, tr[0], tr[1], tr[2], a.dt, (double)tg.w + (double)(t + 1), tgt);
     observe<double, NT>(x, c, tgt, o, r);
@@ -238,7 +286,7 @@ __device__ void fp64_env(const Fp64Args& a, const SegDesc& sd, int64_t i) {
   }
 }
 
-template <int NT>
+template <int NT, int VAR, bool PAY>
 __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp64Args a) {
   if ((int)blockIdx.x >= a.n_tiles) return;
   const int tile = a.tile_lo + blockIdx.x;
@@ -246,7 +294,7 @@ __global__ void __launch_bounds__(128) mg_fp64_kernel(const __grid_constant__ Fp
   const SegDesc& sd = a.segs[si];
   const int64_t i = (int64_t)(tile - sd.tile_begin) * blockDim.x + threadIdx.x;
   if (i >= sd.n_envs) return;
-  fp64_env<NT>(a, sd, i);
+  fp64_env<NT, VAR, PAY>(a, sd, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -329,12 +377,23 @@ cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg,
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st) {
-  if (a.n_tiles <= 0) return cudaSuccess;
-#define MG_L(N) mg_fp64_kernel<N><<<a.n_tiles, block, 0, st>>>(a)
+// FP64 launch of one group: var 0 propellers with Euler, 1 generic
+// actuators with Euler, 2 RK4; a.pay_plane > 0: payload run.
+template <int VAR, bool PAY>
+static cudaError_t launch_fp64_t(const Fp64Args& a, int nt, int block, cudaStream_t st) {
+#define MG_L(N) mg_fp64_kernel<N, VAR, PAY><<<a.n_tiles, block, 0, st>>>(a)
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L
   return cudaGetLastError();
+}
+
+cudaError_t launch_fp64(const Fp64Args& a, int nt, int var, int block, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  const bool pay = a.pay_plane > 0;
+  if (var == 0) return pay ? launch_fp64_t<0, true>(a, nt, block, st) : launch_fp64_t<0, false>(a, nt, block, st);
+  if (var == 1) return pay ? launch_fp64_t<1, true>(a, nt, block, st) : launch_fp64_t<1, false>(a, nt, block, st);
+  if (var == 2) return pay ? launch_fp64_t<2, true>(a, nt, block, st) : launch_fp64_t<2, false>(a, nt, block, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_pm0(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,

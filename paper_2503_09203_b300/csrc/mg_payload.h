@@ -27,14 +27,15 @@ namespace mg {
 
 constexpr double kPayloadGravity = 9.81;
 
-// Writes the PAY_DIM floats of the payload planes (layout PAY_*). Returns
-// false (and leaves `out` untouched) if M is not positive definite.
-MG_PAY_HD bool payload_block(double m, const double Ig[3], const double Ma[6], double W, double mp,
-                             const double rp[3], float out[PAY_DIM]) {
+// The combined body in FP64: mass mt, first moment s, inertia about the
+// origin Io, weight Wt and Mi = (M_RB + diag(Ma))^-1. Returns false if M is
+// not positive definite.
+MG_PAY_HD bool payload_body(double m, const double Ig[3], const double Ma[6], double W, double mp,
+                            const double rp[3], double* mt_out, double s[3], double Io[3][3], double* Wt,
+                            double Mi[6][6]) {
   const double mt = m + mp;
-  const double s[3] = {mp * rp[0], mp * rp[1], mp * rp[2]};
+  for (int j = 0; j < 3; ++j) s[j] = mp * rp[j];
   const double rp2 = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
-  double Io[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Io[i][j] = (i == j ? Ig[i] + mp * rp2 : 0.0) - mp * rp[i] * rp[j];
   // S(s) = [[0, -s_z, s_y], [s_z, 0, -s_x], [-s_y, s_x, 0]].
@@ -63,7 +64,6 @@ MG_PAY_HD bool payload_block(double m, const double Ig[3], const double Ma[6], d
     }
   }
   // Column c of M^-1 solves L L^T x = e_c.
-  double Mi[6][6];
   for (int c = 0; c < 6; ++c) {
     double y[6], x[6];
     for (int i = 0; i < 6; ++i) {
@@ -78,6 +78,17 @@ MG_PAY_HD bool payload_block(double m, const double Ig[3], const double Ma[6], d
     }
     for (int i = 0; i < 6; ++i) Mi[i][c] = x[i];
   }
+  *mt_out = mt;
+  *Wt = W + mp * kPayloadGravity;
+  return true;
+}
+
+// Writes the PAY_DIM floats of the payload planes (layout PAY_*). Returns
+// false (and leaves `out` untouched) if M is not positive definite.
+MG_PAY_HD bool payload_block(double m, const double Ig[3], const double Ma[6], double W, double mp,
+                             const double rp[3], float out[PAY_DIM]) {
+  double mt, s[3], Io[3][3], Wt, Mi[6][6];
+  if (!payload_body(m, Ig, Ma, W, mp, rp, &mt, s, Io, &Wt, Mi)) return false;
   int q = PAY_MINV;
   for (int i = 0; i < 6; ++i)
     for (int j = i; j < 6; ++j) out[q++] = (float)(0.5 * (Mi[i][j] + Mi[j][i]));
@@ -89,7 +100,7 @@ MG_PAY_HD bool payload_block(double m, const double Ig[3], const double Ma[6], d
   out[PAY_IO + 5] = (float)Io[2][2];
   for (int j = 0; j < 3; ++j) out[PAY_S + j] = (float)s[j];
   out[PAY_M] = (float)mt;
-  out[PAY_W] = (float)(W + mp * kPayloadGravity);
+  out[PAY_W] = (float)Wt;
   out[PAY_MP] = (float)mp;
   for (int j = 0; j < 3; ++j) out[PAY_RP + j] = (float)rp[j];
   return true;

@@ -35,7 +35,7 @@ size_t step_kernel_smem(int nt, int pm, bool track);
 }  // namespace mg
 
 namespace mg {
-cudaError_t launch_fp64(const Fp64Args& a, int nt, int block, cudaStream_t st);
+cudaError_t launch_fp64(const Fp64Args& a, int nt, int var, int block, cudaStream_t st);
 }  // namespace mg
 
 using namespace mg;
@@ -79,6 +79,7 @@ struct mg_sim {
   int32_t n_planes = 0;
   ClassF* d_cls = nullptr;
   ClassG* d_gen = nullptr;
+  ClassGD* d_gen64 = nullptr;   // the generic tables in FP64 (check path)
   ClassD* d_cls64 = nullptr;
   ClassNominal* d_nominal = nullptr;
   SegDesc* d_segs = nullptr;
@@ -209,12 +210,15 @@ static bool generic_class(const mg_class_desc& c) {
   return false;
 }
 
-// Generic actuator table of a class (FP64 geometry, stored FP32): fins
+// Generic actuator table of a class (FP64 geometry, stored as GT: ClassG in
+// FP32 for the kernels, ClassGD in FP64 for the check path): fins
 // e1, e2 = a x e1, r x e1, r x e2, 1/2 rho S (C_L_alpha, C_D0, C_D_alpha),
 // range; tilted propellers B0 = [d ; r x d], B1 = [a x d ; r x (a x d)],
 // B2 = (a . d) [a ; r x a], servo channel, servo range.
-static ClassG generic_table(const mg_class_desc& c) {
-  ClassG g;
+template <typename GT>
+static GT generic_table(const mg_class_desc& c) {
+  using V = tt::decay_t<decltype(GT::v[0][0])>;
+  GT g;
   std::memset(&g, 0, sizeof(g));
   auto crs = [](const double* a, const double* b, double* o) {
     o[0] = a[1] * b[2] - a[2] * b[1]; o[1] = a[2] * b[0] - a[0] * b[2]; o[2] = a[0] * b[1] - a[1] * b[0];
@@ -230,14 +234,14 @@ static ClassG generic_table(const mg_class_desc& c) {
       crs(r, e1, re1);
       crs(r, e2, re2);
       for (int k = 0; k < 3; ++k) {
-        g.v[i][k] = (float)e1[k]; g.v[i][3 + k] = (float)e2[k];
-        g.v[i][6 + k] = (float)re1[k]; g.v[i][9 + k] = (float)re2[k];
+        g.v[i][k] = (V)e1[k]; g.v[i][3 + k] = (V)e2[k];
+        g.v[i][6 + k] = (V)re1[k]; g.v[i][9 + k] = (V)re2[k];
       }
       const double qS = 0.5 * c.rho * c.fin_area[i];
-      g.v[i][12] = (float)(qS * c.fin_cl[i]);
-      g.v[i][13] = (float)(qS * c.fin_cd0[i]);
-      g.v[i][14] = (float)(qS * c.fin_cda[i]);
-      g.v[i][15] = (float)c.act_range[i];
+      g.v[i][12] = (V)(qS * c.fin_cl[i]);
+      g.v[i][13] = (V)(qS * c.fin_cd0[i]);
+      g.v[i][14] = (V)(qS * c.fin_cda[i]);
+      g.v[i][15] = (V)c.act_range[i];
     } else if (c.act_kind[i] == MG_ACT_TILT) {
       const double* d = c.thr_dir[i];
       double rd[3], ad[3], rad[3], ra[3];
@@ -247,12 +251,12 @@ static ClassG generic_table(const mg_class_desc& c) {
       crs(r, a, ra);
       const double adot = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
       for (int k = 0; k < 3; ++k) {
-        g.v[i][k] = (float)d[k]; g.v[i][3 + k] = (float)rd[k];
-        g.v[i][6 + k] = (float)ad[k]; g.v[i][9 + k] = (float)rad[k];
-        g.v[i][12 + k] = (float)(adot * a[k]); g.v[i][15 + k] = (float)(adot * ra[k]);
+        g.v[i][k] = (V)d[k]; g.v[i][3 + k] = (V)rd[k];
+        g.v[i][6 + k] = (V)ad[k]; g.v[i][9 + k] = (V)rad[k];
+        g.v[i][12 + k] = (V)(adot * a[k]); g.v[i][15 + k] = (V)(adot * ra[k]);
       }
-      g.v[i][18] = (float)c.act_link[i];
-      g.v[i][19] = (float)c.act_range[c.act_link[i]];
+      g.v[i][18] = (V)c.act_link[i];
+      g.v[i][19] = (V)c.act_range[c.act_link[i]];
     }
   }
   return g;
@@ -363,7 +367,7 @@ static int dev_alloc(mg_sim* sim, void** p, size_t bytes) {
 }
 
 static void free_all(mg_sim* sim) {
-  void* ps[] = {sim->d_state, sim->d_planes, sim->d_cls, sim->d_gen, sim->d_cls64, sim->d_nominal,
+  void* ps[] = {sim->d_state, sim->d_planes, sim->d_cls, sim->d_gen, sim->d_gen64, sim->d_cls64, sim->d_nominal,
                 sim->d_segs, sim->d_status, sim->d_ckpt, sim->d_scratch, sim->d_stage};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -498,6 +502,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if ((rc = dev_alloc(sim, (void**)&sim->d_planes, sizeof(float4) * sim->n_planes * slot)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_cls, sizeof(ClassF) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_gen, sizeof(ClassG) * sim->n_classes)) != MG_OK) return bail(rc);
+  if ((rc = dev_alloc(sim, (void**)&sim->d_gen64, sizeof(ClassGD) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_cls64, sizeof(ClassD) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_nominal, sizeof(ClassNominal) * sim->n_classes)) != MG_OK) return bail(rc);
   if ((rc = dev_alloc(sim, (void**)&sim->d_segs, sizeof(SegDesc) * MG_MAX_CLASSES)) != MG_OK) return bail(rc);
@@ -522,9 +527,11 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   std::vector<ClassD> cd(sim->n_classes);
   std::vector<ClassNominal> cn(sim->n_classes);
   std::vector<ClassG> cg(sim->n_classes);
+  std::vector<ClassGD> cgd(sim->n_classes);
   for (int c = 0; c < sim->n_classes; ++c) {
     const mg_class_desc& d = sim->classes[c];
-    cg[c] = generic_table(d);
+    cg[c] = generic_table<ClassG>(d);
+    cgd[c] = generic_table<ClassGD>(d);
     double B[6][8], al[8];
     alloc_of(d, B);
     alpha_of(d, sim->h, al);
@@ -564,6 +571,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_cls64, cd.data(), sizeof(ClassD) * cd.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_nominal, cn.data(), sizeof(ClassNominal) * cn.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_gen, cg.data(), sizeof(ClassG) * cg.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(sim->d_gen64, cgd.data(), sizeof(ClassGD) * cgd.size(), cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) { fail(sim, MG_ERR_CUDA, "class upload: %s", cudaGetErrorString(ce)); return bail(MG_ERR_CUDA); }
   if ((rc = upload_segs(sim)) != MG_OK) return bail(rc);
   // Rest state with nominal parameters.
@@ -1196,10 +1204,6 @@ int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, cons
                     const double* ddq, double eps, double* reward_dev, double* state_dev, mg_stream_t stream) {
   if (!sim) return MG_ERR_INVALID_ARG;
   if (!sim->cfg.per_env_params) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64 needs per_env_params");
-  if (sim->cfg.payload) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: not available for payload runs");
-  for (const Group& g : sim->groups)
-    if (g.var != 0)
-      return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: needs propeller-only classes and the Euler integrator");
   if (!actions_dev || !reward_dev || n_steps < 1) return fail(sim, MG_ERR_INVALID_ARG, "rollout_fp64: bad arguments");
   Fp64Args a;
   std::memset(&a, 0, sizeof(a));
@@ -1217,9 +1221,11 @@ int mg_rollout_fp64(mg_sim* sim, const float* actions_dev, int32_t n_steps, cons
   a.h = sim->h;
   a.reward = reward_dev;
   a.state_out = state_dev;
+  a.gen = sim->d_gen64;
+  a.pay_plane = sim->cfg.payload ? pay_plane(sim->cfg.task == 1) : 0;
   for (const Group& g : sim->groups) {
     a.seg_lo = g.seg_lo; a.seg_hi = g.seg_hi; a.tile_lo = g.tile_lo; a.n_tiles = g.n_tiles;
-    CK(launch_fp64(a, g.nt, sim->threads, (cudaStream_t)stream));
+    CK(launch_fp64(a, g.nt, g.var, sim->threads, (cudaStream_t)stream));
   }
   return MG_OK;
 }

@@ -57,3 +57,25 @@ def adjoint_vs_oracle_tangents(classes, sub_envs, s0, a, dt, K, g, go, gr, nthr,
         gv, rv = np.stack(got, 1), np.stack(want, 1)
         err = np.linalg.norm(gv - rv, axis=1) / np.maximum(np.linalg.norm(rv, axis=1), 1e-6)
         assert err.max() <= tol, (name, err.max(), int(ids[np.argmax(err)]))
+
+
+def fp64_reward_differences(sim, a_dev, T, dA, ddl, ddq, eps=1e-6):
+    """Per env, the central difference of the summed rewards of the FP64
+    check path (mg_rollout_fp64) along (dA, ddl, ddq) [n_envs][6] each, from
+    the simulator's current state."""
+    import torch
+    from paper_2503_09203_b300 import binding as B
+    slots = sim.slots_of_envs()
+
+    def to_slots(x):
+        out = np.zeros((sim.n_slots, 6))
+        out[slots] = x
+        return torch.from_numpy(out).cuda()
+
+    d = [to_slots(x) for x in (dA, ddl, ddq)]
+    r_p = torch.zeros(T, sim.n_slots, dtype=torch.float64, device="cuda")
+    r_m = torch.zeros_like(r_p)
+    B.mg_rollout_fp64(sim.handle, a_dev, T, d[0], d[1], d[2], eps, r_p)
+    B.mg_rollout_fp64(sim.handle, a_dev, T, d[0], d[1], d[2], -eps, r_m)
+    torch.cuda.synchronize()
+    return ((r_p - r_m).cpu().numpy()[:, slots] / (2 * eps)).sum(0)

@@ -147,13 +147,31 @@ def test_rest_stays_rest_bit_exact_for_every_type_and_integrator():
         sim.close()
 
 
-def test_rk4_run_refuses_the_fp64_check_path():
-    classes = vehicles.actuated_classes()
-    sim = B.Sim(classes, [4, 4, 4], dt=0.01, K=1, per_env_params=True, reset=dict(vehicles.HOVER),
-                integrator=B.MG_INTEG_RK4)
-    acts = sim.new_actions(2)
-    rew = torch.zeros(sim.n_slots, dtype=torch.float64, device="cuda")
-    with pytest.raises(B.MGError) as e:
-        B.mg_rollout_fp64(sim.handle, acts, 2, reward=rew)
-    assert e.value.code == B.MG_ERR_INVALID_ARG
+@pytest.mark.parametrize("integrator", [B.MG_INTEG_EULER, B.MG_INTEG_RK4])
+def test_fp64_check_path_matches_oracle(integrator):
+    """The FP64 rollout of the check path (fins and tilted propellers with
+    their FP64 tables, Euler or RK4) equals the oracle's FP64 rollout to near
+    machine precision, from the same state and per-env parameters (current
+    included)."""
+    classes = mixed_classes()
+    counts = [5, 6, 4, 3, 3]
+    T, K = 30, 4
+    cfg = vehicles.HOVER
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=True, reset=dict(cfg), integrator=integrator)
+    # Parameters both sides hold exactly (the GPU stores them in FP32).
+    p = workloads.random_params(23, classes, counts)
+    sim.set_params(B.dict_to_params(p, sim.n_envs))
+    envs = oracle.make_envs(oracle_env_arrays(p))
+    s0 = workloads.random_states(24, sim.n_envs, n_thr_of(classes, counts), pos_scale=2.0, vel_scale=0.3)
+    sim.set_state(s0)
+    a = workloads.actions(25, T, sim.n_envs)
+    rew = torch.zeros(T, sim.n_slots, dtype=torch.float64, device="cuda")
+    s_end = torch.zeros(sim.n_slots, 21, dtype=torch.float64, device="cuda")
+    B.mg_rollout_fp64(sim.handle, sim.pack_actions(a), T, reward=rew, state=s_end)
+    torch.cuda.synchronize()
+    slots = sim.slots_of_envs()
+    ref_s, _, ref_r = oracle.rollout(classes, envs, s0.astype(np.float64), a, 0.01, K, integ=integ_of(integrator))
+    np.testing.assert_allclose(rew.cpu().numpy()[:, slots], ref_r, rtol=1e-10, atol=1e-10)
+    got = align_q(s_end.cpu().numpy()[slots], ref_s)
+    np.testing.assert_allclose(got, ref_s, rtol=1e-10, atol=1e-10)
     sim.close()

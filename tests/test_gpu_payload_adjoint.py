@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 import oracle
 from paper_2503_09203_b300 import binding as B
 from paper_2503_09203_b300 import vehicles, workloads
-from tests.helpers import adjoint_vs_oracle_tangents
+from tests.helpers import adjoint_vs_oracle_tangents, fp64_reward_differences
 from tests.test_gpu_adjoint import gpu_gradients
 
 pytestmark = pytest.mark.gpu
@@ -94,3 +94,26 @@ def test_set_payload_discards_the_recording():
         B.mg_step_backward(sim.handle, a_dev, None, None, None, g_act, None, None, None)
     assert e.value.code == B.MG_ERR_STATE
     sim.close()
+
+
+def test_fp32_adjoint_against_fp64_differences():
+    """The FP32 adjoint's added-mass and damping gradients of the summed
+    reward against central differences of the GPU's FP64 check path
+    (h = 1e-6), and those differences against the oracle's tangents."""
+    counts = [3, 2, 2, 3, 2]
+    T, K = 30, 4
+    classes, sim, envs, s0, nthr = payload_sim(counts, T, K, 10, seed=101)
+    E = sim.n_envs
+    rng = np.random.default_rng(102)
+    a = workloads.actions(103, T, E, lo=-0.99, hi=0.99)
+    dA, ddl, ddq = (rng.normal(size=(E, 6)) for _ in range(3))
+    fd = fp64_reward_differences(sim, sim.pack_actions(a), T, dA, ddl, ddq)
+    j = oracle.rollout_jvp(classes, envs, s0.astype(np.float64), a, DT, K, d_Ma=dA, d_dl=ddl, d_dq=ddq)
+    jv = j["d_reward"].sum(0)
+    _, _, ref_r = oracle.rollout(classes, envs, s0.astype(np.float64), a, DT, K)
+    roundoff = 64 * np.finfo(np.float64).eps * np.abs(ref_r).sum(0) / 2e-6
+    assert np.all(np.abs(fd - jv) <= 1e-6 * np.abs(jv) + roundoff), np.abs(fd - jv).max()
+    g = gpu_gradients(sim, a, T, np.zeros((T, E, 13)), np.ones((T, E)), np.zeros((E, 21)))
+    sim.close()
+    adj = np.einsum("ek,ek->e", g["A"], dA) + np.einsum("ek,ek->e", g["dl"], ddl) + np.einsum("ek,ek->e", g["dq"], ddq)
+    assert (np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-3)).max() <= 1e-3
