@@ -31,6 +31,16 @@ struct SegDesc {
 };
 static_assert(sizeof(SegDesc) == 128, "SegDesc layout");
 
+// Generic actuator table of a class (fins, servo-tilted propellers): the kind
+// of each channel (as the bits of a float, so that the table stages into
+// shared memory as one float array) and 20 values per channel (layout in the
+// step arithmetic's header).
+struct ClassG {
+  int32_t kind[8];
+  float v[8][20];
+};
+static_assert(sizeof(ClassG) == (8 + 160) * 4, "ClassG layout");
+
 // Per-class constants in FP32 (staged into shared memory per tile).
 struct ClassF {
   float alloc[6][8];
@@ -38,8 +48,9 @@ struct ClassF {
   float dz[8];
   float phys[36];       // nominal Phys block (current 0)
   float pad[4];
+  ClassG gen;           // generic actuator table (serving ticks stage it per warp)
 };
-static_assert(sizeof(ClassF) == 104 * 4, "ClassF layout");
+static_assert(sizeof(ClassF) == (104 + 168) * 4, "ClassF layout");
 
 // Propeller steps with class-constant or payload parameters take allocation
 // rows premultiplied by the thrust constants (rows of B diag(k)): the thrust
@@ -65,16 +76,6 @@ struct ClassK {
   uint32_t pad[3];
 };
 static_assert(sizeof(ClassK) == 112 * 4, "ClassK layout");
-
-// Generic actuator table of a class (fins, servo-tilted propellers): the kind
-// of each channel (as the bits of a float, so that the table stages into
-// shared memory as one float array) and 20 values per channel (layout in the
-// step arithmetic's header).
-struct ClassG {
-  int32_t kind[8];
-  float v[8][20];
-};
-static_assert(sizeof(ClassG) == (8 + 160) * 4, "ClassG layout");
 
 // The same table in FP64 (the finite-difference check path).
 struct ClassGD {

@@ -282,6 +282,13 @@ static void alloc_of(const mg_class_desc& c, double B[6][8]) {
   }
 }
 
+// Class tables shared with the serving loop: the fixed-propeller allocation
+// columns (zero for the other channels), the generic actuator table, and
+// whether a class has channels other than fixed propellers.
+void class_alloc_table(const mg_class_desc& c, double B[6][8]) { alloc_of(c, B); }
+ClassG class_generic_table(const mg_class_desc& c) { return generic_table<ClassG>(c); }
+bool class_is_generic(const mg_class_desc& c) { return generic_class(c); }
+
 // Step variant of a class: 2 with the RK4 integrator, else 1 for a generic
 // class, 0 for a propeller-only class.
 static int class_var(const mg_sim* sim, int c) {
@@ -539,6 +546,7 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
     ClassD& g = cd[c];
     std::memset(&f, 0, sizeof(f));
     std::memset(&g, 0, sizeof(g));
+    f.gen = cg[c];
     for (int k = 0; k < 6; ++k)
       for (int i = 0; i < 8; ++i) { f.alloc[k][i] = (float)B[k][i]; g.alloc[k][i] = B[k][i]; }
     for (int i = 0; i < 8; ++i) {

@@ -43,9 +43,14 @@ namespace mg {
 cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                         bool dependent, bool shared_sm, cudaStream_t st);
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
-cudaError_t prepare_tick_pm0(int nt);
-cudaError_t prepare_tick_pm1(int nt);
+cudaError_t prepare_tick_pm0(int nt, int var);
+cudaError_t prepare_tick_pm1(int nt, int var);
 }  // namespace mg
+
+// Class tables built as the simulator builds them (mg_runtime.cpp).
+void class_alloc_table(const mg_class_desc& c, double B[6][8]);
+mg::ClassG class_generic_table(const mg_class_desc& c);
+bool class_is_generic(const mg_class_desc& c);
 
 using namespace mg;
 
@@ -155,6 +160,7 @@ struct Tick {
 struct mg_server {
   mg_server_config cfg{};
   std::vector<mg_class_desc> classes;
+  std::vector<int> class_var;   // step variant per class: 0 propellers, 1 generic actuators
   int device = 0;
   int num_sms = 148;
   // device
@@ -319,20 +325,22 @@ static bool enqueue_tick(mg_server* s, Tick& t) {
       cudaMemsetAsync(s->d_ret + sd.slot_off, 0, sizeof(float) * sd.n4, st);
     }
   }
-  // Tick table in one pass: requests grouped by thruster count, and the
-  // segment (within its group) of every tile.
-  struct G { int nt, lo, hi, tile_lo, tiles; };
+  // Tick table in one pass: requests grouped by thruster count and step
+  // variant (propellers, generic actuators), and the segment (within its
+  // group) of every tile.
+  struct G { int nt, var, lo, hi, tile_lo, tiles; };
   std::vector<G> groups;
-  std::vector<const Req*> by_nt[MG_MAX_THR + 1];
+  std::vector<const Req*> by_nt[2][MG_MAX_THR + 1];
   for (const Req* q : t.act) {
-    by_nt[q->n_thr].push_back(q);
+    by_nt[s->class_var[q->r.cls]][q->n_thr].push_back(q);
     t.envs += q->r.n_envs;
   }
   int n_seg = 0, tiles = 0;
-  for (int nt = 1; nt <= MG_MAX_THR; ++nt) {
-    if (by_nt[nt].empty()) continue;
-    G g{nt, n_seg, 0, tiles, 0};
-    for (const Req* q : by_nt[nt]) {
+  for (int key = 0; key < 2 * MG_MAX_THR; ++key) {
+    const int var = key / MG_MAX_THR, nt = 1 + key % MG_MAX_THR;
+    if (by_nt[var][nt].empty()) continue;
+    G g{nt, var, n_seg, 0, tiles, 0};
+    for (const Req* q : by_nt[var][nt]) {
       SegDesc& sd = b.h_segs[n_seg];
       sd = seg_of(*q);
       sd.tile_begin = tiles;
@@ -366,7 +374,7 @@ static bool enqueue_tick(mg_server* s, Tick& t) {
   for (const G& g : groups) {
     a.seg_lo = g.lo; a.seg_hi = g.hi; a.tile_lo = g.tile_lo; a.n_tiles = g.tiles;
     a.tile_seg = s->d_tile_seg + g.tile_lo;
-    launch_step(a, nullptr, nullptr, g.nt, 0, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
+    launch_step(a, nullptr, nullptr, g.nt, g.var, std::min(g.tiles, 4 * s->num_sms), !first, false, st);
     first = false;
   }
   cudaEventRecord(b.ev1, st);
@@ -537,12 +545,11 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     const mg_class_desc& d = classes[c];
     if (d.n_thr < 1 || d.n_thr > 8 || !(d.mass > 0) || d.rg[0] != 0 || d.rg[1] != 0 || d.rg[2] != 0)
       return MG_ERR_INVALID_ARG;
-    for (int i = 0; i < d.n_thr; ++i)
-      if (d.act_kind[i] != MG_ACT_PROP) return MG_ERR_INVALID_ARG;   // serving runs propeller-only classes
   }
   mg_server* s = new mg_server();
   s->cfg = *cfg;
   s->classes.assign(classes, classes + n_classes);
+  for (int c = 0; c < n_classes; ++c) s->class_var.push_back(class_is_generic(classes[c]) ? 1 : 0);
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   size_t budget = cfg->budget_bytes;
@@ -598,15 +605,14 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     const mg_class_desc& d = classes[c];
     ClassF& f = cf[c];
     std::memset(&f, 0, sizeof(f));
+    double B[6][8];
+    class_alloc_table(d, B);   // fixed propellers; zero columns for servos, fins and tilted propellers
     for (int i = 0; i < d.n_thr; ++i) {
-      const double* r = d.thr_pos[i];
-      const double* u = d.thr_dir[i];
-      const double B[6] = {u[0], u[1], u[2], r[1] * u[2] - r[2] * u[1], r[2] * u[0] - r[0] * u[2],
-                           r[0] * u[1] - r[1] * u[0]};
-      for (int k = 0; k < 6; ++k) f.alloc[k][i] = (float)B[k];
+      for (int k = 0; k < 6; ++k) f.alloc[k][i] = (float)B[k][i];
       f.kf[i] = (float)d.k_f[i];
       f.dz[i] = (float)d.deadzone[i];
     }
+    f.gen = class_generic_table(d);
     // Nominal physics block (class-constant ticks), in the order of the
     // per-env parameter block; no current.
     const double Mrb[6] = {d.mass, d.mass, d.mass, d.Ig[0], d.Ig[1], d.Ig[2]};
@@ -627,7 +633,8 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
     for (int j = 0; j < 6; ++j) { n.Ma[j] = d.Ma[j]; n.dl[j] = d.dl[j]; n.dq[j] = d.dq[j]; }
   }
   for (int c = 0; c < n_classes; ++c) {   // tick kernels loaded before the first request
-    const cudaError_t e = s->class_const ? prepare_tick_pm0(classes[c].n_thr) : prepare_tick_pm1(classes[c].n_thr);
+    const cudaError_t e = s->class_const ? prepare_tick_pm0(classes[c].n_thr, s->class_var[c])
+                                         : prepare_tick_pm1(classes[c].n_thr, s->class_var[c]);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cleanup(MG_ERR_CUDA);

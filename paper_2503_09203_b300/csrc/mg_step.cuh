@@ -500,20 +500,25 @@ __device__ __forceinline__ void stage_tables(const StepArgs& a, const SegDesc& s
 }
 
 // Class tables of segment `sd` into one warp's copies (lanes of that warp):
-// the actuator table, and for class-constant ticks (PM = 0) the nominal
-// physics block. Serving ticks: propeller steps, rows as staged above.
-template <int PM>
+// the actuator table, for class-constant ticks (PM = 0) the nominal physics
+// block, and for generic classes (VAR = 1) the generic actuator table.
+// Serving ticks: rows as staged above.
+template <int PM, int VAR>
 __device__ __forceinline__ void stage_tables_warp(const StepArgs& a, const SegDesc& sd, float* act, float* phys,
-                                                  int lane) {
+                                                  float* gen, int lane) {
   const ClassF& cf = a.classes[sd.cls];
   for (int k = lane; k < SA_DIM; k += WENV) {
-    if (k < 48) act[k] = Premul<PM, 0>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
+    if (k < 48) act[k] = Premul<PM, VAR>::value ? cf.alloc[k / 8][k % 8] * cf.kf[k % 8] : cf.alloc[k / 8][k % 8];
     else if (k < 56) act[k] = cf.kf[k - 48];
     else if (k < 64) act[k] = cf.dz[k - 56];
     else act[k] = sd.alpha[k - 64];
   }
   if (PM == 0)
     for (int k = lane; k < PAR_DIM; k += WENV) phys[k] = cf.phys[k];
+  if (VAR) {
+    const float* g = reinterpret_cast<const float*>(&cf.gen);
+    for (int k = lane; k < GEN_FLOATS; k += WENV) gen[k] = g[k];
+  }
 }
 
 // Issue the bulk copies of one warp's slice of a tile (lane 0 only). `nvw`
@@ -923,7 +928,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   // time. Other launches keep one per block.
   __shared__ __align__(16) float s_act[TM ? N_WARPS * SA_DIM : SA_DIM];
   __shared__ __align__(16) float s_phys[TM ? N_WARPS * PAR_DIM : PAR_DIM];
-  __shared__ __align__(16) float s_gen[VAR ? GEN_FLOATS : 4];
+  __shared__ __align__(16) float s_gen[VAR ? (TM ? N_WARPS * GEN_FLOATS : GEN_FLOATS) : 4];
   __shared__ __align__(8) uint64_t s_bar[N_WARPS][2];
   __shared__ SegDesc s_seg[SEG_CACHE];
   // The next launch of a step (another thruster count, disjoint envs) may
@@ -992,7 +997,8 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       // Per-env physics; the warp rewrites its own actuator table (its lanes
       // finished the previous tile at the warp barrier that ends each round).
       if (si != prev_seg) {
-        stage_tables_warp<PM>(a, sd, s_act + warp * SA_DIM, s_phys + warp * PAR_DIM, lane);
+        stage_tables_warp<PM, VAR>(a, sd, s_act + warp * SA_DIM, s_phys + warp * PAR_DIM,
+                                   s_gen + (TM && VAR ? warp * GEN_FLOATS : 0), lane);
         __syncwarp();
         prev_seg = si;
       }
@@ -1017,7 +1023,8 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
     }
     if (!failed)
       step_tile<NT, PM, VAR, KP, MS, PA>(a, kc, kg, sd, tile, smem_addr(s_act + (TM ? warp * SA_DIM : 0)),
-                                 smem_addr(s_phys + (TM ? warp * PAR_DIM : 0)), smem_addr(s_gen), b ? buf1 : buf0,
+                                 smem_addr(s_phys + (TM ? warp * PAR_DIM : 0)),
+                                 smem_addr(s_gen + (TM && VAR ? warp * GEN_FLOATS : 0)), b ? buf1 : buf0,
                                  MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     if (PA && !failed && tt_next < a.n_tiles) {
       // This thread is done with its parameter column: bring in the next tile's.
@@ -1147,10 +1154,13 @@ template <int PM>
 static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                                   bool dependent, bool shared_sm, cudaStream_t st) {
   if (kc && var != 0 && !kg) return cudaErrorInvalidValue;
-  if (a.act_mode == 1 && var == 0) {
-    // Serving ticks: per-env parameters (DR or current on), or class constants.
+  if (a.act_mode == 1 && var <= 1) {
+    // Serving ticks: per-env parameters (DR or current on), or class
+    // constants; propeller classes (var 0) or generic ones (var 1, the
+    // generic table staged per warp from the class records).
     if constexpr (PM <= 1) {
       if (kc) return cudaErrorInvalidValue;
+      if (var == 1) return launch_step_pv<PM, 1, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
       return launch_step_pv<PM, 0, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
     } else {
       return cudaErrorInvalidValue;
@@ -1179,7 +1189,12 @@ static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const Cla
 // ahead of the first tick: with lazy module loading the first launch of each
 // kernel otherwise pays the load, and early requests queue behind it.
 template <int PM>
-static cudaError_t prepare_tick_pm(int nt) {
+static cudaError_t prepare_tick_pm(int nt, int var) {
+  if (var == 1) {
+#define MG_L(N) return step_attrs<N, PM, 1, false, true, false>()
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  }
 #define MG_L(N) return step_attrs<N, PM, 0, false, true, false>()
   MG_NT_SWITCH(nt, MG_L)
 #undef MG_L

@@ -9,7 +9,7 @@ cudaError_t launch_step_pm1(const StepArgs& a, const ClassK* kc, const ClassG* k
   return launch_step_pm<1>(a, kc, kg, nt, var, grid, dependent, shared_sm, st);
 }
 
-cudaError_t prepare_tick_pm1(int nt) { return prepare_tick_pm<1>(nt); }
+cudaError_t prepare_tick_pm1(int nt, int var) { return prepare_tick_pm<1>(nt, var); }
 
 cudaError_t occupancy_pm1(int nt, int var, bool kp, bool track, int* blocks_per_sm) {
   return occupancy_pm<1>(nt, var, kp, track, blocks_per_sm);

@@ -134,9 +134,12 @@ def test_create_rejects_bad_actuators_before_touching_the_device(lib, bad):
     assert e.value.code == B.MG_ERR_INVALID_ARG
 
 
-def test_server_refuses_generic_classes(lib):
+def test_server_refuses_bad_classes_before_touching_the_device(lib):
+    """Generic classes are served; a class whose CoG is off the origin (only a
+    payload moves it) is refused before any device work."""
     with pytest.raises(B.MGError) as e:
-        B.mg_server_create([vehicles.heavy8(), vehicles.lauv()], dt=0.01, max_requests=4, max_queue=4)
+        B.mg_server_create([vehicles.lauv(), dict(vehicles.heavy8(), rg=(0.0, 0.0, 0.01))], dt=0.01,
+                           max_requests=4, max_queue=4)
     assert e.value.code == B.MG_ERR_INVALID_ARG
 
 

@@ -85,6 +85,40 @@ def test_request_alone_equals_in_mix_and_matches_oracle(cfg):
     np.testing.assert_allclose(alone["returns"], ret_ref, rtol=1e-4, atol=1e-3)
 
 
+@pytest.mark.parametrize("cfg", [CFG, dict(vehicles.HOVER)], ids=["per_env_dr", "class_constants"])
+def test_generic_classes_alone_equal_in_mix_and_match_oracle(cfg):
+    """The model library's other propulsion types served beside propeller
+    classes: a rudder-propeller (fins) and a tiltrotor (servo-tilted
+    propellers) request, each identical alone and in a mix of all five
+    classes, and equal to the oracle."""
+    classes = vehicles.actuated_classes() + [vehicles.five_classes()[1], vehicles.five_classes()[4]]
+    probes = [(1, 29, 30, 4, 424242), (2, 33, 25, 2, 737373)]
+    alone = [run_alone(classes, p, cfg=cfg) for p in probes]
+    for a in alone:
+        assert a["status"] == B.MG_REQ_DONE
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=cfg)
+    rng = np.random.default_rng(3)
+    others = [(int(rng.integers(0, 5)), int(rng.integers(1, 2000)), int(rng.integers(5, 40)),
+               int(rng.integers(1, 9)), int(rng.integers(1 << 40))) for _ in range(40)]
+    ids = [B.mg_server_submit(srv, *r) for r in others[:20]]
+    time.sleep(0.02)
+    pids = [B.mg_server_submit(srv, *p) for p in probes]
+    for r in others[20:]:
+        ids.append(B.mg_server_submit(srv, *r))
+        time.sleep(0.002)
+    B.mg_server_wait_idle(srv, 300)
+    mixed = [B.mg_server_poll(srv, pid) for pid in pids]
+    B.mg_server_destroy(srv)
+    for p, a, m in zip(probes, alone, mixed):
+        assert m["status"] == B.MG_REQ_DONE
+        assert np.array_equal(m["final_state"], a["final_state"])
+        assert np.array_equal(m["returns"], a["returns"])
+        s_ref, ret_ref = oracle_request(classes, p, cfg=cfg)
+        err = rel_state_err(a["final_state"].astype(np.float64), s_ref)
+        assert err.max() <= 1e-3, (p, err.max())
+        np.testing.assert_allclose(a["returns"], ret_ref, rtol=1e-4, atol=1e-3)
+
+
 def test_admission_waits_for_memory_and_refuses_impossible_requests():
     classes = vehicles.five_classes()
     # Budget for roughly 2 x 4096 envs: requests queue until space frees up.
