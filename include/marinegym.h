@@ -99,8 +99,8 @@ enum {
  * and the inverse inertia in FP64 and stores them FP32. The class's own CoG
  * is the body origin (r_g = 0) and its added mass is diagonal; an off-origin
  * CoG arises from a payload (see mg_set_payload). A class with any channel
- * other than MG_ACT_PROP (a "generic" class) has the step and the adjoint
- * (Euler) but no FP64 check path, payload or serving. */
+ * other than MG_ACT_PROP (a "generic" class) has the step, the adjoint
+ * (Euler), the FP64 check path and serving, but no payload. */
 typedef struct {
   int32_t n_thr;            /* 1..8 (the workloads use 4, 6, 8) */
   int32_t pad0;
@@ -524,8 +524,9 @@ typedef struct {
   int32_t pad0;
 } mg_server_stats;
 
-/* Errors of mg_server_create: INVALID_ARG (bad config, a class that is not
- * propeller-only or has r_g != 0), OOM. */
+/* Errors of mg_server_create: INVALID_ARG (bad config, a class with r_g != 0),
+ * OOM. Every actuator type is served (fixed propellers, fins, servo-tilted
+ * propellers; semi-implicit Euler). */
 int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, int32_t n_classes,
                      mg_server** out);
 int mg_server_submit(mg_server* srv, const mg_request* req, int64_t* id_out);
