@@ -93,7 +93,7 @@ def lib():
         _lib.or_rollout.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
                                     fp, dp, dp, dp, C.c_int, C.c_int, C.c_int]
         _lib.or_rollout_jvp.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
-                                        fp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+                                        fp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int, C.c_int]
         _lib.or_reset.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_int64, C.c_void_p,
                                   C.c_uint64, C.POINTER(C.c_int64), C.c_void_p, dp]
         _lib.or_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]
@@ -263,8 +263,9 @@ def rollout(classes, envs, state, actions, dt, K, obs=True, form=0, threads=0, i
 
 
 def rollout_jvp(classes, envs, state, actions, dt, K, d_actions=None, d_state0=None, d_Ma=None,
-                d_dl=None, d_dq=None, threads=0):
-    """Directional derivative of a rollout. Returns dict of values and tangents."""
+                d_dl=None, d_dq=None, threads=0, integ=0):
+    """Directional derivative of a rollout (integ: 0 semi-implicit Euler, 1
+    RK4). Returns dict of values and tangents."""
     L = lib()
     actions = np.ascontiguousarray(actions, dtype=np.float32)
     T, E = actions.shape[0], actions.shape[1]
@@ -277,7 +278,7 @@ def rollout_jvp(classes, envs, state, actions, dt, K, d_actions=None, d_state0=N
     cls = pack_classes(classes)
     rc = L.or_rollout_jvp(C.cast(cls, C.c_void_p), C.cast(envs, C.c_void_p), E, float(dt), int(K), T,
                           _fp(actions), _dp(d_actions), _dp(state), _dp(d_state0), _dp(d_Ma), _dp(d_dl),
-                          _dp(d_dq), _dp(d_state), _dp(o), _dp(do), _dp(r), _dp(dr), int(threads))
+                          _dp(d_dq), _dp(d_state), _dp(o), _dp(do), _dp(r), _dp(dr), int(threads), int(integ))
     if rc != 0:
         raise ValueError(f"or_rollout_jvp failed: {rc}")
     return dict(state=state, d_state=d_state, obs=o, d_obs=do, reward=r, d_reward=dr)

@@ -858,12 +858,13 @@ int or_rollout(const or_class* classes, const or_env* envs, int64_t n_envs, doub
 // Forward-mode directional derivative of a rollout (dual numbers). Tangent
 // inputs: d_actions [n_steps][n_envs][8], d_state0 [n_envs][21],
 // d_Ma/d_dl/d_dq [n_envs][6] (any may be NULL = 0). Outputs: values as in
-// or_rollout plus tangents d_state [n_envs][21], d_obs, d_reward.
+// or_rollout plus tangents d_state [n_envs][21], d_obs, d_reward. integ: the
+// integrator of the substep (0 semi-implicit Euler, 1 RK4), as in or_rollout.
 int or_rollout_jvp(const or_class* classes, const or_env* envs, int64_t n_envs, double dt, int K, int n_steps,
                    const float* actions, const double* d_actions, double* state, const double* d_state0,
                    const double* d_Ma, const double* d_dl, const double* d_dq, double* d_state, double* obs,
-                   double* d_obs, double* reward, double* d_reward, int n_threads) {
-  if (K < 1 || dt <= 0.0) return -1;
+                   double* d_obs, double* reward, double* d_reward, int n_threads, int integ) {
+  if (K < 1 || dt <= 0.0 || integ < 0 || integ > 1) return -1;
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(static)
   for (int64_t ei = 0; ei < n_envs; ++ei) {
@@ -885,7 +886,7 @@ int or_rollout_jvp(const or_class* classes, const or_env* envs, int64_t n_envs, 
       const int64_t ai = ((int64_t)t * n_envs + ei) * 8;
       for (int i = 0; i < c.n_thr; ++i)
         cmd[i] = clamp1(Dual((double)actions[ai + i], d_actions ? d_actions[ai + i] : 0.0));
-      for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, 0, s);
+      for (int k = 0; k < K; ++k) substep(c, e, alpha, h, cmd, 0, s, integ);
       Dual o[13], r;
       observe(c, e, (e.k0 + t + 1) * dt, s, cmd, o, &r);
       for (int i = 0; i < 13; ++i) {

@@ -158,7 +158,7 @@ struct AdjPrefetch {
 
 // Producer: recompute segment s from its checkpoint into the records of
 // buffer `buf`.
-template <int NT, bool PAY, typename ActT, typename GenT>
+template <int NT, bool PAY, int VAR, typename ActT, typename GenT>
 __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
                                             const Phys<float>& P, unsigned p_base, int64_t i, int s, float* buf) {
   const int64_t ns = a.n_slots, slot = sd.slot_off + i;
@@ -174,22 +174,34 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
     for (int q = 0; q < NT; ++q) c[q] = clamp1(raw[q]);
     for (int k = 0; k < sd.K; ++k) {
       St<float, NT> x0 = x;
-      Tape<float, NT> tp;
-      if constexpr (PAY) {
-        unsigned pb = p_base;
-        asm volatile("" : "+r"(pb));
-        substep<float, NT, true>(x, c, AdjPhysPay(pb), A, sd.h, &tp);
+      if constexpr (VAR == 2) {
+        // RK4: the record is the start state (the reverse pass recomputes the stages).
+        if constexpr (PAY) {
+          unsigned pb = p_base;
+          asm volatile("" : "+r"(pb));
+          substep_rk4<float, NT, ActT, AdjPhysPay, true, GenT>(x, c, AdjPhysPay(pb), A, sd.h, G);
+        } else {
+          substep_rk4<float, NT, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, G);
+        }
+        store_record<NT>(rec, x0, nullptr);
       } else {
-        substep<float, NT, true, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, &tp, G);
+        Tape<float, NT> tp;
+        if constexpr (PAY) {
+          unsigned pb = p_base;
+          asm volatile("" : "+r"(pb));
+          substep<float, NT, true>(x, c, AdjPhysPay(pb), A, sd.h, &tp);
+        } else {
+          substep<float, NT, true, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, &tp, G);
+        }
+        store_record<NT>(rec, x0, tp.rhs);
       }
-      store_record<NT>(rec, x0, tp.rhs);
       rec += rstride;
     }
   }
   store_record<NT>(rec, x, nullptr);
 }
 
-template <int NT, bool PAY, typename ActT, typename GenT>
+template <int NT, bool PAY, int VAR, typename ActT, typename GenT>
 __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
                                             int64_t i, bool valid, float* s_rec, float* s_step, float* s_par) {
   const int role = threadIdx.x / ADJ_ENVS;   // 0: reverse pass, 1: forward recompute
@@ -254,7 +266,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 
   for (int it = 0; it <= n_seg; ++it) {
     if (role == 1 && it < n_seg && valid)
-      adj_produce<NT, PAY>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
+      adj_produce<NT, PAY, VAR>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
     if (role == 0 && it >= 1 && valid) {
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
@@ -297,16 +309,27 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
           pf.read<NT>(j % ADJ_RING, xs, rhs);
           // Records j - 1 and j - 2 stream in while this substep's product runs.
           if (j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
-          Tape<float, NT> tp;
-          if constexpr (PAY) {
-            unsigned pb = p_base;
-            asm volatile("" : "+r"(pb));
-            const AdjPhysPay Pv(pb);
-            tape_from_rhs<float, NT>(xs, c, Pv, A, sd.h, rhs, tp, q1);
-            vjp_from_tape<float, NT>(xs, q1, tp, c, Pv, A, sd.h, lam, lc, g);
+          if constexpr (VAR == 2) {
+            // RK4: the stages are recomputed from the substep's start state.
+            if constexpr (PAY) {
+              unsigned pb = p_base;
+              asm volatile("" : "+r"(pb));
+              substep_rk4_vjp<float, NT, ActT, AdjPhysPay, true, GenT>(xs, c, AdjPhysPay(pb), A, sd.h, lam, lc, g, G);
+            } else {
+              substep_rk4_vjp<float, NT, ActT, Phys<float>, true, GenT>(xs, c, P, A, sd.h, lam, lc, g, G);
+            }
           } else {
-            tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
-            vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g, G);
+            Tape<float, NT> tp;
+            if constexpr (PAY) {
+              unsigned pb = p_base;
+              asm volatile("" : "+r"(pb));
+              const AdjPhysPay Pv(pb);
+              tape_from_rhs<float, NT>(xs, c, Pv, A, sd.h, rhs, tp, q1);
+              vjp_from_tape<float, NT>(xs, q1, tp, c, Pv, A, sd.h, lam, lc, g);
+            } else {
+              tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
+              vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g, G);
+            }
           }
         }
         if (a.g_actions) {
@@ -352,13 +375,15 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
 // (literal operands: zero allocation entries and a zero dead zone drop out).
 // PAY: payload runs (the combined body's full inverse and inertia, read
 // from a shared-memory column per env: ADJ_PAY_SMEM bytes of dynamic shared
-// memory). GEN: classes with fins or servo-tilted propellers (the kernel
+// memory). VAR: 0 propeller classes with Euler, 1 classes with fins or
+// servo-tilted propellers with Euler, 2 RK4 runs (1 and 2: the kernel
 // parameter carries the generic actuator table too).
-template <int NT, bool PAY = false, class LIT = NoLit, bool GEN = false>
+template <int NT, bool PAY = false, class LIT = NoLit, int VAR = 0>
 __global__ void __launch_bounds__(ADJ_THREADS)
     mg_adjoint_kernel(const __grid_constant__ AdjArgs a,
-                      const __grid_constant__ tt::conditional_t<GEN, ClassKG, ClassK> kp) {
-  static_assert(!(PAY && GEN), "payload runs are propeller classes");
+                      const __grid_constant__ tt::conditional_t<VAR != 0, ClassKG, ClassK> kp) {
+  constexpr bool GEN = VAR != 0;
+  static_assert(!(PAY && VAR == 1), "payload runs are propeller classes");
   constexpr bool HAS_LIT = !tt::is_same<LIT, NoLit>::value;
   [[maybe_unused]] constexpr ClassK klit = LIT::make();
   const ClassK* kt;
@@ -385,8 +410,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
     // Every thread of the block takes part in the per-segment barriers.
     const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track};
-    if constexpr (GEN) adjoint_env<NT, PAY>(a, sr, *kt, GenK{kp.g}, i, valid, s_rec, s_step, s_dyn);
-    else adjoint_env<NT, PAY>(a, sr, *kt, NoGen{}, i, valid, s_rec, s_step, s_dyn);
+    if constexpr (GEN) adjoint_env<NT, PAY, VAR>(a, sr, *kt, GenK{kp.g}, i, valid, s_rec, s_step, s_dyn);
+    else adjoint_env<NT, PAY, VAR>(a, sr, *kt, NoGen{}, i, valid, s_rec, s_step, s_dyn);
   }
   // Completion stays ordered along the stream (see the step kernel).
   asm volatile("griddepcontrol.wait;" ::: "memory");

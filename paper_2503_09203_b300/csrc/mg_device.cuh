@@ -706,6 +706,116 @@ MG_HD void observe_vjp(const St<S, NT>& x, const S (&c)[NT], const S tgt[3], con
   for (int i = 0; i < NT; ++i) lc[i] = lc[i] - S(0.02) * c[i] * g_rew;
 }
 
+// Adjoint of the body terms of rhs (a4-a7: C_RB, C_A with the current term,
+// damping and restoring; the vehicle alone or, PhysT::kFull, the combined
+// body of a payload run) given lrhs: accumulates the adjoints of v, w, v_r,
+// v_c and e = R^T e_3 and of the added-mass and damping coefficients. The
+// wrench tau enters rhs with +1 (its adjoint is lrhs).
+template <typename S, typename PhysT>
+MG_HD void body_rhs_vjp(const S lrhs[6], const S v[3], const S w[3], const S vr[3], const S vc[3], const PhysT& P,
+                        S lv[3], S lw[3], S lvr[3], S lvc[3], S le[3], HydroGrad<S>& g) {
+  const S z0 = S(0.0f);
+  // (W-B) e  and  -(B rb) x e
+  const S WmB = S(P.W) - S(P.B);
+  S Brb[3] = {S(P.B) * S(P.rb[0]), S(P.B) * S(P.rb[1]), S(P.B) * S(P.rb[2])};
+  if constexpr (PhysT::kFull) {
+    // Weight at r_g = s / m: the moment arm is B r_b - (W / m) s.
+    const S wpm = S(P.W) / S(P.m);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Brb[j] = Brb[j] - wpm * S(P.s[j]);
+  }
+  {
+    // d/de of -(B rb) x e contracted with lrhs_ang: (-lrhs_ang) x (B rb).
+    const S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    S t[3];
+    cross3(nl, Brb, t);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) le[j] = le[j] + t[j] + WmB * lrhs[j];
+  }
+  // damping on nu_r
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const S ldm = -lrhs[j];
+    const S a = mabs(vr[j]);
+    lvr[j] = lvr[j] + ldm * (P.dl[j] + S(2.0f) * P.dq[j] * a);
+    g.dl[j] = g.dl[j] + ldm * vr[j];
+    g.dq[j] = g.dq[j] + ldm * a * vr[j];
+    const S ldw = -lrhs[3 + j];
+    const S b = mabs(w[j]);
+    lw[j] = lw[j] + ldw * (P.dl[3 + j] + S(2.0f) * P.dq[3 + j] * b);
+    g.dl[3 + j] = g.dl[3 + j] + ldw * w[j];
+    g.dq[3 + j] = g.dq[3 + j] + ldw * b * w[j];
+  }
+  // C_RB + C_A in the forward's merged form: rhs_lin -= w x bl with
+  // bl = m v + a1; rhs_ang -= w x ba + vr x a1 with ba = A_ang o w + Iw
+  // (Iw = Ig o w, or Io w about the origin with a payload); a1 = A_lin o vr.
+  {
+    S a1[3], bl[3], ba[3], Iw[3];
+    if constexpr (PhysT::kFull) {
+      Iw[0] = S(P.Io[0]) * w[0] + S(P.Io[1]) * w[1] + S(P.Io[2]) * w[2];
+      Iw[1] = S(P.Io[1]) * w[0] + S(P.Io[3]) * w[1] + S(P.Io[4]) * w[2];
+      Iw[2] = S(P.Io[2]) * w[0] + S(P.Io[4]) * w[1] + S(P.Io[5]) * w[2];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Iw[j] = S(P.Ig[j]) * w[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a1[j] = S(P.A[j]) * vr[j];
+      bl[j] = S(P.m) * v[j] + a1[j];
+      ba[j] = S(P.A[3 + j]) * w[j] + Iw[j];
+    }
+    S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
+    S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
+    S lbl[3] = {z0, z0, z0}, lba[3] = {z0, z0, z0}, la1[3] = {z0, z0, z0};
+    cross_vjp(w, bl, nl, lw, lbl);
+    cross_vjp(w, ba, na, lw, lba);
+    cross_vjp(vr, a1, na, lvr, la1);
+    // d(Iw)/dw contracted with lba: Ig o lba, or Io lba (symmetric).
+    S lIw[3];
+    if constexpr (PhysT::kFull) {
+      lIw[0] = S(P.Io[0]) * lba[0] + S(P.Io[1]) * lba[1] + S(P.Io[2]) * lba[2];
+      lIw[1] = S(P.Io[1]) * lba[0] + S(P.Io[3]) * lba[1] + S(P.Io[4]) * lba[2];
+      lIw[2] = S(P.Io[2]) * lba[0] + S(P.Io[4]) * lba[1] + S(P.Io[5]) * lba[2];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) lIw[j] = S(P.Ig[j]) * lba[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lv[j] = lv[j] + S(P.m) * lbl[j];
+      la1[j] = la1[j] + lbl[j];
+      lw[j] = lw[j] + S(P.A[3 + j]) * lba[j] + lIw[j];
+      g.A[3 + j] = g.A[3 + j] + lba[j] * w[j];
+      g.A[j] = g.A[j] + la1[j] * vr[j];
+      lvr[j] = lvr[j] + la1[j] * S(P.A[j]);
+    }
+    if constexpr (PhysT::kFull) {
+      // Off-origin centre of gravity: rhs_lin -= w x (w x s),
+      // rhs_ang -= s x (w x v).
+      const S sv[3] = {S(P.s[0]), S(P.s[1]), S(P.s[2])};
+      S wxs[3], lwxs[3] = {z0, z0, z0}, t[3], lz[3];
+      cross3(w, sv, wxs);
+      cross_vjp(w, wxs, nl, lw, lwxs);
+      cross3(sv, lwxs, t);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) lw[j] = lw[j] + t[j];
+      cross3(na, sv, lz);
+      cross_vjp(w, v, lz, lw, lv);
+    }
+    // current-acceleration term A_lin o (w x vc)
+    S wxvc[3];
+    cross3(w, vc, wxvc);
+    S lwv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      g.A[j] = g.A[j] - lrhs[j] * wxvc[j];
+      lwv[j] = -lrhs[j] * S(P.A[j]);
+    }
+    cross_vjp(w, vc, lwv, lw, lvc);
+  }
+}
+
 // Tape of one substep rebuilt from its start state x0 and its right-hand side
 // rhs (M nu_dot of a4-a7, which the forward recompute stores with the state):
 // the rest of the tape (rotor states, R, current, relative velocity, the new
@@ -837,104 +947,7 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
   const S v[3] = {x0.nu[0], x0.nu[1], x0.nu[2]};
   S lv[3] = {z0, z0, z0}, lw[3] = {z0, z0, z0}, lvr[3] = {z0, z0, z0}, lvc[3] = {z0, z0, z0};
   S le[3] = {z0, z0, z0};
-  // (W-B) e  and  -(B rb) x e
-  const S WmB = S(P.W) - S(P.B);
-  S Brb[3] = {S(P.B) * S(P.rb[0]), S(P.B) * S(P.rb[1]), S(P.B) * S(P.rb[2])};
-  if constexpr (PhysT::kFull) {
-    // Weight at r_g = s / m: the moment arm is B r_b - (W / m) s.
-    const S wpm = S(P.W) / S(P.m);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Brb[j] = Brb[j] - wpm * S(P.s[j]);
-  }
-  {
-    // d/de of -(B rb) x e contracted with lrhs_ang: (-lrhs_ang) x (B rb).
-    const S nl[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
-    cross3(nl, Brb, le);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) le[j] = le[j] + WmB * lrhs[j];
-  }
-  // damping on nu_r
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const S ldm = -lrhs[j];
-    const S a = mabs(vr[j]);
-    lvr[j] = lvr[j] + ldm * (P.dl[j] + S(2.0f) * P.dq[j] * a);
-    g.dl[j] = g.dl[j] + ldm * vr[j];
-    g.dq[j] = g.dq[j] + ldm * a * vr[j];
-    const S ldw = -lrhs[3 + j];
-    const S b = mabs(w[j]);
-    lw[j] = lw[j] + ldw * (P.dl[3 + j] + S(2.0f) * P.dq[3 + j] * b);
-    g.dl[3 + j] = g.dl[3 + j] + ldw * w[j];
-    g.dq[3 + j] = g.dq[3 + j] + ldw * b * w[j];
-  }
-  // C_RB + C_A in the forward's merged form: rhs_lin -= w x bl with
-  // bl = m v + a1; rhs_ang -= w x ba + vr x a1 with ba = A_ang o w + Iw
-  // (Iw = Ig o w, or Io w about the origin with a payload); a1 = A_lin o vr.
-  {
-    S a1[3], bl[3], ba[3], Iw[3];
-    if constexpr (PhysT::kFull) {
-      Iw[0] = S(P.Io[0]) * w[0] + S(P.Io[1]) * w[1] + S(P.Io[2]) * w[2];
-      Iw[1] = S(P.Io[1]) * w[0] + S(P.Io[3]) * w[1] + S(P.Io[4]) * w[2];
-      Iw[2] = S(P.Io[2]) * w[0] + S(P.Io[4]) * w[1] + S(P.Io[5]) * w[2];
-    } else {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Iw[j] = S(P.Ig[j]) * w[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      a1[j] = S(P.A[j]) * vr[j];
-      bl[j] = S(P.m) * v[j] + a1[j];
-      ba[j] = S(P.A[3 + j]) * w[j] + Iw[j];
-    }
-    S nl[3] = {-lrhs[0], -lrhs[1], -lrhs[2]};
-    S na[3] = {-lrhs[3], -lrhs[4], -lrhs[5]};
-    S lbl[3] = {z0, z0, z0}, lba[3] = {z0, z0, z0}, la1[3] = {z0, z0, z0};
-    cross_vjp(w, bl, nl, lw, lbl);
-    cross_vjp(w, ba, na, lw, lba);
-    cross_vjp(vr, a1, na, lvr, la1);
-    // d(Iw)/dw contracted with lba: Ig o lba, or Io lba (symmetric).
-    S lIw[3];
-    if constexpr (PhysT::kFull) {
-      lIw[0] = S(P.Io[0]) * lba[0] + S(P.Io[1]) * lba[1] + S(P.Io[2]) * lba[2];
-      lIw[1] = S(P.Io[1]) * lba[0] + S(P.Io[3]) * lba[1] + S(P.Io[4]) * lba[2];
-      lIw[2] = S(P.Io[2]) * lba[0] + S(P.Io[4]) * lba[1] + S(P.Io[5]) * lba[2];
-    } else {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) lIw[j] = S(P.Ig[j]) * lba[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      lv[j] = lv[j] + S(P.m) * lbl[j];
-      la1[j] = la1[j] + lbl[j];
-      lw[j] = lw[j] + S(P.A[3 + j]) * lba[j] + lIw[j];
-      g.A[3 + j] = g.A[3 + j] + lba[j] * w[j];
-      g.A[j] = g.A[j] + la1[j] * vr[j];
-      lvr[j] = lvr[j] + la1[j] * S(P.A[j]);
-    }
-    if constexpr (PhysT::kFull) {
-      // Off-origin centre of gravity: rhs_lin -= w x (w x s),
-      // rhs_ang -= s x (w x v).
-      const S sv[3] = {S(P.s[0]), S(P.s[1]), S(P.s[2])};
-      S wxs[3], lwxs[3] = {z0, z0, z0}, t[3], lz[3];
-      cross3(w, sv, wxs);
-      cross_vjp(w, wxs, nl, lw, lwxs);
-      cross3(sv, lwxs, t);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) lw[j] = lw[j] + t[j];
-      cross3(na, sv, lz);
-      cross_vjp(w, v, lz, lw, lv);
-    }
-    // current-acceleration term A_lin o (w x vc)
-    S wxvc[3];
-    cross3(w, vc, wxvc);
-    S lwv[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      g.A[j] = g.A[j] - lrhs[j] * wxvc[j];
-      lwv[j] = -lrhs[j] * S(P.A[j]);
-    }
-    cross_vjp(w, vc, lwv, lw, lvc);
-  }
+  body_rhs_vjp<S, PhysT>(lrhs, v, w, vr, vc, P, lv, lw, lvr, lvc, le, g);
   if constexpr (GEN) fin_wrench_vjp<S, NT>(G, tp.n1, vr, w, lrhs, lnx, lvr, lw);
   // vr = v - vc ; vc = R^T Vc
 #pragma unroll
@@ -984,6 +997,193 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
 #pragma unroll
   for (int i = 0; i < 4; ++i) lx.q[i] = lq[i];
   // lx.p: identity through p1 = p + ...
+}
+
+// Adjoint of one RK4 stage derivative F(q, nu) = (R v, 1/2 q (x) (0, w),
+// M^-1 rhs) at the stage point (q, nu) (R from the normalised q), with the
+// actuator states n and the state-independent wrench tau_n held: from the
+// adjoints ldp, ldq, ldnu of F it accumulates those of the stage point (lq,
+// lnu), of tau_n (ltau), of the fin angles (ln) and of the coefficients (g).
+template <typename S, int NT, typename PhysT, bool CURRENT, typename GenT>
+MG_HD void rk4_stage_vjp(const S q[4], const S nu[6], const S (&n)[NT], const S tau_n[6], const PhysT& P,
+                         const GenT& G, const S ldp[3], const S ldq[4], const S ldnu[6], S lq[4], S lnu[6],
+                         S ltau[6], S (&ln)[NT], HydroGrad<S>& g) {
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
+  const S z0 = S(0.0f);
+  // Forward internals.
+  const S iq = minvsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const S qh[4] = {q[0] * iq, q[1] * iq, q[2] * iq, q[3] * iq};
+  S R[3][3];
+  rot(qh, R);
+  const S v[3] = {nu[0], nu[1], nu[2]};
+  const S w[3] = {nu[3], nu[4], nu[5]};
+  S vc[3], vr[3], tau[6];
+  rel_velocity<S, PhysT, CURRENT>(R, v, P, vc, vr);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) tau[k] = tau_n[k];
+  if constexpr (GEN) fin_wrench<S, NT>(G, n, vr, w, tau);
+  S rhs[6];
+  body_rhs<S, PhysT, CURRENT>(R, v, w, vc, vr, tau, P, rhs);
+  // dnu = M^-1 rhs.
+  S lrhs[6];
+  if constexpr (PhysT::kFull) {
+    S nd[6];
+    apply_minv<S>(P, ldnu, lrhs);
+    apply_minv<S>(P, rhs, nd);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) g.A[j] = g.A[j] - lrhs[j] * nd[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      lrhs[j] = S(P.minv[j]) * ldnu[j];
+      g.A[j] = g.A[j] - rhs[j] * lrhs[j] * S(P.minv[j]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) ltau[k] = ltau[k] + lrhs[k];
+  S lv[3] = {z0, z0, z0}, lw[3] = {z0, z0, z0}, lvr[3] = {z0, z0, z0}, lvc[3] = {z0, z0, z0};
+  S le[3] = {z0, z0, z0};
+  body_rhs_vjp<S, PhysT>(lrhs, v, w, vr, vc, P, lv, lw, lvr, lvc, le, g);
+  if constexpr (GEN) fin_wrench_vjp<S, NT>(G, n, vr, w, lrhs, ln, lvr, lw);
+  // dp = R v
+  S LR[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) LR[i][j] = ldp[i] * v[j];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) lv[j] = lv[j] + R[0][j] * ldp[0] + R[1][j] * ldp[1] + R[2][j] * ldp[2];
+  // dq = 1/2 q (x) (0, w)
+  const S qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+  const S hq = S(0.5f);
+  lq[0] = lq[0] + hq * (w[0] * ldq[1] + w[1] * ldq[2] + w[2] * ldq[3]);
+  lq[1] = lq[1] + hq * (-w[0] * ldq[0] - w[2] * ldq[2] + w[1] * ldq[3]);
+  lq[2] = lq[2] + hq * (-w[1] * ldq[0] + w[2] * ldq[1] - w[0] * ldq[3]);
+  lq[3] = lq[3] + hq * (-w[2] * ldq[0] - w[1] * ldq[1] + w[0] * ldq[2]);
+  lw[0] = lw[0] + hq * (-qx * ldq[0] + qw * ldq[1] + qz * ldq[2] - qy * ldq[3]);
+  lw[1] = lw[1] + hq * (-qy * ldq[0] - qz * ldq[1] + qw * ldq[2] + qx * ldq[3]);
+  lw[2] = lw[2] + hq * (-qz * ldq[0] + qy * ldq[1] - qx * ldq[2] + qw * ldq[3]);
+  // vr = v - vc ; vc = R^T Vc ; e = R^T e_3 ; R = R(q / |q|)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lv[j] = lv[j] + lvr[j];
+    lvc[j] = lvc[j] - lvr[j];
+  }
+  if (CURRENT) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) LR[i][j] = LR[i][j] + S(P.Vc[i]) * lvc[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) LR[2][j] = LR[2][j] + le[j];
+  S lqh[4] = {z0, z0, z0, z0};
+  rot_vjp(qh, LR, lqh);
+  const S dot = qh[0] * lqh[0] + qh[1] * lqh[1] + qh[2] * lqh[2] + qh[3] * lqh[3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lq[i] = lq[i] + iq * (lqh[i] - qh[i] * dot);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lnu[j] = lnu[j] + lv[j];
+    lnu[3 + j] = lnu[3 + j] + lw[j];
+  }
+}
+
+// Adjoint of one RK4 substep (substep_rk4) from its start state x0: the
+// stages are recomputed, then reversed. `lx` holds the adjoint of the end
+// state on entry and of x0 on exit; lc and g accumulate.
+template <typename S, int NT, typename ActT, typename PhysT, bool CURRENT = true, typename GenT = NoGen>
+MG_HD void substep_rk4_vjp(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, const ActT& A, S h, St<S, NT>& lx,
+                           S (&lc)[NT], HydroGrad<S>& g, const GenT& G = GenT()) {
+  constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
+  const S z0 = S(0.0f);
+  // Forward: actuators, then the four stage points and the sum.
+  St<S, NT> xa = x0;
+  S f[NT], tau_n[6];
+  actuate<S, NT>(xa, c, A, f, tau_n);
+  if constexpr (GEN) tilt_wrench<S, NT>(G, xa.n, f, tau_n);
+  const S h2 = S(0.5f) * h, h6 = h / S(6.0f), h3 = h / S(3.0f);
+  S yq[4][4], ynu[4][6], sq[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { yq[0][i] = x0.q[i]; sq[i] = x0.q[i]; }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) ynu[0][i] = x0.nu[i];
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    S dp[3], dq[4], dnu[6];
+    rk4_stage<S, NT, PhysT, CURRENT>(yq[st], ynu[st], xa.n, tau_n, P, G, dp, dq, dnu);
+    const S wsum = (st == 0 || st == 3) ? h6 : h3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sq[i] = sq[i] + wsum * dq[i];
+    if (st < 3) {
+      const S hs = (st == 2) ? h : h2;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) yq[st + 1][i] = x0.q[i] + hs * dq[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) ynu[st + 1][i] = x0.nu[i] + hs * dnu[i];
+    }
+  }
+  const S inv = minvsqrt(sq[0] * sq[0] + sq[1] * sq[1] + sq[2] * sq[2] + sq[3] * sq[3]);
+  // Reverse: q1 = sum_q / |sum_q|.
+  S q1[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q1[i] = sq[i] * inv;
+  const S dot = q1[0] * lx.q[0] + q1[1] * lx.q[1] + q1[2] * lx.q[2] + q1[3] * lx.q[3];
+  S lsq[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lsq[i] = inv * (lx.q[i] - q1[i] * dot);
+  // Adjoints of the stage derivatives k_s and of the stage points g_s:
+  // k4 <- h/6 ly; k3 <- h/3 ly + h g4; k2 <- h/3 ly + h/2 g3; k1 <- h/6 ly + h/2 g2.
+  S ltau[6] = {z0, z0, z0, z0, z0, z0};
+  S lnx[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) lnx[i] = z0;
+  S gq[4] = {z0, z0, z0, z0}, gnu[6] = {z0, z0, z0, z0, z0, z0};     // g of the later stage point
+  S aq[4], anu[6];                                                   // sum of the stage points' g
+#pragma unroll
+  for (int i = 0; i < 4; ++i) aq[i] = z0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) anu[i] = z0;
+#pragma unroll
+  for (int st = 3; st >= 0; --st) {
+    const S wsum = (st == 0 || st == 3) ? h6 : h3;
+    const S hn = (st == 2) ? h : h2;   // the next stage point's step (stage st + 1 = y0 + hn k_st)
+    S ldp[3], ldq[4], ldnu[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ldp[i] = wsum * lx.p[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ldq[i] = wsum * lsq[i] + (st < 3 ? hn * gq[i] : z0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ldnu[i] = wsum * lx.nu[i] + (st < 3 ? hn * gnu[i] : z0);
+    S nq[4] = {z0, z0, z0, z0}, nnu[6] = {z0, z0, z0, z0, z0, z0};
+    rk4_stage_vjp<S, NT, PhysT, CURRENT>(yq[st], ynu[st], xa.n, tau_n, P, G, ldp, ldq, ldnu, nq, nnu, ltau, lnx, g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { gq[i] = nq[i]; aq[i] = aq[i] + nq[i]; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { gnu[i] = nnu[i]; anu[i] = anu[i] + nnu[i]; }
+  }
+  // y0 = (q0, nu0) enters the sum and every stage point; p enters only the sum.
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lx.q[i] = lsq[i] + aq[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) lx.nu[i] = lx.nu[i] + anu[i];
+  // tau_n = B f (+ the tilt wrench) ; f_i = k n1 |n1| ; n1 = n + alpha (c - n)
+  S lfx[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) lfx[i] = z0;
+  if constexpr (GEN) tilt_wrench_vjp<S, NT>(G, xa.n, f, ltau, lfx, lnx);
+#pragma unroll
+  for (int i = 0; i < NT; ++i) {
+    S lf = S(A.alloc[0][i]) * ltau[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) lf = lf + S(A.alloc[k][i]) * ltau[k];
+    lf = lf + lfx[i];
+    const S an = mabs(xa.n[i]);
+    const S df = (an < S(A.dz[i])) ? z0 : S(2.0f) * S(A.kf[i]) * an;
+    const S ln1 = lx.n[i] + lnx[i] + lf * df;
+    lc[i] = lc[i] + S(A.alpha[i]) * ln1;
+    lx.n[i] = (S(1.0f) - S(A.alpha[i])) * ln1;
+  }
 }
 
 // Adjoint of one substep with its forward recomputed in full.

@@ -336,45 +336,54 @@ static cudaError_t launch_adjoint_k(const void* kern, const AdjArgs& a, const Cl
   return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
-// kg: the class's generic actuator table (classes with fins or tilted
-// propellers), else null. jit_kernel: a class-specialised adjoint kernel for
-// nt thrusters compiled at run time (null: the library's).
-cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg, int nt, bool dependent,
+// var: 0 propeller classes with Euler, 1 classes with fins or tilted
+// propellers with Euler, 2 RK4 runs; kg: the class's generic actuator table
+// (var >= 1), else null. jit_kernel: a class-specialised adjoint kernel for
+// nt thrusters compiled at run time (var 0 without a payload; null: the
+// library's).
+template <bool PAY, int VAR>
+static const void* adjoint_fn(int nt) {
+  switch (nt) {
+    case 1: return reinterpret_cast<const void*>(&mg_adjoint_kernel<1, PAY, NoLit, VAR>);
+    case 2: return reinterpret_cast<const void*>(&mg_adjoint_kernel<2, PAY, NoLit, VAR>);
+    case 3: return reinterpret_cast<const void*>(&mg_adjoint_kernel<3, PAY, NoLit, VAR>);
+    case 4: return reinterpret_cast<const void*>(&mg_adjoint_kernel<4, PAY, NoLit, VAR>);
+    case 5: return reinterpret_cast<const void*>(&mg_adjoint_kernel<5, PAY, NoLit, VAR>);
+    case 6: return reinterpret_cast<const void*>(&mg_adjoint_kernel<6, PAY, NoLit, VAR>);
+    case 7: return reinterpret_cast<const void*>(&mg_adjoint_kernel<7, PAY, NoLit, VAR>);
+    case 8: return reinterpret_cast<const void*>(&mg_adjoint_kernel<8, PAY, NoLit, VAR>);
+    default: return nullptr;
+  }
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg, int nt, int var, bool dependent,
                            cudaStream_t st, const void* jit_kernel) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (a.tile_envs <= 0 || a.tile_envs % ADJ_ENVS != 0 || a.seg_hi - a.seg_lo != 1) return cudaErrorInvalidValue;
-  if (a.pay_plane > 0) {
-    // Payload runs: the library's kernel with the parameter column in
-    // dynamic shared memory (above the default 48 KB with the static part:
-    // the attribute is set once per device and kernel).
+  if (var < 0 || var > 2 || (var != 0 && !kg)) return cudaErrorInvalidValue;
+  const bool pay = a.pay_plane > 0;
+  if (pay && var == 1) return cudaErrorInvalidValue;   // payload runs are propeller classes
+  if (jit_kernel && var == 0 && !pay) return launch_adjoint_k(jit_kernel, a, kc, nullptr, dependent, st);
+  const void* k = pay ? (var == 2 ? adjoint_fn<true, 2>(nt) : adjoint_fn<true, 0>(nt))
+                      : (var == 2 ? adjoint_fn<false, 2>(nt) : var == 1 ? adjoint_fn<false, 1>(nt)
+                                                                          : adjoint_fn<false, 0>(nt));
+  if (!k) return cudaErrorInvalidValue;
+  if (pay) {
+    // Payload runs: the parameter column in dynamic shared memory (above the
+    // default 48 KB with the static part: the attribute is set once per
+    // device and kernel).
     static std::atomic<uint32_t> attr_set[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
-    const void* k = nullptr;
-#define MG_L(N) k = reinterpret_cast<const void*>(&mg_adjoint_kernel<N, true>)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-    const uint32_t bit = 1u << nt;
+    const uint32_t bit = 1u << (nt + (var == 2 ? 9 : 0));
     if (dev >= 0 && dev < 64 && !(attr_set[dev].load() & bit)) {
       const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_PAY_SMEM);
       if (e != cudaSuccess) return e;
       attr_set[dev].fetch_or(bit);
     }
-    return launch_adjoint_k(k, a, kc, nullptr, dependent, st, ADJ_PAY_SMEM);
+    return launch_adjoint_k(k, a, kc, var ? kg : nullptr, dependent, st, ADJ_PAY_SMEM);
   }
-  if (kg) {
-#define MG_L(N)                                                                                               \
-  return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N, false, NoLit, true>), a, kc, kg, \
-                          dependent, st)
-    MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  }
-  if (jit_kernel) return launch_adjoint_k(jit_kernel, a, kc, nullptr, dependent, st);
-#define MG_L(N) \
-  return launch_adjoint_k(reinterpret_cast<const void*>(&mg_adjoint_kernel<N>), a, kc, nullptr, dependent, st)
-  MG_NT_SWITCH(nt, MG_L)
-#undef MG_L
-  return cudaErrorInvalidValue;
+  return launch_adjoint_k(k, a, kc, var ? kg : nullptr, dependent, st);
 }
 
 // FP64 launch of one group: var 0 propellers with Euler, 1 generic

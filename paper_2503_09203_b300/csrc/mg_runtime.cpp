@@ -23,7 +23,7 @@ cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, i
 cudaError_t launch_reset(const ResetArgs& a, cudaStream_t st);
 cudaError_t launch_set_hydro(float4* planes, int64_t n_slots, const float* A, const float* dl, const float* dq,
                              cudaStream_t st);
-cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg, int nt, bool dependent,
+cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg, int nt, int var, bool dependent,
                            cudaStream_t st, const void* jit_kernel);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
@@ -470,10 +470,6 @@ int mg_create(const mg_config* cfg, const mg_class_desc* classes, mg_sim** out) 
   for (int c = 0; c < sim->n_classes; ++c) {
     if (validate_class(sim, sim->classes[c], c) != MG_OK) return bail(MG_ERR_INVALID_ARG);
     if (sim->counts[c] < 0) return bail(MG_ERR_INVALID_ARG);
-    if (cfg->record_steps > 0 && cfg->integrator != MG_INTEG_EULER) {
-      sim->err = "gradients need the Euler integrator (record_steps must be 0 in RK4 runs)";
-      return bail(MG_ERR_INVALID_ARG);
-    }
   }
   sim->h = cfg->dt / cfg->K;
   sim->ckpt_every = cfg->ckpt_every > 0 ? cfg->ckpt_every : 20;
@@ -1159,7 +1155,7 @@ static int launch_backward(mg_sim* sim, AdjArgs a, cudaStream_t st) {
         jk = jit_adjoint_kernel(kc, g.nt, &err);
         if (!jk) sim->jit_err = err;
       }
-      CK(launch_adjoint(a, kc, gen ? &sim->h_gen[g.cls] : nullptr, g.nt, !first, st, jk));
+      CK(launch_adjoint(a, kc, gen ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var, !first, st, jk));
       first = false;
     }
   }

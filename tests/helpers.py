@@ -24,12 +24,12 @@ def oracle_env_arrays(p: dict) -> dict:
     return {k: p[k] for k in keys}
 
 
-def adjoint_vs_oracle_tangents(classes, sub_envs, s0, a, dt, K, g, go, gr, nthr, ids, rng, tol=1e-3):
+def adjoint_vs_oracle_tangents(classes, sub_envs, s0, a, dt, K, g, go, gr, nthr, ids, rng, tol=1e-3, integ=0):
     """Per env: <gpu gradient, d> against the oracle's tangent of
     sum_t <g_obs, obs_t> + <g_rew, rew_t> along d, for three directions per
     gradient group (g: the GPU gradients of all envs; sub_envs: the oracle's
     records of the envs `ids`). Per env the relative error over the directions
-    is at most `tol`."""
+    is at most `tol`. integ: the integrator (0 semi-implicit Euler, 1 RK4)."""
     import oracle
     n = len(ids)
     T = a.shape[0]
@@ -44,7 +44,7 @@ def adjoint_vs_oracle_tangents(classes, sub_envs, s0, a, dt, K, g, go, gr, nthr,
         got, want = [], []
         for _ in range(3):
             d = mk()
-            j = oracle.rollout_jvp(classes, sub_envs, s0[ids].astype(np.float64), a[:, ids], dt, K, **d)
+            j = oracle.rollout_jvp(classes, sub_envs, s0[ids].astype(np.float64), a[:, ids], dt, K, integ=integ, **d)
             want.append(np.einsum("te,te->e", gr[:, ids], j["d_reward"]) +
                         np.einsum("tek,tek->e", go[:, ids], j["d_obs"]))
             if name == "act":

@@ -7,7 +7,8 @@
 // Prints the worst relative difference and, with a nonzero argument, the
 // same for a product whose added-mass gradient is scaled by 1.01 (the check
 // must see that). For the vehicle alone, with a point-mass payload, and for a
-// class with fins and a servo-tilted propeller.
+// class with fins and a servo-tilted propeller; the semi-implicit Euler substep
+// (vjp_from_tape) and RK4 (substep_rk4_vjp).
 #include <cstdio>
 #include <algorithm>
 #include <cmath>
@@ -16,18 +17,19 @@
 using namespace mg;
 template <int NT>
 struct In { St<double, NT> x; double c[NT]; double A[6], dl[6], dq[6]; };
-template <int NT>
+template <int NT, bool RK = false>
 void fwd(const In<NT>& in, const Phys<double>& P0, const Act<double>& Ac, double h, St<double, NT>& out) {
   Phys<double> P = P0;
   const double Mrb[6] = {P0.m, P0.m, P0.m, P0.Ig[0], P0.Ig[1], P0.Ig[2]};
   for (int j = 0; j < 6; ++j) { P.A[j] = in.A[j]; P.dl[j] = in.dl[j]; P.dq[j] = in.dq[j]; P.minv[j] = 1.0 / (Mrb[j] + in.A[j]); }
   out = in.x;
   double c[NT]; for (int i = 0; i < NT; ++i) c[i] = in.c[i];
-  substep<double, NT, false>(out, c, P, Ac, h, nullptr);
+  if constexpr (RK) substep_rk4<double, NT>(out, c, P, Ac, h);
+  else substep<double, NT, false>(out, c, P, Ac, h, nullptr);
 }
 static double g_scale = 1.0;
 
-template <int NT>
+template <int NT, bool RK = false>
 double run(std::mt19937_64& rng) {
   std::uniform_real_distribution<double> U(-1, 1), P01(0.2, 2.0);
   Phys<double> P; Act<double> Ac; In<NT> in;
@@ -51,7 +53,8 @@ double run(std::mt19937_64& rng) {
   St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
-  vjp_from_tape<double, NT>(in.x, x.q, tp, in.c, Pb, Ac, h, lx, lc, g);
+  if constexpr (RK) substep_rk4_vjp<double, NT>(in.x, in.c, Pb, Ac, h, lx, lc, g);
+  else vjp_from_tape<double, NT>(in.x, x.q, tp, in.c, Pb, Ac, h, lx, lc, g);
   // random direction
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
@@ -65,7 +68,7 @@ double run(std::mt19937_64& rng) {
     for (int j = 0; j < NT; ++j) o.c[j] += s * d.c[j];
     for (int j = 0; j < 6; ++j) { o.A[j] += s * d.A[j]; o.dl[j] += s * d.dl[j]; o.dq[j] += s * d.dq[j]; }
     return o; };
-  St<double, NT> yp, ym; fwd<NT>(shift(eps), P, Ac, h, yp); fwd<NT>(shift(-eps), P, Ac, h, ym);
+  St<double, NT> yp, ym; fwd<NT, RK>(shift(eps), P, Ac, h, yp); fwd<NT, RK>(shift(-eps), P, Ac, h, ym);
   double fd = 0;
   for (int j = 0; j < 3; ++j) fd += lam.p[j] * (yp.p[j] - ym.p[j]); for (int j = 0; j < 4; ++j) fd += lam.q[j] * (yp.q[j] - ym.q[j]);
   for (int j = 0; j < 6; ++j) fd += lam.nu[j] * (yp.nu[j] - ym.nu[j]); for (int j = 0; j < NT; ++j) fd += lam.n[j] * (yp.n[j] - ym.n[j]);
@@ -128,7 +131,7 @@ static void pay_fill(PhysPay<double>& P, const double A[6]) {
   for (int j = 0; j < 6; ++j) P.A[j] = A[j];
 }
 
-template <int NT>
+template <int NT, bool RK = false>
 double run_pay(std::mt19937_64& rng) {
   std::uniform_real_distribution<double> U(-1, 1), P01(0.2, 2.0);
   PhysPay<double> P; Act<double> Ac; In<NT> in;
@@ -154,7 +157,8 @@ double run_pay(std::mt19937_64& rng) {
     for (int j = 0; j < 6; ++j) { Q.dl[j] = i2.dl[j]; Q.dq[j] = i2.dq[j]; }
     out = i2.x;
     double c[NT]; for (int k = 0; k < NT; ++k) c[k] = i2.c[k];
-    substep<double, NT, false>(out, c, Q, Ac, h, nullptr);
+    if constexpr (RK) substep_rk4<double, NT>(out, c, Q, Ac, h);
+    else substep<double, NT, false>(out, c, Q, Ac, h, nullptr);
   };
   PhysPay<double> Pb = P;
   pay_fill(Pb, in.A);
@@ -167,7 +171,8 @@ double run_pay(std::mt19937_64& rng) {
   Tape<double, NT> tr; double q1[4];
   tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
-  vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g);
+  if constexpr (RK) substep_rk4_vjp<double, NT>(in.x, in.c, Pb, Ac, h, lx, lc, g);
+  else vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g);
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
@@ -203,7 +208,7 @@ struct GenH {
   double v(int i, int j) const { return vals[i][j]; }
 };
 
-template <int NT>
+template <int NT, bool RK = false>
 double run_gen(std::mt19937_64& rng) {
   static_assert(NT == 8, "channel layout of the generic check");
   std::uniform_real_distribution<double> U(-1, 1), P01(0.2, 2.0);
@@ -238,7 +243,8 @@ double run_gen(std::mt19937_64& rng) {
     const Phys<double> Q = phys_of(i2);
     out = i2.x;
     double c[NT]; for (int k = 0; k < NT; ++k) c[k] = i2.c[k];
-    substep<double, NT, false, Act<double>, Phys<double>, true, GenH>(out, c, Q, Ac, h, nullptr, G);
+    if constexpr (RK) substep_rk4<double, NT, Act<double>, Phys<double>, true, GenH>(out, c, Q, Ac, h, G);
+    else substep<double, NT, false, Act<double>, Phys<double>, true, GenH>(out, c, Q, Ac, h, nullptr, G);
   };
   const Phys<double> Pb = phys_of(in);
   St<double, NT> x = in.x; Tape<double, NT> tp;
@@ -248,7 +254,9 @@ double run_gen(std::mt19937_64& rng) {
   Tape<double, NT> tr; double q1[4];
   tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
-  vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g, G);
+  if constexpr (RK)
+    substep_rk4_vjp<double, NT, Act<double>, Phys<double>, true, GenH>(in.x, in.c, Pb, Ac, h, lx, lc, g, G);
+  else vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g, G);
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
@@ -287,6 +295,12 @@ int main(int argc, char** argv) {
     printf("%s %.6e\n", pass ? "scaled" : "worst", w);
     printf("%s %.6e\n", pass ? "scaled_payload" : "worst_payload", wp);
     printf("%s %.6e\n", pass ? "scaled_generic" : "worst_generic", wg);
+    double wr = 0;
+    for (int k = 0; k < 200; ++k) {
+      wr = std::max(wr, run<8, true>(rng)); wr = std::max(wr, run<5, true>(rng));
+      wr = std::max(wr, run_pay<8, true>(rng)); wr = std::max(wr, run_gen<8, true>(rng));
+    }
+    printf("%s %.6e\n", pass ? "scaled_rk4" : "worst_rk4", wr);
   }
   return 0;
 }

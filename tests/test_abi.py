@@ -113,13 +113,11 @@ def test_error_strings(lib):
         assert lib.mg_strerror(code)
 
 
-@pytest.mark.parametrize("bad", ["record_rk4", "integrator", "fin_chord", "tilt_link", "kind", "fin_rho"])
+@pytest.mark.parametrize("bad", ["integrator", "fin_chord", "tilt_link", "kind", "fin_rho"])
 def test_create_rejects_bad_actuators_before_touching_the_device(lib, bad):
     classes = [vehicles.lauv(), vehicles.tilt_hauv()]
     counts, record, integ = [4, 4], 0, B.MG_INTEG_EULER
-    if bad == "record_rk4":
-        classes, counts, record, integ = [vehicles.heavy8()], [4], 10, B.MG_INTEG_RK4
-    elif bad == "integrator":
+    if bad == "integrator":
         integ = 7
     elif bad == "fin_chord":
         classes[0]["act_chord"] = [(0.0, 0.0, 0.0)] + [(0.0, 0.6, 0.8)] * 4   # not normal to the y/z span axes

@@ -395,7 +395,9 @@ def test_brute_force_one_substep():
 # ---------------------------------------------------------------------------
 # Forward-mode gradients against FP64 central differences.
 # ---------------------------------------------------------------------------
-def test_jvp_matches_central_differences():
+@pytest.mark.parametrize("integ", [0, 1])
+def test_jvp_matches_central_differences(integ):
+    """Tangents of the semi-implicit Euler and the RK4 rollouts."""
     classes = vehicles.five_classes()
     counts = [2, 2, 2, 2, 2]
     ec = workloads.env_classes(counts)
@@ -407,7 +409,7 @@ def test_jvp_matches_central_differences():
     da = rng.normal(size=a.shape); dMa = rng.normal(size=(E, 6)); ddl = rng.normal(size=(E, 6))
     ddq = rng.normal(size=(E, 6)); ds0 = rng.normal(size=(E, 21)) * 0.1
     ds0[:, 13:] = 0.0
-    j = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, ds0, dMa, ddl, ddq)
+    j = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, ds0, dMa, ddl, ddq, integ=integ)
     arr = oracle.envs_to_arrays(envs)
 
     def f(eps):
@@ -418,19 +420,19 @@ def test_jvp_matches_central_differences():
         e2 = oracle.make_envs(arr2)
         # Actions enter as float32; perturb through the FP64 path by rescaling
         # the tangent onto the state instead: use only param/state directions.
-        s, o, r = oracle.rollout(classes, e2, (s0 + eps * ds0).copy(), a, dt, K)
+        s, o, r = oracle.rollout(classes, e2, (s0 + eps * ds0).copy(), a, dt, K, integ=integ)
         return s, o, r
 
     hstep = 1e-6
     sp, op, rp = f(hstep)
     sm, om, rm = f(-hstep)
-    j0 = oracle.rollout_jvp(classes, envs, s0, a, dt, K, None, ds0, dMa, ddl, ddq)
+    j0 = oracle.rollout_jvp(classes, envs, s0, a, dt, K, None, ds0, dMa, ddl, ddq, integ=integ)
     fd_r = (rp - rm) / (2 * hstep)
     fd_s = (sp - sm) / (2 * hstep)
     assert np.linalg.norm(j0["d_reward"] - fd_r) <= 1e-6 * np.linalg.norm(fd_r)
     assert np.linalg.norm(j0["d_state"] - fd_s) <= 1e-6 * np.linalg.norm(fd_s)
     # Action tangent: linearity check of the JVP in its direction argument.
-    ja = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, None, None, None, None)
+    ja = oracle.rollout_jvp(classes, envs, s0, a, dt, K, da, None, None, None, None, integ=integ)
     np.testing.assert_allclose(j["d_reward"], j0["d_reward"] + ja["d_reward"], rtol=1e-10, atol=1e-10)
 
 

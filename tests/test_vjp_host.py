@@ -3,7 +3,8 @@ compiled for the host in FP64) against central differences of the forward
 substep: the product is the transpose of the forward map, term by term
 (Eq. 1-3 with the actuators of Sec. III-D), for the vehicle alone (diagonal
 inverse), with a payload (combined body about the origin, full inverse), and
-for a class with fins and a servo-tilted propeller. No GPU: the device functions are
+for a class with fins and a servo-tilted propeller; with the semi-implicit
+Euler substep and with RK4. No GPU: the device functions are
 host/device code; nvcc compiles them for the host."""
 import os
 import shutil
@@ -37,7 +38,9 @@ def test_vjp_matches_central_differences(tmp_path):
     assert vals["worst"] <= 1e-8, vals
     assert vals["worst_payload"] <= 1e-8, vals
     assert vals["worst_generic"] <= 1e-8, vals
+    assert vals["worst_rk4"] <= 1e-8, vals
     # A 1% error in one gradient term is seen.
     assert vals["scaled"] >= 1e-5, vals
     assert vals["scaled_payload"] >= 1e-5, vals
     assert vals["scaled_generic"] >= 1e-5, vals
+    assert vals["scaled_rk4"] >= 1e-5, vals
