@@ -173,7 +173,9 @@ typedef struct {
   int32_t integrator;           /* MG_INTEG_EULER (semi-implicit Euler per
                                    substep) or MG_INTEG_RK4 (classical RK4 on
                                    p, q, nu with the actuator states held over
-                                   the substep; step only, no adjoint) */
+                                   the substep; mg_step_backward reverses its
+                                   four stages from the recorded substep
+                                   start) */
   int32_t pad1;
 } mg_config;
 
