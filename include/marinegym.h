@@ -495,6 +495,8 @@ typedef struct {
   int32_t max_requests;     /* simultaneously admitted requests (<= 4096) */
   int32_t max_queue;        /* pending requests before submit refuses */
   mg_reset_cfg reset;       /* initial state / DR per request (seeded by request) */
+  int32_t integrator;       /* MG_INTEG_EULER or MG_INTEG_RK4, for every request */
+  int32_t pad0;
 } mg_server_config;
 
 typedef struct {
@@ -526,9 +528,10 @@ typedef struct {
   int32_t pad0;
 } mg_server_stats;
 
-/* Errors of mg_server_create: INVALID_ARG (bad config, a class with r_g != 0),
- * OOM. Every actuator type is served (fixed propellers, fins, servo-tilted
- * propellers; semi-implicit Euler). */
+/* Errors of mg_server_create: INVALID_ARG (bad config, an integrator other
+ * than MG_INTEG_EULER / MG_INTEG_RK4, a class with r_g != 0), OOM. Every
+ * actuator type is served (fixed propellers, fins, servo-tilted propellers)
+ * with either integrator. */
 int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, int32_t n_classes,
                      mg_server** out);
 int mg_server_submit(mg_server* srv, const mg_request* req, int64_t* id_out);

@@ -100,7 +100,8 @@ class mg_launch_shape(C.Structure):
 
 class mg_server_config(C.Structure):
     _fields_ = [("dt", C.c_double), ("budget_bytes", C.c_size_t), ("max_requests", C.c_int32),
-                ("max_queue", C.c_int32), ("reset", mg_reset_cfg)]
+                ("max_queue", C.c_int32), ("reset", mg_reset_cfg), ("integrator", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 class mg_request(C.Structure):
@@ -625,11 +626,11 @@ class Sim:
 # ---------------------------------------------------------------------------
 
 def mg_server_create(classes, dt: float, budget_bytes: int = 0, max_requests: int = 1024, max_queue: int = 100000,
-                     reset: Optional[dict] = None):
+                     reset: Optional[dict] = None, integrator: int = MG_INTEG_EULER):
     L = lib()
     arr = (mg_class_desc * len(classes))(*[pack_class(c) for c in classes])
     cfg = mg_server_config(dt=float(dt), budget_bytes=int(budget_bytes), max_requests=int(max_requests),
-                           max_queue=int(max_queue), reset=pack_reset(reset or {}))
+                           max_queue=int(max_queue), reset=pack_reset(reset or {}), integrator=int(integrator))
     h = _VP()
     rc = L.mg_server_create(C.byref(cfg), arr, len(classes), C.byref(h))
     if rc != MG_OK:

@@ -160,7 +160,7 @@ struct Tick {
 struct mg_server {
   mg_server_config cfg{};
   std::vector<mg_class_desc> classes;
-  std::vector<int> class_var;   // step variant per class: 0 propellers, 1 generic actuators
+  std::vector<int> class_var;   // step variant per class: 0 propellers, 1 generic actuators, 2 RK4
   int device = 0;
   int num_sms = 148;
   // device
@@ -326,17 +326,17 @@ static bool enqueue_tick(mg_server* s, Tick& t) {
     }
   }
   // Tick table in one pass: requests grouped by thruster count and step
-  // variant (propellers, generic actuators), and the segment (within its
-  // group) of every tile.
+  // variant (propellers, generic actuators, RK4), and the segment (within
+  // its group) of every tile.
   struct G { int nt, var, lo, hi, tile_lo, tiles; };
   std::vector<G> groups;
-  std::vector<const Req*> by_nt[2][MG_MAX_THR + 1];
+  std::vector<const Req*> by_nt[3][MG_MAX_THR + 1];
   for (const Req* q : t.act) {
     by_nt[s->class_var[q->r.cls]][q->n_thr].push_back(q);
     t.envs += q->r.n_envs;
   }
   int n_seg = 0, tiles = 0;
-  for (int key = 0; key < 2 * MG_MAX_THR; ++key) {
+  for (int key = 0; key < 3 * MG_MAX_THR; ++key) {
     const int var = key / MG_MAX_THR, nt = 1 + key % MG_MAX_THR;
     if (by_nt[var][nt].empty()) continue;
     G g{nt, var, n_seg, 0, tiles, 0};
@@ -541,6 +541,7 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   *out = nullptr;
   if (!(cfg->dt > 0) || cfg->max_requests < 1 || cfg->max_requests > 4096 || cfg->max_queue < 1)
     return MG_ERR_INVALID_ARG;
+  if (cfg->integrator != MG_INTEG_EULER && cfg->integrator != MG_INTEG_RK4) return MG_ERR_INVALID_ARG;
   for (int c = 0; c < n_classes; ++c) {
     const mg_class_desc& d = classes[c];
     if (d.n_thr < 1 || d.n_thr > 8 || !(d.mass > 0) || d.rg[0] != 0 || d.rg[1] != 0 || d.rg[2] != 0)
@@ -549,7 +550,8 @@ int mg_server_create(const mg_server_config* cfg, const mg_class_desc* classes, 
   mg_server* s = new mg_server();
   s->cfg = *cfg;
   s->classes.assign(classes, classes + n_classes);
-  for (int c = 0; c < n_classes; ++c) s->class_var.push_back(class_is_generic(classes[c]) ? 1 : 0);
+  for (int c = 0; c < n_classes; ++c)
+    s->class_var.push_back(cfg->integrator == MG_INTEG_RK4 ? 2 : class_is_generic(classes[c]) ? 1 : 0);
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   size_t budget = cfg->budget_bytes;

@@ -1154,12 +1154,14 @@ template <int PM>
 static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const ClassG* kg, int nt, int var, int grid,
                                   bool dependent, bool shared_sm, cudaStream_t st) {
   if (kc && var != 0 && !kg) return cudaErrorInvalidValue;
-  if (a.act_mode == 1 && var <= 1) {
+  if (a.act_mode == 1) {
     // Serving ticks: per-env parameters (DR or current on), or class
-    // constants; propeller classes (var 0) or generic ones (var 1, the
-    // generic table staged per warp from the class records).
+    // constants; propeller classes (var 0), generic ones (var 1) or RK4
+    // (var 2); variants 1 and 2 stage the actuator table per warp from the
+    // class records.
     if constexpr (PM <= 1) {
       if (kc) return cudaErrorInvalidValue;
+      if (var == 2) return launch_step_pv<PM, 2, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
       if (var == 1) return launch_step_pv<PM, 1, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
       return launch_step_pv<PM, 0, false, true>(a, kc, kg, nt, grid, dependent, shared_sm, st);
     } else {
@@ -1190,6 +1192,11 @@ static cudaError_t launch_step_pm(const StepArgs& a, const ClassK* kc, const Cla
 // kernel otherwise pays the load, and early requests queue behind it.
 template <int PM>
 static cudaError_t prepare_tick_pm(int nt, int var) {
+  if (var == 2) {
+#define MG_L(N) return step_attrs<N, PM, 2, false, true, false>()
+    MG_NT_SWITCH(nt, MG_L)
+#undef MG_L
+  }
   if (var == 1) {
 #define MG_L(N) return step_attrs<N, PM, 1, false, true, false>()
     MG_NT_SWITCH(nt, MG_L)

@@ -139,6 +139,9 @@ def test_server_refuses_bad_classes_before_touching_the_device(lib):
         B.mg_server_create([vehicles.lauv(), dict(vehicles.heavy8(), rg=(0.0, 0.0, 0.01))], dt=0.01,
                            max_requests=4, max_queue=4)
     assert e.value.code == B.MG_ERR_INVALID_ARG
+    with pytest.raises(B.MGError) as e:
+        B.mg_server_create([vehicles.lauv(), vehicles.heavy8()], dt=0.01, max_requests=4, max_queue=4, integrator=3)
+    assert e.value.code == B.MG_ERR_INVALID_ARG
 
 
 

@@ -25,8 +25,8 @@ pytestmark = pytest.mark.gpu
 CFG = dict(vehicles.HOVER_DR)
 
 
-def run_alone(classes, req, budget=256 << 20, cfg=CFG):
-    srv = B.mg_server_create(classes, 0.01, budget_bytes=budget, max_requests=64, reset=cfg)
+def run_alone(classes, req, budget=256 << 20, cfg=CFG, integ=B.MG_INTEG_EULER):
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=budget, max_requests=64, reset=cfg, integrator=integ)
     rid = B.mg_server_submit(srv, *req)
     B.mg_server_wait_idle(srv, 120)
     out = B.mg_server_poll(srv, rid)
@@ -34,7 +34,7 @@ def run_alone(classes, req, budget=256 << 20, cfg=CFG):
     return out
 
 
-def oracle_request(classes, req, cfg=CFG):
+def oracle_request(classes, req, cfg=CFG, integ=0):
     cls, n, horizon, K, seed = req
     envs, s = oracle.reset(classes, np.full(n, cls, np.int32), cfg, seed)
     a = np.zeros((horizon, n, 8), np.float32)
@@ -43,7 +43,7 @@ def oracle_request(classes, req, cfg=CFG):
         for e in range(n):
             for i in range(nt):
                 a[t, e, i] = oracle.action(seed, e, t, i)
-    s, _, r = oracle.rollout(classes, envs, s, a, 0.01, K)
+    s, _, r = oracle.rollout(classes, envs, s, a, 0.01, K, integ=integ)
     return s, r.sum(0)
 
 
@@ -85,18 +85,21 @@ def test_request_alone_equals_in_mix_and_matches_oracle(cfg):
     np.testing.assert_allclose(alone["returns"], ret_ref, rtol=1e-4, atol=1e-3)
 
 
-@pytest.mark.parametrize("cfg", [CFG, dict(vehicles.HOVER)], ids=["per_env_dr", "class_constants"])
-def test_generic_classes_alone_equal_in_mix_and_match_oracle(cfg):
+@pytest.mark.parametrize("cfg,integ", [(CFG, B.MG_INTEG_EULER), (dict(vehicles.HOVER), B.MG_INTEG_EULER),
+                                       (CFG, B.MG_INTEG_RK4), (dict(vehicles.HOVER), B.MG_INTEG_RK4)],
+                         ids=["per_env_dr", "class_constants", "per_env_dr_rk4", "class_constants_rk4"])
+def test_generic_classes_alone_equal_in_mix_and_match_oracle(cfg, integ):
     """The model library's other propulsion types served beside propeller
-    classes: a rudder-propeller (fins) and a tiltrotor (servo-tilted
-    propellers) request, each identical alone and in a mix of all five
-    classes, and equal to the oracle."""
+    classes: a rudder-propeller (fins), a tiltrotor (servo-tilted
+    propellers) and a multirotor request, each identical alone and in a mix
+    of all five classes, and equal to the oracle; with the semi-implicit
+    Euler or the RK4 substep for every request."""
     classes = vehicles.actuated_classes() + [vehicles.five_classes()[1], vehicles.five_classes()[4]]
-    probes = [(1, 29, 30, 4, 424242), (2, 33, 25, 2, 737373)]
-    alone = [run_alone(classes, p, cfg=cfg) for p in probes]
+    probes = [(1, 29, 30, 4, 424242), (2, 33, 25, 2, 737373), (4, 41, 20, 3, 919191)]
+    alone = [run_alone(classes, p, cfg=cfg, integ=integ) for p in probes]
     for a in alone:
         assert a["status"] == B.MG_REQ_DONE
-    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=cfg)
+    srv = B.mg_server_create(classes, 0.01, budget_bytes=256 << 20, max_requests=64, reset=cfg, integrator=integ)
     rng = np.random.default_rng(3)
     others = [(int(rng.integers(0, 5)), int(rng.integers(1, 2000)), int(rng.integers(5, 40)),
                int(rng.integers(1, 9)), int(rng.integers(1 << 40))) for _ in range(40)]
@@ -113,7 +116,7 @@ def test_generic_classes_alone_equal_in_mix_and_match_oracle(cfg):
         assert m["status"] == B.MG_REQ_DONE
         assert np.array_equal(m["final_state"], a["final_state"])
         assert np.array_equal(m["returns"], a["returns"])
-        s_ref, ret_ref = oracle_request(classes, p, cfg=cfg)
+        s_ref, ret_ref = oracle_request(classes, p, cfg=cfg, integ=integ)
         err = rel_state_err(a["final_state"].astype(np.float64), s_ref)
         assert err.max() <= 1e-3, (p, err.max())
         np.testing.assert_allclose(a["returns"], ret_ref, rtol=1e-4, atol=1e-3)
