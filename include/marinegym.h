@@ -466,9 +466,9 @@ int mg_graph_destroy(mg_graph* g);
  * arithmetic with a counting scalar on the host: one substep (with_current:
  * including the ocean-current terms, which class-constant runs compile out),
  * the observation + reward, and one substep's adjoint as the reverse pass
- * runs it (the forward recompute that records the right-hand side, the tape
- * rebuilt from that record, and the vector-Jacobian product). Any output may
- * be NULL. */
+ * runs it (the forward recompute that records the states, the tape rebuilt
+ * from the records of the substep's start and end, and the vector-Jacobian
+ * product). Any output may be NULL. */
 int mg_count_flops(int32_t n_thr, int32_t with_current, double* substep_flops, double* observe_flops,
                    double* adjoint_flops);
 

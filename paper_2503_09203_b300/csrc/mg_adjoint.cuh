@@ -18,18 +18,16 @@ namespace mg {
 // The reverse pass walks the checkpoint segments from the last to the first.
 // Warps 2-3 (the producer) recompute segment s - 1 from its checkpoint while
 // warps 0-1 (the consumer) run the vector-Jacobian products of segment s, so
-// the forward recompute leaves the consumer's dependent chain. Per substep
-// and env the producer stores one record: the start state and the
-// right-hand side M nu_dot of a4-a7 (ADJ_REC floats, seven 16-byte vectors;
-// in the scratch buffer the records of four consecutive slots interleave by
-// vector, so that a warp's stores and copies of one vector touch whole 64-byte
-// runs);
-// the consumer rebuilds the rest of the substep's tape from it (rotor
-// states, R, current, the new velocity and attitude: a few dozen operations
-// instead of the full substep) and applies its VJP. Two scratch buffers
-// alternate between the warps, with one block barrier per segment. Each
-// consumer lane prefetches its next record (and the next step's cotangents
-// and actions) into shared memory by cp.async while it computes the current
+// the forward recompute leaves the consumer's dependent chain. The producer
+// stores the state at every substep boundary (q, nu, n, and p at step
+// boundaries: the records of Rec<NT>); the consumer rebuilds a substep's tape
+// from the records of its start and end (the end gives the new actuator
+// states, the new velocity and so M^-1 rhs, and the end attitude; R, the
+// current, the relative velocity and the quaternion update are a few dozen
+// operations) and applies its VJP. Two buffers per class segment alternate
+// between the warps, with one block barrier per segment. Each consumer lane
+// prefetches its next records (and the next step's cotangents and actions)
+// into shared memory by cp.async while it computes the current
 // substep; record copies go through L2 only (the producer wrote them).
 // ---------------------------------------------------------------------------
 template <int NT>
@@ -61,7 +59,7 @@ static_assert(ADJ_ENVS % 32 == 0, "whole warps per role");
 struct AdjSeg {
   int64_t act_off, slot_off;
   float h, dt;
-  int K, track;
+  int K, track, n4;
 };
 
 // Payload runs: the env's combined-body parameters in a shared-memory
@@ -70,7 +68,6 @@ struct AdjSeg {
 using AdjPhysPay = PhysSmemFull<ADJ_ENVS>;
 constexpr int ADJ_PAY_SMEM = PF_DIM * ADJ_ENVS * 4;
 constexpr int ADJ_STEPF = 14 + 8;            // per-step slot: g_obs 13, g_rew 1, actions 8
-static_assert(ADJ_REC % 4 == 0 && ADJ_REC >= 27, "record of whole 16-byte vectors");
 
 __device__ __forceinline__ void cp4(unsigned dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
@@ -83,63 +80,132 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_grou
 // All but the most recent group complete.
 __device__ __forceinline__ void cp_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Record of one env: state fields (canonical order p3 q4 nu6 n[NT]), rhs at
-// 21. In the scratch buffer, record j of slot s starts at
-// j * n_slots * ADJ_REC + rec_off(s) and its vector k lies 16 k floats further.
-__device__ __forceinline__ int64_t rec_off(int64_t s) { return (s >> 2) * (4 * ADJ_REC) + (s & 3) * 4; }
+// Record of one env at one substep boundary: the state fields q4 nu6 n[NT]
+// and, at step boundaries (substep 0 of a step, and the segment's end), p3
+// after them, in whole 16-byte vectors (Rec<NT>::IN or Rec<NT>::ST). The
+// reverse pass of a substep reads the records of its start and end: the end
+// gives the new actuator states, the new velocity (so M^-1 rhs = (nu1 -
+// nu0) / h) and the end attitude, and p is needed only where the
+// observation is taken.
+//
+// Layout of a class segment's buffer: the records of one checkpoint segment
+// in time order, record j a plane of V(j) vectors over the segment's n4
+// slots, in which four consecutive slots interleave by vector (slot i at
+// (i / 4) 16 V + (i % 4) 4 floats, vector k 16 k floats further), so that a
+// warp's stores and copies of one vector touch whole 64-byte runs.
 template <int NT>
-__device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x, const float* rhs) {
-  float sf[13 + NT], f[ADJ_REC];
-  state_to_fields<NT>(x, sf);
+struct Rec {
+  static constexpr int IN = (10 + NT + 3) / 4;   // vectors of a record inside a step
+  static constexpr int ST = (13 + NT + 3) / 4;   // vectors of a record at a step boundary
+  // Floats per env of a shared-memory record slot: an odd number of
+  // vectors, so that the lanes' 16-byte accesses fall in distinct banks.
+  static constexpr int SLOT = 4 * (ST | 1);
+  static_assert(4 * ST <= ADJ_REC, "records fit the scratch share");
+};
+
+// Float offset of slot i inside a record plane of V vectors.
+__device__ __forceinline__ int64_t rec_in_plane(int64_t i, int V) { return (i >> 2) * (16 * V) + (i & 3) * 4; }
+
+template <int NT, bool STEP>
+__device__ __forceinline__ void store_record(float* rec, const St<float, NT>& x) {
+  constexpr int V = STEP ? Rec<NT>::ST : Rec<NT>::IN;
+  float f[4 * V];
 #pragma unroll
-  for (int j = 0; j < 21; ++j) f[j] = j < 13 + NT ? sf[j % (13 + NT)] : 0.0f;
+  for (int j = 0; j < 4; ++j) f[j] = x.q[j];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) f[21 + j] = rhs ? rhs[j] : 0.0f;
+  for (int j = 0; j < 6; ++j) f[4 + j] = x.nu[j];
 #pragma unroll
-  for (int j = 27; j < ADJ_REC; ++j) f[j] = 0.0f;
+  for (int j = 0; j < NT; ++j) f[10 + j] = x.n[j];
+#pragma unroll
+  for (int j = 10 + NT; j < 4 * V; ++j) f[j] = (STEP && j < 13 + NT) ? x.p[(j - 10 - NT) % 3] : 0.0f;
   float4* r4 = reinterpret_cast<float4*>(rec);
 #pragma unroll
-  for (int k = 0; k < ADJ_REC / 4; ++k) r4[4 * k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+  for (int k = 0; k < V; ++k) r4[4 * k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
-// Consumer-side prefetch slots of one lane: a ring of ADJ_RING records
-// [ADJ_RING][ADJ_ENVS][ADJ_REC] (record j in slot j % ADJ_RING: while the reverse
-// pass works on record j, records j - 1 and j - 2 stream in) and a ring of
-// per-step data [ADJ_RING][ADJ_STEPF][ADJ_ENVS] (step t in slot t % ADJ_RING,
-// issued two steps ahead). Every issue is its own cp.async group.
+// Records of one segment buffer as the consumer lane sees them: record
+// (tl, k) (step tl of the segment, substep k) starts at its plane, then the
+// lane's slot inside it.
+template <int NT>
+struct RecSrc {
+  const float* buf;
+  int64_t step4, off_st, off_in;   // floats per vector plane; slot offsets in step / inner planes
+  int K;
+  __device__ __forceinline__ const float* at(int tl, int k) const {
+    const int64_t plane = (int64_t)tl * (Rec<NT>::ST + (K - 1) * Rec<NT>::IN) +
+                          (k ? Rec<NT>::ST + (k - 1) * Rec<NT>::IN : 0);
+    return buf + plane * step4 + (k ? off_in : off_st);
+  }
+};
+
+// Consumer-side prefetch slots of one lane: a ring of four records
+// [4][ADJ_ENVS][Rec<NT>::SLOT] (record j in slot j % 4: while the reverse pass
+// works on the substep between records j and j + 1, records j - 1 and j - 2
+// stream in) and a ring of per-step data [ADJ_RING][ADJ_STEPF][ADJ_ENVS]
+// (step t in slot t % ADJ_RING, issued two steps ahead). Every issue is its
+// own cp.async group.
 constexpr int ADJ_RING = 3;
+constexpr int ADJ_RREC = 4;
+template <int NT>
 struct AdjPrefetch {
   float* rec;
   float* stp;
   int lane;
-  __device__ __forceinline__ float* rslot(int b) const { return rec + (b * ADJ_ENVS + lane) * ADJ_REC; }
+  __device__ __forceinline__ float* rslot(int j) const {
+    return rec + ((j & (ADJ_RREC - 1)) * ADJ_ENVS + lane) * Rec<NT>::SLOT;
+  }
   __device__ __forceinline__ float* sslot(int b) const { return stp + b * ADJ_STEPF * ADJ_ENVS + lane; }
-  __device__ __forceinline__ void issue_rec(const float* src, int b) const {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(rslot(b));
+  template <bool STEP>
+  __device__ __forceinline__ void issue_rec(const float* src, int j) const {
+    constexpr int V = STEP ? Rec<NT>::ST : Rec<NT>::IN;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(rslot(j));
 #pragma unroll
-    for (int k = 0; k < ADJ_REC / 4; ++k) cp16_l2(dst + 16u * k, src + 16 * k);
+    for (int k = 0; k < V; ++k) cp16_l2(dst + 16u * k, src + 16 * k);
     cp_commit();
   }
-  template <int NT>
-  __device__ __forceinline__ void read(int b, St<float, NT>& x, float rhs[6]) const {
-    float f[ADJ_REC];
-    const float4* p = reinterpret_cast<const float4*>(rslot(b));
+  // Record (tl, k), record j of the segment, into its slot.
+  __device__ __forceinline__ void issue(const RecSrc<NT>& r, int tl, int k, int j) const {
+    if (k == 0) issue_rec<true>(r.at(tl, 0), j);
+    else issue_rec<false>(r.at(tl, k), j);
+  }
+  // Record j - 2, given record j = (tl, k).
+  __device__ __forceinline__ void issue_back2(const RecSrc<NT>& r, int tl, int k, int j) const {
+    if (j < 2) return;
+    k -= 2;
+    while (k < 0) { k += r.K; --tl; }
+    issue(r, tl, k, j - 2);
+  }
+  // q, nu and n of record j (and p if P3, a step-boundary record).
+  template <bool P3>
+  __device__ __forceinline__ void read(int j, St<float, NT>& x) const {
+    constexpr int V = P3 ? Rec<NT>::ST : Rec<NT>::IN;
+    float f[4 * V];
+    const float4* p = reinterpret_cast<const float4*>(rslot(j));
 #pragma unroll
-    for (int k = 0; k < ADJ_REC / 4; ++k) {
+    for (int k = 0; k < V; ++k) {
       const float4 v = p[k];
       f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
     }
-    float sf[13 + NT];
 #pragma unroll
-    for (int j = 0; j < 13 + NT; ++j) sf[j] = f[j];
-    fields_to_state<NT>(sf, x);
-    if (rhs) {
+    for (int i = 0; i < 4; ++i) x.q[i] = f[i];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) rhs[j] = f[21 + j];
+    for (int i = 0; i < 6; ++i) x.nu[i] = f[4 + i];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) x.n[i] = f[10 + i];
+    if constexpr (P3) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x.p[i] = f[10 + NT + i];
     }
   }
+  // q and nu of record j (the start of a substep).
+  __device__ __forceinline__ void read_qnu(int j, St<float, NT>& x) const {
+    const float4* p = reinterpret_cast<const float4*>(rslot(j));
+    const float4 v0 = p[0], v1 = p[1], v2 = p[2];
+    x.q[0] = v0.x; x.q[1] = v0.y; x.q[2] = v0.z; x.q[3] = v0.w;
+    x.nu[0] = v1.x; x.nu[1] = v1.y; x.nu[2] = v1.z; x.nu[3] = v1.w;
+    x.nu[4] = v2.x; x.nu[5] = v2.y;
+  }
   // Step t's cotangents and actions into per-step slot b.
-  template <int NT>
   __device__ __forceinline__ void issue_step(const AdjArgs& a, const AdjSeg& sd, int64_t i, int t, int b) const {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(sslot(b));
     const int64_t slot = sd.slot_off + i;
@@ -156,8 +222,16 @@ struct AdjPrefetch {
   }
 };
 
+// Record planes of a segment buffer: record j = tl K + k (step tl of the
+// segment, substep k) starts rec_plane(tl, k) vectors per slot into the
+// buffer; a step spans ST + (K - 1) IN.
+template <int NT>
+__device__ __forceinline__ int64_t rec_plane(int tl, int k, int K) {
+  return (int64_t)tl * (Rec<NT>::ST + (K - 1) * Rec<NT>::IN) + (k ? Rec<NT>::ST + (k - 1) * Rec<NT>::IN : 0);
+}
+
 // Producer: recompute segment s from its checkpoint into the records of
-// buffer `buf`.
+// buffer `buf` (the states at every substep boundary).
 template <int NT, bool PAY, int VAR, typename ActT, typename GenT>
 __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
                                             const Phys<float>& P, unsigned p_base, int64_t i, int s, float* buf) {
@@ -165,17 +239,24 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
   const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
   St<float, NT> x;
   ld21<NT>(a.ckpt + (int64_t)s * 21 * ns + slot, ns, x);
-  float* rec = buf + rec_off(slot);
-  const int64_t rstride = ns * ADJ_REC;
+  const int64_t step4 = 4 * sd.n4;   // floats per vector plane
+  float* rs = buf + rec_in_plane(i, Rec<NT>::ST);
+  float* ri = buf + rec_in_plane(i, Rec<NT>::IN);
+  int64_t plane = 0;                  // floats to the current record's plane
   for (int t = t0; t < t1; ++t) {
     float raw[NT], c[NT];
     load_actions<NT>(a.actions + (int64_t)t * a.act_stride + sd.act_off + i * NT, raw);
 #pragma unroll
     for (int q = 0; q < NT; ++q) c[q] = clamp1(raw[q]);
     for (int k = 0; k < sd.K; ++k) {
-      St<float, NT> x0 = x;
+      if (k == 0) {
+        store_record<NT, true>(rs + plane, x);
+        plane += Rec<NT>::ST * step4;
+      } else {
+        store_record<NT, false>(ri + plane, x);
+        plane += Rec<NT>::IN * step4;
+      }
       if constexpr (VAR == 2) {
-        // RK4: the record is the start state (the reverse pass recomputes the stages).
         if constexpr (PAY) {
           unsigned pb = p_base;
           asm volatile("" : "+r"(pb));
@@ -183,22 +264,16 @@ __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, 
         } else {
           substep_rk4<float, NT, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, G);
         }
-        store_record<NT>(rec, x0, nullptr);
+      } else if constexpr (PAY) {
+        unsigned pb = p_base;
+        asm volatile("" : "+r"(pb));
+        substep<float, NT, false>(x, c, AdjPhysPay(pb), A, sd.h, nullptr);
       } else {
-        Tape<float, NT> tp;
-        if constexpr (PAY) {
-          unsigned pb = p_base;
-          asm volatile("" : "+r"(pb));
-          substep<float, NT, true>(x, c, AdjPhysPay(pb), A, sd.h, &tp);
-        } else {
-          substep<float, NT, true, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, &tp, G);
-        }
-        store_record<NT>(rec, x0, tp.rhs);
+        substep<float, NT, false, ActT, Phys<float>, true, GenT>(x, c, P, A, sd.h, nullptr, G);
       }
-      rec += rstride;
     }
   }
-  store_record<NT>(rec, x, nullptr);
+  store_record<NT, true>(rs + plane, x);
 }
 
 template <int NT, bool PAY, int VAR, typename ActT, typename GenT>
@@ -231,8 +306,12 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
   }
   const int K = sd.K;
   const int n_seg = (a.T + a.ckpt_every - 1) / a.ckpt_every;
-  const int64_t buf_floats = (int64_t)(a.ckpt_every * K + 1) * ns * ADJ_REC;
-  const int64_t rstride = ns * ADJ_REC;
+  // The segment's two buffers, in its share of the scratch.
+  const int64_t buf_floats = rec_plane<NT>(a.ckpt_every, 0, K) * 4 * sd.n4 + Rec<NT>::ST * 4 * sd.n4;
+  float* const seg_scratch = a.scratch + (int64_t)2 * (a.ckpt_every * K + 1) * ADJ_REC * sd.slot_off;
+  const int64_t step4 = 4 * sd.n4;
+  const int64_t off_st = rec_in_plane(i, Rec<NT>::ST), off_in = rec_in_plane(i, Rec<NT>::IN);
+  const float inv_h = 1.0f / sd.h;
 
   // Consumer state.
   St<float, NT> lam;
@@ -240,7 +319,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
   float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 tr[3] = {tg, tg, tg};
   float k_start = 0.0f;
-  AdjPrefetch pf{s_rec, s_step, lane};
+  AdjPrefetch<NT> pf{s_rec, s_step, lane};
   if (role == 0 && valid) {
     tg = __ldg(&a.planes[TGT_PLANE * ns + slot]);
     if (sd.track) {
@@ -259,23 +338,26 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
     for (int j = 0; j < 6; ++j) { g.A[j] = 0.0f; g.dl[j] = 0.0f; g.dq[j] = 0.0f; }
     // The first two steps back (the last steps of the rollout): their
     // cotangents and actions.
-    pf.issue_step<NT>(a, sd, i, a.T - 1, (a.T - 1) % ADJ_RING);
-    if (a.T >= 2) pf.issue_step<NT>(a, sd, i, a.T - 2, (a.T - 2) % ADJ_RING);
+    pf.issue_step(a, sd, i, a.T - 1, (a.T - 1) % ADJ_RING);
+    if (a.T >= 2) pf.issue_step(a, sd, i, a.T - 2, (a.T - 2) % ADJ_RING);
   }
   float tgt[3] = {tg.x, tg.y, tg.z};
 
   for (int it = 0; it <= n_seg; ++it) {
     if (role == 1 && it < n_seg && valid)
-      adj_produce<NT, PAY, VAR>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, a.scratch + (int64_t)(it & 1) * buf_floats);
+      adj_produce<NT, PAY, VAR>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, seg_scratch + (int64_t)(it & 1) * buf_floats);
     if (role == 0 && it >= 1 && valid) {
       const int s = n_seg - it;
       const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
-      const float* rec0 = a.scratch + (int64_t)((it - 1) & 1) * buf_floats + rec_off(slot);
-      int j = (t1 - t0) * K;   // record of the segment's end state (j >= 1)
-      pf.issue_rec(rec0 + (int64_t)j * rstride, j % ADJ_RING);
-      pf.issue_rec(rec0 + (int64_t)(j - 1) * rstride, (j - 1) % ADJ_RING);
+      const RecSrc<NT> rsrc{seg_scratch + (int64_t)((it - 1) & 1) * buf_floats, step4, off_st, off_in, K};
+      const int n = t1 - t0;
+      int j = n * K;   // record of the segment's end state (j >= 1)
+      pf.issue(rsrc, n, 0, j);
+      if (K == 1) pf.issue(rsrc, n - 1, 0, j - 1);
+      else pf.issue(rsrc, n - 1, K - 1, j - 1);
       cp_wait_but1();   // record j (record j - 1 was committed after it)
       for (int t = t1 - 1; t >= t0; --t) {
+        const int tl = t - t0;
         // Step t's cotangents and actions, issued two steps ahead: complete
         // after the last wait (at least one record group followed them).
         float go[13], raw[NT], c[NT], lc[NT];
@@ -289,34 +371,40 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
           c[q] = clamp1(raw[q]);
           lc[q] = 0.0f;
         }
-        if (t >= 2) pf.issue_step<NT>(a, sd, i, t - 2, (t - 2) % ADJ_RING);
-        // State at the end of step t: record j (the segment's end on the
-        // first step back, else the first substep record of step t + 1).
-        St<float, NT> xe;
-        pf.read<NT>(j % ADJ_RING, xe, nullptr);
-        // After reading record j, record j - 2 is issued (records j and
-        // j - 1 were issued before): every record once, two ahead.
-        if (t == t1 - 1 && j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
-        if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
-        observe_vjp<float, NT>(xe, c, tgt, a.g_obs ? go : nullptr, gr, lam, lc);
+        if (t >= 2) pf.issue_step(a, sd, i, t - 2, (t - 2) % ADJ_RING);
+        // State at the end of step t: record j (a step-boundary record).
+        {
+          St<float, NT> xe;
+          pf.template read<true>(j, xe);
+          // After reading record j, record j - 2 is issued (records j and
+          // j - 1 were issued before): every record once, two ahead.
+          if (t == t1 - 1) pf.issue_back2(rsrc, tl + 1, 0, j);
+          if (sd.track) track_ref<float>(tg, tr[0], tr[1], tr[2], sd.dt, k_start + (float)(t + 1), tgt);
+          observe_vjp<float, NT>(xe, c, tgt, a.g_obs ? go : nullptr, gr, lam, lc);
+        }
         for (int k = K - 1; k >= 0; --k) {
           --j;
           // Record j: record j - 1 was committed after it, except for j = 0.
           if (j >= 1) cp_wait_but1();
           else cp_wait_all();
-          St<float, NT> xs;
-          float rhs[6], q1[4];
-          pf.read<NT>(j % ADJ_RING, xs, rhs);
+          // The substep from record j to record j + 1 (still in its slot).
+          St<float, NT> x0, x1;
+          pf.read_qnu(j, x0);
+          pf.template read<false>(j + 1, x1);
           // Records j - 1 and j - 2 stream in while this substep's product runs.
-          if (j >= 2) pf.issue_rec(rec0 + (int64_t)(j - 2) * rstride, (j - 2) % ADJ_RING);
+          pf.issue_back2(rsrc, tl, k, j);
           if constexpr (VAR == 2) {
-            // RK4: the stages are recomputed from the substep's start state.
+            // RK4: the stages are recomputed from the substep's start state,
+            // with the new actuator states of its end.
+#pragma unroll
+            for (int q = 0; q < NT; ++q) x0.n[q] = x1.n[q];
             if constexpr (PAY) {
               unsigned pb = p_base;
               asm volatile("" : "+r"(pb));
-              substep_rk4_vjp<float, NT, ActT, AdjPhysPay, true, GenT>(xs, c, AdjPhysPay(pb), A, sd.h, lam, lc, g, G);
+              substep_rk4_vjp<float, NT, ActT, AdjPhysPay, true, GenT, true>(x0, c, AdjPhysPay(pb), A, sd.h, lam,
+                                                                           lc, g, G);
             } else {
-              substep_rk4_vjp<float, NT, ActT, Phys<float>, true, GenT>(xs, c, P, A, sd.h, lam, lc, g, G);
+              substep_rk4_vjp<float, NT, ActT, Phys<float>, true, GenT, true>(x0, c, P, A, sd.h, lam, lc, g, G);
             }
           } else {
             Tape<float, NT> tp;
@@ -324,11 +412,11 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
               unsigned pb = p_base;
               asm volatile("" : "+r"(pb));
               const AdjPhysPay Pv(pb);
-              tape_from_rhs<float, NT>(xs, c, Pv, A, sd.h, rhs, tp, q1);
-              vjp_from_tape<float, NT>(xs, q1, tp, c, Pv, A, sd.h, lam, lc, g);
+              tape_from_states<float, NT>(x0, x1, Pv, sd.h, inv_h, tp);
+              vjp_from_tape<float, NT>(x0, x1.q, tp, c, Pv, A, sd.h, lam, lc, g);
             } else {
-              tape_from_rhs<float, NT>(xs, c, P, A, sd.h, rhs, tp, q1);
-              vjp_from_tape<float, NT>(xs, q1, tp, c, P, A, sd.h, lam, lc, g, G);
+              tape_from_states<float, NT>(x0, x1, P, sd.h, inv_h, tp);
+              vjp_from_tape<float, NT>(x0, x1.q, tp, c, P, A, sd.h, lam, lc, g, G);
             }
           }
         }
@@ -390,7 +478,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
   if constexpr (GEN) kt = &kp.k;
   else kt = &kp;
   if constexpr (HAS_LIT) kt = &klit;
-  __shared__ __align__(16) float s_rec[ADJ_RING * ADJ_ENVS * ADJ_REC];
+  __shared__ __align__(16) float s_rec[ADJ_RREC * ADJ_ENVS * Rec<NT>::SLOT];
   __shared__ __align__(16) float s_step[ADJ_RING * ADJ_STEPF * ADJ_ENVS];
   extern __shared__ __align__(16) float s_dyn[];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -409,7 +497,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
       if (a.g_state0) for (int j = 0; j < 21; ++j) a.g_state0[slot * 21 + j] = 0.0f;
     }
     // Every thread of the block takes part in the per-segment barriers.
-    const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track};
+    const AdjSeg sr{sd.act_off, sd.slot_off, sd.h, sd.dt, sd.K, sd.track, sd.n4};
     if constexpr (GEN) adjoint_env<NT, PAY, VAR>(a, sr, *kt, GenK{kp.g}, i, valid, s_rec, s_step, s_dyn);
     else adjoint_env<NT, PAY, VAR>(a, sr, *kt, NoGen{}, i, valid, s_rec, s_step, s_dyn);
   }

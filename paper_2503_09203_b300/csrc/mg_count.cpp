@@ -70,19 +70,17 @@ static void count(bool with_current, double* sub, double* obs, double* adj) {
   mg::observe<Cnt, NT>(x, c, tgt, o, r);
   *obs = (double)mgcount::g_ops;
   // Adjoint of one substep as the reverse pass runs it: the forward
-  // recompute (which records the right-hand side), the tape rebuilt from that
-  // record, and the vector-Jacobian product.
+  // recompute (which records the states), the tape rebuilt from the records of
+  // the substep's start and end, and the vector-Jacobian product.
   mg::St<Cnt, NT> lam = x;
   Cnt lc[NT];
   mg::HydroGrad<Cnt> g;
   mgcount::g_ops = 0;
   mg::St<Cnt, NT> xf = x;
-  mg::Tape<Cnt, NT> tf;
-  mg::substep<Cnt, NT, true>(xf, c, P, A, Cnt(0.01), &tf);
+  mg::substep<Cnt, NT, false>(xf, c, P, A, Cnt(0.01), nullptr);
   mg::Tape<Cnt, NT> tp;
-  Cnt q1[4];
-  mg::tape_from_rhs<Cnt, NT>(x, c, P, A, Cnt(0.01), tf.rhs, tp, q1);
-  mg::vjp_from_tape<Cnt, NT>(x, q1, tp, c, P, A, Cnt(0.01), lam, lc, g);
+  mg::tape_from_states<Cnt, NT>(x, xf, P, Cnt(0.01), Cnt(100.0), tp);
+  mg::vjp_from_tape<Cnt, NT>(x, xf.q, tp, c, P, A, Cnt(0.01), lam, lc, g);
   *adj = (double)mgcount::g_ops;
 }
 

@@ -145,9 +145,10 @@ MG_HD void act_rotor_nodz(const ActT& A, S (&kf)[NT], S (&al)[NT]) {
 
 
 // Intermediates of one substep kept for the vector-Jacobian product.
+// nd: the velocity rate M^-1 rhs of a4-a7.
 template <typename S, int NT>
 struct Tape {
-  S n1[NT], R[3][3], vc[3], vr[3], w[3], rhs[6], nu1[6], qn[4], inv;
+  S n1[NT], R[3][3], vc[3], vr[3], w[3], nd[6], nu1[6], qn[4], inv;
 };
 
 // Actuator kinds (Sec. III-D): propeller with a fixed direction (its column
@@ -189,7 +190,9 @@ struct ActPremul {
   static constexpr bool value = false;
 };
 
-template <typename S, int NT, typename ActT>
+// LAG = false: x.n already holds the new actuator states (the adjoint takes
+// them from the recorded end state of the substep).
+template <typename S, int NT, typename ActT, bool LAG = true>
 MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S tau[6]) {
   constexpr bool PRE = ActPremul<ActT>::value;
   if (dz_active(A)) {
@@ -197,7 +200,7 @@ MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S 
     act_rotor<S, NT>(A, kf, dz, al);
 #pragma unroll
     for (int i = 0; i < NT; ++i) {
-      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+      if (LAG) x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
       const S an = mabs(x.n[i]);
       f[i] = (an < dz[i]) ? S(0.0f) : (PRE ? x.n[i] * an : kf[i] * x.n[i] * an);
     }
@@ -207,7 +210,7 @@ MG_HD void actuate(St<S, NT>& x, const S (&c)[NT], const ActT& A, S (&f)[NT], S 
     act_rotor_nodz<S, NT>(A, kf, al);
 #pragma unroll
     for (int i = 0; i < NT; ++i) {
-      x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
+      if (LAG) x.n[i] = x.n[i] + al[i] * (c[i] - x.n[i]);
       f[i] = PRE ? x.n[i] * mabs(x.n[i]) : kf[i] * x.n[i] * mabs(x.n[i]);
     }
   }
@@ -509,7 +512,15 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
     apply_minv<S>(P, rhs, nd);
 #pragma unroll
     for (int j = 0; j < 6; ++j) x.nu[j] = x.nu[j] + h * nd[j];
+    if (TAPE) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) tp->nd[j] = nd[j];
+    }
   } else {
+    if (TAPE) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) tp->nd[j] = S(P.minv[j]) * rhs[j];
+    }
     // Diagonal M^-1: nu += (h M^-1_jj) rhs_j; h M^-1 is the same for every
     // substep of the step loop, so the compiler can keep it in registers.
 #pragma unroll
@@ -537,7 +548,7 @@ MG_HD void substep(St<S, NT>& x, const S (&c)[NT], const PhysT& P, const ActT& A
       for (int j = 0; j < 3; ++j) tp->R[i][j] = R[i][j];
     }
 #pragma unroll
-    for (int j = 0; j < 6; ++j) { tp->rhs[j] = rhs[j]; tp->nu1[j] = x.nu[j]; }
+    for (int j = 0; j < 6; ++j) tp->nu1[j] = x.nu[j];
 #pragma unroll
     for (int i = 0; i < 4; ++i) tp->qn[i] = qn[i];
     tp->inv = inv;
@@ -816,37 +827,26 @@ MG_HD void body_rhs_vjp(const S lrhs[6], const S v[3], const S w[3], const S vr[
   }
 }
 
-// Tape of one substep rebuilt from its start state x0 and its right-hand side
-// rhs (M nu_dot of a4-a7, which the forward recompute stores with the state):
-// the rest of the tape (rotor states, R, current, relative velocity, the new
-// velocity and the quaternion update) is cheap to recompute, in the same
-// operations as the substep. q1 receives the end attitude.
-template <typename S, int NT, typename ActT, typename PhysT>
-MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, const ActT& A, S h,
-                         const S rhs[6], Tape<S, NT>& tp, S q1[4]) {
-  S kf[NT], dz[NT], al[NT];
-  act_rotor<S, NT>(A, kf, dz, al);
+// Tape of one substep rebuilt from its start state x0 and its end state x1
+// (consecutive records of the forward recompute): the new actuator states n1
+// and velocity nu1 are those of x1, the velocity rate M^-1 rhs of a4-a7 is
+// (nu1 - nu0) / h, and R, the current, the relative velocity and the
+// quaternion update are recomputed from the start attitude in the same
+// operations as the substep. The end attitude q1 is x1.q.
+template <typename S, int NT, typename PhysT>
+MG_HD void tape_from_states(const St<S, NT>& x0, const St<S, NT>& x1, const PhysT& P, S h, S inv_h,
+                            Tape<S, NT>& tp) {
 #pragma unroll
-  for (int i = 0; i < NT; ++i) tp.n1[i] = x0.n[i] + al[i] * (c[i] - x0.n[i]);
+  for (int i = 0; i < NT; ++i) tp.n1[i] = x1.n[i];
   rot(x0.q, tp.R);
   const S v[3] = {x0.nu[0], x0.nu[1], x0.nu[2]};
 #pragma unroll
   for (int i = 0; i < 3; ++i) tp.w[i] = x0.nu[3 + i];
   rel_velocity<S, PhysT, true>(tp.R, v, P, tp.vc, tp.vr);
-  if constexpr (PhysT::kFull) {
-    S nd[6];
-    apply_minv<S>(P, rhs, nd);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      tp.rhs[j] = rhs[j];
-      tp.nu1[j] = x0.nu[j] + h * nd[j];
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      tp.rhs[j] = rhs[j];
-      tp.nu1[j] = x0.nu[j] + (h * S(P.minv[j])) * rhs[j];
-    }
+  for (int j = 0; j < 6; ++j) {
+    tp.nu1[j] = x1.nu[j];
+    tp.nd[j] = (x1.nu[j] - x0.nu[j]) * inv_h;
   }
   const S hh = S(0.5f) * h;
   const S wn[3] = {tp.nu1[3], tp.nu1[4], tp.nu1[5]};
@@ -855,8 +855,6 @@ MG_HD void tape_from_rhs(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, 
 #pragma unroll
   for (int i = 0; i < 4; ++i) tp.qn[i] = x0.q[i] + hh * qd[i];
   tp.inv = minvsqrt(tp.qn[0] * tp.qn[0] + tp.qn[1] * tp.qn[1] + tp.qn[2] * tp.qn[2] + tp.qn[3] * tp.qn[3]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) q1[i] = tp.qn[i] * tp.inv;
 }
 
 // Adjoint of one substep from its tape. x0 is the substep's start state and
@@ -918,22 +916,21 @@ MG_HD void vjp_from_tape(const St<S, NT>& x0, const S q1[4], const Tape<S, NT>& 
   if constexpr (PhysT::kFull) {
     // nu1 = nu + h Mi rhs with Mi = (M_RB + diag(A))^-1 symmetric:
     // lrhs = h Mi lnu1, and d(Mi rhs)/dA_j = -Mi e_j (Mi rhs)_j, so
-    // g.A_j -= lrhs_j (Mi rhs)_j.
-    S t[6], nd[6];
+    // g.A_j -= lrhs_j (Mi rhs)_j = lrhs_j nd_j.
+    S t[6];
     apply_minv<S>(P, lnu1, t);
-    apply_minv<S>(P, tp.rhs, nd);
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       lrhs[j] = h * t[j];
-      g.A[j] = g.A[j] - lrhs[j] * nd[j];
+      g.A[j] = g.A[j] - lrhs[j] * tp.nd[j];
     }
   } else {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       lrhs[j] = h * P.minv[j] * lnu1[j];
       // minv_j = 1/(M_RB,jj + A_j): d minv / dA = -minv^2, and
-      // h minv^2 lnu1 rhs = minv lrhs rhs.
-      g.A[j] = g.A[j] - tp.rhs[j] * lrhs[j] * P.minv[j];
+      // h minv^2 lnu1 rhs = lrhs (minv rhs) = lrhs nd.
+      g.A[j] = g.A[j] - lrhs[j] * tp.nd[j];
     }
   }
   S lnu[6];
@@ -1091,8 +1088,11 @@ MG_HD void rk4_stage_vjp(const S q[4], const S nu[6], const S (&n)[NT], const S 
 
 // Adjoint of one RK4 substep (substep_rk4) from its start state x0: the
 // stages are recomputed, then reversed. `lx` holds the adjoint of the end
-// state on entry and of x0 on exit; lc and g accumulate.
-template <typename S, int NT, typename ActT, typename PhysT, bool CURRENT = true, typename GenT = NoGen>
+// state on entry and of x0 on exit; lc and g accumulate. N1: x0.n holds the
+// substep's new actuator states (those of its recorded end state) instead of
+// the start ones.
+template <typename S, int NT, typename ActT, typename PhysT, bool CURRENT = true, typename GenT = NoGen,
+          bool N1 = false>
 MG_HD void substep_rk4_vjp(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P, const ActT& A, S h, St<S, NT>& lx,
                            S (&lc)[NT], HydroGrad<S>& g, const GenT& G = GenT()) {
   constexpr bool GEN = !tt::is_same<GenT, NoGen>::value;
@@ -1100,7 +1100,7 @@ MG_HD void substep_rk4_vjp(const St<S, NT>& x0, const S (&c)[NT], const PhysT& P
   // Forward: actuators, then the four stage points and the sum.
   St<S, NT> xa = x0;
   S f[NT], tau_n[6];
-  actuate<S, NT>(xa, c, A, f, tau_n);
+  actuate<S, NT, ActT, !N1>(xa, c, A, f, tau_n);
   if constexpr (GEN) tilt_wrench<S, NT>(G, xa.n, f, tau_n);
   const S h2 = S(0.5f) * h, h6 = h / S(6.0f), h3 = h / S(3.0f);
   S yq[4][4], ynu[4][6], sq[4];

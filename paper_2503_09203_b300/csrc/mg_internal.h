@@ -164,13 +164,13 @@ struct StepArgs {
 };
 static_assert(sizeof(StepArgs) == 152, "StepArgs layout");
 
-// Adjoint scratch: per recomputed substep and env one record of ADJ_REC
-// floats, the substep's start state (21 floats, the canonical record), its
-// right-hand side M nu_dot (6) and one pad float, so that a record is seven
-// 16-byte vectors; records are [record][slot] (AoS per env). Two buffers of
-// (ckpt_every K + 1) records alternate between the forward recompute and the
-// reverse pass.
-enum { ADJ_REC = 28 };
+// Adjoint scratch: per recomputed substep boundary and env one record of at
+// most ADJ_REC floats (the state q, nu, n and, at step boundaries, p, in
+// whole 16-byte vectors). Each class segment owns 2 (ckpt_every K + 1)
+// ADJ_REC floats per slot, from its first slot on: two buffers of one
+// checkpoint segment's records that alternate between the forward recompute
+// and the reverse pass.
+enum { ADJ_REC = 24 };
 inline size_t adjoint_scratch_floats(int64_t ckpt_every, int64_t K, int64_t n_slots) {
   return (size_t)2 * (size_t)(ckpt_every * K + 1) * ADJ_REC * (size_t)n_slots;
 }
@@ -188,7 +188,7 @@ struct AdjArgs {
   int32_t T;
   int32_t ckpt_every;
   const float* ckpt;          // [n_ckpt][21][n_slots]
-  float* scratch;             // [2][(ckpt_every*K+1)][n_slots][ADJ_REC]
+  float* scratch;             // per class segment: 2 (ckpt_every K + 1) ADJ_REC floats per slot
   const float* g_obs;         // [T][n_slots][13] or null
   const float* g_rew;         // [T][n_slots] or null
   const float* g_state_T;     // [n_slots][21] or null

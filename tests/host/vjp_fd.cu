@@ -1,5 +1,6 @@
 // Host check of the step kernel's vector-Jacobian product (vjp_from_tape in
-// mg_device.cuh, the arithmetic the adjoint kernel runs) in FP64: for random
+// mg_device.cuh on the tape that tape_from_states rebuilds from a substep's
+// start and end states: the arithmetic the adjoint kernel runs) in FP64: for random
 // states, commands, parameters and directions d, the product's
 // <vjp(lambda), d> must equal <lambda, J d> from central differences of the
 // forward substep (h = 1e-6), over the state, the commands and the added-mass
@@ -52,9 +53,14 @@ double run(std::mt19937_64& rng) {
   substep<double, NT, true>(x, in.c, Pb, Ac, h, &tp);
   St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
+  // As the reverse pass: the tape from the start and end states.
+  Tape<double, NT> tr;
+  tape_from_states<double, NT>(in.x, x, Pb, h, 1.0 / h, tr);
+  St<double, NT> xn = in.x;
+  for (int j = 0; j < NT; ++j) xn.n[j] = x.n[j];
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
-  if constexpr (RK) substep_rk4_vjp<double, NT>(in.x, in.c, Pb, Ac, h, lx, lc, g);
-  else vjp_from_tape<double, NT>(in.x, x.q, tp, in.c, Pb, Ac, h, lx, lc, g);
+  if constexpr (RK) substep_rk4_vjp<double, NT, Act<double>, Phys<double>, true, NoGen, true>(xn, in.c, Pb, Ac, h, lx, lc, g);
+  else vjp_from_tape<double, NT>(in.x, x.q, tr, in.c, Pb, Ac, h, lx, lc, g);
   // random direction
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
@@ -167,12 +173,15 @@ double run_pay(std::mt19937_64& rng) {
   substep<double, NT, true>(x, in.c, Pb, Ac, h, &tp);
   St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
-  // The reverse pass rebuilds the tape from the start state and rhs.
-  Tape<double, NT> tr; double q1[4];
-  tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
+  // The reverse pass rebuilds the tape from the start and end states.
+  Tape<double, NT> tr;
+  tape_from_states<double, NT>(in.x, x, Pb, h, 1.0 / h, tr);
+  St<double, NT> xn = in.x;
+  for (int j = 0; j < NT; ++j) xn.n[j] = x.n[j];
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
-  if constexpr (RK) substep_rk4_vjp<double, NT>(in.x, in.c, Pb, Ac, h, lx, lc, g);
-  else vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g);
+  if constexpr (RK)
+    substep_rk4_vjp<double, NT, Act<double>, PhysPay<double>, true, NoGen, true>(xn, in.c, Pb, Ac, h, lx, lc, g);
+  else vjp_from_tape<double, NT>(in.x, x.q, tr, in.c, Pb, Ac, h, lx, lc, g);
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
@@ -251,12 +260,14 @@ double run_gen(std::mt19937_64& rng) {
   substep<double, NT, true, Act<double>, Phys<double>, true, GenH>(x, in.c, Pb, Ac, h, &tp, G);
   St<double, NT> lam; for (int j = 0; j < 3; ++j) lam.p[j] = U(rng); for (int j = 0; j < 4; ++j) lam.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) lam.nu[j] = U(rng); for (int j = 0; j < NT; ++j) lam.n[j] = U(rng);
-  Tape<double, NT> tr; double q1[4];
-  tape_from_rhs<double, NT>(in.x, in.c, Pb, Ac, h, tp.rhs, tr, q1);
+  Tape<double, NT> tr;
+  tape_from_states<double, NT>(in.x, x, Pb, h, 1.0 / h, tr);
+  St<double, NT> xn = in.x;
+  for (int j = 0; j < NT; ++j) xn.n[j] = x.n[j];
   St<double, NT> lx = lam; double lc[NT] = {}; HydroGrad<double> g{};
   if constexpr (RK)
-    substep_rk4_vjp<double, NT, Act<double>, Phys<double>, true, GenH>(in.x, in.c, Pb, Ac, h, lx, lc, g, G);
-  else vjp_from_tape<double, NT>(in.x, q1, tr, in.c, Pb, Ac, h, lx, lc, g, G);
+    substep_rk4_vjp<double, NT, Act<double>, Phys<double>, true, GenH, true>(xn, in.c, Pb, Ac, h, lx, lc, g, G);
+  else vjp_from_tape<double, NT>(in.x, x.q, tr, in.c, Pb, Ac, h, lx, lc, g, G);
   In<NT> d;
   for (int j = 0; j < 3; ++j) d.x.p[j] = U(rng); for (int j = 0; j < 4; ++j) d.x.q[j] = U(rng);
   for (int j = 0; j < 6; ++j) d.x.nu[j] = U(rng); for (int j = 0; j < NT; ++j) d.x.n[j] = U(rng);
