@@ -15,17 +15,18 @@ namespace mg {
 // launch per class with the class tables as the kernel parameter
 // (constant-bank operands in the vector-Jacobian product).
 //
-// The reverse pass walks the checkpoint segments from the last to the first.
-// Warps 2-3 (the producer) recompute segment s - 1 from its checkpoint while
-// warps 0-1 (the consumer) run the vector-Jacobian products of segment s, so
-// the forward recompute leaves the consumer's dependent chain. The producer
+// The reverse pass walks the rollout in units (a checkpoint segment, or a
+// part of one: AdjUnit) from the last to the first. Warps 2-3 (the producer)
+// recompute unit u - 1 from its segment's checkpoint while warps 0-1 (the
+// consumer) run the vector-Jacobian products of unit u, so the forward
+// recompute leaves the consumer's dependent chain. The producer
 // stores the state at every substep boundary (q, nu, n, and p at step
 // boundaries: the records of Rec<NT>); the consumer rebuilds a substep's tape
 // from the records of its start and end (the end gives the new actuator
 // states, the new velocity and so M^-1 rhs, and the end attitude; R, the
 // current, the relative velocity and the quaternion update are a few dozen
 // operations) and applies its VJP. Two buffers per class segment alternate
-// between the warps, with one block barrier per segment. Each consumer lane
+// between the warps, with one block barrier per unit. Each consumer lane
 // prefetches its next records (and the next step's cotangents and actions)
 // into shared memory by cp.async while it computes the current
 // substep; record copies go through L2 only (the producer wrote them).
@@ -230,31 +231,57 @@ __device__ __forceinline__ int64_t rec_plane(int tl, int k, int K) {
   return (int64_t)tl * (Rec<NT>::ST + (K - 1) * Rec<NT>::IN) + (k ? Rec<NT>::ST + (k - 1) * Rec<NT>::IN : 0);
 }
 
-// Producer: recompute segment s from its checkpoint into the records of
-// buffer `buf` (the states at every substep boundary).
+// Reverse units: checkpoint segment s (steps [s c, (s + 1) c), c =
+// ckpt_every) splits into units of unit_steps steps; unit q (in time order)
+// covers steps [t0, t1) of segment s.
+struct AdjUnit {
+  int s, t0, t1;
+};
+__device__ __forceinline__ int adj_units(const AdjArgs& a) {
+  const int c = a.ckpt_every, L = a.unit_steps;
+  const int n_seg = (a.T + c - 1) / c, per_seg = (c + L - 1) / L;
+  return (n_seg - 1) * per_seg + (a.T - (n_seg - 1) * c + L - 1) / L;
+}
+__device__ __forceinline__ AdjUnit adj_unit(const AdjArgs& a, int q) {
+  const int c = a.ckpt_every, L = a.unit_steps, per_seg = (c + L - 1) / L;
+  AdjUnit r;
+  r.s = q / per_seg;
+  const int u = q - r.s * per_seg;
+  r.t0 = r.s * c + u * L;
+  r.t1 = min(min(r.t0 + L, (r.s + 1) * c), a.T);
+  return r;
+}
+
+// Producer: recompute unit `un` from its segment's checkpoint (steps before
+// the unit without records) into the records of buffer `buf` (the states at
+// every substep boundary of the unit).
 template <int NT, bool PAY, int VAR, typename ActT, typename GenT>
 __device__ __forceinline__ void adj_produce(const AdjArgs& a, const AdjSeg& sd, const ActT& A, const GenT& G,
-                                            const Phys<float>& P, unsigned p_base, int64_t i, int s, float* buf) {
+                                            const Phys<float>& P, unsigned p_base, int64_t i, const AdjUnit& un,
+                                            float* buf) {
   const int64_t ns = a.n_slots, slot = sd.slot_off + i;
-  const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
+  const int t0 = un.t0, t1 = un.t1;
   St<float, NT> x;
-  ld21<NT>(a.ckpt + (int64_t)s * 21 * ns + slot, ns, x);
+  ld21<NT>(a.ckpt + (int64_t)un.s * 21 * ns + slot, ns, x);
   const int64_t step4 = 4 * sd.n4;   // floats per vector plane
   float* rs = buf + rec_in_plane(i, Rec<NT>::ST);
   float* ri = buf + rec_in_plane(i, Rec<NT>::IN);
   int64_t plane = 0;                  // floats to the current record's plane
-  for (int t = t0; t < t1; ++t) {
+  for (int t = un.s * a.ckpt_every; t < t1; ++t) {
     float raw[NT], c[NT];
     load_actions<NT>(a.actions + (int64_t)t * a.act_stride + sd.act_off + i * NT, raw);
 #pragma unroll
     for (int q = 0; q < NT; ++q) c[q] = clamp1(raw[q]);
+    const bool rec = t >= t0;
     for (int k = 0; k < sd.K; ++k) {
-      if (k == 0) {
-        store_record<NT, true>(rs + plane, x);
-        plane += Rec<NT>::ST * step4;
-      } else {
-        store_record<NT, false>(ri + plane, x);
-        plane += Rec<NT>::IN * step4;
+      if (rec) {
+        if (k == 0) {
+          store_record<NT, true>(rs + plane, x);
+          plane += Rec<NT>::ST * step4;
+        } else {
+          store_record<NT, false>(ri + plane, x);
+          plane += Rec<NT>::IN * step4;
+        }
       }
       if constexpr (VAR == 2) {
         if constexpr (PAY) {
@@ -305,9 +332,10 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
     if (valid) load_phys(a.planes, ns, slot, P);
   }
   const int K = sd.K;
-  const int n_seg = (a.T + a.ckpt_every - 1) / a.ckpt_every;
-  // The segment's two buffers, in its share of the scratch.
-  const int64_t buf_floats = rec_plane<NT>(a.ckpt_every, 0, K) * 4 * sd.n4 + Rec<NT>::ST * 4 * sd.n4;
+  const int n_units = adj_units(a);
+  // The class segment's two buffers (one reverse unit each), in its share of
+  // the scratch.
+  const int64_t buf_floats = rec_plane<NT>(a.unit_steps, 0, K) * 4 * sd.n4 + Rec<NT>::ST * 4 * sd.n4;
   float* const seg_scratch = a.scratch + (int64_t)2 * (a.ckpt_every * K + 1) * ADJ_REC * sd.slot_off;
   const int64_t step4 = 4 * sd.n4;
   const int64_t off_st = rec_in_plane(i, Rec<NT>::ST), off_in = rec_in_plane(i, Rec<NT>::IN);
@@ -343,12 +371,13 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
   }
   float tgt[3] = {tg.x, tg.y, tg.z};
 
-  for (int it = 0; it <= n_seg; ++it) {
-    if (role == 1 && it < n_seg && valid)
-      adj_produce<NT, PAY, VAR>(a, sd, A, G, P, p_base, i, n_seg - 1 - it, seg_scratch + (int64_t)(it & 1) * buf_floats);
+  for (int it = 0; it <= n_units; ++it) {
+    if (role == 1 && it < n_units && valid)
+      adj_produce<NT, PAY, VAR>(a, sd, A, G, P, p_base, i, adj_unit(a, n_units - 1 - it),
+                                seg_scratch + (int64_t)(it & 1) * buf_floats);
     if (role == 0 && it >= 1 && valid) {
-      const int s = n_seg - it;
-      const int t0 = s * a.ckpt_every, t1 = min(a.T, t0 + a.ckpt_every);
+      const AdjUnit un = adj_unit(a, n_units - it);
+      const int t0 = un.t0, t1 = un.t1;
       const RecSrc<NT> rsrc{seg_scratch + (int64_t)((it - 1) & 1) * buf_floats, step4, off_st, off_in, K};
       const int n = t1 - t0;
       int j = n * K;   // record of the segment's end state (j >= 1)
@@ -427,7 +456,7 @@ __device__ __forceinline__ void adjoint_env(const AdjArgs& a, const AdjSeg& sd, 
         }
       }
     }
-    // The producer's records of this round are complete and the consumer is
+    // The producer's records of this unit are complete and the consumer is
     // done with the buffer the producer fills next.
     __syncthreads();
   }

@@ -198,6 +198,8 @@ struct AdjArgs {
   float* g_state0;            // [n_slots][21] or null
   int32_t tile_envs;          // envs per tile (the launch's blocks cover a tile in tile_envs / blockDim parts)
   int32_t pay_plane;          // payload runs: first payload plane; 0: no payload
+  int32_t unit_steps;         // steps of one reverse unit (a checkpoint segment splits into units)
+  int32_t pad1;
 };
 
 // Class nominal record for the reset kernel (FP64).
