@@ -21,12 +21,14 @@ from tests.helpers import rel_state_err
 pytestmark = pytest.mark.gpu
 
 
-def test_specialised_kernels_run_and_match_oracle_and_library_kernels():
+@pytest.mark.parametrize("K", [4, 1, 8])
+def test_specialised_kernels_run_and_match_oracle_and_library_kernels(K):
+    """At K = 4 (the workload), 1 and 8 substeps per step."""
     classes = vehicles.five_classes()
     classes[1] = dict(classes[1], deadzone=[0.25] * 4)        # a class with a dead zone among them
     counts = workloads.class_counts(1 << 20, 5)
     cfg = dict(vehicles.HOVER)
-    sim = B.Sim(classes, counts, dt=0.01, K=4, per_env_params=False, reset=cfg)
+    sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
     shape = B.mg_get_launch_shape(sim.handle)
     assert shape["specialised"] == 1 and shape["specialised_launches"] == 5, shape
     sim.reset(seed=81)
@@ -49,7 +51,7 @@ def test_specialised_kernels_run_and_match_oracle_and_library_kernels():
         out[spec] = (sim.get_state(), sim.obs.cpu().numpy().copy(), sim.reward.cpu().numpy().copy())
     slots = sim.slots_of_envs()[ids]
     envs, _ = oracle.reset(classes, workloads.env_classes(counts)[ids], cfg, 81, env_ids=ids)
-    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0[ids].astype(np.float64), a_s, 0.01, 4)
+    ref, o_ref, r_ref = oracle.rollout(classes, envs, s0[ids].astype(np.float64), a_s, 0.01, K)
     err = rel_state_err(out[1][0][ids], ref)
     assert err.max() <= 1e-5, (err.max(), int(ids[np.argmax(err)]))
     np.testing.assert_allclose(out[1][1][slots], o_ref[0], rtol=2e-5, atol=2e-5)
