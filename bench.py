@@ -49,19 +49,24 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "step_kernel_dram_hover_1M_K4.json")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "step_kernel_dram_hover_K4.json")
 
 
 def profiled_traffic(E, K):
     """DRAM bytes (read + write) per step of the workload, from the committed
-    machine-readable ncu record, if it measured these kernel sources at this
-    workload; else None. Returns (bytes per step, record)."""
+    machine-readable ncu record of these kernel sources: bytes per env-step
+    measured on smaller batches of the same launches (each larger than L2, the
+    bytes per env-step equal at the sizes measured), times E; None if the
+    record measured other sources, another K, or batches whose bytes per
+    env-step disagree. Returns (bytes per step, record)."""
     if not os.path.exists(TRAFFIC_RECORD):
         return None, None
     rec = json.load(open(TRAFFIC_RECORD))
-    if rec.get("source_sha") != kernel_sha() or rec.get("envs") != E or rec.get("K") != K:
+    if rec.get("source_sha") != kernel_sha() or rec.get("K") != K or not rec.get("proportional"):
         return None, rec
-    return float(rec["dram_bytes_per_step"]), rec
+    if E < max(rec["envs_measured"]):
+        return None, rec
+    return float(rec["dram_bytes_per_env_step"]) * E, rec
 
 
 def num_sms() -> int:
@@ -739,8 +744,10 @@ def main():
                 "peak_src": f"2 x 128 FP32 lanes x {num_sms()} SMs x max SM clock"}
     traffic, trec = profiled_traffic(E, K)
     roof["traffic"] = traffic
-    roof["traffic_note"] = (f"DRAM read+write bytes per step, difference of two ncu range replays of 2 and 6 "
-                            f"consecutive steps ({trec['launches_per_step']} launches a step, write-backs included): "
+    roof["traffic_note"] = (f"DRAM read+write bytes per step: bytes per env-step from ncu range replays of 2 and "
+                            f"6 consecutive steps (differenced; write-backs included) at "
+                            f"{' and '.join(str(e) for e in trec['envs_measured'])} envs, the same launches "
+                            f"({trec['launches_per_step']} a step), times {E} envs: "
                             f"{os.path.relpath(TRAFFIC_RECORD, ROOT)}"
                             if traffic else "null: no ncu record of these kernel sources at this workload")
     shape = B.mg_get_launch_shape(sim.handle)
