@@ -77,6 +77,28 @@ def test_flop_count_is_host_only_and_sane(lib):
     assert e.value.code == B.MG_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("nt", range(1, 9))
+def test_flop_count_equals_hand_count(lib, nt):
+    """mg_count_flops against a count by hand of the substep and observation
+    as the kernels write them (add, sub, mul = 1, a fused multiply-add 2,
+    reciprocal square root 1; compare, abs, negate 0):
+    rotor lag 3 and thrust k n|n| 2 per thruster, allocation 6 (2 NT - 1);
+    R(q) from doubled components 27; body right-hand side 100 (I w 3, a1 / m v
+    + a1 / A_a w + I w 15, three cross products 27, damping 18, W - B 1, B r_b 3,
+    (B r_b) x e 9, linear rows 12, angular rows 12); velocity update
+    (h minv_j) rhs_j 18; position 21; attitude 41 (h/2 1, quaternion rate 20,
+    q + h/2 qdot 8, norm and reciprocal square root 8, scaling 4). The ocean
+    current adds R^T V_c and v - v_c (18), w x v_c (9) and A_l o (w x v_c) in
+    the linear rows (6). Observation: R(q) 27, p - p* 3, R^T d 15, sign 4,
+    |d|^2 5, |nu|^2 11, |c|^2 2 NT - 1, reward 4."""
+    sub_plain = 5 * nt + 6 * (2 * nt - 1) + 27 + 100 + 18 + 21 + 41
+    s0, o0 = B.mg_count_flops(nt, with_current=False)
+    s1, o1 = B.mg_count_flops(nt, with_current=True)
+    assert s0 == sub_plain == 17 * nt + 201
+    assert s1 == sub_plain + 18 + 9 + 6
+    assert o0 == o1 == 27 + 3 + 15 + 4 + 5 + 11 + (2 * nt - 1) + 4
+
+
 @pytest.mark.parametrize("bad", ["dt", "K", "n_thr", "rg", "counts", "per_env", "payload_per_env",
                                  "ckpt_every", "payload_range"])
 def test_create_rejects_bad_arguments_before_touching_the_device(lib, bad):
