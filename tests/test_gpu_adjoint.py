@@ -64,8 +64,12 @@ def gpu_gradients(sim, a, T, g_obs, g_rew, g_sT):
 
 
 @pytest.mark.parametrize("counts,T,K,ckpt", [([3, 2, 2, 3, 2], 27, 4, 10), ([4, 4, 4, 4, 4], 200, 4, 20),
-                                             ([5, 0, 3, 1, 2], 9, 1, 4)])
+                                             ([5, 0, 3, 1, 2], 9, 1, 4), ([2, 3, 2, 2, 3], 100, 2, 45)])
 def test_adjoint_matches_oracle_tangents(counts, T, K, ckpt):
+    """Cotangents on every observation and reward and on the final state. In
+    the last case checkpoints fall every 45 steps: each segment is reversed in
+    units of 15 steps recomputed from its checkpoint, the last segment 10 steps
+    long."""
     classes, sim, p, s0, a, nthr = setup(counts, T, K, ckpt)
     E = sim.n_envs
     rng = np.random.default_rng(3)
