@@ -99,7 +99,9 @@ struct PairHalf {
   float Vc[3];         // current (NED)
 };
 
-// PM: 0 class constants from kc; 1 per-env planes. PRE: rows carry k.
+// PM: 0 class constants from kc; 1 per-env planes. PRE: the host's rows
+// carry k (class-constant launches); per-env launches multiply their rows by
+// k here, once, so that every launch's substep takes f = n|n|.
 template <int NT, int PM, bool CURRENT>
 __global__ void __launch_bounds__(PAIR_BLK, 1)
     mg_pair_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ ClassK kc) {
@@ -156,7 +158,8 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
 #pragma unroll
-    for (int q = 0; q < NT; ++q) Q.rows[j][q] = hsel ? kc.alloc[3 + j][q] : kc.alloc[j][q];
+    for (int q = 0; q < NT; ++q)
+      Q.rows[j][q] = (hsel ? kc.alloc[3 + j][q] : kc.alloc[j][q]) * (PRE ? 1.0f : kc.kf[q]);
     Q.hminv[j] = h * (hsel ? minv6[3 + j] : minv6[j]);
     Q.M1[j] = hsel ? Ig[j] : m;
     Q.M2[j] = hsel ? A6[3 + j] : A6[j];
@@ -209,13 +212,13 @@ __global__ void __launch_bounds__(PAIR_BLK, 1)
         for (int q = 0; q < NT; ++q) {
           x.n[q] = x.n[q] + kc.alpha[q] * (c[q] - x.n[q]);
           const float an = fabsf(x.n[q]);
-          f[q] = (an < kc.dz[q]) ? 0.0f : (PRE ? x.n[q] * an : kc.kf[q] * x.n[q] * an);
+          f[q] = (an < kc.dz[q]) ? 0.0f : x.n[q] * an;
         }
       } else {
 #pragma unroll
         for (int q = 0; q < NT; ++q) {
           x.n[q] = x.n[q] + kc.alpha[q] * (c[q] - x.n[q]);
-          f[q] = PRE ? x.n[q] * fabsf(x.n[q]) : kc.kf[q] * x.n[q] * fabsf(x.n[q]);
+          f[q] = x.n[q] * fabsf(x.n[q]);
         }
       }
       float tau[3];
