@@ -237,10 +237,14 @@ def link_bound(h2d_bytes, d2h_bytes, steps=50):
 
 
 def time_steps(sim, acts, steps, warmup, stream):
-    """Device time of `steps` mg_step calls (events on the launching stream)."""
+    """Device time of `steps` mg_step calls (events on the launching stream).
+    The host thread spins first: it has just waited for the simulator's setup,
+    and a thread that waited launches several times slower for a while (a
+    1M-env step at K=1 or 4 then measures the host, about 74 us per call)."""
     import torch
     from paper_2503_09203_b300 import binding as B
     n_act = acts.shape[0]
+    spin(0.2)
     for i in range(warmup):
         B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
     e0 = torch.cuda.Event(enable_timing=True)
