@@ -238,18 +238,21 @@ def link_bound(h2d_bytes, d2h_bytes, steps=50):
 
 def time_steps(sim, acts, steps, warmup, stream):
     """Device time of `steps` mg_step calls (events on the launching stream).
-    The host thread spins first: it has just waited for the simulator's setup,
-    and a thread that waited launches several times slower for a while (a
-    1M-env step at K=1 or 4 then measures the host, about 74 us per call)."""
+    The first warm-up steps compile the class-specialised kernels of this K;
+    the host thread then spins and warms up again: a thread that has waited
+    (setup, compiles) launches several times slower for a while, and a 1M-env
+    step at K=1 or 4 would measure the host (about 75 us per call)."""
     import torch
     from paper_2503_09203_b300 import binding as B
     n_act = acts.shape[0]
-    spin(0.2)
     for i in range(warmup):
+        B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
+    torch.cuda.synchronize()
+    spin(0.3)
+    for i in range(max(warmup, 100)):   # the slow launches last about 100 calls
         B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
     e0.record(stream)
     for i in range(steps):
         B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
