@@ -236,12 +236,14 @@ def link_bound(h2d_bytes, d2h_bytes, steps=50):
     return (time.perf_counter() - t0) / steps
 
 
-def time_steps(sim, acts, steps, warmup, stream):
-    """Device time of `steps` mg_step calls (events on the launching stream).
+def time_steps(sim, acts, steps, warmup, stream, repeats=1):
+    """Device time of `steps` mg_step calls (events on the launching stream);
+    with repeats > 1 the fastest of that many consecutive timed regions.
     The first warm-up steps compile the class-specialised kernels of this K;
     the host thread then spins and warms up again: a thread that has waited
-    (setup, compiles) launches several times slower for a while, and a 1M-env
-    step at K=1 or 4 would measure the host (about 75 us per call)."""
+    (setup, compiles) launches several times slower for a while, and a short
+    step would measure the host (a 1M-env step at K=1: about 75 us per call
+    against 46 us on the device)."""
     import torch
     from paper_2503_09203_b300 import binding as B
     n_act = acts.shape[0]
@@ -251,14 +253,18 @@ def time_steps(sim, acts, steps, warmup, stream):
     spin(0.3)
     for i in range(max(warmup, 100)):   # the slow launches last about 100 calls
         B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(steps):
-        B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
-    e1.record(stream)
-    e1.synchronize()
-    return e0.elapsed_time(e1) * 1e-3
+    best = None
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            B.mg_step(sim.handle, acts[i % n_act], 1, sim.obs, sim.reward, stream)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    return best
 
 
 def action_pool(sim, n_pool, seed):
@@ -309,7 +315,7 @@ def sweep(pk, stream, sizes=(65536, 131072, 262144, 524288, 1048576), Ks=(1, 4, 
             sim = B.Sim(classes, counts, dt=0.01, K=K, per_env_params=False, reset=cfg)
             sim.reset(seed=SEED)
             acts = action_pool(sim, 4, 7)
-            t = time_steps(sim, acts, steps, 10, stream)
+            t = time_steps(sim, acts, steps, 10, stream, repeats=3)
             bpe, fpe = algorithmic(classes, counts, K)
             v = E * steps / t
             alu_peak = fp32_peak(pk)
@@ -779,6 +785,8 @@ def main():
         sim.close()
         line["parity"] = parity_sample(classes, counts, K)
         line["sweep"] = sweep(pk, stream)
+        line["sweep_timing"] = ("per configuration: warm-up, the host thread kept busy, 100 more steps, then the "
+                                "fastest of 3 consecutive timed regions of 200 mg_step calls (CUDA events)")
         line["tracking"] = tracking_bench(pk, stream)
         line["payload"] = payload_bench(pk, stream)
         line["actuated"] = actuated_bench(pk, stream)
