@@ -812,6 +812,11 @@ static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
       if (h.n_tiles > 0) p.groups.push_back(h);
     }
   }
+  // Launches one after the other: the heaviest classes first, so that the
+  // launch whose tail ends the step (the next step's first launch waits for
+  // it) has the shortest tiles.
+  if (!p.cores && split)
+    std::stable_sort(p.groups.begin(), p.groups.end(), [](const Group& x, const Group& y) { return x.nt > y.nt; });
   const size_t n = p.groups.size();
   if (!p.cores || split) p.grid.assign(n, 1);
   p.carve_max.assign(n, 0);
