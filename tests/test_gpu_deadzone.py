@@ -96,11 +96,14 @@ def straddling_rotors(rng, classes, ec, n_envs):
     return n0, cmd
 
 
-def one_step_case(classes, counts, per_env, ids, seed):
+def one_step_case(classes, counts, per_env, ids, seed, specialised=1):
     """Step the sampled envs once from straddling rotor states; return the GPU
-    and oracle states, observations and rewards, and the rotor decisions."""
+    and oracle states, observations and rewards, and the rotor decisions.
+    specialised=0: the library's kernels instead of the class-specialised ones."""
     reset = dict(vehicles.HOVER_DR if per_env else vehicles.HOVER)
     sim = B.Sim(classes, counts, dt=DT, K=K, per_env_params=per_env, reset=reset)
+    if not specialised:
+        B.mg_set_launch_shape(sim.handle, 1, 0, 0)
     sim.reset(seed=seed)
     ec_all = workloads.env_classes(counts)
     ec = ec_all[ids]
@@ -134,16 +137,17 @@ def sample_ids(counts, n, seed):
     return np.unique(np.concatenate([ids, [0, E - 1], b[:-1], b[:-1] - 1]).clip(0, E - 1))
 
 
-@pytest.mark.parametrize("per_env,counts,launches", [
-    (False, [300001, 3, 240001, 5, 9], 5),   # one launch per class, tables as the kernel parameter
-    (False, [20001, 3, 15001, 5, 9], 3),     # groups side by side, tables in shared memory
-    (True, [300001, 3, 240001, 5, 9], 5),    # per-env parameters, one launch per class
-    (True, [301, 7, 141, 9, 65], 3),         # per-env parameters, side by side
+@pytest.mark.parametrize("per_env,counts,launches,spec", [
+    (False, [300001, 3, 240001, 5, 9], 5, 1),   # one launch per class, class-specialised kernels (tables as literals)
+    (False, [300001, 3, 240001, 5, 9], 5, 0),   # one launch per class, library kernels (tables as the kernel parameter)
+    (False, [20001, 3, 15001, 5, 9], 3, 1),     # groups side by side, tables in shared memory
+    (True, [300001, 3, 240001, 5, 9], 5, 1),    # per-env parameters, one launch per class
+    (True, [301, 7, 141, 9, 65], 3, 1),         # per-env parameters, side by side
 ])
-def test_dead_zone_one_step_matches_oracle(per_env, counts, launches):
+def test_dead_zone_one_step_matches_oracle(per_env, counts, launches, spec):
     classes = dz_classes()
     ids = sample_ids(counts, 768, 17)
-    r = one_step_case(classes, counts, per_env, ids, seed=21 + int(per_env))
+    r = one_step_case(classes, counts, per_env, ids, seed=21 + int(per_env), specialised=spec)
     assert r["launches"] == launches
     err = rel_state_err(r["gpu"], r["ref"])
     assert err.max() <= ONE_STEP_TOL, (err.max(), int(ids[np.argmax(err)]))
