@@ -38,12 +38,14 @@ SEED = 0x4D47
 
 def kernel_sha() -> str:
     """Hash of the sources that define the step kernel (the profile summaries
-    record the one they measured; runtime and serving code are not part of it)."""
+    record the one they measured; runtime and serving code are not part of it):
+    its headers and instantiations, and mg_jit.cpp, which compiles its
+    class-specialised form and chooses that form's launch bounds."""
     import glob
     import hashlib
     csrc = os.path.join(ROOT, "paper_2503_09203_b300", "csrc")
     h = hashlib.sha256()
-    for f in sorted([os.path.join(csrc, n) for n in ("mg_step.cuh", "mg_device.cuh", "mg_internal.h")] +
+    for f in sorted([os.path.join(csrc, n) for n in ("mg_step.cuh", "mg_device.cuh", "mg_internal.h", "mg_jit.cpp")] +
                     glob.glob(os.path.join(csrc, "mg_step_pm*.cu")) + glob.glob(os.path.join(ROOT, "include", "*.h"))):
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]

@@ -129,8 +129,9 @@ std::string kernel_name(Kind kind, int nt, bool ms) {
          ", mg::JitLit>";
 }
 
-// Compile and load one specialised kernel (caller holds g_mu).
-void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch) {
+// Compile and load one specialised kernel (caller holds g_mu). Step kernels
+// are compiled for min_blocks resident blocks per SM (their launch bounds).
+void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int min_blocks) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) { e.failed = true; e.err = "NVRTC not available"; return; }
   const std::string src = class_source(k, kind == ADJOINT ? "mg_adjoint.cuh" : "mg_step.cuh");
@@ -142,8 +143,9 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch) {
   const std::string name = kernel_name(kind, nt, ms);
   n.add_name(prog, name.c_str());
   const std::string arch_opt = "--gpu-architecture=sm_" + std::to_string(arch) + "a";
-  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "-default-device", "-lineinfo"};
-  const nvrtcResult rc = n.compile(prog, 4, opts);
+  const std::string blocks_opt = "-DMG_KSTEP_MIN_BLOCKS=" + std::to_string(min_blocks);
+  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "-default-device", "-lineinfo", blocks_opt.c_str()};
+  const nvrtcResult rc = n.compile(prog, kind == ADJOINT ? 4 : 5, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t ls = 0;
     n.log_size(prog, &ls);
@@ -182,7 +184,7 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch) {
   }
 }
 
-const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, std::string* err) {
+const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, int min_blocks, std::string* err) {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) !=
                                                 cudaSuccess ||
@@ -194,10 +196,10 @@ const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, std::string*
   const int arch = major * 10 + minor;
   std::string key(reinterpret_cast<const char*>(&k), sizeof(k));
   key += ":" + std::to_string((int)kind) + ":" + std::to_string(dev) + ":" + std::to_string(arch) + ":" +
-         std::to_string(nt) + (ms ? ":ms" : ":1");
+         std::to_string(nt) + (ms ? ":ms" : ":1") + ":" + std::to_string(min_blocks);
   std::lock_guard<std::mutex> lk(g_mu);
   Entry& e = g_cache[key];
-  if (!e.kern && !e.failed) build(e, kind, k, nt, ms, arch);
+  if (!e.kern && !e.failed) build(e, kind, k, nt, ms, arch, min_blocks);
   if (e.failed) {
     if (err) *err = e.err;
     return nullptr;
@@ -207,16 +209,31 @@ const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, std::string*
 
 }  // namespace
 
+// Resident blocks per SM that the class-specialised step kernel of a launch
+// of n_tiles tiles at K substeps is compiled for. The literal class tables
+// bring these kernels to 89-95 registers at 5 blocks per SM (105-114 at 4,
+// the bound of the library's kernels), without spills: 5 blocks hide more of
+// the substep's dependency latency, but the persistent grid's blocks walk
+// fewer tiles. Measured, five classes with class constants (us per step, 4
+// -> 5 blocks): K=4 1M envs 58.3 -> 56.8, 917k 52.8 -> 50.9, 786k 47.7 ->
+// 46.6, 655k 39.45 -> 39.3, 524k 32.96 -> 33.23; K=8 1M 79.7 -> 79.55, 786k
+// 63.1 -> 62.2; K=1 1M 45.4 -> 45.9. So 5 where K >= 4 and the 5-block
+// grid's blocks walk at least 1.25 tiles each, else 4.
+int jit_step_min_blocks(int K, int n_tiles, int num_sms) {
+  return K >= 4 && 4 * (int64_t)n_tiles >= 5 * (int64_t)(5 * num_sms) ? 5 : 4;
+}
+
 // The class-specialised one-class propeller step kernel for class table k
-// (nt thrusters; ms: the multi-step instantiation) on the current device, or
-// null if it cannot be had (err says why).
-const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err) {
-  return jit_kernel(STEP, k, nt, ms, err);
+// (nt thrusters; ms: the multi-step instantiation; compiled for min_blocks
+// resident blocks per SM) on the current device, or null if it cannot be had
+// (err says why).
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int min_blocks, std::string* err) {
+  return jit_kernel(STEP, k, nt, ms, min_blocks, err);
 }
 
 // The class-specialised adjoint kernel for class table k (nt thrusters).
 const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err) {
-  return jit_kernel(ADJOINT, k, nt, false, err);
+  return jit_kernel(ADJOINT, k, nt, false, 0, err);
 }
 
 // Launch of a class-specialised kernel (same arguments and launch shape as

@@ -27,7 +27,8 @@ cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg,
                            cudaStream_t st, const void* jit_kernel);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
-const void* jit_step_kernel(const ClassK& k, int nt, bool ms, std::string* err);
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int min_blocks, std::string* err);
+int jit_step_min_blocks(int K, int n_tiles, int num_sms);
 const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err);
 cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st);
@@ -870,7 +871,7 @@ static const void* plan_jit(mg_sim* sim, mg_sim::Plan& p, size_t i, bool ms) {
   if (!p.jit_tried[v][i]) {
     p.jit_tried[v][i] = 1;
     std::string err;
-    const void* k = jit_step_kernel(p.kc[i], g.nt, ms, &err);
+    const void* k = jit_step_kernel(p.kc[i], g.nt, ms, jit_step_min_blocks(sim->cfg.K, g.n_tiles, sim->num_sms), &err);
     if (!k) sim->jit_err = err;
     int occ = 0;
     if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem(g.nt, 0, false)) !=
