@@ -35,7 +35,7 @@
 
 namespace mg {
 
-size_t step_kernel_smem(int nt, int pm, bool track);
+size_t step_kernel_smem_jit(int nt);
 
 namespace {
 
@@ -144,8 +144,11 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int 
   n.add_name(prog, name.c_str());
   const std::string arch_opt = "--gpu-architecture=sm_" + std::to_string(arch) + "a";
   const std::string blocks_opt = "-DMG_KSTEP_MIN_BLOCKS=" + std::to_string(min_blocks);
-  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "-default-device", "-lineinfo", blocks_opt.c_str()};
-  const nvrtcResult rc = n.compile(prog, kind == ADJOINT ? 4 : 5, opts);
+  // Step kernels alias each warp's observation tile into its stage buffer
+  // (a sixth block of every thruster count then fits an SM's shared memory).
+  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "-default-device", "-lineinfo", blocks_opt.c_str(),
+                        "-DMG_OBS_ALIAS=1"};
+  const nvrtcResult rc = n.compile(prog, kind == ADJOINT ? 4 : 6, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t ls = 0;
     n.log_size(prog, &ls);
@@ -174,7 +177,7 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int 
     return;
   }
   if (kind == ADJOINT) return;   // static shared memory only
-  const int smem = (int)step_kernel_smem(nt, 0, false);
+  const int smem = (int)step_kernel_smem_jit(nt);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -211,16 +214,19 @@ const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, int min_bloc
 
 // Resident blocks per SM that the class-specialised step kernel of a launch
 // of n_tiles tiles at K substeps is compiled for. The literal class tables
-// bring these kernels to 89-95 registers at 5 blocks per SM (105-114 at 4,
-// the bound of the library's kernels), without spills: 5 blocks hide more of
-// the substep's dependency latency, but the persistent grid's blocks walk
-// fewer tiles. Measured, five classes with class constants (us per step, 4
-// -> 5 blocks): K=4 1M envs 58.3 -> 56.8, 917k 52.8 -> 50.9, 786k 47.7 ->
-// 46.6, 655k 39.45 -> 39.3, 524k 32.96 -> 33.23; K=8 1M 79.7 -> 79.55, 786k
-// 63.1 -> 62.2; K=1 1M 45.4 -> 45.9. So 5 where K >= 4 and the 5-block
+// bring these kernels to 80 registers at a bound of 6 blocks per SM (105-114
+// at 4, the bound of the library's kernels), without spills, and with each
+// warp's observation tile aliased into its stage buffer six blocks of every
+// thruster count fit an SM's shared memory: more warps hide more of the
+// substep's dependency latency, but the persistent grid's blocks walk fewer
+// tiles. Measured, five classes with class constants (us per step, 4 blocks
+// -> 5 blocks -> 6 blocks with the aliased observation tile): K=4 1M envs
+// 58.3 -> 56.8 -> 54.8, 917k 52.8 -> 50.9 -> 51.1, 786k 47.7 -> 46.6 ->
+// 46.0, 655k 39.45 -> 39.3 -> 39.7, 524k 32.96 -> 33.23 (5); K=8 1M 79.7 ->
+// 79.55 -> 76.4; K=1 1M 45.4 -> 45.9 (5). So 6 where K >= 4 and the 6-block
 // grid's blocks walk at least 1.25 tiles each, else 4.
 int jit_step_min_blocks(int K, int n_tiles, int num_sms) {
-  return K >= 4 && 4 * (int64_t)n_tiles >= 5 * (int64_t)(5 * num_sms) ? 5 : 4;
+  return K >= 4 && 4 * (int64_t)n_tiles >= 5 * (int64_t)(6 * num_sms) ? 6 : 4;
 }
 
 // The class-specialised one-class propeller step kernel for class table k
@@ -243,7 +249,7 @@ cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& k
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = step_kernel_smem(nt, 0, false);
+  cfg.dynamicSmemBytes = step_kernel_smem_jit(nt);
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   int na = 0;

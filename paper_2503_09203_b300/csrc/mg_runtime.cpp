@@ -33,6 +33,7 @@ const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err);
 cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st);
 size_t step_kernel_smem(int nt, int pm, bool track);
+size_t step_kernel_smem_jit(int nt);
 }  // namespace mg
 
 namespace mg {
@@ -874,7 +875,7 @@ static const void* plan_jit(mg_sim* sim, mg_sim::Plan& p, size_t i, bool ms) {
     const void* k = jit_step_kernel(p.kc[i], g.nt, ms, jit_step_min_blocks(sim->cfg.K, g.n_tiles, sim->num_sms), &err);
     if (!k) sim->jit_err = err;
     int occ = 0;
-    if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem(g.nt, 0, false)) !=
+    if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem_jit(g.nt)) !=
                  cudaSuccess) {
       cudaGetLastError();
       occ = 0;
