@@ -445,20 +445,6 @@ size_t step_kernel_smem_jit(int nt) {
 #undef MG_S
 }
 
-// Dynamic shared memory of the step kernels of thruster count nt and
-// parameter source pm.
-size_t step_kernel_smem(int nt, int pm, bool track) {
-#define MG_S(N)                                     \
-  case N:                                           \
-    return pm == 0 ? step_smem<N, 0>(track)         \
-                   : (pm == 1 ? step_smem<N, 1>(track) : step_smem<N, 2>(track));
-  switch (nt) {
-    MG_S(1) MG_S(2) MG_S(3) MG_S(4) MG_S(5) MG_S(6) MG_S(7) MG_S(8)
-    default: return 0;
-  }
-#undef MG_S
-}
-
 // Resident blocks per SM of a step instantiation (kp: class tables as the
 // kernel parameter).
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm) {

@@ -32,7 +32,6 @@ int jit_step_min_blocks(int K, int n_tiles, int num_sms);
 const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err);
 cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st);
-size_t step_kernel_smem(int nt, int pm, bool track);
 size_t step_kernel_smem_jit(int nt);
 }  // namespace mg
 

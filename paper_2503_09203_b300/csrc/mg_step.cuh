@@ -450,11 +450,24 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 
 // Per-warp stage buffer: the warp's 32 envs of one tile. State planes (NF4
 // float4 planes, then REM float planes, 32 entries each), actions [32][NT],
-// target [32] float4. Each warp of a block owns two stage buffers and one
-// observation buffer [32][13] and runs its own copy pipeline.
+// target [32] float4. Each warp of a block owns two stage buffers and runs
+// its own copy pipeline. The observation tile [32][13] is a third buffer of
+// the warp, or (aliased) rows 0..12 per env of the tile's own stage buffer,
+// written once the tile's inputs are in registers (below the action slot and
+// the trajectory section); lane 0 then waits for the observation store to
+// read the buffer before refilling it. Aliased: the per-env propeller kernels
+// (measured at 1M envs, DR + current, K=4: 94.9 -> 91.7 us; 262k envs 31.05
+// -> 29.3 us: a fourth block then fits an SM's shared memory) and, with
+// MG_OBS_ALIAS, every kernel (the class-specialised kernels are compiled so);
+// not aliased: the others (no gain measured with class constants at 4
+// blocks per SM, tracking 70.4 -> 70.9 us, payload 126.7 -> 127.0 us).
 #ifndef MG_OBS_ALIAS
 #define MG_OBS_ALIAS 0
 #endif
+template <int PM, int VAR, bool TM>
+struct ObsAlias {
+  static constexpr bool value = MG_OBS_ALIAS || (PM == 1 && VAR == 0 && !TM);
+};
 constexpr int WENV = 32;
 constexpr int N_WARPS = STEP_BLK / WENV;
 template <int NT>
@@ -467,14 +480,10 @@ struct Stage {
   // Stage buffer and per-warp sizes (floats); smaller shared memory pays off,
   // so the trajectory section exists only in tracking runs.
   static __host__ __device__ constexpr int floats(bool track) { return TRJ_OFF + (track ? 12 * WENV : 0); }
-#if MG_OBS_ALIAS
-  // The observation tile reuses the tile's own stage buffer once its inputs
-  // are in registers (rows 0..12 per env lie below the trajectory section).
-  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track); }
-  static_assert(OBS <= TRJ_OFF, "observation tile must fit below the trajectory section");
-#else
-  static __host__ __device__ constexpr int warp_floats(bool track) { return 2 * floats(track) + OBS; }
-#endif
+  static __host__ __device__ constexpr int warp_floats(bool track, bool alias) {
+    return 2 * floats(track) + (alias ? 0 : OBS);
+  }
+  static_assert(OBS <= ACT_OFF, "an aliased observation tile lies below the action slot");
   static_assert((ACT_OFF % 4) == 0 && (TGT_OFF % 4) == 0 && (TRJ_OFF % 4) == 0 && (OBS % 4) == 0,
                 "16-byte aligned sections");
 };
@@ -917,7 +926,8 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   if constexpr (HAS_LIT) kc = &klit;
   extern __shared__ __align__(16) float s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0);
+  constexpr bool ALIAS = ObsAlias<PM, VAR, TM>::value;
+  const int fl = SG::floats(a.track != 0), wfl = SG::warp_floats(a.track != 0, ALIAS);
   float* const w_base = s_dyn + warp * wfl;
   float* const buf0 = w_base;
   float* const buf1 = w_base + fl;
@@ -984,10 +994,8 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       const int64_t ln = (int64_t)(tile_n - sn.tile_begin) * STEP_BLK;
       nvw_next = warp_envs(sn, ln, warp);
       if (lane == 0 && nvw_next > 0 && !failed && !(sn.flags & 2)) {
-#if MG_OBS_ALIAS
         // The buffer may still be the source of the previous tile's observation store.
-        bulk_wait_read0();
-#endif
+        if (ALIAS) bulk_wait_read0();
         fence_async_smem();
         issue_warp_loads<NT, PM>(a, sn, ln + warp * WENV, nvw_next, b ? buf0 : buf1, b ? full0 : full1);
       }
@@ -1025,7 +1033,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
       step_tile<NT, PM, VAR, KP, MS, PA>(a, kc, kg, sd, tile, smem_addr(s_act + (TM ? warp * SA_DIM : 0)),
                                  smem_addr(s_phys + (TM ? warp * PAR_DIM : 0)),
                                  smem_addr(s_gen + (TM && VAR ? warp * GEN_FLOATS : 0)), b ? buf1 : buf0,
-                                 MG_OBS_ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
+                                 ALIAS ? (b ? buf1 : buf0) : obs_sep, s_par, n_emit);
     if (PA && !failed && tt_next < a.n_tiles) {
       // This thread is done with its parameter column: bring in the next tile's.
       const int tile_n = a.tile_lo + tt_next;
@@ -1063,11 +1071,11 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
     default: return cudaErrorInvalidValue; \
   }
 
-// Dynamic shared memory of mg_step_kernel<NT, PM, *, *>.
-template <int NT, int PM>
+// Dynamic shared memory of mg_step_kernel<NT, PM, VAR, *, TM>.
+template <int NT, int PM, int VAR, bool TM>
 static size_t step_smem(bool track) {
   const int cols = PM == 2 ? PF_DIM : (PM == 1 ? PAR_DIM : 0);
-  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track) + cols * STEP_BLK);
+  return sizeof(float) * (N_WARPS * Stage<NT>::warp_floats(track, ObsAlias<PM, VAR, TM>::value) + cols * STEP_BLK);
 }
 
 template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>
@@ -1089,7 +1097,7 @@ static cudaError_t step_attrs() {
   const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
   if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   e = cudaFuncSetAttribute(step_fn<NT, PM, VAR, KP, TM, MS>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem<NT, PM>(true));
+                           (int)step_smem<NT, PM, VAR, TM>(true));
   if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
@@ -1103,7 +1111,7 @@ static cudaError_t step_attrs() {
 template <int NT, int PM, int VAR, bool KP, bool TM, bool MS = false>
 static cudaError_t launch_step_t(const StepArgs& a, const ClassK* kc, const ClassG* kg, int grid, bool dependent,
                                  bool shared_sm, cudaStream_t st) {
-  const size_t smem = step_smem<NT, PM>(a.track != 0);
+  const size_t smem = step_smem<NT, PM, VAR, TM>(a.track != 0);
   cudaError_t e = step_attrs<NT, PM, VAR, KP, TM, MS>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1213,7 +1221,7 @@ static cudaError_t occupancy_t(bool track, int* blocks_per_sm) {
   cudaError_t e = step_attrs<NT, PM, VAR, KP, TM, MS>();
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_fn<NT, PM, VAR, KP, TM, MS>(), STEP_BLK,
-                                                       step_smem<NT, PM>(track));
+                                                       step_smem<NT, PM, VAR, TM>(track));
 }
 
 template <int PM, int VAR, bool KP>
