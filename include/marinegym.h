@@ -422,10 +422,11 @@ typedef struct {
   int32_t lanes_per_env;    /* 1 or 2 */
   int32_t envs_per_block;   /* 128 / lanes_per_env (output only) */
   int32_t blocks_per_sm;    /* one-lane launches: resident blocks per SM (0: occupancy limit) */
-  int32_t specialised;      /* 1 (default): one-lane launches of one class with class-constant
-                               parameters (propellers, Euler, hover task) run a kernel compiled at
-                               run time (NVRTC) with that class's constants as literals, when NVRTC
-                               is available; 0: the kernels built with the library */
+  int32_t specialised;      /* 1 (default): one-lane launches of one class (propellers, Euler,
+                               hover task; class-constant or per-env parameters, no payload) run a
+                               kernel compiled at run time (NVRTC) with that class's constants
+                               (per-env runs: its actuator tables) as literals, when NVRTC is
+                               available; 0: the kernels built with the library */
   double us_per_step;       /* mg_autotune: the chosen shape's measured time per step (output only) */
   int32_t specialised_launches; /* output: launches of one step that run specialised kernels */
   int32_t pad0;

@@ -35,7 +35,7 @@
 
 namespace mg {
 
-size_t step_kernel_smem_jit(int nt);
+size_t step_kernel_smem_jit(int nt, int pm);
 
 namespace {
 
@@ -123,15 +123,15 @@ std::string class_source(const ClassK& k, const char* header) {
 
 enum Kind { STEP = 0, ADJOINT = 1 };
 
-std::string kernel_name(Kind kind, int nt, bool ms) {
+std::string kernel_name(Kind kind, int nt, bool ms, int pm) {
   if (kind == ADJOINT) return "mg::mg_adjoint_kernel<" + std::to_string(nt) + ", false, mg::JitLit>";
-  return "mg::mg_step_kernel<" + std::to_string(nt) + ", 0, 0, true, false, " + (ms ? "true" : "false") +
-         ", mg::JitLit>";
+  return "mg::mg_step_kernel<" + std::to_string(nt) + ", " + std::to_string(pm) + ", 0, true, false, " +
+         (ms ? "true" : "false") + ", mg::JitLit>";
 }
 
 // Compile and load one specialised kernel (caller holds g_mu). Step kernels
 // are compiled for min_blocks resident blocks per SM (their launch bounds).
-void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int min_blocks) {
+void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int pm, int arch, int min_blocks) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) { e.failed = true; e.err = "NVRTC not available"; return; }
   const std::string src = class_source(k, kind == ADJOINT ? "mg_adjoint.cuh" : "mg_step.cuh");
@@ -140,7 +140,7 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int 
       NVRTC_SUCCESS) {
     e.failed = true; e.err = "nvrtcCreateProgram failed"; return;
   }
-  const std::string name = kernel_name(kind, nt, ms);
+  const std::string name = kernel_name(kind, nt, ms, pm);
   n.add_name(prog, name.c_str());
   const std::string arch_opt = "--gpu-architecture=sm_" + std::to_string(arch) + "a";
   const std::string blocks_opt = "-DMG_KSTEP_MIN_BLOCKS=" + std::to_string(min_blocks);
@@ -177,7 +177,7 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int 
     return;
   }
   if (kind == ADJOINT) return;   // static shared memory only
-  const int smem = (int)step_kernel_smem_jit(nt);
+  const int smem = (int)step_kernel_smem_jit(nt, pm);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -187,7 +187,7 @@ void build(Entry& e, Kind kind, const ClassK& k, int nt, bool ms, int arch, int 
   }
 }
 
-const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, int min_blocks, std::string* err) {
+const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, int pm, int min_blocks, std::string* err) {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) !=
                                                 cudaSuccess ||
@@ -199,10 +199,10 @@ const void* jit_kernel(Kind kind, const ClassK& k, int nt, bool ms, int min_bloc
   const int arch = major * 10 + minor;
   std::string key(reinterpret_cast<const char*>(&k), sizeof(k));
   key += ":" + std::to_string((int)kind) + ":" + std::to_string(dev) + ":" + std::to_string(arch) + ":" +
-         std::to_string(nt) + (ms ? ":ms" : ":1") + ":" + std::to_string(min_blocks);
+         std::to_string(nt) + (ms ? ":ms" : ":1") + ":" + std::to_string(min_blocks) + ":pm" + std::to_string(pm);
   std::lock_guard<std::mutex> lk(g_mu);
   Entry& e = g_cache[key];
-  if (!e.kern && !e.failed) build(e, kind, k, nt, ms, arch, min_blocks);
+  if (!e.kern && !e.failed) build(e, kind, k, nt, ms, pm, arch, min_blocks);
   if (e.failed) {
     if (err) *err = e.err;
     return nullptr;
@@ -230,26 +230,27 @@ int jit_step_min_blocks(int K, int n_tiles, int num_sms) {
 }
 
 // The class-specialised one-class propeller step kernel for class table k
-// (nt thrusters; ms: the multi-step instantiation; compiled for min_blocks
-// resident blocks per SM) on the current device, or null if it cannot be had
-// (err says why).
-const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int min_blocks, std::string* err) {
-  return jit_kernel(STEP, k, nt, ms, min_blocks, err);
+// (nt thrusters; ms: the multi-step instantiation; pm 0: the class's physics
+// as literals too, 1: per-env physics from the parameter planes, the
+// actuator tables as literals; compiled for min_blocks resident blocks per
+// SM) on the current device, or null if it cannot be had (err says why).
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int pm, int min_blocks, std::string* err) {
+  return jit_kernel(STEP, k, nt, ms, pm, min_blocks, err);
 }
 
 // The class-specialised adjoint kernel for class table k (nt thrusters).
 const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err) {
-  return jit_kernel(ADJOINT, k, nt, false, 0, err);
+  return jit_kernel(ADJOINT, k, nt, false, 0, 0, err);
 }
 
 // Launch of a class-specialised kernel (same arguments and launch shape as
 // the kernel built with the library).
-cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
+cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int pm, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = step_kernel_smem_jit(nt);
+  cfg.dynamicSmemBytes = step_kernel_smem_jit(nt, pm);
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   int na = 0;

@@ -434,10 +434,12 @@ cudaError_t launch_step(const StepArgs& a, const ClassK* kc, const ClassG* kg, i
 
 // Dynamic shared memory of the class-specialised step kernels (compiled at
 // run time with the observation tile aliased into the stage buffer: two
-// stage buffers per warp, class constants, no trajectory section).
-size_t step_kernel_smem_jit(int nt) {
+// stage buffers per warp, no trajectory section; per-env parameters (pm 1)
+// add their shared-memory columns).
+size_t step_kernel_smem_jit(int nt, int pm) {
+  const size_t cols = pm == 1 ? sizeof(float) * PAR_DIM * STEP_BLK : 0;
 #define MG_S(N) \
-  case N: return sizeof(float) * N_WARPS * 2 * (size_t)Stage<N>::floats(false);
+  case N: return cols + sizeof(float) * N_WARPS * 2 * (size_t)Stage<N>::floats(false);
   switch (nt) {
     MG_S(1) MG_S(2) MG_S(3) MG_S(4) MG_S(5) MG_S(6) MG_S(7) MG_S(8)
     default: return 0;

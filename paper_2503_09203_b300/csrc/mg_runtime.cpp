@@ -27,12 +27,12 @@ cudaError_t launch_adjoint(const AdjArgs& a, const ClassK& kc, const ClassG* kg,
                            cudaStream_t st, const void* jit_kernel);
 cudaError_t step_kernel_occupancy(int nt, int pm, int var, bool kp, bool track, int* blocks_per_sm);
 cudaError_t launch_pair(const StepArgs& a, const ClassK& kc, int nt, bool dependent, cudaStream_t st);
-const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int min_blocks, std::string* err);
+const void* jit_step_kernel(const ClassK& k, int nt, bool ms, int pm, int min_blocks, std::string* err);
 int jit_step_min_blocks(int K, int n_tiles, int num_sms);
 const void* jit_adjoint_kernel(const ClassK& k, int nt, std::string* err);
-cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int grid, bool dependent,
+cudaError_t launch_step_jit(const void* kern, const StepArgs& a, const ClassK& kc, int nt, int pm, int grid, bool dependent,
                             bool shared_sm, cudaStream_t st);
-size_t step_kernel_smem_jit(int nt);
+size_t step_kernel_smem_jit(int nt, int pm);
 }  // namespace mg
 
 namespace mg {
@@ -855,10 +855,10 @@ static const mg_sim::Plan& step_plan(mg_sim* sim, bool ms) {
 }
 
 // Whether launch i of a plan may run a class-specialised kernel: one class
-// with class-constant parameters, propellers with the Euler substep, the
-// hover task.
+// with class-constant or per-env parameters (no payload), propellers with
+// the Euler substep, the hover task.
 static bool jit_eligible(const mg_sim* sim, const Group& g) {
-  return sim->specialise && g.cls >= 0 && g.var == 0 && param_mode(sim) == 0 && sim->cfg.task == 0;
+  return sim->specialise && g.cls >= 0 && g.var == 0 && param_mode(sim) <= 1 && sim->cfg.task == 0;
 }
 
 // The class-specialised kernel of launch i (single- or multi-step
@@ -871,10 +871,14 @@ static const void* plan_jit(mg_sim* sim, mg_sim::Plan& p, size_t i, bool ms) {
   if (!p.jit_tried[v][i]) {
     p.jit_tried[v][i] = 1;
     std::string err;
-    const void* k = jit_step_kernel(p.kc[i], g.nt, ms, jit_step_min_blocks(sim->cfg.K, g.n_tiles, sim->num_sms), &err);
+    // Per-env kernels keep the 4-block bound (their parameter columns fill
+    // shared memory at 4 blocks per SM).
+    const int pm = param_mode(sim);
+    const int mb = pm == 0 ? jit_step_min_blocks(sim->cfg.K, g.n_tiles, sim->num_sms) : 4;
+    const void* k = jit_step_kernel(p.kc[i], g.nt, ms, pm, mb, &err);
     if (!k) sim->jit_err = err;
     int occ = 0;
-    if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem_jit(g.nt)) !=
+    if (k && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 128, step_kernel_smem_jit(g.nt, pm)) !=
                  cudaSuccess) {
       cudaGetLastError();
       occ = 0;
@@ -929,7 +933,7 @@ static int launch_groups(mg_sim* sim, StepArgs a, cudaStream_t st) {
     if (sim->lanes == 2 && pair_eligible(sim, g, a))
       CK(launch_pair(a, p.kc[i], g.nt, !first || p.first_pdl, st));
     else if ((jk = plan_jit(sim, const_cast<mg_sim::Plan&>(p), i, ms)) != nullptr)
-      CK(launch_step_jit(jk, a, p.kc[i], g.nt, p.jit_grid[ms ? 1 : 0][i], !first || p.first_pdl, p.carve_max[i] != 0,
+      CK(launch_step_jit(jk, a, p.kc[i], g.nt, param_mode(sim), p.jit_grid[ms ? 1 : 0][i], !first || p.first_pdl, p.carve_max[i] != 0,
                          st));
     else
       CK(launch_step(a, g.cls >= 0 ? &p.kc[i] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt, g.var,
@@ -1116,7 +1120,7 @@ int mg_step_host(mg_sim* sim, const float* actions_host, int32_t n_steps, float*
     const bool ms = g.var == 0 && n_steps > 1;
     const void* jk = plan_jit(sim, const_cast<mg_sim::Plan&>(plan), ch.g, ms);
     if (jk)
-      CK(launch_step_jit(jk, a, plan.kc[ch.g], g.nt, std::max(1, std::min(ch.nt, plan.jit_grid[ms ? 1 : 0][ch.g])), false,
+      CK(launch_step_jit(jk, a, plan.kc[ch.g], g.nt, param_mode(sim), std::max(1, std::min(ch.nt, plan.jit_grid[ms ? 1 : 0][ch.g])), false,
                          carveout_max(sim, g, false), st));
     else
       CK(launch_step(a, g.cls >= 0 ? &plan.kc[ch.g] : nullptr, g.cls >= 0 ? &sim->h_gen[g.cls] : nullptr, g.nt,

@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(STEP_BLK, (StepMinBlocks<PM, VAR, KP, TM>::val
   using SG = Stage<NT>;
   constexpr bool PA = PM == 1 && !TM && MG_PAR_ASYNC;
   constexpr bool HAS_LIT = !tt::is_same<LIT, NoLit>::value;
-  static_assert(!HAS_LIT || (KP && PM == 0 && VAR == 0 && !TM), "literal class constants: one-class propeller launches");
+  static_assert(!HAS_LIT || (KP && PM <= 1 && VAR == 0 && !TM), "literal class constants: one-class propeller launches");
   const ClassK* kc = nullptr;
   const ClassG* kg = nullptr;
   if constexpr (KP && VAR == 0) kc = &kp;
