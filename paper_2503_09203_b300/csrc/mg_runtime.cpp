@@ -68,7 +68,7 @@ struct mg_sim {
   int32_t threads = 128;
   int32_t blocks_per_sm = 0;   // persistent blocks per SM (0: occupancy limit)
   int32_t lanes = 1;           // lanes per env of eligible launches (1 or 2)
-  int32_t specialise = 1;      // class-specialised kernels for class-constant launches (when available)
+  int32_t specialise = 1;      // class-specialised kernels for one-class propeller launches (when available)
   int32_t num_sms = 148;
   int32_t n_tiles = 0, n_segs = 0;
   double h = 0.0;

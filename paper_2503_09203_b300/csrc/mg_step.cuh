@@ -893,11 +893,12 @@ struct StepMinBlocks {
 struct NoClassK {};
 
 // Class constants known when the kernel is compiled: the class-specialised
-// step kernels that the library compiles at run time (NVRTC) for
-// class-constant launches take a type whose make() returns the class's
-// ClassK, so that the arithmetic sees literals (zero allocation entries, a
-// zero restoring arm, W = B drop out). NoLit: the constants come from the
-// kernel parameter.
+// step kernels that the library compiles at run time (NVRTC) for one-class
+// propeller launches take a type whose make() returns the class's ClassK,
+// so that the arithmetic sees literals (zero allocation entries and, with
+// class-constant physics, a zero restoring arm and W = B drop out; per-env
+// launches take only the actuator tables from it). NoLit: the constants come
+// from the kernel parameter.
 struct NoLit {
   MG_HD static constexpr ClassK make() { return ClassK{}; }
 };
